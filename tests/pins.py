@@ -1,0 +1,333 @@
+"""Pins for the FP64 oracle: checks against things other than the oracle itself.
+
+Each ``pin_*`` takes an oracle library handle (``oracle.load()`` or a build with
+a planted mistake) and raises AssertionError when the oracle disagrees with:
+  * brute-force pure-Python decoding of the PLINK 2-bit layout (Sec. 2.3.2);
+  * exact rational statistics (fractions.Fraction) and numpy's nan-aware
+    mean / std (ddof=1) for the per-SNP u, v vectors (Sec. 2.3.2);
+  * numpy dense products for the gradient (Eq. normal_grad) and the
+    standardisation identity X_st b = X diag(v) b - 1 u^T diag(v) b (Sec. 2.3.2);
+  * numpy lexsort for the projection P_{S_k} (Eq. ihta);
+  * closed forms of IHT (Sec. 2.2, 2.3.1): single-marker regression at k = 1,
+    least squares on the support at a fixed point (Eq. normal_equations), OLS
+    when k = p < n, exact recovery of noiseless sparse models, brute force over
+    all k-subsets, a monotone objective, |supp beta| <= k, and the sign
+    symmetry of allele orientation.
+"""
+from __future__ import annotations
+
+import itertools
+from fractions import Fraction
+
+import numpy as np
+
+import oracle
+
+# --------------------------------------------------------------------------
+# independent references
+
+
+def py_decode(body: np.ndarray, n: int, p: int, rb: int) -> np.ndarray:
+    """Pure-Python loop decode: sample i of SNP j = bits 2(i%4)..+1 of byte i//4."""
+    out = np.empty((p, n), dtype=np.int8)
+    b = bytes(body)
+    for j in range(p):
+        for i in range(n):
+            byte = b[j * rb + i // 4]
+            out[j, i] = (byte >> (2 * (i % 4))) & 3
+    return out
+
+
+DOSE = {0: 0.0, 2: 1.0, 3: 2.0}
+
+
+def np_dosage(codes: np.ndarray) -> np.ndarray:
+    """Dosage with NaN for missing (code 0 -> 0, 2 -> 1, 3 -> 2, 1 -> NaN)."""
+    d = np.full(codes.shape, np.nan)
+    for c, x in DOSE.items():
+        d[codes == c] = x
+    return d
+
+
+def np_Z(codes: np.ndarray, rows=None) -> np.ndarray:
+    """Standardised matrix Z[rows, snps] via numpy nanmean / nanstd(ddof=1); missing -> 0."""
+    d = np_dosage(codes)
+    if rows is not None:
+        d = d[:, rows]
+    with np.errstate(invalid="ignore", divide="ignore"):
+        m = np.nanmean(d, axis=1, keepdims=True)
+        s = np.nanstd(d, axis=1, ddof=1, keepdims=True)
+        z = (d - m) / s
+    z[~np.isfinite(z)] = 0.0
+    z[(s[:, 0] == 0) | ~np.isfinite(s[:, 0]), :] = 0.0
+    return z.T
+
+
+def random_geno(rng, n, p, miss=0.05, rb=None):
+    """Random .bed body with genotype frequencies varying per SNP."""
+    rb = (n + 3) // 4 if rb is None else rb
+    q = rng.uniform(0.05, 0.5, size=p)
+    codes = np.empty((p, n), dtype=np.int64)
+    for j in range(p):
+        pr = np.array([(1 - q[j]) ** 2, 2 * q[j] * (1 - q[j]), q[j] ** 2]) * (1 - miss)
+        codes[j] = rng.choice([0, 2, 3, 1], size=n, p=np.append(pr, miss))
+    body = np.zeros(p * rb, dtype=np.uint8)
+    for j in range(p):
+        for i in range(n):
+            body[j * rb + i // 4] |= codes[j, i] << (2 * (i % 4))
+    return oracle.Geno(body, n, p, rb), codes.astype(np.int8)
+
+
+def geno_from_codes(codes: np.ndarray) -> oracle.Geno:
+    p, n = codes.shape
+    rb = (n + 3) // 4
+    body = np.zeros(p * rb, dtype=np.uint8)
+    for j in range(p):
+        for i in range(n):
+            body[j * rb + i // 4] |= int(codes[j, i]) << (2 * (i % 4))
+    return oracle.Geno(body, n, p, rb)
+
+
+def lstsq_obj(Z, y, cols):
+    """Least-squares refit on the given columns: (coef, 1/2 ||y - Z_S coef||^2)."""
+    if len(cols) == 0:
+        return np.zeros(0), 0.5 * float(y @ y)
+    A = Z[:, list(cols)]
+    coef, *_ = np.linalg.lstsq(A, y, rcond=None)
+    res = y - A @ coef
+    return coef, 0.5 * float(res @ res)
+
+
+# --------------------------------------------------------------------------
+# pins
+
+
+def pin_decode(lib):
+    rng = np.random.default_rng(11)
+    for n in (1, 2, 3, 4, 5, 7, 13, 33):
+        for extra in (0, 5):
+            rb = (n + 3) // 4 + extra
+            p = 6
+            body = rng.integers(0, 256, size=p * rb, dtype=np.uint8)
+            got = oracle.decode(oracle.Geno(body, n, p, rb), lib=lib)
+            assert np.array_equal(got, py_decode(body, n, p, rb)), f"decode n={n} rb={rb}"
+
+
+def pin_counts_stats(lib):
+    rng = np.random.default_rng(12)
+    for n, miss in ((9, 0.1), (37, 0.02), (64, 0.3)):
+        G, codes = random_geno(rng, n, 25, miss=miss)
+        for rows in (None, np.sort(rng.choice(n, size=max(3, n // 2), replace=False))):
+            c, u, v = oracle.counts(G, rows, lib=lib)
+            sub = codes if rows is None else codes[:, rows]
+            want = np.stack([np.bincount(sub[j], minlength=4) for j in range(G.p)])
+            assert np.array_equal(c, want), "counts"
+            d = np_dosage(sub)
+            with np.errstate(invalid="ignore", divide="ignore"):
+                m = np.nanmean(d, axis=1)
+                s = np.nanstd(d, axis=1, ddof=1)
+            ok = np.isfinite(s) & (s > 0)
+            assert np.allclose(u[ok], m[ok], rtol=1e-14, atol=0), "mean u"
+            assert np.allclose(v[ok], 1.0 / s[ok], rtol=1e-13, atol=0), "inverse sd v"
+            assert np.all(v[~ok] == 0.0), "v = 0 for monomorphic columns"
+
+
+def pin_stats_exact(lib):
+    """u and v against exact rational arithmetic (v within 2 ulp of 1/sqrt(var))."""
+    codes = np.array([[0, 2, 3, 1, 2, 0, 3],      # mixed, one missing
+                      [3, 3, 3, 3, 1, 3, 3],      # monomorphic among observed -> v = 0
+                      [1, 1, 1, 1, 1, 1, 2],      # one observed call -> v = 0
+                      [2, 2, 0, 0, 3, 1, 1]], dtype=np.int8)
+    G = geno_from_codes(codes)
+    _, u, v = oracle.counts(G, lib=lib)
+    for j in range(codes.shape[0]):
+        xs = [Fraction(int(DOSE[c])) for c in codes[j] if c != 1]
+        m = sum(xs, Fraction(0)) / len(xs) if xs else Fraction(0)
+        assert u[j] == float(m), f"u[{j}]"
+        if len(xs) >= 2:
+            var = sum(((x - m) ** 2 for x in xs), Fraction(0)) / (len(xs) - 1)
+        else:
+            var = Fraction(0)
+        if var == 0:
+            assert v[j] == 0.0, f"v[{j}] should be 0"
+        else:
+            want = 1.0 / np.sqrt(float(var))
+            assert abs(v[j] - want) <= 4e-16 * want, f"v[{j}]"
+
+
+def pin_gradient(lib):
+    rng = np.random.default_rng(13)
+    for n, p in ((50, 30), (123, 17)):
+        G, codes = random_geno(rng, n, p, miss=0.05)
+        for rows in (None, np.sort(rng.choice(n, size=n - 7, replace=False))):
+            nr = n if rows is None else rows.size
+            r = rng.normal(size=nr)
+            g = oracle.gradient(G, r, rows, lib=lib)
+            Z = np_Z(codes, rows)
+            want = Z.T @ r
+            assert np.max(np.abs(g - want)) <= 1e-12 * np.max(np.abs(want)), "g = Z^T r"
+            # centring: a constant residual has zero gradient
+            g1 = oracle.gradient(G, np.ones(nr), rows, lib=lib)
+            assert np.max(np.abs(g1)) <= 1e-11, "columns centred"
+            # unit variance with the (n_obs - 1) denominator: z_j^T z_j = n_obs - 1
+            sub = codes if rows is None else codes[:, rows]
+            for j in range(0, p, 5):
+                gz = oracle.gradient(G, Z[:, j], rows, lib=lib)[j]
+                n_obs = int(np.sum(sub[j] != 1))
+                if np.any(Z[:, j] != 0):
+                    assert abs(gz - (n_obs - 1)) <= 1e-10 * n_obs, "z^T z = n_obs - 1"
+
+
+def pin_identity(lib):
+    """X_st b = X diag(v) b - 1 u^T diag(v) b on mean-imputed X (Sec. 2.3.2)."""
+    rng = np.random.default_rng(14)
+    G, codes = random_geno(rng, 71, 23, miss=0.08)
+    _, u, v = oracle.counts(G, lib=lib)
+    X = np_dosage(codes).T                       # n x p, NaN for missing
+    X = np.where(np.isnan(X), u[None, :], X)     # mean imputation
+    cols = np.array([0, 3, 4, 9, 22], dtype=np.int32)
+    b = rng.normal(size=cols.size)
+    want = X[:, cols] @ (v[cols] * b) - np.ones(G.n) * (u[cols] @ (v[cols] * b))
+    got = oracle.zmul(G, cols, b, lib=lib)
+    assert np.max(np.abs(got - want)) <= 1e-12 * (1 + np.max(np.abs(want))), "identity"
+    # and against the numpy-standardised matrix
+    Z = np_Z(codes)
+    assert np.allclose(got, Z[:, cols] @ b, rtol=1e-12, atol=1e-12), "zmul vs numpy"
+    # held-out rows with training statistics
+    tr = np.arange(0, G.n, 2)
+    te = np.arange(1, G.n, 2)
+    _, ut, vt = oracle.counts(G, tr, lib=lib)
+    got_te = oracle.zmul(G, cols, b, rows=te, u=ut, v=vt, lib=lib)
+    d = np_dosage(codes)[:, te]
+    zt = np.where(np.isnan(d), 0.0, vt[:, None] * (d - ut[:, None])).T
+    assert np.allclose(got_te, zt[:, cols] @ b, rtol=1e-12, atol=1e-12), "held-out rows"
+
+
+def pin_topk(lib):
+    rng = np.random.default_rng(15)
+    for p, k in ((10, 1), (10, 10), (100, 7), (1000, 37)):
+        for kind in ("real", "ties"):
+            w = rng.normal(size=p) if kind == "real" else rng.integers(-3, 4, size=p).astype(float)
+            got = oracle.topk(w, k, lib=lib)
+            want = np.lexsort((np.arange(p), -np.abs(w)))[:k]
+            assert np.array_equal(got, want), f"topk {kind} p={p} k={k}"
+
+
+def _panel(seed, n, p, miss=0.01):
+    rng = np.random.default_rng(seed)
+    G, codes = random_geno(rng, n, p, miss=miss)
+    return rng, G, codes
+
+
+def pin_k1_marginal(lib):
+    """k = 1: S^0 = argmax |z_j^T y| and beta = z_j^T y / z_j^T z_j (marginal regression)."""
+    for seed in (21, 22, 23):
+        rng, G, codes = _panel(seed, 200, 60)
+        y = rng.normal(size=G.n)
+        Z = np_Z(codes)
+        f = oracle.iht(G, y, 1, max_iter=1, lib=lib)
+        s = Z.T @ y
+        j = int(np.lexsort((np.arange(G.p), -np.abs(s)))[0])
+        assert f.trace["supp"][0, 0] == j, "k=1 first support is the single-marker scan"
+        want = s[j] / (Z[:, j] @ Z[:, j])
+        assert abs(f.beta[j] - want) <= 1e-12 * abs(want), "k=1 step solves the marginal LS"
+
+
+def pin_fixed_point(lib):
+    """At convergence with a stable support, beta_S solves the normal equations on S."""
+    for seed in (31, 32, 33, 34):
+        rng, G, codes = _panel(seed, 300, 80)
+        Z = np_Z(codes)
+        true = rng.choice(G.p, size=4, replace=False)
+        y = Z[:, true] @ rng.normal(0, 1.0, size=4) + rng.normal(size=G.n)
+        f = oracle.iht(G, y, 4, tol=1e-11, max_iter=5000, lib=lib)
+        assert f.status == oracle.OK
+        coef, obj = lstsq_obj(Z, y, f.support)
+        assert np.allclose(f.beta[f.support], coef, rtol=1e-7, atol=1e-9), "normal equations"
+        assert abs(f.objective - obj) <= 1e-9 * obj
+
+
+def pin_full_ols(lib):
+    """k = p < n: normalized steepest descent converges to the OLS fit."""
+    rng, G, codes = _panel(41, 120, 6, miss=0.0)
+    Z = np_Z(codes)
+    y = Z @ rng.normal(size=6) + rng.normal(size=G.n)
+    f = oracle.iht(G, y, 6, tol=1e-13, max_iter=20000, lib=lib)
+    coef, _ = lstsq_obj(Z, y, range(6))
+    assert np.allclose(f.beta, coef, rtol=1e-8, atol=1e-10), "OLS"
+
+
+def pin_noiseless(lib):
+    """y = Z_S b exactly, well-separated effects: exact recovery of S and b."""
+    for seed in (51, 52):
+        rng, G, codes = _panel(seed, 400, 50, miss=0.0)
+        Z = np_Z(codes)
+        S = np.sort(rng.choice(G.p, size=3, replace=False))
+        b = np.array([3.0, -2.5, 2.0])
+        y = Z[:, S] @ b
+        f = oracle.iht(G, y, 3, tol=1e-12, max_iter=5000, lib=lib)
+        assert np.array_equal(np.sort(f.support), S), "support recovery"
+        assert np.allclose(f.beta[S], b, rtol=1e-7, atol=1e-9), "coefficients"
+        assert f.objective <= 1e-12 * float(y @ y)
+
+
+def pin_bruteforce(lib):
+    """f(beta_IHT) >= min over all k-subsets of the LS objective; equality on strong signals."""
+    for seed in (61, 62, 63, 64, 65):
+        rng, G, codes = _panel(seed, 40, 12, miss=0.0)
+        Z = np_Z(codes)
+        for k in (1, 2, 3):
+            for strong in (False, True):
+                if strong:
+                    S = rng.choice(G.p, size=k, replace=False)
+                    y = Z[:, S] @ (rng.choice([-1, 1], size=k) * rng.uniform(4, 6, size=k)) \
+                        + 0.3 * rng.normal(size=G.n)
+                else:
+                    y = rng.normal(size=G.n)
+                best = min(lstsq_obj(Z, y, c)[1] for c in itertools.combinations(range(G.p), k))
+                f = oracle.iht(G, y, k, tol=1e-12, max_iter=5000, lib=lib)
+                assert f.objective >= best - 1e-9 * (1 + best), "objective below the subset optimum"
+                if strong:
+                    assert abs(f.objective - best) <= 1e-7 * (1 + best), "strong signal: optimum"
+
+
+def pin_invariants(lib):
+    """Monotone objective, |supp beta| <= k, sorted support, accepted steps satisfy mu < omega."""
+    for seed in (71, 72, 73):
+        rng, G, codes = _panel(seed, 150, 300, miss=0.02)
+        Z = np_Z(codes)
+        S = rng.choice(G.p, size=8, replace=False)
+        y = Z[:, S] @ rng.normal(0, 0.5, size=8) + rng.normal(size=G.n)
+        for k in (1, 5, 8, 20):
+            f = oracle.iht(G, y, k, tol=1e-8, max_iter=300, lib=lib)
+            obj = np.concatenate([[0.5 * float(y @ y)], f.trace["objective"]])
+            assert np.all(np.diff(obj) <= 1e-12 * obj[:-1]), "monotone objective"
+            assert np.count_nonzero(f.beta) <= k
+            assert np.all(np.diff(f.support) > 0) and f.support.size == k
+            off = np.setdiff1d(np.arange(G.p), f.support)
+            assert np.all(f.beta[off] == 0.0)
+            ch = (f.trace["changed"] == 1) & (f.trace["backtracks"] < 50)
+            assert np.all(f.trace["mu"][ch] < f.trace["omega"][ch]), "accepted mu < omega"
+            # objective reported = 1/2 ||y - Z beta||^2 from scratch
+            res = y - Z @ f.beta
+            assert abs(f.objective - 0.5 * res @ res) <= 1e-10 * f.objective
+
+
+def pin_orientation(lib):
+    """Swapping hom-ref and hom-alt codes flips z: same support, beta -> -beta."""
+    rng, G, codes = _panel(81, 200, 40, miss=0.03)
+    Z = np_Z(codes)
+    y = Z[:, [3, 17]] @ np.array([1.5, -1.0]) + rng.normal(size=G.n)
+    flipped = codes.copy()
+    flipped[codes == 0] = 3
+    flipped[codes == 3] = 0
+    G2 = geno_from_codes(flipped)
+    a = oracle.iht(G, y, 2, tol=1e-10, max_iter=1000, lib=lib)
+    b = oracle.iht(G2, y, 2, tol=1e-10, max_iter=1000, lib=lib)
+    assert np.array_equal(a.support, b.support)
+    assert np.allclose(a.beta, -b.beta, rtol=1e-9, atol=1e-12)
+
+
+ALL_PINS = [pin_decode, pin_counts_stats, pin_stats_exact, pin_gradient, pin_identity, pin_topk,
+            pin_k1_marginal, pin_fixed_point, pin_full_ols, pin_noiseless, pin_bruteforce,
+            pin_invariants, pin_orientation]
