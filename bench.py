@@ -1,0 +1,315 @@
+#!/usr/bin/env python3
+"""Benchmark: IHT iterations/s on the single-solve panel (n=5000, p=500000, k=50).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                    [--config 1|2] [--grad-impl 0|1|2] [--no-cpu-baseline]
+
+One step = one full IHT least-squares solve (beta = 0 to convergence, every
+step of the hot path: standardised gradient, top-k projection, step size,
+backtracking, sparse residual update) on synthetic PLINK-packed genotypes
+with the shapes of the paper's GWAS panels.  ``value`` = IHT iterations per
+second over the K timed solves, inputs resident in HBM, device-timed with CUDA
+events; ``e2e`` = the same metric through the host-buffer C-ABI call (y copied
+in, beta/support copied out inside the timed region).  The packed genotype
+matrix (625 MB) is larger than L2, so no flush is needed between steps.
+
+Under torchrun (N > 1) every rank runs an independent replica of the same
+solve on its own GPU (the single-solve path has no exchange step), value =
+iterations of all ranks / max elapsed.
+
+``--impl reference`` times the FP64 CPU oracle on the host cores (bounded
+sample of the same workload); on rank 0 only.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+
+FALLBACK_HBM_GBS = 6400.0
+
+
+def log(*a):
+    print(*a, file=sys.stderr, flush=True)
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    return int(os.environ.get("RANK", "0")), int(os.environ.get("LOCAL_RANK", "0")), ws
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled every 200 ms during the timed region."""
+    FIELDS = ("uuid,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, uuid: str | None):
+        self.uuid = uuid
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(prefix="clocks", suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                if self.uuid and self.uuid not in parts[0] and parts[0] not in self.uuid:
+                    continue
+                rows.append(parts)
+        os.unlink(self.path)
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i] == "Active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(rows)}
+
+
+def gpu_uuid(torch, dev):
+    try:
+        u = torch.cuda.get_device_properties(dev).uuid
+        s = str(u)
+        return s if s.startswith("GPU-") else "GPU-" + s
+    except Exception:
+        return None
+
+
+def run_oracle_sample(cfg: int, max_iter: int, pn=None, bed=None, y=None):
+    """FP64 oracle, as it stands, on the host cores: (iterations, seconds, threads)."""
+    import oracle
+    c = synth.CONFIGS[cfg]
+    if pn is None:
+        pn = synth.config_panel(cfg)
+        bed = pn.bed()
+        y, _, _ = synth.config_phenotype(cfg, pn)
+    G = oracle.Geno.from_bed(bed, pn.n, pn.p)
+    t0 = time.perf_counter()
+    f = oracle.iht(G, y, c["k"], max_iter=max_iter, tol=c["tol"], trace=False)
+    dt = time.perf_counter() - t0
+    return f.iterations, dt, oracle.max_threads()
+
+
+def reference_arm(args):
+    rank, _, world = dist_env()
+    if rank != 0:
+        return 0
+    cfg = args.config
+    c = synth.CONFIGS[cfg]
+    pn = synth.config_panel(cfg)
+    bed = pn.bed()
+    y, _, _ = synth.config_phenotype(cfg, pn)
+    cap = args.oracle_iters
+    for _ in range(args.warmup):
+        run_oracle_sample(cfg, cap, pn, bed, y)
+    its, secs = 0, 0.0
+    threads = 1
+    for _ in range(args.steps):
+        i, dt, threads = run_oracle_sample(cfg, cap, pn, bed, y)
+        its += i
+        secs += dt
+    value = its / secs
+    sample = (f"FP64 oracle IHT on {c['name']} capped at {cap} iterations per step "
+              f"(setup + {cap} gradient passes, projections, step sizes)")
+    out = {"impl": "reference", "metric": "IHT iterations/sec", "value": value, "unit": "iter/s",
+           "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": 1e3 * secs / args.steps, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": c["name"], "n": c["n"], "p": c["p"], "k": c["k"]},
+           "cpu_baseline": {"value": value, "unit": "iter/s", "cores": threads, "kind": "oracle",
+                            "sample": sample},
+           "e2e": {"value": value, "unit": "iter/s", "h2d_bytes_per_step": 0,
+                   "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+    return 0
+
+
+def ours_arm(args):
+    import torch
+    import paper_1608_01398_b300 as iht
+
+    rank, local_rank, world = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device(f"cuda:{local_rank}"))
+    torch.cuda.set_device(local_rank)
+    dev = local_rank
+    cfg = args.config
+    c = synth.CONFIGS[cfg]
+    n, p, k = c["n"], c["p"], c["k"]
+
+    t0 = time.perf_counter()
+    pn = synth.config_panel(cfg)
+    bed = pn.bed()
+    y, causal, _ = synth.config_phenotype(cfg, pn)
+    log(f"[bench] rank {rank}: generated {bed.nbytes / 1e6:.0f} MB panel in "
+        f"{time.perf_counter() - t0:.1f}s")
+
+    stream = torch.cuda.current_stream(dev)
+    ctx = iht.Context(dev, stream)
+    ds = iht.Dataset(ctx, bed, n, p)
+    y_dev = torch.from_numpy(y).to(f"cuda:{dev}")
+    fit_kw = dict(out_device=True, grad_impl=args.grad_impl, tol=c["tol"], max_iter=c["max_iter"])
+
+    for _ in range(max(args.warmup, 0)):
+        iht.iht_fit(ds, y_dev, k, **fit_kw)
+    torch.cuda.synchronize(dev)
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+
+    # ---- device-timed region: inputs resident in HBM -------------------------
+    clocks = ClockSampler(gpu_uuid(torch, dev))
+    clocks.start()
+    time.sleep(0.3)
+    barrier()
+    torch.cuda.synchronize(dev)
+    l0 = iht.iht_kernel_launches()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    its, grad_ms, grad_n = 0, 0.0, 0
+    statuses = []
+    for _ in range(args.steps):
+        r = iht.iht_fit(ds, y_dev, k, profile=1, **fit_kw)
+        its += r.iterations
+        grad_ms += r.grad_ms
+        grad_n += r.grad_launches
+        statuses.append(r.status)
+    ev1.record(stream)
+    torch.cuda.synchronize(dev)
+    barrier()
+    launches = iht.iht_kernel_launches() - l0
+    clk = clocks.stop()
+    elapsed = ev0.elapsed_time(ev1) / 1e3
+
+    # ---- end to end through the host-buffer call ------------------------------
+    y_pin = torch.empty(n, dtype=torch.float64).pin_memory()
+    y_pin.numpy()[:] = y
+    y_host = y_pin.numpy()
+    barrier()
+    torch.cuda.synchronize(dev)
+    w0 = time.perf_counter()
+    e2e_its = 0
+    for _ in range(args.steps):
+        r = iht.iht_fit(ds, y_host, k, grad_impl=args.grad_impl, tol=c["tol"],
+                        max_iter=c["max_iter"])
+        e2e_its += r.iterations
+    torch.cuda.synchronize(dev)
+    e2e_wall = time.perf_counter() - w0
+    barrier()
+    beta_host, supp_host = r.beta, r.support
+
+    # ---- aggregate over ranks --------------------------------------------------
+    vals = torch.tensor([its, elapsed, e2e_its, e2e_wall, grad_ms, grad_n], dtype=torch.float64,
+                        device=f"cuda:{dev}")
+    if world > 1:
+        gathered = [torch.zeros_like(vals) for _ in range(world)]
+        torch.distributed.all_gather(gathered, vals)
+        allv = torch.stack(gathered).cpu().numpy()
+    else:
+        allv = vals.cpu().numpy()[None, :]
+    if rank == 0:
+        tot_its = float(allv[:, 0].sum())
+        max_el = float(allv[:, 1].max())
+        value = tot_its / max_el
+        e2e_value = float(allv[:, 2].sum()) / float(allv[:, 3].max())
+        hbm_peak, peak_kind = measured_peaks()
+        alg_bytes = p * ((n + 3) // 4) + 12 * p + 4 * n      # packed genotypes + u, v, g + r
+        per_launch_ms = grad_ms / max(grad_n, 1)
+        achieved = alg_bytes / (per_launch_ms / 1e3) / 1e9 if grad_n else None
+        iters_mean = its / args.steps
+        ctl = 4 + 2 * 120 + 4 * iters_mean                   # status words and done flags
+        out = {
+            "metric": "IHT iterations/sec", "value": value, "unit": "iter/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * max_el / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": c["name"], "n": n, "p": p, "k": k,
+                       "packed_bytes": p * ((n + 3) // 4), "iterations_per_solve": iters_mean,
+                       "grad_impl": args.grad_impl, "l2": "inputs larger than L2 (no flush)",
+                       "parallelism": "replicas" if world > 1 else "single"},
+            "genotype_gbs": achieved, "pct_hbm_peak": (100.0 * achieved / hbm_peak) if achieved else None,
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+                         "frac": (achieved / hbm_peak) if achieved else None, "traffic": None,
+                         "kernel": "gradient pass g = Z^T r", "peak_source": peak_kind,
+                         "algorithmic_bytes_per_launch": alg_bytes},
+            "e2e": {"value": e2e_value, "unit": "iter/s", "h2d_bytes_per_step": 8 * n + 120,
+                    "d2h_bytes_per_step": int(12 * k + ctl)},
+            "gpu_launches": int(launches), "clocks": clk,
+            "statuses": sorted(set(int(s) for s in statuses)),
+        }
+        if not args.no_cpu_baseline and world == 1:
+            iters, secs, threads = run_oracle_sample(cfg, args.oracle_iters, pn, bed, y)
+            out["cpu_baseline"] = {
+                "value": iters / secs, "unit": "iter/s", "cores": threads, "kind": "oracle",
+                "sample": f"FP64 oracle IHT on {c['name']}, first {iters} iterations "
+                          f"(incl. setup), {secs:.1f}s"}
+        print(json.dumps(out), flush=True)
+    del ds, ctx
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--config", type=int, default=2, choices=[1, 2])
+    ap.add_argument("--grad-impl", type=int, default=0, choices=[0, 1, 2])
+    ap.add_argument("--oracle-iters", type=int, default=10)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return reference_arm(args)
+    return ours_arm(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,186 @@
+/*
+ * iht.h -- C ABI of the B300 (sm_103a) library for iterative hard
+ * thresholding (IHT) least squares on PLINK-packed genotypes.
+ *
+ * Method: Keys, Chen & Lange, "Iterative Hard Thresholding for Model
+ * Selection in Genome-Wide Association Studies".  The library minimises
+ *   f(beta) = 1/2 ||y - Z beta||^2   subject to ||beta||_0 <= k
+ * (Eq. leastsquaresloss, Sec. 2.2) by projected gradient steps
+ *   beta+ = P_{S_k}[beta + mu g],  g = Z^T (y - Z beta)   (Eq. ihta, Eq. normal_grad)
+ * with the normalized step size and its backtracking check (Sec. 2.3.1),
+ * where Z is the genotype matrix standardised on the fly (Sec. 2.3.2).
+ *
+ * Conventions (every entry point):
+ *   - Return an int status (iht_status).  No C++ exception crosses the ABI.
+ *   - Work is ordered on the context's CUDA stream.  Calls that return host
+ *     results synchronise that stream before returning.
+ *   - The caller owns every input and output buffer.  The library owns the
+ *     context, datasets and all scratch memory.
+ *   - Genotype codes (PLINK .bed, SNP-major): 00 hom-ref (dosage 0),
+ *     01 missing, 10 het (dosage 1), 11 hom-alt (dosage 2).
+ *   - Standardisation: u_j = mean dosage over observed calls of the rows in
+ *     use, v_j = 1/SD with an (n_obs - 1) denominator (v_j = 0 when the SD is
+ *     0 or n_obs < 2); z_ij = v_j (x_ij - u_j) for observed calls, 0 for
+ *     missing calls (Sec. 2.3.2 identity; Sec. 3.1).
+ */
+#ifndef IHT_H
+#define IHT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum iht_status {
+    IHT_OK = 0,
+    IHT_EINVAL = 1,    /* bad argument: k < 1, k > p, n_rows < 2, bad .bed magic/size, ... */
+    IHT_ENOMEM = 2,    /* device or host allocation failed                               */
+    IHT_ENOTCONV = 3,  /* max_iter reached before convergence; results are valid          */
+    IHT_ENUMERIC = 4,  /* NaN/Inf input, or a zero step-size denominator with g_S != 0    */
+    IHT_ETIMEOUT = 5,  /* a bounded device wait gave up                                  */
+    IHT_ECUDA = 6,     /* a CUDA runtime call failed (iht_last_cuda_error tells which)    */
+    IHT_EAGAIN = 7     /* result not ready yet                                            */
+} iht_status;
+
+typedef enum iht_mem { IHT_HOST = 0, IHT_DEVICE = 1 } iht_mem;
+
+typedef struct iht_ctx iht_ctx;
+typedef struct iht_dataset iht_dataset;
+
+/* Solver options (Sec. 2.3.1; readings of unstated constants in brackets). */
+typedef struct iht_options {
+    int32_t max_iter;      /* iteration cap [100]                                   */
+    int32_t max_backtrack; /* step shrinks per iteration [50]                       */
+    double tol;            /* stop when ||beta+ - beta|| / (||beta|| + 1) < tol [1e-4] */
+    double c;              /* omega = (1-c)||d||^2/||Z d||^2, 0 < c << 1 [0.01]       */
+    double kappa;          /* shrink mu <- mu / kappa while mu >= omega [2]           */
+    int32_t in_mem;        /* where rows and y live: IHT_HOST or IHT_DEVICE          */
+    int32_t out_mem;       /* where beta_out and support_out live                    */
+    int32_t grad_impl;     /* gradient kernel: 0 default, 1 CUDA-core, 2 tensor-core  */
+    int32_t profile;       /* 1: time every gradient launch with CUDA events [0]     */
+} iht_options;
+
+typedef struct iht_result {
+    int32_t iterations;    /* updates performed                                */
+    int32_t status;        /* iht_status of the solve                          */
+    int32_t backtracks;    /* total step shrinks                               */
+    int32_t reserved;
+    double objective;      /* 1/2 ||y - Z beta||^2 at exit (FP64)              */
+    double mu;             /* last accepted step size                          */
+    double grad_ms;        /* total device time of the gradient launches (profile = 1) */
+    int32_t grad_launches; /* gradient launches timed                          */
+    int32_t reserved2;
+} iht_result;
+
+/* Optional per-iteration record of iht_fit_trace (host arrays; any may be NULL).
+ * Arrays have max_iter entries; supp and beta have max_iter * k. */
+typedef struct iht_trace {
+    double *objective;     /* f after each update                               */
+    double *mu;            /* accepted step size                                */
+    int32_t *backtracks;   /* shrinks in the iteration                          */
+    int32_t *changed;      /* 1 if the support changed                          */
+    int32_t *supp;         /* accepted support, ascending (k per iteration)     */
+    double *beta;          /* beta on that support (k per iteration)           */
+} iht_trace;
+
+/* Fill *opt with the defaults in brackets above (host in/out, default kernels). */
+void iht_default_options(iht_options *opt);
+
+/* Static string for a status code. */
+const char *iht_strerror(int status);
+
+/* Name of the last CUDA error seen by this thread ("" if none). */
+const char *iht_last_cuda_error(void);
+
+/* Number of CUDA kernel launches this library has issued in this process
+ * (all threads, all devices).  Host-only; lets callers count device work. */
+uint64_t iht_kernel_launches(void);
+
+/* Create a context on CUDA device `device` that orders all work on `stream`
+ * (a cudaStream_t; NULL = the legacy default stream).  *out receives the
+ * context.  EINVAL for a bad device, ECUDA if the device cannot be used. */
+int iht_create(iht_ctx **out, int device, void *stream);
+
+/* Free a context (datasets created from it must be freed first). */
+int iht_destroy(iht_ctx *ctx);
+
+/* a0 -- upload a PLINK .bed image once; the packed matrix then stays resident
+ * on the device for every later call (Sec. 2.3.3 device data placement).
+ *   bed, bed_bytes : the whole file image, 3-byte magic 0x6C 0x1B 0x01 then
+ *                    p SNP rows of ceil(n/4) bytes; host or device memory
+ *                    as `mem` says.  Read only during the call.
+ *   n, p           : subjects and SNPs.
+ * The library keeps a repacked copy: row stride rounded up to 16 bytes, pad
+ * samples set to the missing code.  EINVAL on bad magic, size mismatch,
+ * n < 1 or p < 1; ENOMEM if the copy does not fit. */
+int iht_load_bed(iht_ctx *ctx, const uint8_t *bed, size_t bed_bytes, int mem, int64_t n,
+                 int64_t p, iht_dataset **out);
+
+/* Free a dataset and its device memory. */
+int iht_dataset_free(iht_dataset *ds);
+
+/* Dataset shape: n, p and the repacked row stride in bytes (any may be NULL). */
+int iht_dataset_shape(const iht_dataset *ds, int64_t *n, int64_t *p, int64_t *stride);
+
+/* a1 -- per-SNP code counts and the cached mean / inverse-SD vectors u, v of
+ * Sec. 2.3.2, over a row set.
+ *   rows       : n_rows distinct subject indices in [0, n), or NULL for all n.
+ *   counts_out : int32[p][4] (index = code 0..3), may be NULL.
+ *   u_out      : double[p] means, v_out: double[p] inverse SDs, may be NULL.
+ * rows and the outputs live in memory of kind `mem`.  The FP64 statistics are
+ * computed from the integer counts in the order n_obs = n_rows - n_miss,
+ * s1 = n_het + 2 n_homalt, s2 = n_het + 4 n_homalt, u = s1/n_obs,
+ * var = (s2 - s1*s1/n_obs)/(n_obs - 1), v = 1/sqrt(var). */
+int iht_counts(iht_dataset *ds, const int32_t *rows, int64_t n_rows, int mem,
+               int32_t *counts_out, double *u_out, double *v_out);
+
+/* a2 -- one standardised gradient pass g = Z^T r (Eq. normal_grad; the
+ * negative gradient of f at the beta whose residual is r).
+ *   rows   : device int32[n_rows] subject indices or NULL (= all n); the
+ *            statistics are those of this row set.
+ *   r      : device float[n_rows], aligned with rows.
+ *   g_out  : device float[p].
+ *   impl   : 0 default, 1 CUDA-core kernel, 2 tensor-core kernel.
+ * Computed as g_j = v_j (S1_j - u_j (R - M_j)), S1 = sum of dosage * r over
+ * observed calls, M = sum of r over missing calls, R = sum of r. */
+int iht_gradient(iht_dataset *ds, const int32_t *rows, int64_t n_rows, const float *r,
+                 float *g_out, int impl);
+
+/* a3 -- projection onto the k-sparse set (Eq. ihta): the k indices of the
+ * largest |w_j|, ties to the lower index, returned ascending.
+ *   w: device float[p]; idx_out: device int32[k].  EINVAL if k < 1 or k > p. */
+int iht_topk(iht_ctx *ctx, const float *w, int64_t p, int32_t k, int32_t *idx_out);
+
+/* a4/a6 -- sparse standardised product out = Z[rows, cols] coef: only the m
+ * listed columns are decoded and standardised (Sec. 2.3.2-2.3.3, X_k beta_k).
+ *   cols: device int32[m]; coef: device double[m]; out: device double[n_rows].
+ *   u, v: device double[p] statistics to standardise with (e.g. a training
+ *   fold's, for held-out rows); NULL = statistics of `rows`. */
+int iht_zmul(iht_dataset *ds, const int32_t *rows, int64_t n_rows, const double *u,
+             const double *v, const int32_t *cols, int32_t m, const double *coef, double *out);
+
+/* a2-a6 -- IHT least squares to convergence (Sec. 2.2-2.3.1).
+ *   rows        : int32[n_rows] subjects the solve uses, or NULL for all n.
+ *   y           : double[n_rows] phenotype aligned with rows.
+ *   k           : sparsity level, 1 <= k <= p.
+ *   opt         : options (NULL = defaults).  rows and y live in opt->in_mem,
+ *                 beta_out and support_out in opt->out_mem.
+ *   beta_out    : double[p], written in full (zeros off the support).
+ *   support_out : int32[k], ascending.
+ *   info        : host iht_result, may be NULL.
+ * Starts from beta = 0 with S^0 = the top-k of |Z^T y|.  Returns the solve's
+ * status: OK, ENOTCONV (results valid), ENUMERIC, EINVAL, ENOMEM, ECUDA. */
+int iht_fit(iht_dataset *ds, const int32_t *rows, int64_t n_rows, const double *y, int32_t k,
+            const iht_options *opt, double *beta_out, int32_t *support_out, iht_result *info);
+
+/* iht_fit with a per-iteration record (host arrays, see iht_trace). */
+int iht_fit_trace(iht_dataset *ds, const int32_t *rows, int64_t n_rows, const double *y,
+                  int32_t k, const iht_options *opt, double *beta_out, int32_t *support_out,
+                  iht_result *info, iht_trace *trace);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* IHT_H */

@@ -33,9 +33,9 @@
  *  R8 statistics over the rows the solve uses.
  *  R9 code 00 = hom-ref (dosage 0), 01 = missing, 10 = het (1), 11 = hom-alt (2).
  *  R10 standardised dosage z = v (x - u) on observed calls, 0 on missing
- *     (Sec. 3.1 "standardized observed genotype dosages and then set
- *     unobserved dosages to 0"; equals the identity of Sec. 2.3.2 on
- *     mean-imputed genotypes).
+ *     (Sec. 3.1 standardises the observed dosages and zeroes the missing
+ *     ones; this equals the identity of Sec. 2.3.2 on mean-imputed
+ *     genotypes).
  */
 #include <math.h>
 #include <stdint.h>

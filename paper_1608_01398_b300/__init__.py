@@ -1,0 +1,328 @@
+"""Python binding of libiht (include/iht.h): argument marshalling only.
+
+Every function here has the name of the C entry point it calls and does
+nothing but check types, hand over pointers and turn status codes into
+exceptions.  All work runs in the CUDA kernels of ``libiht.so``; there is no
+CPU fallback, and loading fails loudly when the library or a CUDA device is
+missing.  PyTorch supplies device memory and the current CUDA stream.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libiht.so")
+
+IHT_OK, IHT_EINVAL, IHT_ENOMEM, IHT_ENOTCONV, IHT_ENUMERIC, IHT_ETIMEOUT, IHT_ECUDA, IHT_EAGAIN = \
+    range(8)
+IHT_HOST, IHT_DEVICE = 0, 1
+
+EXPORTED = ["iht_default_options", "iht_strerror", "iht_last_cuda_error", "iht_kernel_launches",
+            "iht_create",
+            "iht_destroy", "iht_load_bed", "iht_dataset_free", "iht_dataset_shape", "iht_counts",
+            "iht_gradient", "iht_topk", "iht_zmul", "iht_fit", "iht_fit_trace"]
+
+
+class IhtError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        msg = f"{where}: {status_name(status)}"
+        if status == IHT_ECUDA:
+            msg += f" [{_lib().iht_last_cuda_error().decode()}]"
+        super().__init__(msg)
+        self.status = status
+
+
+class iht_options(ctypes.Structure):
+    _fields_ = [("max_iter", ctypes.c_int32), ("max_backtrack", ctypes.c_int32),
+                ("tol", ctypes.c_double), ("c", ctypes.c_double), ("kappa", ctypes.c_double),
+                ("in_mem", ctypes.c_int32), ("out_mem", ctypes.c_int32),
+                ("grad_impl", ctypes.c_int32), ("profile", ctypes.c_int32)]
+
+
+class iht_result(ctypes.Structure):
+    _fields_ = [("iterations", ctypes.c_int32), ("status", ctypes.c_int32),
+                ("backtracks", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("objective", ctypes.c_double), ("mu", ctypes.c_double),
+                ("grad_ms", ctypes.c_double), ("grad_launches", ctypes.c_int32),
+                ("reserved2", ctypes.c_int32)]
+
+
+class iht_trace(ctypes.Structure):
+    _fields_ = [("objective", ctypes.c_void_p), ("mu", ctypes.c_void_p),
+                ("backtracks", ctypes.c_void_p), ("changed", ctypes.c_void_p),
+                ("supp", ctypes.c_void_p), ("beta", ctypes.c_void_p)]
+
+
+_LIB = None
+
+
+def _lib(build_if_stale: bool = True):
+    """The loaded libiht.so (compiled in-tree when missing or stale)."""
+    global _LIB
+    if _LIB is not None:
+        return _LIB
+    if build_if_stale:
+        from . import build as _build
+        try:
+            if _build.stale():
+                _build.build()
+        except (OSError, RuntimeError) as e:
+            if not os.path.exists(LIB_PATH):
+                raise ImportError(f"libiht.so is missing and could not be built: {e}") from e
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"libiht.so not found at {LIB_PATH}")
+    L = ctypes.CDLL(LIB_PATH)
+    P, i32, i64, sz = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_size_t
+    sig = {
+        "iht_default_options": (None, [ctypes.POINTER(iht_options)]),
+        "iht_strerror": (ctypes.c_char_p, [ctypes.c_int]),
+        "iht_last_cuda_error": (ctypes.c_char_p, []),
+        "iht_kernel_launches": (ctypes.c_uint64, []),
+        "iht_create": (ctypes.c_int, [ctypes.POINTER(P), ctypes.c_int, P]),
+        "iht_destroy": (ctypes.c_int, [P]),
+        "iht_load_bed": (ctypes.c_int, [P, P, sz, ctypes.c_int, i64, i64, ctypes.POINTER(P)]),
+        "iht_dataset_free": (ctypes.c_int, [P]),
+        "iht_dataset_shape": (ctypes.c_int, [P, ctypes.POINTER(i64), ctypes.POINTER(i64),
+                                             ctypes.POINTER(i64)]),
+        "iht_counts": (ctypes.c_int, [P, P, i64, ctypes.c_int, P, P, P]),
+        "iht_gradient": (ctypes.c_int, [P, P, i64, P, P, ctypes.c_int]),
+        "iht_topk": (ctypes.c_int, [P, P, i64, i32, P]),
+        "iht_zmul": (ctypes.c_int, [P, P, i64, P, P, P, i32, P, P]),
+        "iht_fit": (ctypes.c_int, [P, P, i64, P, i32, ctypes.POINTER(iht_options), P, P,
+                                   ctypes.POINTER(iht_result)]),
+        "iht_fit_trace": (ctypes.c_int, [P, P, i64, P, i32, ctypes.POINTER(iht_options), P, P,
+                                         ctypes.POINTER(iht_result), ctypes.POINTER(iht_trace)]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(L, name)
+        f.restype = res
+        f.argtypes = args
+    _LIB = L
+    return L
+
+
+def iht_kernel_launches() -> int:
+    """Kernel launches issued by libiht in this process."""
+    return int(_lib().iht_kernel_launches())
+
+
+def status_name(s: int) -> str:
+    return _lib().iht_strerror(int(s)).decode()
+
+
+def _check(rc: int, where: str, ok=(IHT_OK,)):
+    if rc not in ok:
+        raise IhtError(rc, where)
+    return rc
+
+
+def _torch():
+    import torch
+    if not torch.cuda.is_available():
+        raise RuntimeError("libiht needs a CUDA device; none is visible")
+    return torch
+
+
+def _dptr(t, dtype, name):
+    torch = _torch()
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype or not t.is_contiguous():
+        raise TypeError(f"{name} must be a contiguous {dtype} CUDA tensor")
+    return t.data_ptr()
+
+
+class Context:
+    """iht_create / iht_destroy.  Orders work on the given torch stream."""
+
+    def __init__(self, device: int = 0, stream=None):
+        torch = _torch()
+        self.device = device
+        self.stream = stream if stream is not None else torch.cuda.current_stream(device)
+        h = ctypes.c_void_p()
+        _check(_lib().iht_create(ctypes.byref(h), device, ctypes.c_void_p(self.stream.cuda_stream)),
+               "iht_create")
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None):
+            _lib().iht_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Dataset:
+    """iht_load_bed / iht_dataset_free."""
+
+    def __init__(self, ctx: Context, bed, n: int, p: int):
+        torch = _torch()
+        self.ctx = ctx
+        h = ctypes.c_void_p()
+        if isinstance(bed, torch.Tensor):
+            ptr, nbytes, mem = _dptr(bed, torch.uint8, "bed"), bed.numel(), IHT_DEVICE
+        else:
+            bed = np.ascontiguousarray(bed, dtype=np.uint8)
+            ptr, nbytes, mem = bed.ctypes.data, bed.size, IHT_HOST
+        _check(_lib().iht_load_bed(ctx.h, ctypes.c_void_p(ptr), nbytes, mem, n, p,
+                                   ctypes.byref(h)), "iht_load_bed")
+        self.h = h
+        n_, p_, s_ = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+        _lib().iht_dataset_shape(h, ctypes.byref(n_), ctypes.byref(p_), ctypes.byref(s_))
+        self.n, self.p, self.stride = n_.value, p_.value, s_.value
+
+    def close(self):
+        if getattr(self, "h", None):
+            _lib().iht_dataset_free(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def iht_default_options(**kw) -> iht_options:
+    o = iht_options()
+    _lib().iht_default_options(ctypes.byref(o))
+    for k, v in kw.items():
+        if not hasattr(o, k):
+            raise AttributeError(k)
+        setattr(o, k, v)
+    return o
+
+
+def iht_counts(ds: Dataset, rows=None):
+    """Host call: (counts int32[p,4], u float64[p], v float64[p])."""
+    c = np.empty((ds.p, 4), dtype=np.int32)
+    u = np.empty(ds.p)
+    v = np.empty(ds.p)
+    if rows is not None:
+        rows = np.ascontiguousarray(rows, dtype=np.int32)
+    _check(_lib().iht_counts(ds.h, None if rows is None else ctypes.c_void_p(rows.ctypes.data),
+                             0 if rows is None else rows.size, IHT_HOST,
+                             ctypes.c_void_p(c.ctypes.data), ctypes.c_void_p(u.ctypes.data),
+                             ctypes.c_void_p(v.ctypes.data)), "iht_counts")
+    return c, u, v
+
+
+def iht_gradient(ds: Dataset, r, rows=None, impl: int = 0, out=None):
+    """g = Z^T r on the device; r float32 CUDA tensor aligned with rows."""
+    torch = _torch()
+    g = out if out is not None else torch.empty(ds.p, dtype=torch.float32, device=r.device)
+    rp = None if rows is None else ctypes.c_void_p(_dptr(rows, torch.int32, "rows"))
+    nr = ds.n if rows is None else rows.numel()
+    if r.numel() != nr:
+        raise ValueError("r must have one entry per row")
+    _check(_lib().iht_gradient(ds.h, rp, nr, ctypes.c_void_p(_dptr(r, torch.float32, "r")),
+                               ctypes.c_void_p(_dptr(g, torch.float32, "g")), impl), "iht_gradient")
+    return g
+
+
+def iht_topk(ctx: Context, w, k: int, out=None):
+    """Indices of the k largest |w| (ties to the lower index), ascending."""
+    torch = _torch()
+    idx = out if out is not None else torch.empty(k, dtype=torch.int32, device=w.device)
+    _check(_lib().iht_topk(ctx.h, ctypes.c_void_p(_dptr(w, torch.float32, "w")), w.numel(), k,
+                           ctypes.c_void_p(_dptr(idx, torch.int32, "idx"))), "iht_topk")
+    return idx
+
+
+def iht_zmul(ds: Dataset, cols, coef, rows=None, u=None, v=None):
+    """Z[rows, cols] @ coef (FP64) on the device."""
+    torch = _torch()
+    nr = ds.n if rows is None else rows.numel()
+    out = torch.empty(nr, dtype=torch.float64, device=coef.device)
+    rp = None if rows is None else ctypes.c_void_p(_dptr(rows, torch.int32, "rows"))
+    up = None if u is None else ctypes.c_void_p(_dptr(u, torch.float64, "u"))
+    vp = None if v is None else ctypes.c_void_p(_dptr(v, torch.float64, "v"))
+    _check(_lib().iht_zmul(ds.h, rp, nr, up, vp, ctypes.c_void_p(_dptr(cols, torch.int32, "cols")),
+                           cols.numel(), ctypes.c_void_p(_dptr(coef, torch.float64, "coef")),
+                           ctypes.c_void_p(out.data_ptr())), "iht_zmul")
+    return out
+
+
+@dataclass
+class FitResult:
+    beta: object
+    support: object
+    iterations: int
+    status: int
+    backtracks: int
+    objective: float
+    mu: float
+    trace: dict | None = None
+    grad_ms: float = 0.0
+    grad_launches: int = 0
+
+
+def _fit(ds: Dataset, y, k: int, rows, opts: iht_options, trace: bool):
+    torch = _torch()
+    dev_in = isinstance(y, torch.Tensor)
+    if dev_in:
+        yp = _dptr(y, torch.float64, "y")
+        nr = y.numel()
+        rp = None if rows is None else _dptr(rows, torch.int32, "rows")
+        opts.in_mem = IHT_DEVICE
+    else:
+        y = np.ascontiguousarray(y, dtype=np.float64)
+        yp, nr = y.ctypes.data, y.size
+        if rows is not None:
+            rows = np.ascontiguousarray(rows, dtype=np.int32)
+        rp = None if rows is None else rows.ctypes.data
+        opts.in_mem = IHT_HOST
+    if rows is None and nr != ds.n:
+        raise ValueError("y must have n entries when rows is None")
+    if opts.out_mem == IHT_DEVICE:
+        beta = torch.empty(ds.p, dtype=torch.float64, device=f"cuda:{ds.ctx.device}")
+        supp = torch.empty(k, dtype=torch.int32, device=f"cuda:{ds.ctx.device}")
+        bp, sp = beta.data_ptr(), supp.data_ptr()
+    else:
+        beta = np.empty(ds.p)
+        supp = np.empty(k, dtype=np.int32)
+        bp, sp = beta.ctypes.data, supp.ctypes.data
+    res = iht_result()
+    tr = None
+    if trace:
+        T = max(opts.max_iter, 1)
+        tr = dict(objective=np.full(T, np.nan), mu=np.full(T, np.nan),
+                  backtracks=np.zeros(T, np.int32), changed=np.zeros(T, np.int32),
+                  supp=np.zeros((T, k), np.int32), beta=np.zeros((T, k)))
+        ct = iht_trace(*(tr[f].ctypes.data for f in
+                         ("objective", "mu", "backtracks", "changed", "supp", "beta")))
+        rc = _lib().iht_fit_trace(ds.h, None if rp is None else ctypes.c_void_p(rp), nr,
+                                  ctypes.c_void_p(yp), k, ctypes.byref(opts), ctypes.c_void_p(bp),
+                                  ctypes.c_void_p(sp), ctypes.byref(res), ctypes.byref(ct))
+    else:
+        rc = _lib().iht_fit(ds.h, None if rp is None else ctypes.c_void_p(rp), nr,
+                            ctypes.c_void_p(yp), k, ctypes.byref(opts), ctypes.c_void_p(bp),
+                            ctypes.c_void_p(sp), ctypes.byref(res))
+    _check(rc, "iht_fit", ok=(IHT_OK, IHT_ENOTCONV, IHT_ENUMERIC))
+    if tr is not None:
+        tr = {f: a[:res.iterations] for f, a in tr.items()}
+    return FitResult(beta, supp, res.iterations, rc, res.backtracks, res.objective, res.mu, tr,
+                     res.grad_ms, res.grad_launches)
+
+
+def iht_fit(ds: Dataset, y, k: int, rows=None, **opt) -> FitResult:
+    """IHT to convergence.  y (and rows) numpy -> host inputs, CUDA tensors -> device inputs."""
+    out_device = opt.pop("out_device", False)
+    o = iht_default_options(**opt)
+    o.out_mem = IHT_DEVICE if out_device else IHT_HOST
+    return _fit(ds, y, k, rows, o, trace=False)
+
+
+def iht_fit_trace(ds: Dataset, y, k: int, rows=None, **opt) -> FitResult:
+    out_device = opt.pop("out_device", False)
+    o = iht_default_options(**opt)
+    o.out_mem = IHT_DEVICE if out_device else IHT_HOST
+    return _fit(ds, y, k, rows, o, trace=True)

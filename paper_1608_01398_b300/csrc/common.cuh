@@ -1,0 +1,192 @@
+// Internal declarations shared by the CUDA translation units of libiht.
+//
+// Device data layout (one dataset):
+//   G        uint8[p][stride]   PLINK 2-bit codes, SNP-major; stride = ceil(n/4)
+//                               rounded up to 16 bytes; pad samples carry the
+//                               missing code 01 so every sum skips them.
+//   used     int32[n_pad]       1 for rows of the current solve, else 0
+//                               (n_pad = 4 * stride samples).
+//   rowmask  uint32[stride/4]   2-bit lanes 11 for used rows, 00 otherwise.
+//   u64,v64  double[p]          per-SNP mean / inverse SD over the used rows.
+//   u32,v32  float[p]           FP32 copies read by the gradient kernels.
+//   y64,r64  double[n_pad]      phenotype and residual (0 off the used rows).
+//   r32      float[n_pad]       centred FP32 residual the gradient pass reads.
+//   g        float[p]           standardised gradient Z^T r.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <algorithm>
+
+#include "../../include/iht.h"
+
+namespace iht {
+
+constexpr int kMaxK = 1024;            // largest sparsity level accepted
+constexpr int kMaxCand = 2 * kMaxK;    // candidate list of the projection
+constexpr int kSelBins = 2048;         // radix-select histogram bins
+constexpr int kPartials = 1024;        // max per-block partial sums
+
+struct Scalars {                       // device-resident state of one solve
+    double num;                        // ||g_S||^2
+    double mu;                         // step size of the current iteration
+    double f;                          // objective after the last update
+    double sum_r;                      // sum of r over used rows
+    double sumsq_r;                    // sum of r^2 over used rows
+    double step;                       // ||beta+ - beta|| / (||beta|| + 1)
+    double c, kappa, tol;              // options
+    int32_t iter;                      // updates performed
+    int32_t status;                    // IHT_OK / ENOTCONV / ENUMERIC
+    int32_t done;                      // 1 once the solve has stopped
+    int32_t bt_total;                  // total shrinks
+    int32_t bt_last;                   // shrinks of the last iteration
+    int32_t changed;                   // support changed in the last iteration
+    int32_t max_iter, max_backtrack;
+    int32_t k, n_rows;
+    int32_t err;                       // bit 0: non-finite input, bit 1: bad rows
+    int32_t pad_;
+};
+
+struct SelState {                      // radix select progress
+    uint32_t prefix, mask, need, count_gt;
+    uint32_t n_gt, err;
+};
+
+// Host-side handles -------------------------------------------------------
+struct Workspace;
+
+struct SelWork {                       // radix-select scratch, one per context
+    uint32_t *hist = nullptr;          // kSelBins
+    uint32_t *chunk_eq = nullptr;      // per-chunk counts of keys equal to the threshold
+    int64_t nchunks_cap = 0;
+    SelState *st = nullptr;
+};
+
+}  // namespace iht
+
+struct iht_ctx {
+    int device;
+    cudaStream_t stream;
+    int num_sms;
+    iht::SelWork sel;
+};
+
+struct iht_dataset {
+    iht_ctx *ctx;
+    int64_t n, p, stride, n_pad;
+    uint8_t *G;
+    iht::Workspace *ws;
+};
+
+namespace iht {
+
+struct Workspace {
+    int64_t p = 0, n_pad = 0;
+    int kcap = 0;
+    int32_t *used = nullptr;
+    uint32_t *rowmask = nullptr;
+    int32_t *counts = nullptr;
+    double *u64 = nullptr, *v64 = nullptr;
+    float *u32 = nullptr, *v32 = nullptr;
+    double *y64 = nullptr, *r64 = nullptr, *zv = nullptr;
+    float *r32 = nullptr, *g = nullptr;
+    double *partials = nullptr;        // kPartials * 2
+    int32_t *rows_dev = nullptr;       // int32[n]: host row lists copied here
+    double *ybuf = nullptr;            // double[n]: host phenotypes copied here
+    float *fbuf = nullptr;             // float[n_pad]: scratch
+    int32_t *cand = nullptr;           // kMaxCand
+    // solver state
+    int32_t *S = nullptr, *Sp = nullptr;   // current / next support (k, ascending)
+    double *bS = nullptr, *bSp = nullptr;  // beta on S / S+
+    double *coef = nullptr;                // scratch coefficients (kMaxCand)
+    int32_t *cols = nullptr;               // scratch columns (kMaxCand)
+    Scalars *sc = nullptr;
+    Scalars *sc_host = nullptr;            // pinned mirror
+    // optional timing of the gradient launches of a solve
+    cudaEvent_t prof_ev[2 * 256] = {};
+    int nprof = 0;
+    double prof_ms = 0.0;
+};
+constexpr int kProfEvents = 256;
+
+// error helpers -----------------------------------------------------------
+void set_cuda_error(cudaError_t e, const char *where);
+void note_launch(int n = 1);           // kernel launches issued (iht_kernel_launches)
+#define IHT_CUDA(call)                                                  \
+    do {                                                                \
+        cudaError_t e_ = (call);                                        \
+        if (e_ != cudaSuccess) {                                        \
+            ::iht::set_cuda_error(e_, #call);                           \
+            return e_ == cudaErrorMemoryAllocation ? IHT_ENOMEM : IHT_ECUDA; \
+        }                                                               \
+    } while (0)
+
+int ensure_workspace(iht_dataset *ds, int kcap);
+void free_workspace(Workspace *ws);
+
+// kernels launched from the host side (stream-ordered) ---------------------
+// geno.cu
+int launch_fix_padding(iht_dataset *ds);
+int setup_rows(iht_dataset *ds, const int32_t *rows_dev, int64_t n_rows);
+int launch_counts(iht_dataset *ds, int64_t n_rows);
+int scatter_rows_f64(iht_dataset *ds, const int32_t *rows_dev, int64_t n_rows, const double *src,
+                     double *dst);
+int scatter_rows_f32(iht_dataset *ds, const int32_t *rows_dev, int64_t n_rows, const float *src,
+                     float *dst);
+// grad_simt.cu / grad_tc.cu
+int launch_grad_simt(iht_dataset *ds, const float *r32, float *g, const int32_t *done);
+int launch_grad_tc(iht_dataset *ds, const float *r32, float *g, const int32_t *done);
+// select.cu
+int ensure_selwork(iht_ctx *ctx, int64_t p);
+int select_topk(iht_ctx *ctx, const float *key_src, int64_t p, int32_t K, int32_t *out_idx,
+                const int32_t *done);
+// solver.cu
+int launch_zmul(iht_dataset *ds, const int32_t *cols, int32_t m, const double *coef,
+                const double *u, const double *v, const int32_t *used, const double *base,
+                double *out, double *partials);
+int gather_rows_f64(iht_dataset *ds, const int32_t *rows_dev, int64_t n_rows, const double *src,
+                    double *dst);
+int check_finite_y(iht_dataset *ds, int64_t n_rows, const double *y_dev);
+int run_solve_host(iht_dataset *ds, int k, const iht_options *opt, int n_rows, iht_trace *trace,
+                   int max_iter);
+int write_beta_device(iht_dataset *ds, int k, double *beta_out);
+
+// device helpers ------------------------------------------------------------
+__device__ __forceinline__ float warp_sum(float x)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    return x;
+}
+
+__device__ __forceinline__ double warp_sum(double x)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    return x;
+}
+
+// Fixed-order block sum (deterministic); every thread gets the result.
+// `sh` needs blockDim.x / 32 doubles.
+__device__ __forceinline__ double block_sum(double x, double *sh)
+{
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    x = warp_sum(x);
+    __syncthreads();
+    if (lane == 0) sh[wid] = x;
+    __syncthreads();
+    double t = 0.0;
+    if (wid == 0) {
+        t = lane < nw ? sh[lane] : 0.0;
+        t = warp_sum(t);
+        if (lane == 0) sh[0] = t;
+    }
+    __syncthreads();
+    t = sh[0];
+    __syncthreads();
+    return t;
+}
+
+inline int ceil_div(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
+
+}  // namespace iht

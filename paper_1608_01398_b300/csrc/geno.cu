@@ -1,0 +1,196 @@
+// a0/a1: genotype upload fix-up, row sets, per-SNP counts and statistics.
+//
+// Counts come from popcounts on 32-bit words of 16 codes: with lo = even bits
+// and hi = odd bits of each 2-bit code, code 11 = lo&hi, 01 = lo&~hi,
+// 10 = hi&~lo; unused rows are masked to 00 and code 00 is n_rows minus the
+// rest.  The FP64 statistics then follow the integer counts in the fixed
+// order of Sec. 2.3.2's u, v vectors (mean over observed calls, variance with
+// an (n_obs - 1) denominator), with every operation correctly rounded so the
+// values match any IEEE FP64 evaluation of the same expression bit for bit.
+#include "common.cuh"
+
+namespace iht {
+
+// Pad samples (n .. 4*stride-1) get code 01 (missing), so no kernel ever
+// needs a bounds test on the sample axis.
+__global__ void k_fix_padding(uint8_t *__restrict__ G, int64_t p, int64_t stride, int64_t nbytes,
+                              int rem)
+{
+    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= p) return;
+    uint8_t *row = G + j * stride;
+    if (rem) {
+        const unsigned keep = (1u << (2 * rem)) - 1u;
+        row[nbytes - 1] = (uint8_t)((row[nbytes - 1] & keep) | (0x55u & ~keep));
+    }
+    for (int64_t b = nbytes; b < stride; ++b) row[b] = 0x55;
+}
+
+int launch_fix_padding(iht_dataset *ds)
+{
+    const int64_t nbytes = (ds->n + 3) / 4;
+    const int rem = (int)(ds->n & 3);
+    if (rem == 0 && nbytes == ds->stride) return IHT_OK;
+    k_fix_padding<<<ceil_div(ds->p, 256), 256, 0, ds->ctx->stream>>>(ds->G, ds->p, ds->stride,
+                                                                     nbytes, rem);
+    note_launch();
+    IHT_CUDA(cudaGetLastError());
+    return IHT_OK;
+}
+
+__global__ void k_mark_rows(const int32_t *__restrict__ rows, int64_t n_rows, int64_t n,
+                            int32_t *__restrict__ used, int32_t *__restrict__ err)
+{
+    const int64_t a = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (a >= n_rows) return;
+    const int32_t i = rows[a];
+    if (i < 0 || i >= n) {
+        atomicOr(err, 2);
+        return;
+    }
+    if (atomicExch(&used[i], 1) != 0) atomicOr(err, 2);   // duplicate row
+}
+
+__global__ void k_mark_all(int64_t n, int64_t n_pad, int32_t *__restrict__ used)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n_pad) used[i] = i < n ? 1 : 0;
+}
+
+__global__ void k_rowmask(const int32_t *__restrict__ used, uint32_t *__restrict__ rowmask,
+                          int64_t nwords)
+{
+    const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= nwords) return;
+    uint32_t m = 0;
+#pragma unroll
+    for (int q = 0; q < 16; ++q)
+        if (used[16 * c + q]) m |= 3u << (2 * q);
+    rowmask[c] = m;
+}
+
+// Marks the rows of a solve (rows_dev == nullptr: all n) and builds the
+// 2-bit row mask.  Bad or duplicate indices set bit 1 of sc->err.
+int setup_rows(iht_dataset *ds, const int32_t *rows_dev, int64_t n_rows)
+{
+    Workspace *ws = ds->ws;
+    cudaStream_t s = ds->ctx->stream;
+    if (rows_dev) {
+        IHT_CUDA(cudaMemsetAsync(ws->used, 0, sizeof(int32_t) * ds->n_pad, s));
+        if (n_rows > 0) {
+            k_mark_rows<<<ceil_div(n_rows, 256), 256, 0, s>>>(rows_dev, n_rows, ds->n, ws->used,
+                                                              &ws->sc->err);
+            note_launch();
+        }
+    } else {
+        k_mark_all<<<ceil_div(ds->n_pad, 256), 256, 0, s>>>(ds->n, ds->n_pad, ws->used);
+        note_launch();
+    }
+    const int64_t nwords = ds->stride / 4;
+    k_rowmask<<<ceil_div(nwords, 256), 256, 0, s>>>(ws->used, ws->rowmask, nwords);
+    note_launch();
+    IHT_CUDA(cudaGetLastError());
+    return IHT_OK;
+}
+
+// One warp per SNP: masked popcounts, then the FP64 statistics.
+__global__ void __launch_bounds__(256) k_counts(const uint8_t *__restrict__ G, int64_t p,
+                                                int64_t stride, const uint32_t *__restrict__ rowmask,
+                                                int64_t n_rows, int32_t *__restrict__ counts,
+                                                double *__restrict__ u64, double *__restrict__ v64,
+                                                float *__restrict__ u32, float *__restrict__ v32)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    const int64_t nwords = stride / 4;
+    for (int64_t j = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); j < p;
+         j += nwarps) {
+        const uint32_t *row = reinterpret_cast<const uint32_t *>(G + j * stride);
+        int c1 = 0, c2 = 0, c3 = 0;
+        for (int64_t c = lane; c < nwords; c += 32) {
+            const uint32_t w = __ldg(row + c) & __ldg(rowmask + c);
+            const uint32_t lo = w & 0x55555555u, hi = (w >> 1) & 0x55555555u;
+            c3 += __popc(lo & hi);
+            c1 += __popc(lo & ~hi);
+            c2 += __popc(hi & ~lo);
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            c1 += __shfl_xor_sync(0xffffffffu, c1, o);
+            c2 += __shfl_xor_sync(0xffffffffu, c2, o);
+            c3 += __shfl_xor_sync(0xffffffffu, c3, o);
+        }
+        if (lane == 0) {
+            const int64_t c0 = n_rows - c1 - c2 - c3;
+            if (counts) {
+                counts[4 * j + 0] = (int32_t)c0;
+                counts[4 * j + 1] = c1;
+                counts[4 * j + 2] = c2;
+                counts[4 * j + 3] = c3;
+            }
+            const double n_obs = (double)(n_rows - c1);
+            const double s1 = (double)(c2 + 2 * c3);
+            const double s2 = (double)(c2 + 4 * c3);
+            const double mean = n_obs > 0.0 ? __ddiv_rn(s1, n_obs) : 0.0;
+            double inv_sd = 0.0;
+            if (n_obs >= 2.0) {
+                const double var = __ddiv_rn(__dsub_rn(s2, __ddiv_rn(__dmul_rn(s1, s1), n_obs)),
+                                             __dsub_rn(n_obs, 1.0));
+                if (var > 0.0) inv_sd = __ddiv_rn(1.0, __dsqrt_rn(var));
+            }
+            u64[j] = mean;
+            v64[j] = inv_sd;
+            u32[j] = (float)mean;
+            v32[j] = (float)inv_sd;
+        }
+    }
+}
+
+int launch_counts(iht_dataset *ds, int64_t n_rows)
+{
+    Workspace *ws = ds->ws;
+    const int blocks = (int)std::min<int64_t>(ceil_div(ds->p, 8), (int64_t)ds->ctx->num_sms * 16);
+    k_counts<<<blocks, 256, 0, ds->ctx->stream>>>(ds->G, ds->p, ds->stride, ws->rowmask, n_rows,
+                                                  ws->counts, ws->u64, ws->v64, ws->u32, ws->v32);
+    note_launch();
+    IHT_CUDA(cudaGetLastError());
+    return IHT_OK;
+}
+
+template <typename T>
+__global__ void k_scatter(const int32_t *__restrict__ rows, int64_t n_rows, const T *__restrict__ src,
+                          T *__restrict__ dst, int64_t n)
+{
+    const int64_t a = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (a >= n_rows) return;
+    const int64_t i = rows ? rows[a] : a;
+    if (i >= 0 && i < n) dst[i] = src[a];
+}
+
+int scatter_rows_f64(iht_dataset *ds, const int32_t *rows_dev, int64_t n_rows, const double *src,
+                     double *dst)
+{
+    cudaStream_t s = ds->ctx->stream;
+    IHT_CUDA(cudaMemsetAsync(dst, 0, sizeof(double) * ds->n_pad, s));
+    if (n_rows > 0) {
+        k_scatter<double><<<ceil_div(n_rows, 256), 256, 0, s>>>(rows_dev, n_rows, src, dst, ds->n);
+        note_launch();
+    }
+    IHT_CUDA(cudaGetLastError());
+    return IHT_OK;
+}
+
+int scatter_rows_f32(iht_dataset *ds, const int32_t *rows_dev, int64_t n_rows, const float *src,
+                     float *dst)
+{
+    cudaStream_t s = ds->ctx->stream;
+    IHT_CUDA(cudaMemsetAsync(dst, 0, sizeof(float) * ds->n_pad, s));
+    if (n_rows > 0) {
+        k_scatter<float><<<ceil_div(n_rows, 256), 256, 0, s>>>(rows_dev, n_rows, src, dst, ds->n);
+        note_launch();
+    }
+    IHT_CUDA(cudaGetLastError());
+    return IHT_OK;
+}
+
+}  // namespace iht

@@ -1,0 +1,281 @@
+// a3: top-K selection by |key| with ties to the lower index (Eq. ihta's
+// projection P_{S_k}; the paper only asks for a fast sort, the tie rule is
+// this library's reading).
+//
+// Radix select on the IEEE bits of |x| (for non-negative floats the unsigned
+// bit pattern is monotone in the value):
+//   pass 0 histograms bits 30..20 (2048 bins), pass 1 bits 19..10, pass 2
+//   bits 9..0, each restricted to keys matching the digits fixed so far; a
+//   single-CTA scan after each pass picks the digit where the running count
+//   from the top reaches K.  The result is the K-th largest key T, the number
+//   of keys above it, and how many keys equal to T are still needed.
+// Collection writes every key > T (unordered) and the lowest-index keys == T
+// (ordered by a per-chunk count and an exclusive scan), then one CTA sorts the
+// K indices ascending.  NaN keys set SelState::err bit 0.
+#include "common.cuh"
+
+namespace iht {
+
+__device__ __forceinline__ uint32_t sel_key(float x) { return __float_as_uint(x) & 0x7fffffffu; }
+
+constexpr int kSelThreads = 256;
+constexpr int kSelItems = 16;                          // consecutive indices per thread
+constexpr int kSelChunk = kSelThreads * kSelItems;     // indices per collection block
+
+__global__ void k_sel_init(SelState *st, uint32_t K, uint32_t *hist, const int32_t *done)
+{
+    if (done && *done) return;
+    if (threadIdx.x == 0) {
+        st->prefix = 0;
+        st->mask = 0;
+        st->need = K;
+        st->count_gt = 0;
+        st->n_gt = 0;
+        st->err = 0;
+    }
+    for (int b = threadIdx.x; b < kSelBins; b += blockDim.x) hist[b] = 0;
+}
+
+__global__ void __launch_bounds__(kSelThreads) k_sel_hist(const float *__restrict__ keys, int64_t p,
+                                                          SelState *st, uint32_t *hist, int shift,
+                                                          uint32_t dmask, const int32_t *done)
+{
+    __shared__ uint32_t sh[kSelBins];
+    if (done && *done) return;
+    for (int b = threadIdx.x; b < kSelBins; b += blockDim.x) sh[b] = 0;
+    __syncthreads();
+    const uint32_t prefix = st->prefix, mask = st->mask;
+    bool nan = false;
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < p;
+         j += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t k = sel_key(keys[j]);
+        nan |= k > 0x7f800000u;
+        if ((k & mask) == prefix) atomicAdd(&sh[(k >> shift) & dmask], 1u);
+    }
+    if (nan && shift == 20) atomicOr(&st->err, 1u);
+    __syncthreads();
+    for (int b = threadIdx.x; b < kSelBins; b += blockDim.x)
+        if (sh[b]) atomicAdd(&hist[b], sh[b]);
+}
+
+// Inclusive scan over a block of 1024 threads, 2 items per thread (fixed order).
+__device__ __forceinline__ void scan2(uint32_t &a, uint32_t &b, uint32_t *wsum)
+{
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    b += a;
+    uint32_t t = b;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t v = __shfl_up_sync(0xffffffffu, t, o);
+        if (lane >= o) t += v;
+    }
+    if (lane == 31) wsum[wid] = t;
+    __syncthreads();
+    if (wid == 0) {
+        uint32_t s = wsum[lane];
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t v = __shfl_up_sync(0xffffffffu, s, o);
+            if (lane >= o) s += v;
+        }
+        wsum[lane] = s;
+    }
+    __syncthreads();
+    const uint32_t off = (t - b) + (wid ? wsum[wid - 1] : 0u);
+    a += off;
+    b += off;
+    __syncthreads();
+}
+
+// Single block of 1024 threads: bins scanned from the top.
+__global__ void __launch_bounds__(1024) k_sel_scan(SelState *st, uint32_t *hist, int shift,
+                                                   uint32_t dmask, int nbins, const int32_t *done)
+{
+    __shared__ uint32_t wsum[32];
+    if (done && *done) return;
+    const int t = threadIdx.x;
+    // reversed order: position q holds bin nbins-1-q
+    const int q0 = 2 * t, q1 = 2 * t + 1;
+    const uint32_t h0 = q0 < nbins ? hist[nbins - 1 - q0] : 0u;
+    const uint32_t h1 = q1 < nbins ? hist[nbins - 1 - q1] : 0u;
+    uint32_t c0 = h0, c1 = h1;
+    scan2(c0, c1, wsum);     // inclusive cumulative counts from the top
+    const uint32_t need = st->need;
+    __syncthreads();
+    int hit = -1;
+    uint32_t above = 0;
+    if (q0 < nbins && c0 >= need && c0 - h0 < need) { hit = nbins - 1 - q0; above = c0 - h0; }
+    if (q1 < nbins && c1 >= need && c1 - h1 < need) { hit = nbins - 1 - q1; above = c1 - h1; }
+    if (hit >= 0) {
+        st->count_gt += above;
+        st->need = need - above;
+        st->prefix |= (uint32_t)hit << shift;
+        st->mask |= dmask << shift;
+    }
+    if (q0 < nbins) hist[nbins - 1 - q0] = 0;
+    if (q1 < nbins) hist[nbins - 1 - q1] = 0;
+}
+
+// Keys > T go to out[0..count_gt) in any order; per-chunk counts of keys == T.
+__global__ void __launch_bounds__(kSelThreads) k_sel_collect_gt(const float *__restrict__ keys,
+                                                                int64_t p, SelState *st,
+                                                                int32_t *__restrict__ out,
+                                                                uint32_t *__restrict__ chunk_eq,
+                                                                const int32_t *done)
+{
+    __shared__ uint32_t sh_eq;
+    if (done && *done) return;
+    if (threadIdx.x == 0) sh_eq = 0;
+    __syncthreads();
+    const uint32_t T = st->prefix;
+    const int64_t base = (int64_t)blockIdx.x * kSelChunk;
+    uint32_t eq = 0;
+    for (int it = 0; it < kSelItems; ++it) {
+        const int64_t j = base + it * kSelThreads + threadIdx.x;
+        if (j < p) {
+            const uint32_t k = sel_key(keys[j]);
+            if (k > T) out[atomicAdd(&st->n_gt, 1u)] = (int32_t)j;
+            eq += k == T;
+        }
+    }
+    if (eq) atomicAdd(&sh_eq, eq);
+    __syncthreads();
+    if (threadIdx.x == 0) chunk_eq[blockIdx.x] = sh_eq;
+}
+
+// Exclusive scan of chunk_eq in place (single block of 1024 threads).
+__global__ void __launch_bounds__(1024) k_sel_scan_chunks(uint32_t *chunk_eq, int64_t nchunks,
+                                                          const int32_t *done)
+{
+    __shared__ uint32_t wsum[32];
+    __shared__ uint32_t carry;
+    if (done && *done) return;
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    for (int64_t base = 0; base < nchunks; base += 2048) {
+        const int64_t i0 = base + 2 * threadIdx.x, i1 = i0 + 1;
+        const uint32_t h0 = i0 < nchunks ? chunk_eq[i0] : 0u;
+        const uint32_t h1 = i1 < nchunks ? chunk_eq[i1] : 0u;
+        uint32_t c0 = h0, c1 = h1;
+        scan2(c0, c1, wsum);
+        const uint32_t cr = carry;
+        if (i0 < nchunks) chunk_eq[i0] = cr + c0 - h0;
+        if (i1 < nchunks) chunk_eq[i1] = cr + c1 - h1;
+        __syncthreads();
+        if (threadIdx.x == blockDim.x - 1) carry = cr + c1;
+        __syncthreads();
+    }
+}
+
+// The lowest-index keys == T, in index order, after the keys > T.
+__global__ void __launch_bounds__(kSelThreads) k_sel_collect_eq(const float *__restrict__ keys,
+                                                                int64_t p, const SelState *st,
+                                                                int32_t *__restrict__ out,
+                                                                const uint32_t *__restrict__ chunk_off,
+                                                                const int32_t *done)
+{
+    __shared__ uint32_t wsum[kSelThreads / 32];
+    if (done && *done) return;
+    const uint32_t T = st->prefix, need = st->need, gt = st->count_gt;
+    const uint32_t off0 = chunk_off[blockIdx.x];
+    if (off0 >= need) return;                 // uniform over the block
+    const int64_t base = (int64_t)blockIdx.x * kSelChunk + (int64_t)threadIdx.x * kSelItems;
+    uint32_t mine = 0;
+    for (int it = 0; it < kSelItems; ++it) {
+        const int64_t j = base + it;
+        mine += (j < p) && sel_key(keys[j]) == T;
+    }
+    // exclusive scan of `mine` over the block
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    uint32_t t = mine;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t v = __shfl_up_sync(0xffffffffu, t, o);
+        if (lane >= o) t += v;
+    }
+    if (lane == 31) wsum[wid] = t;
+    __syncthreads();
+    uint32_t woff = 0;
+    for (int w = 0; w < wid; ++w) woff += wsum[w];
+    uint32_t rank = off0 + woff + t - mine;
+    for (int it = 0; it < kSelItems && rank < need; ++it) {
+        const int64_t j = base + it;
+        if (j < p && sel_key(keys[j]) == T) out[gt + rank++] = (int32_t)j;
+    }
+}
+
+// Sort K (<= kMaxCand) indices ascending in one block (bitonic in shared memory).
+__global__ void __launch_bounds__(1024) k_sort_idx(int32_t *idx, int K, const int32_t *done)
+{
+    __shared__ int32_t s[kMaxCand];
+    if (done && *done) return;
+    int P = 1;
+    while (P < K) P <<= 1;
+    for (int i = threadIdx.x; i < P; i += blockDim.x) s[i] = i < K ? idx[i] : 0x7fffffff;
+    __syncthreads();
+    for (int size = 2; size <= P; size <<= 1) {
+        for (int stride = size >> 1; stride > 0; stride >>= 1) {
+            for (int i = threadIdx.x; i < P; i += blockDim.x) {
+                const int jx = i ^ stride;
+                if (jx > i) {
+                    const bool up = (i & size) == 0;
+                    const int32_t a = s[i], b = s[jx];
+                    if ((a > b) == up) {
+                        s[i] = b;
+                        s[jx] = a;
+                    }
+                }
+            }
+            __syncthreads();
+        }
+    }
+    for (int i = threadIdx.x; i < K; i += blockDim.x) idx[i] = s[i];
+}
+
+int ensure_selwork(iht_ctx *ctx, int64_t p)
+{
+    SelWork &w = ctx->sel;
+    const int64_t nchunks = (p + kSelChunk - 1) / kSelChunk;
+    if (!w.hist) {
+        IHT_CUDA(cudaMalloc(&w.hist, sizeof(uint32_t) * kSelBins));
+        IHT_CUDA(cudaMalloc(&w.st, sizeof(SelState)));
+        IHT_CUDA(cudaMemsetAsync(w.hist, 0, sizeof(uint32_t) * kSelBins, ctx->stream));
+    }
+    if (nchunks > w.nchunks_cap) {
+        if (w.chunk_eq) cudaFree(w.chunk_eq);
+        w.chunk_eq = nullptr;
+        w.nchunks_cap = 0;
+        IHT_CUDA(cudaMalloc(&w.chunk_eq, sizeof(uint32_t) * nchunks));
+        w.nchunks_cap = nchunks;
+    }
+    return IHT_OK;
+}
+
+int select_topk(iht_ctx *ctx, const float *keys, int64_t p, int32_t K, int32_t *out,
+                const int32_t *done)
+{
+    SelWork *ws = &ctx->sel;
+    cudaStream_t s = ctx->stream;
+    if (K < 1 || K > p || K > kMaxCand) return IHT_EINVAL;
+    const int64_t nchunks = (p + kSelChunk - 1) / kSelChunk;
+    if (nchunks > ws->nchunks_cap) return IHT_EINVAL;
+    const int hblocks = (int)std::min<int64_t>(ceil_div(p, kSelThreads), (int64_t)ctx->num_sms * 4);
+    k_sel_init<<<1, 256, 0, s>>>(ws->st, (uint32_t)K, ws->hist, done);
+    const int shifts[3] = {20, 10, 0};
+    const uint32_t dmasks[3] = {0x7ffu, 0x3ffu, 0x3ffu};
+    for (int ps = 0; ps < 3; ++ps) {
+        k_sel_hist<<<hblocks, kSelThreads, 0, s>>>(keys, p, ws->st, ws->hist, shifts[ps], dmasks[ps],
+                                                   done);
+        k_sel_scan<<<1, 1024, 0, s>>>(ws->st, ws->hist, shifts[ps], dmasks[ps],
+                                      (int)dmasks[ps] + 1, done);
+    }
+    k_sel_collect_gt<<<(int)nchunks, kSelThreads, 0, s>>>(keys, p, ws->st, out, ws->chunk_eq, done);
+    k_sel_scan_chunks<<<1, 1024, 0, s>>>(ws->chunk_eq, nchunks, done);
+    k_sel_collect_eq<<<(int)nchunks, kSelThreads, 0, s>>>(keys, p, ws->st, out, ws->chunk_eq, done);
+    k_sort_idx<<<1, 1024, 0, s>>>(out, K, done);
+    note_launch(11);
+    IHT_CUDA(cudaGetLastError());
+    return IHT_OK;
+}
+
+}  // namespace iht

@@ -1,0 +1,723 @@
+// a3-a6: the O(nk) part of one IHT iteration, on the device.
+//
+//   k_gather_gS   coef = g_S, num = ||g_S||^2                     (Sec. 2.3.1)
+//   k_zmul        out = base + sign * Z[:, cols] coef, per-block partial sums
+//                 of out and out^2 (sparse product X_k beta_k, Sec. 2.3.2-2.3.3)
+//   k_merge       mu = num / den; w = beta + mu g on S u C; S+ = top-k |w|;
+//                 backtracking while mu >= omega (Eq. ihta, Sec. 2.3.1)
+//   k_finalize    objective, convergence test, state copy, trace
+//   k_center      r32 = r - mean(r) on the used rows (exact: every column of Z
+//                 sums to zero over the used rows)
+// Every kernel returns at once when the solve is done, so a fixed launch
+// sequence can run past convergence without changing the result.
+//
+// C is the candidate list: the top min(2k, p) of |g| over all SNPs.  Off the
+// support w_j = mu g_j, so the order of |w| there is the order of |g|; at most
+// k candidates lie on S, hence the top-k of |w| over all p lies in S u C.
+#include <math.h>
+
+#include "common.cuh"
+
+namespace iht {
+
+__device__ __forceinline__ int dosage_of(uint32_t code)   // -1 = missing
+{
+    return code == 0u ? 0 : (code == 2u ? 1 : (code == 3u ? 2 : -1));
+}
+
+__global__ void __launch_bounds__(1024) k_gather_gS(const float *__restrict__ g,
+                                                    const int32_t *__restrict__ S, int k,
+                                                    double *__restrict__ coef, Scalars *sc)
+{
+    __shared__ double red[32];
+    if (sc->done) return;
+    double s = 0.0;
+    for (int c = threadIdx.x; c < k; c += blockDim.x) {
+        const double x = (double)g[S[c]];
+        coef[c] = x;
+        s += x * x;
+    }
+    s = block_sum(s, red);
+    if (threadIdx.x == 0) sc->num = s;
+}
+
+constexpr int kZmulCols = 512;
+
+// One thread per packed byte (4 samples); columns staged in shared memory.
+__global__ void __launch_bounds__(256) k_zmul(const uint8_t *__restrict__ G, int64_t stride,
+                                              const int32_t *__restrict__ cols, int m,
+                                              const double *__restrict__ coef, double sign,
+                                              const double *__restrict__ u64,
+                                              const double *__restrict__ v64,
+                                              const int32_t *__restrict__ used,
+                                              const double *__restrict__ base,
+                                              double *__restrict__ out,
+                                              double *__restrict__ partials,
+                                              const int32_t *__restrict__ done)
+{
+    __shared__ double sa[kZmulCols], sb[kZmulCols];
+    __shared__ int64_t so[kZmulCols];
+    __shared__ double red[8];
+    if (done && *done) return;
+    const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    double acc[4] = {0.0, 0.0, 0.0, 0.0};
+    for (int c0 = 0; c0 < m; c0 += kZmulCols) {
+        const int cn = min(kZmulCols, m - c0);
+        __syncthreads();
+        for (int t = threadIdx.x; t < cn; t += blockDim.x) {
+            const int col = cols[c0 + t];
+            const double a = sign * coef[c0 + t] * v64[col];
+            sa[t] = a;
+            sb[t] = a * u64[col];
+            so[t] = (int64_t)col * stride;
+        }
+        __syncthreads();
+        if (b < stride) {
+            for (int t = 0; t < cn; t += 8) {
+                uint32_t by[8];
+#pragma unroll
+                for (int q = 0; q < 8; ++q) by[q] = t + q < cn ? __ldg(G + so[t + q] + b) : 0x55u;
+#pragma unroll
+                for (int q = 0; q < 8; ++q) {
+                    if (t + q < cn) {
+#pragma unroll
+                        for (int e = 0; e < 4; ++e) {
+                            const int x = dosage_of((by[q] >> (2 * e)) & 3u);
+                            if (x >= 0) acc[e] += sa[t + q] * (double)x - sb[t + q];
+                        }
+                    }
+                }
+            }
+        }
+    }
+    double s = 0.0, s2 = 0.0;
+    if (b < stride) {
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            const int64_t i = 4 * b + e;
+            const double o = used[i] ? (base ? base[i] : 0.0) + acc[e] : 0.0;
+            out[i] = o;
+            s += o;
+            s2 += o * o;
+        }
+    }
+    s = block_sum(s, red);
+    s2 = block_sum(s2, red);
+    if (threadIdx.x == 0 && partials) {
+        partials[2 * blockIdx.x] = s;
+        partials[2 * blockIdx.x + 1] = s2;
+    }
+}
+
+int zmul_blocks(const iht_dataset *ds) { return ceil_div(ds->stride, 256); }
+
+int launch_zmul(iht_dataset *ds, const int32_t *cols, int32_t m, const double *coef,
+                const double *u, const double *v, const int32_t *used, const double *base,
+                double *out, double *partials)
+{
+    k_zmul<<<zmul_blocks(ds), 256, 0, ds->ctx->stream>>>(ds->G, ds->stride, cols, m, coef, 1.0, u,
+                                                         v, used, base, out, partials, nullptr);
+    note_launch();
+    IHT_CUDA(cudaGetLastError());
+    return IHT_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Projection, step size and backtracking: one block of 1024 threads.
+
+struct MergeArgs {
+    const uint8_t *G;
+    int64_t stride;
+    const float *g;
+    const double *u64, *v64;
+    const int32_t *used;
+    const int32_t *S;     // k, ascending
+    const double *bS;     // beta on S
+    const int32_t *cand;  // K, ascending
+    int K;
+    const double *partials;
+    int npart;
+    int32_t *Sp;
+    double *bSp;
+    Scalars *sc;
+};
+
+constexpr int kMergeThreads = 1024;
+constexpr int kMergeU = 3 * kMaxK;      // |S u C| <= k + 2k
+constexpr int kMergeSort = 4 * kMaxK;   // power of two >= kMergeU
+
+struct MergeShared {
+    int32_t uidx[kMergeU];
+    double ubeta[kMergeU];
+    double ug[kMergeU];
+    double uw[kMergeU];
+    uint8_t inS[kMergeU];
+    uint8_t inSp[kMergeU];
+    unsigned long long skey[kMergeSort];
+    int32_t spos[kMergeSort];
+    double ca[2 * kMaxK], cb[2 * kMaxK];
+    int64_t coff[2 * kMaxK];
+    double red[32];
+    uint32_t wsum[32];
+    int nU, nS_extra, ncol;
+    int stop;
+};
+
+__device__ __forceinline__ bool before(unsigned long long ka, int32_t ia, unsigned long long kb,
+                                       int32_t ib)
+{
+    return ka > kb || (ka == kb && ia < ib);
+}
+
+__device__ int lower_bound_i32(const int32_t *a, int n, int32_t x)
+{
+    int lo = 0, hi = n;
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (a[mid] < x) lo = mid + 1; else hi = mid;
+    }
+    return lo;
+}
+
+// Sort positions 0..nU-1 of U by (|w| descending, index ascending).
+__device__ void sort_by_w(MergeShared &sh, int nU)
+{
+    int P = 1;
+    while (P < nU) P <<= 1;
+    for (int i = threadIdx.x; i < P; i += blockDim.x) {
+        if (i < nU) {
+            sh.skey[i] = (unsigned long long)__double_as_longlong(fabs(sh.uw[i]));
+            sh.spos[i] = i;
+        } else {
+            sh.skey[i] = 0ull;
+            sh.spos[i] = -1;
+        }
+    }
+    __syncthreads();
+    for (int size = 2; size <= P; size <<= 1) {
+        for (int st = size >> 1; st > 0; st >>= 1) {
+            for (int i = threadIdx.x; i < P; i += blockDim.x) {
+                const int j = i ^ st;
+                if (j > i) {
+                    const bool up = (i & size) == 0;
+                    const unsigned long long ki = sh.skey[i], kj = sh.skey[j];
+                    const int32_t pi = sh.spos[i], pj = sh.spos[j];
+                    const int32_t xi = pi < 0 ? 0x7fffffff : sh.uidx[pi];
+                    const int32_t xj = pj < 0 ? 0x7fffffff : sh.uidx[pj];
+                    // ascending in "before" order when up
+                    const bool swap = up ? before(kj, xj, ki, xi) : before(ki, xi, kj, xj);
+                    if (swap) {
+                        sh.skey[i] = kj; sh.skey[j] = ki;
+                        sh.spos[i] = pj; sh.spos[j] = pi;
+                    }
+                }
+            }
+            __syncthreads();
+        }
+    }
+}
+
+// ||Z d||^2 over the used rows for the columns staged in ca/cb/coff.
+__device__ double znorm2(MergeShared &sh, const MergeArgs &A)
+{
+    double s = 0.0;
+    for (int64_t b = threadIdx.x; b < A.stride; b += blockDim.x) {
+        double acc[4] = {0.0, 0.0, 0.0, 0.0};
+        for (int c = 0; c < sh.ncol; ++c) {
+            const uint32_t by = __ldg(A.G + sh.coff[c] + b);
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const int x = dosage_of((by >> (2 * e)) & 3u);
+                if (x >= 0) acc[e] += sh.ca[c] * (double)x - sh.cb[c];
+            }
+        }
+#pragma unroll
+        for (int e = 0; e < 4; ++e)
+            if (A.used[4 * b + e]) s += acc[e] * acc[e];
+    }
+    return block_sum(s, sh.red);
+}
+
+__global__ void __launch_bounds__(kMergeThreads) k_merge(MergeArgs A)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    MergeShared &sh = *reinterpret_cast<MergeShared *>(smem_raw);
+    Scalars *sc = A.sc;
+    if (sc->done) return;
+    const int k = sc->k;
+
+    // step size mu = ||g_S||^2 / ||Z_S g_S||^2
+    if (threadIdx.x == 0) {
+        double den = 0.0;
+        for (int b = 0; b < A.npart; ++b) den += A.partials[2 * b + 1];
+        const double num = sc->num;
+        sh.stop = 0;
+        if (num == 0.0) {
+            sc->status = IHT_OK;            // g_S = 0: fixed point
+            sc->done = 1;
+            sh.stop = 1;
+        } else if (!(den > 0.0) || !isfinite(den) || !isfinite(num)) {
+            sc->status = IHT_ENUMERIC;
+            sc->done = 1;
+            sh.stop = 1;
+        } else {
+            sc->mu = num / den;
+        }
+        sh.nS_extra = 0;
+    }
+    __syncthreads();
+    if (sh.stop) return;
+
+    // U = C (ascending) followed by S \ C (in S order)
+    const int K = A.K;
+    for (int b = threadIdx.x; b < K; b += blockDim.x) {
+        const int32_t j = A.cand[b];
+        const int pos = lower_bound_i32(A.S, k, j);
+        const bool on = pos < k && A.S[pos] == j;
+        sh.uidx[b] = j;
+        sh.inS[b] = on;
+        sh.ubeta[b] = on ? A.bS[pos] : 0.0;
+        sh.ug[b] = (double)A.g[j];
+    }
+    // S \ C with a block scan for deterministic positions (k <= 1024 = blockDim)
+    {
+        const int a = threadIdx.x;
+        int32_t j = 0;
+        bool extra = false;
+        if (a < k) {
+            j = A.S[a];
+            const int pos = lower_bound_i32(A.cand, K, j);
+            extra = !(pos < K && A.cand[pos] == j);
+        }
+        const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+        const unsigned bal = __ballot_sync(0xffffffffu, extra);
+        if (lane == 0) sh.wsum[wid] = __popc(bal);
+        __syncthreads();
+        int off = 0;
+        for (int w = 0; w < wid; ++w) off += sh.wsum[w];
+        off += __popc(bal & ((1u << lane) - 1u));
+        if (extra) {
+            const int u = K + off;
+            sh.uidx[u] = j;
+            sh.inS[u] = 1;
+            sh.ubeta[u] = A.bS[a];
+            sh.ug[u] = (double)A.g[j];
+        }
+        if (threadIdx.x == blockDim.x - 1) sh.nS_extra = off + (extra ? 1 : 0);
+    }
+    __syncthreads();
+    const int nU = K + sh.nS_extra;
+    double mu = sc->mu;
+    const double c = sc->c, kappa = sc->kappa;
+    const int max_bt = sc->max_backtrack;
+    int bt = 0;
+    bool changed = false;
+
+    for (;;) {
+        for (int u = threadIdx.x; u < nU; u += blockDim.x)
+            sh.uw[u] = __dadd_rn(sh.ubeta[u], __dmul_rn(mu, sh.ug[u]));
+        __syncthreads();
+        sort_by_w(sh, nU);
+        for (int u = threadIdx.x; u < nU; u += blockDim.x) sh.inSp[u] = 0;
+        __syncthreads();
+        for (int r = threadIdx.x; r < k; r += blockDim.x) sh.inSp[sh.spos[r]] = 1;
+        __syncthreads();
+        int kept = 0;
+        for (int u = threadIdx.x; u < nU; u += blockDim.x) kept += sh.inS[u] && sh.inSp[u];
+        kept = (int)block_sum((double)kept, sh.red);
+        changed = kept < k;
+        if (!changed) break;
+        // d = beta+ - beta on S u S+; omega = (1-c) ||d||^2 / ||Z d||^2
+        if (threadIdx.x == 0) sh.ncol = 0;
+        __syncthreads();
+        double dd = 0.0;
+        for (int u = threadIdx.x; u < nU; u += blockDim.x) {
+            const double bp = sh.inSp[u] ? sh.uw[u] : 0.0;
+            const double d = bp - sh.ubeta[u];
+            dd += d * d;
+        }
+        dd = block_sum(dd, sh.red);
+        // stage the columns of S u S+ in U order (deterministic)
+        {
+            for (int base0 = 0; base0 < nU; base0 += blockDim.x) {
+                const int u = base0 + threadIdx.x;
+                bool on = false;
+                double d = 0.0;
+                if (u < nU) {
+                    on = sh.inS[u] || sh.inSp[u];
+                    d = (sh.inSp[u] ? sh.uw[u] : 0.0) - sh.ubeta[u];
+                }
+                const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+                const unsigned bal = __ballot_sync(0xffffffffu, on);
+                if (lane == 0) sh.wsum[wid] = __popc(bal);
+                __syncthreads();
+                int off = sh.ncol;
+                for (int w = 0; w < wid; ++w) off += sh.wsum[w];
+                off += __popc(bal & ((1u << lane) - 1u));
+                if (on) {
+                    const int32_t j = sh.uidx[u];
+                    const double a = d * A.v64[j];
+                    sh.ca[off] = a;
+                    sh.cb[off] = a * A.u64[j];
+                    sh.coff[off] = (int64_t)j * A.stride;
+                }
+                __syncthreads();
+                if (threadIdx.x == 0) {
+                    int tot = 0;
+                    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) tot += sh.wsum[w];
+                    sh.ncol += tot;
+                }
+                __syncthreads();
+            }
+        }
+        const double zz = znorm2(sh, A);
+        if (!(zz > 0.0)) break;                       // Z d = 0: accept
+        const double omega = (1.0 - c) * dd / zz;
+        if (mu < omega || bt >= max_bt) break;
+        mu = mu / kappa;
+        ++bt;
+        __syncthreads();
+    }
+
+    // accepted candidate: step size of the test, S+ ascending with beta+
+    double dd = 0.0, bb = 0.0;
+    for (int u = threadIdx.x; u < nU; u += blockDim.x) {
+        const double bp = sh.inSp[u] ? sh.uw[u] : 0.0;
+        const double d = bp - sh.ubeta[u];
+        dd += d * d;
+        bb += sh.ubeta[u] * sh.ubeta[u];
+    }
+    dd = block_sum(dd, sh.red);
+    bb = block_sum(bb, sh.red);
+    // S+ in index order: positions of the selected entries, sorted by index
+    __syncthreads();
+    for (int r = threadIdx.x; r < kMergeSort; r += blockDim.x) sh.skey[r] = ~0ull;
+    __syncthreads();
+    for (int r = threadIdx.x; r < k; r += blockDim.x) {
+        const int u = sh.spos[r];
+        sh.skey[r] = ((unsigned long long)(uint32_t)sh.uidx[u] << 32) | (uint32_t)u;
+    }
+    __syncthreads();
+    {
+        int P = 1;
+        while (P < k) P <<= 1;
+        for (int size = 2; size <= P; size <<= 1)
+            for (int st = size >> 1; st > 0; st >>= 1) {
+                for (int i = threadIdx.x; i < P; i += blockDim.x) {
+                    const int j = i ^ st;
+                    if (j > i) {
+                        const bool up = (i & size) == 0;
+                        const unsigned long long a = sh.skey[i], b = sh.skey[j];
+                        if ((a > b) == up) { sh.skey[i] = b; sh.skey[j] = a; }
+                    }
+                }
+                __syncthreads();
+            }
+    }
+    for (int r = threadIdx.x; r < k; r += blockDim.x) {
+        const int u = (int)(uint32_t)(sh.skey[r] & 0xffffffffull);
+        A.Sp[r] = sh.uidx[u];
+        A.bSp[r] = sh.uw[u];
+    }
+    if (threadIdx.x == 0) {
+        sc->mu = mu;
+        sc->bt_last = bt;
+        sc->bt_total += bt;
+        sc->changed = changed ? 1 : 0;
+        sc->step = sqrt(dd) / (sqrt(bb) + 1.0);
+    }
+}
+
+// ---------------------------------------------------------------------------
+struct TraceDev {
+    double *objective, *mu;
+    int32_t *backtracks, *changed, *supp;
+    double *beta;
+};
+
+__global__ void __launch_bounds__(1024) k_finalize(Scalars *sc, const double *partials, int npart,
+                                                   int32_t *S, double *bS, const int32_t *Sp,
+                                                   const double *bSp, TraceDev tr, int first)
+{
+    __shared__ int stop;
+    if (sc->done) return;
+    const int k = sc->k;
+    if (threadIdx.x == 0) {
+        double s = 0.0, s2 = 0.0;
+        for (int b = 0; b < npart; ++b) {
+            s += partials[2 * b];
+            s2 += partials[2 * b + 1];
+        }
+        sc->sum_r = s;
+        sc->sumsq_r = s2;
+        sc->f = 0.5 * s2;
+        stop = 0;
+        if (!first) {
+            const int it = sc->iter;
+            if (tr.objective) tr.objective[it] = sc->f;
+            if (tr.mu) tr.mu[it] = sc->mu;
+            if (tr.backtracks) tr.backtracks[it] = sc->bt_last;
+            if (tr.changed) tr.changed[it] = sc->changed;
+            sc->iter = it + 1;
+            if (sc->step < sc->tol) {
+                sc->status = IHT_OK;
+                stop = 1;
+            } else if (sc->iter >= sc->max_iter) {
+                sc->status = IHT_ENOTCONV;
+                stop = 1;
+            }
+        }
+    }
+    __syncthreads();
+    if (!first) {
+        const int it = sc->iter - 1;
+        for (int c = threadIdx.x; c < k; c += blockDim.x) {
+            S[c] = Sp[c];
+            bS[c] = bSp[c];
+            if (tr.supp) tr.supp[(size_t)it * k + c] = Sp[c];
+            if (tr.beta) tr.beta[(size_t)it * k + c] = bSp[c];
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0 && stop) sc->done = 1;
+}
+
+__global__ void k_center(const double *__restrict__ r64, const int32_t *__restrict__ used,
+                         int64_t n_pad, const Scalars *sc, float *__restrict__ r32)
+{
+    if (sc->done) return;
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n_pad) return;
+    const double mean = sc->sum_r / (double)sc->n_rows;
+    r32[i] = used[i] ? (float)(r64[i] - mean) : 0.0f;
+}
+
+__global__ void k_check_finite(const double *__restrict__ y, int64_t n, Scalars *sc)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n && !isfinite(y[i])) atomicOr(&sc->err, 1);
+}
+
+// ---------------------------------------------------------------------------
+// Host orchestration of one solve.
+
+struct SolveArgs {
+    int k;
+    const iht_options *opt;
+    TraceDev tr;
+};
+
+int launch_merge(iht_dataset *ds, int k, int K)
+{
+    static thread_local int configured_dev = -1;
+    const int smem = (int)sizeof(MergeShared);
+    if (configured_dev != ds->ctx->device) {
+        IHT_CUDA(cudaFuncSetAttribute(k_merge, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+        configured_dev = ds->ctx->device;
+    }
+    Workspace *ws = ds->ws;
+    MergeArgs A;
+    A.G = ds->G;
+    A.stride = ds->stride;
+    A.g = ws->g;
+    A.u64 = ws->u64;
+    A.v64 = ws->v64;
+    A.used = ws->used;
+    A.S = ws->S;
+    A.bS = ws->bS;
+    A.cand = ws->cand;
+    A.K = K;
+    A.partials = ws->partials;
+    A.npart = zmul_blocks(ds);
+    A.Sp = ws->Sp;
+    A.bSp = ws->bSp;
+    A.sc = ws->sc;
+    k_merge<<<1, kMergeThreads, smem, ds->ctx->stream>>>(A);
+    note_launch();
+    IHT_CUDA(cudaGetLastError());
+    return IHT_OK;
+}
+
+int launch_grad(iht_dataset *ds, int impl, const int32_t *done, bool profile)
+{
+    Workspace *ws = ds->ws;
+    cudaStream_t s = ds->ctx->stream;
+    const bool rec = profile && ws->nprof < kProfEvents;
+    if (rec) IHT_CUDA(cudaEventRecord(ws->prof_ev[2 * ws->nprof], s));
+    int rc = impl == 2 ? launch_grad_tc(ds, ws->r32, ws->g, done)
+                       : launch_grad_simt(ds, ws->r32, ws->g, done);
+    if (rc) return rc;
+    if (rec) {
+        IHT_CUDA(cudaEventRecord(ws->prof_ev[2 * ws->nprof + 1], s));
+        ++ws->nprof;
+    }
+    return IHT_OK;
+}
+
+// y64 and the row set are in place; runs the solve, leaves S/bS and scalars.
+int run_solve(iht_dataset *ds, int k, const iht_options *opt, int n_rows, const TraceDev &tr)
+{
+    Workspace *ws = ds->ws;
+    cudaStream_t s = ds->ctx->stream;
+    const int npart = zmul_blocks(ds);
+    const int K = (int)std::min<int64_t>(2 * (int64_t)k, ds->p);
+    int rc;
+
+    // scalars
+    Scalars h{};
+    h.c = opt->c;
+    h.kappa = opt->kappa;
+    h.tol = opt->tol;
+    h.max_iter = opt->max_iter;
+    h.max_backtrack = opt->max_backtrack;
+    h.k = k;
+    h.n_rows = n_rows;
+    h.status = IHT_ENOTCONV;
+    h.done = opt->max_iter <= 0 ? 1 : 0;
+    // err may already hold row / input flags: keep it
+    IHT_CUDA(cudaMemcpyAsync(ws->sc_host, ws->sc, sizeof(Scalars), cudaMemcpyDeviceToHost, s));
+    IHT_CUDA(cudaStreamSynchronize(s));
+    h.err = ws->sc_host->err;
+    if (h.err) return (h.err & 1) ? IHT_ENUMERIC : IHT_EINVAL;
+    if (opt->max_iter <= 0) h.status = IHT_ENOTCONV;
+    *ws->sc_host = h;
+    IHT_CUDA(cudaMemcpyAsync(ws->sc, ws->sc_host, sizeof(Scalars), cudaMemcpyHostToDevice, s));
+
+    // r = y (beta = 0), objective, centred residual, g^0, S^0 = top-k |g^0|
+    k_zmul<<<npart, 256, 0, s>>>(ds->G, ds->stride, ws->cols, 0, ws->coef, -1.0, ws->u64, ws->v64,
+                                 ws->used, ws->y64, ws->r64, ws->partials, nullptr);
+    k_finalize<<<1, 1024, 0, s>>>(ws->sc, ws->partials, npart, ws->S, ws->bS, ws->Sp, ws->bSp, tr, 1);
+    k_center<<<ceil_div(ds->n_pad, 256), 256, 0, s>>>(ws->r64, ws->used, ds->n_pad, ws->sc, ws->r32);
+    note_launch(3);
+    IHT_CUDA(cudaGetLastError());
+    const int32_t *done = &ws->sc->done;
+    const bool prof = opt->profile != 0;
+    ws->nprof = 0;
+    if (prof && !ws->prof_ev[0]) {
+        for (int e = 0; e < 2 * kProfEvents; ++e) IHT_CUDA(cudaEventCreate(&ws->prof_ev[e]));
+    }
+    if ((rc = launch_grad(ds, opt->grad_impl, done, prof))) return rc;
+    if ((rc = select_topk(ds->ctx, ws->g, ds->p, k, ws->S, done))) return rc;
+    IHT_CUDA(cudaMemsetAsync(ws->bS, 0, sizeof(double) * k, s));
+
+    for (int it = 0; it < opt->max_iter; ++it) {
+        if (it > 0 && (rc = launch_grad(ds, opt->grad_impl, done, prof))) return rc;
+        if ((rc = select_topk(ds->ctx, ws->g, ds->p, K, ws->cand, done))) return rc;
+        k_gather_gS<<<1, 1024, 0, s>>>(ws->g, ws->S, k, ws->coef, ws->sc);
+        k_zmul<<<npart, 256, 0, s>>>(ds->G, ds->stride, ws->S, k, ws->coef, 1.0, ws->u64, ws->v64,
+                                     ws->used, nullptr, ws->zv, ws->partials, done);
+        if ((rc = launch_merge(ds, k, K))) return rc;
+        k_zmul<<<npart, 256, 0, s>>>(ds->G, ds->stride, ws->Sp, k, ws->bSp, -1.0, ws->u64, ws->v64,
+                                     ws->used, ws->y64, ws->r64, ws->partials, done);
+        k_finalize<<<1, 1024, 0, s>>>(ws->sc, ws->partials, npart, ws->S, ws->bS, ws->Sp, ws->bSp,
+                                      tr, 0);
+        k_center<<<ceil_div(ds->n_pad, 256), 256, 0, s>>>(ws->r64, ws->used, ds->n_pad, ws->sc,
+                                                          ws->r32);
+        note_launch(5);   // gather, zmul, zmul, finalize, center (merge counts itself)
+        IHT_CUDA(cudaGetLastError());
+        IHT_CUDA(cudaMemcpyAsync(&ws->sc_host->done, &ws->sc->done, sizeof(int32_t),
+                                 cudaMemcpyDeviceToHost, s));
+        IHT_CUDA(cudaStreamSynchronize(s));
+        if (ws->sc_host->done) break;
+    }
+    IHT_CUDA(cudaMemcpyAsync(ws->sc_host, ws->sc, sizeof(Scalars), cudaMemcpyDeviceToHost, s));
+    IHT_CUDA(cudaStreamSynchronize(s));
+    ws->prof_ms = 0.0;
+    for (int e = 0; prof && e < ws->nprof; ++e) {
+        float ms = 0.0f;
+        IHT_CUDA(cudaEventElapsedTime(&ms, ws->prof_ev[2 * e], ws->prof_ev[2 * e + 1]));
+        ws->prof_ms += ms;
+    }
+    return IHT_OK;
+}
+
+int run_solve_host(iht_dataset *ds, int k, const iht_options *opt, int n_rows, iht_trace *trace,
+                   int max_iter)
+{
+    TraceDev tr{};
+    void *buf = nullptr;
+    const size_t T = (size_t)std::max(max_iter, 1);
+    if (trace) {
+        const size_t bytes = T * (2 * sizeof(double) + 2 * sizeof(int32_t)) +
+                             T * k * (sizeof(int32_t) + sizeof(double));
+        IHT_CUDA(cudaMalloc(&buf, bytes));
+        char *p = (char *)buf;
+        tr.objective = (double *)p; p += T * sizeof(double);
+        tr.mu = (double *)p; p += T * sizeof(double);
+        tr.beta = (double *)p; p += T * k * sizeof(double);
+        tr.backtracks = (int32_t *)p; p += T * sizeof(int32_t);
+        tr.changed = (int32_t *)p; p += T * sizeof(int32_t);
+        tr.supp = (int32_t *)p;
+    }
+    int rc = run_solve(ds, k, opt, n_rows, tr);
+    if (rc == IHT_OK && trace) {
+        cudaStream_t s = ds->ctx->stream;
+        const int it = ds->ws->sc_host->iter;
+        auto get = [&](void *dst, const void *src, size_t bytes) -> int {
+            if (dst && bytes) IHT_CUDA(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToHost, s));
+            return IHT_OK;
+        };
+        if ((rc = get(trace->objective, tr.objective, it * sizeof(double))) ||
+            (rc = get(trace->mu, tr.mu, it * sizeof(double))) ||
+            (rc = get(trace->backtracks, tr.backtracks, it * sizeof(int32_t))) ||
+            (rc = get(trace->changed, tr.changed, it * sizeof(int32_t))) ||
+            (rc = get(trace->supp, tr.supp, (size_t)it * k * sizeof(int32_t))) ||
+            (rc = get(trace->beta, tr.beta, (size_t)it * k * sizeof(double)))) {
+        }
+        if (rc == IHT_OK) IHT_CUDA(cudaStreamSynchronize(s));
+    }
+    if (buf) cudaFree(buf);
+    return rc;
+}
+
+int check_finite_y(iht_dataset *ds, int64_t n_rows, const double *y_dev)
+{
+    if (n_rows > 0) {
+        k_check_finite<<<ceil_div(n_rows, 256), 256, 0, ds->ctx->stream>>>(y_dev, n_rows, ds->ws->sc);
+        note_launch();
+    }
+    IHT_CUDA(cudaGetLastError());
+    return IHT_OK;
+}
+
+}  // namespace iht
+
+namespace iht {
+
+__global__ void k_gather_rows(const int32_t *__restrict__ rows, int64_t n_rows,
+                              const double *__restrict__ src, double *__restrict__ dst)
+{
+    const int64_t a = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (a < n_rows) dst[a] = src[rows ? rows[a] : a];
+}
+
+int gather_rows_f64(iht_dataset *ds, const int32_t *rows_dev, int64_t n_rows, const double *src,
+                    double *dst)
+{
+    if (n_rows > 0) {
+        k_gather_rows<<<ceil_div(n_rows, 256), 256, 0, ds->ctx->stream>>>(rows_dev, n_rows, src, dst);
+        note_launch();
+    }
+    IHT_CUDA(cudaGetLastError());
+    return IHT_OK;
+}
+
+__global__ void k_scatter_beta(const int32_t *__restrict__ S, const double *__restrict__ bS, int k,
+                               double *__restrict__ beta)
+{
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c < k) beta[S[c]] = bS[c];
+}
+
+// beta_out (device, p doubles): zeros off the support, beta_S on it.
+int write_beta_device(iht_dataset *ds, int k, double *beta_out)
+{
+    cudaStream_t s = ds->ctx->stream;
+    IHT_CUDA(cudaMemsetAsync(beta_out, 0, sizeof(double) * ds->p, s));
+    k_scatter_beta<<<ceil_div(k, 256), 256, 0, s>>>(ds->ws->S, ds->ws->bS, k, beta_out);
+    note_launch();
+    IHT_CUDA(cudaGetLastError());
+    return IHT_OK;
+}
+
+}  // namespace iht
