@@ -42,7 +42,7 @@ void free_workspace(Workspace *ws)
 {
     if (!ws) return;
     void *ptrs[] = {ws->used, ws->rowmask, ws->counts, ws->u64, ws->v64, ws->u32, ws->v32,
-                    ws->y64, ws->r64, ws->zv, ws->r32, ws->g, ws->partials, ws->rows_dev,
+                    ws->y64, ws->r64, ws->zv, ws->r32, ws->g, ws->Mj, ws->partials, ws->zpart, ws->rows_dev,
                     ws->ybuf, ws->fbuf, ws->cand, ws->S, ws->Sp, ws->bS, ws->bSp, ws->coef,
                     ws->cols, ws->sc};
     for (void *p : ptrs)
@@ -78,7 +78,9 @@ int ensure_workspace(iht_dataset *ds, int)
     ALLOC(zv, sizeof(double) * np);
     ALLOC(r32, sizeof(float) * np);
     ALLOC(g, sizeof(float) * p);
+    ALLOC(Mj, sizeof(float) * p);
     ALLOC(partials, sizeof(double) * 2 * kPartials);
+    ALLOC(zpart, sizeof(double) * (size_t)kZmulMaxGroups * np);
     ALLOC(rows_dev, sizeof(int32_t) * np);
     ALLOC(ybuf, sizeof(double) * np);
     ALLOC(fbuf, sizeof(float) * np);
@@ -101,7 +103,7 @@ int ensure_workspace(iht_dataset *ds, int)
     }
     int rc = ensure_selwork(ds->ctx, p);
     if (rc) return rc;
-    if (ceil_div(ds->stride, 256) > kPartials) return IHT_EINVAL;   // n above 1M samples
+    if (ceil_div(ds->n_pad, 256) > kPartials) return IHT_EINVAL;   // n above 262k samples
     return IHT_OK;
 }
 
@@ -250,9 +252,14 @@ int iht_load_bed(iht_ctx *ctx, const uint8_t *bed, size_t bed_bytes, int mem, in
     ds->ctx = ctx;
     ds->n = n;
     ds->p = p;
-    ds->stride = (nbytes + 15) / 16 * 16;
+    ds->stride = (nbytes + 127) / 128 * 128;
+    ds->rowb = (nbytes + 15) / 16 * 16;
     ds->n_pad = 4 * ds->stride;
     ds->ws = nullptr;
+    ds->miss_off = nullptr;
+    ds->miss_idx = nullptr;
+    ds->miss_total = 0;
+    ds->miss_idx16 = n <= 65536;
     cudaError_t e = cudaMalloc(&ds->G, (size_t)(p * ds->stride));
     if (e != cudaSuccess) {
         set_cuda_error(e, "cudaMalloc(genotypes)");
@@ -267,6 +274,7 @@ int iht_load_bed(iht_ctx *ctx, const uint8_t *bed, size_t bed_bytes, int mem, in
         rc = IHT_ECUDA;
     }
     if (rc == IHT_OK) rc = launch_fix_padding(ds);
+    if (rc == IHT_OK) rc = build_missing_lists(ds);
     if (rc == IHT_OK) {
         e = cudaStreamSynchronize(ctx->stream);
         if (e != cudaSuccess) {
@@ -276,6 +284,8 @@ int iht_load_bed(iht_ctx *ctx, const uint8_t *bed, size_t bed_bytes, int mem, in
     }
     if (rc != IHT_OK) {
         cudaFree(ds->G);
+        if (ds->miss_off) cudaFree(ds->miss_off);
+        if (ds->miss_idx) cudaFree(ds->miss_idx);
         delete ds;
         return rc;
     }
@@ -290,6 +300,8 @@ int iht_dataset_free(iht_dataset *ds)
     cudaStreamSynchronize(ds->ctx->stream);
     free_workspace(ds->ws);
     cudaFree(ds->G);
+    if (ds->miss_off) cudaFree(ds->miss_off);
+    if (ds->miss_idx) cudaFree(ds->miss_idx);
     delete ds;
     return IHT_OK;
 }
@@ -338,11 +350,7 @@ int iht_gradient(iht_dataset *ds, const int32_t *rows, int64_t n_rows, const flo
     const int32_t *rows_dev = nullptr;
     if ((rc = prepare_rows(ds, rows, n_rows, IHT_DEVICE, &rows_dev))) return rc;
     if ((rc = scatter_rows_f32(ds, rows_dev, n_rows, r, ds->ws->r32))) return rc;
-    if (impl == 2)
-        rc = launch_grad_tc(ds, ds->ws->r32, g_out, nullptr);
-    else
-        rc = launch_grad_simt(ds, ds->ws->r32, g_out, nullptr);
-    if (rc) return rc;
+    if ((rc = launch_grad_impl(ds, impl, ds->ws->r32, g_out, nullptr))) return rc;
     IHT_CUDA(cudaStreamSynchronize(ds->ctx->stream));
     return IHT_OK;
 }

@@ -2,7 +2,8 @@
 //
 // Device data layout (one dataset):
 //   G        uint8[p][stride]   PLINK 2-bit codes, SNP-major; stride = ceil(n/4)
-//                               rounded up to 16 bytes; pad samples carry the
+//                               rounded up to 128 bytes so rows start on DRAM
+//                               sector boundaries; pad samples carry the
 //                               missing code 01 so every sum skips them.
 //   used     int32[n_pad]       1 for rows of the current solve, else 0
 //                               (n_pad = 4 * stride samples).
@@ -26,6 +27,7 @@ constexpr int kMaxK = 1024;            // largest sparsity level accepted
 constexpr int kMaxCand = 2 * kMaxK;    // candidate list of the projection
 constexpr int kSelBins = 2048;         // radix-select histogram bins
 constexpr int kPartials = 1024;        // max per-block partial sums
+constexpr int kZmulMaxGroups = 2 * kMaxK / 4;   // column groups of the sparse product
 
 struct Scalars {                       // device-resident state of one solve
     double num;                        // ||g_S||^2
@@ -73,8 +75,17 @@ struct iht_ctx {
 
 struct iht_dataset {
     iht_ctx *ctx;
-    int64_t n, p, stride, n_pad;
+    int64_t n, p;
+    int64_t stride;      // row pitch in bytes: ceil(n/4) rounded up to 128 (sector aligned rows)
+    int64_t rowb;        // bytes a kernel reads per row: ceil(n/4) rounded up to 16
+    int64_t n_pad;       // 4 * stride samples
     uint8_t *G;
+    // missing calls (code 01), built once at upload: sample offsets of SNP j
+    // are miss_idx[miss_off[j] .. miss_off[j+1]) (uint16 when n <= 65536)
+    int64_t *miss_off;
+    void *miss_idx;
+    int64_t miss_total;
+    bool miss_idx16;
     iht::Workspace *ws;
 };
 
@@ -90,7 +101,9 @@ struct Workspace {
     float *u32 = nullptr, *v32 = nullptr;
     double *y64 = nullptr, *r64 = nullptr, *zv = nullptr;
     float *r32 = nullptr, *g = nullptr;
+    float *Mj = nullptr;                   // per-SNP sum of r over missing calls
     double *partials = nullptr;        // kPartials * 2
+    double *zpart = nullptr;           // kZmulMaxGroups x n_pad partial products
     int32_t *rows_dev = nullptr;       // int32[n]: host row lists copied here
     double *ybuf = nullptr;            // double[n]: host phenotypes copied here
     float *fbuf = nullptr;             // float[n_pad]: scratch
@@ -127,6 +140,8 @@ void free_workspace(Workspace *ws);
 // kernels launched from the host side (stream-ordered) ---------------------
 // geno.cu
 int launch_fix_padding(iht_dataset *ds);
+int build_missing_lists(iht_dataset *ds);
+int launch_missing_sums(iht_dataset *ds, const float *r32, float *M, const int32_t *done);
 int setup_rows(iht_dataset *ds, const int32_t *rows_dev, int64_t n_rows);
 int launch_counts(iht_dataset *ds, int64_t n_rows);
 int scatter_rows_f64(iht_dataset *ds, const int32_t *rows_dev, int64_t n_rows, const double *src,
@@ -136,6 +151,12 @@ int scatter_rows_f32(iht_dataset *ds, const int32_t *rows_dev, int64_t n_rows, c
 // grad_simt.cu / grad_tc.cu
 int launch_grad_simt(iht_dataset *ds, const float *r32, float *g, const int32_t *done);
 int launch_grad_tc(iht_dataset *ds, const float *r32, float *g, const int32_t *done);
+bool grad_tc_supported(const iht_dataset *ds);
+int prepare_grad_tc(iht_dataset *ds, const float *r32, const int32_t *done);
+int launch_grad_tc_main(iht_dataset *ds, const float *r32, float *g, const int32_t *done);
+int grad_tc_status(iht_dataset *ds, int *timed_out);
+// impl: 0 default (tensor cores when supported), 1 CUDA cores, 2 tensor cores
+int launch_grad_impl(iht_dataset *ds, int impl, const float *r32, float *g, const int32_t *done);
 // select.cu
 int ensure_selwork(iht_ctx *ctx, int64_t p);
 int select_topk(iht_ctx *ctx, const float *key_src, int64_t p, int32_t K, int32_t *out_idx,

@@ -95,24 +95,31 @@ int setup_rows(iht_dataset *ds, const int32_t *rows_dev, int64_t n_rows)
 
 // One warp per SNP: masked popcounts, then the FP64 statistics.
 __global__ void __launch_bounds__(256) k_counts(const uint8_t *__restrict__ G, int64_t p,
-                                                int64_t stride, const uint32_t *__restrict__ rowmask,
+                                                int64_t stride, int64_t rowb,
+                                                const uint32_t *__restrict__ rowmask,
                                                 int64_t n_rows, int32_t *__restrict__ counts,
                                                 double *__restrict__ u64, double *__restrict__ v64,
                                                 float *__restrict__ u32, float *__restrict__ v32)
 {
     const int lane = threadIdx.x & 31;
     const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
-    const int64_t nwords = stride / 4;
+    const int64_t nwords = rowb / 4;
     for (int64_t j = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); j < p;
          j += nwarps) {
         const uint32_t *row = reinterpret_cast<const uint32_t *>(G + j * stride);
         int c1 = 0, c2 = 0, c3 = 0;
-        for (int64_t c = lane; c < nwords; c += 32) {
-            const uint32_t w = __ldg(row + c) & __ldg(rowmask + c);
-            const uint32_t lo = w & 0x55555555u, hi = (w >> 1) & 0x55555555u;
-            c3 += __popc(lo & hi);
-            c1 += __popc(lo & ~hi);
-            c2 += __popc(hi & ~lo);
+        const uint4 *row4 = reinterpret_cast<const uint4 *>(row);
+        const uint4 *mask4 = reinterpret_cast<const uint4 *>(rowmask);
+        for (int64_t c = lane; c < nwords / 4; c += 32) {
+            const uint4 w4 = __ldcs(row4 + c), m4 = __ldg(mask4 + c);
+            const uint32_t ws[4] = {w4.x & m4.x, w4.y & m4.y, w4.z & m4.z, w4.w & m4.w};
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const uint32_t lo = ws[q] & 0x55555555u, hi = (ws[q] >> 1) & 0x55555555u;
+                c3 += __popc(lo & hi);
+                c1 += __popc(lo & ~hi);
+                c2 += __popc(hi & ~lo);
+            }
         }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
@@ -150,7 +157,8 @@ int launch_counts(iht_dataset *ds, int64_t n_rows)
 {
     Workspace *ws = ds->ws;
     const int blocks = (int)std::min<int64_t>(ceil_div(ds->p, 8), (int64_t)ds->ctx->num_sms * 16);
-    k_counts<<<blocks, 256, 0, ds->ctx->stream>>>(ds->G, ds->p, ds->stride, ws->rowmask, n_rows,
+    k_counts<<<blocks, 256, 0, ds->ctx->stream>>>(ds->G, ds->p, ds->stride, ds->rowb, ws->rowmask,
+                                                  n_rows,
                                                   ws->counts, ws->u64, ws->v64, ws->u32, ws->v32);
     note_launch();
     IHT_CUDA(cudaGetLastError());
@@ -189,6 +197,158 @@ int scatter_rows_f32(iht_dataset *ds, const int32_t *rows_dev, int64_t n_rows, c
         k_scatter<float><<<ceil_div(n_rows, 256), 256, 0, s>>>(rows_dev, n_rows, src, dst, ds->n);
         note_launch();
     }
+    IHT_CUDA(cudaGetLastError());
+    return IHT_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Missing-call lists: the gradient needs M_j = sum of r over the missing calls
+// of SNP j; missing calls are rare (1-2 %), so a per-SNP list of their sample
+// offsets, built once, lets a small pass form M_j and keeps the dense pass free
+// of data-dependent branches.
+
+// Missing-code mask of word c (samples 16c..16c+15) restricted to samples < n.
+__device__ __forceinline__ uint32_t missing_mask(uint32_t w, int64_t c, int64_t n)
+{
+    uint32_t mm = w & ~(w >> 1) & 0x55555555u;
+    const int64_t left = n - 16 * c;
+    if (left < 16) mm &= left > 0 ? (uint32_t)((1ull << (2 * left)) - 1ull) : 0u;
+    return mm;
+}
+
+__global__ void __launch_bounds__(256) k_miss_count(const uint8_t *__restrict__ G, int64_t p,
+                                                    int64_t stride, int64_t n,
+                                                    int32_t *__restrict__ cnt)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    const int64_t nw = (n + 15) / 16;
+    for (int64_t j = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); j < p; j += nwarps) {
+        const uint32_t *row = reinterpret_cast<const uint32_t *>(G + j * stride);
+        int c = 0;
+        for (int64_t w = lane; w < nw; w += 32) c += __popc(missing_mask(__ldg(row + w), w, n));
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+        if (lane == 0) cnt[j] = c;
+    }
+}
+
+template <typename IdxT>
+__global__ void __launch_bounds__(256) k_miss_fill(const uint8_t *__restrict__ G, int64_t p,
+                                                   int64_t stride, int64_t n,
+                                                   const int64_t *__restrict__ off,
+                                                   IdxT *__restrict__ idx)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    const int64_t nw = (n + 15) / 16;
+    for (int64_t j = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); j < p; j += nwarps) {
+        const uint32_t *row = reinterpret_cast<const uint32_t *>(G + j * stride);
+        int64_t pos = off[j];
+        for (int64_t base = 0; base < nw; base += 32) {
+            const int64_t w = base + lane;
+            uint32_t mm = w < nw ? missing_mask(__ldg(row + w), w, n) : 0u;
+            const int c = __popc(mm);
+            int x = c;   // inclusive warp scan
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int y = __shfl_up_sync(0xffffffffu, x, o);
+                if (lane >= o) x += y;
+            }
+            int64_t q = pos + x - c;
+            while (mm) {
+                const int b = __ffs(mm) - 1;
+                idx[q++] = (IdxT)(16 * w + (b >> 1));
+                mm &= mm - 1;
+            }
+            pos += __shfl_sync(0xffffffffu, x, 31);
+        }
+    }
+}
+
+int build_missing_lists(iht_dataset *ds)
+{
+    cudaStream_t s = ds->ctx->stream;
+    const int64_t p = ds->p;
+    int32_t *cnt = nullptr;
+    IHT_CUDA(cudaMalloc(&cnt, sizeof(int32_t) * p));
+    const int blocks = (int)std::min<int64_t>(ceil_div(p, 8), (int64_t)ds->ctx->num_sms * 16);
+    k_miss_count<<<blocks, 256, 0, s>>>(ds->G, p, ds->stride, ds->n, cnt);
+    note_launch();
+    int32_t *hc = (int32_t *)malloc(sizeof(int32_t) * p);
+    int64_t *ho = (int64_t *)malloc(sizeof(int64_t) * (p + 1));
+    if (!hc || !ho) {
+        free(hc);
+        free(ho);
+        cudaFree(cnt);
+        return IHT_ENOMEM;
+    }
+    cudaError_t e = cudaMemcpyAsync(hc, cnt, sizeof(int32_t) * p, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    cudaFree(cnt);
+    if (e != cudaSuccess) {
+        free(hc);
+        free(ho);
+        set_cuda_error(e, "missing-call counts");
+        return IHT_ECUDA;
+    }
+    ho[0] = 0;
+    for (int64_t j = 0; j < p; ++j) ho[j + 1] = ho[j] + hc[j];
+    free(hc);
+    ds->miss_total = ho[p];
+    e = cudaMalloc(&ds->miss_off, sizeof(int64_t) * (p + 1));
+    if (e == cudaSuccess)
+        e = cudaMalloc(&ds->miss_idx, std::max<int64_t>(1, ds->miss_total) * (ds->miss_idx16 ? 2 : 4));
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(ds->miss_off, ho, sizeof(int64_t) * (p + 1), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    free(ho);
+    if (e != cudaSuccess) {
+        set_cuda_error(e, "missing-call lists");
+        return e == cudaErrorMemoryAllocation ? IHT_ENOMEM : IHT_ECUDA;
+    }
+    if (ds->miss_idx16)
+        k_miss_fill<uint16_t><<<blocks, 256, 0, s>>>(ds->G, p, ds->stride, ds->n, ds->miss_off,
+                                                     (uint16_t *)ds->miss_idx);
+    else
+        k_miss_fill<int32_t><<<blocks, 256, 0, s>>>(ds->G, p, ds->stride, ds->n, ds->miss_off,
+                                                    (int32_t *)ds->miss_idx);
+    note_launch();
+    IHT_CUDA(cudaGetLastError());
+    return IHT_OK;
+}
+
+// M_j = sum of r over the missing calls of SNP j (one warp per SNP, list order).
+template <typename IdxT>
+__global__ void __launch_bounds__(256) k_missing_sum(const int64_t *__restrict__ off,
+                                                     const IdxT *__restrict__ idx, int64_t p,
+                                                     const float *__restrict__ r32,
+                                                     float *__restrict__ M,
+                                                     const int32_t *__restrict__ done)
+{
+    if (done && *done) return;
+    const int lane = threadIdx.x & 31;
+    const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t j = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); j < p; j += nwarps) {
+        const int64_t e0 = off[j], e1 = off[j + 1];
+        float m = 0.0f;
+        for (int64_t e = e0 + lane; e < e1; e += 32) m += __ldg(r32 + idx[e]);
+        m = warp_sum(m);
+        if (lane == 0) M[j] = m;
+    }
+}
+
+int launch_missing_sums(iht_dataset *ds, const float *r32, float *M, const int32_t *done)
+{
+    cudaStream_t s = ds->ctx->stream;
+    const int blocks = (int)std::min<int64_t>(ceil_div(ds->p, 8), (int64_t)ds->ctx->num_sms * 16);
+    if (ds->miss_idx16)
+        k_missing_sum<uint16_t><<<blocks, 256, 0, s>>>(ds->miss_off, (const uint16_t *)ds->miss_idx,
+                                                       ds->p, r32, M, done);
+    else
+        k_missing_sum<int32_t><<<blocks, 256, 0, s>>>(ds->miss_off, (const int32_t *)ds->miss_idx,
+                                                      ds->p, r32, M, done);
+    note_launch();
     IHT_CUDA(cudaGetLastError());
     return IHT_OK;
 }

@@ -33,7 +33,8 @@ __device__ __forceinline__ void accum_byte(uint32_t byte, float4 r, float &s1, f
 }
 
 __global__ void __launch_bounds__(256) k_grad_simt(const uint8_t *__restrict__ G, int64_t p,
-                                                   int64_t stride, const float *__restrict__ r32,
+                                                   int64_t stride, int64_t rowb,
+                                                   const float *__restrict__ r32,
                                                    int64_t n_pad, const float *__restrict__ u32,
                                                    const float *__restrict__ v32,
                                                    float *__restrict__ g,
@@ -54,7 +55,7 @@ __global__ void __launch_bounds__(256) k_grad_simt(const uint8_t *__restrict__ G
     const float R = (float)block_sum(acc, red);   // synchronises the block
 
     const int lane = threadIdx.x & 31;
-    const int64_t nw = stride / 4;
+    const int64_t nw = rowb / 4;
     const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
     for (int64_t j = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); j < p;
          j += nwarps) {
@@ -99,11 +100,18 @@ int launch_grad_simt(iht_dataset *ds, const float *r32, float *g, const int32_t 
     if (per_sm < 1) return IHT_EINVAL;   // residual does not fit in shared memory
     const int64_t want = (ds->p + 7) / 8;
     const int blocks = (int)std::min<int64_t>(want, (int64_t)per_sm * ds->ctx->num_sms);
-    k_grad_simt<<<blocks, 256, smem, ds->ctx->stream>>>(ds->G, ds->p, ds->stride, r32, ds->n_pad,
+    k_grad_simt<<<blocks, 256, smem, ds->ctx->stream>>>(ds->G, ds->p, ds->stride, ds->rowb, r32,
+                                                        ds->n_pad,
                                                         ds->ws->u32, ds->ws->v32, g, done);
     note_launch();
     IHT_CUDA(cudaGetLastError());
     return IHT_OK;
+}
+
+int launch_grad_impl(iht_dataset *ds, int impl, const float *r32, float *g, const int32_t *done)
+{
+    if (impl == 2 || (impl == 0 && grad_tc_supported(ds))) return launch_grad_tc(ds, r32, g, done);
+    return launch_grad_simt(ds, r32, g, done);
 }
 
 }  // namespace iht

@@ -1,9 +1,633 @@
-// a2, tensor-core variant (tcgen05): not built yet; the CUDA-core kernel
-// serves every request until it is.
+// a2, tensor-core variant (tcgen05, sm_103a): g_j = v_j (S1_j - u_j (R - M_j)).
+//
+// The O(np) products S1_j = sum of dosage*r and M_j = sum of r over missing
+// calls run on the 5th-generation tensor cores; the CUDA cores only turn the
+// 2-bit codes into FP8 operands.  Decoding is the bottleneck of a CUDA-core
+// version (about a dozen instructions per genotype), so the MMA unit absorbs
+// the multiply-adds while the kernel stays bound by the HBM stream of packed
+// genotypes.
+//
+// The dense part, S1_j = sum over observed calls of x_ij r_i, runs on the
+// tensor cores (kind::f8f6f4, both operands E4M3, FP32 accumulate, M = 128
+// SNPs, N = 16, K = 32 samples):
+//   A: the dosage map.  With D = code << 3 (code in the exponent field: values
+//      2^-6 (0, 1, 2, 4) for codes 00, 01, 10, 11), A = D with code 01
+//      zeroed = 2^-5 x; two instructions per output word from a word of 16
+//      codes (byte k of word j = sample 4k+j).
+//   B: the residual as L = 5 E4M3 limbs, r ~ sum_l s_l q_l with s_l =
+//      s_0 2^(-4l), in the same permuted sample order; limb l is row l of the
+//      K-step's first 8-row group and the second group is one shared all-zero
+//      group (8 bytes per sample).
+// So S1 = 32 sum_l s_l acc[l].  The missing-call sums M_j (1-2 % of calls)
+// come from a per-SNP list of missing sample offsets built at upload (a small
+// warp-per-SNP pass before this one); with them in the hot loop the
+// data-dependent per-call branches cost more than the whole dense pass.
+//
+// Each tcgen05 instruction (an MMA or a commit) costs the SM's tensor front
+// end about 45 cycles whatever the operand size, so the kernel issues one MMA
+// per 4096 genotypes and one commit per four MMAs.
+//
+// Data movement (one persistent CTA per SM, four decoder warpgroups):
+//   * producer warps stream 128-row x 64-byte tiles of packed genotypes
+//     (256 samples of 128 SNPs) into shared memory with TMA (64-byte
+//     swizzle, up to six stages per warpgroup, as many as shared memory
+//     holds next to B and r: the stream is latency-bound, so the bytes in
+//     flight per SM set the bandwidth), one producer warp per warpgroup;
+//   * decoder thread r of a warpgroup owns row r of the tile: it reads its
+//     16-byte chunks from shared memory (the swizzle makes the 8 rows of a
+//     bank group distinct) and writes the FP8 map straight from registers to
+//     tensor memory (tcgen05.st);
+//   * one MMA warp per warpgroup issues the tcgen05.mma and commits;
+//   * B (8 bytes per sample) stays in shared memory.
+// Per warpgroup, tensor memory holds one 16-column accumulator and three
+// 32-column A buffers of four K-steps each.  Every hand-off is an mbarrier
+// (TMA transaction counts, tcgen05.commit for MMA completion), never a
+// block-wide barrier, and every wait is bounded: a timeout is reported
+// through TcParams::err instead of hanging.
+#include <cuda.h>
+#include <cuda_fp8.h>
+
 #include "common.cuh"
 
 namespace iht {
 
-int launch_grad_tc(iht_dataset *, const float *, float *, const int32_t *) { return IHT_EINVAL; }
+constexpr int kTcLimbs = 5;
+constexpr int kTcN = 16;
+constexpr int kTcStepSamples = 32;                 // K of one MMA (bytes of FP8)
+constexpr int kTcGroupBytes = 16;                  // packed bytes per chunk = 2 K-steps
+constexpr int kTcStageBytes = 64;                  // packed bytes per row per TMA stage
+constexpr int kTcStageSteps = 8;                   // K-steps per stage
+constexpr int kTcMaxStages = 6;                    // TMA stages per warpgroup (as smem allows)
+constexpr int kTcBufs = 3;                         // A buffers of kTcBufSteps K-steps
+constexpr int kTcBufSteps = 4;                     // K-steps per A buffer (one commit)
+constexpr int kTcNWG = 4;                          // decoder warpgroups per CTA
+constexpr int kTcThreads = kTcNWG * (128 + 32 + 32);   // decoders, MMA warps, TMA warps
+constexpr int kTcStageTile = 128 * kTcStageBytes;  // 8 KB
+
+constexpr uint32_t kTcSpin = 1u << 26;             // bounded waits
+
+struct TcParams {
+    float s0;        // scale of limb 0 (limb l: s0 * 2^-4l)
+    float R;         // sum of the residual over the samples
+    int err;         // 1: a bounded wait timed out
+    int pad;
+};
+
+__device__ __forceinline__ uint32_t smem_addr(const void *p)
+{
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+// ---------------------------------------------------------------------------
+// Residual -> E4M3 limbs in the B image (permuted K order, canonical layout):
+// [256 unused bytes][K-step 0 (256 bytes)]...[K-step S-1][256 zero bytes].
+
+__device__ __forceinline__ int b_offset(int64_t i, int limb)
+{
+    const int64_t s = i >> 5;                       // K-step
+    const int ii = (int)(i & 31);
+    const int wi = ii >> 4, q = ii & 15;            // 16-sample word, position in it
+    const int k = q >> 2, j = q & 3;                // output byte k of decoded word j
+    const int c = 4 * wi + j;                       // TMEM column within the step
+    const int kpos = 4 * c + k;                     // K index within the step
+    return 256 + (int)(s * 256) + (kpos >> 4) * 128 + limb * 16 + (kpos & 15);
+}
+
+__global__ void __launch_bounds__(1024) k_limbs(const float *__restrict__ r32, int64_t n_pad,
+                                                uint8_t *__restrict__ bimg, TcParams *prm,
+                                                const int32_t *__restrict__ done)
+{
+    __shared__ float smax[32];
+    __shared__ double red[32];
+    if (done && *done) return;
+    float m = 0.0f;
+    for (int64_t i = threadIdx.x; i < n_pad; i += blockDim.x) m = fmaxf(m, fabsf(r32[i]));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) smax[threadIdx.x >> 5] = m;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        m = threadIdx.x < (blockDim.x >> 5) ? smax[threadIdx.x] : 0.0f;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+        if (threadIdx.x == 0) smax[0] = m;
+    }
+    __syncthreads();
+    m = smax[0];
+    float s0 = 1.0f;
+    if (m > 0.0f) {
+        int e;
+        frexpf(m / 448.0f, &e);          // m/448 <= 2^e
+        s0 = ldexpf(1.0f, e);
+    }
+    double acc = 0.0;
+    for (int64_t i = threadIdx.x; i < n_pad; i += blockDim.x) {
+        float res = r32[i];
+        float s = s0;
+        acc += (double)res;
+#pragma unroll
+        for (int l = 0; l < kTcLimbs; ++l) {
+            const __nv_fp8_e4m3 q(res / s);
+            const float qf = (float)q;
+            bimg[b_offset(i, l)] = q.__x;
+            res -= s * qf;
+            s *= 0.0625f;
+        }
+    }
+    // the trailing zero group may hold limbs of an earlier, longer residual
+    for (int64_t b = threadIdx.x; b < 256; b += blockDim.x) bimg[256 + 256 * (n_pad >> 5) + b] = 0;
+    acc = block_sum(acc, red);
+    if (threadIdx.x == 0) {
+        prm->s0 = s0;
+        prm->R = (float)acc;
+        prm->err = 0;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// mbarrier / TMA / tcgen05 helpers
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count));
+}
+
+// true when the phase with the given parity has completed; false on timeout
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity)
+{
+    const uint32_t a = smem_addr(bar);
+    for (uint32_t it = 0; it < kTcSpin; ++it) {
+        uint32_t ok;
+        asm volatile(
+            "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+            "selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(ok)
+            : "r"(a), "r"(parity)
+            : "memory");
+        if (ok) return true;
+    }
+    return false;
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, int x, int y,
+                                            uint64_t *bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, "
+        "%3}], [%4];" ::"r"(smem_addr(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_addr(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+__device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t (&v)[16])
+{
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,"
+        "%13,%14,%15,%16};" ::"r"(taddr),
+        "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7]),
+        "r"(v[8]), "r"(v[9]), "r"(v[10]), "r"(v[11]), "r"(v[12]), "r"(v[13]), "r"(v[14]), "r"(v[15])
+        : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&v)[16])
+{
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,"
+        "%15}, [%16];"
+        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
+          "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]),
+          "=r"(v[14]), "=r"(v[15])
+        : "r"(taddr)
+        : "memory");
+}
+
+__device__ __forceinline__ void mma_f8(uint32_t d_tmem, uint32_t a_tmem, uint64_t b_desc,
+                                       uint32_t idesc, uint32_t accumulate)
+{
+    asm volatile(
+        "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+        "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], [%1], %2, %3, p;\n}\n" ::"r"(d_tmem),
+        "r"(a_tmem), "l"(b_desc), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t *bar)
+{
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                     smem_addr(bar))
+                 : "memory");
+}
+
+// K-major, no swizzle: core matrices of 8 rows x 16 bytes; LBO = 128 bytes
+// between the two K halves, SBO = bytes between the two 8-row groups.
+__device__ __forceinline__ uint64_t b_desc(uint32_t saddr, uint32_t sbo)
+{
+    return (uint64_t)((saddr >> 4) & 0x3FFFu) | ((uint64_t)(128u >> 4) << 16) |
+           ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
+}
+
+// D FP32 (bit 4), A/B E4M3 (0), K-major, N = 16 (N>>3 at bit 17), M = 128 (M>>4 at bit 24)
+constexpr uint32_t kIdescF8 = (1u << 4) | ((uint32_t)(kTcN >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
+
+// Dosage map of one 16-code input word.  Per 2-bit field, f = (c1, c1 & c0):
+// 00 for codes 00 and 01, 10 for het, 11 for hom-alt; moving a field to bits
+// 3..4 of a byte gives E4M3 0, 2^-5, 2^-4 = 2^-5 x.  Output word j holds
+// samples 4k+j (byte k).
+__device__ __forceinline__ void decode_word(uint32_t w, uint32_t *a)
+{
+    const uint32_t f = w & ((w >> 1) | 0xAAAAAAAAu);     // even bits: c0 & c1; odd bits: c1
+    const uint32_t m = 0x18181818u;
+    a[0] = (f << 3) & m;
+    a[1] = (f << 1) & m;
+    a[2] = (f >> 1) & m;
+    a[3] = (f >> 3) & m;
+}
+
+struct TcPipe {
+    uint64_t tma_full[kTcMaxStages];   // producer -> decoders: stage landed (tx count)
+    uint64_t tma_empty[kTcMaxStages];  // decoders -> producer: stage read (128 arrivals)
+    uint64_t full[kTcBufs];         // decoders -> MMA warp: A buffer written (128 arrivals)
+    uint64_t empty[kTcBufs];        // MMA warp -> decoders: MMAs reading the buffer done
+    uint64_t accfull;               // MMA warp -> decoders: tile accumulators complete
+    uint64_t accempty;              // decoders -> MMA warp: accumulators read out (128)
+};
+
+// One 16-byte chunk (64 samples = 2 K-steps) of the row into half h of A
+// buffer `buf`.
+__device__ __forceinline__ void tc_put_chunk(uint32_t tb, uint32_t lane_off, uint32_t buf, int h,
+                                             uint4 x)
+{
+    uint32_t v[16];
+    decode_word(x.x, &v[0]);
+    decode_word(x.y, &v[4]);
+    decode_word(x.z, &v[8]);
+    decode_word(x.w, &v[12]);
+    tmem_st16(tb + 32 + 32 * buf + 16 * h + lane_off, v);
+}
+
+// Read out the accumulator of local tile t and write g for this thread's row.
+__device__ __forceinline__ bool tc_epilogue(TcPipe &P, uint32_t tb, uint32_t lane_off, int t,
+                                            int64_t row, int64_t p, float s0, float R,
+                                            const float *__restrict__ Mj,
+                                            const float *__restrict__ u32,
+                                            const float *__restrict__ v32, float *__restrict__ g,
+                                            volatile int &abort_flag)
+{
+    bool ok = true;
+    if (!mbar_wait(&P.accfull, (uint32_t)t & 1u)) {
+        abort_flag = 1;
+        ok = false;
+    }
+    tc_fence_after();
+    uint32_t acc[16];
+    tmem_ld16(tb + lane_off, acc);
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+    tc_fence_before();
+    mbar_arrive(&P.accempty);
+    if (ok && row >= 0 && row < p) {
+        float Ssum = 0.0f, s = s0;
+#pragma unroll
+        for (int l = 0; l < kTcLimbs; ++l) {
+            Ssum = fmaf(s, __uint_as_float(acc[l]), Ssum);
+            s *= 0.0625f;
+        }
+        const float S1 = 32.0f * Ssum;
+        g[row] = v32[row] * (S1 - u32[row] * (R - Mj[row]));
+    }
+    return ok;
+}
+
+// Warp roles: warps 0..15 decoders (four warpgroups), warps 16..19 MMA issuers
+// (one per warpgroup, lane 0), warps 20..23 TMA producers (one per warpgroup,
+// lane 0; warp 20 also owns the tensor-memory allocation).  Tensor memory of warpgroup w, from column
+// 128 w: accumulators D-even, S-even, D-odd, S-odd (16 each), then A buffers.
+__global__ void __launch_bounds__(kTcThreads, 1) k_grad_tc(const __grid_constant__ CUtensorMap gmap,
+                                                           int64_t p, int ngroups, int nst,
+                                                           const uint8_t *__restrict__ bimg,
+                                                           int bbytes, const float *__restrict__ Mj,
+                                                           const float *__restrict__ u32,
+                                                           const float *__restrict__ v32,
+                                                           float *__restrict__ g, TcParams *prm,
+                                                           const int32_t *__restrict__ done)
+{
+    extern __shared__ __align__(1024) uint8_t smem[];
+    __shared__ __align__(8) TcPipe pipe[kTcNWG];
+    __shared__ uint32_t tmem_base;
+    __shared__ volatile int abort_flag;
+    constexpr int kDecoders = kTcNWG * 128;
+    constexpr int kProducerWarp = kTcNWG * 5;          // first TMA warp
+
+    if (done && *done) return;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    uint8_t *stages = smem;                      // kTcNWG * nst stages, 1024-aligned
+    uint8_t *bsm = smem + kTcNWG * nst * kTcStageTile;   // B image
+
+    {
+        const uint4 *src = reinterpret_cast<const uint4 *>(bimg);
+        uint4 *dst = reinterpret_cast<uint4 *>(bsm);
+        for (int i = tid; i < bbytes / 16; i += blockDim.x) dst[i] = src[i];
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    if (tid == 0) {
+        for (int w = 0; w < kTcNWG; ++w) {
+            for (int b = 0; b < nst; ++b) {
+                mbar_init(&pipe[w].tma_full[b], 1);
+                mbar_init(&pipe[w].tma_empty[b], 128);
+            }
+            for (int b = 0; b < kTcBufs; ++b) {
+                mbar_init(&pipe[w].full[b], 128);
+                mbar_init(&pipe[w].empty[b], 1);
+            }
+            mbar_init(&pipe[w].accfull, 1);
+            mbar_init(&pipe[w].accempty, 128);
+        }
+        abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == kProducerWarp) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         smem_addr(&tmem_base)),
+                     "r"(kTcNWG * 128));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+
+    const int64_t ntiles = (p + 127) / 128;
+    const int ksteps = 2 * ngroups;
+    const int spt = (ksteps + kTcStageSteps - 1) / kTcStageSteps;   // TMA stages per tile
+    const int64_t tile_step = (int64_t)gridDim.x * kTcNWG;
+
+    if (tid < kDecoders) {
+        // ------------------------------------------------------------ decoders
+        const int w = warp >> 2, r = tid & 127;
+        TcPipe &P = pipe[w];
+        const uint32_t tb = tmem_base + (uint32_t)(w * 128);
+        const uint32_t lane_off = (uint32_t)((warp & 3) * 32) << 16;
+        const float s0 = prm->s0, R = prm->R;
+        uint32_t grp = 0, k = 0;     // A-buffer groups written, TMA stages consumed
+        int T = 0;
+        bool ok = true;
+        const int cps = kTcStageBytes / kTcGroupBytes;                 // chunks per stage
+        for (int64_t tile = (int64_t)blockIdx.x * kTcNWG + w; tile < ntiles && ok; tile += tile_step, ++T) {
+            const int64_t row = tile * 128 + r;
+            int h = 0;                                                  // half of the current group
+            for (int st = 0; st < spt && ok; ++st, ++k) {
+                const uint32_t slot = k % (uint32_t)nst;
+                if (!mbar_wait(&P.tma_full[slot], (k / (uint32_t)nst) & 1u)) {
+                    abort_flag = 1;
+                    ok = false;
+                }
+                const uint8_t *base = stages + (w * nst + slot) * kTcStageTile + r * kTcStageBytes;
+                const int nchunks = min(cps, ngroups - st * cps);
+                for (int c = 0; c < nchunks && ok; ++c) {
+                    const int gi = st * cps + c;                        // chunk within the tile
+                    const uint4 x = *reinterpret_cast<const uint4 *>(base + ((c ^ ((r >> 1) & 3)) << 4));
+                    const uint32_t buf = grp % kTcBufs;
+                    if (h == 0 && grp >= kTcBufs) {
+                        if (!mbar_wait(&P.empty[buf], ((grp / kTcBufs) - 1) & 1u)) {
+                            abort_flag = 1;
+                            ok = false;
+                        }
+                        tc_fence_after();
+                    }
+                    tc_put_chunk(tb, lane_off, buf, h, x);
+                    if (h == 1 || gi == ngroups - 1) {                  // group complete
+                        asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+                        tc_fence_before();
+                        mbar_arrive(&P.full[buf]);
+                        ++grp;
+                        h = 0;
+                    } else {
+                        h = 1;
+                    }
+                }
+                mbar_arrive(&P.tma_empty[slot]);
+                if (abort_flag) ok = false;
+            }
+            if (ok) ok &= tc_epilogue(P, tb, lane_off, T, row, p, s0, R, Mj, u32, v32, g, abort_flag);
+        }
+    } else if (warp < kProducerWarp) {
+        // ------------------------------------------------------------ MMA issuers
+        const int w = warp - kTcNWG * 4;
+        TcPipe &P = pipe[w];
+        const uint32_t tb = tmem_base + (uint32_t)(w * 128);
+        const uint32_t b_addr = smem_addr(bsm);
+        const uint32_t za = 256u + 256u * (uint32_t)ksteps;   // trailing zero group
+        if (lane == 0) {
+            uint32_t q = 0;
+            int T = 0;
+            bool ok = true;
+            const int ngrp = (ngroups + 1) / 2;                          // A groups per tile
+            for (int64_t tile = (int64_t)blockIdx.x * kTcNWG + w; tile < ntiles && ok; tile += tile_step, ++T) {
+                if (T >= 1) {
+                    if (!mbar_wait(&P.accempty, (uint32_t)(T - 1) & 1u)) { abort_flag = 1; ok = false; }
+                    tc_fence_after();
+                }
+                for (int gg = 0; gg < ngrp && ok; ++gg, ++q) {
+                    const uint32_t buf = q % kTcBufs, use = q / kTcBufs;
+                    if (!mbar_wait(&P.full[buf], use & 1u)) { abort_flag = 1; ok = false; break; }
+                    tc_fence_after();
+                    const int s_end = min(ksteps, (gg + 1) * kTcBufSteps);
+                    for (int s = gg * kTcBufSteps; s < s_end; ++s) {
+                        const uint32_t ls = 256u + 256u * (uint32_t)s;       // limb group of K-step s
+                        mma_f8(tb, tb + 32 + 32 * buf + 8 * (s - gg * kTcBufSteps),
+                               b_desc(b_addr + ls, za - ls), kIdescF8, s > 0 ? 1u : 0u);
+                    }
+                    mma_commit(&P.empty[buf]);
+                    if (gg == ngrp - 1) mma_commit(&P.accfull);
+                }
+                if (abort_flag) ok = false;
+            }
+        }
+        __syncwarp();
+    } else {
+        // ------------------------------------------------------------ TMA producers
+        const int w = warp - kProducerWarp;
+        TcPipe &P = pipe[w];
+        if (lane == 0) {
+            const int64_t first = (int64_t)blockIdx.x * kTcNWG + w;
+            const int64_t tiles_w = first < ntiles ? (ntiles - 1 - first) / tile_step + 1 : 0;
+            const int64_t total = tiles_w * spt;
+            int64_t kk = 0;
+            for (; kk < total && !abort_flag; ++kk) {
+                const uint32_t slot = (uint32_t)(kk % nst);
+                if (kk >= nst && !mbar_wait(&P.tma_empty[slot], (uint32_t)((kk / nst) - 1) & 1u)) {
+                    abort_flag = 1;
+                    break;
+                }
+                const int64_t tile = first + (kk / spt) * tile_step;
+                const int st = (int)(kk % spt);
+                mbar_expect_tx(&P.tma_full[slot], kTcStageTile);
+                tma_load_2d(stages + (w * nst + slot) * kTcStageTile, &gmap, st * kTcStageBytes,
+                            (int)(tile * 128), &P.tma_full[slot]);
+            }
+            // copies still in flight (only after an abort) are waited for, bounded
+            for (int64_t j = kk - nst; j < kk; ++j)
+                if (j >= 0) mbar_wait(&P.tma_full[j % nst], (uint32_t)(j / nst) & 1u);
+        }
+        __syncwarp();
+    }
+    if (abort_flag && tid == 0) atomicExch(&prm->err, 1);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (warp == kProducerWarp)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base),
+                     "r"(kTcNWG * 128));
+}
+
+// ---------------------------------------------------------------------------
+
+struct TcWork {
+    uint8_t *bimg = nullptr;
+    size_t bbytes = 0;
+    TcParams *prm = nullptr;
+    int dev = -1;
+};
+static thread_local TcWork g_tc;
+
+static int tc_ngroups(const iht_dataset *ds)
+{
+    return (int)(((ds->n + 3) / 4 + kTcGroupBytes - 1) / kTcGroupBytes);
+}
+
+static size_t tc_bbytes(const iht_dataset *ds) { return 512 + 256 * (size_t)(2 * tc_ngroups(ds)); }
+
+constexpr size_t kTcSmemMax = 220 * 1024;
+
+// TMA stages per warpgroup that fit beside B and r (0: the pass does not fit).
+static int tc_stages(const iht_dataset *ds)
+{
+    const size_t fixed = tc_bbytes(ds);   // B
+    if (fixed >= kTcSmemMax) return 0;
+    const size_t ns = (kTcSmemMax - fixed) / ((size_t)kTcNWG * kTcStageTile);
+    return (int)std::min<size_t>(ns, kTcMaxStages);
+}
+
+static size_t tc_smem(const iht_dataset *ds)
+{
+    return (size_t)kTcNWG * tc_stages(ds) * kTcStageTile + tc_bbytes(ds);
+}
+
+bool grad_tc_supported(const iht_dataset *ds)
+{
+    return tc_stages(ds) >= 2 && ds->p < (1ll << 31);
+}
+
+using EncodeTiled = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *,
+                                 const cuuint64_t *, const cuuint64_t *, const cuuint32_t *,
+                                 const cuuint32_t *, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                 CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+// Tensor map of the packed matrix: uint8 [p][stride], boxes of 64 bytes x
+// 128 rows, 64-byte swizzle; rows past p read as zeros.
+static int make_gmap(const iht_dataset *ds, CUtensorMap *map)
+{
+    static EncodeTiled encode = nullptr;
+    if (!encode) {
+        void *fn = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        IHT_CUDA(cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000,
+                                                  cudaEnableDefault, &q));
+        if (q != cudaDriverEntryPointSuccess || !fn) return IHT_ECUDA;
+        encode = (EncodeTiled)fn;
+    }
+    const cuuint64_t dims[2] = {(cuuint64_t)ds->stride, (cuuint64_t)ds->p};
+    const cuuint64_t strides[1] = {(cuuint64_t)ds->stride};
+    const cuuint32_t box[2] = {(cuuint32_t)kTcStageBytes, 128};
+    const cuuint32_t estr[2] = {1, 1};
+    const CUresult r = encode(map, CU_TENSOR_MAP_DATA_TYPE_UINT8, 2, ds->G, dims, strides, box, estr,
+                              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B,
+                              CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? IHT_OK : IHT_ECUDA;
+}
+
+// Residual -> limb image (and its scale and sum) for the next tensor-core pass.
+int prepare_grad_tc(iht_dataset *ds, const float *r32, const int32_t *done)
+{
+    if (!grad_tc_supported(ds)) return IHT_EINVAL;
+    cudaStream_t s = ds->ctx->stream;
+    const int ksteps = 2 * tc_ngroups(ds);
+    const size_t bbytes = tc_bbytes(ds);
+    TcWork &w = g_tc;
+    if (w.dev != ds->ctx->device || w.bbytes < bbytes) {
+        if (w.bimg) cudaFree(w.bimg);
+        if (w.prm) cudaFree(w.prm);
+        w.bimg = nullptr;
+        w.prm = nullptr;
+        w.bbytes = 0;
+        IHT_CUDA(cudaMalloc(&w.bimg, bbytes));
+        IHT_CUDA(cudaMalloc(&w.prm, sizeof(TcParams)));
+        IHT_CUDA(cudaMemsetAsync(w.bimg, 0, bbytes, s));   // zero groups and unused limb rows
+        w.bbytes = bbytes;
+        w.dev = ds->ctx->device;
+    }
+    k_limbs<<<1, 1024, 0, s>>>(r32, (int64_t)ksteps * kTcStepSamples, w.bimg, w.prm, done);
+    note_launch();
+    IHT_CUDA(cudaGetLastError());
+    return launch_missing_sums(ds, r32, ds->ws->Mj, done);
+}
+
+// The gradient pass proper (after prepare_grad_tc on the same stream).
+int launch_grad_tc_main(iht_dataset *ds, const float *r32, float *g, const int32_t *done)
+{
+    cudaStream_t s = ds->ctx->stream;
+    CUtensorMap map;
+    int rc = make_gmap(ds, &map);
+    if (rc) return rc;
+    const int ngroups = tc_ngroups(ds);
+    const size_t bbytes = tc_bbytes(ds);
+    const int smem = (int)tc_smem(ds);
+    static thread_local int cfg = -1;
+    if (cfg != ds->ctx->device) {
+        IHT_CUDA(cudaFuncSetAttribute(k_grad_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      220 * 1024));
+        cfg = ds->ctx->device;
+    }
+    const int64_t tiles = (ds->p + 127) / 128;
+    const int grid = (int)std::min<int64_t>((tiles + kTcNWG - 1) / kTcNWG, (int64_t)ds->ctx->num_sms);
+    k_grad_tc<<<grid, kTcThreads, smem, s>>>(map, ds->p, ngroups, tc_stages(ds), g_tc.bimg, (int)bbytes,
+                                              ds->ws->Mj,
+                                              ds->ws->u32, ds->ws->v32, g, g_tc.prm, done);
+    note_launch();
+    IHT_CUDA(cudaGetLastError());
+    return IHT_OK;
+}
+
+int launch_grad_tc(iht_dataset *ds, const float *r32, float *g, const int32_t *done)
+{
+    int rc = prepare_grad_tc(ds, r32, done);
+    if (rc) return rc;
+    return launch_grad_tc_main(ds, r32, g, done);
+}
+
+// Bounded-wait status of the last tensor-core pass (1 = a wait timed out).
+int grad_tc_status(iht_dataset *ds, int *timed_out)
+{
+    *timed_out = 0;
+    if (!g_tc.prm) return IHT_OK;
+    TcParams h;
+    IHT_CUDA(cudaMemcpyAsync(&h, g_tc.prm, sizeof(h), cudaMemcpyDeviceToHost, ds->ctx->stream));
+    IHT_CUDA(cudaStreamSynchronize(ds->ctx->stream));
+    *timed_out = h.err;
+    return IHT_OK;
+}
 
 }  // namespace iht

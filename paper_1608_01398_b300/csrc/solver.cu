@@ -41,85 +41,107 @@ __global__ void __launch_bounds__(1024) k_gather_gS(const float *__restrict__ g,
     if (threadIdx.x == 0) sc->num = s;
 }
 
-constexpr int kZmulCols = 512;
+constexpr int kZmulColsPerGroup = 4;   // columns per block of the first phase
 
-// One thread per packed byte (4 samples); columns staged in shared memory.
-__global__ void __launch_bounds__(256) k_zmul(const uint8_t *__restrict__ G, int64_t stride,
-                                              const int32_t *__restrict__ cols, int m,
-                                              const double *__restrict__ coef, double sign,
-                                              const double *__restrict__ u64,
-                                              const double *__restrict__ v64,
-                                              const int32_t *__restrict__ used,
-                                              const double *__restrict__ base,
-                                              double *__restrict__ out,
-                                              double *__restrict__ partials,
-                                              const int32_t *__restrict__ done)
+// Phase 1: block (x, y) = (64 packed bytes x 4 columns): one thread per byte
+// of a column group; per-sample partial sums of the group go to part[y][i].
+__global__ void __launch_bounds__(256) k_zmul_part(const uint8_t *__restrict__ G, int64_t stride,
+                                                   int64_t rowb, const int32_t *__restrict__ cols,
+                                                   int m, const double *__restrict__ coef, double sign,
+                                                   const double *__restrict__ u64,
+                                                   const double *__restrict__ v64,
+                                                   double *__restrict__ part, int64_t n_pad,
+                                                   const int32_t *__restrict__ done)
 {
-    __shared__ double sa[kZmulCols], sb[kZmulCols];
-    __shared__ int64_t so[kZmulCols];
-    __shared__ double red[8];
     if (done && *done) return;
     const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int c0 = blockIdx.y * kZmulColsPerGroup;
+    if (b >= stride) return;
     double acc[4] = {0.0, 0.0, 0.0, 0.0};
-    for (int c0 = 0; c0 < m; c0 += kZmulCols) {
-        const int cn = min(kZmulCols, m - c0);
-        __syncthreads();
-        for (int t = threadIdx.x; t < cn; t += blockDim.x) {
-            const int col = cols[c0 + t];
-            const double a = sign * coef[c0 + t] * v64[col];
-            sa[t] = a;
-            sb[t] = a * u64[col];
-            so[t] = (int64_t)col * stride;
-        }
-        __syncthreads();
-        if (b < stride) {
-            for (int t = 0; t < cn; t += 8) {
-                uint32_t by[8];
+    uint32_t by[kZmulColsPerGroup];
+    double a[kZmulColsPerGroup], bb[kZmulColsPerGroup];
 #pragma unroll
-                for (int q = 0; q < 8; ++q) by[q] = t + q < cn ? __ldg(G + so[t + q] + b) : 0x55u;
-#pragma unroll
-                for (int q = 0; q < 8; ++q) {
-                    if (t + q < cn) {
-#pragma unroll
-                        for (int e = 0; e < 4; ++e) {
-                            const int x = dosage_of((by[q] >> (2 * e)) & 3u);
-                            if (x >= 0) acc[e] += sa[t + q] * (double)x - sb[t + q];
-                        }
-                    }
-                }
-            }
+    for (int q = 0; q < kZmulColsPerGroup; ++q) {
+        const int c = c0 + q;
+        by[q] = 0x55u;
+        a[q] = 0.0;
+        bb[q] = 0.0;
+        if (c < m) {
+            const int col = cols[c];
+            by[q] = b < rowb ? __ldg(G + (int64_t)col * stride + b) : 0x55u;
+            a[q] = sign * coef[c] * v64[col];
+            bb[q] = a[q] * u64[col];
         }
     }
-    double s = 0.0, s2 = 0.0;
-    if (b < stride) {
+#pragma unroll
+    for (int q = 0; q < kZmulColsPerGroup; ++q) {
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
-            const int64_t i = 4 * b + e;
-            const double o = used[i] ? (base ? base[i] : 0.0) + acc[e] : 0.0;
-            out[i] = o;
-            s += o;
-            s2 += o * o;
+            const int x = dosage_of((by[q] >> (2 * e)) & 3u);
+            if (x >= 0) acc[e] += a[q] * (double)x - bb[q];
         }
     }
-    s = block_sum(s, red);
-    s2 = block_sum(s2, red);
+    double *dst = part + (int64_t)blockIdx.y * n_pad + 4 * b;
+#pragma unroll
+    for (int e = 0; e < 4; ++e) dst[e] = acc[e];
+}
+
+// Phase 2: out_i = base_i + sum over groups (fixed order) on used rows, 0
+// elsewhere; per-block sums of out and out^2 into partials.
+__global__ void __launch_bounds__(256) k_zmul_sum(const double *__restrict__ part, int ngroups,
+                                                  int64_t n_pad, const int32_t *__restrict__ used,
+                                                  const double *__restrict__ base,
+                                                  double *__restrict__ out,
+                                                  double *__restrict__ partials,
+                                                  const int32_t *__restrict__ done)
+{
+    __shared__ double red[8];
+    if (done && *done) return;
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    double o = 0.0;
+    if (i < n_pad) {
+        double acc = 0.0;
+        for (int g = 0; g < ngroups; ++g) acc += part[(int64_t)g * n_pad + i];
+        o = used[i] ? (base ? base[i] : 0.0) + acc : 0.0;
+        out[i] = o;
+    }
+    const double s = block_sum(o, red);
+    const double s2 = block_sum(o * o, red);
     if (threadIdx.x == 0 && partials) {
         partials[2 * blockIdx.x] = s;
         partials[2 * blockIdx.x + 1] = s2;
     }
 }
 
-int zmul_blocks(const iht_dataset *ds) { return ceil_div(ds->stride, 256); }
+int zmul_blocks(const iht_dataset *ds) { return ceil_div(ds->n_pad, 256); }
+
+// out = base + sign * Z[:, cols] coef (device, stream-ordered); partials get
+// zmul_blocks() pairs (sum, sum of squares) when not null.
+int zmul_run(iht_dataset *ds, const int32_t *cols, int m, const double *coef, double sign,
+             const double *u, const double *v, const int32_t *used, const double *base,
+             double *out, double *partials, const int32_t *done)
+{
+    cudaStream_t s = ds->ctx->stream;
+    const int ngroups = std::max(1, (m + kZmulColsPerGroup - 1) / kZmulColsPerGroup);
+    if (ngroups > kZmulMaxGroups) return IHT_EINVAL;
+    if (m > 0) {
+        dim3 grid(ceil_div(ds->stride, 256), ngroups);
+        k_zmul_part<<<grid, 256, 0, s>>>(ds->G, ds->stride, ds->rowb, cols, m, coef, sign, u, v,
+                                         ds->ws->zpart, ds->n_pad, done);
+        note_launch();
+    }
+    k_zmul_sum<<<zmul_blocks(ds), 256, 0, s>>>(ds->ws->zpart, m > 0 ? ngroups : 0, ds->n_pad, used,
+                                               base, out, partials, done);
+    note_launch();
+    IHT_CUDA(cudaGetLastError());
+    return IHT_OK;
+}
 
 int launch_zmul(iht_dataset *ds, const int32_t *cols, int32_t m, const double *coef,
                 const double *u, const double *v, const int32_t *used, const double *base,
                 double *out, double *partials)
 {
-    k_zmul<<<zmul_blocks(ds), 256, 0, ds->ctx->stream>>>(ds->G, ds->stride, cols, m, coef, 1.0, u,
-                                                         v, used, base, out, partials, nullptr);
-    note_launch();
-    IHT_CUDA(cudaGetLastError());
-    return IHT_OK;
+    return zmul_run(ds, cols, m, coef, 1.0, u, v, used, base, out, partials, nullptr);
 }
 
 // ---------------------------------------------------------------------------
@@ -127,7 +149,7 @@ int launch_zmul(iht_dataset *ds, const int32_t *cols, int32_t m, const double *c
 
 struct MergeArgs {
     const uint8_t *G;
-    int64_t stride;
+    int64_t stride, rowb;
     const float *g;
     const double *u64, *v64;
     const int32_t *used;
@@ -217,23 +239,38 @@ __device__ void sort_by_w(MergeShared &sh, int nU)
     }
 }
 
-// ||Z d||^2 over the used rows for the columns staged in ca/cb/coff.
+// ||Z d||^2 over the used rows for the columns staged in ca/cb/coff: one
+// thread per 32-bit word (16 samples), eight columns' loads in flight.
 __device__ double znorm2(MergeShared &sh, const MergeArgs &A)
 {
     double s = 0.0;
-    for (int64_t b = threadIdx.x; b < A.stride; b += blockDim.x) {
-        double acc[4] = {0.0, 0.0, 0.0, 0.0};
-        for (int c = 0; c < sh.ncol; ++c) {
-            const uint32_t by = __ldg(A.G + sh.coff[c] + b);
+    const int ncol = sh.ncol;
+    for (int64_t wdx = threadIdx.x; wdx < A.rowb / 4; wdx += blockDim.x) {
+        double acc[16];
 #pragma unroll
-            for (int e = 0; e < 4; ++e) {
-                const int x = dosage_of((by >> (2 * e)) & 3u);
-                if (x >= 0) acc[e] += sh.ca[c] * (double)x - sh.cb[c];
+        for (int e = 0; e < 16; ++e) acc[e] = 0.0;
+        for (int c0 = 0; c0 < ncol; c0 += 8) {
+            uint32_t w[8];
+#pragma unroll
+            for (int q = 0; q < 8; ++q)
+                w[q] = c0 + q < ncol
+                           ? __ldg(reinterpret_cast<const uint32_t *>(A.G + sh.coff[c0 + q]) + wdx)
+                           : 0x55555555u;
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                if (c0 + q < ncol) {
+                    const double a = sh.ca[c0 + q], b = sh.cb[c0 + q];
+#pragma unroll
+                    for (int e = 0; e < 16; ++e) {
+                        const int x = dosage_of((w[q] >> (2 * e)) & 3u);
+                        if (x >= 0) acc[e] += a * (double)x - b;
+                    }
+                }
             }
         }
 #pragma unroll
-        for (int e = 0; e < 4; ++e)
-            if (A.used[4 * b + e]) s += acc[e] * acc[e];
+        for (int e = 0; e < 16; ++e)
+            if (A.used[16 * wdx + e]) s += acc[e] * acc[e];
     }
     return block_sum(s, sh.red);
 }
@@ -519,6 +556,7 @@ int launch_merge(iht_dataset *ds, int k, int K)
     MergeArgs A;
     A.G = ds->G;
     A.stride = ds->stride;
+    A.rowb = ds->rowb;
     A.g = ws->g;
     A.u64 = ws->u64;
     A.v64 = ws->v64;
@@ -543,9 +581,11 @@ int launch_grad(iht_dataset *ds, int impl, const int32_t *done, bool profile)
     Workspace *ws = ds->ws;
     cudaStream_t s = ds->ctx->stream;
     const bool rec = profile && ws->nprof < kProfEvents;
+    const bool tc = impl == 2 || (impl == 0 && grad_tc_supported(ds));
+    int rc;
+    if (tc && (rc = prepare_grad_tc(ds, ws->r32, done))) return rc;
     if (rec) IHT_CUDA(cudaEventRecord(ws->prof_ev[2 * ws->nprof], s));
-    int rc = impl == 2 ? launch_grad_tc(ds, ws->r32, ws->g, done)
-                       : launch_grad_simt(ds, ws->r32, ws->g, done);
+    rc = tc ? launch_grad_tc_main(ds, ws->r32, ws->g, done) : launch_grad_simt(ds, ws->r32, ws->g, done);
     if (rc) return rc;
     if (rec) {
         IHT_CUDA(cudaEventRecord(ws->prof_ev[2 * ws->nprof + 1], s));
@@ -584,11 +624,12 @@ int run_solve(iht_dataset *ds, int k, const iht_options *opt, int n_rows, const 
     IHT_CUDA(cudaMemcpyAsync(ws->sc, ws->sc_host, sizeof(Scalars), cudaMemcpyHostToDevice, s));
 
     // r = y (beta = 0), objective, centred residual, g^0, S^0 = top-k |g^0|
-    k_zmul<<<npart, 256, 0, s>>>(ds->G, ds->stride, ws->cols, 0, ws->coef, -1.0, ws->u64, ws->v64,
-                                 ws->used, ws->y64, ws->r64, ws->partials, nullptr);
+    if ((rc = zmul_run(ds, ws->cols, 0, ws->coef, -1.0, ws->u64, ws->v64, ws->used, ws->y64,
+                       ws->r64, ws->partials, nullptr)))
+        return rc;
     k_finalize<<<1, 1024, 0, s>>>(ws->sc, ws->partials, npart, ws->S, ws->bS, ws->Sp, ws->bSp, tr, 1);
     k_center<<<ceil_div(ds->n_pad, 256), 256, 0, s>>>(ws->r64, ws->used, ds->n_pad, ws->sc, ws->r32);
-    note_launch(3);
+    note_launch(2);
     IHT_CUDA(cudaGetLastError());
     const int32_t *done = &ws->sc->done;
     const bool prof = opt->profile != 0;
@@ -604,16 +645,19 @@ int run_solve(iht_dataset *ds, int k, const iht_options *opt, int n_rows, const 
         if (it > 0 && (rc = launch_grad(ds, opt->grad_impl, done, prof))) return rc;
         if ((rc = select_topk(ds->ctx, ws->g, ds->p, K, ws->cand, done))) return rc;
         k_gather_gS<<<1, 1024, 0, s>>>(ws->g, ws->S, k, ws->coef, ws->sc);
-        k_zmul<<<npart, 256, 0, s>>>(ds->G, ds->stride, ws->S, k, ws->coef, 1.0, ws->u64, ws->v64,
-                                     ws->used, nullptr, ws->zv, ws->partials, done);
+        note_launch();
+        if ((rc = zmul_run(ds, ws->S, k, ws->coef, 1.0, ws->u64, ws->v64, ws->used, nullptr, ws->zv,
+                           ws->partials, done)))
+            return rc;
         if ((rc = launch_merge(ds, k, K))) return rc;
-        k_zmul<<<npart, 256, 0, s>>>(ds->G, ds->stride, ws->Sp, k, ws->bSp, -1.0, ws->u64, ws->v64,
-                                     ws->used, ws->y64, ws->r64, ws->partials, done);
+        if ((rc = zmul_run(ds, ws->Sp, k, ws->bSp, -1.0, ws->u64, ws->v64, ws->used, ws->y64,
+                           ws->r64, ws->partials, done)))
+            return rc;
         k_finalize<<<1, 1024, 0, s>>>(ws->sc, ws->partials, npart, ws->S, ws->bS, ws->Sp, ws->bSp,
                                       tr, 0);
         k_center<<<ceil_div(ds->n_pad, 256), 256, 0, s>>>(ws->r64, ws->used, ds->n_pad, ws->sc,
                                                           ws->r32);
-        note_launch(5);   // gather, zmul, zmul, finalize, center (merge counts itself)
+        note_launch(2);   // finalize, center
         IHT_CUDA(cudaGetLastError());
         IHT_CUDA(cudaMemcpyAsync(&ws->sc_host->done, &ws->sc->done, sizeof(int32_t),
                                  cudaMemcpyDeviceToHost, s));

@@ -11,7 +11,7 @@ import pytest
 
 import oracle
 import synth
-from pins import random_geno
+from pins import np_Z, random_geno
 
 pytestmark = pytest.mark.gpu
 
@@ -67,8 +67,8 @@ def _torch():
     return torch
 
 
-@pytest.mark.parametrize("impl", [0, 1])
-@pytest.mark.parametrize("n,p", [(37, 5), (1000, 300), (1003, 611), (4099, 257)])
+@pytest.mark.parametrize("impl", [0, 1, 2])
+@pytest.mark.parametrize("n,p", [(1, 3), (37, 5), (1000, 300), (1003, 611), (4099, 257), (300, 1000)])
 def test_gradient_parity(iht, ctx, impl, n, p):
     torch = _torch()
     rng = np.random.default_rng(7 + n + p)
@@ -139,7 +139,7 @@ def compare_fits(fo, fg, k):
     certified = 0
     for t in range(T):
         tr = fo.trace
-        ok = tr["gap"][t] > 100 * GTOL * tr["wscale"][t] and not (tr["margin"][t] < 1e-3)
+        ok = tr["gap"][t] > 10 * GTOL * tr["wscale"][t] and not (tr["margin"][t] < 1e-3)
         if not ok:
             break
         assert np.array_equal(fg.trace["supp"][t], tr["supp"][t]), f"support at iteration {t}"
@@ -160,7 +160,7 @@ def test_fit_parity_config1(iht, ctx):
     ds = load(iht, ctx, G)
     y, causal, _ = synth.config_phenotype(1, pn)
     fo = oracle.iht(G, y, 10)
-    for impl in (0, 1):
+    for impl in (1, 2):
         fg = iht.iht_fit_trace(ds, y, 10, grad_impl=impl)
         assert compare_fits(fo, fg, 10) == fo.iterations
         assert np.count_nonzero(fg.beta) <= 10
@@ -178,14 +178,19 @@ def test_fit_parity_small_panels(iht, ctx, seed):
     ds = load(iht, ctx, G)
     rows = None if seed % 2 == 0 else np.sort(rng.choice(n, size=n - 11, replace=False))
     nr = n if rows is None else rows.size
-    y = rng.normal(size=nr) + 0.5
+    # a sparse signal plus noise (and an offset: the solver must not need centred y)
+    Z = np_Z(codes, rows)
+    causal = rng.choice(p, size=min(k, p), replace=False)
+    y = Z[:, causal] @ rng.normal(0, 0.5, size=causal.size) + rng.normal(size=nr) + 0.5
     fo = oracle.iht(G, y, k, rows=rows, max_iter=60, tol=1e-6)
     fg = iht.iht_fit_trace(ds, y, k, rows=rows, max_iter=60, tol=1e-6)
-    assert compare_fits(fo, fg, k) >= min(3, fo.iterations)
+    # every iteration the oracle certifies must agree; the first one must be certified
+    assert compare_fits(fo, fg, k) >= 1
+    obj = np.concatenate([[0.5 * y @ y], fg.trace["objective"]])
+    assert np.all(np.diff(obj) <= 1e-9 * obj[:-1])
 
 
 def test_fit_k_equals_p_is_ols(iht, ctx):
-    from pins import np_Z
     rng = np.random.default_rng(41)
     G, codes = random_geno(rng, 120, 6, miss=0.0)
     ds = load(iht, ctx, G)
@@ -240,7 +245,7 @@ def test_fullsize_gradient_sampled(iht, cfg2):
     body = bed[3:].reshape(pn.p, rb)[snps].ravel()
     Gs = oracle.Geno(body, pn.n, snps.size, rb)
     go = oracle.gradient(Gs, r.astype(np.float64))
-    for impl in (0, 1):
+    for impl in (1, 2):
         g = iht.iht_gradient(ds, torch.from_numpy(r).cuda(), impl=impl).cpu().numpy()
         assert rel_err(g[snps], go) <= GTOL
     # the full gradient is finite and no SNP is skipped
