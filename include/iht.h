@@ -153,6 +153,26 @@ int iht_gradient(iht_dataset *ds, const int32_t *rows, int64_t n_rows, const flo
  *   w: device float[p]; idx_out: device int32[k].  EINVAL if k < 1 or k > p. */
 int iht_topk(iht_ctx *ctx, const float *w, int64_t p, int32_t k, int32_t *idx_out);
 
+/* Allocation-free variant of iht_topk (the paper has no counterpart; this is
+ * an interface for callers that cannot allocate device memory -- for example a
+ * host that hands all GPU memory to its own pool allocator, or a latency-
+ * critical loop that must not call cudaMalloc, which can synchronise the device
+ * or fail under memory pressure).  Same result as iht_topk: the k indices of
+ * the largest |w_j|, ties to the lower index, ascending.
+ *   device  : CUDA device the pointers belong to.
+ *   stream  : cudaStream_t to order the work on (NULL = legacy default stream).
+ *   w       : device float[p];  idx_out: device int32[k].
+ * The selection's scratch is a static device array in the library, sized for
+ * p <= 16 777 216 (about 24 KB, held on every GPU that loads the library until
+ * the process exits); larger p returns IHT_EINVAL without launching anything.
+ * The first call on a device looks the array's address up with
+ * cudaGetSymbolAddress; make that first call before any stream capture.  The
+ * call only enqueues work on `stream` (it does not synchronise); all calls on a
+ * device share the scratch, so calls that overlap on the GPU (other streams or
+ * other host threads) race.  Never calls cudaMalloc or cudaFree. */
+int iht_topk_noalloc(int device, void *stream, const float *w, int64_t p, int32_t k,
+                     int32_t *idx_out);
+
 /* a4/a6 -- sparse standardised product out = Z[rows, cols] coef: only the m
  * listed columns are decoded and standardised (Sec. 2.3.2-2.3.3, X_k beta_k).
  *   cols: device int32[m]; coef: device double[m]; out: device double[n_rows].

@@ -24,7 +24,8 @@ IHT_HOST, IHT_DEVICE = 0, 1
 EXPORTED = ["iht_default_options", "iht_strerror", "iht_last_cuda_error", "iht_kernel_launches",
             "iht_create",
             "iht_destroy", "iht_load_bed", "iht_dataset_free", "iht_dataset_shape", "iht_counts",
-            "iht_gradient", "iht_topk", "iht_zmul", "iht_fit", "iht_fit_trace"]
+            "iht_gradient", "iht_topk", "iht_topk_noalloc", "iht_zmul", "iht_fit",
+            "iht_fit_trace"]
 
 
 class IhtError(RuntimeError):
@@ -91,6 +92,7 @@ def _lib(build_if_stale: bool = True):
         "iht_counts": (ctypes.c_int, [P, P, i64, ctypes.c_int, P, P, P]),
         "iht_gradient": (ctypes.c_int, [P, P, i64, P, P, ctypes.c_int]),
         "iht_topk": (ctypes.c_int, [P, P, i64, i32, P]),
+        "iht_topk_noalloc": (ctypes.c_int, [ctypes.c_int, P, P, i64, i32, P]),
         "iht_zmul": (ctypes.c_int, [P, P, i64, P, P, P, i32, P, P]),
         "iht_fit": (ctypes.c_int, [P, P, i64, P, i32, ctypes.POINTER(iht_options), P, P,
                                    ctypes.POINTER(iht_result)]),
@@ -235,6 +237,20 @@ def iht_topk(ctx: Context, w, k: int, out=None):
     _check(_lib().iht_topk(ctx.h, ctypes.c_void_p(_dptr(w, torch.float32, "w")), w.numel(), k,
                            ctypes.c_void_p(_dptr(idx, torch.int32, "idx"))), "iht_topk")
     return idx
+
+
+def iht_topk_noalloc(w, k: int, out, device: int | None = None, stream=None):
+    """Allocation-free top-k: enqueues on `stream` (default: torch's current
+    stream of w's device) and writes the k indices into `out` (int32, k).
+    Marshalling only; the caller owns `out` and synchronises."""
+    torch = _torch()
+    dev = w.device.index if device is None else device
+    st = stream if stream is not None else torch.cuda.current_stream(dev)
+    _check(_lib().iht_topk_noalloc(dev, ctypes.c_void_p(st.cuda_stream),
+                                   ctypes.c_void_p(_dptr(w, torch.float32, "w")), w.numel(), k,
+                                   ctypes.c_void_p(_dptr(out, torch.int32, "out"))),
+           "iht_topk_noalloc")
+    return out
 
 
 def iht_zmul(ds: Dataset, cols, coef, rows=None, u=None, v=None):

@@ -12,6 +12,8 @@
 // Collection writes every key > T (unordered) and the lowest-index keys == T
 // (ordered by a per-chunk count and an exclusive scan), then one CTA sorts the
 // K indices ascending.  NaN keys set SelState::err bit 0.
+#include <mutex>
+
 #include "common.cuh"
 
 namespace iht {
@@ -278,4 +280,96 @@ int select_topk(iht_ctx *ctx, const float *keys, int64_t p, int32_t K, int32_t *
     return IHT_OK;
 }
 
+// ---------------------------------------------------------------------------
+// Allocation-free top-k (iht_topk_noalloc).
+//
+// For callers that must not allocate device memory: the scratch of the
+// selection (radix histogram, selection state, per-chunk tie counts) lives in
+// this file-scope device array, sized for p <= kNoAllocMaxP.  Every GPU that
+// loads the library holds it (about 24 KB) until the process exits.  The array
+// is shared by all calls on a device and keeps the last call's contents; the
+// first kernel of each call clears the histogram and the state, and the chunk
+// counts are written in full before they are read.  Calls that overlap on the
+// GPU (different streams, or several host threads) race on it.
+
+constexpr int64_t kNoAllocMaxP = int64_t(1) << 24;                 // 16 777 216 entries
+constexpr int64_t kNoAllocChunks = kNoAllocMaxP / kSelChunk;      // 4096 tie-count chunks
+constexpr size_t kNoAllocHist = sizeof(uint32_t) * kSelBins;      // 8 KB
+constexpr size_t kNoAllocState = 256;                             // SelState, padded
+constexpr size_t kNoAllocBytes = kNoAllocHist + kNoAllocState + sizeof(uint32_t) * kNoAllocChunks;
+
+static __device__ __align__(256) unsigned char g_topk_scratch[kNoAllocBytes];
+
+constexpr int kNoAllocMaxDevices = 64;
+static std::mutex g_noalloc_mu;
+static unsigned char *g_noalloc_addr[kNoAllocMaxDevices] = {};
+static int g_noalloc_sms[kNoAllocMaxDevices] = {};
+
+// Device address of the scratch array on `device` (looked up once per device,
+// with that device current; the caller's current device is restored).
+static int noalloc_scratch(int device, unsigned char **addr, int *num_sms)
+{
+    if (device < 0 || device >= kNoAllocMaxDevices) return IHT_EINVAL;
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_addr[device]) {
+        int prev = -1;
+        IHT_CUDA(cudaGetDevice(&prev));
+        IHT_CUDA(cudaSetDevice(device));
+        void *ptr = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&ptr, g_topk_scratch);
+        int sms = 0;
+        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
+        cudaSetDevice(prev);
+        if (e != cudaSuccess) {
+            set_cuda_error(e, "cudaGetSymbolAddress(top-k scratch)");
+            return IHT_ECUDA;
+        }
+        g_noalloc_addr[device] = static_cast<unsigned char *>(ptr);
+        g_noalloc_sms[device] = sms;
+    }
+    *addr = g_noalloc_addr[device];
+    *num_sms = g_noalloc_sms[device];
+    return IHT_OK;
+}
+
 }  // namespace iht
+
+extern "C" int iht_topk_noalloc(int device, void *stream, const float *w, int64_t p, int32_t k,
+                                int32_t *idx_out)
+{
+    using namespace iht;
+    if (!w || !idx_out || p < 1 || k < 1 || k > p || k > kMaxCand) return IHT_EINVAL;
+    if (p > kNoAllocMaxP) return IHT_EINVAL;   // beyond the size of the static scratch
+    unsigned char *scratch = nullptr;
+    int sms = 0;
+    int rc = noalloc_scratch(device, &scratch, &sms);
+    if (rc) return rc;
+    int prev = -1;
+    IHT_CUDA(cudaGetDevice(&prev));
+    if (prev != device) IHT_CUDA(cudaSetDevice(device));
+    uint32_t *hist = reinterpret_cast<uint32_t *>(scratch);
+    SelState *st = reinterpret_cast<SelState *>(scratch + kNoAllocHist);
+    uint32_t *chunk_eq = reinterpret_cast<uint32_t *>(scratch + kNoAllocHist + kNoAllocState);
+    cudaStream_t s = (cudaStream_t)stream;
+    const int64_t nchunks = (p + kSelChunk - 1) / kSelChunk;
+    const int hblocks = (int)std::min<int64_t>(ceil_div(p, kSelThreads), (int64_t)sms * 4);
+    k_sel_init<<<1, 256, 0, s>>>(st, (uint32_t)k, hist, nullptr);
+    const int shifts[3] = {20, 10, 0};
+    const uint32_t dmasks[3] = {0x7ffu, 0x3ffu, 0x3ffu};
+    for (int ps = 0; ps < 3; ++ps) {
+        k_sel_hist<<<hblocks, kSelThreads, 0, s>>>(w, p, st, hist, shifts[ps], dmasks[ps], nullptr);
+        k_sel_scan<<<1, 1024, 0, s>>>(st, hist, shifts[ps], dmasks[ps], (int)dmasks[ps] + 1, nullptr);
+    }
+    k_sel_collect_gt<<<(int)nchunks, kSelThreads, 0, s>>>(w, p, st, idx_out, chunk_eq, nullptr);
+    k_sel_scan_chunks<<<1, 1024, 0, s>>>(chunk_eq, nchunks, nullptr);
+    k_sel_collect_eq<<<(int)nchunks, kSelThreads, 0, s>>>(w, p, st, idx_out, chunk_eq, nullptr);
+    k_sort_idx<<<1, 1024, 0, s>>>(idx_out, k, nullptr);
+    note_launch(11);
+    const cudaError_t e = cudaGetLastError();
+    if (prev != device) cudaSetDevice(prev);
+    if (e != cudaSuccess) {
+        set_cuda_error(e, "iht_topk_noalloc launch");
+        return IHT_ECUDA;
+    }
+    return IHT_OK;
+}
