@@ -42,7 +42,7 @@ void free_workspace(Workspace *ws)
 {
     if (!ws) return;
     void *ptrs[] = {ws->used, ws->rowmask, ws->counts, ws->u64, ws->v64, ws->u32, ws->v32,
-                    ws->y64, ws->r64, ws->zv, ws->r32, ws->g, ws->Mj, ws->partials, ws->zpart, ws->rows_dev,
+                    ws->y64, ws->r64, ws->zv, ws->rc64, ws->r32, ws->g, ws->Mj, ws->partials, ws->zpart, ws->rows_dev,
                     ws->ybuf, ws->fbuf, ws->cand, ws->S, ws->Sp, ws->bS, ws->bSp, ws->coef,
                     ws->cols, ws->sc};
     for (void *p : ptrs)
@@ -76,10 +76,11 @@ int ensure_workspace(iht_dataset *ds, int)
     ALLOC(y64, sizeof(double) * np);
     ALLOC(r64, sizeof(double) * np);
     ALLOC(zv, sizeof(double) * np);
+    ALLOC(rc64, sizeof(double) * np);
     ALLOC(r32, sizeof(float) * np);
     ALLOC(g, sizeof(float) * p);
     ALLOC(Mj, sizeof(float) * p);
-    ALLOC(partials, sizeof(double) * 2 * kPartials);
+    ALLOC(partials, sizeof(double) * 3 * kPartials);
     ALLOC(zpart, sizeof(double) * (size_t)kZmulMaxGroups * np);
     ALLOC(rows_dev, sizeof(int32_t) * np);
     ALLOC(ybuf, sizeof(double) * np);
@@ -141,18 +142,29 @@ static int stage_rows(iht_dataset *ds, const int32_t *rows, int64_t n_rows, int 
     return IHT_OK;
 }
 
-// Row set + statistics of a call; EINVAL for bad or duplicate rows.
+// Row set + statistics of a call; EINVAL for bad or duplicate rows.  The
+// all-rows statistics are cached: a call without a row list reuses them when
+// the workspace still holds them (u, v are computed once and kept, Sec. 2.3.2).
 static int prepare_rows(iht_dataset *ds, const int32_t *rows, int64_t n_rows, int mem,
                         const int32_t **rows_dev)
 {
     int rc;
     if ((rc = reset_err(ds))) return rc;
+    if (!rows && ds->ws->rowset_all) {
+        *rows_dev = nullptr;
+        return IHT_OK;
+    }
+    ds->ws->rowset_all = false;
     if ((rc = stage_rows(ds, rows, n_rows, mem, rows_dev))) return rc;
     if ((rc = setup_rows(ds, *rows_dev, n_rows))) return rc;
-    int32_t err = 0;
-    if ((rc = read_err(ds, &err))) return rc;
-    if (err & 2) return IHT_EINVAL;
-    return launch_counts(ds, n_rows);
+    if (rows) {
+        int32_t err = 0;
+        if ((rc = read_err(ds, &err))) return rc;
+        if (err & 2) return IHT_EINVAL;
+    }
+    if ((rc = launch_counts(ds, n_rows))) return rc;
+    ds->ws->rowset_all = rows == nullptr;
+    return IHT_OK;
 }
 
 }  // namespace iht

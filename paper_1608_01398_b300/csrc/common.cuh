@@ -26,7 +26,7 @@ namespace iht {
 constexpr int kMaxK = 1024;            // largest sparsity level accepted
 constexpr int kMaxCand = 2 * kMaxK;    // candidate list of the projection
 constexpr int kSelBins = 2048;         // radix-select histogram bins
-constexpr int kPartials = 1024;        // max per-block partial sums
+constexpr int kPartials = 1024;        // max blocks of per-block partial sums (3 values each)
 constexpr int kZmulMaxGroups = 2 * kMaxK / 4;   // column groups of the sparse product
 
 struct Scalars {                       // device-resident state of one solve
@@ -37,16 +37,18 @@ struct Scalars {                       // device-resident state of one solve
     double sumsq_r;                    // sum of r^2 over used rows
     double step;                       // ||beta+ - beta|| / (||beta|| + 1)
     double c, kappa, tol;              // options
+    double dd;                         // ||beta+ - beta||^2 of the candidate
+    double bb;                         // ||beta||^2
     int32_t iter;                      // updates performed
     int32_t status;                    // IHT_OK / ENOTCONV / ENUMERIC
     int32_t done;                      // 1 once the solve has stopped
+    int32_t retry;                     // 1: candidate rejected, mu shrunk (read with done)
     int32_t bt_total;                  // total shrinks
     int32_t bt_last;                   // shrinks of the last iteration
     int32_t changed;                   // support changed in the last iteration
     int32_t max_iter, max_backtrack;
     int32_t k, n_rows;
     int32_t err;                       // bit 0: non-finite input, bit 1: bad rows
-    int32_t pad_;
 };
 
 struct SelState {                      // radix select progress
@@ -94,12 +96,14 @@ namespace iht {
 struct Workspace {
     int64_t p = 0, n_pad = 0;
     int kcap = 0;
+    bool rowset_all = false;               // used/rowmask/statistics hold the all-rows set
     int32_t *used = nullptr;
     uint32_t *rowmask = nullptr;
     int32_t *counts = nullptr;
     double *u64 = nullptr, *v64 = nullptr;
     float *u32 = nullptr, *v32 = nullptr;
     double *y64 = nullptr, *r64 = nullptr, *zv = nullptr;
+    double *rc64 = nullptr;                // residual of the candidate update
     float *r32 = nullptr, *g = nullptr;
     float *Mj = nullptr;                   // per-SNP sum of r over missing calls
     double *partials = nullptr;        // kPartials * 2
@@ -162,6 +166,7 @@ int ensure_selwork(iht_ctx *ctx, int64_t p);
 int select_topk(iht_ctx *ctx, const float *key_src, int64_t p, int32_t K, int32_t *out_idx,
                 const int32_t *done);
 // solver.cu
+int zmul_blocks(const iht_dataset *ds);
 int launch_zmul(iht_dataset *ds, const int32_t *cols, int32_t m, const double *coef,
                 const double *u, const double *v, const int32_t *used, const double *base,
                 double *out, double *partials);

@@ -318,7 +318,8 @@ int build_missing_lists(iht_dataset *ds)
     return IHT_OK;
 }
 
-// M_j = sum of r over the missing calls of SNP j (one warp per SNP, list order).
+// M_j = sum of r over the missing calls of SNP j.  Four lanes per SNP (eight
+// SNPs per warp, 16 list entries in flight per group), fixed summation order.
 template <typename IdxT>
 __global__ void __launch_bounds__(256) k_missing_sum(const int64_t *__restrict__ off,
                                                      const IdxT *__restrict__ idx, int64_t p,
@@ -327,21 +328,32 @@ __global__ void __launch_bounds__(256) k_missing_sum(const int64_t *__restrict__
                                                      const int32_t *__restrict__ done)
 {
     if (done && *done) return;
-    const int lane = threadIdx.x & 31;
-    const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
-    for (int64_t j = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); j < p; j += nwarps) {
-        const int64_t e0 = off[j], e1 = off[j + 1];
+    const int lane = threadIdx.x & 31, q = lane & 3;
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t base = warp * 8; base < p; base += nwarps * 8) {      // warp-uniform
+        const int64_t j = base + (lane >> 2);
+        const bool live = j < p;
+        const int64_t e0 = live ? off[j] : 0, e1 = live ? off[j + 1] : 0;
         float m = 0.0f;
-        for (int64_t e = e0 + lane; e < e1; e += 32) m += __ldg(r32 + idx[e]);
-        m = warp_sum(m);
-        if (lane == 0) M[j] = m;
+        for (int64_t e = e0 + q; e < e1; e += 16) {
+            IdxT i[4];
+#pragma unroll
+            for (int t = 0; t < 4; ++t) i[t] = e + 4 * t < e1 ? idx[e + 4 * t] : (IdxT)0;
+#pragma unroll
+            for (int t = 0; t < 4; ++t)
+                if (e + 4 * t < e1) m += __ldg(r32 + i[t]);
+        }
+        m += __shfl_xor_sync(0xffffffffu, m, 1);
+        m += __shfl_xor_sync(0xffffffffu, m, 2);
+        if (live && q == 0) M[j] = m;
     }
 }
 
 int launch_missing_sums(iht_dataset *ds, const float *r32, float *M, const int32_t *done)
 {
     cudaStream_t s = ds->ctx->stream;
-    const int blocks = (int)std::min<int64_t>(ceil_div(ds->p, 8), (int64_t)ds->ctx->num_sms * 16);
+    const int blocks = (int)std::min<int64_t>(ceil_div(ds->p, 64), (int64_t)ds->ctx->num_sms * 16);
     if (ds->miss_idx16)
         k_missing_sum<uint16_t><<<blocks, 256, 0, s>>>(ds->miss_off, (const uint16_t *)ds->miss_idx,
                                                        ds->p, r32, M, done);

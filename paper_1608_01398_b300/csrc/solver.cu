@@ -1,11 +1,15 @@
 // a3-a6: the O(nk) part of one IHT iteration, on the device.
 //
 //   k_gather_gS   coef = g_S, num = ||g_S||^2                     (Sec. 2.3.1)
-//   k_zmul        out = base + sign * Z[:, cols] coef, per-block partial sums
-//                 of out and out^2 (sparse product X_k beta_k, Sec. 2.3.2-2.3.3)
-//   k_merge       mu = num / den; w = beta + mu g on S u C; S+ = top-k |w|;
-//                 backtracking while mu >= omega (Eq. ihta, Sec. 2.3.1)
-//   k_finalize    objective, convergence test, state copy, trace
+//   k_zmul_*      out = base + sign * Z[:, cols] coef, per-block partial sums
+//                 of out, out^2 and (out - prev)^2 (sparse product X_k beta_k,
+//                 Sec. 2.3.2-2.3.3)
+//   k_merge       mu = num / den on the first attempt; w = beta + mu g on S u C;
+//                 S+ = top-k |w|, beta+ = w on S+ (Eq. ihta)
+//   k_decide      backtracking test (Sec. 2.3.1): with d = beta+ - beta,
+//                 Z d = r - r+, so ||Z d||^2 is the (out - prev)^2 sum of the
+//                 residual pass; mu >= omega -> mu / kappa and another attempt,
+//                 else accept: objective, convergence test, state copy, trace
 //   k_center      r32 = r - mean(r) on the used rows (exact: every column of Z
 //                 sums to zero over the used rows)
 // Every kernel returns at once when the solve is done, so a fixed launch
@@ -87,10 +91,12 @@ __global__ void __launch_bounds__(256) k_zmul_part(const uint8_t *__restrict__ G
 }
 
 // Phase 2: out_i = base_i + sum over groups (fixed order) on used rows, 0
-// elsewhere; per-block sums of out and out^2 into partials.
+// elsewhere; per-block sums of out, out^2 and (out - prev)^2 (0 without prev)
+// into partials[3 b .. 3 b + 2].
 __global__ void __launch_bounds__(256) k_zmul_sum(const double *__restrict__ part, int ngroups,
                                                   int64_t n_pad, const int32_t *__restrict__ used,
                                                   const double *__restrict__ base,
+                                                  const double *__restrict__ prev,
                                                   double *__restrict__ out,
                                                   double *__restrict__ partials,
                                                   const int32_t *__restrict__ done)
@@ -98,28 +104,32 @@ __global__ void __launch_bounds__(256) k_zmul_sum(const double *__restrict__ par
     __shared__ double red[8];
     if (done && *done) return;
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    double o = 0.0;
+    double o = 0.0, d = 0.0;
     if (i < n_pad) {
         double acc = 0.0;
         for (int g = 0; g < ngroups; ++g) acc += part[(int64_t)g * n_pad + i];
         o = used[i] ? (base ? base[i] : 0.0) + acc : 0.0;
         out[i] = o;
+        if (prev) d = o - prev[i];
     }
     const double s = block_sum(o, red);
     const double s2 = block_sum(o * o, red);
+    const double d2 = block_sum(d * d, red);
     if (threadIdx.x == 0 && partials) {
-        partials[2 * blockIdx.x] = s;
-        partials[2 * blockIdx.x + 1] = s2;
+        partials[3 * blockIdx.x] = s;
+        partials[3 * blockIdx.x + 1] = s2;
+        partials[3 * blockIdx.x + 2] = d2;
     }
 }
 
 int zmul_blocks(const iht_dataset *ds) { return ceil_div(ds->n_pad, 256); }
 
 // out = base + sign * Z[:, cols] coef (device, stream-ordered); partials get
-// zmul_blocks() pairs (sum, sum of squares) when not null.
+// zmul_blocks() triples (sum, sum of squares, sum of (out - prev)^2) when not
+// null.
 int zmul_run(iht_dataset *ds, const int32_t *cols, int m, const double *coef, double sign,
              const double *u, const double *v, const int32_t *used, const double *base,
-             double *out, double *partials, const int32_t *done)
+             double *out, double *partials, const int32_t *done, const double *prev = nullptr)
 {
     cudaStream_t s = ds->ctx->stream;
     const int ngroups = std::max(1, (m + kZmulColsPerGroup - 1) / kZmulColsPerGroup);
@@ -131,7 +141,7 @@ int zmul_run(iht_dataset *ds, const int32_t *cols, int m, const double *coef, do
         note_launch();
     }
     k_zmul_sum<<<zmul_blocks(ds), 256, 0, s>>>(ds->ws->zpart, m > 0 ? ngroups : 0, ds->n_pad, used,
-                                               base, out, partials, done);
+                                               base, prev, out, partials, done);
     note_launch();
     IHT_CUDA(cudaGetLastError());
     return IHT_OK;
@@ -145,20 +155,17 @@ int launch_zmul(iht_dataset *ds, const int32_t *cols, int32_t m, const double *c
 }
 
 // ---------------------------------------------------------------------------
-// Projection, step size and backtracking: one block of 1024 threads.
+// Projection for one step size: one block of 1024 threads.
 
 struct MergeArgs {
-    const uint8_t *G;
-    int64_t stride, rowb;
     const float *g;
-    const double *u64, *v64;
-    const int32_t *used;
     const int32_t *S;     // k, ascending
     const double *bS;     // beta on S
     const int32_t *cand;  // K, ascending
     int K;
-    const double *partials;
+    const double *partials;   // ||Z_S g_S||^2 pieces (first attempt)
     int npart;
+    int first;                // 1: compute mu from num / den
     int32_t *Sp;
     double *bSp;
     Scalars *sc;
@@ -177,11 +184,9 @@ struct MergeShared {
     uint8_t inSp[kMergeU];
     unsigned long long skey[kMergeSort];
     int32_t spos[kMergeSort];
-    double ca[2 * kMaxK], cb[2 * kMaxK];
-    int64_t coff[2 * kMaxK];
     double red[32];
     uint32_t wsum[32];
-    int nU, nS_extra, ncol;
+    int nS_extra;
     int stop;
 };
 
@@ -226,7 +231,6 @@ __device__ void sort_by_w(MergeShared &sh, int nU)
                     const int32_t pi = sh.spos[i], pj = sh.spos[j];
                     const int32_t xi = pi < 0 ? 0x7fffffff : sh.uidx[pi];
                     const int32_t xj = pj < 0 ? 0x7fffffff : sh.uidx[pj];
-                    // ascending in "before" order when up
                     const bool swap = up ? before(kj, xj, ki, xi) : before(ki, xi, kj, xj);
                     if (swap) {
                         sh.skey[i] = kj; sh.skey[j] = ki;
@@ -239,42 +243,6 @@ __device__ void sort_by_w(MergeShared &sh, int nU)
     }
 }
 
-// ||Z d||^2 over the used rows for the columns staged in ca/cb/coff: one
-// thread per 32-bit word (16 samples), eight columns' loads in flight.
-__device__ double znorm2(MergeShared &sh, const MergeArgs &A)
-{
-    double s = 0.0;
-    const int ncol = sh.ncol;
-    for (int64_t wdx = threadIdx.x; wdx < A.rowb / 4; wdx += blockDim.x) {
-        double acc[16];
-#pragma unroll
-        for (int e = 0; e < 16; ++e) acc[e] = 0.0;
-        for (int c0 = 0; c0 < ncol; c0 += 8) {
-            uint32_t w[8];
-#pragma unroll
-            for (int q = 0; q < 8; ++q)
-                w[q] = c0 + q < ncol
-                           ? __ldg(reinterpret_cast<const uint32_t *>(A.G + sh.coff[c0 + q]) + wdx)
-                           : 0x55555555u;
-#pragma unroll
-            for (int q = 0; q < 8; ++q) {
-                if (c0 + q < ncol) {
-                    const double a = sh.ca[c0 + q], b = sh.cb[c0 + q];
-#pragma unroll
-                    for (int e = 0; e < 16; ++e) {
-                        const int x = dosage_of((w[q] >> (2 * e)) & 3u);
-                        if (x >= 0) acc[e] += a * (double)x - b;
-                    }
-                }
-            }
-        }
-#pragma unroll
-        for (int e = 0; e < 16; ++e)
-            if (A.used[16 * wdx + e]) s += acc[e] * acc[e];
-    }
-    return block_sum(s, sh.red);
-}
-
 __global__ void __launch_bounds__(kMergeThreads) k_merge(MergeArgs A)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -283,27 +251,31 @@ __global__ void __launch_bounds__(kMergeThreads) k_merge(MergeArgs A)
     if (sc->done) return;
     const int k = sc->k;
 
-    // step size mu = ||g_S||^2 / ||Z_S g_S||^2
     if (threadIdx.x == 0) {
-        double den = 0.0;
-        for (int b = 0; b < A.npart; ++b) den += A.partials[2 * b + 1];
-        const double num = sc->num;
         sh.stop = 0;
-        if (num == 0.0) {
-            sc->status = IHT_OK;            // g_S = 0: fixed point
-            sc->done = 1;
-            sh.stop = 1;
-        } else if (!(den > 0.0) || !isfinite(den) || !isfinite(num)) {
-            sc->status = IHT_ENUMERIC;
-            sc->done = 1;
-            sh.stop = 1;
-        } else {
-            sc->mu = num / den;
-        }
         sh.nS_extra = 0;
+        if (A.first) {
+            // step size mu = ||g_S||^2 / ||Z_S g_S||^2 (reading of Sec. 2.3.1)
+            double den = 0.0;
+            for (int b = 0; b < A.npart; ++b) den += A.partials[3 * b + 1];
+            const double num = sc->num;
+            sc->bt_last = 0;
+            if (num == 0.0) {
+                sc->status = IHT_OK;            // g_S = 0: fixed point
+                sc->done = 1;
+                sh.stop = 1;
+            } else if (!(den > 0.0) || !isfinite(den) || !isfinite(num)) {
+                sc->status = IHT_ENUMERIC;
+                sc->done = 1;
+                sh.stop = 1;
+            } else {
+                sc->mu = num / den;
+            }
+        }
     }
     __syncthreads();
     if (sh.stop) return;
+    const double mu = sc->mu;
 
     // U = C (ascending) followed by S \ C (in S order)
     const int K = A.K;
@@ -316,7 +288,6 @@ __global__ void __launch_bounds__(kMergeThreads) k_merge(MergeArgs A)
         sh.ubeta[b] = on ? A.bS[pos] : 0.0;
         sh.ug[b] = (double)A.g[j];
     }
-    // S \ C with a block scan for deterministic positions (k <= 1024 = blockDim)
     {
         const int a = threadIdx.x;
         int32_t j = 0;
@@ -344,90 +315,28 @@ __global__ void __launch_bounds__(kMergeThreads) k_merge(MergeArgs A)
     }
     __syncthreads();
     const int nU = K + sh.nS_extra;
-    double mu = sc->mu;
-    const double c = sc->c, kappa = sc->kappa;
-    const int max_bt = sc->max_backtrack;
-    int bt = 0;
-    bool changed = false;
 
-    for (;;) {
-        for (int u = threadIdx.x; u < nU; u += blockDim.x)
-            sh.uw[u] = __dadd_rn(sh.ubeta[u], __dmul_rn(mu, sh.ug[u]));
-        __syncthreads();
-        sort_by_w(sh, nU);
-        for (int u = threadIdx.x; u < nU; u += blockDim.x) sh.inSp[u] = 0;
-        __syncthreads();
-        for (int r = threadIdx.x; r < k; r += blockDim.x) sh.inSp[sh.spos[r]] = 1;
-        __syncthreads();
-        int kept = 0;
-        for (int u = threadIdx.x; u < nU; u += blockDim.x) kept += sh.inS[u] && sh.inSp[u];
-        kept = (int)block_sum((double)kept, sh.red);
-        changed = kept < k;
-        if (!changed) break;
-        // d = beta+ - beta on S u S+; omega = (1-c) ||d||^2 / ||Z d||^2
-        if (threadIdx.x == 0) sh.ncol = 0;
-        __syncthreads();
-        double dd = 0.0;
-        for (int u = threadIdx.x; u < nU; u += blockDim.x) {
-            const double bp = sh.inSp[u] ? sh.uw[u] : 0.0;
-            const double d = bp - sh.ubeta[u];
-            dd += d * d;
-        }
-        dd = block_sum(dd, sh.red);
-        // stage the columns of S u S+ in U order (deterministic)
-        {
-            for (int base0 = 0; base0 < nU; base0 += blockDim.x) {
-                const int u = base0 + threadIdx.x;
-                bool on = false;
-                double d = 0.0;
-                if (u < nU) {
-                    on = sh.inS[u] || sh.inSp[u];
-                    d = (sh.inSp[u] ? sh.uw[u] : 0.0) - sh.ubeta[u];
-                }
-                const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-                const unsigned bal = __ballot_sync(0xffffffffu, on);
-                if (lane == 0) sh.wsum[wid] = __popc(bal);
-                __syncthreads();
-                int off = sh.ncol;
-                for (int w = 0; w < wid; ++w) off += sh.wsum[w];
-                off += __popc(bal & ((1u << lane) - 1u));
-                if (on) {
-                    const int32_t j = sh.uidx[u];
-                    const double a = d * A.v64[j];
-                    sh.ca[off] = a;
-                    sh.cb[off] = a * A.u64[j];
-                    sh.coff[off] = (int64_t)j * A.stride;
-                }
-                __syncthreads();
-                if (threadIdx.x == 0) {
-                    int tot = 0;
-                    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) tot += sh.wsum[w];
-                    sh.ncol += tot;
-                }
-                __syncthreads();
-            }
-        }
-        const double zz = znorm2(sh, A);
-        if (!(zz > 0.0)) break;                       // Z d = 0: accept
-        const double omega = (1.0 - c) * dd / zz;
-        if (mu < omega || bt >= max_bt) break;
-        mu = mu / kappa;
-        ++bt;
-        __syncthreads();
-    }
-
-    // accepted candidate: step size of the test, S+ ascending with beta+
+    for (int u = threadIdx.x; u < nU; u += blockDim.x)
+        sh.uw[u] = __dadd_rn(sh.ubeta[u], __dmul_rn(mu, sh.ug[u]));
+    __syncthreads();
+    sort_by_w(sh, nU);
+    for (int u = threadIdx.x; u < nU; u += blockDim.x) sh.inSp[u] = 0;
+    __syncthreads();
+    for (int r = threadIdx.x; r < k; r += blockDim.x) sh.inSp[sh.spos[r]] = 1;
+    __syncthreads();
+    int kept = 0;
     double dd = 0.0, bb = 0.0;
     for (int u = threadIdx.x; u < nU; u += blockDim.x) {
-        const double bp = sh.inSp[u] ? sh.uw[u] : 0.0;
-        const double d = bp - sh.ubeta[u];
+        kept += sh.inS[u] && sh.inSp[u];
+        const double d = (sh.inSp[u] ? sh.uw[u] : 0.0) - sh.ubeta[u];
         dd += d * d;
         bb += sh.ubeta[u] * sh.ubeta[u];
     }
+    kept = (int)block_sum((double)kept, sh.red);
     dd = block_sum(dd, sh.red);
     bb = block_sum(bb, sh.red);
-    // S+ in index order: positions of the selected entries, sorted by index
-    __syncthreads();
+
+    // S+ in index order with beta+
     for (int r = threadIdx.x; r < kMergeSort; r += blockDim.x) sh.skey[r] = ~0ull;
     __syncthreads();
     for (int r = threadIdx.x; r < k; r += blockDim.x) {
@@ -457,11 +366,9 @@ __global__ void __launch_bounds__(kMergeThreads) k_merge(MergeArgs A)
         A.bSp[r] = sh.uw[u];
     }
     if (threadIdx.x == 0) {
-        sc->mu = mu;
-        sc->bt_last = bt;
-        sc->bt_total += bt;
-        sc->changed = changed ? 1 : 0;
-        sc->step = sqrt(dd) / (sqrt(bb) + 1.0);
+        sc->changed = kept < k ? 1 : 0;
+        sc->dd = dd;
+        sc->bb = bb;
     }
 }
 
@@ -472,61 +379,93 @@ struct TraceDev {
     double *beta;
 };
 
-__global__ void __launch_bounds__(1024) k_finalize(Scalars *sc, const double *partials, int npart,
-                                                   int32_t *S, double *bS, const int32_t *Sp,
-                                                   const double *bSp, TraceDev tr, int first)
+// Backtracking decision for the candidate of k_merge, whose residual r+ the
+// preceding pass wrote (partials: sum r+, sum r+^2, sum (r+ - r)^2).
+__global__ void __launch_bounds__(256) k_decide(Scalars *sc, const double *partials, int npart,
+                                                int32_t *S, double *bS, const int32_t *Sp,
+                                                const double *bSp, TraceDev tr)
 {
-    __shared__ int stop;
+    __shared__ int accept;
     if (sc->done) return;
     const int k = sc->k;
     if (threadIdx.x == 0) {
-        double s = 0.0, s2 = 0.0;
+        double s = 0.0, s2 = 0.0, zz = 0.0;
         for (int b = 0; b < npart; ++b) {
-            s += partials[2 * b];
-            s2 += partials[2 * b + 1];
+            s += partials[3 * b];
+            s2 += partials[3 * b + 1];
+            zz += partials[3 * b + 2];
         }
-        sc->sum_r = s;
-        sc->sumsq_r = s2;
-        sc->f = 0.5 * s2;
-        stop = 0;
-        if (!first) {
+        accept = 1;
+        if (sc->changed && zz > 0.0) {
+            const double omega = (1.0 - sc->c) * sc->dd / zz;
+            if (sc->mu >= omega && sc->bt_last < sc->max_backtrack) {
+                sc->mu = sc->mu / sc->kappa;
+                sc->bt_last += 1;
+                accept = 0;
+            }
+        }
+        sc->retry = accept ? 0 : 1;
+        if (accept) {
             const int it = sc->iter;
+            sc->bt_total += sc->bt_last;
+            sc->sum_r = s;
+            sc->sumsq_r = s2;
+            sc->f = 0.5 * s2;
+            sc->step = sqrt(sc->dd) / (sqrt(sc->bb) + 1.0);
             if (tr.objective) tr.objective[it] = sc->f;
             if (tr.mu) tr.mu[it] = sc->mu;
             if (tr.backtracks) tr.backtracks[it] = sc->bt_last;
             if (tr.changed) tr.changed[it] = sc->changed;
-            sc->iter = it + 1;
-            if (sc->step < sc->tol) {
-                sc->status = IHT_OK;
-                stop = 1;
-            } else if (sc->iter >= sc->max_iter) {
-                sc->status = IHT_ENOTCONV;
-                stop = 1;
-            }
         }
     }
     __syncthreads();
-    if (!first) {
-        const int it = sc->iter - 1;
-        for (int c = threadIdx.x; c < k; c += blockDim.x) {
-            S[c] = Sp[c];
-            bS[c] = bSp[c];
-            if (tr.supp) tr.supp[(size_t)it * k + c] = Sp[c];
-            if (tr.beta) tr.beta[(size_t)it * k + c] = bSp[c];
-        }
+    if (!accept) return;
+    const int it = sc->iter;
+    for (int c = threadIdx.x; c < k; c += blockDim.x) {
+        S[c] = Sp[c];
+        bS[c] = bSp[c];
+        if (tr.supp) tr.supp[(size_t)it * k + c] = Sp[c];
+        if (tr.beta) tr.beta[(size_t)it * k + c] = bSp[c];
     }
     __syncthreads();
-    if (threadIdx.x == 0 && stop) sc->done = 1;
+    if (threadIdx.x == 0) {
+        sc->iter = it + 1;
+        if (sc->step < sc->tol) {
+            sc->status = IHT_OK;
+            sc->done = 1;
+        } else if (sc->iter >= sc->max_iter) {
+            sc->status = IHT_ENOTCONV;
+            sc->done = 1;
+        }
+    }
 }
 
-__global__ void k_center(const double *__restrict__ r64, const int32_t *__restrict__ used,
-                         int64_t n_pad, const Scalars *sc, float *__restrict__ r32)
+// Objective of beta = 0 (r = y) before the first iteration.
+__global__ void k_init_objective(Scalars *sc, const double *partials, int npart)
 {
-    if (sc->done) return;
+    if (sc->done || threadIdx.x != 0) return;
+    double s = 0.0, s2 = 0.0;
+    for (int b = 0; b < npart; ++b) {
+        s += partials[3 * b];
+        s2 += partials[3 * b + 1];
+    }
+    sc->sum_r = s;
+    sc->sumsq_r = s2;
+    sc->f = 0.5 * s2;
+}
+
+// Accepted residual: r64 <- src, r32 <- src - mean on the used rows.
+__global__ void k_center(const double *__restrict__ src, double *__restrict__ r64,
+                         const int32_t *__restrict__ used, int64_t n_pad, const Scalars *sc,
+                         float *__restrict__ r32)
+{
+    if (sc->done || sc->retry) return;
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n_pad) return;
     const double mean = sc->sum_r / (double)sc->n_rows;
-    r32[i] = used[i] ? (float)(r64[i] - mean) : 0.0f;
+    const double v = src[i];
+    if (src != r64) r64[i] = v;
+    r32[i] = used[i] ? (float)(v - mean) : 0.0f;
 }
 
 __global__ void k_check_finite(const double *__restrict__ y, int64_t n, Scalars *sc)
@@ -538,13 +477,7 @@ __global__ void k_check_finite(const double *__restrict__ y, int64_t n, Scalars 
 // ---------------------------------------------------------------------------
 // Host orchestration of one solve.
 
-struct SolveArgs {
-    int k;
-    const iht_options *opt;
-    TraceDev tr;
-};
-
-int launch_merge(iht_dataset *ds, int k, int K)
+int launch_merge(iht_dataset *ds, int K, int first)
 {
     static thread_local int configured_dev = -1;
     const int smem = (int)sizeof(MergeShared);
@@ -554,19 +487,14 @@ int launch_merge(iht_dataset *ds, int k, int K)
     }
     Workspace *ws = ds->ws;
     MergeArgs A;
-    A.G = ds->G;
-    A.stride = ds->stride;
-    A.rowb = ds->rowb;
     A.g = ws->g;
-    A.u64 = ws->u64;
-    A.v64 = ws->v64;
-    A.used = ws->used;
     A.S = ws->S;
     A.bS = ws->bS;
     A.cand = ws->cand;
     A.K = K;
     A.partials = ws->partials;
     A.npart = zmul_blocks(ds);
+    A.first = first;
     A.Sp = ws->Sp;
     A.bSp = ws->bSp;
     A.sc = ws->sc;
@@ -603,7 +531,6 @@ int run_solve(iht_dataset *ds, int k, const iht_options *opt, int n_rows, const 
     const int K = (int)std::min<int64_t>(2 * (int64_t)k, ds->p);
     int rc;
 
-    // scalars
     Scalars h{};
     h.c = opt->c;
     h.kappa = opt->kappa;
@@ -614,21 +541,20 @@ int run_solve(iht_dataset *ds, int k, const iht_options *opt, int n_rows, const 
     h.n_rows = n_rows;
     h.status = IHT_ENOTCONV;
     h.done = opt->max_iter <= 0 ? 1 : 0;
-    // err may already hold row / input flags: keep it
     IHT_CUDA(cudaMemcpyAsync(ws->sc_host, ws->sc, sizeof(Scalars), cudaMemcpyDeviceToHost, s));
     IHT_CUDA(cudaStreamSynchronize(s));
-    h.err = ws->sc_host->err;
+    h.err = ws->sc_host->err;        // row / input flags from the set-up kernels
     if (h.err) return (h.err & 1) ? IHT_ENUMERIC : IHT_EINVAL;
-    if (opt->max_iter <= 0) h.status = IHT_ENOTCONV;
     *ws->sc_host = h;
     IHT_CUDA(cudaMemcpyAsync(ws->sc, ws->sc_host, sizeof(Scalars), cudaMemcpyHostToDevice, s));
 
-    // r = y (beta = 0), objective, centred residual, g^0, S^0 = top-k |g^0|
+    // beta = 0: r = y, objective, centred residual, g^0, S^0 = top-k |g^0|
     if ((rc = zmul_run(ds, ws->cols, 0, ws->coef, -1.0, ws->u64, ws->v64, ws->used, ws->y64,
                        ws->r64, ws->partials, nullptr)))
         return rc;
-    k_finalize<<<1, 1024, 0, s>>>(ws->sc, ws->partials, npart, ws->S, ws->bS, ws->Sp, ws->bSp, tr, 1);
-    k_center<<<ceil_div(ds->n_pad, 256), 256, 0, s>>>(ws->r64, ws->used, ds->n_pad, ws->sc, ws->r32);
+    k_init_objective<<<1, 32, 0, s>>>(ws->sc, ws->partials, npart);
+    k_center<<<ceil_div(ds->n_pad, 256), 256, 0, s>>>(ws->r64, ws->r64, ws->used, ds->n_pad, ws->sc,
+                                                      ws->r32);
     note_launch(2);
     IHT_CUDA(cudaGetLastError());
     const int32_t *done = &ws->sc->done;
@@ -649,19 +575,21 @@ int run_solve(iht_dataset *ds, int k, const iht_options *opt, int n_rows, const 
         if ((rc = zmul_run(ds, ws->S, k, ws->coef, 1.0, ws->u64, ws->v64, ws->used, nullptr, ws->zv,
                            ws->partials, done)))
             return rc;
-        if ((rc = launch_merge(ds, k, K))) return rc;
-        if ((rc = zmul_run(ds, ws->Sp, k, ws->bSp, -1.0, ws->u64, ws->v64, ws->used, ws->y64,
-                           ws->r64, ws->partials, done)))
-            return rc;
-        k_finalize<<<1, 1024, 0, s>>>(ws->sc, ws->partials, npart, ws->S, ws->bS, ws->Sp, ws->bSp,
-                                      tr, 0);
-        k_center<<<ceil_div(ds->n_pad, 256), 256, 0, s>>>(ws->r64, ws->used, ds->n_pad, ws->sc,
-                                                          ws->r32);
-        note_launch(2);   // finalize, center
-        IHT_CUDA(cudaGetLastError());
-        IHT_CUDA(cudaMemcpyAsync(&ws->sc_host->done, &ws->sc->done, sizeof(int32_t),
-                                 cudaMemcpyDeviceToHost, s));
-        IHT_CUDA(cudaStreamSynchronize(s));
+        for (int attempt = 0;; ++attempt) {
+            if ((rc = launch_merge(ds, K, attempt == 0))) return rc;
+            if ((rc = zmul_run(ds, ws->Sp, k, ws->bSp, -1.0, ws->u64, ws->v64, ws->used, ws->y64,
+                               ws->rc64, ws->partials, done, ws->r64)))
+                return rc;
+            k_decide<<<1, 256, 0, s>>>(ws->sc, ws->partials, npart, ws->S, ws->bS, ws->Sp, ws->bSp, tr);
+            k_center<<<ceil_div(ds->n_pad, 256), 256, 0, s>>>(ws->rc64, ws->r64, ws->used, ds->n_pad,
+                                                              ws->sc, ws->r32);
+            note_launch(2);
+            IHT_CUDA(cudaGetLastError());
+            IHT_CUDA(cudaMemcpyAsync(&ws->sc_host->done, &ws->sc->done, 2 * sizeof(int32_t),
+                                     cudaMemcpyDeviceToHost, s));
+            IHT_CUDA(cudaStreamSynchronize(s));
+            if (ws->sc_host->done || !ws->sc_host->retry) break;
+        }
         if (ws->sc_host->done) break;
     }
     IHT_CUDA(cudaMemcpyAsync(ws->sc_host, ws->sc, sizeof(Scalars), cudaMemcpyDeviceToHost, s));
