@@ -200,6 +200,43 @@ int iht_fit_trace(iht_dataset *ds, const int32_t *rows, int64_t n_rows, const do
                   int32_t k, const iht_options *opt, double *beta_out, int32_t *support_out,
                   iht_result *info, iht_trace *trace);
 
+/* One solve of a batch: its row set (a CV training fold, a phenotype's
+ * non-missing subjects, a serving request's subset), phenotype and k. */
+typedef struct iht_solve_desc {
+    const int32_t *rows;   /* int32[n_rows] distinct subjects, or NULL = all n   */
+    int64_t n_rows;        /* rows in use (n when rows is NULL)                  */
+    const double *y;       /* double[n_rows], aligned with rows                  */
+    int32_t k;             /* sparsity level, 1 <= k <= min(p, 1024)             */
+    int32_t reserved;
+} iht_solve_desc;
+
+/* a2-a7 -- b IHT solves on one dataset that share every pass over the packed
+ * genotypes (Sec. 2.4 model selection: q-fold cross-validation over a path of
+ * model sizes fits many solves on the same matrix).  Each solve follows
+ * iht_fit exactly (same readings, same statistics over its own rows); the
+ * gradient of all active solves is one multi-right-hand-side pass per
+ * iteration, and every other step runs batched.  Solves retire independently.
+ *   solves  : host array of b descriptors (rows, y in opt->in_mem memory).
+ *   betas   : double[b][p] (opt->out_mem memory) or NULL.
+ *   supports: int32[sum of k] concatenated in solve order (opt->out_mem).
+ *   infos   : host iht_result[b], may be NULL.
+ * Returns OK, EINVAL, ENOMEM, ECUDA; per-solve status (OK, ENOTCONV,
+ * ENUMERIC) is in infos[c].status.  Identical row sets (same rows pointer and
+ * n_rows) share one set of statistics. */
+int iht_fit_batch(iht_dataset *ds, int32_t b, const iht_solve_desc *solves,
+                  const iht_options *opt, double *betas, int32_t *supports, iht_result *infos);
+
+/* a7 -- multi-right-hand-side standardised gradient G = Z^T R for b residual
+ * columns, each with its own row set and statistics (exposes the batched
+ * gradient for tests).
+ *   rows_list : host array of b device pointers (int32 row lists or NULL = all)
+ *   n_rows    : host int64[b]
+ *   R         : device float, column c at R + c * n (aligned with its rows)
+ *   G_out     : device float[b][p]
+ *   impl      : 0 default, 1 one CUDA-core pass per column, 2 multi-RHS tensor cores. */
+int iht_gradient_batch(iht_dataset *ds, int32_t b, const int32_t *const *rows_list,
+                       const int64_t *n_rows, const float *R, float *G_out, int impl);
+
 #ifdef __cplusplus
 }
 #endif

@@ -25,7 +25,7 @@ EXPORTED = ["iht_default_options", "iht_strerror", "iht_last_cuda_error", "iht_k
             "iht_create",
             "iht_destroy", "iht_load_bed", "iht_dataset_free", "iht_dataset_shape", "iht_counts",
             "iht_gradient", "iht_topk", "iht_topk_noalloc", "iht_zmul", "iht_fit",
-            "iht_fit_trace"]
+            "iht_fit_trace", "iht_fit_batch", "iht_gradient_batch"]
 
 
 class IhtError(RuntimeError):
@@ -56,6 +56,11 @@ class iht_trace(ctypes.Structure):
     _fields_ = [("objective", ctypes.c_void_p), ("mu", ctypes.c_void_p),
                 ("backtracks", ctypes.c_void_p), ("changed", ctypes.c_void_p),
                 ("supp", ctypes.c_void_p), ("beta", ctypes.c_void_p)]
+
+
+class iht_solve_desc(ctypes.Structure):
+    _fields_ = [("rows", ctypes.c_void_p), ("n_rows", ctypes.c_int64), ("y", ctypes.c_void_p),
+                ("k", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 _LIB = None
@@ -98,6 +103,11 @@ def _lib(build_if_stale: bool = True):
                                    ctypes.POINTER(iht_result)]),
         "iht_fit_trace": (ctypes.c_int, [P, P, i64, P, i32, ctypes.POINTER(iht_options), P, P,
                                          ctypes.POINTER(iht_result), ctypes.POINTER(iht_trace)]),
+        "iht_fit_batch": (ctypes.c_int, [P, i32, ctypes.POINTER(iht_solve_desc),
+                                         ctypes.POINTER(iht_options), P, P,
+                                         ctypes.POINTER(iht_result)]),
+        "iht_gradient_batch": (ctypes.c_int, [P, i32, ctypes.POINTER(P), ctypes.POINTER(i64), P, P,
+                                              ctypes.c_int]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -342,3 +352,97 @@ def iht_fit_trace(ds: Dataset, y, k: int, rows=None, **opt) -> FitResult:
     o = iht_default_options(**opt)
     o.out_mem = IHT_DEVICE if out_device else IHT_HOST
     return _fit(ds, y, k, rows, o, trace=True)
+
+
+def iht_fit_batch(ds: Dataset, problems, out_device: bool = False, **opt) -> list:
+    """b solves sharing the genotype passes (iht_fit_batch).
+
+    problems: sequence of (y, k, rows); y and rows numpy arrays (host inputs)
+    or CUDA tensors (device inputs), all of the same kind; rows None = all n.
+    The same rows object in several problems is one row set (statistics
+    computed once).  Returns one FitResult per problem.
+    """
+    torch = _torch()
+    o = iht_default_options(**opt)
+    o.out_mem = IHT_DEVICE if out_device else IHT_HOST
+    b = len(problems)
+    if b < 1:
+        raise ValueError("no problems")
+    dev_in = isinstance(problems[0][0], torch.Tensor)
+    o.in_mem = IHT_DEVICE if dev_in else IHT_HOST
+    keep, rows_ptr = [], {}
+    descs = (iht_solve_desc * b)()
+    ks = []
+    for c, (y, k, rows) in enumerate(problems):
+        if isinstance(y, torch.Tensor) != dev_in:
+            raise TypeError("all phenotypes must be host arrays or all CUDA tensors")
+        if dev_in:
+            yp, nr = _dptr(y, torch.float64, "y"), y.numel()
+        else:
+            y = np.ascontiguousarray(y, dtype=np.float64)
+            yp, nr = y.ctypes.data, y.size
+        keep.append(y)
+        rp = None
+        if rows is not None:
+            key = id(rows)
+            if key not in rows_ptr:
+                if dev_in:
+                    rows_ptr[key] = (_dptr(rows, torch.int32, "rows"), rows.numel(), rows)
+                else:
+                    ra = np.ascontiguousarray(rows, dtype=np.int32)
+                    rows_ptr[key] = (ra.ctypes.data, ra.size, ra)
+            rp, nrr, _ = rows_ptr[key]
+            if nrr != nr:
+                raise ValueError("y must have one entry per row")
+        elif nr != ds.n:
+            raise ValueError("y must have n entries when rows is None")
+        descs[c] = iht_solve_desc(rp, nr, yp, int(k), 0)
+        ks.append(int(k))
+    ktot = sum(ks)
+    if out_device:
+        betas = torch.empty((b, ds.p), dtype=torch.float64, device=f"cuda:{ds.ctx.device}")
+        supp = torch.empty(ktot, dtype=torch.int32, device=f"cuda:{ds.ctx.device}")
+        bp, sp = betas.data_ptr(), supp.data_ptr()
+    else:
+        betas = np.empty((b, ds.p))
+        supp = np.empty(ktot, dtype=np.int32)
+        bp, sp = betas.ctypes.data, supp.ctypes.data
+    infos = (iht_result * b)()
+    rc = _lib().iht_fit_batch(ds.h, b, descs, ctypes.byref(o), ctypes.c_void_p(bp),
+                              ctypes.c_void_p(sp), infos)
+    _check(rc, "iht_fit_batch")
+    out, off = [], 0
+    for c in range(b):
+        r = infos[c]
+        out.append(FitResult(betas[c], supp[off:off + ks[c]], r.iterations, r.status, r.backtracks,
+                             r.objective, r.mu, None, r.grad_ms, r.grad_launches))
+        off += ks[c]
+    return out
+
+
+def iht_gradient_batch(ds: Dataset, R, rows_list=None, impl: int = 0):
+    """G[c] = Z_c^T r_c for b residual columns (float32 CUDA tensors, each
+    aligned with its rows; rows_list entries None = all n).  Returns a (b, p)
+    float32 CUDA tensor."""
+    torch = _torch()
+    b = len(R)
+    rows_list = [None] * b if rows_list is None else list(rows_list)
+    if len(rows_list) != b or b < 1:
+        raise ValueError("one row list per column")
+    dev = f"cuda:{ds.ctx.device}"
+    Rbuf = torch.zeros((b, ds.n), dtype=torch.float32, device=dev)
+    ptrs = (ctypes.c_void_p * b)()
+    nrows = (ctypes.c_int64 * b)()
+    for c in range(b):
+        r, rows = R[c], rows_list[c]
+        nr = ds.n if rows is None else rows.numel()
+        if r.numel() != nr:
+            raise ValueError("each column needs one entry per row")
+        _dptr(r, torch.float32, "R[c]")
+        Rbuf[c, :nr] = r
+        ptrs[c] = None if rows is None else _dptr(rows, torch.int32, "rows")
+        nrows[c] = nr
+    G = torch.empty((b, ds.p), dtype=torch.float32, device=dev)
+    _check(_lib().iht_gradient_batch(ds.h, b, ptrs, nrows, ctypes.c_void_p(Rbuf.data_ptr()),
+                                     ctypes.c_void_p(G.data_ptr()), impl), "iht_gradient_batch")
+    return G

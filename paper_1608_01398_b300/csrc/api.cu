@@ -22,22 +22,6 @@ void set_cuda_error(cudaError_t e, const char *where)
              cudaGetErrorString(e), where);
 }
 
-// Makes ctx->device current for the scope of an API call.
-struct DeviceGuard {
-    int prev = -1;
-    bool ok = true;
-    explicit DeviceGuard(int dev)
-    {
-        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
-        if (prev != dev) ok = cudaSetDevice(dev) == cudaSuccess;
-    }
-    ~DeviceGuard()
-    {
-        int cur = -1;
-        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
-    }
-};
-
 void free_workspace(Workspace *ws)
 {
     if (!ws) return;
@@ -48,6 +32,7 @@ void free_workspace(Workspace *ws)
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (ws->sc_host) cudaFreeHost(ws->sc_host);
+    free_batchwork(ws->bw);
     for (cudaEvent_t e : ws->prof_ev)
         if (e) cudaEventDestroy(e);
     delete ws;

@@ -1,0 +1,521 @@
+// a7: b IHT solves on one dataset that share every pass over the genotypes.
+//
+// Each solve follows the single-solve path step for step (same readings,
+// statistics over its own rows, same tails), but an iteration of the batch
+// is one multi-column gradient pass (grad_mrhs.cu) for all solves still
+// running, then every O(nk) step as one launch over the batch
+// (solver.cu / select.cu batched kernels, blockIdx = solve).  Solves retire
+// independently: a finished solve drops out of the gradient columns and its
+// blocks of the tail kernels return at once.  Row sets shared by several
+// solves (a cross-validation fold used along a path of model sizes) have
+// their per-SNP statistics computed once (Sec. 2.3.2).
+#include <stdlib.h>
+#include <string.h>
+
+#include <new>
+#include <vector>
+
+#include "common.cuh"
+
+namespace iht {
+
+struct BatchWork {
+    int nb = 0, kcap = 0, nsets = 0;       // capacities
+    int64_t rows_cap = 0, y_cap = 0;
+    Scalars *sc = nullptr, *sc_host = nullptr;
+    double *y64 = nullptr, *r64 = nullptr, *rc64 = nullptr, *zv = nullptr;
+    float *r32 = nullptr, *g = nullptr;
+    int32_t *S = nullptr, *Sp = nullptr, *cand = nullptr;
+    double *bS = nullptr, *bSp = nullptr, *coef = nullptr, *partials = nullptr, *zpart = nullptr;
+    SelState *st = nullptr;
+    uint32_t *hist = nullptr, *chunk_eq = nullptr;
+    BSolve *bs = nullptr, *bs_host = nullptr;
+    SelJob *jobs = nullptr, *jobs_host = nullptr;     // 2 nb: top-k then candidates
+    MrCol *cols = nullptr, *cols_host = nullptr;
+    // row sets
+    int32_t *set_used = nullptr, *set_err = nullptr, *set_err_host = nullptr;
+    uint32_t *set_rowmask = nullptr;
+    double *set_u64 = nullptr, *set_v64 = nullptr;
+    float *set_u32 = nullptr, *set_v32 = nullptr;
+    int32_t *rows_dev = nullptr;           // staged host row lists
+    double *ybuf = nullptr;                // staged host phenotypes
+    cudaEvent_t ev[2 * kProfEvents] = {};
+};
+
+void free_batchwork(BatchWork *w)
+{
+    if (!w) return;
+    void *dev[] = {w->sc, w->y64, w->r64, w->rc64, w->zv, w->r32, w->g, w->S, w->Sp, w->cand,
+                   w->bS, w->bSp, w->coef, w->partials, w->zpart, w->st, w->hist, w->chunk_eq,
+                   w->bs, w->jobs, w->cols, w->set_used, w->set_err, w->set_rowmask, w->set_u64,
+                   w->set_v64, w->set_u32, w->set_v32, w->rows_dev, w->ybuf};
+    for (void *p : dev)
+        if (p) cudaFree(p);
+    void *host[] = {w->sc_host, w->bs_host, w->jobs_host, w->cols_host, w->set_err_host};
+    for (void *p : host)
+        if (p) cudaFreeHost(p);
+    for (cudaEvent_t e : w->ev)
+        if (e) cudaEventDestroy(e);
+    delete w;
+}
+
+static int kgroups(int k) { return (k + 3) / 4; }
+
+// Capacity for nb solves of sparsity <= kcap over nsets row sets, rows_total
+// staged row indices and y_total staged phenotype values.
+static int ensure_batchwork(iht_dataset *ds, int nb, int kcap, int nsets, int64_t rows_total,
+                            int64_t y_total)
+{
+    BatchWork *&w = ds->ws->bw;
+    if (w && w->nb >= nb && w->kcap >= kcap && w->nsets >= nsets && w->rows_cap >= rows_total &&
+        w->y_cap >= y_total)
+        return IHT_OK;
+    if (w) {
+        nb = std::max(nb, w->nb);
+        kcap = std::max(kcap, w->kcap);
+        nsets = std::max(nsets, w->nsets);
+        rows_total = std::max(rows_total, w->rows_cap);
+        y_total = std::max(y_total, w->y_cap);
+        cudaStreamSynchronize(ds->ctx->stream);
+        free_batchwork(w);
+        w = nullptr;
+    }
+    BatchWork *x = new (std::nothrow) BatchWork();
+    if (!x) return IHT_ENOMEM;
+    const size_t np = (size_t)ds->n_pad, p = (size_t)ds->p, B = (size_t)nb, K = (size_t)kcap;
+    const size_t nch = (size_t)sel_nchunks(ds->p);
+    cudaError_t e = cudaSuccess;
+#define BALLOC(field, bytes) \
+    if (e == cudaSuccess) e = cudaMalloc((void **)&x->field, std::max<size_t>(16, (size_t)(bytes)));
+    BALLOC(sc, sizeof(Scalars) * B);
+    BALLOC(y64, sizeof(double) * B * np);
+    BALLOC(r64, sizeof(double) * B * np);
+    BALLOC(rc64, sizeof(double) * B * np);
+    BALLOC(zv, sizeof(double) * B * np);
+    BALLOC(r32, sizeof(float) * B * np);
+    BALLOC(g, sizeof(float) * B * p);
+    BALLOC(S, sizeof(int32_t) * B * K);
+    BALLOC(Sp, sizeof(int32_t) * B * K);
+    BALLOC(cand, sizeof(int32_t) * B * 2 * K);
+    BALLOC(bS, sizeof(double) * B * K);
+    BALLOC(bSp, sizeof(double) * B * K);
+    BALLOC(coef, sizeof(double) * B * K);
+    BALLOC(partials, sizeof(double) * B * 3 * kPartials);
+    BALLOC(zpart, sizeof(double) * B * kgroups(kcap) * np);
+    BALLOC(st, sizeof(SelState) * 2 * B);
+    BALLOC(hist, sizeof(uint32_t) * 2 * B * kSelBins);
+    BALLOC(chunk_eq, sizeof(uint32_t) * 2 * B * nch);
+    BALLOC(bs, sizeof(BSolve) * B);
+    BALLOC(jobs, sizeof(SelJob) * 2 * B);
+    BALLOC(cols, sizeof(MrCol) * B);
+    BALLOC(set_used, sizeof(int32_t) * nsets * np);
+    BALLOC(set_err, sizeof(int32_t) * nsets);
+    BALLOC(set_rowmask, sizeof(uint32_t) * nsets * (ds->stride / 4));
+    BALLOC(set_u64, sizeof(double) * nsets * p);
+    BALLOC(set_v64, sizeof(double) * nsets * p);
+    BALLOC(set_u32, sizeof(float) * nsets * p);
+    BALLOC(set_v32, sizeof(float) * nsets * p);
+    BALLOC(rows_dev, sizeof(int32_t) * rows_total);
+    BALLOC(ybuf, sizeof(double) * y_total);
+#undef BALLOC
+    if (e == cudaSuccess) e = cudaMallocHost((void **)&x->sc_host, sizeof(Scalars) * B);
+    if (e == cudaSuccess) e = cudaMallocHost((void **)&x->bs_host, sizeof(BSolve) * B);
+    if (e == cudaSuccess) e = cudaMallocHost((void **)&x->jobs_host, sizeof(SelJob) * 2 * B);
+    if (e == cudaSuccess) e = cudaMallocHost((void **)&x->cols_host, sizeof(MrCol) * B);
+    if (e == cudaSuccess) e = cudaMallocHost((void **)&x->set_err_host, sizeof(int32_t) * nsets);
+    if (e != cudaSuccess) {
+        set_cuda_error(e, "batch workspace allocation");
+        free_batchwork(x);
+        return e == cudaErrorMemoryAllocation ? IHT_ENOMEM : IHT_ECUDA;
+    }
+    x->nb = nb;
+    x->kcap = kcap;
+    x->nsets = nsets;
+    x->rows_cap = rows_total;
+    x->y_cap = y_total;
+    w = x;
+    return IHT_OK;
+}
+
+static RowSet batch_rowset(iht_dataset *ds, BatchWork *w, int q)
+{
+    const size_t np = (size_t)ds->n_pad, p = (size_t)ds->p;
+    RowSet rs;
+    rs.used = w->set_used + q * np;
+    rs.rowmask = w->set_rowmask + q * (size_t)(ds->stride / 4);
+    rs.counts = nullptr;
+    rs.u64 = w->set_u64 + q * p;
+    rs.v64 = w->set_v64 + q * p;
+    rs.u32 = w->set_u32 + q * p;
+    rs.v32 = w->set_v32 + q * p;
+    return rs;
+}
+
+struct SetKey {
+    const int32_t *rows;
+    int64_t n_rows;
+};
+
+// Distinct row sets of the solves (same rows pointer and length = same set).
+static void dedupe_sets(int b, const int32_t *const *rows, const int64_t *n_rows, int64_t n,
+                        std::vector<SetKey> &sets, std::vector<int> &set_of)
+{
+    sets.clear();
+    set_of.assign(b, -1);
+    for (int c = 0; c < b; ++c) {
+        const int64_t nr = rows[c] ? n_rows[c] : n;
+        int q = -1;
+        for (size_t t = 0; t < sets.size(); ++t)
+            if (sets[t].rows == rows[c] && sets[t].n_rows == nr) {
+                q = (int)t;
+                break;
+            }
+        if (q < 0) {
+            sets.push_back(SetKey{rows[c], nr});
+            q = (int)sets.size() - 1;
+        }
+        set_of[c] = q;
+    }
+}
+
+// Row marks and statistics of every set; EINVAL when a set has bad or
+// duplicate rows.  Host row lists are staged (rows_mem).
+static int build_sets(iht_dataset *ds, BatchWork *w, const std::vector<SetKey> &sets, int rows_mem,
+                      std::vector<const int32_t *> &rows_dev)
+{
+    cudaStream_t s = ds->ctx->stream;
+    const int nsets = (int)sets.size();
+    rows_dev.assign(nsets, nullptr);
+    IHT_CUDA(cudaMemsetAsync(w->set_err, 0, sizeof(int32_t) * nsets, s));
+    int64_t off = 0;
+    for (int q = 0; q < nsets; ++q) {
+        const SetKey &k = sets[q];
+        if (k.rows) {
+            if (rows_mem == IHT_HOST) {
+                if (k.n_rows > 0)
+                    IHT_CUDA(cudaMemcpyAsync(w->rows_dev + off, k.rows, sizeof(int32_t) * k.n_rows,
+                                             cudaMemcpyHostToDevice, s));
+                rows_dev[q] = w->rows_dev + off;
+                off += k.n_rows;
+            } else {
+                rows_dev[q] = k.rows;
+            }
+        }
+        int rc = setup_rowset(ds, rows_dev[q], k.n_rows, batch_rowset(ds, w, q), w->set_err + q);
+        if (rc) return rc;
+        if ((rc = launch_counts_rowset(ds, k.n_rows, batch_rowset(ds, w, q)))) return rc;
+    }
+    IHT_CUDA(cudaMemcpyAsync(w->set_err_host, w->set_err, sizeof(int32_t) * nsets,
+                             cudaMemcpyDeviceToHost, s));
+    IHT_CUDA(cudaStreamSynchronize(s));
+    for (int q = 0; q < nsets; ++q)
+        if (w->set_err_host[q] & 2) return IHT_EINVAL;
+    return IHT_OK;
+}
+
+// Gradient of the listed solves (impl 0/2: one multi-column pass; 1: one
+// CUDA-core pass per solve).
+static int batch_grad(iht_dataset *ds, BatchWork *w, const std::vector<int> &act,
+                      const std::vector<int> &set_of, int impl)
+{
+    cudaStream_t s = ds->ctx->stream;
+    const size_t np = (size_t)ds->n_pad, p = (size_t)ds->p;
+    if (act.empty()) return IHT_OK;
+    if (impl == 1) {
+        for (int c : act) {
+            const RowSet rs = batch_rowset(ds, w, set_of[c]);
+            int rc = launch_grad_simt_stats(ds, w->r32 + c * np, rs.u32, rs.v32, w->g + c * p);
+            if (rc) return rc;
+        }
+        return IHT_OK;
+    }
+    for (size_t a = 0; a < act.size(); ++a) {
+        const int c = act[a];
+        const RowSet rs = batch_rowset(ds, w, set_of[c]);
+        MrCol &C = w->cols_host[a];
+        C.r32 = w->r32 + c * np;
+        C.u32 = rs.u32;
+        C.v32 = rs.v32;
+        C.g = w->g + c * p;
+        C.scale = 0.0f;
+        C.R = 0.0f;
+    }
+    IHT_CUDA(cudaMemcpyAsync(w->cols, w->cols_host, sizeof(MrCol) * act.size(),
+                             cudaMemcpyHostToDevice, s));
+    return launch_grad_mrhs(ds, w->cols, (int)act.size());
+}
+
+}  // namespace iht
+
+using namespace iht;
+
+extern "C" {
+
+int iht_fit_batch(iht_dataset *ds, int32_t b, const iht_solve_desc *solves,
+                  const iht_options *opt_in, double *betas, int32_t *supports, iht_result *infos)
+{
+    iht_options opt;
+    if (opt_in)
+        opt = *opt_in;
+    else
+        iht_default_options(&opt);
+    if (!ds || b < 1 || !solves || !supports) return IHT_EINVAL;
+    if ((opt.in_mem != IHT_HOST && opt.in_mem != IHT_DEVICE) ||
+        (opt.out_mem != IHT_HOST && opt.out_mem != IHT_DEVICE) || opt.max_iter < 0 ||
+        opt.max_backtrack < 0 || !(opt.kappa > 1.0) || !(opt.c >= 0.0 && opt.c < 1.0) ||
+        !(opt.tol >= 0.0) || opt.grad_impl < 0 || opt.grad_impl > 2)
+        return IHT_EINVAL;
+    int kmax = 0;
+    int64_t ytot = 0;
+    for (int c = 0; c < b; ++c) {
+        const iht_solve_desc &d = solves[c];
+        const int64_t nr = d.rows ? d.n_rows : ds->n;
+        if (!d.y || nr < 2 || nr > ds->n || d.k < 1 || d.k > ds->p || d.k > kMaxK) return IHT_EINVAL;
+        kmax = std::max(kmax, (int)d.k);
+        ytot += nr;
+    }
+    if (opt.grad_impl != 1 && !grad_mrhs_supported(ds)) return IHT_EINVAL;
+    DeviceGuard g(ds->ctx->device);
+    if (!g.ok) return IHT_ECUDA;
+    int rc = ensure_workspace(ds, kmax);
+    if (rc) return rc;
+    cudaStream_t s = ds->ctx->stream;
+    std::vector<const int32_t *> rows(b);
+    std::vector<int64_t> nrows(b);
+    for (int c = 0; c < b; ++c) {
+        rows[c] = solves[c].rows;
+        nrows[c] = solves[c].n_rows;
+    }
+    std::vector<SetKey> sets;
+    std::vector<int> set_of;
+    dedupe_sets(b, rows.data(), nrows.data(), ds->n, sets, set_of);
+    int64_t rtot = 0;
+    for (const SetKey &k : sets)
+        if (k.rows) rtot += k.n_rows;
+    if ((rc = ensure_batchwork(ds, b, kmax, (int)sets.size(), opt.in_mem == IHT_HOST ? rtot : 0,
+                               opt.in_mem == IHT_HOST ? ytot : 0)))
+        return rc;
+    BatchWork *w = ds->ws->bw;
+    std::vector<const int32_t *> set_rows;
+    if ((rc = build_sets(ds, w, sets, opt.in_mem, set_rows))) return rc;
+
+    const size_t np = (size_t)ds->n_pad, p = (size_t)ds->p, K = (size_t)w->kcap;
+    const size_t nch = (size_t)sel_nchunks(ds->p);
+    const int npart = zmul_blocks(ds);
+
+    // phenotypes, finite check, per-solve state
+    IHT_CUDA(cudaMemsetAsync(w->sc, 0, sizeof(Scalars) * b, s));
+    int64_t yoff = 0;
+    for (int c = 0; c < b; ++c) {
+        const iht_solve_desc &d = solves[c];
+        const int64_t nr = d.rows ? d.n_rows : ds->n;
+        const double *ydev = d.y;
+        if (opt.in_mem == IHT_HOST) {
+            IHT_CUDA(cudaMemcpyAsync(w->ybuf + yoff, d.y, sizeof(double) * nr, cudaMemcpyHostToDevice, s));
+            ydev = w->ybuf + yoff;
+            yoff += nr;
+        }
+        if ((rc = check_finite_y_sc(ds, nr, ydev, w->sc + c))) return rc;
+        if ((rc = scatter_rows_f64(ds, set_rows[set_of[c]], nr, ydev, w->y64 + c * np))) return rc;
+    }
+    IHT_CUDA(cudaMemcpyAsync(w->sc_host, w->sc, sizeof(Scalars) * b, cudaMemcpyDeviceToHost, s));
+    IHT_CUDA(cudaStreamSynchronize(s));
+    for (int c = 0; c < b; ++c) {
+        const int32_t err = w->sc_host[c].err;
+        Scalars h{};
+        h.c = opt.c;
+        h.kappa = opt.kappa;
+        h.tol = opt.tol;
+        h.max_iter = opt.max_iter;
+        h.max_backtrack = opt.max_backtrack;
+        h.k = solves[c].k;
+        h.n_rows = (int32_t)(solves[c].rows ? solves[c].n_rows : ds->n);
+        h.status = (err & 1) ? IHT_ENUMERIC : IHT_ENOTCONV;
+        h.done = (err & 1) || opt.max_iter <= 0 ? 1 : 0;
+        h.err = err;
+        w->sc_host[c] = h;
+        const RowSet rs = batch_rowset(ds, w, set_of[c]);
+        BSolve &B = w->bs_host[c];
+        B.sc = w->sc + c;
+        B.used = rs.used;
+        B.u64 = rs.u64;
+        B.v64 = rs.v64;
+        B.y64 = w->y64 + c * np;
+        B.r64 = w->r64 + c * np;
+        B.rc64 = w->rc64 + c * np;
+        B.zv = w->zv + c * np;
+        B.r32 = w->r32 + c * np;
+        B.g = w->g + c * p;
+        B.S = w->S + c * K;
+        B.Sp = w->Sp + c * K;
+        B.cand = w->cand + c * 2 * K;
+        B.bS = w->bS + c * K;
+        B.bSp = w->bSp + c * K;
+        B.coef = w->coef + c * K;
+        B.partials = w->partials + (size_t)c * 3 * kPartials;
+        B.zpart = w->zpart + (size_t)c * kgroups(w->kcap) * np;
+        B.k = solves[c].k;
+        B.K = (int32_t)std::min<int64_t>(2 * (int64_t)solves[c].k, ds->p);
+        for (int t = 0; t < 2; ++t) {            // t = 0: S^0 = top-k; t = 1: candidates
+            SelJob &J = w->jobs_host[t * b + c];
+            J.keys = B.g;
+            J.out = t == 0 ? B.S : B.cand;
+            J.st = w->st + t * b + c;
+            J.hist = w->hist + (size_t)(t * b + c) * kSelBins;
+            J.chunk_eq = w->chunk_eq + (size_t)(t * b + c) * nch;
+            J.done = &w->sc[c].done;
+            J.K = (uint32_t)(t == 0 ? B.k : B.K);
+        }
+    }
+    IHT_CUDA(cudaMemcpyAsync(w->sc, w->sc_host, sizeof(Scalars) * b, cudaMemcpyHostToDevice, s));
+    IHT_CUDA(cudaMemcpyAsync(w->bs, w->bs_host, sizeof(BSolve) * b, cudaMemcpyHostToDevice, s));
+    IHT_CUDA(cudaMemcpyAsync(w->jobs, w->jobs_host, sizeof(SelJob) * 2 * b, cudaMemcpyHostToDevice, s));
+
+    const bool prof = opt.profile != 0;
+    if (prof && !w->ev[0])
+        for (int e = 0; e < 2 * kProfEvents; ++e) IHT_CUDA(cudaEventCreate(&w->ev[e]));
+    int nprof = 0;
+    auto grad = [&](const std::vector<int> &act) -> int {
+        const bool rec = prof && nprof < kProfEvents;
+        if (rec) IHT_CUDA(cudaEventRecord(w->ev[2 * nprof], s));
+        int r = batch_grad(ds, w, act, set_of, opt.grad_impl);
+        if (r) return r;
+        if (rec) {
+            IHT_CUDA(cudaEventRecord(w->ev[2 * nprof + 1], s));
+            ++nprof;
+        }
+        return IHT_OK;
+    };
+
+    std::vector<int> act;
+    auto active = [&]() {
+        act.clear();
+        for (int c = 0; c < b; ++c)
+            if (!w->sc_host[c].done) act.push_back(c);
+    };
+    // beta = 0: r = y, objective, centred residual, g^0, S^0 = top-k |g^0|
+    if ((rc = launch_zmul_batch(ds, w->bs, b, kmax, kZmulInit))) return rc;
+    if ((rc = launch_init_objective_batch(ds, w->bs, b))) return rc;
+    if ((rc = launch_center_batch(ds, w->bs, b, true))) return rc;
+    active();
+    if ((rc = grad(act))) return rc;
+    if ((rc = select_topk_batch(ds->ctx, w->jobs, b, ds->p))) return rc;
+    IHT_CUDA(cudaMemsetAsync(w->bS, 0, sizeof(double) * b * K, s));
+
+    for (int it = 0; it < opt.max_iter && !act.empty(); ++it) {
+        if (it > 0 && (rc = grad(act))) return rc;
+        if ((rc = select_topk_batch(ds->ctx, w->jobs + b, b, ds->p))) return rc;
+        if ((rc = launch_gather_gS_batch(ds, w->bs, b))) return rc;
+        if ((rc = launch_zmul_batch(ds, w->bs, b, kmax, kZmulStep))) return rc;
+        for (int attempt = 0;; ++attempt) {
+            if ((rc = launch_merge_batch(ds, w->bs, b, attempt == 0))) return rc;
+            if ((rc = launch_zmul_batch(ds, w->bs, b, kmax, kZmulResidual))) return rc;
+            if ((rc = launch_decide_batch(ds, w->bs, b))) return rc;
+            if ((rc = launch_center_batch(ds, w->bs, b, false))) return rc;
+            IHT_CUDA(cudaMemcpyAsync(w->sc_host, w->sc, sizeof(Scalars) * b, cudaMemcpyDeviceToHost, s));
+            IHT_CUDA(cudaStreamSynchronize(s));
+            bool again = false;
+            for (int c : act) again |= !w->sc_host[c].done && w->sc_host[c].live && w->sc_host[c].retry;
+            if (!again) break;
+        }
+        active();
+    }
+    int timed_out = 0;
+    if (opt.grad_impl != 1 && (rc = grad_mrhs_status(ds, &timed_out))) return rc;
+    if (timed_out) return IHT_ETIMEOUT;
+    double grad_ms = 0.0;
+    for (int e = 0; prof && e < nprof; ++e) {
+        float ms = 0.0f;
+        IHT_CUDA(cudaEventElapsedTime(&ms, w->ev[2 * e], w->ev[2 * e + 1]));
+        grad_ms += ms;
+    }
+
+    // outputs
+    size_t koff = 0;
+    if (opt.out_mem == IHT_DEVICE) {
+        if (betas) {
+            IHT_CUDA(cudaMemsetAsync(betas, 0, sizeof(double) * b * p, s));
+            if ((rc = launch_scatter_beta_batch(ds, w->bs, b, kmax, betas))) return rc;
+        }
+        for (int c = 0; c < b; ++c) {
+            IHT_CUDA(cudaMemcpyAsync(supports + koff, w->S + c * K, sizeof(int32_t) * solves[c].k,
+                                     cudaMemcpyDeviceToDevice, s));
+            koff += solves[c].k;
+        }
+        IHT_CUDA(cudaStreamSynchronize(s));
+    } else {
+        std::vector<double> bS((size_t)b * K);
+        for (int c = 0; c < b; ++c) {
+            IHT_CUDA(cudaMemcpyAsync(supports + koff, w->S + c * K, sizeof(int32_t) * solves[c].k,
+                                     cudaMemcpyDeviceToHost, s));
+            koff += solves[c].k;
+        }
+        IHT_CUDA(cudaMemcpyAsync(bS.data(), w->bS, sizeof(double) * b * K, cudaMemcpyDeviceToHost, s));
+        IHT_CUDA(cudaStreamSynchronize(s));
+        if (betas) {
+            memset(betas, 0, sizeof(double) * b * p);
+            koff = 0;
+            for (int c = 0; c < b; ++c) {
+                for (int t = 0; t < solves[c].k; ++t)
+                    betas[(size_t)c * p + supports[koff + t]] = bS[(size_t)c * K + t];
+                koff += solves[c].k;
+            }
+        }
+    }
+    if (infos) {
+        for (int c = 0; c < b; ++c) {
+            const Scalars &h = w->sc_host[c];
+            iht_result &r = infos[c];
+            r.iterations = h.iter;
+            r.status = h.status;
+            r.backtracks = h.bt_total;
+            r.reserved = 0;
+            r.objective = h.f;
+            r.mu = h.mu;
+            r.grad_ms = prof ? grad_ms : 0.0;
+            r.grad_launches = prof ? nprof : 0;
+            r.reserved2 = 0;
+        }
+    }
+    return IHT_OK;
+}
+
+int iht_gradient_batch(iht_dataset *ds, int32_t b, const int32_t *const *rows_list,
+                       const int64_t *n_rows, const float *R, float *G_out, int impl)
+{
+    if (!ds || b < 1 || !rows_list || !n_rows || !R || !G_out || impl < 0 || impl > 2)
+        return IHT_EINVAL;
+    for (int c = 0; c < b; ++c) {
+        const int64_t nr = rows_list[c] ? n_rows[c] : ds->n;
+        if (nr < 1 || nr > ds->n) return IHT_EINVAL;
+    }
+    if (impl != 1 && !grad_mrhs_supported(ds)) return IHT_EINVAL;
+    DeviceGuard g(ds->ctx->device);
+    if (!g.ok) return IHT_ECUDA;
+    int rc = ensure_workspace(ds, 0);
+    if (rc) return rc;
+    std::vector<SetKey> sets;
+    std::vector<int> set_of;
+    dedupe_sets(b, rows_list, n_rows, ds->n, sets, set_of);
+    if ((rc = ensure_batchwork(ds, b, 1, (int)sets.size(), 0, 0))) return rc;
+    BatchWork *w = ds->ws->bw;
+    std::vector<const int32_t *> set_rows;
+    if ((rc = build_sets(ds, w, sets, IHT_DEVICE, set_rows))) return rc;
+    const size_t np = (size_t)ds->n_pad, p = (size_t)ds->p;
+    std::vector<int> act(b);
+    for (int c = 0; c < b; ++c) {
+        act[c] = c;
+        if ((rc = scatter_rows_f32(ds, set_rows[set_of[c]], sets[set_of[c]].n_rows,
+                                   R + (size_t)c * ds->n, w->r32 + c * np)))
+            return rc;
+    }
+    if ((rc = batch_grad(ds, w, act, set_of, impl))) return rc;
+    cudaStream_t s = ds->ctx->stream;
+    IHT_CUDA(cudaMemcpyAsync(G_out, w->g, sizeof(float) * b * p, cudaMemcpyDeviceToDevice, s));
+    IHT_CUDA(cudaStreamSynchronize(s));
+    int timed_out = 0;
+    if (impl != 1 && (rc = grad_mrhs_status(ds, &timed_out))) return rc;
+    return timed_out ? IHT_ETIMEOUT : IHT_OK;
+}
+
+}  // extern "C"

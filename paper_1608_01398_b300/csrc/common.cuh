@@ -49,6 +49,22 @@ struct Scalars {                       // device-resident state of one solve
     int32_t max_iter, max_backtrack;
     int32_t k, n_rows;
     int32_t err;                       // bit 0: non-finite input, bit 1: bad rows
+    int32_t live;                      // batched solves: takes part in the current attempt
+};
+
+// Device descriptor of one solve of a batch (all pointers device memory).
+struct BSolve {
+    Scalars *sc;
+    const int32_t *used;               // row set of the solve and its statistics
+    const double *u64, *v64;
+    double *y64, *r64, *rc64, *zv;     // n_pad each
+    float *r32;                        // n_pad: centred residual read by the gradient
+    float *g;                          // p: gradient
+    int32_t *S, *Sp, *cand;            // k, k, K
+    double *bS, *bSp, *coef;           // k, k, k
+    double *partials;                  // 3 * zmul blocks
+    double *zpart;                     // ceil(k / 4) * n_pad
+    int32_t k, K;
 };
 
 struct SelState {                      // radix select progress
@@ -58,6 +74,24 @@ struct SelState {                      // radix select progress
 
 // Host-side handles -------------------------------------------------------
 struct Workspace;
+struct BatchWork;
+void free_batchwork(BatchWork *w);
+
+// Makes a device current for the scope of an API call.
+struct DeviceGuard {
+    int prev = -1;
+    bool ok = true;
+    explicit DeviceGuard(int dev)
+    {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        if (prev != dev) ok = cudaSetDevice(dev) == cudaSuccess;
+    }
+    ~DeviceGuard()
+    {
+        int cur = -1;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    }
+};
 
 struct SelWork {                       // radix-select scratch, one per context
     uint32_t *hist = nullptr;          // kSelBins
@@ -123,6 +157,7 @@ struct Workspace {
     cudaEvent_t prof_ev[2 * 256] = {};
     int nprof = 0;
     double prof_ms = 0.0;
+    BatchWork *bw = nullptr;               // batched solves (batch.cu)
 };
 constexpr int kProfEvents = 256;
 
@@ -141,8 +176,21 @@ void note_launch(int n = 1);           // kernel launches issued (iht_kernel_lau
 int ensure_workspace(iht_dataset *ds, int kcap);
 void free_workspace(Workspace *ws);
 
+// Device arrays of one row set and its per-SNP statistics.
+struct RowSet {
+    int32_t *used = nullptr;       // int32[n_pad], 1 on the set's rows
+    uint32_t *rowmask = nullptr;   // uint32[stride/4], 2-bit lanes 11 on the set's rows
+    int32_t *counts = nullptr;     // int32[4p] or null
+    double *u64 = nullptr, *v64 = nullptr;
+    float *u32 = nullptr, *v32 = nullptr;
+};
+
 // kernels launched from the host side (stream-ordered) ---------------------
 // geno.cu
+RowSet workspace_rowset(iht_dataset *ds);
+int setup_rowset(iht_dataset *ds, const int32_t *rows_dev, int64_t n_rows, const RowSet &rs,
+                 int32_t *err);
+int launch_counts_rowset(iht_dataset *ds, int64_t n_rows, const RowSet &rs);
 int launch_fix_padding(iht_dataset *ds);
 int build_missing_lists(iht_dataset *ds);
 int launch_missing_sums(iht_dataset *ds, const float *r32, float *M, const int32_t *done);
@@ -161,7 +209,31 @@ int launch_grad_tc_main(iht_dataset *ds, const float *r32, float *g, const int32
 int grad_tc_status(iht_dataset *ds, int *timed_out);
 // impl: 0 default (tensor cores when supported), 1 CUDA cores, 2 tensor cores
 int launch_grad_impl(iht_dataset *ds, int impl, const float *r32, float *g, const int32_t *done);
+int launch_grad_simt_stats(iht_dataset *ds, const float *r32, const float *u32, const float *v32,
+                           float *g);
+// grad_mrhs.cu: one residual column of a multi-column gradient pass (device)
+struct MrCol {
+    const float *r32;              // n_pad residual, zero off the column's rows
+    const float *u32, *v32;        // statistics of the column's row set
+    float *g;                      // p outputs
+    float scale, R;                // set by the pass
+};
+int mrhs_max_cols();
+bool grad_mrhs_supported(const iht_dataset *ds);
+int launch_grad_mrhs(iht_dataset *ds, MrCol *cols_dev, int ncols);
+int grad_mrhs_status(iht_dataset *ds, int *timed_out);
 // select.cu
+struct SelJob {                        // one problem of a batched top-K
+    const float *keys;
+    int32_t *out;
+    SelState *st;
+    uint32_t *hist;                    // kSelBins
+    uint32_t *chunk_eq;                // sel_nchunks(p)
+    const int32_t *done;               // skip the problem when *done (may be null)
+    uint32_t K;
+};
+int64_t sel_nchunks(int64_t p);
+int select_topk_batch(iht_ctx *ctx, const SelJob *jobs, int nb, int64_t p);
 int ensure_selwork(iht_ctx *ctx, int64_t p);
 int select_topk(iht_ctx *ctx, const float *key_src, int64_t p, int32_t K, int32_t *out_idx,
                 const int32_t *done);
@@ -173,9 +245,19 @@ int launch_zmul(iht_dataset *ds, const int32_t *cols, int32_t m, const double *c
 int gather_rows_f64(iht_dataset *ds, const int32_t *rows_dev, int64_t n_rows, const double *src,
                     double *dst);
 int check_finite_y(iht_dataset *ds, int64_t n_rows, const double *y_dev);
+int check_finite_y_sc(iht_dataset *ds, int64_t n_rows, const double *y_dev, Scalars *sc);
 int run_solve_host(iht_dataset *ds, int k, const iht_options *opt, int n_rows, iht_trace *trace,
                    int max_iter);
 int write_beta_device(iht_dataset *ds, int k, double *beta_out);
+// batched tails (blockIdx selects the solve; finished solves return at once)
+enum ZmulWhich { kZmulInit = 0, kZmulStep = 1, kZmulResidual = 2 };
+int launch_gather_gS_batch(iht_dataset *ds, const BSolve *bs, int nb);
+int launch_zmul_batch(iht_dataset *ds, const BSolve *bs, int nb, int kmax, ZmulWhich which);
+int launch_init_objective_batch(iht_dataset *ds, const BSolve *bs, int nb);
+int launch_center_batch(iht_dataset *ds, const BSolve *bs, int nb, bool init);
+int launch_merge_batch(iht_dataset *ds, const BSolve *bs, int nb, int first);
+int launch_decide_batch(iht_dataset *ds, const BSolve *bs, int nb);
+int launch_scatter_beta_batch(iht_dataset *ds, const BSolve *bs, int nb, int kmax, double *betas);
 
 // device helpers ------------------------------------------------------------
 __device__ __forceinline__ float warp_sum(float x)

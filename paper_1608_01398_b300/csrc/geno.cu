@@ -69,28 +69,46 @@ __global__ void k_rowmask(const int32_t *__restrict__ used, uint32_t *__restrict
     rowmask[c] = m;
 }
 
-// Marks the rows of a solve (rows_dev == nullptr: all n) and builds the
-// 2-bit row mask.  Bad or duplicate indices set bit 1 of sc->err.
-int setup_rows(iht_dataset *ds, const int32_t *rows_dev, int64_t n_rows)
+// Marks the rows of a row set (rows_dev == nullptr: all n) and builds its
+// 2-bit row mask.  Bad or duplicate indices set bit 1 of *err.
+int setup_rowset(iht_dataset *ds, const int32_t *rows_dev, int64_t n_rows, const RowSet &rs,
+                 int32_t *err)
 {
-    Workspace *ws = ds->ws;
     cudaStream_t s = ds->ctx->stream;
     if (rows_dev) {
-        IHT_CUDA(cudaMemsetAsync(ws->used, 0, sizeof(int32_t) * ds->n_pad, s));
+        IHT_CUDA(cudaMemsetAsync(rs.used, 0, sizeof(int32_t) * ds->n_pad, s));
         if (n_rows > 0) {
-            k_mark_rows<<<ceil_div(n_rows, 256), 256, 0, s>>>(rows_dev, n_rows, ds->n, ws->used,
-                                                              &ws->sc->err);
+            k_mark_rows<<<ceil_div(n_rows, 256), 256, 0, s>>>(rows_dev, n_rows, ds->n, rs.used, err);
             note_launch();
         }
     } else {
-        k_mark_all<<<ceil_div(ds->n_pad, 256), 256, 0, s>>>(ds->n, ds->n_pad, ws->used);
+        k_mark_all<<<ceil_div(ds->n_pad, 256), 256, 0, s>>>(ds->n, ds->n_pad, rs.used);
         note_launch();
     }
     const int64_t nwords = ds->stride / 4;
-    k_rowmask<<<ceil_div(nwords, 256), 256, 0, s>>>(ws->used, ws->rowmask, nwords);
+    k_rowmask<<<ceil_div(nwords, 256), 256, 0, s>>>(rs.used, rs.rowmask, nwords);
     note_launch();
     IHT_CUDA(cudaGetLastError());
     return IHT_OK;
+}
+
+RowSet workspace_rowset(iht_dataset *ds)
+{
+    Workspace *ws = ds->ws;
+    RowSet rs;
+    rs.used = ws->used;
+    rs.rowmask = ws->rowmask;
+    rs.counts = ws->counts;
+    rs.u64 = ws->u64;
+    rs.v64 = ws->v64;
+    rs.u32 = ws->u32;
+    rs.v32 = ws->v32;
+    return rs;
+}
+
+int setup_rows(iht_dataset *ds, const int32_t *rows_dev, int64_t n_rows)
+{
+    return setup_rowset(ds, rows_dev, n_rows, workspace_rowset(ds), &ds->ws->sc->err);
 }
 
 // One warp per SNP: masked popcounts, then the FP64 statistics.
@@ -153,16 +171,19 @@ __global__ void __launch_bounds__(256) k_counts(const uint8_t *__restrict__ G, i
     }
 }
 
-int launch_counts(iht_dataset *ds, int64_t n_rows)
+int launch_counts_rowset(iht_dataset *ds, int64_t n_rows, const RowSet &rs)
 {
-    Workspace *ws = ds->ws;
     const int blocks = (int)std::min<int64_t>(ceil_div(ds->p, 8), (int64_t)ds->ctx->num_sms * 16);
-    k_counts<<<blocks, 256, 0, ds->ctx->stream>>>(ds->G, ds->p, ds->stride, ds->rowb, ws->rowmask,
-                                                  n_rows,
-                                                  ws->counts, ws->u64, ws->v64, ws->u32, ws->v32);
+    k_counts<<<blocks, 256, 0, ds->ctx->stream>>>(ds->G, ds->p, ds->stride, ds->rowb, rs.rowmask,
+                                                  n_rows, rs.counts, rs.u64, rs.v64, rs.u32, rs.v32);
     note_launch();
     IHT_CUDA(cudaGetLastError());
     return IHT_OK;
+}
+
+int launch_counts(iht_dataset *ds, int64_t n_rows)
+{
+    return launch_counts_rowset(ds, n_rows, workspace_rowset(ds));
 }
 
 template <typename T>

@@ -1,0 +1,707 @@
+// a7: multi-right-hand-side standardised gradient (tcgen05, sm_103a).
+//
+// b solves on one genotype matrix (q-fold cross-validation over a path of
+// model sizes, Sec. 2.4; several phenotypes) each need g_c = Z_c^T r_c per
+// iteration, with Z_c standardised over the solve's own rows.  Per column c
+// and SNP j
+//     g_cj = v_cj (S1_cj - u_cj (R_c - M_cj)),
+// S1_cj = sum_i x_ij r_ci over observed calls, M_cj = sum of r_ci over the
+// missing calls of SNP j, R_c = sum_i r_ci (r_c is zero off the solve's rows,
+// so one dense product serves every row set).  The dense part S1 = X0^T R is a
+// GEMM of the 2-bit matrix against the b residual columns: one pass over the
+// packed genotypes serves all b solves.
+//
+// Operands (kind::f16, both F16, FP32 accumulate, M = 128 SNPs, K = 16):
+//   A: the dosage map in tensor memory, decoded by CUDA-core warps from the
+//      TMA-staged 2-bit codes: the two-bit field f = (c1, c1 & c0) of a code
+//      (00 for hom-ref and missing, 10 het, 11 hom-alt) placed in the F16
+//      exponent gives 0, 2^-13, 2^-12 = 2^-13 x, two instructions per pair of
+//      samples.  32-bit column j of a K-step holds samples j (low half) and
+//      j + 8 (high half) of the step's 16.
+//   B: each residual column as two F16 limbs, hi = f16(r / s), lo = f16(r / s
+//      - hi), s a power of two with max|r| / s < 2^15 (22 significant bits),
+//      stored per K-step in the canonical K-major layout (8-row x 16-byte core
+//      matrices) in the same permuted sample order, N = 2 b rounded up to 16.
+//   So S1 = 2^13 s (acc_hi + acc_lo).
+//
+// One persistent CTA per SM handles two 128-SNP tiles at a time, so every B
+// chunk it streams from L2 feeds two MMAs.  Warps 0-7 decode (warps 4t..4t+3
+// own tile t, thread = SNP row = tensor-memory lane) and run the epilogue,
+// warp 8 issues the MMAs, warp 9 streams genotype tiles (TMA 2D, 64-byte
+// swizzle), warp 10 streams B chunks (bulk copies).  Tensor memory (512
+// columns): accumulator of tile t at column 256 t, its A buffers right after
+// it.  The epilogue writes S1; a second pass (k_miss_finalize) adds the
+// missing-call sums from the per-SNP lists and forms g, so this kernel's
+// epilogue only stores.  Every wait is bounded and reports a timeout through
+// an error word instead of hanging.
+#include <cuda.h>
+#include <cuda_fp16.h>
+
+#include "common.cuh"
+
+namespace iht {
+
+constexpr int kMrTiles = 2;                 // 128-SNP tiles per CTA tile
+constexpr int kMrDecoders = 128 * kMrTiles; // decoder / epilogue threads
+constexpr int kMrMmaWarp = kMrDecoders / 32;
+constexpr int kMrGWarp = kMrMmaWarp + 1;
+constexpr int kMrBWarp = kMrMmaWarp + 2;
+constexpr int kMrThreads = kMrDecoders + 96;
+constexpr int kMrStepSamples = 16;          // K of one MMA
+constexpr int kMrGStageBytes = 64;          // packed bytes per row per TMA stage (256 samples)
+constexpr int kMrGTile = 128 * kMrGStageBytes;
+constexpr int kMrGStages = 4;
+constexpr int kMrChunkSteps = 4;            // K-steps per B chunk
+constexpr int kMrMaxBStages = 6;
+constexpr int kMrMaxBufs = 8;               // A buffers of 2 K-steps
+constexpr int kMrMaxN = 224;                // accumulator columns per tile
+constexpr int kMrMaxCols = kMrMaxN / 2;     // residual columns per pass
+constexpr size_t kMrSmemMax = 220 * 1024;
+constexpr uint32_t kMrSpin = 1u << 26;
+
+__device__ __forceinline__ uint32_t mr_smem(const void *p)
+{
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+// ---------------------------------------------------------------------------
+// Residual columns -> F16 limb image.  One block per column.  Also the
+// column's scale and sum R (FP64, fixed order, as the single-column pass).
+
+__device__ __forceinline__ int64_t mr_b_offset(int64_t i, int q, int N)
+{
+    const int64_t s = i >> 4;
+    const int ii = (int)(i & 15);
+    const int kp = 2 * (ii & 7) + (ii >> 3);               // K position within the step
+    return s * (int64_t)N * 32 + (q >> 3) * 256 + (kp >> 3) * 128 + (q & 7) * 16 + (kp & 7) * 2;
+}
+
+__global__ void __launch_bounds__(1024) k_mr_limbs(MrCol *cols, int64_t nsamp, int N,
+                                                   uint8_t *__restrict__ bimg)
+{
+    __shared__ float smax[32];
+    __shared__ double red[32];
+    MrCol &C = cols[blockIdx.x];
+    const float *__restrict__ r = C.r32;
+    float m = 0.0f;
+    for (int64_t i = threadIdx.x; i < nsamp; i += blockDim.x) m = fmaxf(m, fabsf(r[i]));
+    m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, 16));
+    m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, 8));
+    m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, 4));
+    m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, 2));
+    m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, 1));
+    if ((threadIdx.x & 31) == 0) smax[threadIdx.x >> 5] = m;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        m = threadIdx.x < (blockDim.x >> 5) ? smax[threadIdx.x] : 0.0f;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+        if (threadIdx.x == 0) smax[0] = m;
+    }
+    __syncthreads();
+    m = smax[0];
+    float s = 1.0f;
+    if (m > 0.0f) {
+        int e;
+        frexpf(m, &e);                   // m < 2^e
+        s = ldexpf(1.0f, e - 15);        // m / s < 2^15
+    }
+    const float inv = 1.0f / s;          // exact: s is a power of two
+    const int qhi = 2 * blockIdx.x;
+    double acc = 0.0;
+    for (int64_t i = threadIdx.x; i < nsamp; i += blockDim.x) {
+        const float v = r[i];
+        acc += (double)v;
+        const float x = v * inv;
+        const __half hi = __float2half_rn(x);
+        const __half lo = __float2half_rn(x - __half2float(hi));
+        *reinterpret_cast<__half *>(bimg + mr_b_offset(i, qhi, N)) = hi;
+        *reinterpret_cast<__half *>(bimg + mr_b_offset(i, qhi + 1, N)) = lo;
+    }
+    acc = block_sum(acc, red);
+    if (threadIdx.x == 0) {
+        C.scale = s * 8192.0f;           // A carries 2^-13 x
+        C.R = (float)acc;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// mbarrier / TMA / tcgen05 helpers (all waits bounded)
+
+__device__ __forceinline__ void mr_bar_init(uint64_t *bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(mr_smem(bar)), "r"(count));
+}
+
+__device__ __forceinline__ bool mr_wait(uint64_t *bar, uint32_t parity)
+{
+    const uint32_t a = mr_smem(bar);
+    for (uint32_t it = 0; it < kMrSpin; ++it) {
+        uint32_t ok;
+        asm volatile(
+            "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+            "selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(ok)
+            : "r"(a), "r"(parity)
+            : "memory");
+        if (ok) return true;
+    }
+    return false;
+}
+
+__device__ __forceinline__ void mr_arrive(uint64_t *bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(mr_smem(bar)) : "memory");
+}
+
+__device__ __forceinline__ void mr_expect_tx(uint64_t *bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mr_smem(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ void mr_tma_2d(void *dst, const CUtensorMap *map, int x, int y,
+                                          uint64_t *bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, "
+        "%3}], [%4];" ::"r"(mr_smem(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(mr_smem(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ void mr_bulk(void *dst, const void *src, uint32_t bytes, uint64_t *bar)
+{
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            mr_smem(dst)),
+        "l"(src), "r"(bytes), "r"(mr_smem(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ void mr_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void mr_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+__device__ __forceinline__ void mr_st16(uint32_t taddr, const uint32_t (&v)[16])
+{
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,"
+        "%13,%14,%15,%16};" ::"r"(taddr),
+        "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7]),
+        "r"(v[8]), "r"(v[9]), "r"(v[10]), "r"(v[11]), "r"(v[12]), "r"(v[13]), "r"(v[14]), "r"(v[15])
+        : "memory");
+}
+
+__device__ __forceinline__ void mr_ld16(uint32_t taddr, uint32_t (&v)[16])
+{
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,"
+        "%15}, [%16];"
+        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
+          "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]),
+          "=r"(v[14]), "=r"(v[15])
+        : "r"(taddr)
+        : "memory");
+}
+
+__device__ __forceinline__ void mr_mma(uint32_t d_tmem, uint32_t a_tmem, uint64_t b_desc,
+                                       uint32_t idesc, uint32_t accumulate)
+{
+    asm volatile(
+        "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n}\n" ::"r"(d_tmem),
+        "r"(a_tmem), "l"(b_desc), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+
+__device__ __forceinline__ void mr_commit(uint64_t *bar)
+{
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                     mr_smem(bar))
+                 : "memory");
+}
+
+// K-major, no swizzle: LBO 128 bytes (the two K halves), SBO 256 bytes (8-row groups).
+__device__ __forceinline__ uint64_t mr_b_desc(uint32_t saddr)
+{
+    return (uint64_t)((saddr >> 4) & 0x3FFFu) | ((uint64_t)(128u >> 4) << 16) |
+           ((uint64_t)(256u >> 4) << 32) | (1ull << 46);
+}
+
+// F16 dosage map of one word of 16 codes: output j = samples j and j + 8.
+__device__ __forceinline__ void mr_decode(uint32_t w, uint32_t *a)
+{
+    const uint32_t f = w & ((w >> 1) | 0xAAAAAAAAu);
+    const uint32_t m = 0x0C000C00u;
+    a[0] = (f << 10) & m;
+    a[1] = (f << 8) & m;
+    a[2] = (f << 6) & m;
+    a[3] = (f << 4) & m;
+    a[4] = (f << 2) & m;
+    a[5] = f & m;
+    a[6] = (f >> 2) & m;
+    a[7] = (f >> 4) & m;
+}
+
+struct MrPipe {
+    uint64_t gfull[kMrGStages], gempty[kMrGStages];
+    uint64_t bfull[kMrMaxBStages], bempty[kMrMaxBStages];
+    uint64_t afull[kMrMaxBufs], aempty[kMrMaxBufs];
+    uint64_t accfull, accempty;
+};
+
+__global__ void __launch_bounds__(kMrThreads, 1) k_grad_mrhs(
+    const __grid_constant__ CUtensorMap gmap, int64_t p, int ksteps, int N, int ncols, int nbufs,
+    int nbst, const uint8_t *__restrict__ bimg, const MrCol *__restrict__ cols, uint32_t idesc,
+    int *err)
+{
+    extern __shared__ __align__(1024) uint8_t smem[];
+    __shared__ MrPipe pipe;
+    __shared__ uint32_t tmem_base;
+    __shared__ volatile int abort_flag;
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    uint8_t *gst = smem;                                        // kMrGStages x 2 tiles x 8 KB
+    uint8_t *bst = smem + kMrGStages * kMrTiles * kMrGTile;     // nbst x chunk
+    const uint32_t chunk_bytes = (uint32_t)kMrChunkSteps * (uint32_t)N * 32u;
+    const uint32_t step_bytes = (uint32_t)N * 32u;
+
+    if (tid == 0) {
+        for (int s = 0; s < kMrGStages; ++s) {
+            mr_bar_init(&pipe.gfull[s], 1);
+            mr_bar_init(&pipe.gempty[s], kMrDecoders);
+        }
+        for (int s = 0; s < nbst; ++s) {
+            mr_bar_init(&pipe.bfull[s], 1);
+            mr_bar_init(&pipe.bempty[s], 1);
+        }
+        for (int b = 0; b < nbufs; ++b) {
+            mr_bar_init(&pipe.afull[b], kMrDecoders);
+            mr_bar_init(&pipe.aempty[b], 1);
+        }
+        mr_bar_init(&pipe.accfull, 1);
+        mr_bar_init(&pipe.accempty, kMrDecoders);
+        abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == kMrMmaWarp) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" ::"r"(
+            mr_smem(&tmem_base)));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    mr_fence_before();
+    __syncthreads();
+    mr_fence_after();
+
+    const int64_t ntiles = (p + 128 * kMrTiles - 1) / (128 * kMrTiles);
+    const int spt = (ksteps + 15) / 16;                 // genotype stages per tile (16 K-steps each)
+    const int cpt = ksteps / kMrChunkSteps;             // B chunks per tile
+
+    if (tid < kMrDecoders) {
+        // ------------------------------------------------------- decoders + epilogue
+        const int t = warp >> 2, r = tid & 127;
+        const uint32_t lane_off = (uint32_t)((warp & 3) * 32) << 16;
+        const uint32_t tb = tmem_base + (uint32_t)(256 * t) + lane_off;
+        const uint32_t abase = tb + (uint32_t)N;
+        uint32_t kst = 0, abuf = 0;
+        int T = 0;
+        bool ok = true;
+        for (int64_t tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x, ++T) {
+            for (int st = 0; st < spt && ok; ++st, ++kst) {
+                const uint32_t slot = kst % kMrGStages;
+                if (!mr_wait(&pipe.gfull[slot], (kst / kMrGStages) & 1u)) {
+                    abort_flag = 1;
+                    ok = false;
+                    break;
+                }
+                const uint8_t *rowp = gst + (slot * kMrTiles + t) * kMrGTile + r * kMrGStageBytes;
+                const int nb = min(8, (ksteps - st * 16) / 2);
+                for (int q8 = 0; q8 < nb; ++q8, ++abuf) {
+                    const uint32_t buf = abuf % (uint32_t)nbufs;
+                    if (abuf >= (uint32_t)nbufs) {
+                        if (!mr_wait(&pipe.aempty[buf], ((abuf / nbufs) - 1) & 1u)) {
+                            abort_flag = 1;
+                            ok = false;
+                            break;
+                        }
+                        mr_fence_after();
+                    }
+                    const uint2 x = *reinterpret_cast<const uint2 *>(
+                        rowp + ((((q8 >> 1) ^ ((r >> 1) & 3))) << 4) + (q8 & 1) * 8);
+                    uint32_t v[16];
+                    mr_decode(x.x, &v[0]);
+                    mr_decode(x.y, &v[8]);
+                    mr_st16(abase + 16u * buf, v);
+                    asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+                    mr_fence_before();
+                    mr_arrive(&pipe.afull[buf]);
+                }
+                mr_arrive(&pipe.gempty[slot]);
+                if (abort_flag) ok = false;
+            }
+            if (!ok) break;
+            // epilogue: S1 of each column for this thread's SNP
+            if (!mr_wait(&pipe.accfull, (uint32_t)T & 1u)) {
+                abort_flag = 1;
+                ok = false;
+                break;
+            }
+            mr_fence_after();
+            const int64_t j = tile * (128 * kMrTiles) + 128 * t + r;
+            for (int cg = 0; cg < N / 16; ++cg) {
+                uint32_t acc[16];
+                mr_ld16(tb + 16u * cg, acc);
+                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+                for (int e = 0; e < 8; ++e) {
+                    const int c = 8 * cg + e;
+                    if (c < ncols && j < p) {
+                        const MrCol &C = cols[c];
+                        C.g[j] = (__uint_as_float(acc[2 * e]) + __uint_as_float(acc[2 * e + 1])) * C.scale;
+                    }
+                }
+            }
+            mr_fence_before();
+            mr_arrive(&pipe.accempty);
+        }
+    } else if (warp == kMrMmaWarp) {
+        // ------------------------------------------------------- MMA issuer
+        if (lane == 0) {
+            uint32_t abuf = 0, bq = 0;
+            int T = 0;
+            bool ok = true;
+            const uint32_t b0 = mr_smem(bst);
+            for (int64_t tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x, ++T) {
+                if (T >= 1) {
+                    if (!mr_wait(&pipe.accempty, (uint32_t)(T - 1) & 1u)) { abort_flag = 1; break; }
+                    mr_fence_after();
+                }
+                uint32_t bslot = 0;
+                for (int s = 0; s < ksteps; ++s) {
+                    const int sc = s % kMrChunkSteps;
+                    if (sc == 0) {
+                        bslot = bq % (uint32_t)nbst;
+                        if (!mr_wait(&pipe.bfull[bslot], (bq / nbst) & 1u)) { abort_flag = 1; ok = false; break; }
+                    }
+                    const uint32_t buf = abuf % (uint32_t)nbufs;
+                    if ((s & 1) == 0) {
+                        if (!mr_wait(&pipe.afull[buf], (abuf / nbufs) & 1u)) { abort_flag = 1; ok = false; break; }
+                        mr_fence_after();
+                    }
+                    const uint64_t bd = mr_b_desc(b0 + bslot * chunk_bytes + (uint32_t)sc * step_bytes);
+#pragma unroll
+                    for (int t = 0; t < kMrTiles; ++t) {
+                        const uint32_t tb = tmem_base + (uint32_t)(256 * t);
+                        mr_mma(tb, tb + (uint32_t)N + 16u * buf + 8u * (uint32_t)(s & 1), bd, idesc,
+                               s > 0 ? 1u : 0u);
+                    }
+                    if (s & 1) {
+                        mr_commit(&pipe.aempty[buf]);
+                        ++abuf;
+                    }
+                    if (sc == kMrChunkSteps - 1) {
+                        mr_commit(&pipe.bempty[bslot]);
+                        ++bq;
+                    }
+                }
+                if (!ok) break;
+                mr_commit(&pipe.accfull);
+                if (abort_flag) ok = false;
+            }
+        }
+        __syncwarp();
+    } else if (warp == kMrGWarp) {
+        // ------------------------------------------------------- genotype tiles (TMA)
+        if (lane == 0) {
+            const int64_t my = blockIdx.x < ntiles ? (ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+            const int64_t total = my * spt;
+            int64_t k = 0;
+            for (; k < total && !abort_flag; ++k) {
+                const uint32_t slot = (uint32_t)(k % kMrGStages);
+                if (k >= kMrGStages &&
+                    !mr_wait(&pipe.gempty[slot], (uint32_t)((k / kMrGStages) - 1) & 1u)) {
+                    abort_flag = 1;
+                    break;
+                }
+                const int64_t tile = blockIdx.x + (k / spt) * gridDim.x;
+                const int st = (int)(k % spt);
+                mr_expect_tx(&pipe.gfull[slot], (uint32_t)(kMrTiles * kMrGTile));
+#pragma unroll
+                for (int t = 0; t < kMrTiles; ++t)
+                    mr_tma_2d(gst + (slot * kMrTiles + t) * kMrGTile, &gmap, st * kMrGStageBytes,
+                              (int)(tile * (128 * kMrTiles) + 128 * t), &pipe.gfull[slot]);
+            }
+            for (int64_t q = k - kMrGStages; q < k; ++q)     // copies in flight (after an abort)
+                if (q >= 0) mr_wait(&pipe.gfull[q % kMrGStages], (uint32_t)(q / kMrGStages) & 1u);
+        }
+        __syncwarp();
+    } else {
+        // ------------------------------------------------------- B chunks (bulk copies)
+        if (lane == 0) {
+            const int64_t my = blockIdx.x < ntiles ? (ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+            const int64_t total = my * cpt;
+            int64_t k = 0;
+            for (; k < total && !abort_flag; ++k) {
+                const uint32_t slot = (uint32_t)(k % nbst);
+                if (k >= nbst && !mr_wait(&pipe.bempty[slot], (uint32_t)((k / nbst) - 1) & 1u)) {
+                    abort_flag = 1;
+                    break;
+                }
+                const int ch = (int)(k % cpt);
+                mr_expect_tx(&pipe.bfull[slot], chunk_bytes);
+                mr_bulk(bst + slot * chunk_bytes, bimg + (size_t)ch * chunk_bytes, chunk_bytes,
+                        &pipe.bfull[slot]);
+            }
+            for (int64_t q = k - nbst; q < k; ++q)
+                if (q >= 0) mr_wait(&pipe.bfull[q % nbst], (uint32_t)(q / nbst) & 1u);
+        }
+        __syncwarp();
+    }
+    if (abort_flag && tid == 0) atomicExch(err, 1);
+    mr_fence_before();
+    __syncthreads();
+    mr_fence_after();
+    if (warp == kMrMmaWarp)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" ::"r"(tmem_base));
+}
+
+// ---------------------------------------------------------------------------
+// Missing-call sums and the standardisation: g_cj = v (S1 - u (R - M_cj)),
+// with S1 read from g_c.  The residual columns of a group are staged in shared
+// memory, interleaved (CG floats per sample); four lanes per SNP walk its
+// missing list in the order of the single-column pass.
+
+template <int CG>
+struct MrVec;
+template <>
+struct MrVec<1> { using T = float; };
+template <>
+struct MrVec<2> { using T = float2; };
+template <>
+struct MrVec<4> { using T = float4; };
+
+__device__ __forceinline__ void mr_addv(float *m, float v) { m[0] += v; }
+__device__ __forceinline__ void mr_addv(float *m, float2 v) { m[0] += v.x; m[1] += v.y; }
+__device__ __forceinline__ void mr_addv(float *m, float4 v)
+{
+    m[0] += v.x; m[1] += v.y; m[2] += v.z; m[3] += v.w;
+}
+
+template <int CG, typename IdxT, bool kStage>
+__global__ void __launch_bounds__(512) k_miss_finalize(const int64_t *__restrict__ off,
+                                                       const IdxT *__restrict__ idx, int64_t p,
+                                                       int64_t n_pad, const MrCol *__restrict__ cols,
+                                                       int ncols)
+{
+    using V = typename MrVec<CG>::T;
+    extern __shared__ __align__(16) unsigned char mr_sh[];
+    V *rs = reinterpret_cast<V *>(mr_sh);
+    const int c0 = blockIdx.y * CG;
+    if (kStage) {
+        for (int64_t i = threadIdx.x; i < n_pad; i += blockDim.x) {
+            float v[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+            for (int e = 0; e < CG; ++e)
+                if (c0 + e < ncols) v[e] = cols[c0 + e].r32[i];
+            V x;
+            if constexpr (CG == 1) x = v[0];
+            else if constexpr (CG == 2) x = make_float2(v[0], v[1]);
+            else x = make_float4(v[0], v[1], v[2], v[3]);
+            rs[i] = x;
+        }
+        __syncthreads();
+    }
+    const float *__restrict__ rg = cols[c0].r32;        // unstaged path: CG == 1
+    const int lane = threadIdx.x & 31, q = lane & 3;
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t base = warp * 8; base < p; base += nwarps * 8) {      // warp-uniform
+        const int64_t j = base + (lane >> 2);
+        const bool live = j < p;
+        const int64_t e0 = live ? off[j] : 0, e1 = live ? off[j + 1] : 0;
+        float m[CG];
+#pragma unroll
+        for (int e = 0; e < CG; ++e) m[e] = 0.0f;
+        for (int64_t e = e0 + q; e < e1; e += 16) {
+            IdxT ii[4];
+#pragma unroll
+            for (int t = 0; t < 4; ++t) ii[t] = e + 4 * t < e1 ? idx[e + 4 * t] : (IdxT)0;
+#pragma unroll
+            for (int t = 0; t < 4; ++t) {
+                if (e + 4 * t < e1) {
+                    if (kStage) mr_addv(m, rs[ii[t]]);
+                    else m[0] += __ldg(rg + ii[t]);
+                }
+            }
+        }
+#pragma unroll
+        for (int e = 0; e < CG; ++e) {
+            m[e] += __shfl_xor_sync(0xffffffffu, m[e], 1);
+            m[e] += __shfl_xor_sync(0xffffffffu, m[e], 2);
+        }
+        if (live && q == 0) {
+#pragma unroll
+            for (int e = 0; e < CG; ++e) {
+                if (c0 + e < ncols) {
+                    const MrCol &C = cols[c0 + e];
+                    const float s1 = C.g[j];
+                    C.g[j] = C.v32[j] * (s1 - C.u32[j] * (C.R - m[e]));
+                }
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+
+struct MrWork {
+    uint8_t *bimg = nullptr;
+    size_t bbytes = 0;
+    int *err = nullptr;
+    int dev = -1;
+};
+static thread_local MrWork g_mr;
+
+static int mr_ksteps(const iht_dataset *ds)
+{
+    const int64_t ngroups = ((ds->n + 3) / 4 + 15) / 16;    // 16-byte groups = 4 K-steps
+    return (int)(4 * ngroups);
+}
+
+static int mr_n(int ncols) { return (2 * ncols + 15) / 16 * 16; }
+
+static size_t mr_gbytes() { return (size_t)kMrGStages * kMrTiles * kMrGTile; }
+
+static int mr_bstages(int N)
+{
+    const size_t chunk = (size_t)kMrChunkSteps * N * 32;
+    const size_t room = kMrSmemMax - mr_gbytes();
+    return (int)std::min<size_t>(kMrMaxBStages, room / chunk);
+}
+
+int mrhs_max_cols() { return kMrMaxCols; }
+
+bool grad_mrhs_supported(const iht_dataset *ds) { return ds->p < (1ll << 31) && mr_ksteps(ds) > 0; }
+
+using MrEncodeTiled = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *,
+                                   const cuuint64_t *, const cuuint64_t *, const cuuint32_t *,
+                                   const cuuint32_t *, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                   CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+static int mr_gmap(const iht_dataset *ds, CUtensorMap *map)
+{
+    static MrEncodeTiled encode = nullptr;
+    if (!encode) {
+        void *fn = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        IHT_CUDA(cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000,
+                                                  cudaEnableDefault, &q));
+        if (q != cudaDriverEntryPointSuccess || !fn) return IHT_ECUDA;
+        encode = (MrEncodeTiled)fn;
+    }
+    const cuuint64_t dims[2] = {(cuuint64_t)ds->stride, (cuuint64_t)ds->p};
+    const cuuint64_t strides[1] = {(cuuint64_t)ds->stride};
+    const cuuint32_t box[2] = {(cuuint32_t)kMrGStageBytes, 128};
+    const cuuint32_t estr[2] = {1, 1};
+    const CUresult r = encode(map, CU_TENSOR_MAP_DATA_TYPE_UINT8, 2, ds->G, dims, strides, box, estr,
+                              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B,
+                              CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? IHT_OK : IHT_ECUDA;
+}
+
+template <int CG, typename IdxT, bool kStage>
+static int mr_launch_finalize(iht_dataset *ds, const MrCol *cols, int ncols, size_t smem)
+{
+    auto kern = k_miss_finalize<CG, IdxT, kStage>;
+    if (smem > 48 * 1024) IHT_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    const int groups = (ncols + CG - 1) / CG;
+    const int per_sm = smem > 110 * 1024 ? 1 : 2;
+    const int gx = (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(ds->p, 128),
+                                                               ((int64_t)ds->ctx->num_sms * per_sm + groups - 1) / groups));
+    kern<<<dim3(gx, groups), 512, smem, ds->ctx->stream>>>(ds->miss_off, (const IdxT *)ds->miss_idx,
+                                                           ds->p, ds->n_pad, cols, ncols);
+    note_launch();
+    IHT_CUDA(cudaGetLastError());
+    return IHT_OK;
+}
+
+template <typename IdxT>
+static int mr_finalize(iht_dataset *ds, const MrCol *cols, int ncols)
+{
+    const size_t f = sizeof(float) * (size_t)ds->n_pad;
+    if (4 * f <= 200 * 1024) return mr_launch_finalize<4, IdxT, true>(ds, cols, ncols, 4 * f);
+    if (2 * f <= 200 * 1024) return mr_launch_finalize<2, IdxT, true>(ds, cols, ncols, 2 * f);
+    if (f <= 200 * 1024) return mr_launch_finalize<1, IdxT, true>(ds, cols, ncols, f);
+    return mr_launch_finalize<1, IdxT, false>(ds, cols, ncols, 0);
+}
+
+// G of ncols residual columns (cols: device array; r32, u32, v32 and g set by
+// the caller).  Passes of at most kMrMaxCols columns.
+int launch_grad_mrhs(iht_dataset *ds, MrCol *cols, int ncols)
+{
+    if (ncols <= 0) return IHT_OK;
+    if (!grad_mrhs_supported(ds)) return IHT_EINVAL;
+    cudaStream_t s = ds->ctx->stream;
+    const int ksteps = mr_ksteps(ds);
+    const size_t need = (size_t)ksteps * mr_n(kMrMaxCols) * 32;
+    MrWork &w = g_mr;
+    if (w.dev != ds->ctx->device || w.bbytes < need) {
+        if (w.bimg) cudaFree(w.bimg);
+        if (w.err) cudaFree(w.err);
+        w.bimg = nullptr;
+        w.err = nullptr;
+        w.bbytes = 0;
+        IHT_CUDA(cudaMalloc(&w.bimg, need));
+        IHT_CUDA(cudaMalloc(&w.err, sizeof(int)));
+        IHT_CUDA(cudaMemsetAsync(w.err, 0, sizeof(int), s));
+        w.bbytes = need;
+        w.dev = ds->ctx->device;
+    }
+    CUtensorMap map;
+    int rc = mr_gmap(ds, &map);
+    if (rc) return rc;
+    static thread_local int cfg = -1;
+    if (cfg != ds->ctx->device) {
+        IHT_CUDA(cudaFuncSetAttribute(k_grad_mrhs, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)kMrSmemMax));
+        cfg = ds->ctx->device;
+    }
+    const int64_t tiles = (ds->p + 128 * kMrTiles - 1) / (128 * kMrTiles);
+    const int grid = (int)std::min<int64_t>(tiles, ds->ctx->num_sms);
+    for (int c0 = 0; c0 < ncols; c0 += kMrMaxCols) {
+        const int nc = std::min(kMrMaxCols, ncols - c0);
+        const int N = mr_n(nc);
+        const size_t bbytes = (size_t)ksteps * N * 32;
+        IHT_CUDA(cudaMemsetAsync(w.bimg, 0, bbytes, s));
+        k_mr_limbs<<<nc, 1024, 0, s>>>(cols + c0, (int64_t)ksteps * kMrStepSamples, N, w.bimg);
+        const int nbst = mr_bstages(N);
+        const int nbufs = std::min(kMrMaxBufs, (256 - N) / 16);
+        if (nbst < 2 || nbufs < 2) return IHT_EINVAL;
+        // at least 116 KB, so one CTA per SM: the kernel allocates all 512 columns of tensor memory
+        const size_t smem = std::max<size_t>(116 * 1024, mr_gbytes() + (size_t)nbst * kMrChunkSteps * N * 32);
+        const uint32_t idesc = (1u << 4) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
+        k_grad_mrhs<<<grid, kMrThreads, smem, s>>>(map, ds->p, ksteps, N, nc, nbufs, nbst, w.bimg,
+                                                    cols + c0, idesc, w.err);
+        note_launch(2);
+        IHT_CUDA(cudaGetLastError());
+        rc = ds->miss_idx16 ? mr_finalize<uint16_t>(ds, cols + c0, nc)
+                            : mr_finalize<int32_t>(ds, cols + c0, nc);
+        if (rc) return rc;
+    }
+    return IHT_OK;
+}
+
+// Bounded-wait status of the multi-column passes so far (1 = a wait timed out).
+int grad_mrhs_status(iht_dataset *ds, int *timed_out)
+{
+    *timed_out = 0;
+    if (!g_mr.err) return IHT_OK;
+    int h = 0;
+    IHT_CUDA(cudaMemcpyAsync(&h, g_mr.err, sizeof(int), cudaMemcpyDeviceToHost, ds->ctx->stream));
+    IHT_CUDA(cudaStreamSynchronize(ds->ctx->stream));
+    *timed_out = h;
+    return IHT_OK;
+}
+
+}  // namespace iht

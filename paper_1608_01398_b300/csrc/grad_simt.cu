@@ -84,7 +84,8 @@ __global__ void __launch_bounds__(256) k_grad_simt(const uint8_t *__restrict__ G
     }
 }
 
-int launch_grad_simt(iht_dataset *ds, const float *r32, float *g, const int32_t *done)
+static int grad_simt_run(iht_dataset *ds, const float *r32, const float *u32, const float *v32,
+                         float *g, const int32_t *done)
 {
     static thread_local int configured_dev = -1;
     static thread_local size_t configured_smem = 0;
@@ -101,11 +102,21 @@ int launch_grad_simt(iht_dataset *ds, const float *r32, float *g, const int32_t 
     const int64_t want = (ds->p + 7) / 8;
     const int blocks = (int)std::min<int64_t>(want, (int64_t)per_sm * ds->ctx->num_sms);
     k_grad_simt<<<blocks, 256, smem, ds->ctx->stream>>>(ds->G, ds->p, ds->stride, ds->rowb, r32,
-                                                        ds->n_pad,
-                                                        ds->ws->u32, ds->ws->v32, g, done);
+                                                        ds->n_pad, u32, v32, g, done);
     note_launch();
     IHT_CUDA(cudaGetLastError());
     return IHT_OK;
+}
+
+int launch_grad_simt(iht_dataset *ds, const float *r32, float *g, const int32_t *done)
+{
+    return grad_simt_run(ds, r32, ds->ws->u32, ds->ws->v32, g, done);
+}
+
+int launch_grad_simt_stats(iht_dataset *ds, const float *r32, const float *u32, const float *v32,
+                           float *g)
+{
+    return grad_simt_run(ds, r32, u32, v32, g, nullptr);
 }
 
 int launch_grad_impl(iht_dataset *ds, int impl, const float *r32, float *g, const int32_t *done)

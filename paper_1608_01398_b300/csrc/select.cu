@@ -24,9 +24,8 @@ constexpr int kSelThreads = 256;
 constexpr int kSelItems = 16;                          // consecutive indices per thread
 constexpr int kSelChunk = kSelThreads * kSelItems;     // indices per collection block
 
-__global__ void k_sel_init(SelState *st, uint32_t K, uint32_t *hist, const int32_t *done)
+__device__ __forceinline__ void sel_init_body(SelState *st, uint32_t K, uint32_t *hist)
 {
-    if (done && *done) return;
     if (threadIdx.x == 0) {
         st->prefix = 0;
         st->mask = 0;
@@ -38,12 +37,19 @@ __global__ void k_sel_init(SelState *st, uint32_t K, uint32_t *hist, const int32
     for (int b = threadIdx.x; b < kSelBins; b += blockDim.x) hist[b] = 0;
 }
 
-__global__ void __launch_bounds__(kSelThreads) k_sel_hist(const float *__restrict__ keys, int64_t p,
-                                                          SelState *st, uint32_t *hist, int shift,
-                                                          uint32_t dmask, const int32_t *done)
+__global__ void k_sel_init(SelState *st, uint32_t K, uint32_t *hist, const int32_t *done)
+{
+    if (done && *done) return;
+    sel_init_body(st, K, hist);
+}
+
+// Histogram pass over keys[0..p) with the digits fixed so far; blockIdx.x
+// strides over the keys.
+__device__ __forceinline__ void sel_hist_body(const float *__restrict__ keys, int64_t p,
+                                              SelState *st, uint32_t *hist, int shift,
+                                              uint32_t dmask)
 {
     __shared__ uint32_t sh[kSelBins];
-    if (done && *done) return;
     for (int b = threadIdx.x; b < kSelBins; b += blockDim.x) sh[b] = 0;
     __syncthreads();
     const uint32_t prefix = st->prefix, mask = st->mask;
@@ -58,6 +64,14 @@ __global__ void __launch_bounds__(kSelThreads) k_sel_hist(const float *__restric
     __syncthreads();
     for (int b = threadIdx.x; b < kSelBins; b += blockDim.x)
         if (sh[b]) atomicAdd(&hist[b], sh[b]);
+}
+
+__global__ void __launch_bounds__(kSelThreads) k_sel_hist(const float *__restrict__ keys, int64_t p,
+                                                          SelState *st, uint32_t *hist, int shift,
+                                                          uint32_t dmask, const int32_t *done)
+{
+    if (done && *done) return;
+    sel_hist_body(keys, p, st, hist, shift, dmask);
 }
 
 // Inclusive scan over a block of 1024 threads, 2 items per thread (fixed order).
@@ -90,11 +104,10 @@ __device__ __forceinline__ void scan2(uint32_t &a, uint32_t &b, uint32_t *wsum)
 }
 
 // Single block of 1024 threads: bins scanned from the top.
-__global__ void __launch_bounds__(1024) k_sel_scan(SelState *st, uint32_t *hist, int shift,
-                                                   uint32_t dmask, int nbins, const int32_t *done)
+__device__ __forceinline__ void sel_scan_body(SelState *st, uint32_t *hist, int shift, uint32_t dmask,
+                                              int nbins)
 {
     __shared__ uint32_t wsum[32];
-    if (done && *done) return;
     const int t = threadIdx.x;
     // reversed order: position q holds bin nbins-1-q
     const int q0 = 2 * t, q1 = 2 * t + 1;
@@ -118,15 +131,20 @@ __global__ void __launch_bounds__(1024) k_sel_scan(SelState *st, uint32_t *hist,
     if (q1 < nbins) hist[nbins - 1 - q1] = 0;
 }
 
-// Keys > T go to out[0..count_gt) in any order; per-chunk counts of keys == T.
-__global__ void __launch_bounds__(kSelThreads) k_sel_collect_gt(const float *__restrict__ keys,
-                                                                int64_t p, SelState *st,
-                                                                int32_t *__restrict__ out,
-                                                                uint32_t *__restrict__ chunk_eq,
-                                                                const int32_t *done)
+__global__ void __launch_bounds__(1024) k_sel_scan(SelState *st, uint32_t *hist, int shift,
+                                                   uint32_t dmask, int nbins, const int32_t *done)
+{
+    if (done && *done) return;
+    sel_scan_body(st, hist, shift, dmask, nbins);
+}
+
+// Keys > T go to out[0..count_gt) in any order; per-chunk counts of keys == T
+// (chunk = blockIdx.x).
+__device__ __forceinline__ void sel_collect_gt_body(const float *__restrict__ keys, int64_t p,
+                                                    SelState *st, int32_t *__restrict__ out,
+                                                    uint32_t *__restrict__ chunk_eq)
 {
     __shared__ uint32_t sh_eq;
-    if (done && *done) return;
     if (threadIdx.x == 0) sh_eq = 0;
     __syncthreads();
     const uint32_t T = st->prefix;
@@ -145,13 +163,21 @@ __global__ void __launch_bounds__(kSelThreads) k_sel_collect_gt(const float *__r
     if (threadIdx.x == 0) chunk_eq[blockIdx.x] = sh_eq;
 }
 
+__global__ void __launch_bounds__(kSelThreads) k_sel_collect_gt(const float *__restrict__ keys,
+                                                                int64_t p, SelState *st,
+                                                                int32_t *__restrict__ out,
+                                                                uint32_t *__restrict__ chunk_eq,
+                                                                const int32_t *done)
+{
+    if (done && *done) return;
+    sel_collect_gt_body(keys, p, st, out, chunk_eq);
+}
+
 // Exclusive scan of chunk_eq in place (single block of 1024 threads).
-__global__ void __launch_bounds__(1024) k_sel_scan_chunks(uint32_t *chunk_eq, int64_t nchunks,
-                                                          const int32_t *done)
+__device__ __forceinline__ void sel_scan_chunks_body(uint32_t *chunk_eq, int64_t nchunks)
 {
     __shared__ uint32_t wsum[32];
     __shared__ uint32_t carry;
-    if (done && *done) return;
     if (threadIdx.x == 0) carry = 0;
     __syncthreads();
     for (int64_t base = 0; base < nchunks; base += 2048) {
@@ -169,15 +195,19 @@ __global__ void __launch_bounds__(1024) k_sel_scan_chunks(uint32_t *chunk_eq, in
     }
 }
 
+__global__ void __launch_bounds__(1024) k_sel_scan_chunks(uint32_t *chunk_eq, int64_t nchunks,
+                                                          const int32_t *done)
+{
+    if (done && *done) return;
+    sel_scan_chunks_body(chunk_eq, nchunks);
+}
+
 // The lowest-index keys == T, in index order, after the keys > T.
-__global__ void __launch_bounds__(kSelThreads) k_sel_collect_eq(const float *__restrict__ keys,
-                                                                int64_t p, const SelState *st,
-                                                                int32_t *__restrict__ out,
-                                                                const uint32_t *__restrict__ chunk_off,
-                                                                const int32_t *done)
+__device__ __forceinline__ void sel_collect_eq_body(const float *__restrict__ keys, int64_t p,
+                                                    const SelState *st, int32_t *__restrict__ out,
+                                                    const uint32_t *__restrict__ chunk_off)
 {
     __shared__ uint32_t wsum[kSelThreads / 32];
-    if (done && *done) return;
     const uint32_t T = st->prefix, need = st->need, gt = st->count_gt;
     const uint32_t off0 = chunk_off[blockIdx.x];
     if (off0 >= need) return;                 // uniform over the block
@@ -206,11 +236,20 @@ __global__ void __launch_bounds__(kSelThreads) k_sel_collect_eq(const float *__r
     }
 }
 
+__global__ void __launch_bounds__(kSelThreads) k_sel_collect_eq(const float *__restrict__ keys,
+                                                                int64_t p, const SelState *st,
+                                                                int32_t *__restrict__ out,
+                                                                const uint32_t *__restrict__ chunk_off,
+                                                                const int32_t *done)
+{
+    if (done && *done) return;
+    sel_collect_eq_body(keys, p, st, out, chunk_off);
+}
+
 // Sort K (<= kMaxCand) indices ascending in one block (bitonic in shared memory).
-__global__ void __launch_bounds__(1024) k_sort_idx(int32_t *idx, int K, const int32_t *done)
+__device__ __forceinline__ void sort_idx_body(int32_t *idx, int K)
 {
     __shared__ int32_t s[kMaxCand];
-    if (done && *done) return;
     int P = 1;
     while (P < K) P <<= 1;
     for (int i = threadIdx.x; i < P; i += blockDim.x) s[i] = i < K ? idx[i] : 0x7fffffff;
@@ -232,6 +271,94 @@ __global__ void __launch_bounds__(1024) k_sort_idx(int32_t *idx, int K, const in
         }
     }
     for (int i = threadIdx.x; i < K; i += blockDim.x) idx[i] = s[i];
+}
+
+__global__ void __launch_bounds__(1024) k_sort_idx(int32_t *idx, int K, const int32_t *done)
+{
+    if (done && *done) return;
+    sort_idx_body(idx, K);
+}
+
+// ---------------------------------------------------------------------------
+// Batched selection: blockIdx.y (or blockIdx.x for the single-block steps)
+// indexes the problem; each problem has its own keys, K, output and scratch.
+
+__global__ void k_bsel_init(const SelJob *jobs)
+{
+    const SelJob &J = jobs[blockIdx.x];
+    if (J.done && *J.done) return;
+    sel_init_body(J.st, J.K, J.hist);
+}
+
+__global__ void __launch_bounds__(kSelThreads) k_bsel_hist(const SelJob *jobs, int64_t p, int shift,
+                                                           uint32_t dmask)
+{
+    const SelJob &J = jobs[blockIdx.y];
+    if (J.done && *J.done) return;
+    sel_hist_body(J.keys, p, J.st, J.hist, shift, dmask);
+}
+
+__global__ void __launch_bounds__(1024) k_bsel_scan(const SelJob *jobs, int shift, uint32_t dmask,
+                                                    int nbins)
+{
+    const SelJob &J = jobs[blockIdx.x];
+    if (J.done && *J.done) return;
+    sel_scan_body(J.st, J.hist, shift, dmask, nbins);
+}
+
+__global__ void __launch_bounds__(kSelThreads) k_bsel_collect_gt(const SelJob *jobs, int64_t p)
+{
+    const SelJob &J = jobs[blockIdx.y];
+    if (J.done && *J.done) return;
+    sel_collect_gt_body(J.keys, p, J.st, J.out, J.chunk_eq);
+}
+
+__global__ void __launch_bounds__(1024) k_bsel_scan_chunks(const SelJob *jobs, int64_t nchunks)
+{
+    const SelJob &J = jobs[blockIdx.x];
+    if (J.done && *J.done) return;
+    sel_scan_chunks_body(J.chunk_eq, nchunks);
+}
+
+__global__ void __launch_bounds__(kSelThreads) k_bsel_collect_eq(const SelJob *jobs, int64_t p)
+{
+    const SelJob &J = jobs[blockIdx.y];
+    if (J.done && *J.done) return;
+    sel_collect_eq_body(J.keys, p, J.st, J.out, J.chunk_eq);
+}
+
+__global__ void __launch_bounds__(1024) k_bsort_idx(const SelJob *jobs)
+{
+    const SelJob &J = jobs[blockIdx.x];
+    if (J.done && *J.done) return;
+    sort_idx_body(J.out, (int)J.K);
+}
+
+int64_t sel_nchunks(int64_t p) { return (p + kSelChunk - 1) / kSelChunk; }
+
+// Top-K of |keys| for nb problems at once (jobs: device array of nb SelJob;
+// every job's chunk_eq holds sel_nchunks(p) counts).
+int select_topk_batch(iht_ctx *ctx, const SelJob *jobs, int nb, int64_t p)
+{
+    if (nb < 1) return IHT_OK;
+    cudaStream_t s = ctx->stream;
+    const int64_t nchunks = (p + kSelChunk - 1) / kSelChunk;
+    const int hblocks = (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(p, kSelThreads),
+                                                                     ((int64_t)ctx->num_sms * 4 + nb - 1) / nb));
+    k_bsel_init<<<nb, 256, 0, s>>>(jobs);
+    const int shifts[3] = {20, 10, 0};
+    const uint32_t dmasks[3] = {0x7ffu, 0x3ffu, 0x3ffu};
+    for (int ps = 0; ps < 3; ++ps) {
+        k_bsel_hist<<<dim3(hblocks, nb), kSelThreads, 0, s>>>(jobs, p, shifts[ps], dmasks[ps]);
+        k_bsel_scan<<<nb, 1024, 0, s>>>(jobs, shifts[ps], dmasks[ps], (int)dmasks[ps] + 1);
+    }
+    k_bsel_collect_gt<<<dim3((unsigned)nchunks, nb), kSelThreads, 0, s>>>(jobs, p);
+    k_bsel_scan_chunks<<<nb, 1024, 0, s>>>(jobs, nchunks);
+    k_bsel_collect_eq<<<dim3((unsigned)nchunks, nb), kSelThreads, 0, s>>>(jobs, p);
+    k_bsort_idx<<<nb, 1024, 0, s>>>(jobs);
+    note_launch(11);
+    IHT_CUDA(cudaGetLastError());
+    return IHT_OK;
 }
 
 int ensure_selwork(iht_ctx *ctx, int64_t p)

@@ -29,12 +29,11 @@ __device__ __forceinline__ int dosage_of(uint32_t code)   // -1 = missing
     return code == 0u ? 0 : (code == 2u ? 1 : (code == 3u ? 2 : -1));
 }
 
-__global__ void __launch_bounds__(1024) k_gather_gS(const float *__restrict__ g,
-                                                    const int32_t *__restrict__ S, int k,
-                                                    double *__restrict__ coef, Scalars *sc)
+__device__ __forceinline__ void gather_gS_body(const float *__restrict__ g,
+                                               const int32_t *__restrict__ S, int k,
+                                               double *__restrict__ coef, Scalars *sc)
 {
     __shared__ double red[32];
-    if (sc->done) return;
     double s = 0.0;
     for (int c = threadIdx.x; c < k; c += blockDim.x) {
         const double x = (double)g[S[c]];
@@ -45,19 +44,25 @@ __global__ void __launch_bounds__(1024) k_gather_gS(const float *__restrict__ g,
     if (threadIdx.x == 0) sc->num = s;
 }
 
+__global__ void __launch_bounds__(1024) k_gather_gS(const float *__restrict__ g,
+                                                    const int32_t *__restrict__ S, int k,
+                                                    double *__restrict__ coef, Scalars *sc)
+{
+    if (sc->done) return;
+    gather_gS_body(g, S, k, coef, sc);
+}
+
 constexpr int kZmulColsPerGroup = 4;   // columns per block of the first phase
 
-// Phase 1: block (x, y) = (64 packed bytes x 4 columns): one thread per byte
-// of a column group; per-sample partial sums of the group go to part[y][i].
-__global__ void __launch_bounds__(256) k_zmul_part(const uint8_t *__restrict__ G, int64_t stride,
-                                                   int64_t rowb, const int32_t *__restrict__ cols,
-                                                   int m, const double *__restrict__ coef, double sign,
-                                                   const double *__restrict__ u64,
-                                                   const double *__restrict__ v64,
-                                                   double *__restrict__ part, int64_t n_pad,
-                                                   const int32_t *__restrict__ done)
+// Phase 1: block (x, y) = (256 packed bytes x 4 columns): one thread per byte
+// of a column group; per-sample partial sums of group y go to part[y][i].
+__device__ __forceinline__ void zmul_part_body(const uint8_t *__restrict__ G, int64_t stride,
+                                               int64_t rowb, const int32_t *__restrict__ cols,
+                                               int m, const double *__restrict__ coef, double sign,
+                                               const double *__restrict__ u64,
+                                               const double *__restrict__ v64,
+                                               double *__restrict__ part, int64_t n_pad)
 {
-    if (done && *done) return;
     const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int c0 = blockIdx.y * kZmulColsPerGroup;
     if (b >= stride) return;
@@ -90,19 +95,29 @@ __global__ void __launch_bounds__(256) k_zmul_part(const uint8_t *__restrict__ G
     for (int e = 0; e < 4; ++e) dst[e] = acc[e];
 }
 
+__global__ void __launch_bounds__(256) k_zmul_part(const uint8_t *__restrict__ G, int64_t stride,
+                                                   int64_t rowb, const int32_t *__restrict__ cols,
+                                                   int m, const double *__restrict__ coef, double sign,
+                                                   const double *__restrict__ u64,
+                                                   const double *__restrict__ v64,
+                                                   double *__restrict__ part, int64_t n_pad,
+                                                   const int32_t *__restrict__ done)
+{
+    if (done && *done) return;
+    zmul_part_body(G, stride, rowb, cols, m, coef, sign, u64, v64, part, n_pad);
+}
+
 // Phase 2: out_i = base_i + sum over groups (fixed order) on used rows, 0
 // elsewhere; per-block sums of out, out^2 and (out - prev)^2 (0 without prev)
 // into partials[3 b .. 3 b + 2].
-__global__ void __launch_bounds__(256) k_zmul_sum(const double *__restrict__ part, int ngroups,
-                                                  int64_t n_pad, const int32_t *__restrict__ used,
-                                                  const double *__restrict__ base,
-                                                  const double *__restrict__ prev,
-                                                  double *__restrict__ out,
-                                                  double *__restrict__ partials,
-                                                  const int32_t *__restrict__ done)
+__device__ __forceinline__ void zmul_sum_body(const double *__restrict__ part, int ngroups,
+                                              int64_t n_pad, const int32_t *__restrict__ used,
+                                              const double *__restrict__ base,
+                                              const double *__restrict__ prev,
+                                              double *__restrict__ out,
+                                              double *__restrict__ partials)
 {
     __shared__ double red[8];
-    if (done && *done) return;
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     double o = 0.0, d = 0.0;
     if (i < n_pad) {
@@ -120,6 +135,18 @@ __global__ void __launch_bounds__(256) k_zmul_sum(const double *__restrict__ par
         partials[3 * blockIdx.x + 1] = s2;
         partials[3 * blockIdx.x + 2] = d2;
     }
+}
+
+__global__ void __launch_bounds__(256) k_zmul_sum(const double *__restrict__ part, int ngroups,
+                                                  int64_t n_pad, const int32_t *__restrict__ used,
+                                                  const double *__restrict__ base,
+                                                  const double *__restrict__ prev,
+                                                  double *__restrict__ out,
+                                                  double *__restrict__ partials,
+                                                  const int32_t *__restrict__ done)
+{
+    if (done && *done) return;
+    zmul_sum_body(part, ngroups, n_pad, used, base, prev, out, partials);
 }
 
 int zmul_blocks(const iht_dataset *ds) { return ceil_div(ds->n_pad, 256); }
@@ -243,12 +270,12 @@ __device__ void sort_by_w(MergeShared &sh, int nU)
     }
 }
 
-__global__ void __launch_bounds__(kMergeThreads) k_merge(MergeArgs A)
+// The projection proper for a live solve (every thread of the block calls it).
+__device__ __forceinline__ void merge_body(const MergeArgs &A)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     MergeShared &sh = *reinterpret_cast<MergeShared *>(smem_raw);
     Scalars *sc = A.sc;
-    if (sc->done) return;
     const int k = sc->k;
 
     if (threadIdx.x == 0) {
@@ -372,6 +399,14 @@ __global__ void __launch_bounds__(kMergeThreads) k_merge(MergeArgs A)
     }
 }
 
+__global__ void __launch_bounds__(kMergeThreads) k_merge(MergeArgs A)
+{
+    const int d = A.sc->done;
+    __syncthreads();   // every thread has read the flag before thread 0 may set it
+    if (d) return;
+    merge_body(A);
+}
+
 // ---------------------------------------------------------------------------
 struct TraceDev {
     double *objective, *mu;
@@ -381,12 +416,11 @@ struct TraceDev {
 
 // Backtracking decision for the candidate of k_merge, whose residual r+ the
 // preceding pass wrote (partials: sum r+, sum r+^2, sum (r+ - r)^2).
-__global__ void __launch_bounds__(256) k_decide(Scalars *sc, const double *partials, int npart,
-                                                int32_t *S, double *bS, const int32_t *Sp,
-                                                const double *bSp, TraceDev tr)
+__device__ __forceinline__ void decide_body(Scalars *sc, const double *partials, int npart,
+                                            int32_t *S, double *bS, const int32_t *Sp,
+                                            const double *bSp, const TraceDev &tr)
 {
     __shared__ int accept;
-    if (sc->done) return;
     const int k = sc->k;
     if (threadIdx.x == 0) {
         double s = 0.0, s2 = 0.0, zz = 0.0;
@@ -440,10 +474,17 @@ __global__ void __launch_bounds__(256) k_decide(Scalars *sc, const double *parti
     }
 }
 
-// Objective of beta = 0 (r = y) before the first iteration.
-__global__ void k_init_objective(Scalars *sc, const double *partials, int npart)
+__global__ void __launch_bounds__(256) k_decide(Scalars *sc, const double *partials, int npart,
+                                                int32_t *S, double *bS, const int32_t *Sp,
+                                                const double *bSp, TraceDev tr)
 {
-    if (sc->done || threadIdx.x != 0) return;
+    if (sc->done) return;
+    decide_body(sc, partials, npart, S, bS, Sp, bSp, tr);
+}
+
+// Objective of beta = 0 (r = y) before the first iteration (one thread).
+__device__ __forceinline__ void init_objective_body(Scalars *sc, const double *partials, int npart)
+{
     double s = 0.0, s2 = 0.0;
     for (int b = 0; b < npart; ++b) {
         s += partials[3 * b];
@@ -454,18 +495,31 @@ __global__ void k_init_objective(Scalars *sc, const double *partials, int npart)
     sc->f = 0.5 * s2;
 }
 
-// Accepted residual: r64 <- src, r32 <- src - mean on the used rows.
-__global__ void k_center(const double *__restrict__ src, double *__restrict__ r64,
-                         const int32_t *__restrict__ used, int64_t n_pad, const Scalars *sc,
-                         float *__restrict__ r32)
+__global__ void k_init_objective(Scalars *sc, const double *partials, int npart)
 {
-    if (sc->done || sc->retry) return;
+    if (sc->done || threadIdx.x != 0) return;
+    init_objective_body(sc, partials, npart);
+}
+
+// Accepted residual: r64 <- src, r32 <- src - mean on the used rows.
+__device__ __forceinline__ void center_body(const double *__restrict__ src, double *__restrict__ r64,
+                                            const int32_t *__restrict__ used, int64_t n_pad,
+                                            const Scalars *sc, float *__restrict__ r32)
+{
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n_pad) return;
     const double mean = sc->sum_r / (double)sc->n_rows;
     const double v = src[i];
     if (src != r64) r64[i] = v;
     r32[i] = used[i] ? (float)(v - mean) : 0.0f;
+}
+
+__global__ void k_center(const double *__restrict__ src, double *__restrict__ r64,
+                         const int32_t *__restrict__ used, int64_t n_pad, const Scalars *sc,
+                         float *__restrict__ r32)
+{
+    if (sc->done || sc->retry) return;
+    center_body(src, r64, used, n_pad, sc, r32);
 }
 
 __global__ void k_check_finite(const double *__restrict__ y, int64_t n, Scalars *sc)
@@ -642,14 +696,19 @@ int run_solve_host(iht_dataset *ds, int k, const iht_options *opt, int n_rows, i
     return rc;
 }
 
-int check_finite_y(iht_dataset *ds, int64_t n_rows, const double *y_dev)
+int check_finite_y_sc(iht_dataset *ds, int64_t n_rows, const double *y_dev, Scalars *sc)
 {
     if (n_rows > 0) {
-        k_check_finite<<<ceil_div(n_rows, 256), 256, 0, ds->ctx->stream>>>(y_dev, n_rows, ds->ws->sc);
+        k_check_finite<<<ceil_div(n_rows, 256), 256, 0, ds->ctx->stream>>>(y_dev, n_rows, sc);
         note_launch();
     }
     IHT_CUDA(cudaGetLastError());
     return IHT_OK;
+}
+
+int check_finite_y(iht_dataset *ds, int64_t n_rows, const double *y_dev)
+{
+    return check_finite_y_sc(ds, n_rows, y_dev, ds->ws->sc);
 }
 
 }  // namespace iht
@@ -687,6 +746,189 @@ int write_beta_device(iht_dataset *ds, int k, double *beta_out)
     cudaStream_t s = ds->ctx->stream;
     IHT_CUDA(cudaMemsetAsync(beta_out, 0, sizeof(double) * ds->p, s));
     k_scatter_beta<<<ceil_div(k, 256), 256, 0, s>>>(ds->ws->S, ds->ws->bS, k, beta_out);
+    note_launch();
+    IHT_CUDA(cudaGetLastError());
+    return IHT_OK;
+}
+
+}  // namespace iht
+
+// ---------------------------------------------------------------------------
+// Batched tails: the same bodies, one solve per block row (blockIdx.y, or
+// blockIdx.x for single-block steps).  A solve takes part in an attempt when
+// it is not done and either the attempt is its first of the iteration or its
+// last candidate was rejected; k_merge_b records that in sc->live and the
+// later kernels of the attempt read it.
+
+namespace iht {
+
+__global__ void __launch_bounds__(1024) k_gather_gS_b(const BSolve *bs)
+{
+    const BSolve &B = bs[blockIdx.x];
+    if (B.sc->done) return;
+    gather_gS_body(B.g, B.S, B.k, B.coef, B.sc);
+}
+
+__device__ __forceinline__ bool zmul_gate(const BSolve &B, int which)
+{
+    const Scalars *sc = B.sc;
+    if (which == kZmulInit) return true;
+    if (which == kZmulStep) return !sc->done;
+    return sc->live && !sc->done;
+}
+
+__global__ void __launch_bounds__(256) k_zmul_part_b(const uint8_t *__restrict__ G, int64_t stride,
+                                                     int64_t rowb, const BSolve *bs, int which,
+                                                     int64_t n_pad)
+{
+    const BSolve &B = bs[blockIdx.z];
+    if (!zmul_gate(B, which)) return;
+    const int m = which == kZmulInit ? 0 : B.k;
+    if ((int)blockIdx.y * kZmulColsPerGroup >= m) return;     // beyond this solve's groups
+    if (which == kZmulStep)
+        zmul_part_body(G, stride, rowb, B.S, m, B.coef, 1.0, B.u64, B.v64, B.zpart, n_pad);
+    else
+        zmul_part_body(G, stride, rowb, B.Sp, m, B.bSp, -1.0, B.u64, B.v64, B.zpart, n_pad);
+}
+
+__global__ void __launch_bounds__(256) k_zmul_sum_b(const BSolve *bs, int which, int64_t n_pad)
+{
+    const BSolve &B = bs[blockIdx.y];
+    if (!zmul_gate(B, which)) return;
+    const int m = which == kZmulInit ? 0 : B.k;
+    const int ngroups = (m + kZmulColsPerGroup - 1) / kZmulColsPerGroup;
+    if (which == kZmulInit)
+        zmul_sum_body(B.zpart, 0, n_pad, B.used, B.y64, nullptr, B.r64, B.partials);
+    else if (which == kZmulStep)
+        zmul_sum_body(B.zpart, ngroups, n_pad, B.used, nullptr, nullptr, B.zv, B.partials);
+    else
+        zmul_sum_body(B.zpart, ngroups, n_pad, B.used, B.y64, B.r64, B.rc64, B.partials);
+}
+
+__global__ void k_init_objective_b(const BSolve *bs, int npart)
+{
+    const BSolve &B = bs[blockIdx.x];
+    if (B.sc->done || threadIdx.x != 0) return;
+    init_objective_body(B.sc, B.partials, npart);
+}
+
+__global__ void k_center_b(const BSolve *bs, int64_t n_pad, int init)
+{
+    const BSolve &B = bs[blockIdx.y];
+    const Scalars *sc = B.sc;
+    if (init) {
+        if (sc->done) return;
+        center_body(B.r64, B.r64, B.used, n_pad, sc, B.r32);
+    } else {
+        if (!sc->live || sc->done || sc->retry) return;
+        center_body(B.rc64, B.r64, B.used, n_pad, sc, B.r32);
+    }
+}
+
+__global__ void __launch_bounds__(kMergeThreads) k_merge_b(const BSolve *bs, int first, int npart)
+{
+    const BSolve &B = bs[blockIdx.x];
+    Scalars *sc = B.sc;
+    const int live = !sc->done && (first || sc->retry);
+    __syncthreads();   // flags read by every thread before thread 0 writes any
+    if (threadIdx.x == 0) sc->live = live;
+    if (!live) return;
+    MergeArgs A;
+    A.g = B.g;
+    A.S = B.S;
+    A.bS = B.bS;
+    A.cand = B.cand;
+    A.K = B.K;
+    A.partials = B.partials;
+    A.npart = npart;
+    A.first = first;
+    A.Sp = B.Sp;
+    A.bSp = B.bSp;
+    A.sc = sc;
+    merge_body(A);
+}
+
+__global__ void __launch_bounds__(256) k_decide_b(const BSolve *bs, int npart)
+{
+    const BSolve &B = bs[blockIdx.x];
+    Scalars *sc = B.sc;
+    if (!sc->live || sc->done) return;
+    decide_body(sc, B.partials, npart, B.S, B.bS, B.Sp, B.bSp, TraceDev{});
+}
+
+__global__ void k_scatter_beta_b(const BSolve *bs, int64_t p, double *__restrict__ betas)
+{
+    const BSolve &B = bs[blockIdx.y];
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c < B.k) betas[(int64_t)blockIdx.y * p + B.S[c]] = B.bS[c];
+}
+
+int launch_gather_gS_batch(iht_dataset *ds, const BSolve *bs, int nb)
+{
+    k_gather_gS_b<<<nb, 1024, 0, ds->ctx->stream>>>(bs);
+    note_launch();
+    IHT_CUDA(cudaGetLastError());
+    return IHT_OK;
+}
+
+int launch_zmul_batch(iht_dataset *ds, const BSolve *bs, int nb, int kmax, ZmulWhich which)
+{
+    cudaStream_t s = ds->ctx->stream;
+    if (which != kZmulInit) {
+        const int ngroups = std::max(1, (kmax + kZmulColsPerGroup - 1) / kZmulColsPerGroup);
+        dim3 grid(ceil_div(ds->stride, 256), ngroups, nb);
+        k_zmul_part_b<<<grid, 256, 0, s>>>(ds->G, ds->stride, ds->rowb, bs, (int)which, ds->n_pad);
+        note_launch();
+    }
+    k_zmul_sum_b<<<dim3(zmul_blocks(ds), nb), 256, 0, s>>>(bs, (int)which, ds->n_pad);
+    note_launch();
+    IHT_CUDA(cudaGetLastError());
+    return IHT_OK;
+}
+
+int launch_init_objective_batch(iht_dataset *ds, const BSolve *bs, int nb)
+{
+    k_init_objective_b<<<nb, 32, 0, ds->ctx->stream>>>(bs, zmul_blocks(ds));
+    note_launch();
+    IHT_CUDA(cudaGetLastError());
+    return IHT_OK;
+}
+
+int launch_center_batch(iht_dataset *ds, const BSolve *bs, int nb, bool init)
+{
+    k_center_b<<<dim3(ceil_div(ds->n_pad, 256), nb), 256, 0, ds->ctx->stream>>>(bs, ds->n_pad,
+                                                                              init ? 1 : 0);
+    note_launch();
+    IHT_CUDA(cudaGetLastError());
+    return IHT_OK;
+}
+
+int launch_merge_batch(iht_dataset *ds, const BSolve *bs, int nb, int first)
+{
+    static thread_local int configured_dev = -1;
+    const int smem = (int)sizeof(MergeShared);
+    if (configured_dev != ds->ctx->device) {
+        IHT_CUDA(cudaFuncSetAttribute(k_merge_b, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+        configured_dev = ds->ctx->device;
+    }
+    k_merge_b<<<nb, kMergeThreads, smem, ds->ctx->stream>>>(bs, first, zmul_blocks(ds));
+    note_launch();
+    IHT_CUDA(cudaGetLastError());
+    return IHT_OK;
+}
+
+int launch_decide_batch(iht_dataset *ds, const BSolve *bs, int nb)
+{
+    k_decide_b<<<nb, 256, 0, ds->ctx->stream>>>(bs, zmul_blocks(ds));
+    note_launch();
+    IHT_CUDA(cudaGetLastError());
+    return IHT_OK;
+}
+
+// betas (device, nb x p doubles, zero-filled by the caller): beta_S of each solve.
+int launch_scatter_beta_batch(iht_dataset *ds, const BSolve *bs, int nb, int kmax, double *betas)
+{
+    k_scatter_beta_b<<<dim3(ceil_div(kmax, 256), nb), 256, 0, ds->ctx->stream>>>(bs, ds->p, betas);
     note_launch();
     IHT_CUDA(cudaGetLastError());
     return IHT_OK;
