@@ -220,9 +220,10 @@ typedef struct iht_solve_desc {
  *   betas   : double[b][p] (opt->out_mem memory) or NULL.
  *   supports: int32[sum of k] concatenated in solve order (opt->out_mem).
  *   infos   : host iht_result[b], may be NULL.
- * Returns OK, EINVAL, ENOMEM, ECUDA; per-solve status (OK, ENOTCONV,
- * ENUMERIC) is in infos[c].status.  Identical row sets (same rows pointer and
- * n_rows) share one set of statistics. */
+ * Returns OK, EINVAL, ENOMEM, ETIMEOUT, ECUDA; per-solve status (OK,
+ * ENOTCONV, ENUMERIC) is in infos[c].status.  A solve whose y is not finite
+ * stops before its first step: beta row 0, support entries -1.  Identical
+ * row sets (same rows pointer and n_rows) share one set of statistics. */
 int iht_fit_batch(iht_dataset *ds, int32_t b, const iht_solve_desc *solves,
                   const iht_options *opt, double *betas, int32_t *supports, iht_result *infos);
 

@@ -399,6 +399,8 @@ int iht_fit_batch(iht_dataset *ds, int32_t b, const iht_solve_desc *solves,
     if ((rc = launch_center_batch(ds, w->bs, b, true))) return rc;
     active();
     if ((rc = grad(act))) return rc;
+    // solves stopped before S^0 (non-finite y, max_iter = 0) report support -1
+    IHT_CUDA(cudaMemsetAsync(w->S, 0xFF, sizeof(int32_t) * b * K, s));
     if ((rc = select_topk_batch(ds->ctx, w->jobs, b, ds->p))) return rc;
     IHT_CUDA(cudaMemsetAsync(w->bS, 0, sizeof(double) * b * K, s));
 
@@ -456,8 +458,10 @@ int iht_fit_batch(iht_dataset *ds, int32_t b, const iht_solve_desc *solves,
             memset(betas, 0, sizeof(double) * b * p);
             koff = 0;
             for (int c = 0; c < b; ++c) {
-                for (int t = 0; t < solves[c].k; ++t)
-                    betas[(size_t)c * p + supports[koff + t]] = bS[(size_t)c * K + t];
+                for (int t = 0; t < solves[c].k; ++t) {
+                    const int32_t j = supports[koff + t];
+                    if (j >= 0 && (size_t)j < p) betas[(size_t)c * p + j] = bS[(size_t)c * K + t];
+                }
                 koff += solves[c].k;
             }
         }

@@ -860,7 +860,9 @@ __global__ void k_scatter_beta_b(const BSolve *bs, int64_t p, double *__restrict
 {
     const BSolve &B = bs[blockIdx.y];
     const int c = blockIdx.x * blockDim.x + threadIdx.x;
-    if (c < B.k) betas[(int64_t)blockIdx.y * p + B.S[c]] = B.bS[c];
+    if (c >= B.k) return;
+    const int32_t j = B.S[c];
+    if (j >= 0 && j < p) betas[(int64_t)blockIdx.y * p + j] = B.bS[c];
 }
 
 int launch_gather_gS_batch(iht_dataset *ds, const BSolve *bs, int nb)
