@@ -2,7 +2,7 @@
 """Benchmark: IHT iterations/s on the single-solve panel (n=5000, p=500000, k=50).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                    [--config 1|2] [--grad-impl 0|1|2] [--no-cpu-baseline]
+                    [--config 1|2|3] [--grad-impl 0|1|2] [--no-cpu-baseline]
 
 One step = one full IHT least-squares solve (beta = 0 to convergence, every
 step of the hot path: standardised gradient, top-k projection, step size,
@@ -19,6 +19,11 @@ iterations of all ranks / max elapsed.
 
 ``--impl reference`` times the FP64 CPU oracle on the host cores (bounded
 sample of the same workload); on rank 0 only.
+
+``--config 3`` measures the batched cross-validation workload instead (n=6000,
+p=1000000, 5 folds x k = 1..20 = 100 solves in one iht_fit_batch call):
+one step = the whole batch to convergence, value = solves/s, beside the same
+100 solves run one at a time through iht_fit on the same GPU.
 """
 from __future__ import annotations
 
@@ -295,17 +300,220 @@ def ours_arm(args):
     return 0
 
 
+MR_PEAK_KEY = "bf16_tflops_sustained"      # kind::f16 runs at the BF16 rate
+FALLBACK_TFLOPS = 1400.0
+
+
+def measured_tensor_peak():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)[MR_PEAK_KEY]), "measured (bf16 sustained; F16 same rate)"
+    except (OSError, KeyError, ValueError):
+        return FALLBACK_TFLOPS, "fallback"
+
+
+def cv_setup(cfg):
+    c = synth.CONFIGS[cfg]
+    pn = synth.config_panel(cfg)
+    bed = pn.bed()
+    y, _, _ = synth.config_phenotype(cfg, pn)
+    lab = synth.cv_folds(pn.n, c["folds"], synth.BASE_SEED + 1000 * cfg + 7)
+    train = [np.flatnonzero(lab != f).astype(np.int32) for f in range(c["folds"])]
+    return c, pn, bed, y, train
+
+
+def cv_reference(args, c, pn, bed, y, train, iters_per_solve=None):
+    """Oracle on a bounded sample: one solve (fold 0, largest k) capped at a few iterations."""
+    import oracle
+    G = oracle.Geno.from_bed(bed, pn.n, pn.p)
+    cap = max(1, min(args.oracle_iters, 3))
+    t0 = time.perf_counter()
+    f = oracle.iht(G, y[train[0]], c["ks"][-1], rows=train[0], max_iter=cap, tol=c["tol"],
+                   trace=False)
+    dt = time.perf_counter() - t0
+    sec_per_iter = dt / max(f.iterations, 1)
+    ips = iters_per_solve if iters_per_solve else 10.0
+    return {"value": 1.0 / (sec_per_iter * ips), "unit": "solves/s", "cores": oracle.max_threads(),
+            "kind": "oracle",
+            "sample": f"FP64 oracle, fold 0 k={c['ks'][-1]} on {c['name']}, {f.iterations} iterations "
+                      f"(incl. setup) in {dt:.1f}s; solves/s extrapolated at {ips:.1f} iterations "
+                      f"per solve"}
+
+
+def cv_reference_arm(args):
+    rank, _, world = dist_env()
+    if rank != 0:
+        return 0
+    c, pn, bed, y, train = cv_setup(3)
+    for _ in range(args.warmup):
+        pass     # the oracle has no warm state: each step is a fresh bounded sample
+    vals = [cv_reference(args, c, pn, bed, y, train) for _ in range(max(args.steps, 1))]
+    value = statistics.median(v["value"] for v in vals)
+    cb = dict(vals[0])
+    cb["value"] = value
+    out = {"impl": "reference", "metric": "batched IHT solves/sec", "value": value,
+           "unit": "solves/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": 1e3 / value, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": c["name"], "n": c["n"], "p": c["p"], "folds": c["folds"],
+                      "ks": [c["ks"][0], c["ks"][-1]]},
+           "cpu_baseline": cb,
+           "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0,
+                   "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+    return 0
+
+
+def cv_arm(args):
+    import torch
+    import paper_1608_01398_b300 as iht
+
+    rank, local_rank, world = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device(f"cuda:{local_rank}"))
+    torch.cuda.set_device(local_rank)
+    dev = local_rank
+    t0 = time.perf_counter()
+    c, pn, bed, y, train = cv_setup(3)
+    n, p = c["n"], c["p"]
+    log(f"[bench] rank {rank}: generated {bed.nbytes / 1e6:.0f} MB panel in "
+        f"{time.perf_counter() - t0:.1f}s")
+    stream = torch.cuda.current_stream(dev)
+    ctx = iht.Context(dev, stream)
+    ds = iht.Dataset(ctx, bed, n, p)
+    cuda = f"cuda:{dev}"
+    tr_dev = [torch.from_numpy(t).to(cuda) for t in train]
+    y_dev = [torch.from_numpy(np.ascontiguousarray(y[t])).to(cuda) for t in train]
+    probs = [(y_dev[f], k, tr_dev[f]) for f in range(c["folds"]) for k in c["ks"]]
+    b = len(probs)
+    kw = dict(out_device=True, dense=False, grad_impl=args.grad_impl, tol=c["tol"],
+              max_iter=c["max_iter"])
+    for _ in range(max(args.warmup, 0)):
+        iht.iht_fit_batch(ds, probs, **kw)
+    torch.cuda.synchronize(dev)
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+
+    clocks = ClockSampler(gpu_uuid(torch, dev))
+    clocks.start()
+    time.sleep(0.3)
+    barrier()
+    torch.cuda.synchronize(dev)
+    l0 = iht.iht_kernel_launches()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    solves, its, cols, grad_ms, grad_n, statuses = 0, 0, 0, 0.0, 0, []
+    for _ in range(args.steps):
+        res = iht.iht_fit_batch(ds, probs, profile=1, **kw)
+        solves += b
+        its += sum(r.iterations for r in res)
+        cols += sum(max(r.iterations, 1) for r in res)
+        grad_ms += res[0].grad_ms
+        grad_n += res[0].grad_launches
+        statuses += [r.status for r in res]
+    ev1.record(stream)
+    torch.cuda.synchronize(dev)
+    barrier()
+    launches = iht.iht_kernel_launches() - l0
+    clk = clocks.stop()
+    elapsed = ev0.elapsed_time(ev1) / 1e3
+
+    # the same solves one at a time (plain single-solve GPU path), timed once
+    iht.iht_fit(ds, y_dev[0], c["ks"][0], rows=tr_dev[0], out_device=True)
+    torch.cuda.synchronize(dev)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    plain_its = 0
+    for (yy, k, rr) in probs:
+        plain_its += iht.iht_fit(ds, yy, k, rows=rr, out_device=True, grad_impl=args.grad_impl,
+                                 tol=c["tol"], max_iter=c["max_iter"]).iterations
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    plain_s = e0.elapsed_time(e1) / 1e3
+
+    # end to end through the host-buffer call: host y and rows in, supports and beta_S out
+    y_host = [np.ascontiguousarray(y[t]) for t in train]
+    probs_h = [(y_host[f], k, train[f]) for f in range(c["folds"]) for k in c["ks"]]
+    torch.cuda.synchronize(dev)
+    w0 = time.perf_counter()
+    for _ in range(args.steps):
+        iht.iht_fit_batch(ds, probs_h, dense=False, grad_impl=args.grad_impl, tol=c["tol"],
+                          max_iter=c["max_iter"])
+    torch.cuda.synchronize(dev)
+    e2e_wall = time.perf_counter() - w0
+
+    vals = torch.tensor([solves, elapsed, args.steps * b, e2e_wall], dtype=torch.float64,
+                        device=cuda)
+    if world > 1:
+        gathered = [torch.zeros_like(vals) for _ in range(world)]
+        torch.distributed.all_gather(gathered, vals)
+        allv = torch.stack(gathered).cpu().numpy()
+    else:
+        allv = vals.cpu().numpy()[None, :]
+    if rank == 0:
+        value = float(allv[:, 0].sum()) / float(allv[:, 1].max())
+        e2e_value = float(allv[:, 2].sum()) / float(allv[:, 3].max())
+        peak, peak_kind = measured_tensor_peak()
+        n_k = 4 * ((((n + 3) // 4) + 15) // 16) * 16     # samples of the contraction (K-steps x 16)
+        flops = 2.0 * n * p * 2 * cols                     # X0^T [r_hi | r_lo] over all passes
+        achieved = flops / (grad_ms / 1e3) / 1e12 if grad_ms > 0 else None
+        ktot = sum(c["ks"]) * c["folds"]
+        h2d = sum(8 * t.size * len(c["ks"]) + 4 * t.size for t in train)   # y per solve, rows per fold
+        out = {
+            "metric": "batched IHT solves/sec", "value": value, "unit": "solves/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * float(allv[:, 1].max()) / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f16 operands, f32 accumulate, f64 scalars",
+            "data": "synthetic",
+            "config": {"workload": c["name"], "n": n, "p": p, "folds": c["folds"],
+                       "ks": [c["ks"][0], c["ks"][-1]], "solves_per_step": b,
+                       "iterations_per_solve": its / max(solves, 1),
+                       "grad_impl": args.grad_impl, "l2": "inputs larger than L2 (no flush)",
+                       "parallelism": "replicas" if world > 1 else "single"},
+            "plain": {"value": b / plain_s, "unit": "solves/s",
+                      "what": "the same 100 solves one at a time through iht_fit (single-column path)",
+                      "iterations": plain_its},
+            "speedup_vs_plain": value / (b / plain_s),
+            "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                         "frac": (achieved / peak) if achieved else None, "traffic": None,
+                         "kernel": "multi-column gradient pass (k_grad_mrhs)",
+                         "peak_source": peak_kind,
+                         "algorithmic_flops": "2 n p per residual limb column, two limb columns "
+                                              "(hi, lo) per solve",
+                         "columns_total": cols, "launches": grad_n,
+                         "ms_per_launch": grad_ms / max(grad_n, 1), "contraction_samples": n_k},
+            "e2e": {"value": e2e_value, "unit": "solves/s", "h2d_bytes_per_step": int(h2d),
+                    "d2h_bytes_per_step": int(12 * ktot)},
+            "gpu_launches": int(launches), "clocks": clk,
+            "statuses": sorted(set(int(s) for s in statuses)),
+        }
+        if not args.no_cpu_baseline and world == 1:
+            out["cpu_baseline"] = cv_reference(args, c, pn, bed, y, train, its / max(solves, 1))
+        print(json.dumps(out), flush=True)
+    del ds, ctx
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--config", type=int, default=2, choices=[1, 2])
+    ap.add_argument("--config", type=int, default=2, choices=[1, 2, 3])
     ap.add_argument("--grad-impl", type=int, default=0, choices=[0, 1, 2])
     ap.add_argument("--oracle-iters", type=int, default=10)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
+    if args.config == 3:
+        return cv_reference_arm(args) if args.impl == "reference" else cv_arm(args)
     if args.impl == "reference":
         return reference_arm(args)
     return ours_arm(args)

@@ -217,15 +217,19 @@ typedef struct iht_solve_desc {
  * gradient of all active solves is one multi-right-hand-side pass per
  * iteration, and every other step runs batched.  Solves retire independently.
  *   solves  : host array of b descriptors (rows, y in opt->in_mem memory).
- *   betas   : double[b][p] (opt->out_mem memory) or NULL.
+ *   betas   : double[b][p] dense coefficients (opt->out_mem memory) or NULL.
  *   supports: int32[sum of k] concatenated in solve order (opt->out_mem).
- *   infos   : host iht_result[b], may be NULL.
+ *   beta_s  : double[sum of k] beta on each support, aligned with supports
+ *             (opt->out_mem), or NULL.
+ *   infos   : host iht_result[b], may be NULL; with opt->profile, grad_ms and
+ *             grad_launches describe the batch's multi-column passes.
  * Returns OK, EINVAL, ENOMEM, ETIMEOUT, ECUDA; per-solve status (OK,
  * ENOTCONV, ENUMERIC) is in infos[c].status.  A solve whose y is not finite
  * stops before its first step: beta row 0, support entries -1.  Identical
  * row sets (same rows pointer and n_rows) share one set of statistics. */
 int iht_fit_batch(iht_dataset *ds, int32_t b, const iht_solve_desc *solves,
-                  const iht_options *opt, double *betas, int32_t *supports, iht_result *infos);
+                  const iht_options *opt, double *betas, int32_t *supports, double *beta_s,
+                  iht_result *infos);
 
 /* a7 -- multi-right-hand-side standardised gradient G = Z^T R for b residual
  * columns, each with its own row set and statistics (exposes the batched

@@ -104,7 +104,7 @@ def _lib(build_if_stale: bool = True):
         "iht_fit_trace": (ctypes.c_int, [P, P, i64, P, i32, ctypes.POINTER(iht_options), P, P,
                                          ctypes.POINTER(iht_result), ctypes.POINTER(iht_trace)]),
         "iht_fit_batch": (ctypes.c_int, [P, i32, ctypes.POINTER(iht_solve_desc),
-                                         ctypes.POINTER(iht_options), P, P,
+                                         ctypes.POINTER(iht_options), P, P, P,
                                          ctypes.POINTER(iht_result)]),
         "iht_gradient_batch": (ctypes.c_int, [P, i32, ctypes.POINTER(P), ctypes.POINTER(i64), P, P,
                                               ctypes.c_int]),
@@ -289,6 +289,7 @@ class FitResult:
     trace: dict | None = None
     grad_ms: float = 0.0
     grad_launches: int = 0
+    beta_s: object = None
 
 
 def _fit(ds: Dataset, y, k: int, rows, opts: iht_options, trace: bool):
@@ -354,13 +355,15 @@ def iht_fit_trace(ds: Dataset, y, k: int, rows=None, **opt) -> FitResult:
     return _fit(ds, y, k, rows, o, trace=True)
 
 
-def iht_fit_batch(ds: Dataset, problems, out_device: bool = False, **opt) -> list:
+def iht_fit_batch(ds: Dataset, problems, out_device: bool = False, dense: bool = True,
+                  **opt) -> list:
     """b solves sharing the genotype passes (iht_fit_batch).
 
     problems: sequence of (y, k, rows); y and rows numpy arrays (host inputs)
     or CUDA tensors (device inputs), all of the same kind; rows None = all n.
     The same rows object in several problems is one row set (statistics
-    computed once).  Returns one FitResult per problem.
+    computed once).  Returns one FitResult per problem with the support, beta
+    on it (beta_s) and, when dense, the full coefficient vector (beta).
     """
     torch = _torch()
     o = iht_default_options(**opt)
@@ -400,22 +403,28 @@ def iht_fit_batch(ds: Dataset, problems, out_device: bool = False, **opt) -> lis
         ks.append(int(k))
     ktot = sum(ks)
     if out_device:
-        betas = torch.empty((b, ds.p), dtype=torch.float64, device=f"cuda:{ds.ctx.device}")
-        supp = torch.empty(ktot, dtype=torch.int32, device=f"cuda:{ds.ctx.device}")
-        bp, sp = betas.data_ptr(), supp.data_ptr()
+        dev = f"cuda:{ds.ctx.device}"
+        betas = torch.empty((b, ds.p), dtype=torch.float64, device=dev) if dense else None
+        supp = torch.empty(ktot, dtype=torch.int32, device=dev)
+        bsv = torch.empty(ktot, dtype=torch.float64, device=dev)
+        bp = None if betas is None else betas.data_ptr()
+        sp, vp = supp.data_ptr(), bsv.data_ptr()
     else:
-        betas = np.empty((b, ds.p))
+        betas = np.empty((b, ds.p)) if dense else None
         supp = np.empty(ktot, dtype=np.int32)
-        bp, sp = betas.ctypes.data, supp.ctypes.data
+        bsv = np.empty(ktot)
+        bp = None if betas is None else betas.ctypes.data
+        sp, vp = supp.ctypes.data, bsv.ctypes.data
     infos = (iht_result * b)()
     rc = _lib().iht_fit_batch(ds.h, b, descs, ctypes.byref(o), ctypes.c_void_p(bp),
-                              ctypes.c_void_p(sp), infos)
+                              ctypes.c_void_p(sp), ctypes.c_void_p(vp), infos)
     _check(rc, "iht_fit_batch")
     out, off = [], 0
     for c in range(b):
         r = infos[c]
-        out.append(FitResult(betas[c], supp[off:off + ks[c]], r.iterations, r.status, r.backtracks,
-                             r.objective, r.mu, None, r.grad_ms, r.grad_launches))
+        out.append(FitResult(None if betas is None else betas[c], supp[off:off + ks[c]],
+                             r.iterations, r.status, r.backtracks, r.objective, r.mu, None,
+                             r.grad_ms, r.grad_launches, bsv[off:off + ks[c]]))
         off += ks[c]
     return out
 

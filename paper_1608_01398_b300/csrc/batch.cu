@@ -216,7 +216,7 @@ static int build_sets(iht_dataset *ds, BatchWork *w, const std::vector<SetKey> &
 // Gradient of the listed solves (impl 0/2: one multi-column pass; 1: one
 // CUDA-core pass per solve).
 static int batch_grad(iht_dataset *ds, BatchWork *w, const std::vector<int> &act,
-                      const std::vector<int> &set_of, int impl)
+                      const std::vector<int> &set_of, int impl, ProfEvents *prof = nullptr)
 {
     cudaStream_t s = ds->ctx->stream;
     const size_t np = (size_t)ds->n_pad, p = (size_t)ds->p;
@@ -224,7 +224,9 @@ static int batch_grad(iht_dataset *ds, BatchWork *w, const std::vector<int> &act
     if (impl == 1) {
         for (int c : act) {
             const RowSet rs = batch_rowset(ds, w, set_of[c]);
+            prof_begin(prof, s);
             int rc = launch_grad_simt_stats(ds, w->r32 + c * np, rs.u32, rs.v32, w->g + c * p);
+            prof_end(prof, s);
             if (rc) return rc;
         }
         return IHT_OK;
@@ -242,7 +244,7 @@ static int batch_grad(iht_dataset *ds, BatchWork *w, const std::vector<int> &act
     }
     IHT_CUDA(cudaMemcpyAsync(w->cols, w->cols_host, sizeof(MrCol) * act.size(),
                              cudaMemcpyHostToDevice, s));
-    return launch_grad_mrhs(ds, w->cols, (int)act.size());
+    return launch_grad_mrhs(ds, w->cols, (int)act.size(), prof);
 }
 
 }  // namespace iht
@@ -252,7 +254,8 @@ using namespace iht;
 extern "C" {
 
 int iht_fit_batch(iht_dataset *ds, int32_t b, const iht_solve_desc *solves,
-                  const iht_options *opt_in, double *betas, int32_t *supports, iht_result *infos)
+                  const iht_options *opt_in, double *betas, int32_t *supports, double *beta_s,
+                  iht_result *infos)
 {
     iht_options opt;
     if (opt_in)
@@ -305,7 +308,7 @@ int iht_fit_batch(iht_dataset *ds, int32_t b, const iht_solve_desc *solves,
 
     // phenotypes, finite check, per-solve state
     IHT_CUDA(cudaMemsetAsync(w->sc, 0, sizeof(Scalars) * b, s));
-    int64_t yoff = 0;
+    int64_t yoff = 0, koff = 0;
     for (int c = 0; c < b; ++c) {
         const iht_solve_desc &d = solves[c];
         const int64_t nr = d.rows ? d.n_rows : ds->n;
@@ -356,6 +359,8 @@ int iht_fit_batch(iht_dataset *ds, int32_t b, const iht_solve_desc *solves,
         B.zpart = w->zpart + (size_t)c * kgroups(w->kcap) * np;
         B.k = solves[c].k;
         B.K = (int32_t)std::min<int64_t>(2 * (int64_t)solves[c].k, ds->p);
+        B.out_off = koff;
+        koff += B.k;
         for (int t = 0; t < 2; ++t) {            // t = 0: S^0 = top-k; t = 1: candidates
             SelJob &J = w->jobs_host[t * b + c];
             J.keys = B.g;
@@ -374,17 +379,11 @@ int iht_fit_batch(iht_dataset *ds, int32_t b, const iht_solve_desc *solves,
     const bool prof = opt.profile != 0;
     if (prof && !w->ev[0])
         for (int e = 0; e < 2 * kProfEvents; ++e) IHT_CUDA(cudaEventCreate(&w->ev[e]));
-    int nprof = 0;
+    ProfEvents pe;
+    pe.ev = w->ev;
+    pe.cap = prof ? kProfEvents : 0;
     auto grad = [&](const std::vector<int> &act) -> int {
-        const bool rec = prof && nprof < kProfEvents;
-        if (rec) IHT_CUDA(cudaEventRecord(w->ev[2 * nprof], s));
-        int r = batch_grad(ds, w, act, set_of, opt.grad_impl);
-        if (r) return r;
-        if (rec) {
-            IHT_CUDA(cudaEventRecord(w->ev[2 * nprof + 1], s));
-            ++nprof;
-        }
-        return IHT_OK;
+        return batch_grad(ds, w, act, set_of, opt.grad_impl, prof ? &pe : nullptr);
     };
 
     std::vector<int> act;
@@ -426,43 +425,40 @@ int iht_fit_batch(iht_dataset *ds, int32_t b, const iht_solve_desc *solves,
     if (opt.grad_impl != 1 && (rc = grad_mrhs_status(ds, &timed_out))) return rc;
     if (timed_out) return IHT_ETIMEOUT;
     double grad_ms = 0.0;
+    const int nprof = pe.n;
     for (int e = 0; prof && e < nprof; ++e) {
         float ms = 0.0f;
         IHT_CUDA(cudaEventElapsedTime(&ms, w->ev[2 * e], w->ev[2 * e + 1]));
         grad_ms += ms;
     }
 
-    // outputs
-    size_t koff = 0;
+    // outputs: supports / beta_S concatenated in solve order (koff entries), dense betas
     if (opt.out_mem == IHT_DEVICE) {
         if (betas) {
             IHT_CUDA(cudaMemsetAsync(betas, 0, sizeof(double) * b * p, s));
             if ((rc = launch_scatter_beta_batch(ds, w->bs, b, kmax, betas))) return rc;
         }
-        for (int c = 0; c < b; ++c) {
-            IHT_CUDA(cudaMemcpyAsync(supports + koff, w->S + c * K, sizeof(int32_t) * solves[c].k,
-                                     cudaMemcpyDeviceToDevice, s));
-            koff += solves[c].k;
-        }
+        if ((rc = launch_compact_support_batch(ds, w->bs, b, kmax, supports, beta_s))) return rc;
         IHT_CUDA(cudaStreamSynchronize(s));
     } else {
-        std::vector<double> bS((size_t)b * K);
-        for (int c = 0; c < b; ++c) {
-            IHT_CUDA(cudaMemcpyAsync(supports + koff, w->S + c * K, sizeof(int32_t) * solves[c].k,
-                                     cudaMemcpyDeviceToHost, s));
-            koff += solves[c].k;
-        }
-        IHT_CUDA(cudaMemcpyAsync(bS.data(), w->bS, sizeof(double) * b * K, cudaMemcpyDeviceToHost, s));
+        // compacted on the device (into the candidate scratch), then one copy each
+        int32_t *sup_dev = w->cand;                               // >= sum of k entries
+        double *bs_dev = w->coef;
+        if ((rc = launch_compact_support_batch(ds, w->bs, b, kmax, sup_dev, bs_dev))) return rc;
+        std::vector<double> bsh(beta_s ? 0 : (size_t)koff);
+        double *bdst = beta_s ? beta_s : bsh.data();
+        IHT_CUDA(cudaMemcpyAsync(supports, sup_dev, sizeof(int32_t) * koff, cudaMemcpyDeviceToHost, s));
+        IHT_CUDA(cudaMemcpyAsync(bdst, bs_dev, sizeof(double) * koff, cudaMemcpyDeviceToHost, s));
         IHT_CUDA(cudaStreamSynchronize(s));
         if (betas) {
             memset(betas, 0, sizeof(double) * b * p);
-            koff = 0;
+            int64_t o = 0;
             for (int c = 0; c < b; ++c) {
                 for (int t = 0; t < solves[c].k; ++t) {
-                    const int32_t j = supports[koff + t];
-                    if (j >= 0 && (size_t)j < p) betas[(size_t)c * p + j] = bS[(size_t)c * K + t];
+                    const int32_t j = supports[o + t];
+                    if (j >= 0 && (size_t)j < p) betas[(size_t)c * p + j] = bdst[o + t];
                 }
-                koff += solves[c].k;
+                o += solves[c].k;
             }
         }
     }

@@ -65,7 +65,26 @@ struct BSolve {
     double *partials;                  // 3 * zmul blocks
     double *zpart;                     // ceil(k / 4) * n_pad
     int32_t k, K;
+    int64_t out_off;                   // offset of this solve in concatenated outputs
 };
+
+// Optional CUDA-event timing of selected launches (pairs begin / end).
+struct ProfEvents {
+    cudaEvent_t *ev = nullptr;
+    int cap = 0;                       // pairs available
+    int n = 0;                         // pairs recorded
+};
+inline void prof_begin(ProfEvents *pe, cudaStream_t s)
+{
+    if (pe && pe->n < pe->cap) cudaEventRecord(pe->ev[2 * pe->n], s);
+}
+inline void prof_end(ProfEvents *pe, cudaStream_t s)
+{
+    if (pe && pe->n < pe->cap) {
+        cudaEventRecord(pe->ev[2 * pe->n + 1], s);
+        ++pe->n;
+    }
+}
 
 struct SelState {                      // radix select progress
     uint32_t prefix, mask, need, count_gt;
@@ -220,7 +239,7 @@ struct MrCol {
 };
 int mrhs_max_cols();
 bool grad_mrhs_supported(const iht_dataset *ds);
-int launch_grad_mrhs(iht_dataset *ds, MrCol *cols_dev, int ncols);
+int launch_grad_mrhs(iht_dataset *ds, MrCol *cols_dev, int ncols, ProfEvents *prof = nullptr);
 int grad_mrhs_status(iht_dataset *ds, int *timed_out);
 // select.cu
 struct SelJob {                        // one problem of a batched top-K
@@ -258,6 +277,8 @@ int launch_center_batch(iht_dataset *ds, const BSolve *bs, int nb, bool init);
 int launch_merge_batch(iht_dataset *ds, const BSolve *bs, int nb, int first);
 int launch_decide_batch(iht_dataset *ds, const BSolve *bs, int nb);
 int launch_scatter_beta_batch(iht_dataset *ds, const BSolve *bs, int nb, int kmax, double *betas);
+int launch_compact_support_batch(iht_dataset *ds, const BSolve *bs, int nb, int kmax,
+                                 int32_t *supports, double *beta_s);
 
 // device helpers ------------------------------------------------------------
 __device__ __forceinline__ float warp_sum(float x)

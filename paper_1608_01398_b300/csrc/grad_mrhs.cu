@@ -298,46 +298,61 @@ __global__ void __launch_bounds__(kMrThreads, 1) k_grad_mrhs(
     const int spt = (ksteps + 15) / 16;                 // genotype stages per tile (16 K-steps each)
     const int cpt = ksteps / kMrChunkSteps;             // B chunks per tile
 
+    // Ring positions advance by increment and compare (slot, phase bit): the
+    // single-thread roles issue work every few hundred cycles, so no division
+    // or modulo sits on their path.
     if (tid < kMrDecoders) {
         // ------------------------------------------------------- decoders + epilogue
         const int t = warp >> 2, r = tid & 127;
         const uint32_t lane_off = (uint32_t)((warp & 3) * 32) << 16;
         const uint32_t tb = tmem_base + (uint32_t)(256 * t) + lane_off;
         const uint32_t abase = tb + (uint32_t)N;
-        uint32_t kst = 0, abuf = 0;
+        const int swz = (r >> 1) & 3;
+        uint32_t gslot = 0, gphase = 0;           // genotype stage ring
+        uint32_t aslot = 0, aphase = 0, aused = 0; // A buffer ring (aused: buffers filled so far, capped)
         int T = 0;
         bool ok = true;
         for (int64_t tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x, ++T) {
-            for (int st = 0; st < spt && ok; ++st, ++kst) {
-                const uint32_t slot = kst % kMrGStages;
-                if (!mr_wait(&pipe.gfull[slot], (kst / kMrGStages) & 1u)) {
+            int left = ksteps;                      // K-steps of this tile still to decode
+            for (int st = 0; st < spt && ok; ++st) {
+                if (!mr_wait(&pipe.gfull[gslot], gphase)) {
                     abort_flag = 1;
                     ok = false;
                     break;
                 }
-                const uint8_t *rowp = gst + (slot * kMrTiles + t) * kMrGTile + r * kMrGStageBytes;
-                const int nb = min(8, (ksteps - st * 16) / 2);
-                for (int q8 = 0; q8 < nb; ++q8, ++abuf) {
-                    const uint32_t buf = abuf % (uint32_t)nbufs;
-                    if (abuf >= (uint32_t)nbufs) {
-                        if (!mr_wait(&pipe.aempty[buf], ((abuf / nbufs) - 1) & 1u)) {
+                const uint8_t *rowp = gst + (gslot * kMrTiles + t) * kMrGTile + r * kMrGStageBytes;
+                const int nb = min(8, left >> 1);
+                left -= 2 * nb;
+                for (int q8 = 0; q8 < nb; ++q8) {
+                    if (aused >= (uint32_t)nbufs) {
+                        if (!mr_wait(&pipe.aempty[aslot], aphase ^ 1u)) {
                             abort_flag = 1;
                             ok = false;
                             break;
                         }
                         mr_fence_after();
+                    } else {
+                        ++aused;
                     }
                     const uint2 x = *reinterpret_cast<const uint2 *>(
-                        rowp + ((((q8 >> 1) ^ ((r >> 1) & 3))) << 4) + (q8 & 1) * 8);
+                        rowp + (((q8 >> 1) ^ swz) << 4) + (q8 & 1) * 8);
                     uint32_t v[16];
                     mr_decode(x.x, &v[0]);
                     mr_decode(x.y, &v[8]);
-                    mr_st16(abase + 16u * buf, v);
+                    mr_st16(abase + 16u * aslot, v);
                     asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
                     mr_fence_before();
-                    mr_arrive(&pipe.afull[buf]);
+                    mr_arrive(&pipe.afull[aslot]);
+                    if (++aslot == (uint32_t)nbufs) {
+                        aslot = 0;
+                        aphase ^= 1u;
+                    }
                 }
-                mr_arrive(&pipe.gempty[slot]);
+                mr_arrive(&pipe.gempty[gslot]);
+                if (++gslot == kMrGStages) {
+                    gslot = 0;
+                    gphase ^= 1u;
+                }
                 if (abort_flag) ok = false;
             }
             if (!ok) break;
@@ -368,7 +383,7 @@ __global__ void __launch_bounds__(kMrThreads, 1) k_grad_mrhs(
     } else if (warp == kMrMmaWarp) {
         // ------------------------------------------------------- MMA issuer
         if (lane == 0) {
-            uint32_t abuf = 0, bq = 0;
+            uint32_t aslot = 0, aphase = 0, bslot = 0, bphase = 0;
             int T = 0;
             bool ok = true;
             const uint32_t b0 = mr_smem(bst);
@@ -377,32 +392,36 @@ __global__ void __launch_bounds__(kMrThreads, 1) k_grad_mrhs(
                     if (!mr_wait(&pipe.accempty, (uint32_t)(T - 1) & 1u)) { abort_flag = 1; break; }
                     mr_fence_after();
                 }
-                uint32_t bslot = 0;
-                for (int s = 0; s < ksteps; ++s) {
-                    const int sc = s % kMrChunkSteps;
-                    if (sc == 0) {
-                        bslot = bq % (uint32_t)nbst;
-                        if (!mr_wait(&pipe.bfull[bslot], (bq / nbst) & 1u)) { abort_flag = 1; ok = false; break; }
-                    }
-                    const uint32_t buf = abuf % (uint32_t)nbufs;
-                    if ((s & 1) == 0) {
-                        if (!mr_wait(&pipe.afull[buf], (abuf / nbufs) & 1u)) { abort_flag = 1; ok = false; break; }
-                        mr_fence_after();
-                    }
-                    const uint64_t bd = mr_b_desc(b0 + bslot * chunk_bytes + (uint32_t)sc * step_bytes);
+                for (int ch = 0; ch < cpt && ok; ++ch) {
+                    if (!mr_wait(&pipe.bfull[bslot], bphase)) { abort_flag = 1; ok = false; break; }
+                    uint32_t baddr = b0 + bslot * chunk_bytes;
 #pragma unroll
-                    for (int t = 0; t < kMrTiles; ++t) {
-                        const uint32_t tb = tmem_base + (uint32_t)(256 * t);
-                        mr_mma(tb, tb + (uint32_t)N + 16u * buf + 8u * (uint32_t)(s & 1), bd, idesc,
-                               s > 0 ? 1u : 0u);
+                    for (int h = 0; h < kMrChunkSteps / 2; ++h) {     // two A buffers per chunk
+                        if (!mr_wait(&pipe.afull[aslot], aphase)) { abort_flag = 1; ok = false; break; }
+                        mr_fence_after();
+#pragma unroll
+                        for (int s2 = 0; s2 < 2; ++s2) {
+                            const uint64_t bd = mr_b_desc(baddr);
+                            const uint32_t acc = (ch | h | s2) ? 1u : 0u;
+#pragma unroll
+                            for (int t = 0; t < kMrTiles; ++t) {
+                                const uint32_t tb = tmem_base + (uint32_t)(256 * t);
+                                mr_mma(tb, tb + (uint32_t)N + 16u * aslot + 8u * (uint32_t)s2, bd, idesc,
+                                       acc);
+                            }
+                            baddr += step_bytes;
+                        }
+                        mr_commit(&pipe.aempty[aslot]);
+                        if (++aslot == (uint32_t)nbufs) {
+                            aslot = 0;
+                            aphase ^= 1u;
+                        }
                     }
-                    if (s & 1) {
-                        mr_commit(&pipe.aempty[buf]);
-                        ++abuf;
-                    }
-                    if (sc == kMrChunkSteps - 1) {
-                        mr_commit(&pipe.bempty[bslot]);
-                        ++bq;
+                    if (!ok) break;
+                    mr_commit(&pipe.bempty[bslot]);
+                    if (++bslot == (uint32_t)nbst) {
+                        bslot = 0;
+                        bphase ^= 1u;
                     }
                 }
                 if (!ok) break;
@@ -414,46 +433,57 @@ __global__ void __launch_bounds__(kMrThreads, 1) k_grad_mrhs(
     } else if (warp == kMrGWarp) {
         // ------------------------------------------------------- genotype tiles (TMA)
         if (lane == 0) {
-            const int64_t my = blockIdx.x < ntiles ? (ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
-            const int64_t total = my * spt;
-            int64_t k = 0;
-            for (; k < total && !abort_flag; ++k) {
-                const uint32_t slot = (uint32_t)(k % kMrGStages);
-                if (k >= kMrGStages &&
-                    !mr_wait(&pipe.gempty[slot], (uint32_t)((k / kMrGStages) - 1) & 1u)) {
-                    abort_flag = 1;
-                    break;
-                }
-                const int64_t tile = blockIdx.x + (k / spt) * gridDim.x;
-                const int st = (int)(k % spt);
-                mr_expect_tx(&pipe.gfull[slot], (uint32_t)(kMrTiles * kMrGTile));
+            uint32_t slot = 0, phase = 0;
+            int64_t issued = 0;
+            bool ok = true;
+            for (int64_t tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
+                const int y0 = (int)(tile * (128 * kMrTiles));
+                for (int st = 0; st < spt; ++st, ++issued) {
+                    if (abort_flag || (issued >= kMrGStages && !mr_wait(&pipe.gempty[slot], phase ^ 1u))) {
+                        abort_flag = 1;
+                        ok = false;
+                        break;
+                    }
+                    mr_expect_tx(&pipe.gfull[slot], (uint32_t)(kMrTiles * kMrGTile));
 #pragma unroll
-                for (int t = 0; t < kMrTiles; ++t)
-                    mr_tma_2d(gst + (slot * kMrTiles + t) * kMrGTile, &gmap, st * kMrGStageBytes,
-                              (int)(tile * (128 * kMrTiles) + 128 * t), &pipe.gfull[slot]);
+                    for (int t = 0; t < kMrTiles; ++t)
+                        mr_tma_2d(gst + (slot * kMrTiles + t) * kMrGTile, &gmap, st * kMrGStageBytes,
+                                  y0 + 128 * t, &pipe.gfull[slot]);
+                    if (++slot == kMrGStages) {
+                        slot = 0;
+                        phase ^= 1u;
+                    }
+                }
             }
-            for (int64_t q = k - kMrGStages; q < k; ++q)     // copies in flight (after an abort)
+            // copies still in flight after an abort: wait for them (bounded)
+            for (int64_t q = issued - kMrGStages; q < issued; ++q)
                 if (q >= 0) mr_wait(&pipe.gfull[q % kMrGStages], (uint32_t)(q / kMrGStages) & 1u);
         }
         __syncwarp();
     } else {
         // ------------------------------------------------------- B chunks (bulk copies)
         if (lane == 0) {
-            const int64_t my = blockIdx.x < ntiles ? (ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
-            const int64_t total = my * cpt;
-            int64_t k = 0;
-            for (; k < total && !abort_flag; ++k) {
-                const uint32_t slot = (uint32_t)(k % nbst);
-                if (k >= nbst && !mr_wait(&pipe.bempty[slot], (uint32_t)((k / nbst) - 1) & 1u)) {
-                    abort_flag = 1;
-                    break;
+            uint32_t slot = 0, phase = 0;
+            int64_t issued = 0;
+            bool ok = true;
+            for (int64_t tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
+                const uint8_t *src = bimg;
+                for (int ch = 0; ch < cpt; ++ch, ++issued) {
+                    if (abort_flag || (issued >= nbst && !mr_wait(&pipe.bempty[slot], phase ^ 1u))) {
+                        abort_flag = 1;
+                        ok = false;
+                        break;
+                    }
+                    mr_expect_tx(&pipe.bfull[slot], chunk_bytes);
+                    mr_bulk(bst + slot * chunk_bytes, src, chunk_bytes, &pipe.bfull[slot]);
+                    src += chunk_bytes;
+                    if (++slot == (uint32_t)nbst) {
+                        slot = 0;
+                        phase ^= 1u;
+                    }
                 }
-                const int ch = (int)(k % cpt);
-                mr_expect_tx(&pipe.bfull[slot], chunk_bytes);
-                mr_bulk(bst + slot * chunk_bytes, bimg + (size_t)ch * chunk_bytes, chunk_bytes,
-                        &pipe.bfull[slot]);
             }
-            for (int64_t q = k - nbst; q < k; ++q)
+            for (int64_t q = issued - nbst; q < issued; ++q)
                 if (q >= 0) mr_wait(&pipe.bfull[q % nbst], (uint32_t)(q / nbst) & 1u);
         }
         __syncwarp();
@@ -638,7 +668,7 @@ static int mr_finalize(iht_dataset *ds, const MrCol *cols, int ncols)
 
 // G of ncols residual columns (cols: device array; r32, u32, v32 and g set by
 // the caller).  Passes of at most kMrMaxCols columns.
-int launch_grad_mrhs(iht_dataset *ds, MrCol *cols, int ncols)
+int launch_grad_mrhs(iht_dataset *ds, MrCol *cols, int ncols, ProfEvents *prof)
 {
     if (ncols <= 0) return IHT_OK;
     if (!grad_mrhs_supported(ds)) return IHT_EINVAL;
@@ -681,8 +711,10 @@ int launch_grad_mrhs(iht_dataset *ds, MrCol *cols, int ncols)
         // at least 116 KB, so one CTA per SM: the kernel allocates all 512 columns of tensor memory
         const size_t smem = std::max<size_t>(116 * 1024, mr_gbytes() + (size_t)nbst * kMrChunkSteps * N * 32);
         const uint32_t idesc = (1u << 4) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
+        prof_begin(prof, s);
         k_grad_mrhs<<<grid, kMrThreads, smem, s>>>(map, ds->p, ksteps, N, nc, nbufs, nbst, w.bimg,
                                                     cols + c0, idesc, w.err);
+        prof_end(prof, s);
         note_launch(2);
         IHT_CUDA(cudaGetLastError());
         rc = ds->miss_idx16 ? mr_finalize<uint16_t>(ds, cols + c0, nc)

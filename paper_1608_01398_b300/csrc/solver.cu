@@ -865,6 +865,26 @@ __global__ void k_scatter_beta_b(const BSolve *bs, int64_t p, double *__restrict
     if (j >= 0 && j < p) betas[(int64_t)blockIdx.y * p + j] = B.bS[c];
 }
 
+__global__ void k_compact_support_b(const BSolve *bs, int32_t *__restrict__ supports,
+                                    double *__restrict__ beta_s)
+{
+    const BSolve &B = bs[blockIdx.y];
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= B.k) return;
+    if (supports) supports[B.out_off + c] = B.S[c];
+    if (beta_s) beta_s[B.out_off + c] = B.bS[c];
+}
+
+int launch_compact_support_batch(iht_dataset *ds, const BSolve *bs, int nb, int kmax,
+                                 int32_t *supports, double *beta_s)
+{
+    k_compact_support_b<<<dim3(ceil_div(kmax, 256), nb), 256, 0, ds->ctx->stream>>>(bs, supports,
+                                                                                  beta_s);
+    note_launch();
+    IHT_CUDA(cudaGetLastError());
+    return IHT_OK;
+}
+
 int launch_gather_gS_batch(iht_dataset *ds, const BSolve *bs, int nb)
 {
     k_gather_gS_b<<<nb, 1024, 0, ds->ctx->stream>>>(bs);

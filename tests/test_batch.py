@@ -203,10 +203,15 @@ def test_fit_batch_status_and_io(iht, ctx):
     yd = torch.from_numpy(y).cuda()
     b = iht.iht_fit_batch(ds, [(yd, 5, None), (yd, 8, None)], out_device=True)
     c = iht.iht_fit_batch(ds, [(y, 5, None), (y, 8, None)])
+    d = iht.iht_fit_batch(ds, [(yd, 5, None), (yd, 8, None)], out_device=True, dense=False)
     for i in range(2):
         assert np.array_equal(a[i].beta, b[i].beta.cpu().numpy())
         assert np.array_equal(a[i].support, b[i].support.cpu().numpy())
         assert np.array_equal(a[i].beta, c[i].beta)
+        assert np.array_equal(a[i].beta[a[i].support], a[i].beta_s)
+        assert d[i].beta is None
+        assert np.array_equal(d[i].support.cpu().numpy(), a[i].support)
+        assert np.array_equal(d[i].beta_s.cpu().numpy(), a[i].beta_s)
 
 
 def test_fit_batch_matches_single_solves(iht, ctx):
