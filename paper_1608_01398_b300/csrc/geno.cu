@@ -319,7 +319,8 @@ int build_missing_lists(iht_dataset *ds)
     ds->miss_total = ho[p];
     e = cudaMalloc(&ds->miss_off, sizeof(int64_t) * (p + 1));
     if (e == cudaSuccess)
-        e = cudaMalloc(&ds->miss_idx, std::max<int64_t>(1, ds->miss_total) * (ds->miss_idx16 ? 2 : 4));
+        // 16 spare entries: readers load the lists in aligned 16-byte pieces
+        e = cudaMalloc(&ds->miss_idx, (ds->miss_total + 16) * (ds->miss_idx16 ? 2 : 4));
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(ds->miss_off, ho, sizeof(int64_t) * (p + 1), cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);

@@ -498,9 +498,12 @@ __global__ void __launch_bounds__(kMrThreads, 1) k_grad_mrhs(
 
 // ---------------------------------------------------------------------------
 // Missing-call sums and the standardisation: g_cj = v (S1 - u (R - M_cj)),
-// with S1 read from g_c.  The residual columns of a group are staged in shared
-// memory, interleaved (CG floats per sample); four lanes per SNP walk its
-// missing list in the order of the single-column pass.
+// with S1 read from g_c.  A block stages CG residual columns in shared memory,
+// interleaved (CG floats per sample); each lane owns one SNP, reads its
+// missing-call list 16 bytes at a time (8 or 4 sample indices) and gathers the
+// CG residual values of every listed sample, so a list entry costs one
+// shared-memory vector load for all CG columns; the lane then writes the CG
+// finished gradient entries of its SNP (consecutive SNPs across the warp).
 
 template <int CG>
 struct MrVec;
@@ -518,13 +521,17 @@ __device__ __forceinline__ void mr_addv(float *m, float4 v)
     m[0] += v.x; m[1] += v.y; m[2] += v.z; m[3] += v.w;
 }
 
+constexpr int kFinThreads = 512;
+
 template <int CG, typename IdxT, bool kStage>
-__global__ void __launch_bounds__(512) k_miss_finalize(const int64_t *__restrict__ off,
-                                                       const IdxT *__restrict__ idx, int64_t p,
-                                                       int64_t n_pad, const MrCol *__restrict__ cols,
-                                                       int ncols)
+__global__ void __launch_bounds__(kFinThreads) k_miss_finalize(const int64_t *__restrict__ off,
+                                                               const IdxT *__restrict__ idx, int64_t p,
+                                                               int64_t n_pad,
+                                                               const MrCol *__restrict__ cols,
+                                                               int ncols)
 {
     using V = typename MrVec<CG>::T;
+    constexpr int kPer = 16 / (int)sizeof(IdxT);               // indices per 16-byte load
     extern __shared__ __align__(16) unsigned char mr_sh[];
     V *rs = reinterpret_cast<V *>(mr_sh);
     const int c0 = blockIdx.y * CG;
@@ -543,34 +550,29 @@ __global__ void __launch_bounds__(512) k_miss_finalize(const int64_t *__restrict
         __syncthreads();
     }
     const float *__restrict__ rg = cols[c0].r32;        // unstaged path: CG == 1
-    const int lane = threadIdx.x & 31, q = lane & 3;
+    const uint4 *__restrict__ idx4 = reinterpret_cast<const uint4 *>(idx);
+    const int lane = threadIdx.x & 31;
     const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t base = warp * 8; base < p; base += nwarps * 8) {      // warp-uniform
-        const int64_t j = base + (lane >> 2);
+    for (int64_t base = warp * 32; base < p; base += nwarps * 32) {
+        const int64_t j = base + lane;
         const bool live = j < p;
         const int64_t e0 = live ? off[j] : 0, e1 = live ? off[j + 1] : 0;
         float m[CG];
 #pragma unroll
         for (int e = 0; e < CG; ++e) m[e] = 0.0f;
-        for (int64_t e = e0 + q; e < e1; e += 16) {
-            IdxT ii[4];
+        for (int64_t a = e0 & ~(int64_t)(kPer - 1); a < e1; a += kPer) {
+            const uint4 w = idx4[a / kPer];
+            const IdxT *ent = reinterpret_cast<const IdxT *>(&w);
 #pragma unroll
-            for (int t = 0; t < 4; ++t) ii[t] = e + 4 * t < e1 ? idx[e + 4 * t] : (IdxT)0;
-#pragma unroll
-            for (int t = 0; t < 4; ++t) {
-                if (e + 4 * t < e1) {
-                    if (kStage) mr_addv(m, rs[ii[t]]);
-                    else m[0] += __ldg(rg + ii[t]);
+            for (int t = 0; t < kPer; ++t) {
+                if (a + t >= e0 && a + t < e1) {
+                    if (kStage) mr_addv(m, rs[ent[t]]);
+                    else m[0] += __ldg(rg + ent[t]);
                 }
             }
         }
-#pragma unroll
-        for (int e = 0; e < CG; ++e) {
-            m[e] += __shfl_xor_sync(0xffffffffu, m[e], 1);
-            m[e] += __shfl_xor_sync(0xffffffffu, m[e], 2);
-        }
-        if (live && q == 0) {
+        if (live) {
 #pragma unroll
             for (int e = 0; e < CG; ++e) {
                 if (c0 + e < ncols) {
@@ -647,9 +649,10 @@ static int mr_launch_finalize(iht_dataset *ds, const MrCol *cols, int ncols, siz
     if (smem > 48 * 1024) IHT_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     const int groups = (ncols + CG - 1) / CG;
     const int per_sm = smem > 110 * 1024 ? 1 : 2;
-    const int gx = (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(ds->p, 128),
-                                                               ((int64_t)ds->ctx->num_sms * per_sm + groups - 1) / groups));
-    kern<<<dim3(gx, groups), 512, smem, ds->ctx->stream>>>(ds->miss_off, (const IdxT *)ds->miss_idx,
+    // one wave: at most per_sm resident blocks on every SM
+    const int gx = (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(ds->p, kFinThreads),
+                                                               (int64_t)ds->ctx->num_sms * per_sm / groups));
+    kern<<<dim3(gx, groups), kFinThreads, smem, ds->ctx->stream>>>(ds->miss_off, (const IdxT *)ds->miss_idx,
                                                            ds->p, ds->n_pad, cols, ncols);
     note_launch();
     IHT_CUDA(cudaGetLastError());

@@ -381,16 +381,17 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_grad_tc(const __grid_constant
         const uint32_t tb = tmem_base + (uint32_t)(w * 128);
         const uint32_t lane_off = (uint32_t)((warp & 3) * 32) << 16;
         const float s0 = prm->s0, R = prm->R;
-        uint32_t grp = 0, k = 0;     // A-buffer groups written, TMA stages consumed
+        uint32_t grp = 0;                       // A-buffer groups written
+        uint32_t slot = 0, sphase = 0;          // TMA stage ring (slot, phase bit)
+        uint32_t buf = 0, bphase = 0;           // A-buffer ring
         int T = 0;
         bool ok = true;
         const int cps = kTcStageBytes / kTcGroupBytes;                 // chunks per stage
         for (int64_t tile = (int64_t)blockIdx.x * kTcNWG + w; tile < ntiles && ok; tile += tile_step, ++T) {
             const int64_t row = tile * 128 + r;
             int h = 0;                                                  // half of the current group
-            for (int st = 0; st < spt && ok; ++st, ++k) {
-                const uint32_t slot = k % (uint32_t)nst;
-                if (!mbar_wait(&P.tma_full[slot], (k / (uint32_t)nst) & 1u)) {
+            for (int st = 0; st < spt && ok; ++st) {
+                if (!mbar_wait(&P.tma_full[slot], sphase)) {
                     abort_flag = 1;
                     ok = false;
                 }
@@ -399,9 +400,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_grad_tc(const __grid_constant
                 for (int c = 0; c < nchunks && ok; ++c) {
                     const int gi = st * cps + c;                        // chunk within the tile
                     const uint4 x = *reinterpret_cast<const uint4 *>(base + ((c ^ ((r >> 1) & 3)) << 4));
-                    const uint32_t buf = grp % kTcBufs;
                     if (h == 0 && grp >= kTcBufs) {
-                        if (!mbar_wait(&P.empty[buf], ((grp / kTcBufs) - 1) & 1u)) {
+                        if (!mbar_wait(&P.empty[buf], bphase ^ 1u)) {
                             abort_flag = 1;
                             ok = false;
                         }
@@ -413,12 +413,20 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_grad_tc(const __grid_constant
                         tc_fence_before();
                         mbar_arrive(&P.full[buf]);
                         ++grp;
+                        if (++buf == kTcBufs) {
+                            buf = 0;
+                            bphase ^= 1u;
+                        }
                         h = 0;
                     } else {
                         h = 1;
                     }
                 }
                 mbar_arrive(&P.tma_empty[slot]);
+                if (++slot == (uint32_t)nst) {
+                    slot = 0;
+                    sphase ^= 1u;
+                }
                 if (abort_flag) ok = false;
             }
             if (ok) ok &= tc_epilogue(P, tb, lane_off, T, row, p, s0, R, Mj, u32, v32, g, abort_flag);
@@ -431,7 +439,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_grad_tc(const __grid_constant
         const uint32_t b_addr = smem_addr(bsm);
         const uint32_t za = 256u + 256u * (uint32_t)ksteps;   // trailing zero group
         if (lane == 0) {
-            uint32_t q = 0;
+            uint32_t buf = 0, use = 0;                                   // A-buffer ring
             int T = 0;
             bool ok = true;
             const int ngrp = (ngroups + 1) / 2;                          // A groups per tile
@@ -440,8 +448,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_grad_tc(const __grid_constant
                     if (!mbar_wait(&P.accempty, (uint32_t)(T - 1) & 1u)) { abort_flag = 1; ok = false; }
                     tc_fence_after();
                 }
-                for (int gg = 0; gg < ngrp && ok; ++gg, ++q) {
-                    const uint32_t buf = q % kTcBufs, use = q / kTcBufs;
+                for (int gg = 0; gg < ngrp && ok; ++gg) {
                     if (!mbar_wait(&P.full[buf], use & 1u)) { abort_flag = 1; ok = false; break; }
                     tc_fence_after();
                     const int s_end = min(ksteps, (gg + 1) * kTcBufSteps);
@@ -452,6 +459,10 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_grad_tc(const __grid_constant
                     }
                     mma_commit(&P.empty[buf]);
                     if (gg == ngrp - 1) mma_commit(&P.accfull);
+                    if (++buf == kTcBufs) {
+                        buf = 0;
+                        use ^= 1u;
+                    }
                 }
                 if (abort_flag) ok = false;
             }
@@ -466,17 +477,25 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_grad_tc(const __grid_constant
             const int64_t tiles_w = first < ntiles ? (ntiles - 1 - first) / tile_step + 1 : 0;
             const int64_t total = tiles_w * spt;
             int64_t kk = 0;
+            uint32_t slot = 0, phase = 0;
+            int64_t tile = first;
+            int st = 0;
             for (; kk < total && !abort_flag; ++kk) {
-                const uint32_t slot = (uint32_t)(kk % nst);
-                if (kk >= nst && !mbar_wait(&P.tma_empty[slot], (uint32_t)((kk / nst) - 1) & 1u)) {
+                if (kk >= nst && !mbar_wait(&P.tma_empty[slot], phase ^ 1u)) {
                     abort_flag = 1;
                     break;
                 }
-                const int64_t tile = first + (kk / spt) * tile_step;
-                const int st = (int)(kk % spt);
                 mbar_expect_tx(&P.tma_full[slot], kTcStageTile);
                 tma_load_2d(stages + (w * nst + slot) * kTcStageTile, &gmap, st * kTcStageBytes,
                             (int)(tile * 128), &P.tma_full[slot]);
+                if (++slot == (uint32_t)nst) {
+                    slot = 0;
+                    phase ^= 1u;
+                }
+                if (++st == spt) {
+                    st = 0;
+                    tile += tile_step;
+                }
             }
             // copies still in flight (only after an abort) are waited for, bounded
             for (int64_t j = kk - nst; j < kk; ++j)
