@@ -242,6 +242,62 @@ int iht_fit_batch(iht_dataset *ds, int32_t b, const iht_solve_desc *solves,
 int iht_gradient_batch(iht_dataset *ds, int32_t b, const int32_t *const *rows_list,
                        const int64_t *n_rows, const float *R, float *G_out, int impl);
 
+/* a8 -- continuous-batching IHT server on one dataset.
+ *
+ * Requests (a phenotype, a subject subset and k: iht_solve_desc with host
+ * pointers, copied at submission) arrive at any time.  A worker thread owned
+ * by the server admits a pending request when a slot is free and its device
+ * footprint (per-SNP statistics, gradient, residuals and scratch of one solve,
+ * about 28 p + 56 n + 8 n ceil(k/4) bytes) fits in hbm_budget, then runs
+ * every admitted solve together: one iteration per tick, one multi-column
+ * gradient pass over the packed genotypes for all active solves (each solve is
+ * a column), the O(nk) steps batched.  A solve retires when it stops (same
+ * rule as iht_fit) and frees its slot and memory for the next request.  Each
+ * solve's arithmetic does not depend on which other solves share its ticks.
+ * The paper fits one model at a time; this is the serving form of the batched
+ * cross-validation above (Sec. 2.4 fits many models on one matrix). */
+typedef struct iht_server iht_server;
+
+typedef struct iht_server_options {
+    int32_t max_slots;       /* solves on the device at once, 1..1024 (default 64)     */
+    int32_t reserved;
+    uint64_t hbm_budget;     /* device bytes for admitted solves; 0 = no limit         */
+    iht_options solve;       /* per-solve options; in_mem, out_mem, profile ignored    */
+} iht_server_options;
+
+typedef struct iht_server_stats {
+    uint64_t submitted, admitted, completed, ticks;
+    int32_t active, max_active;              /* solves on the device now / at most   */
+    uint64_t bytes_in_use, max_bytes_in_use; /* footprint of the admitted solves     */
+} iht_server_stats;
+
+void iht_server_default_options(iht_server_options *o);
+
+/* Starts the worker on its own stream of the dataset's device.  The dataset
+ * must outlive the server; other calls on the same dataset while a server is
+ * running are not supported.  Returns OK, EINVAL, ENOMEM, ECUDA. */
+int iht_server_create(iht_dataset *ds, const iht_server_options *opt, iht_server **out);
+
+/* Queues one request (host rows or NULL for all n, host y).  EINVAL for k
+ * outside 1..min(p, 1024), n_rows < 2, a request that can never fit the
+ * budget, or a server whose worker has failed (then ECUDA). */
+int iht_server_submit(iht_server *s, const iht_solve_desc *req, uint64_t *ticket);
+
+/* Result of a finished request: support (int32[k], ascending), beta on it
+ * (double[k]), info (info->status: OK, ENOTCONV, ENUMERIC for non-finite y,
+ * EINVAL for bad rows) and the time from submission to retirement in
+ * seconds; any output may be NULL.  Returns EAGAIN while the request is queued
+ * or running, EINVAL for an unknown (or already collected) ticket, ECUDA if
+ * the worker failed.  A collected result is released. */
+int iht_server_poll(iht_server *s, uint64_t ticket, int32_t *support, double *beta_s,
+                    iht_result *info, double *latency_s);
+
+int iht_server_get_stats(iht_server *s, iht_server_stats *out);
+
+/* Stops the worker after its current tick; requests not yet finished are
+ * dropped.  Frees everything the server holds. */
+int iht_server_destroy(iht_server *s);
+
 #ifdef __cplusplus
 }
 #endif

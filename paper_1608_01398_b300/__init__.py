@@ -25,7 +25,9 @@ EXPORTED = ["iht_default_options", "iht_strerror", "iht_last_cuda_error", "iht_k
             "iht_create",
             "iht_destroy", "iht_load_bed", "iht_dataset_free", "iht_dataset_shape", "iht_counts",
             "iht_gradient", "iht_topk", "iht_topk_noalloc", "iht_zmul", "iht_fit",
-            "iht_fit_trace", "iht_fit_batch", "iht_gradient_batch"]
+            "iht_fit_trace", "iht_fit_batch", "iht_gradient_batch", "iht_server_default_options",
+            "iht_server_create", "iht_server_submit", "iht_server_poll", "iht_server_get_stats",
+            "iht_server_destroy"]
 
 
 class IhtError(RuntimeError):
@@ -61,6 +63,18 @@ class iht_trace(ctypes.Structure):
 class iht_solve_desc(ctypes.Structure):
     _fields_ = [("rows", ctypes.c_void_p), ("n_rows", ctypes.c_int64), ("y", ctypes.c_void_p),
                 ("k", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
+class iht_server_options(ctypes.Structure):
+    _fields_ = [("max_slots", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("hbm_budget", ctypes.c_uint64), ("solve", iht_options)]
+
+
+class iht_server_stats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_uint64), ("admitted", ctypes.c_uint64),
+                ("completed", ctypes.c_uint64), ("ticks", ctypes.c_uint64),
+                ("active", ctypes.c_int32), ("max_active", ctypes.c_int32),
+                ("bytes_in_use", ctypes.c_uint64), ("max_bytes_in_use", ctypes.c_uint64)]
 
 
 _LIB = None
@@ -108,6 +122,15 @@ def _lib(build_if_stale: bool = True):
                                          ctypes.POINTER(iht_result)]),
         "iht_gradient_batch": (ctypes.c_int, [P, i32, ctypes.POINTER(P), ctypes.POINTER(i64), P, P,
                                               ctypes.c_int]),
+        "iht_server_default_options": (None, [ctypes.POINTER(iht_server_options)]),
+        "iht_server_create": (ctypes.c_int, [P, ctypes.POINTER(iht_server_options),
+                                             ctypes.POINTER(P)]),
+        "iht_server_submit": (ctypes.c_int, [P, ctypes.POINTER(iht_solve_desc),
+                                             ctypes.POINTER(ctypes.c_uint64)]),
+        "iht_server_poll": (ctypes.c_int, [P, ctypes.c_uint64, P, P, ctypes.POINTER(iht_result),
+                                           ctypes.POINTER(ctypes.c_double)]),
+        "iht_server_get_stats": (ctypes.c_int, [P, ctypes.POINTER(iht_server_stats)]),
+        "iht_server_destroy": (ctypes.c_int, [P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -455,3 +478,86 @@ def iht_gradient_batch(ds: Dataset, R, rows_list=None, impl: int = 0):
     _check(_lib().iht_gradient_batch(ds.h, b, ptrs, nrows, ctypes.c_void_p(Rbuf.data_ptr()),
                                      ctypes.c_void_p(G.data_ptr()), impl), "iht_gradient_batch")
     return G
+
+
+@dataclass
+class ServedResult:
+    support: np.ndarray
+    beta_s: np.ndarray
+    iterations: int
+    status: int
+    backtracks: int
+    objective: float
+    mu: float
+    latency_s: float
+
+
+class Server:
+    """iht_server_*: continuous-batching IHT solves on one dataset.
+
+    submit() queues a request (host y and rows, copied) and returns a ticket;
+    poll() returns None while it is queued or running, then its ServedResult
+    (once).  The server's worker runs on its own stream of the dataset's
+    device until close()."""
+
+    def __init__(self, ds: Dataset, max_slots: int = 64, hbm_budget: int = 0, **solve):
+        _torch()
+        o = iht_server_options()
+        _lib().iht_server_default_options(ctypes.byref(o))
+        o.max_slots = max_slots
+        o.hbm_budget = hbm_budget
+        for k, v in solve.items():
+            if not hasattr(o.solve, k):
+                raise AttributeError(k)
+            setattr(o.solve, k, v)
+        h = ctypes.c_void_p()
+        _check(_lib().iht_server_create(ds.h, ctypes.byref(o), ctypes.byref(h)), "iht_server_create")
+        self.h = h
+        self.ds = ds
+        self._k = {}
+
+    def submit(self, y, k: int, rows=None) -> int:
+        y = np.ascontiguousarray(y, dtype=np.float64)
+        if rows is not None:
+            rows = np.ascontiguousarray(rows, dtype=np.int32)
+            if rows.size != y.size:
+                raise ValueError("y must have one entry per row")
+        elif y.size != self.ds.n:
+            raise ValueError("y must have n entries when rows is None")
+        d = iht_solve_desc(None if rows is None else rows.ctypes.data, y.size, y.ctypes.data, int(k), 0)
+        t = ctypes.c_uint64()
+        _check(_lib().iht_server_submit(self.h, ctypes.byref(d), ctypes.byref(t)), "iht_server_submit")
+        self._k[t.value] = int(k)
+        return t.value
+
+    def poll(self, ticket: int):
+        k = self._k[ticket]
+        supp = np.empty(k, dtype=np.int32)
+        bs = np.empty(k)
+        info = iht_result()
+        lat = ctypes.c_double()
+        rc = _lib().iht_server_poll(self.h, ticket, ctypes.c_void_p(supp.ctypes.data),
+                                    ctypes.c_void_p(bs.ctypes.data), ctypes.byref(info),
+                                    ctypes.byref(lat))
+        if rc == IHT_EAGAIN:
+            return None
+        _check(rc, "iht_server_poll")
+        del self._k[ticket]
+        return ServedResult(supp, bs, info.iterations, info.status, info.backtracks, info.objective,
+                            info.mu, lat.value)
+
+    def stats(self) -> dict:
+        st = iht_server_stats()
+        _check(_lib().iht_server_get_stats(self.h, ctypes.byref(st)), "iht_server_get_stats")
+        return {f: getattr(st, f) for f, _ in st._fields_}
+
+    def close(self):
+        if getattr(self, "h", None):
+            _lib().iht_server_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

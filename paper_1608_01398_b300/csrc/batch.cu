@@ -203,7 +203,16 @@ static int build_sets(iht_dataset *ds, BatchWork *w, const std::vector<SetKey> &
         }
         int rc = setup_rowset(ds, rows_dev[q], k.n_rows, batch_rowset(ds, w, q), w->set_err + q);
         if (rc) return rc;
-        if ((rc = launch_counts_rowset(ds, k.n_rows, batch_rowset(ds, w, q)))) return rc;
+    }
+    {   // statistics of all sets, several per pass over the genotypes
+        std::vector<RowSet> rs(nsets);
+        std::vector<int64_t> nr(nsets);
+        for (int q = 0; q < nsets; ++q) {
+            rs[q] = batch_rowset(ds, w, q);
+            nr[q] = sets[q].n_rows;
+        }
+        int rc = launch_counts_sets(ds, rs.data(), nr.data(), nsets);
+        if (rc) return rc;
     }
     IHT_CUDA(cudaMemcpyAsync(w->set_err_host, w->set_err, sizeof(int32_t) * nsets,
                              cudaMemcpyDeviceToHost, s));
@@ -336,6 +345,7 @@ int iht_fit_batch(iht_dataset *ds, int32_t b, const iht_solve_desc *solves,
         h.status = (err & 1) ? IHT_ENUMERIC : IHT_ENOTCONV;
         h.done = (err & 1) || opt.max_iter <= 0 ? 1 : 0;
         h.err = err;
+        h.fresh = 1;
         w->sc_host[c] = h;
         const RowSet rs = batch_rowset(ds, w, set_of[c]);
         BSolve &B = w->bs_host[c];

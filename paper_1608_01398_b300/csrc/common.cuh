@@ -50,6 +50,7 @@ struct Scalars {                       // device-resident state of one solve
     int32_t k, n_rows;
     int32_t err;                       // bit 0: non-finite input, bit 1: bad rows
     int32_t live;                      // batched solves: takes part in the current attempt
+    int32_t fresh;                     // batched solves: beta = 0 set-up still to run
 };
 
 // Device descriptor of one solve of a batch (all pointers device memory).
@@ -210,6 +211,7 @@ RowSet workspace_rowset(iht_dataset *ds);
 int setup_rowset(iht_dataset *ds, const int32_t *rows_dev, int64_t n_rows, const RowSet &rs,
                  int32_t *err);
 int launch_counts_rowset(iht_dataset *ds, int64_t n_rows, const RowSet &rs);
+int launch_counts_sets(iht_dataset *ds, const RowSet *sets, const int64_t *n_rows, int nsets);
 int launch_fix_padding(iht_dataset *ds);
 int build_missing_lists(iht_dataset *ds);
 int launch_missing_sums(iht_dataset *ds, const float *r32, float *M, const int32_t *done);
@@ -241,6 +243,7 @@ int mrhs_max_cols();
 bool grad_mrhs_supported(const iht_dataset *ds);
 int launch_grad_mrhs(iht_dataset *ds, MrCol *cols_dev, int ncols, ProfEvents *prof = nullptr);
 int grad_mrhs_status(iht_dataset *ds, int *timed_out);
+void grad_mrhs_release_thread();
 // select.cu
 struct SelJob {                        // one problem of a batched top-K
     const float *keys;
@@ -277,6 +280,7 @@ int launch_center_batch(iht_dataset *ds, const BSolve *bs, int nb, bool init);
 int launch_merge_batch(iht_dataset *ds, const BSolve *bs, int nb, int first);
 int launch_decide_batch(iht_dataset *ds, const BSolve *bs, int nb);
 int launch_scatter_beta_batch(iht_dataset *ds, const BSolve *bs, int nb, int kmax, double *betas);
+int launch_finish_fresh_batch(iht_dataset *ds, const BSolve *bs, int nb, int kmax);
 int launch_compact_support_batch(iht_dataset *ds, const BSolve *bs, int nb, int kmax,
                                  int32_t *supports, double *beta_s);
 

@@ -186,6 +186,119 @@ int launch_counts(iht_dataset *ds, int64_t n_rows)
     return launch_counts_rowset(ds, n_rows, workspace_rowset(ds));
 }
 
+// Several row sets in one pass over the genotypes: a warp reads SNP j's row
+// once and applies up to kMultiSets row masks (same arithmetic as k_counts).
+constexpr int kMultiSets = 8;
+
+struct MultiSets {
+    const uint32_t *rowmask[kMultiSets];
+    int64_t n_rows[kMultiSets];
+    double *u64[kMultiSets], *v64[kMultiSets];
+    float *u32[kMultiSets], *v32[kMultiSets];
+};
+
+template <int NS>
+__global__ void __launch_bounds__(256) k_counts_multi(const uint8_t *__restrict__ G, int64_t p,
+                                                      int64_t stride, int64_t rowb, MultiSets ms)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    const int64_t nwords = rowb / 4;
+    for (int64_t j = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); j < p;
+         j += nwarps) {
+        const uint4 *row4 = reinterpret_cast<const uint4 *>(G + j * stride);
+        int c1[NS], c2[NS], c3[NS];
+#pragma unroll
+        for (int q = 0; q < NS; ++q) c1[q] = c2[q] = c3[q] = 0;
+        for (int64_t c = lane; c < nwords / 4; c += 32) {
+            const uint4 w4 = __ldcs(row4 + c);
+#pragma unroll
+            for (int q = 0; q < NS; ++q) {
+                const uint4 m4 = __ldg(reinterpret_cast<const uint4 *>(ms.rowmask[q]) + c);
+                const uint32_t ws[4] = {w4.x & m4.x, w4.y & m4.y, w4.z & m4.z, w4.w & m4.w};
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    const uint32_t lo = ws[e] & 0x55555555u, hi = (ws[e] >> 1) & 0x55555555u;
+                    c3[q] += __popc(lo & hi);
+                    c1[q] += __popc(lo & ~hi);
+                    c2[q] += __popc(hi & ~lo);
+                }
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < NS; ++q) {
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                c1[q] += __shfl_xor_sync(0xffffffffu, c1[q], o);
+                c2[q] += __shfl_xor_sync(0xffffffffu, c2[q], o);
+                c3[q] += __shfl_xor_sync(0xffffffffu, c3[q], o);
+            }
+        }
+        if (lane < NS) {
+            // lane q finishes set q (registers indexed by a compile-time loop)
+#pragma unroll
+            for (int q = 0; q < NS; ++q) {
+                if (q != lane) continue;
+                const double n_obs = (double)(ms.n_rows[q] - c1[q]);
+                const double s1 = (double)(c2[q] + 2 * c3[q]);
+                const double s2 = (double)(c2[q] + 4 * c3[q]);
+                const double mean = n_obs > 0.0 ? __ddiv_rn(s1, n_obs) : 0.0;
+                double inv_sd = 0.0;
+                if (n_obs >= 2.0) {
+                    const double var = __ddiv_rn(__dsub_rn(s2, __ddiv_rn(__dmul_rn(s1, s1), n_obs)),
+                                                 __dsub_rn(n_obs, 1.0));
+                    if (var > 0.0) inv_sd = __ddiv_rn(1.0, __dsqrt_rn(var));
+                }
+                ms.u64[q][j] = mean;
+                ms.v64[q][j] = inv_sd;
+                ms.u32[q][j] = (float)mean;
+                ms.v32[q][j] = (float)inv_sd;
+            }
+        }
+    }
+}
+
+template <int NS>
+static int launch_counts_multi_n(iht_dataset *ds, const MultiSets &ms)
+{
+    const int blocks = (int)std::min<int64_t>(ceil_div(ds->p, 8), (int64_t)ds->ctx->num_sms * 16);
+    k_counts_multi<NS><<<blocks, 256, 0, ds->ctx->stream>>>(ds->G, ds->p, ds->stride, ds->rowb, ms);
+    note_launch();
+    IHT_CUDA(cudaGetLastError());
+    return IHT_OK;
+}
+
+// Statistics of several row sets (rowmasks already built), kMultiSets per pass.
+int launch_counts_sets(iht_dataset *ds, const RowSet *sets, const int64_t *n_rows, int nsets)
+{
+    for (int s0 = 0; s0 < nsets; s0 += kMultiSets) {
+        const int ns = std::min(kMultiSets, nsets - s0);
+        MultiSets ms{};
+        for (int q = 0; q < ns; ++q) {
+            const RowSet &r = sets[s0 + q];
+            ms.rowmask[q] = r.rowmask;
+            ms.n_rows[q] = n_rows[s0 + q];
+            ms.u64[q] = r.u64;
+            ms.v64[q] = r.v64;
+            ms.u32[q] = r.u32;
+            ms.v32[q] = r.v32;
+        }
+        int rc;
+        switch (ns) {
+        case 1: rc = launch_counts_multi_n<1>(ds, ms); break;
+        case 2: rc = launch_counts_multi_n<2>(ds, ms); break;
+        case 3: rc = launch_counts_multi_n<3>(ds, ms); break;
+        case 4: rc = launch_counts_multi_n<4>(ds, ms); break;
+        case 5: rc = launch_counts_multi_n<5>(ds, ms); break;
+        case 6: rc = launch_counts_multi_n<6>(ds, ms); break;
+        case 7: rc = launch_counts_multi_n<7>(ds, ms); break;
+        default: rc = launch_counts_multi_n<8>(ds, ms); break;
+        }
+        if (rc) return rc;
+    }
+    return IHT_OK;
+}
+
 template <typename T>
 __global__ void k_scatter(const int32_t *__restrict__ rows, int64_t n_rows, const T *__restrict__ src,
                           T *__restrict__ dst, int64_t n)

@@ -727,6 +727,15 @@ int launch_grad_mrhs(iht_dataset *ds, MrCol *cols, int ncols, ProfEvents *prof)
     return IHT_OK;
 }
 
+// Frees the calling thread's pass scratch (a server's worker before it exits).
+void grad_mrhs_release_thread()
+{
+    MrWork &w = g_mr;
+    if (w.bimg) cudaFree(w.bimg);
+    if (w.err) cudaFree(w.err);
+    w = MrWork();
+}
+
 // Bounded-wait status of the multi-column passes so far (1 = a wait timed out).
 int grad_mrhs_status(iht_dataset *ds, int *timed_out)
 {

@@ -772,7 +772,7 @@ __global__ void __launch_bounds__(1024) k_gather_gS_b(const BSolve *bs)
 __device__ __forceinline__ bool zmul_gate(const BSolve &B, int which)
 {
     const Scalars *sc = B.sc;
-    if (which == kZmulInit) return true;
+    if (which == kZmulInit) return sc->fresh && !sc->done;
     if (which == kZmulStep) return !sc->done;
     return sc->live && !sc->done;
 }
@@ -808,7 +808,7 @@ __global__ void __launch_bounds__(256) k_zmul_sum_b(const BSolve *bs, int which,
 __global__ void k_init_objective_b(const BSolve *bs, int npart)
 {
     const BSolve &B = bs[blockIdx.x];
-    if (B.sc->done || threadIdx.x != 0) return;
+    if (!B.sc->fresh || B.sc->done || threadIdx.x != 0) return;
     init_objective_body(B.sc, B.partials, npart);
 }
 
@@ -817,7 +817,7 @@ __global__ void k_center_b(const BSolve *bs, int64_t n_pad, int init)
     const BSolve &B = bs[blockIdx.y];
     const Scalars *sc = B.sc;
     if (init) {
-        if (sc->done) return;
+        if (!sc->fresh || sc->done) return;
         center_body(B.r64, B.r64, B.used, n_pad, sc, B.r32);
     } else {
         if (!sc->live || sc->done || sc->retry) return;
@@ -873,6 +873,26 @@ __global__ void k_compact_support_b(const BSolve *bs, int32_t *__restrict__ supp
     if (c >= B.k) return;
     if (supports) supports[B.out_off + c] = B.S[c];
     if (beta_s) beta_s[B.out_off + c] = B.bS[c];
+}
+
+// After S^0 of newly set-up solves: beta_S = 0, set-up flag cleared.
+__global__ void k_finish_fresh_b(const BSolve *bs)
+{
+    const BSolve &B = bs[blockIdx.x];
+    Scalars *sc = B.sc;
+    const int fresh = sc->fresh, done = sc->done;
+    __syncthreads();   // flags read by every thread before thread 0 clears one
+    if (!fresh) return;
+    for (int c = threadIdx.x; c < B.k && !done; c += blockDim.x) B.bS[c] = 0.0;
+    if (threadIdx.x == 0) sc->fresh = 0;
+}
+
+int launch_finish_fresh_batch(iht_dataset *ds, const BSolve *bs, int nb, int)
+{
+    k_finish_fresh_b<<<nb, 256, 0, ds->ctx->stream>>>(bs);
+    note_launch();
+    IHT_CUDA(cudaGetLastError());
+    return IHT_OK;
 }
 
 int launch_compact_support_batch(iht_dataset *ds, const BSolve *bs, int nb, int kmax,
