@@ -2,7 +2,8 @@
 """Benchmark: IHT iterations/s on the single-solve panel (n=5000, p=500000, k=50).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                    [--config 1|2|3] [--grad-impl 0|1|2] [--no-cpu-baseline]
+                    [--config 1|2|3|4] [--grad-impl 0|1|2] [--no-cpu-baseline]
+                    [--requests R]
 
 One step = one full IHT least-squares solve (beta = 0 to convergence, every
 step of the hot path: standardised gradient, top-k projection, step size,
@@ -24,6 +25,13 @@ sample of the same workload); on rank 0 only.
 p=1000000, 5 folds x k = 1..20 = 100 solves in one iht_fit_batch call):
 one step = the whole batch to convergence, value = solves/s, beside the same
 100 solves run one at a time through iht_fit on the same GPU.
+
+``--config 4`` measures the serving stream (n=10000, p=1000000; requests with
+a random subject subset of 2000-10000 rows, k in 5..200, fresh phenotype):
+value = solves/s of the continuous-batching server with every request queued
+at once (one step = R requests), beside Poisson arrivals at 0.5x and 1.2x
+the one-at-a-time GPU rate with p50/p99 latency, and that one-at-a-time rate
+itself (iht_fit per request, host inputs).
 """
 from __future__ import annotations
 
@@ -501,19 +509,201 @@ def cv_arm(args):
     return 0
 
 
+def serve_setup(args):
+    cfg = 4
+    c = synth.CONFIGS[cfg]
+    pn = synth.config_panel(cfg)
+    bed = pn.bed()
+    reqs = synth.serving_requests(pn, args.requests, synth.BASE_SEED + 1000 * cfg + 11,
+                                  workers=min(16, os.cpu_count() or 1))
+    return c, pn, bed, reqs
+
+
+def serve_reference_arm(args):
+    """Oracle on a bounded sample: the first request, a few iterations, extrapolated."""
+    import oracle
+    rank, _, world = dist_env()
+    if rank != 0:
+        return 0
+    c, pn, bed, reqs = serve_setup(args)
+    G = oracle.Geno.from_bed(bed, pn.n, pn.p)
+    cap = max(1, min(args.oracle_iters, 3))
+    vals, secs = [], 0.0
+    for s in range(max(args.steps, 1)):
+        q = reqs[s % len(reqs)]
+        t0 = time.perf_counter()
+        f = oracle.iht(G, q["y"], q["k"], rows=q["rows"], max_iter=cap, tol=c["tol"], trace=False)
+        dt = time.perf_counter() - t0
+        secs += dt
+        vals.append(1.0 / (dt / max(f.iterations, 1) * 20.0))
+    value = statistics.median(vals)
+    out = {"impl": "reference", "metric": "served IHT solves/sec", "value": value,
+           "unit": "solves/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": 1e3 * secs / max(args.steps, 1), "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": c["name"], "n": c["n"], "p": c["p"], "requests": args.requests},
+           "cpu_baseline": {"value": value, "unit": "solves/s", "cores": oracle.max_threads(),
+                            "kind": "oracle",
+                            "sample": f"FP64 oracle, one request per step capped at {cap} iterations "
+                                      f"(incl. its statistics pass); solves/s extrapolated at 20 "
+                                      f"iterations per solve"},
+           "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0,
+                   "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+    return 0
+
+
+def _serve_run(iht, srv, reqs, arrivals):
+    """Submits reqs at the given offsets (s, from now), collects every result."""
+    t0 = time.perf_counter()
+    tickets, res = [], {}
+    i = 0
+    while i < len(reqs) or len(res) < len(reqs):
+        now = time.perf_counter() - t0
+        while i < len(reqs) and arrivals[i] <= now:
+            q = reqs[i]
+            tickets.append(srv.submit(q["y"], q["k"], q["rows"]))
+            i += 1
+        for t in tickets:
+            if t not in res:
+                r = srv.poll(t)
+                if r is not None:
+                    res[t] = r
+        if i < len(reqs):
+            time.sleep(max(0.0, min(0.0005, arrivals[i] - (time.perf_counter() - t0))))
+        else:
+            time.sleep(0.0005)
+    wall = time.perf_counter() - t0
+    out = [res[t] for t in tickets]
+    lat = np.array([r.latency_s for r in out])
+    return wall, lat, out
+
+
+def _mg1_latency(service, arrivals):
+    """Latency of one-at-a-time service (measured service times, cycled) under the arrivals."""
+    free, lat = 0.0, []
+    for i, a in enumerate(arrivals):
+        start = max(a, free)
+        free = start + service[i % len(service)]
+        lat.append(free - a)
+    return np.array(lat)
+
+
+def serve_arm(args):
+    import torch
+    import paper_1608_01398_b300 as iht
+
+    rank, local_rank, world = dist_env()
+    t0 = time.perf_counter()
+    c, pn, bed, reqs = serve_setup(args)          # before any CUDA work (spawned workers)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device(f"cuda:{local_rank}"))
+    torch.cuda.set_device(local_rank)
+    dev = local_rank
+    log(f"[bench] rank {rank}: generated {bed.nbytes / 1e6:.0f} MB panel and {len(reqs)} requests in "
+        f"{time.perf_counter() - t0:.1f}s")
+    stream = torch.cuda.current_stream(dev)
+    ctx = iht.Context(dev, stream)
+    ds = iht.Dataset(ctx, bed, pn.n, pn.p)
+    solve = dict(tol=c["tol"], max_iter=c["max_iter"])
+
+    # one request at a time through iht_fit (host inputs and outputs)
+    nplain = min(len(reqs), args.plain_requests)
+    for q in reqs[:2]:
+        iht.iht_fit(ds, q["y"], q["k"], rows=q["rows"], **solve)
+    service = []
+    for q in reqs[:nplain]:
+        w0 = time.perf_counter()
+        iht.iht_fit(ds, q["y"], q["k"], rows=q["rows"], **solve)
+        service.append(time.perf_counter() - w0)
+    plain_rate = len(service) / sum(service)
+
+    srv = iht.Server(ds, max_slots=args.slots, hbm_budget=int(args.hbm_gb * 2**30), **solve)
+    _serve_run(iht, srv, reqs[:min(len(reqs), 2 * args.slots)], np.zeros(len(reqs)))   # warm-up
+    clocks = ClockSampler(gpu_uuid(torch, dev))
+    clocks.start()
+    time.sleep(0.3)
+    l0 = iht.iht_kernel_launches()
+    cap_walls, lat_all, iters = [], [], []
+    for _ in range(args.steps):
+        wall, lat, out = _serve_run(iht, srv, reqs, np.zeros(len(reqs)))
+        cap_walls.append(wall)
+        lat_all.append(lat)
+        iters += [r.iterations for r in out]
+    launches = iht.iht_kernel_launches() - l0
+    clk = clocks.stop()
+    st = srv.stats()
+    value = len(reqs) * args.steps / sum(cap_walls)
+    rng = np.random.Generator(np.random.PCG64(synth.BASE_SEED + 4099))
+    poisson = {}
+    for mult in (0.5, 1.2):
+        lam = mult * plain_rate
+        npo = min(len(reqs), args.poisson_requests)
+        arr = np.cumsum(rng.exponential(1.0 / lam, size=npo))
+        arr -= arr[0]
+        wall, lat, _ = _serve_run(iht, srv, reqs[:npo], arr)
+        plain_lat = _mg1_latency(service, arr)
+        poisson[f"{mult}x_plain_rate"] = {
+            "arrival_rate": lam, "requests": npo, "served_solves_per_s": npo / wall,
+            "p50_ms": 1e3 * float(np.percentile(lat, 50)), "p99_ms": 1e3 * float(np.percentile(lat, 99)),
+            "plain_p50_ms": 1e3 * float(np.percentile(plain_lat, 50)),
+            "plain_p99_ms": 1e3 * float(np.percentile(plain_lat, 99)),
+            "plain_latency": "one-at-a-time queue replayed with the measured iht_fit service times"}
+    srv.close()
+    if rank == 0:
+        lat = np.concatenate(lat_all)
+        h2d = sum(8 * q["y"].size + 4 * q["rows"].size for q in reqs)
+        d2h = sum(12 * q["k"] + 48 for q in reqs)
+        out = {
+            "metric": "served IHT solves/sec", "value": value, "unit": "solves/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * sum(cap_walls) / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": "f16 operands, f32 accumulate, f64 scalars", "data": "synthetic",
+            "config": {"workload": c["name"], "n": pn.n, "p": pn.p, "requests_per_step": len(reqs),
+                       "max_slots": args.slots, "hbm_budget_gib": args.hbm_gb,
+                       "iterations_per_solve": float(np.mean(iters)),
+                       "l2": "inputs larger than L2 (no flush)",
+                       "arrivals": "all queued at once (capacity)"},
+            "latency_ms_all_queued": {"p50": 1e3 * float(np.percentile(lat, 50)),
+                                      "p99": 1e3 * float(np.percentile(lat, 99))},
+            "plain": {"value": plain_rate, "unit": "solves/s", "requests": len(service),
+                      "what": "iht_fit one request at a time, host inputs"},
+            "speedup_vs_plain": value / plain_rate,
+            "poisson": poisson,
+            "server": {k: int(v) for k, v in st.items()},
+            "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": int(h2d),
+                    "d2h_bytes_per_step": int(d2h)},
+            "gpu_launches": int(launches), "clocks": clk,
+        }
+        print(json.dumps(out), flush=True)
+    del ds, ctx
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--config", type=int, default=2, choices=[1, 2, 3])
+    ap.add_argument("--config", type=int, default=2, choices=[1, 2, 3, 4])
+    ap.add_argument("--requests", type=int, default=2000)
+    ap.add_argument("--plain-requests", type=int, default=40)
+    ap.add_argument("--poisson-requests", type=int, default=300)
+    ap.add_argument("--slots", type=int, default=64)
+    ap.add_argument("--hbm-gb", type=float, default=64.0)
     ap.add_argument("--grad-impl", type=int, default=0, choices=[0, 1, 2])
     ap.add_argument("--oracle-iters", type=int, default=10)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     if args.config == 3:
         return cv_reference_arm(args) if args.impl == "reference" else cv_arm(args)
+    if args.config == 4:
+        return serve_reference_arm(args) if args.impl == "reference" else serve_arm(args)
     if args.impl == "reference":
         return reference_arm(args)
     return ours_arm(args)

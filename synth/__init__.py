@@ -138,13 +138,16 @@ def panel(n: int, p: int, seed: int, maf=("uniform", 0.05, 0.5), miss: float = 0
 def _pop_standardised(pn: Panel, snps: np.ndarray, rows: np.ndarray | None) -> np.ndarray:
     """Causal columns standardised with the population frequency (missing -> 0)."""
     codes = pn.codes(snps)                                    # [m, n]
-    dose = np.select([codes == 0, codes == 2, codes == 3], [0.0, 1.0, 2.0], 0.0)
+    if rows is not None:
+        codes = codes[:, rows]
+    dose = _DOSE[codes]                                       # missing -> 0 (zeroed below)
     q = pn.maf[snps][:, None]
     z = (dose - 2.0 * q) / np.sqrt(2.0 * q * (1.0 - q))
     z[codes == 1] = 0.0
-    if rows is not None:
-        z = z[:, rows]
     return z.T                                                # [n_rows, m]
+
+
+_DOSE = np.array([0.0, 0.0, 1.0, 2.0])
 
 
 def phenotype(pn: Panel, k_star: int, effect_var: float, noise_var: float, seed: int,
@@ -209,17 +212,37 @@ def cv_folds(n: int, folds: int, seed: int) -> np.ndarray:
     return lab
 
 
+def _request_phenotype(args):
+    pn, k_star, pseed, rows, h2 = args
+    return phenotype(pn, k_star, 1.0, 1.0, pseed, rows=rows, h2=h2)
+
+
 def serving_requests(pn: Panel, count: int, seed: int, n_lo: int = 2000, n_hi: int = 10000,
-                     k_lo: int = 5, k_hi: int = 200, h2_lo: float = 0.1, h2_hi: float = 0.6):
-    """Serving-stream requests: fresh phenotype, random subject subset, requested k."""
+                     k_lo: int = 5, k_hi: int = 200, h2_lo: float = 0.1, h2_hi: float = 0.6,
+                     workers: int = 1):
+    """Serving-stream requests: fresh phenotype, random subject subset, requested k.
+
+    The request parameters come from one sequential stream; the phenotypes
+    (own seeds) may be drawn by ``workers`` spawned processes, with identical
+    results.  Call it before any CUDA work in the process when workers > 1.
+    """
     rng = np.random.Generator(np.random.PCG64(seed))
-    out = []
+    params = []
     for r in range(count):
         n_rows = int(rng.integers(n_lo, min(n_hi, pn.n) + 1))
         rows = np.sort(rng.choice(pn.n, size=n_rows, replace=False)).astype(np.int32)
         k_star = int(rng.integers(k_lo, k_hi + 1))
         k = int(rng.integers(k_lo, k_hi + 1))
         h2 = float(rng.uniform(h2_lo, h2_hi))
-        y, causal, beta = phenotype(pn, k_star, 1.0, 1.0, seed * 7919 + r, rows=rows, h2=h2)
+        params.append((rows, k_star, k, h2, seed * 7919 + r))
+    jobs = [(pn, ks, ps, rows, h2) for rows, ks, _, h2, ps in params]
+    if workers > 1 and count > 1:
+        import multiprocessing as mp
+        with mp.get_context("spawn").Pool(workers) as pool:
+            phen = pool.map(_request_phenotype, jobs, chunksize=max(1, count // (4 * workers)))
+    else:
+        phen = [_request_phenotype(j) for j in jobs]
+    out = []
+    for (rows, k_star, k, h2, _), (y, causal, beta) in zip(params, phen):
         out.append(dict(rows=rows, y=y, k=k, k_star=k_star, h2=h2, causal=causal))
     return out
