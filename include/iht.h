@@ -248,7 +248,7 @@ int iht_gradient_batch(iht_dataset *ds, int32_t b, const int32_t *const *rows_li
  * pointers, copied at submission) arrive at any time.  A worker thread owned
  * by the server admits a pending request when a slot is free and its device
  * footprint (per-SNP statistics, gradient, residuals and scratch of one solve,
- * about 28 p + 56 n + 8 n ceil(k/4) bytes) fits in hbm_budget, then runs
+ * about 28 p + 56 n bytes plus a few kB) fits in hbm_budget, then runs
  * every admitted solve together: one iteration per tick, one multi-column
  * gradient pass over the packed genotypes for all active solves (each solve is
  * a column), the O(nk) steps batched.  A solve retires when it stops (same

@@ -26,7 +26,7 @@ void free_workspace(Workspace *ws)
 {
     if (!ws) return;
     void *ptrs[] = {ws->used, ws->rowmask, ws->counts, ws->u64, ws->v64, ws->u32, ws->v32,
-                    ws->y64, ws->r64, ws->zv, ws->rc64, ws->r32, ws->g, ws->Mj, ws->partials, ws->zpart, ws->rows_dev,
+                    ws->y64, ws->r64, ws->zv, ws->rc64, ws->r32, ws->g, ws->Mj, ws->partials, ws->rows_dev,
                     ws->ybuf, ws->fbuf, ws->cand, ws->S, ws->Sp, ws->bS, ws->bSp, ws->coef,
                     ws->cols, ws->sc};
     for (void *p : ptrs)
@@ -66,7 +66,6 @@ int ensure_workspace(iht_dataset *ds, int)
     ALLOC(g, sizeof(float) * p);
     ALLOC(Mj, sizeof(float) * p);
     ALLOC(partials, sizeof(double) * 3 * kPartials);
-    ALLOC(zpart, sizeof(double) * (size_t)kZmulMaxGroups * np);
     ALLOC(rows_dev, sizeof(int32_t) * np);
     ALLOC(ybuf, sizeof(double) * np);
     ALLOC(fbuf, sizeof(float) * np);
@@ -89,7 +88,7 @@ int ensure_workspace(iht_dataset *ds, int)
     }
     int rc = ensure_selwork(ds->ctx, p);
     if (rc) return rc;
-    if (ceil_div(ds->n_pad, 256) > kPartials) return IHT_EINVAL;   // n above 262k samples
+    if (zmul_blocks(ds) > kPartials) return IHT_EINVAL;   // n above 262k samples
     return IHT_OK;
 }
 

@@ -26,7 +26,7 @@ struct BatchWork {
     double *y64 = nullptr, *r64 = nullptr, *rc64 = nullptr, *zv = nullptr;
     float *r32 = nullptr, *g = nullptr;
     int32_t *S = nullptr, *Sp = nullptr, *cand = nullptr;
-    double *bS = nullptr, *bSp = nullptr, *coef = nullptr, *partials = nullptr, *zpart = nullptr;
+    double *bS = nullptr, *bSp = nullptr, *coef = nullptr, *partials = nullptr;
     SelState *st = nullptr;
     uint32_t *hist = nullptr, *chunk_eq = nullptr;
     BSolve *bs = nullptr, *bs_host = nullptr;
@@ -46,7 +46,7 @@ void free_batchwork(BatchWork *w)
 {
     if (!w) return;
     void *dev[] = {w->sc, w->y64, w->r64, w->rc64, w->zv, w->r32, w->g, w->S, w->Sp, w->cand,
-                   w->bS, w->bSp, w->coef, w->partials, w->zpart, w->st, w->hist, w->chunk_eq,
+                   w->bS, w->bSp, w->coef, w->partials, w->st, w->hist, w->chunk_eq,
                    w->bs, w->jobs, w->cols, w->set_used, w->set_err, w->set_rowmask, w->set_u64,
                    w->set_v64, w->set_u32, w->set_v32, w->rows_dev, w->ybuf};
     for (void *p : dev)
@@ -58,8 +58,6 @@ void free_batchwork(BatchWork *w)
         if (e) cudaEventDestroy(e);
     delete w;
 }
-
-static int kgroups(int k) { return (k + 3) / 4; }
 
 // Capacity for nb solves of sparsity <= kcap over nsets row sets, rows_total
 // staged row indices and y_total staged phenotype values.
@@ -101,7 +99,6 @@ static int ensure_batchwork(iht_dataset *ds, int nb, int kcap, int nsets, int64_
     BALLOC(bSp, sizeof(double) * B * K);
     BALLOC(coef, sizeof(double) * B * K);
     BALLOC(partials, sizeof(double) * B * 3 * kPartials);
-    BALLOC(zpart, sizeof(double) * B * kgroups(kcap) * np);
     BALLOC(st, sizeof(SelState) * 2 * B);
     BALLOC(hist, sizeof(uint32_t) * 2 * B * kSelBins);
     BALLOC(chunk_eq, sizeof(uint32_t) * 2 * B * nch);
@@ -366,7 +363,6 @@ int iht_fit_batch(iht_dataset *ds, int32_t b, const iht_solve_desc *solves,
         B.bSp = w->bSp + c * K;
         B.coef = w->coef + c * K;
         B.partials = w->partials + (size_t)c * 3 * kPartials;
-        B.zpart = w->zpart + (size_t)c * kgroups(w->kcap) * np;
         B.k = solves[c].k;
         B.K = (int32_t)std::min<int64_t>(2 * (int64_t)solves[c].k, ds->p);
         B.out_off = koff;

@@ -26,8 +26,7 @@ namespace iht {
 constexpr int kMaxK = 1024;            // largest sparsity level accepted
 constexpr int kMaxCand = 2 * kMaxK;    // candidate list of the projection
 constexpr int kSelBins = 2048;         // radix-select histogram bins
-constexpr int kPartials = 1024;        // max blocks of per-block partial sums (3 values each)
-constexpr int kZmulMaxGroups = 2 * kMaxK / 4;   // column groups of the sparse product
+constexpr int kPartials = 2048;        // max blocks of per-block partial sums (3 values each)
 
 struct Scalars {                       // device-resident state of one solve
     double num;                        // ||g_S||^2
@@ -64,7 +63,6 @@ struct BSolve {
     int32_t *S, *Sp, *cand;            // k, k, K
     double *bS, *bSp, *coef;           // k, k, k
     double *partials;                  // 3 * zmul blocks
-    double *zpart;                     // ceil(k / 4) * n_pad
     int32_t k, K;
     int64_t out_off;                   // offset of this solve in concatenated outputs
 };
@@ -161,7 +159,6 @@ struct Workspace {
     float *r32 = nullptr, *g = nullptr;
     float *Mj = nullptr;                   // per-SNP sum of r over missing calls
     double *partials = nullptr;        // kPartials * 2
-    double *zpart = nullptr;           // kZmulMaxGroups x n_pad partial products
     int32_t *rows_dev = nullptr;       // int32[n]: host row lists copied here
     double *ybuf = nullptr;            // double[n]: host phenotypes copied here
     float *fbuf = nullptr;             // float[n_pad]: scratch

@@ -453,6 +453,38 @@ int build_missing_lists(iht_dataset *ds)
     return IHT_OK;
 }
 
+// M_j = sum of r over the missing calls of SNP j.  The block stages r in
+// shared memory; each lane owns one SNP and reads its list 16 bytes (8 or 4
+// sample offsets) at a time, adding in list order.
+template <typename IdxT>
+__global__ void __launch_bounds__(512) k_missing_sum_smem(const int64_t *__restrict__ off,
+                                                          const IdxT *__restrict__ idx, int64_t p,
+                                                          const float *__restrict__ r32,
+                                                          int64_t n_pad, float *__restrict__ M,
+                                                          const int32_t *__restrict__ done)
+{
+    extern __shared__ float rs_miss[];
+    if (done && *done) return;
+    constexpr int kPer = 16 / (int)sizeof(IdxT);
+    for (int64_t i = threadIdx.x; i < n_pad; i += blockDim.x) rs_miss[i] = r32[i];
+    __syncthreads();
+    const uint4 *__restrict__ idx4 = reinterpret_cast<const uint4 *>(idx);
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < p;
+         j += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t e0 = off[j], e1 = off[j + 1];
+        float m = 0.0f;
+        for (int64_t a = e0 & ~(int64_t)(kPer - 1); a < e1; a += kPer) {
+            const uint4 w = idx4[a / kPer];
+            const IdxT *ent = reinterpret_cast<const IdxT *>(&w);
+#pragma unroll
+            for (int t = 0; t < kPer; ++t)
+                if (a + t >= e0 && a + t < e1) m += rs_miss[ent[t]];
+        }
+        M[j] = m;
+    }
+}
+
+// (global-memory variant for residuals too long for shared memory)
 // M_j = sum of r over the missing calls of SNP j.  Four lanes per SNP (eight
 // SNPs per warp, 16 list entries in flight per group), fixed summation order.
 template <typename IdxT>
@@ -488,6 +520,28 @@ __global__ void __launch_bounds__(256) k_missing_sum(const int64_t *__restrict__
 int launch_missing_sums(iht_dataset *ds, const float *r32, float *M, const int32_t *done)
 {
     cudaStream_t s = ds->ctx->stream;
+    const size_t smem = sizeof(float) * (size_t)ds->n_pad;
+    if (smem <= 160 * 1024) {
+        static thread_local int configured = -1;
+        if (configured != ds->ctx->device) {
+            IHT_CUDA(cudaFuncSetAttribute(k_missing_sum_smem<uint16_t>,
+                                          cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024));
+            IHT_CUDA(cudaFuncSetAttribute(k_missing_sum_smem<int32_t>,
+                                          cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024));
+            configured = ds->ctx->device;
+        }
+        const int per_sm = smem <= 48 * 1024 ? 3 : 1;
+        const int blocks = (int)std::min<int64_t>(ceil_div(ds->p, 512), (int64_t)ds->ctx->num_sms * per_sm);
+        if (ds->miss_idx16)
+            k_missing_sum_smem<uint16_t><<<blocks, 512, smem, s>>>(
+                ds->miss_off, (const uint16_t *)ds->miss_idx, ds->p, r32, ds->n_pad, M, done);
+        else
+            k_missing_sum_smem<int32_t><<<blocks, 512, smem, s>>>(
+                ds->miss_off, (const int32_t *)ds->miss_idx, ds->p, r32, ds->n_pad, M, done);
+        note_launch();
+        IHT_CUDA(cudaGetLastError());
+        return IHT_OK;
+    }
     const int blocks = (int)std::min<int64_t>(ceil_div(ds->p, 64), (int64_t)ds->ctx->num_sms * 16);
     if (ds->miss_idx16)
         k_missing_sum<uint16_t><<<blocks, 256, 0, s>>>(ds->miss_off, (const uint16_t *)ds->miss_idx,

@@ -56,7 +56,7 @@ struct SlotMem {
     double *y64, *r64, *rc64, *zv;
     float *r32, *g;
     int32_t *S, *Sp, *cand;
-    double *bS, *bSp, *coef, *partials, *zpart;
+    double *bS, *bSp, *coef, *partials;
     SelState *st;
     uint32_t *hist, *chunk_eq;
     int32_t *rows;
@@ -110,7 +110,6 @@ static size_t slot_layout(const iht_dataset *ds, int k, int64_t n_rows, char *ba
     t.bSp = (double *)take(sizeof(double) * k);
     t.coef = (double *)take(sizeof(double) * k);
     t.partials = (double *)take(sizeof(double) * 3 * kPartials);
-    t.zpart = (double *)take(sizeof(double) * (size_t)((k + 3) / 4) * np);
     t.st = (SelState *)take(sizeof(SelState) * 2);
     t.hist = (uint32_t *)take(sizeof(uint32_t) * 2 * kSelBins);
     t.chunk_eq = (uint32_t *)take(sizeof(uint32_t) * 2 * nch);
@@ -221,7 +220,6 @@ static int srv_admit_setup(iht_server *S, const std::vector<int> &fresh, std::ve
         B.bSp = m.bSp;
         B.coef = m.coef;
         B.partials = m.partials;
-        B.zpart = m.zpart;
         B.k = q.k;
         B.K = sl.K;
         B.out_off = 0;
@@ -476,7 +474,7 @@ int iht_server_create(iht_dataset *ds, const iht_server_options *opt_in, iht_ser
     if (opt.max_slots < 1 || opt.max_slots > 1024 || so.max_iter < 0 || so.max_backtrack < 0 ||
         !(so.kappa > 1.0) || !(so.c >= 0.0 && so.c < 1.0) || !(so.tol >= 0.0))
         return IHT_EINVAL;
-    if (!grad_mrhs_supported(ds) || ceil_div(ds->n_pad, 256) > kPartials) return IHT_EINVAL;
+    if (!grad_mrhs_supported(ds) || zmul_blocks(ds) > kPartials) return IHT_EINVAL;
     DeviceGuard g(ds->ctx->device);
     if (!g.ok) return IHT_ECUDA;
     iht_server *S = new (std::nothrow) iht_server();

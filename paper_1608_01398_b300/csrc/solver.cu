@@ -29,6 +29,26 @@ __device__ __forceinline__ int dosage_of(uint32_t code)   // -1 = missing
     return code == 0u ? 0 : (code == 2u ? 1 : (code == 3u ? 2 : -1));
 }
 
+// Sums of the per-block partial triples (stride 3) by one full warp: lane l
+// adds blocks l, l + 32, ... in order, then a fixed shuffle tree; every lane
+// gets the totals (deterministic, and 32 loads in flight instead of one).
+__device__ __forceinline__ void warp_partials(const double *__restrict__ partials, int npart,
+                                              double &s, double &s2, double &d2)
+{
+    const int lane = threadIdx.x & 31;
+    s = 0.0;
+    s2 = 0.0;
+    d2 = 0.0;
+    for (int b = lane; b < npart; b += 32) {
+        s += partials[3 * b];
+        s2 += partials[3 * b + 1];
+        d2 += partials[3 * b + 2];
+    }
+    s = warp_sum(s);
+    s2 = warp_sum(s2);
+    d2 = warp_sum(d2);
+}
+
 __device__ __forceinline__ void gather_gS_body(const float *__restrict__ g,
                                                const int32_t *__restrict__ S, int k,
                                                double *__restrict__ coef, Scalars *sc)
@@ -52,77 +72,63 @@ __global__ void __launch_bounds__(1024) k_gather_gS(const float *__restrict__ g,
     gather_gS_body(g, S, k, coef, sc);
 }
 
-constexpr int kZmulColsPerGroup = 4;   // columns per block of the first phase
+// out_i = base_i + sum_c a_c (x_i,col_c - u_col_c), a_c = sign coef_c v_col_c, over
+// the observed calls (Z[:, cols] coef, Sec. 2.3.2-2.3.3), on used rows (0
+// elsewhere); per-block sums of out, out^2 and (out - prev)^2 (0 without
+// prev) go to partials[3 b .. 3 b + 2].  One thread per sample, kZmulThreads
+// samples per block; each column's three possible terms a (x - u) for
+// x = 0, 1, 2 are staged in shared memory kZmulChunk columns at a time, so a
+// term costs one FP64 add (FP64 issue is the scarce resource here), added in
+// column order.
+constexpr int kZmulChunk = 256;
+constexpr int kZmulThreads = 128;
 
-// Phase 1: block (x, y) = (256 packed bytes x 4 columns): one thread per byte
-// of a column group; per-sample partial sums of group y go to part[y][i].
-__device__ __forceinline__ void zmul_part_body(const uint8_t *__restrict__ G, int64_t stride,
-                                               int64_t rowb, const int32_t *__restrict__ cols,
-                                               int m, const double *__restrict__ coef, double sign,
-                                               const double *__restrict__ u64,
-                                               const double *__restrict__ v64,
-                                               double *__restrict__ part, int64_t n_pad)
-{
-    const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const int c0 = blockIdx.y * kZmulColsPerGroup;
-    if (b >= stride) return;
-    double acc[4] = {0.0, 0.0, 0.0, 0.0};
-    uint32_t by[kZmulColsPerGroup];
-    double a[kZmulColsPerGroup], bb[kZmulColsPerGroup];
-#pragma unroll
-    for (int q = 0; q < kZmulColsPerGroup; ++q) {
-        const int c = c0 + q;
-        by[q] = 0x55u;
-        a[q] = 0.0;
-        bb[q] = 0.0;
-        if (c < m) {
-            const int col = cols[c];
-            by[q] = b < rowb ? __ldg(G + (int64_t)col * stride + b) : 0x55u;
-            a[q] = sign * coef[c] * v64[col];
-            bb[q] = a[q] * u64[col];
-        }
-    }
-#pragma unroll
-    for (int q = 0; q < kZmulColsPerGroup; ++q) {
-#pragma unroll
-        for (int e = 0; e < 4; ++e) {
-            const int x = dosage_of((by[q] >> (2 * e)) & 3u);
-            if (x >= 0) acc[e] += a[q] * (double)x - bb[q];
-        }
-    }
-    double *dst = part + (int64_t)blockIdx.y * n_pad + 4 * b;
-#pragma unroll
-    for (int e = 0; e < 4; ++e) dst[e] = acc[e];
-}
-
-__global__ void __launch_bounds__(256) k_zmul_part(const uint8_t *__restrict__ G, int64_t stride,
-                                                   int64_t rowb, const int32_t *__restrict__ cols,
-                                                   int m, const double *__restrict__ coef, double sign,
-                                                   const double *__restrict__ u64,
-                                                   const double *__restrict__ v64,
-                                                   double *__restrict__ part, int64_t n_pad,
-                                                   const int32_t *__restrict__ done)
-{
-    if (done && *done) return;
-    zmul_part_body(G, stride, rowb, cols, m, coef, sign, u64, v64, part, n_pad);
-}
-
-// Phase 2: out_i = base_i + sum over groups (fixed order) on used rows, 0
-// elsewhere; per-block sums of out, out^2 and (out - prev)^2 (0 without prev)
-// into partials[3 b .. 3 b + 2].
-__device__ __forceinline__ void zmul_sum_body(const double *__restrict__ part, int ngroups,
-                                              int64_t n_pad, const int32_t *__restrict__ used,
-                                              const double *__restrict__ base,
-                                              const double *__restrict__ prev,
-                                              double *__restrict__ out,
-                                              double *__restrict__ partials)
+__device__ __forceinline__ void zmul_body(const uint8_t *__restrict__ G, int64_t stride,
+                                          int64_t rowb, const int32_t *__restrict__ cols, int m,
+                                          const double *__restrict__ coef, double sign,
+                                          const double *__restrict__ u64,
+                                          const double *__restrict__ v64,
+                                          const int32_t *__restrict__ used,
+                                          const double *__restrict__ base,
+                                          const double *__restrict__ prev, double *__restrict__ out,
+                                          double *__restrict__ partials, int64_t n_pad)
 {
     __shared__ double red[8];
+    __shared__ double term[kZmulChunk][4];     // terms for codes 00, 01 (missing: 0), 10, 11
+    __shared__ const uint8_t *srow[kZmulChunk];
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t byte = i >> 2;
+    const int shift = 2 * (int)(i & 3);
+    const bool inb = i < n_pad && byte < rowb;
+    double acc = 0.0;
+    for (int c0 = 0; c0 < m; c0 += kZmulChunk) {
+        const int mc = min(kZmulChunk, m - c0);
+        __syncthreads();
+        for (int c = threadIdx.x; c < mc; c += blockDim.x) {
+            const int col = cols[c0 + c];
+            const double a = sign * coef[c0 + c] * v64[col];
+            const double b = a * u64[col];
+            term[c][0] = a * 0.0 - b;
+            term[c][1] = 0.0;
+            term[c][2] = a * 1.0 - b;
+            term[c][3] = a * 2.0 - b;
+            srow[c] = G + (int64_t)col * stride;
+        }
+        __syncthreads();
+        if (inb) {
+            int c = 0;
+            for (; c + 4 <= mc; c += 4) {
+                uint32_t b[4];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) b[q] = __ldg(srow[c + q] + byte);
+#pragma unroll
+                for (int q = 0; q < 4; ++q) acc += term[c + q][(b[q] >> shift) & 3u];
+            }
+            for (; c < mc; ++c) acc += term[c][((uint32_t)__ldg(srow[c] + byte) >> shift) & 3u];
+        }
+    }
     double o = 0.0, d = 0.0;
     if (i < n_pad) {
-        double acc = 0.0;
-        for (int g = 0; g < ngroups; ++g) acc += part[(int64_t)g * n_pad + i];
         o = used[i] ? (base ? base[i] : 0.0) + acc : 0.0;
         out[i] = o;
         if (prev) d = o - prev[i];
@@ -137,19 +143,22 @@ __device__ __forceinline__ void zmul_sum_body(const double *__restrict__ part, i
     }
 }
 
-__global__ void __launch_bounds__(256) k_zmul_sum(const double *__restrict__ part, int ngroups,
-                                                  int64_t n_pad, const int32_t *__restrict__ used,
-                                                  const double *__restrict__ base,
-                                                  const double *__restrict__ prev,
-                                                  double *__restrict__ out,
-                                                  double *__restrict__ partials,
-                                                  const int32_t *__restrict__ done)
+__global__ void __launch_bounds__(kZmulThreads) k_zmul(const uint8_t *__restrict__ G, int64_t stride,
+                                              int64_t rowb, const int32_t *__restrict__ cols, int m,
+                                              const double *__restrict__ coef, double sign,
+                                              const double *__restrict__ u64,
+                                              const double *__restrict__ v64,
+                                              const int32_t *__restrict__ used,
+                                              const double *__restrict__ base,
+                                              const double *__restrict__ prev,
+                                              double *__restrict__ out, double *__restrict__ partials,
+                                              int64_t n_pad, const int32_t *__restrict__ done)
 {
     if (done && *done) return;
-    zmul_sum_body(part, ngroups, n_pad, used, base, prev, out, partials);
+    zmul_body(G, stride, rowb, cols, m, coef, sign, u64, v64, used, base, prev, out, partials, n_pad);
 }
 
-int zmul_blocks(const iht_dataset *ds) { return ceil_div(ds->n_pad, 256); }
+int zmul_blocks(const iht_dataset *ds) { return ceil_div(ds->n_pad, kZmulThreads); }
 
 // out = base + sign * Z[:, cols] coef (device, stream-ordered); partials get
 // zmul_blocks() triples (sum, sum of squares, sum of (out - prev)^2) when not
@@ -158,17 +167,9 @@ int zmul_run(iht_dataset *ds, const int32_t *cols, int m, const double *coef, do
              const double *u, const double *v, const int32_t *used, const double *base,
              double *out, double *partials, const int32_t *done, const double *prev = nullptr)
 {
-    cudaStream_t s = ds->ctx->stream;
-    const int ngroups = std::max(1, (m + kZmulColsPerGroup - 1) / kZmulColsPerGroup);
-    if (ngroups > kZmulMaxGroups) return IHT_EINVAL;
-    if (m > 0) {
-        dim3 grid(ceil_div(ds->stride, 256), ngroups);
-        k_zmul_part<<<grid, 256, 0, s>>>(ds->G, ds->stride, ds->rowb, cols, m, coef, sign, u, v,
-                                         ds->ws->zpart, ds->n_pad, done);
-        note_launch();
-    }
-    k_zmul_sum<<<zmul_blocks(ds), 256, 0, s>>>(ds->ws->zpart, m > 0 ? ngroups : 0, ds->n_pad, used,
-                                               base, prev, out, partials, done);
+    k_zmul<<<zmul_blocks(ds), kZmulThreads, 0, ds->ctx->stream>>>(ds->G, ds->stride, ds->rowb, cols, m, coef,
+                                                         sign, u, v, used, base, prev, out, partials,
+                                                         ds->n_pad, done);
     note_launch();
     IHT_CUDA(cudaGetLastError());
     return IHT_OK;
@@ -201,6 +202,7 @@ struct MergeArgs {
 constexpr int kMergeThreads = 1024;
 constexpr int kMergeU = 3 * kMaxK;      // |S u C| <= k + 2k
 constexpr int kMergeSort = 4 * kMaxK;   // power of two >= kMergeU
+constexpr int kMergeRank = 768;         // up to this many candidates: selection by rank
 
 struct MergeShared {
     int32_t uidx[kMergeU];
@@ -278,13 +280,16 @@ __device__ __forceinline__ void merge_body(const MergeArgs &A)
     Scalars *sc = A.sc;
     const int k = sc->k;
 
+    double den = 0.0;
+    if (A.first && threadIdx.x < 32) {
+        double s_, d2_;
+        warp_partials(A.partials, A.npart, s_, den, d2_);
+    }
     if (threadIdx.x == 0) {
         sh.stop = 0;
         sh.nS_extra = 0;
         if (A.first) {
             // step size mu = ||g_S||^2 / ||Z_S g_S||^2 (reading of Sec. 2.3.1)
-            double den = 0.0;
-            for (int b = 0; b < A.npart; ++b) den += A.partials[3 * b + 1];
             const double num = sc->num;
             sc->bt_last = 0;
             if (num == 0.0) {
@@ -343,14 +348,31 @@ __device__ __forceinline__ void merge_body(const MergeArgs &A)
     __syncthreads();
     const int nU = K + sh.nS_extra;
 
-    for (int u = threadIdx.x; u < nU; u += blockDim.x)
+    for (int u = threadIdx.x; u < nU; u += blockDim.x) {
         sh.uw[u] = __dadd_rn(sh.ubeta[u], __dmul_rn(mu, sh.ug[u]));
+        sh.skey[u] = (unsigned long long)__double_as_longlong(fabs(sh.uw[u]));
+    }
     __syncthreads();
-    sort_by_w(sh, nU);
-    for (int u = threadIdx.x; u < nU; u += blockDim.x) sh.inSp[u] = 0;
-    __syncthreads();
-    for (int r = threadIdx.x; r < k; r += blockDim.x) sh.inSp[sh.spos[r]] = 1;
-    __syncthreads();
+    const bool small = nU <= kMergeRank;
+    if (small) {
+        // S+ by rank: u is in S+ iff fewer than k entries come before it
+        // (|w| descending, index ascending); every thread reads the same v
+        // at the same time (shared-memory broadcast)
+        for (int u = threadIdx.x; u < nU; u += blockDim.x) {
+            const unsigned long long ku = sh.skey[u];
+            const int32_t iu = sh.uidx[u];
+            int rank = 0;
+            for (int v = 0; v < nU; ++v) rank += before(sh.skey[v], sh.uidx[v], ku, iu) ? 1 : 0;
+            sh.inSp[u] = rank < k ? 1 : 0;
+        }
+        __syncthreads();
+    } else {
+        sort_by_w(sh, nU);
+        for (int u = threadIdx.x; u < nU; u += blockDim.x) sh.inSp[u] = 0;
+        __syncthreads();
+        for (int r = threadIdx.x; r < k; r += blockDim.x) sh.inSp[sh.spos[r]] = 1;
+        __syncthreads();
+    }
     int kept = 0;
     double dd = 0.0, bb = 0.0;
     for (int u = threadIdx.x; u < nU; u += blockDim.x) {
@@ -364,6 +386,24 @@ __device__ __forceinline__ void merge_body(const MergeArgs &A)
     bb = block_sum(bb, sh.red);
 
     // S+ in index order with beta+
+    if (small) {
+        // position of u among the members of S+ = members with a lower index
+        for (int u = threadIdx.x; u < nU; u += blockDim.x) {
+            if (!sh.inSp[u]) continue;
+            const int32_t iu = sh.uidx[u];
+            int pos = 0;
+            for (int v = 0; v < nU; ++v) pos += (sh.inSp[v] && sh.uidx[v] < iu) ? 1 : 0;
+            A.Sp[pos] = iu;
+            A.bSp[pos] = sh.uw[u];
+        }
+        if (threadIdx.x == 0) {
+            sc->changed = kept < k ? 1 : 0;
+            sc->dd = dd;
+            sc->bb = bb;
+        }
+        return;
+    }
+    __syncthreads();
     for (int r = threadIdx.x; r < kMergeSort; r += blockDim.x) sh.skey[r] = ~0ull;
     __syncthreads();
     for (int r = threadIdx.x; r < k; r += blockDim.x) {
@@ -422,13 +462,9 @@ __device__ __forceinline__ void decide_body(Scalars *sc, const double *partials,
 {
     __shared__ int accept;
     const int k = sc->k;
+    double s = 0.0, s2 = 0.0, zz = 0.0;
+    if (threadIdx.x < 32) warp_partials(partials, npart, s, s2, zz);
     if (threadIdx.x == 0) {
-        double s = 0.0, s2 = 0.0, zz = 0.0;
-        for (int b = 0; b < npart; ++b) {
-            s += partials[3 * b];
-            s2 += partials[3 * b + 1];
-            zz += partials[3 * b + 2];
-        }
         accept = 1;
         if (sc->changed && zz > 0.0) {
             const double omega = (1.0 - sc->c) * sc->dd / zz;
@@ -483,21 +519,21 @@ __global__ void __launch_bounds__(256) k_decide(Scalars *sc, const double *parti
 }
 
 // Objective of beta = 0 (r = y) before the first iteration (one thread).
+// One full warp; lane 0 writes.
 __device__ __forceinline__ void init_objective_body(Scalars *sc, const double *partials, int npart)
 {
-    double s = 0.0, s2 = 0.0;
-    for (int b = 0; b < npart; ++b) {
-        s += partials[3 * b];
-        s2 += partials[3 * b + 1];
+    double s, s2, d2;
+    warp_partials(partials, npart, s, s2, d2);
+    if (threadIdx.x == 0) {
+        sc->sum_r = s;
+        sc->sumsq_r = s2;
+        sc->f = 0.5 * s2;
     }
-    sc->sum_r = s;
-    sc->sumsq_r = s2;
-    sc->f = 0.5 * s2;
 }
 
 __global__ void k_init_objective(Scalars *sc, const double *partials, int npart)
 {
-    if (sc->done || threadIdx.x != 0) return;
+    if (sc->done) return;
     init_objective_body(sc, partials, npart);
 }
 
@@ -777,38 +813,27 @@ __device__ __forceinline__ bool zmul_gate(const BSolve &B, int which)
     return sc->live && !sc->done;
 }
 
-__global__ void __launch_bounds__(256) k_zmul_part_b(const uint8_t *__restrict__ G, int64_t stride,
-                                                     int64_t rowb, const BSolve *bs, int which,
-                                                     int64_t n_pad)
-{
-    const BSolve &B = bs[blockIdx.z];
-    if (!zmul_gate(B, which)) return;
-    const int m = which == kZmulInit ? 0 : B.k;
-    if ((int)blockIdx.y * kZmulColsPerGroup >= m) return;     // beyond this solve's groups
-    if (which == kZmulStep)
-        zmul_part_body(G, stride, rowb, B.S, m, B.coef, 1.0, B.u64, B.v64, B.zpart, n_pad);
-    else
-        zmul_part_body(G, stride, rowb, B.Sp, m, B.bSp, -1.0, B.u64, B.v64, B.zpart, n_pad);
-}
-
-__global__ void __launch_bounds__(256) k_zmul_sum_b(const BSolve *bs, int which, int64_t n_pad)
+__global__ void __launch_bounds__(kZmulThreads) k_zmul_b(const uint8_t *__restrict__ G, int64_t stride,
+                                                int64_t rowb, const BSolve *bs, int which,
+                                                int64_t n_pad)
 {
     const BSolve &B = bs[blockIdx.y];
     if (!zmul_gate(B, which)) return;
-    const int m = which == kZmulInit ? 0 : B.k;
-    const int ngroups = (m + kZmulColsPerGroup - 1) / kZmulColsPerGroup;
     if (which == kZmulInit)
-        zmul_sum_body(B.zpart, 0, n_pad, B.used, B.y64, nullptr, B.r64, B.partials);
+        zmul_body(G, stride, rowb, nullptr, 0, nullptr, -1.0, B.u64, B.v64, B.used, B.y64, nullptr,
+                  B.r64, B.partials, n_pad);
     else if (which == kZmulStep)
-        zmul_sum_body(B.zpart, ngroups, n_pad, B.used, nullptr, nullptr, B.zv, B.partials);
+        zmul_body(G, stride, rowb, B.S, B.k, B.coef, 1.0, B.u64, B.v64, B.used, nullptr, nullptr,
+                  B.zv, B.partials, n_pad);
     else
-        zmul_sum_body(B.zpart, ngroups, n_pad, B.used, B.y64, B.r64, B.rc64, B.partials);
+        zmul_body(G, stride, rowb, B.Sp, B.k, B.bSp, -1.0, B.u64, B.v64, B.used, B.y64, B.r64,
+                  B.rc64, B.partials, n_pad);
 }
 
 __global__ void k_init_objective_b(const BSolve *bs, int npart)
 {
     const BSolve &B = bs[blockIdx.x];
-    if (!B.sc->fresh || B.sc->done || threadIdx.x != 0) return;
+    if (!B.sc->fresh || B.sc->done) return;
     init_objective_body(B.sc, B.partials, npart);
 }
 
@@ -913,16 +938,10 @@ int launch_gather_gS_batch(iht_dataset *ds, const BSolve *bs, int nb)
     return IHT_OK;
 }
 
-int launch_zmul_batch(iht_dataset *ds, const BSolve *bs, int nb, int kmax, ZmulWhich which)
+int launch_zmul_batch(iht_dataset *ds, const BSolve *bs, int nb, int, ZmulWhich which)
 {
-    cudaStream_t s = ds->ctx->stream;
-    if (which != kZmulInit) {
-        const int ngroups = std::max(1, (kmax + kZmulColsPerGroup - 1) / kZmulColsPerGroup);
-        dim3 grid(ceil_div(ds->stride, 256), ngroups, nb);
-        k_zmul_part_b<<<grid, 256, 0, s>>>(ds->G, ds->stride, ds->rowb, bs, (int)which, ds->n_pad);
-        note_launch();
-    }
-    k_zmul_sum_b<<<dim3(zmul_blocks(ds), nb), 256, 0, s>>>(bs, (int)which, ds->n_pad);
+    k_zmul_b<<<dim3(zmul_blocks(ds), nb), kZmulThreads, 0, ds->ctx->stream>>>(ds->G, ds->stride, ds->rowb, bs,
+                                                                   (int)which, ds->n_pad);
     note_launch();
     IHT_CUDA(cudaGetLastError());
     return IHT_OK;
