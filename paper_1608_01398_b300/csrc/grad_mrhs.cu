@@ -57,7 +57,7 @@ constexpr int kMrMaxBufs = 8;               // A buffers of 2 K-steps
 constexpr int kMrMaxN = 224;                // accumulator columns per tile
 constexpr int kMrMaxCols = kMrMaxN / 2;     // residual columns per pass
 constexpr size_t kMrSmemMax = 220 * 1024;
-constexpr uint32_t kMrSpin = 1u << 26;
+constexpr uint32_t kMrSpin = 1u << 24;             // bounded waits (each poll may suspend up to 128 ns)
 
 __device__ __forceinline__ uint32_t mr_smem(const void *p)
 {
@@ -139,10 +139,10 @@ __device__ __forceinline__ bool mr_wait(uint64_t *bar, uint32_t parity)
     for (uint32_t it = 0; it < kMrSpin; ++it) {
         uint32_t ok;
         asm volatile(
-            "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+            "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n"
             "selp.u32 %0, 1, 0, p;\n}\n"
             : "=r"(ok)
-            : "r"(a), "r"(parity)
+            : "r"(a), "r"(parity), "n"(128)
             : "memory");
         if (ok) return true;
     }
@@ -230,18 +230,34 @@ __device__ __forceinline__ uint64_t mr_b_desc(uint32_t saddr)
 }
 
 // F16 dosage map of one word of 16 codes: output j = samples j and j + 8.
+// Shifts as multiplies / high multiplies (FMA pipe); the decode is bound by
+// the integer pipe, which then only does the masks.
+__device__ __forceinline__ uint32_t mr_shl(uint32_t x, uint32_t pow2)
+{
+    uint32_t y;
+    asm("mul.lo.u32 %0, %1, %2;" : "=r"(y) : "r"(x), "r"(pow2));
+    return y;
+}
+
+__device__ __forceinline__ uint32_t mr_shr(uint32_t x, uint32_t pow2)   // x >> (32 - log2 pow2)
+{
+    uint32_t y;
+    asm("mul.hi.u32 %0, %1, %2;" : "=r"(y) : "r"(x), "r"(pow2));
+    return y;
+}
+
 __device__ __forceinline__ void mr_decode(uint32_t w, uint32_t *a)
 {
-    const uint32_t f = w & ((w >> 1) | 0xAAAAAAAAu);
+    const uint32_t f = w & (mr_shr(w, 0x80000000u) | 0xAAAAAAAAu);
     const uint32_t m = 0x0C000C00u;
-    a[0] = (f << 10) & m;
-    a[1] = (f << 8) & m;
-    a[2] = (f << 6) & m;
-    a[3] = (f << 4) & m;
-    a[4] = (f << 2) & m;
+    a[0] = mr_shl(f, 1024u) & m;
+    a[1] = mr_shl(f, 256u) & m;
+    a[2] = mr_shl(f, 64u) & m;
+    a[3] = mr_shl(f, 16u) & m;
+    a[4] = mr_shl(f, 4u) & m;
     a[5] = f & m;
-    a[6] = (f >> 2) & m;
-    a[7] = (f >> 4) & m;
+    a[6] = mr_shr(f, 0x40000000u) & m;
+    a[7] = mr_shr(f, 0x10000000u) & m;
 }
 
 struct MrPipe {

@@ -64,7 +64,7 @@ constexpr int kTcNWG = 4;                          // decoder warpgroups per CTA
 constexpr int kTcThreads = kTcNWG * (128 + 32 + 32);   // decoders, MMA warps, TMA warps
 constexpr int kTcStageTile = 128 * kTcStageBytes;  // 8 KB
 
-constexpr uint32_t kTcSpin = 1u << 26;             // bounded waits
+constexpr uint32_t kTcSpin = 1u << 24;             // bounded waits (each poll may suspend up to 128 ns)
 
 struct TcParams {
     float s0;        // scale of limb 0 (limb l: s0 * 2^-4l)
@@ -159,10 +159,10 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity)
     for (uint32_t it = 0; it < kTcSpin; ++it) {
         uint32_t ok;
         asm volatile(
-            "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+            "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n"
             "selp.u32 %0, 1, 0, p;\n}\n"
             : "=r"(ok)
-            : "r"(a), "r"(parity)
+            : "r"(a), "r"(parity), "n"(128)
             : "memory");
         if (ok) return true;
     }
@@ -267,17 +267,32 @@ struct TcPipe {
     uint64_t accempty;              // decoders -> MMA warp: accumulators read out (128)
 };
 
-// One 16-byte chunk (64 samples = 2 K-steps) of the row into half h of A
-// buffer `buf`.
-__device__ __forceinline__ void tc_put_chunk(uint32_t tb, uint32_t lane_off, uint32_t buf, int h,
-                                             uint4 x)
+__device__ __forceinline__ void tmem_st32(uint32_t taddr, const uint32_t (&v)[32])
 {
-    uint32_t v[16];
-    decode_word(x.x, &v[0]);
-    decode_word(x.y, &v[4]);
-    decode_word(x.z, &v[8]);
-    decode_word(x.w, &v[12]);
-    tmem_st16(tb + 32 + 32 * buf + 16 * h + lane_off, v);
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,"
+        "%13,%14,%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31,%32};" ::"r"(taddr),
+        "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7]),
+        "r"(v[8]), "r"(v[9]), "r"(v[10]), "r"(v[11]), "r"(v[12]), "r"(v[13]), "r"(v[14]), "r"(v[15]),
+        "r"(v[16]), "r"(v[17]), "r"(v[18]), "r"(v[19]), "r"(v[20]), "r"(v[21]), "r"(v[22]), "r"(v[23]),
+        "r"(v[24]), "r"(v[25]), "r"(v[26]), "r"(v[27]), "r"(v[28]), "r"(v[29]), "r"(v[30]), "r"(v[31])
+        : "memory");
+}
+
+// One group of two 16-byte chunks (128 samples = 4 K-steps) of the row into A
+// buffer `buf` with one 32-column store (x1 is zero past the row's last chunk).
+__device__ __forceinline__ void tc_put_group(uint32_t taddr, uint4 x0, uint4 x1)
+{
+    uint32_t v[32];
+    decode_word(x0.x, &v[0]);
+    decode_word(x0.y, &v[4]);
+    decode_word(x0.z, &v[8]);
+    decode_word(x0.w, &v[12]);
+    decode_word(x1.x, &v[16]);
+    decode_word(x1.y, &v[20]);
+    decode_word(x1.z, &v[24]);
+    decode_word(x1.w, &v[28]);
+    tmem_st32(taddr, v);
 }
 
 // Read out the accumulator of local tile t and write g for this thread's row.
@@ -386,10 +401,14 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_grad_tc(const __grid_constant
         uint32_t buf = 0, bphase = 0;           // A-buffer ring
         int T = 0;
         bool ok = true;
-        const int cps = kTcStageBytes / kTcGroupBytes;                 // chunks per stage
+        const int cps = kTcStageBytes / kTcGroupBytes;                 // chunks per stage (4)
+        // swizzled offsets of the stage's four 16-byte chunks in this thread's row
+        const int swz = (r >> 1) & 3;
+        const uint32_t off0 = (uint32_t)((0 ^ swz) << 4), off1 = (uint32_t)((1 ^ swz) << 4);
+        const uint32_t off2 = (uint32_t)((2 ^ swz) << 4), off3 = (uint32_t)((3 ^ swz) << 4);
+        const uint32_t abase = tb + 32 + lane_off;
         for (int64_t tile = (int64_t)blockIdx.x * kTcNWG + w; tile < ntiles && ok; tile += tile_step, ++T) {
             const int64_t row = tile * 128 + r;
-            int h = 0;                                                  // half of the current group
             for (int st = 0; st < spt && ok; ++st) {
                 if (!mbar_wait(&P.tma_full[slot], sphase)) {
                     abort_flag = 1;
@@ -397,29 +416,26 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_grad_tc(const __grid_constant
                 }
                 const uint8_t *base = stages + (w * nst + slot) * kTcStageTile + r * kTcStageBytes;
                 const int nchunks = min(cps, ngroups - st * cps);
-                for (int c = 0; c < nchunks && ok; ++c) {
-                    const int gi = st * cps + c;                        // chunk within the tile
-                    const uint4 x = *reinterpret_cast<const uint4 *>(base + ((c ^ ((r >> 1) & 3)) << 4));
-                    if (h == 0 && grp >= kTcBufs) {
+                for (int c = 0; c < nchunks && ok; c += 2) {              // one A group per pair
+                    const uint4 x0 = *reinterpret_cast<const uint4 *>(base + (c == 0 ? off0 : off2));
+                    uint4 x1 = make_uint4(0u, 0u, 0u, 0u);
+                    if (c + 1 < nchunks)
+                        x1 = *reinterpret_cast<const uint4 *>(base + (c == 0 ? off1 : off3));
+                    if (grp >= kTcBufs) {
                         if (!mbar_wait(&P.empty[buf], bphase ^ 1u)) {
                             abort_flag = 1;
                             ok = false;
                         }
                         tc_fence_after();
                     }
-                    tc_put_chunk(tb, lane_off, buf, h, x);
-                    if (h == 1 || gi == ngroups - 1) {                  // group complete
-                        asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
-                        tc_fence_before();
-                        mbar_arrive(&P.full[buf]);
-                        ++grp;
-                        if (++buf == kTcBufs) {
-                            buf = 0;
-                            bphase ^= 1u;
-                        }
-                        h = 0;
-                    } else {
-                        h = 1;
+                    tc_put_group(abase + 32 * buf, x0, x1);
+                    asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+                    tc_fence_before();
+                    mbar_arrive(&P.full[buf]);
+                    ++grp;
+                    if (++buf == kTcBufs) {
+                        buf = 0;
+                        bphase ^= 1u;
                     }
                 }
                 mbar_arrive(&P.tma_empty[slot]);
