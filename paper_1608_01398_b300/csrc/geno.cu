@@ -111,7 +111,60 @@ int setup_rows(iht_dataset *ds, const int32_t *rows_dev, int64_t n_rows)
     return setup_rowset(ds, rows_dev, n_rows, workspace_rowset(ds), &ds->ws->sc->err);
 }
 
-// One warp per SNP: masked popcounts, then the FP64 statistics.
+constexpr int kCountUnroll = 4;        // 16-byte words per lane and SNP in flight (2 KB of a row)
+
+// FP64 statistics from the integer counts, every operation correctly rounded
+// (Sec. 2.3.2: mean over observed calls, variance with n_obs - 1).
+__device__ __forceinline__ void snp_stats(int64_t n_rows, int c1, int c2, int c3, double &mean,
+                                          double &inv_sd)
+{
+    const double n_obs = (double)(n_rows - c1);
+    const double s1 = (double)(c2 + 2 * c3);
+    const double s2 = (double)(c2 + 4 * c3);
+    mean = n_obs > 0.0 ? __ddiv_rn(s1, n_obs) : 0.0;
+    inv_sd = 0.0;
+    if (n_obs >= 2.0) {
+        const double var = __ddiv_rn(__dsub_rn(s2, __ddiv_rn(__dmul_rn(s1, s1), n_obs)),
+                                     __dsub_rn(n_obs, 1.0));
+        if (var > 0.0) inv_sd = __ddiv_rn(1.0, __dsqrt_rn(var));
+    }
+}
+
+// This lane's masked counts (missing, het, hom-alt) over one pass of a row.
+__device__ __forceinline__ void count_words(const uint4 (&w4)[kCountUnroll], const uint4 *mask4,
+                                            int64_t c0, int lane, int64_t nw4, int &c1, int &c2,
+                                            int &c3)
+{
+#pragma unroll
+    for (int u = 0; u < kCountUnroll; ++u) {
+        const int64_t c = c0 + lane + 32 * u;
+        if (c >= nw4) break;
+        const uint4 m4 = __ldg(mask4 + c);
+        const uint32_t ws[4] = {w4[u].x & m4.x, w4[u].y & m4.y, w4[u].z & m4.z, w4[u].w & m4.w};
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const uint32_t lo = ws[q] & 0x55555555u, hi = (ws[q] >> 1) & 0x55555555u;
+            c3 += __popc(lo & hi);
+            c1 += __popc(lo & ~hi);
+            c2 += __popc(hi & ~lo);
+        }
+    }
+}
+
+__device__ __forceinline__ void load_pass(const uint4 *row4, int64_t c0, int lane, int64_t nw4,
+                                          uint4 (&w4)[kCountUnroll])
+{
+#pragma unroll
+    for (int u = 0; u < kCountUnroll; ++u) {
+        const int64_t c = c0 + lane + 32 * u;
+        w4[u] = c < nw4 ? __ldcs(row4 + c) : make_uint4(0u, 0u, 0u, 0u);
+    }
+}
+
+// A warp takes 32 consecutive SNPs: two at a time it counts (all loads of
+// both rows in flight) and reduces across the lanes, lane s keeping SNP s's
+// totals; then every lane computes its SNP's FP64 statistics at once and the
+// warp writes 32 consecutive entries.
 __global__ void __launch_bounds__(256) k_counts(const uint8_t *__restrict__ G, int64_t p,
                                                 int64_t stride, int64_t rowb,
                                                 const uint32_t *__restrict__ rowmask,
@@ -121,48 +174,46 @@ __global__ void __launch_bounds__(256) k_counts(const uint8_t *__restrict__ G, i
 {
     const int lane = threadIdx.x & 31;
     const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
-    const int64_t nwords = rowb / 4;
-    for (int64_t j = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); j < p;
-         j += nwarps) {
-        const uint32_t *row = reinterpret_cast<const uint32_t *>(G + j * stride);
-        int c1 = 0, c2 = 0, c3 = 0;
-        const uint4 *row4 = reinterpret_cast<const uint4 *>(row);
-        const uint4 *mask4 = reinterpret_cast<const uint4 *>(rowmask);
-        for (int64_t c = lane; c < nwords / 4; c += 32) {
-            const uint4 w4 = __ldcs(row4 + c), m4 = __ldg(mask4 + c);
-            const uint32_t ws[4] = {w4.x & m4.x, w4.y & m4.y, w4.z & m4.z, w4.w & m4.w};
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                const uint32_t lo = ws[q] & 0x55555555u, hi = (ws[q] >> 1) & 0x55555555u;
-                c3 += __popc(lo & hi);
-                c1 += __popc(lo & ~hi);
-                c2 += __popc(hi & ~lo);
+    const int64_t nw4 = rowb / 16;
+    const uint4 *mask4 = reinterpret_cast<const uint4 *>(rowmask);
+    for (int64_t base = ((int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * 32; base < p;
+         base += nwarps * 32) {
+        int m1 = 0, m2 = 0, m3 = 0;                 // totals of SNP base + lane
+        for (int s = 0; s < 32 && base + s < p; s += 2) {
+            const int64_t ja = base + s;
+            const bool two = s + 1 < 32 && ja + 1 < p;
+            const uint4 *ra = reinterpret_cast<const uint4 *>(G + ja * stride);
+            const uint4 *rb = reinterpret_cast<const uint4 *>(G + (two ? ja + 1 : ja) * stride);
+            int a1 = 0, a2 = 0, a3 = 0, b1 = 0, b2 = 0, b3 = 0;
+            for (int64_t c0 = 0; c0 < nw4; c0 += 32 * kCountUnroll) {
+                uint4 wa[kCountUnroll], wb[kCountUnroll];
+                load_pass(ra, c0, lane, nw4, wa);
+                load_pass(rb, c0, lane, nw4, wb);
+                count_words(wa, mask4, c0, lane, nw4, a1, a2, a3);
+                count_words(wb, mask4, c0, lane, nw4, b1, b2, b3);
             }
-        }
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            c1 += __shfl_xor_sync(0xffffffffu, c1, o);
-            c2 += __shfl_xor_sync(0xffffffffu, c2, o);
-            c3 += __shfl_xor_sync(0xffffffffu, c3, o);
+            for (int o = 16; o > 0; o >>= 1) {
+                a1 += __shfl_xor_sync(0xffffffffu, a1, o);
+                a2 += __shfl_xor_sync(0xffffffffu, a2, o);
+                a3 += __shfl_xor_sync(0xffffffffu, a3, o);
+                b1 += __shfl_xor_sync(0xffffffffu, b1, o);
+                b2 += __shfl_xor_sync(0xffffffffu, b2, o);
+                b3 += __shfl_xor_sync(0xffffffffu, b3, o);
+            }
+            if (lane == s) { m1 = a1; m2 = a2; m3 = a3; }
+            if (two && lane == s + 1) { m1 = b1; m2 = b2; m3 = b3; }
         }
-        if (lane == 0) {
-            const int64_t c0 = n_rows - c1 - c2 - c3;
+        const int64_t j = base + lane;
+        if (j < p) {
             if (counts) {
-                counts[4 * j + 0] = (int32_t)c0;
-                counts[4 * j + 1] = c1;
-                counts[4 * j + 2] = c2;
-                counts[4 * j + 3] = c3;
+                counts[4 * j + 0] = (int32_t)(n_rows - m1 - m2 - m3);
+                counts[4 * j + 1] = m1;
+                counts[4 * j + 2] = m2;
+                counts[4 * j + 3] = m3;
             }
-            const double n_obs = (double)(n_rows - c1);
-            const double s1 = (double)(c2 + 2 * c3);
-            const double s2 = (double)(c2 + 4 * c3);
-            const double mean = n_obs > 0.0 ? __ddiv_rn(s1, n_obs) : 0.0;
-            double inv_sd = 0.0;
-            if (n_obs >= 2.0) {
-                const double var = __ddiv_rn(__dsub_rn(s2, __ddiv_rn(__dmul_rn(s1, s1), n_obs)),
-                                             __dsub_rn(n_obs, 1.0));
-                if (var > 0.0) inv_sd = __ddiv_rn(1.0, __dsqrt_rn(var));
-            }
+            double mean, inv_sd;
+            snp_stats(n_rows, m1, m2, m3, mean, inv_sd);
             u64[j] = mean;
             v64[j] = inv_sd;
             u32[j] = (float)mean;
@@ -173,7 +224,7 @@ __global__ void __launch_bounds__(256) k_counts(const uint8_t *__restrict__ G, i
 
 int launch_counts_rowset(iht_dataset *ds, int64_t n_rows, const RowSet &rs)
 {
-    const int blocks = (int)std::min<int64_t>(ceil_div(ds->p, 8), (int64_t)ds->ctx->num_sms * 16);
+    const int blocks = (int)std::min<int64_t>(ceil_div(ds->p, 8 * 32), (int64_t)ds->ctx->num_sms * 8);
     k_counts<<<blocks, 256, 0, ds->ctx->stream>>>(ds->G, ds->p, ds->stride, ds->rowb, rs.rowmask,
                                                   n_rows, rs.counts, rs.u64, rs.v64, rs.u32, rs.v32);
     note_launch();
@@ -203,52 +254,68 @@ __global__ void __launch_bounds__(256) k_counts_multi(const uint8_t *__restrict_
 {
     const int lane = threadIdx.x & 31;
     const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
-    const int64_t nwords = rowb / 4;
-    for (int64_t j = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); j < p;
-         j += nwarps) {
-        const uint4 *row4 = reinterpret_cast<const uint4 *>(G + j * stride);
-        int c1[NS], c2[NS], c3[NS];
+    const int64_t nw4 = rowb / 16;
+    for (int64_t base = ((int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * 32; base < p;
+         base += nwarps * 32) {
+        int m1[NS], m2[NS], m3[NS];                 // totals of SNP base + lane, per set
 #pragma unroll
-        for (int q = 0; q < NS; ++q) c1[q] = c2[q] = c3[q] = 0;
-        for (int64_t c = lane; c < nwords / 4; c += 32) {
-            const uint4 w4 = __ldcs(row4 + c);
+        for (int q = 0; q < NS; ++q) m1[q] = m2[q] = m3[q] = 0;
+        for (int s = 0; s < 32 && base + s < p; ++s) {
+            const uint4 *row4 = reinterpret_cast<const uint4 *>(G + (base + s) * stride);
+            int c1[NS], c2[NS], c3[NS];
+#pragma unroll
+            for (int q = 0; q < NS; ++q) c1[q] = c2[q] = c3[q] = 0;
+            for (int64_t c0 = 0; c0 < nw4; c0 += 32 * kCountUnroll) {
+                uint4 w4[kCountUnroll];
+                load_pass(row4, c0, lane, nw4, w4);
+#pragma unroll
+                for (int u = 0; u < kCountUnroll; ++u) {
+                    const int64_t c = c0 + lane + 32 * u;
+                    if (c >= nw4) break;
+                    // the genotype word split once into its lo / hi bit planes
+                    const uint32_t wv[4] = {w4[u].x, w4[u].y, w4[u].z, w4[u].w};
+                    uint32_t lo[4], hi[4];
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) {
+                        lo[e] = wv[e] & 0x55555555u;
+                        hi[e] = (wv[e] >> 1) & 0x55555555u;
+                    }
+#pragma unroll
+                    for (int q = 0; q < NS; ++q) {
+                        const uint4 mk = __ldg(reinterpret_cast<const uint4 *>(ms.rowmask[q]) + c);
+                        const uint32_t mv[4] = {mk.x & 0x55555555u, mk.y & 0x55555555u,
+                                                mk.z & 0x55555555u, mk.w & 0x55555555u};
+#pragma unroll
+                        for (int e = 0; e < 4; ++e) {
+                            const uint32_t l = lo[e] & mv[e], h = hi[e] & mv[e];
+                            c3[q] += __popc(l & h);
+                            c1[q] += __popc(l & ~h);
+                            c2[q] += __popc(h & ~l);
+                        }
+                    }
+                }
+            }
 #pragma unroll
             for (int q = 0; q < NS; ++q) {
-                const uint4 m4 = __ldg(reinterpret_cast<const uint4 *>(ms.rowmask[q]) + c);
-                const uint32_t ws[4] = {w4.x & m4.x, w4.y & m4.y, w4.z & m4.z, w4.w & m4.w};
 #pragma unroll
-                for (int e = 0; e < 4; ++e) {
-                    const uint32_t lo = ws[e] & 0x55555555u, hi = (ws[e] >> 1) & 0x55555555u;
-                    c3[q] += __popc(lo & hi);
-                    c1[q] += __popc(lo & ~hi);
-                    c2[q] += __popc(hi & ~lo);
+                for (int o = 16; o > 0; o >>= 1) {
+                    c1[q] += __shfl_xor_sync(0xffffffffu, c1[q], o);
+                    c2[q] += __shfl_xor_sync(0xffffffffu, c2[q], o);
+                    c3[q] += __shfl_xor_sync(0xffffffffu, c3[q], o);
+                }
+                if (lane == s) {
+                    m1[q] = c1[q];
+                    m2[q] = c2[q];
+                    m3[q] = c3[q];
                 }
             }
         }
-#pragma unroll
-        for (int q = 0; q < NS; ++q) {
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) {
-                c1[q] += __shfl_xor_sync(0xffffffffu, c1[q], o);
-                c2[q] += __shfl_xor_sync(0xffffffffu, c2[q], o);
-                c3[q] += __shfl_xor_sync(0xffffffffu, c3[q], o);
-            }
-        }
-        if (lane < NS) {
-            // lane q finishes set q (registers indexed by a compile-time loop)
+        const int64_t j = base + lane;
+        if (j < p) {
 #pragma unroll
             for (int q = 0; q < NS; ++q) {
-                if (q != lane) continue;
-                const double n_obs = (double)(ms.n_rows[q] - c1[q]);
-                const double s1 = (double)(c2[q] + 2 * c3[q]);
-                const double s2 = (double)(c2[q] + 4 * c3[q]);
-                const double mean = n_obs > 0.0 ? __ddiv_rn(s1, n_obs) : 0.0;
-                double inv_sd = 0.0;
-                if (n_obs >= 2.0) {
-                    const double var = __ddiv_rn(__dsub_rn(s2, __ddiv_rn(__dmul_rn(s1, s1), n_obs)),
-                                                 __dsub_rn(n_obs, 1.0));
-                    if (var > 0.0) inv_sd = __ddiv_rn(1.0, __dsqrt_rn(var));
-                }
+                double mean, inv_sd;
+                snp_stats(ms.n_rows[q], m1[q], m2[q], m3[q], mean, inv_sd);
                 ms.u64[q][j] = mean;
                 ms.v64[q][j] = inv_sd;
                 ms.u32[q][j] = (float)mean;
@@ -261,7 +328,7 @@ __global__ void __launch_bounds__(256) k_counts_multi(const uint8_t *__restrict_
 template <int NS>
 static int launch_counts_multi_n(iht_dataset *ds, const MultiSets &ms)
 {
-    const int blocks = (int)std::min<int64_t>(ceil_div(ds->p, 8), (int64_t)ds->ctx->num_sms * 16);
+    const int blocks = (int)std::min<int64_t>(ceil_div(ds->p, 8 * 32), (int64_t)ds->ctx->num_sms * 8);
     k_counts_multi<NS><<<blocks, 256, 0, ds->ctx->stream>>>(ds->G, ds->p, ds->stride, ds->rowb, ms);
     note_launch();
     IHT_CUDA(cudaGetLastError());

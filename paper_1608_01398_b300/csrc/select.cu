@@ -54,12 +54,30 @@ __device__ __forceinline__ void sel_hist_body(const float *__restrict__ keys, in
     __syncthreads();
     const uint32_t prefix = st->prefix, mask = st->mask;
     bool nan = false;
-    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < p;
-         j += (int64_t)gridDim.x * blockDim.x) {
-        const uint32_t k = sel_key(keys[j]);
+    // 16-byte loads, two in flight per thread, over the 16-byte aligned middle of
+    // keys; the (at most 3 + 3) keys before and after it one at a time
+    auto one = [&](float x) {
+        const uint32_t k = sel_key(x);
         nan |= k > 0x7f800000u;
         if ((k & mask) == prefix) atomicAdd(&sh[(k >> shift) & dmask], 1u);
+    };
+    const int64_t head = std::min<int64_t>(p, (int64_t)((16u - ((uintptr_t)keys & 15u)) & 15u) >> 2);
+    const float4 *k4 = reinterpret_cast<const float4 *>(keys + head);
+    const int64_t n4 = (p - head) >> 2, step = (int64_t)gridDim.x * blockDim.x;
+    const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    int64_t q = tid;
+    for (; q + step < n4; q += 2 * step) {
+        const float4 a = k4[q], b = k4[q + step];
+        one(a.x); one(a.y); one(a.z); one(a.w);
+        one(b.x); one(b.y); one(b.z); one(b.w);
     }
+    if (q < n4) {
+        const float4 a = k4[q];
+        one(a.x); one(a.y); one(a.z); one(a.w);
+    }
+    if (tid < head) one(keys[tid]);
+    const int64_t t = head + (n4 << 2) + tid;
+    if (t < p) one(keys[t]);
     if (nan && shift == 20) atomicOr(&st->err, 1u);
     __syncthreads();
     for (int b = threadIdx.x; b < kSelBins; b += blockDim.x)

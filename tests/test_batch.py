@@ -230,3 +230,17 @@ def test_fit_batch_matches_single_solves(iht, ctx):
             assert np.array_equal(fs.support, fb.support)
             assert rel_err(fb.beta, fs.beta) <= BTOL
             assert fs.iterations == fb.iterations
+
+
+def test_fit_batch_odd_p(iht, ctx):
+    """p not a multiple of 4: per-solve gradient rows start off 16-byte boundaries."""
+    n, p = 500, 1003
+    G, codes, y, _, rng = _signal_panel(31, n, p, 3, effect=0.7)
+    ds = load(iht, ctx, G)
+    probs = [(y, 3, None), (y, 5, None), (y, 2, None)]
+    res = iht.iht_fit_batch(ds, probs)
+    for (yy, k, rows), fg in zip(probs, res):
+        check_solve(oracle.iht(G, yy, k, rows=rows), fg)
+        s = iht.iht_fit(ds, yy, k, rows=rows)
+        if certified(oracle.iht(G, yy, k, rows=rows)):
+            assert np.array_equal(s.support, fg.support)

@@ -261,3 +261,16 @@ def test_fullsize_fit(iht, cfg2):
     fo = oracle.iht(G, y, 50)
     assert compare_fits(fo, fg, 50) >= min(5, fo.iterations)
     assert np.count_nonzero(fg.beta) <= 50
+
+
+@pytest.mark.parametrize("offset", [1, 2, 3])
+def test_topk_unaligned_keys(iht, ctx, offset):
+    """Keys that do not start on a 16-byte boundary (a slice of a larger array)."""
+    torch = _torch()
+    rng = np.random.default_rng(offset)
+    p, k = 50003, 37
+    w = rng.normal(size=p + offset).astype(np.float32)
+    wd = torch.from_numpy(w).cuda()[offset:]
+    idx = iht.iht_topk(ctx, wd, k).cpu().numpy()
+    ww = w[offset:].astype(np.float64)
+    assert np.array_equal(idx, np.sort(np.lexsort((np.arange(p), -np.abs(ww)))[:k]))
