@@ -53,6 +53,14 @@ import synth  # noqa: E402
 
 FALLBACK_HBM_GBS = 6400.0
 
+# DRAM bytes (read + write) of one single-column gradient launch on the
+# n = 5000, p = 500 000 panel, from one ncu capture of this kernel version
+# (dram__bytes_read.sum + dram__bytes_write.sum; summary in profiles/).
+K1_TRAFFIC_BYTES = 646332672 + 4857856
+# The same for the first multi-column launch of the cross-validation batch
+# (100 solves = 200 limb columns), the only launch with every solve active.
+K2_TRAFFIC_FIRST_LAUNCH_BYTES = 1557640192 + 380114688
+
 
 def log(*a):
     print(*a, file=sys.stderr, flush=True)
@@ -287,7 +295,8 @@ def ours_arm(args):
                        "parallelism": "replicas" if world > 1 else "single"},
             "genotype_gbs": achieved, "pct_hbm_peak": (100.0 * achieved / hbm_peak) if achieved else None,
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
-                         "frac": (achieved / hbm_peak) if achieved else None, "traffic": None,
+                         "frac": (achieved / hbm_peak) if achieved else None,
+                         "traffic": K1_TRAFFIC_BYTES if cfg == 2 else None,
                          "kernel": "gradient pass g = Z^T r", "peak_source": peak_kind,
                          "algorithmic_bytes_per_launch": alg_bytes},
             "e2e": {"value": e2e_value, "unit": "iter/s", "h2d_bytes_per_step": 8 * n + 120,
@@ -488,7 +497,9 @@ def cv_arm(args):
                       "iterations": plain_its},
             "speedup_vs_plain": value / (b / plain_s),
             "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                         "frac": (achieved / peak) if achieved else None, "traffic": None,
+                         "frac": (achieved / peak) if achieved else None,
+                         "traffic": None,
+                         "traffic_first_launch": K2_TRAFFIC_FIRST_LAUNCH_BYTES,
                          "kernel": "multi-column gradient pass (k_grad_mrhs)",
                          "peak_source": peak_kind,
                          "algorithmic_flops": "2 n p per residual limb column, two limb columns "
