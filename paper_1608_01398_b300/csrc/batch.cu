@@ -427,9 +427,10 @@ int iht_fit_batch(iht_dataset *ds, int32_t b, const iht_solve_desc *solves,
         }
         active();
     }
-    int timed_out = 0;
+    int timed_out = 0, tc_timed_out = 0;
     if (opt.grad_impl != 1 && (rc = grad_mrhs_status(ds, &timed_out))) return rc;
-    if (timed_out) return IHT_ETIMEOUT;
+    if (opt.grad_impl == 0 && (rc = grad_tc_status(ds, &tc_timed_out))) return rc;
+    if (timed_out || tc_timed_out) return IHT_ETIMEOUT;
     double grad_ms = 0.0;
     const int nprof = pe.n;
     for (int e = 0; prof && e < nprof; ++e) {
@@ -519,9 +520,10 @@ int iht_gradient_batch(iht_dataset *ds, int32_t b, const int32_t *const *rows_li
     cudaStream_t s = ds->ctx->stream;
     IHT_CUDA(cudaMemcpyAsync(G_out, w->g, sizeof(float) * b * p, cudaMemcpyDeviceToDevice, s));
     IHT_CUDA(cudaStreamSynchronize(s));
-    int timed_out = 0;
+    int timed_out = 0, tc_timed_out = 0;
     if (impl != 1 && (rc = grad_mrhs_status(ds, &timed_out))) return rc;
-    return timed_out ? IHT_ETIMEOUT : IHT_OK;
+    if (impl == 0 && (rc = grad_tc_status(ds, &tc_timed_out))) return rc;
+    return timed_out || tc_timed_out ? IHT_ETIMEOUT : IHT_OK;
 }
 
 }  // extern "C"

@@ -224,6 +224,10 @@ int launch_grad_tc(iht_dataset *ds, const float *r32, float *g, const int32_t *d
 bool grad_tc_supported(const iht_dataset *ds);
 int prepare_grad_tc(iht_dataset *ds, const float *r32, const int32_t *done);
 int launch_grad_tc_main(iht_dataset *ds, const float *r32, float *g, const int32_t *done);
+int prepare_grad_tc_to(iht_dataset *ds, const float *r32, float *Mj, const int32_t *done);
+int launch_grad_tc_main_with(iht_dataset *ds, const float *r32, float *g, const float *u32,
+                             const float *v32, const float *Mj, const int32_t *done);
+void grad_tc_release_thread();
 int grad_tc_status(iht_dataset *ds, int *timed_out);
 // impl: 0 default (tensor cores when supported), 1 CUDA cores, 2 tensor cores
 int launch_grad_impl(iht_dataset *ds, int impl, const float *r32, float *g, const int32_t *done);

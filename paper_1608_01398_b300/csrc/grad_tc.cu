@@ -594,8 +594,9 @@ static int make_gmap(const iht_dataset *ds, CUtensorMap *map)
     return r == CUDA_SUCCESS ? IHT_OK : IHT_ECUDA;
 }
 
-// Residual -> limb image (and its scale and sum) for the next tensor-core pass.
-int prepare_grad_tc(iht_dataset *ds, const float *r32, const int32_t *done)
+// Residual -> limb image (and its scale and sum) for the next tensor-core pass,
+// and the missing-call sums of r into Mj (p floats).
+int prepare_grad_tc_to(iht_dataset *ds, const float *r32, float *Mj, const int32_t *done)
 {
     if (!grad_tc_supported(ds)) return IHT_EINVAL;
     cudaStream_t s = ds->ctx->stream;
@@ -617,11 +618,18 @@ int prepare_grad_tc(iht_dataset *ds, const float *r32, const int32_t *done)
     k_limbs<<<1, 1024, 0, s>>>(r32, (int64_t)ksteps * kTcStepSamples, w.bimg, w.prm, done);
     note_launch();
     IHT_CUDA(cudaGetLastError());
-    return launch_missing_sums(ds, r32, ds->ws->Mj, done);
+    return launch_missing_sums(ds, r32, Mj, done);
 }
 
-// The gradient pass proper (after prepare_grad_tc on the same stream).
-int launch_grad_tc_main(iht_dataset *ds, const float *r32, float *g, const int32_t *done)
+int prepare_grad_tc(iht_dataset *ds, const float *r32, const int32_t *done)
+{
+    return prepare_grad_tc_to(ds, r32, ds->ws->Mj, done);
+}
+
+// The gradient pass proper (after prepare_grad_tc on the same stream) with
+// explicit statistics and missing-call sums.
+int launch_grad_tc_main_with(iht_dataset *ds, const float *r32, float *g, const float *u32,
+                             const float *v32, const float *Mj, const int32_t *done)
 {
     cudaStream_t s = ds->ctx->stream;
     CUtensorMap map;
@@ -639,11 +647,24 @@ int launch_grad_tc_main(iht_dataset *ds, const float *r32, float *g, const int32
     const int64_t tiles = (ds->p + 127) / 128;
     const int grid = (int)std::min<int64_t>((tiles + kTcNWG - 1) / kTcNWG, (int64_t)ds->ctx->num_sms);
     k_grad_tc<<<grid, kTcThreads, smem, s>>>(map, ds->p, ngroups, tc_stages(ds), g_tc.bimg, (int)bbytes,
-                                              ds->ws->Mj,
-                                              ds->ws->u32, ds->ws->v32, g, g_tc.prm, done);
+                                              Mj, u32, v32, g, g_tc.prm, done);
     note_launch();
     IHT_CUDA(cudaGetLastError());
     return IHT_OK;
+}
+
+int launch_grad_tc_main(iht_dataset *ds, const float *r32, float *g, const int32_t *done)
+{
+    return launch_grad_tc_main_with(ds, r32, g, ds->ws->u32, ds->ws->v32, ds->ws->Mj, done);
+}
+
+// Frees the calling thread's pass scratch (a server's worker before it exits).
+void grad_tc_release_thread()
+{
+    TcWork &w = g_tc;
+    if (w.bimg) cudaFree(w.bimg);
+    if (w.prm) cudaFree(w.prm);
+    w = TcWork();
 }
 
 int launch_grad_tc(iht_dataset *ds, const float *r32, float *g, const int32_t *done)

@@ -407,9 +407,10 @@ static void srv_run(iht_server *S)
         if ((rc = srv_tick(S, fresh))) break;
         if ((rc = srv_retire(S))) break;
         if ((S->st.ticks & 15) == 0) {             // bounded waits of the gradient passes
-            int timed_out = 0;
+            int timed_out = 0, tc_timed_out = 0;
             if ((rc = grad_mrhs_status(&S->view, &timed_out))) break;
-            if (timed_out) {
+            if ((rc = grad_tc_status(&S->view, &tc_timed_out))) break;
+            if (timed_out || tc_timed_out) {
                 rc = IHT_ETIMEOUT;
                 break;
             }
@@ -421,6 +422,7 @@ static void srv_run(iht_server *S)
     }
     cudaStreamSynchronize(S->ctx.stream);
     grad_mrhs_release_thread();
+    grad_tc_release_thread();
 }
 
 static size_t srv_footprint(const iht_dataset *ds, int k, int64_t n_rows)
