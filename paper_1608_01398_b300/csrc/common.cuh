@@ -323,4 +323,11 @@ __device__ __forceinline__ double block_sum(double x, double *sh)
 
 inline int ceil_div(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
 
+// g = v (S1 - u (R - M)) with every operation rounded on its own (no
+// contraction), so the single- and multi-column passes give the same value.
+__device__ __forceinline__ float standardise(float S1, float R, float M, float u, float v)
+{
+    return __fmul_rn(v, __fsub_rn(S1, __fmul_rn(u, __fsub_rn(R, M))));
+}
+
 }  // namespace iht

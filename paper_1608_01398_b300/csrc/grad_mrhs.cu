@@ -11,43 +11,48 @@
 // GEMM of the 2-bit matrix against the b residual columns: one pass over the
 // packed genotypes serves all b solves.
 //
-// Operands (kind::f16, both F16, FP32 accumulate, M = 128 SNPs, K = 16):
+// Operands (kind::f8f6f4, both E4M3, FP32 accumulate, M = 128 SNPs, K = 32),
+// the same numbers as the single-column pass (grad_tc.cu), column by column:
 //   A: the dosage map in tensor memory, decoded by CUDA-core warps from the
-//      TMA-staged 2-bit codes: the two-bit field f = (c1, c1 & c0) of a code
-//      (00 for hom-ref and missing, 10 het, 11 hom-alt) placed in the F16
-//      exponent gives 0, 2^-13, 2^-12 = 2^-13 x, two instructions per pair of
-//      samples.  32-bit column j of a K-step holds samples j (low half) and
-//      j + 8 (high half) of the step's 16.
-//   B: each residual column as two F16 limbs, hi = f16(r / s), lo = f16(r / s
-//      - hi), s a power of two with max|r| / s < 2^15 (22 significant bits),
+//      TMA-staged 2-bit codes: the field f = (c1, c1 & c0) of a code (00 for
+//      hom-ref and missing, 10 het, 11 hom-alt) moved to bits 3-4 of a byte is
+//      the E4M3 value 2^-5 x; output word j of an input word holds samples
+//      4k + j (byte k).
+//   B: each residual column as 5 E4M3 limbs r ~ sum_l s_l q_l, s_l = s_0 2^-4l,
+//      s_0 = 2^ceil(log2(max|r| / 448)) (the single-column pass's limbs), one
+//      B row per limb (row 5c + l for column c), N = 5 b rounded up to 16,
 //      stored per K-step in the canonical K-major layout (8-row x 16-byte core
-//      matrices) in the same permuted sample order, N = 2 b rounded up to 16.
-//   So S1 = 2^13 s (acc_hi + acc_lo).
+//      matrices) in the same permuted sample order as A.
+//   So S1 = 32 sum_l s_l acc_l, summed over l in the single-column order.
 //
 // One persistent CTA per SM handles two 128-SNP tiles at a time, so every B
-// chunk it streams from L2 feeds two MMAs.  Warps 0-7 decode (warps 4t..4t+3
-// own tile t, thread = SNP row = tensor-memory lane) and run the epilogue,
-// warp 8 issues the MMAs, warp 9 streams genotype tiles (TMA 2D, 64-byte
-// swizzle), warp 10 streams B chunks (bulk copies).  Tensor memory (512
+// chunk it streams from L2 feeds two MMAs.  Warps 0-15 decode (warps 8t..8t+7
+// own tile t, thread = SNP row = tensor-memory lane; two groups of four per
+// tile take alternate A buffers) and run the epilogue, warp 16 issues the
+// MMAs, warp 17 streams genotype tiles (TMA 2D, 64-byte swizzle), warp 18
+// streams B chunks (bulk copies).  Tensor memory (512
 // columns): accumulator of tile t at column 256 t, its A buffers right after
 // it.  The epilogue writes S1; a second pass (k_miss_finalize) adds the
 // missing-call sums from the per-SNP lists and forms g, so this kernel's
 // epilogue only stores.  Every wait is bounded and reports a timeout through
 // an error word instead of hanging.
 #include <cuda.h>
-#include <cuda_fp16.h>
+#include <cuda_fp8.h>
 
 #include "common.cuh"
 
 namespace iht {
 
 constexpr int kMrTiles = 2;                 // 128-SNP tiles per CTA tile
-constexpr int kMrDecoders = 128 * kMrTiles; // decoder / epilogue threads
+constexpr int kMrDecGroups = 2;             // decoder groups per tile (alternate A buffers)
+constexpr int kMrDecoders = 128 * kMrTiles * kMrDecGroups;   // decoder / epilogue threads
+constexpr int kMrBufArrivals = 128 * kMrTiles;               // decoders that fill one A buffer
 constexpr int kMrMmaWarp = kMrDecoders / 32;
 constexpr int kMrGWarp = kMrMmaWarp + 1;
 constexpr int kMrBWarp = kMrMmaWarp + 2;
 constexpr int kMrThreads = kMrDecoders + 96;
-constexpr int kMrStepSamples = 16;          // K of one MMA
+constexpr int kMrStepSamples = 32;          // K of one MMA
+constexpr int kMrLimbs = 5;                 // E4M3 limbs per residual column
 constexpr int kMrGStageBytes = 64;          // packed bytes per row per TMA stage (256 samples)
 constexpr int kMrGTile = 128 * kMrGStageBytes;
 constexpr int kMrGStages = 4;
@@ -55,7 +60,7 @@ constexpr int kMrChunkSteps = 4;            // K-steps per B chunk
 constexpr int kMrMaxBStages = 6;
 constexpr int kMrMaxBufs = 8;               // A buffers of 2 K-steps
 constexpr int kMrMaxN = 224;                // accumulator columns per tile
-constexpr int kMrMaxCols = kMrMaxN / 2;     // residual columns per pass
+constexpr int kMrMaxCols = kMrMaxN / kMrLimbs;   // residual columns per pass (44)
 constexpr size_t kMrSmemMax = 220 * 1024;
 constexpr uint32_t kMrSpin = 1u << 24;             // bounded waits (each poll may suspend up to 128 ns)
 
@@ -65,15 +70,21 @@ __device__ __forceinline__ uint32_t mr_smem(const void *p)
 }
 
 // ---------------------------------------------------------------------------
-// Residual columns -> F16 limb image.  One block per column.  Also the
-// column's scale and sum R (FP64, fixed order, as the single-column pass).
+// Residual columns -> E4M3 limb image.  One block per column; the scale, the
+// limbs and the sum R (FP64, fixed order) follow the single-column pass's
+// arithmetic exactly.
 
+// Byte offset of sample i, limb row q: K-step s = i / 32; inside the step,
+// sample 16 wi + 4 k + j sits at K position 4 (4 wi + j) + k, the order in
+// which the decoded A words hold it.
 __device__ __forceinline__ int64_t mr_b_offset(int64_t i, int q, int N)
 {
-    const int64_t s = i >> 4;
-    const int ii = (int)(i & 15);
-    const int kp = 2 * (ii & 7) + (ii >> 3);               // K position within the step
-    return s * (int64_t)N * 32 + (q >> 3) * 256 + (kp >> 3) * 128 + (q & 7) * 16 + (kp & 7) * 2;
+    const int64_t s = i >> 5;
+    const int ii = (int)(i & 31);
+    const int wi = ii >> 4, q16 = ii & 15;
+    const int k = q16 >> 2, j = q16 & 3;
+    const int kpos = 4 * (4 * wi + j) + k;
+    return s * (int64_t)N * 32 + (q >> 3) * 256 + (kpos >> 4) * 128 + (q & 7) * 16 + (kpos & 15);
 }
 
 __global__ void __launch_bounds__(1024) k_mr_limbs(MrCol *cols, int64_t nsamp, int N,
@@ -85,11 +96,8 @@ __global__ void __launch_bounds__(1024) k_mr_limbs(MrCol *cols, int64_t nsamp, i
     const float *__restrict__ r = C.r32;
     float m = 0.0f;
     for (int64_t i = threadIdx.x; i < nsamp; i += blockDim.x) m = fmaxf(m, fabsf(r[i]));
-    m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, 16));
-    m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, 8));
-    m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, 4));
-    m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, 2));
-    m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, 1));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
     if ((threadIdx.x & 31) == 0) smax[threadIdx.x >> 5] = m;
     __syncthreads();
     if (threadIdx.x < 32) {
@@ -100,27 +108,30 @@ __global__ void __launch_bounds__(1024) k_mr_limbs(MrCol *cols, int64_t nsamp, i
     }
     __syncthreads();
     m = smax[0];
-    float s = 1.0f;
+    float s0 = 1.0f;
     if (m > 0.0f) {
         int e;
-        frexpf(m, &e);                   // m < 2^e
-        s = ldexpf(1.0f, e - 15);        // m / s < 2^15
+        frexpf(m / 448.0f, &e);          // m/448 <= 2^e
+        s0 = ldexpf(1.0f, e);
     }
-    const float inv = 1.0f / s;          // exact: s is a power of two
-    const int qhi = 2 * blockIdx.x;
+    const int q0 = kMrLimbs * blockIdx.x;
     double acc = 0.0;
     for (int64_t i = threadIdx.x; i < nsamp; i += blockDim.x) {
-        const float v = r[i];
-        acc += (double)v;
-        const float x = v * inv;
-        const __half hi = __float2half_rn(x);
-        const __half lo = __float2half_rn(x - __half2float(hi));
-        *reinterpret_cast<__half *>(bimg + mr_b_offset(i, qhi, N)) = hi;
-        *reinterpret_cast<__half *>(bimg + mr_b_offset(i, qhi + 1, N)) = lo;
+        float res = r[i];
+        float sc = s0;
+        acc += (double)res;
+#pragma unroll
+        for (int l = 0; l < kMrLimbs; ++l) {
+            const __nv_fp8_e4m3 q(res / sc);
+            const float qf = (float)q;
+            bimg[mr_b_offset(i, q0 + l, N)] = q.__x;
+            res -= sc * qf;
+            sc *= 0.0625f;
+        }
     }
     acc = block_sum(acc, red);
     if (threadIdx.x == 0) {
-        C.scale = s * 8192.0f;           // A carries 2^-13 x
+        C.scale = s0;                    // limb l scale: s0 16^-l; S1 = 32 sum_l s_l acc_l
         C.R = (float)acc;
     }
 }
@@ -210,7 +221,7 @@ __device__ __forceinline__ void mr_mma(uint32_t d_tmem, uint32_t a_tmem, uint64_
 {
     asm volatile(
         "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
-        "tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n}\n" ::"r"(d_tmem),
+        "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], [%1], %2, %3, p;\n}\n" ::"r"(d_tmem),
         "r"(a_tmem), "l"(b_desc), "r"(idesc), "r"(accumulate)
         : "memory");
 }
@@ -229,35 +240,16 @@ __device__ __forceinline__ uint64_t mr_b_desc(uint32_t saddr)
            ((uint64_t)(256u >> 4) << 32) | (1ull << 46);
 }
 
-// F16 dosage map of one word of 16 codes: output j = samples j and j + 8.
-// Shifts as multiplies / high multiplies (FMA pipe); the decode is bound by
-// the integer pipe, which then only does the masks.
-__device__ __forceinline__ uint32_t mr_shl(uint32_t x, uint32_t pow2)
-{
-    uint32_t y;
-    asm("mul.lo.u32 %0, %1, %2;" : "=r"(y) : "r"(x), "r"(pow2));
-    return y;
-}
-
-__device__ __forceinline__ uint32_t mr_shr(uint32_t x, uint32_t pow2)   // x >> (32 - log2 pow2)
-{
-    uint32_t y;
-    asm("mul.hi.u32 %0, %1, %2;" : "=r"(y) : "r"(x), "r"(pow2));
-    return y;
-}
-
+// E4M3 dosage map of one word of 16 codes (as the single-column pass):
+// output j holds samples 4k + j (byte k), value 2^-5 x.
 __device__ __forceinline__ void mr_decode(uint32_t w, uint32_t *a)
 {
-    const uint32_t f = w & (mr_shr(w, 0x80000000u) | 0xAAAAAAAAu);
-    const uint32_t m = 0x0C000C00u;
-    a[0] = mr_shl(f, 1024u) & m;
-    a[1] = mr_shl(f, 256u) & m;
-    a[2] = mr_shl(f, 64u) & m;
-    a[3] = mr_shl(f, 16u) & m;
-    a[4] = mr_shl(f, 4u) & m;
-    a[5] = f & m;
-    a[6] = mr_shr(f, 0x40000000u) & m;
-    a[7] = mr_shr(f, 0x10000000u) & m;
+    const uint32_t f = w & ((w >> 1) | 0xAAAAAAAAu);     // even bits: c0 & c1; odd bits: c1
+    const uint32_t m = 0x18181818u;
+    a[0] = (f << 3) & m;
+    a[1] = (f << 1) & m;
+    a[2] = (f >> 1) & m;
+    a[3] = (f >> 3) & m;
 }
 
 struct MrPipe {
@@ -293,7 +285,7 @@ __global__ void __launch_bounds__(kMrThreads, 1) k_grad_mrhs(
             mr_bar_init(&pipe.bempty[s], 1);
         }
         for (int b = 0; b < nbufs; ++b) {
-            mr_bar_init(&pipe.afull[b], kMrDecoders);
+            mr_bar_init(&pipe.afull[b], kMrBufArrivals);
             mr_bar_init(&pipe.aempty[b], 1);
         }
         mr_bar_init(&pipe.accfull, 1);
@@ -311,7 +303,7 @@ __global__ void __launch_bounds__(kMrThreads, 1) k_grad_mrhs(
     mr_fence_after();
 
     const int64_t ntiles = (p + 128 * kMrTiles - 1) / (128 * kMrTiles);
-    const int spt = (ksteps + 15) / 16;                 // genotype stages per tile (16 K-steps each)
+    const int spt = (ksteps + 7) / 8;                   // genotype stages per tile (8 K-steps each)
     const int cpt = ksteps / kMrChunkSteps;             // B chunks per tile
 
     // Ring positions advance by increment and compare (slot, phase bit): the
@@ -319,17 +311,24 @@ __global__ void __launch_bounds__(kMrThreads, 1) k_grad_mrhs(
     // or modulo sits on their path.
     if (tid < kMrDecoders) {
         // ------------------------------------------------------- decoders + epilogue
-        const int t = warp >> 2, r = tid & 127;
+        // warps 8t .. 8t+7 serve tile t: group dg = 0 fills the even A buffers of
+        // the sequence, dg = 1 the odd ones, so two buffers are in flight per
+        // lane quarter and each group's latency chain (decode, tcgen05.st, wait,
+        // arrive) overlaps the other's
+        const int t = warp / (4 * kMrDecGroups), dg = (warp >> 2) % kMrDecGroups, r = tid & 127;
         const uint32_t lane_off = (uint32_t)((warp & 3) * 32) << 16;
         const uint32_t tb = tmem_base + (uint32_t)(256 * t) + lane_off;
         const uint32_t abase = tb + (uint32_t)N;
         const int swz = (r >> 1) & 3;
         uint32_t gslot = 0, gphase = 0;           // genotype stage ring
-        uint32_t aslot = 0, aphase = 0, aused = 0; // A buffer ring (aused: buffers filled so far, capped)
+        // A buffer ring position of this group's next buffer (sequence number aseq)
+        uint32_t aslot = (uint32_t)dg % (uint32_t)nbufs, aphase = (uint32_t)dg / (uint32_t)nbufs;
+        uint32_t aseq = (uint32_t)dg;
         int T = 0;
         bool ok = true;
+        uint32_t gseq = 0;                         // sequence number of the stage's first buffer
         for (int64_t tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x, ++T) {
-            int left = ksteps;                      // K-steps of this tile still to decode
+            int left = ksteps >> 1;                 // A buffers (2 K-steps, 16 packed bytes) left in the tile
             for (int st = 0; st < spt && ok; ++st) {
                 if (!mr_wait(&pipe.gfull[gslot], gphase)) {
                     abort_flag = 1;
@@ -337,33 +336,36 @@ __global__ void __launch_bounds__(kMrThreads, 1) k_grad_mrhs(
                     break;
                 }
                 const uint8_t *rowp = gst + (gslot * kMrTiles + t) * kMrGTile + r * kMrGStageBytes;
-                const int nb = min(8, left >> 1);
-                left -= 2 * nb;
-                for (int q8 = 0; q8 < nb; ++q8) {
-                    if (aused >= (uint32_t)nbufs) {
+                const int nb = min(4, left);
+                left -= nb;
+                // group dg fills the buffers whose sequence number has parity dg
+                for (int q4 = (int)((uint32_t)dg - gseq) & 1; q4 < nb; q4 += kMrDecGroups) {
+                    if (aseq >= (uint32_t)nbufs) {
                         if (!mr_wait(&pipe.aempty[aslot], aphase ^ 1u)) {
                             abort_flag = 1;
                             ok = false;
                             break;
                         }
                         mr_fence_after();
-                    } else {
-                        ++aused;
                     }
-                    const uint2 x = *reinterpret_cast<const uint2 *>(
-                        rowp + (((q8 >> 1) ^ swz) << 4) + (q8 & 1) * 8);
+                    const uint4 x = *reinterpret_cast<const uint4 *>(rowp + ((q4 ^ swz) << 4));
                     uint32_t v[16];
                     mr_decode(x.x, &v[0]);
-                    mr_decode(x.y, &v[8]);
+                    mr_decode(x.y, &v[4]);
+                    mr_decode(x.z, &v[8]);
+                    mr_decode(x.w, &v[12]);
                     mr_st16(abase + 16u * aslot, v);
                     asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
                     mr_fence_before();
                     mr_arrive(&pipe.afull[aslot]);
-                    if (++aslot == (uint32_t)nbufs) {
-                        aslot = 0;
+                    aseq += kMrDecGroups;
+                    aslot += kMrDecGroups;
+                    while (aslot >= (uint32_t)nbufs) {       // at most twice (nbufs >= 2)
+                        aslot -= (uint32_t)nbufs;
                         aphase ^= 1u;
                     }
                 }
+                gseq += (uint32_t)nb;
                 mr_arrive(&pipe.gempty[gslot]);
                 if (++gslot == kMrGStages) {
                     gslot = 0;
@@ -380,16 +382,32 @@ __global__ void __launch_bounds__(kMrThreads, 1) k_grad_mrhs(
             }
             mr_fence_after();
             const int64_t j = tile * (128 * kMrTiles) + 128 * t + r;
-            for (int cg = 0; cg < N / 16; ++cg) {
-                uint32_t acc[16];
-                mr_ld16(tb + 16u * cg, acc);
-                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+            {
+                // the groups take halves of the solves; solve c's limbs are the
+                // accumulator columns 5c .. 5c+4, combined in limb order as the
+                // single-column epilogue does: S1 = 32 sum_l s0 16^-l acc_l
+                const int half = (ncols + 1) / 2;
+                const int c_lo = dg == 0 ? 0 : half, c_hi = dg == 0 ? half : ncols;
+                int c = c_lo, l = 0;
+                float ssum = 0.0f, sc = c < c_hi ? cols[c].scale : 0.0f;
+                const int col_lo = kMrLimbs * c_lo, col_hi = kMrLimbs * c_hi;
+                for (int cg = col_lo >> 4; (cg << 4) < col_hi; ++cg) {
+                    uint32_t acc[16];
+                    mr_ld16(tb + 16u * cg, acc);
+                    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
-                for (int e = 0; e < 8; ++e) {
-                    const int c = 8 * cg + e;
-                    if (c < ncols && j < p) {
-                        const MrCol &C = cols[c];
-                        C.g[j] = (__uint_as_float(acc[2 * e]) + __uint_as_float(acc[2 * e + 1])) * C.scale;
+                    for (int e = 0; e < 16; ++e) {
+                        const int col = 16 * cg + e;
+                        if (col < col_lo || col >= col_hi) continue;
+                        ssum = fmaf(sc, __uint_as_float(acc[e]), ssum);
+                        sc *= 0.0625f;
+                        if (++l == kMrLimbs) {
+                            if (j < p) cols[c].g[j] = 32.0f * ssum;
+                            ++c;
+                            l = 0;
+                            ssum = 0.0f;
+                            sc = c < c_hi ? cols[c].scale : 0.0f;
+                        }
                     }
                 }
             }
@@ -594,7 +612,7 @@ __global__ void __launch_bounds__(kFinThreads) k_miss_finalize(const int64_t *__
                 if (c0 + e < ncols) {
                     const MrCol &C = cols[c0 + e];
                     const float s1 = C.g[j];
-                    C.g[j] = C.v32[j] * (s1 - C.u32[j] * (C.R - m[e]));
+                    C.g[j] = standardise(s1, C.R, m[e], C.u32[j], C.v32[j]);
                 }
             }
         }
@@ -611,13 +629,17 @@ struct MrWork {
 };
 static thread_local MrWork g_mr;
 
+// 16-byte groups of packed samples per row (2 K-steps of 32 samples each)
+static int64_t mr_ngroups(const iht_dataset *ds) { return ((ds->n + 3) / 4 + 15) / 16; }
+
+// K-steps of a pass: the single-column pass's 2 ngroups, rounded up to whole
+// B chunks (the extra K-steps multiply zero limbs and add exactly 0).
 static int mr_ksteps(const iht_dataset *ds)
 {
-    const int64_t ngroups = ((ds->n + 3) / 4 + 15) / 16;    // 16-byte groups = 4 K-steps
-    return (int)(4 * ngroups);
+    return (int)((2 * mr_ngroups(ds) + kMrChunkSteps - 1) / kMrChunkSteps * kMrChunkSteps);
 }
 
-static int mr_n(int ncols) { return (2 * ncols + 15) / 16 * 16; }
+static int mr_n(int ncols) { return (kMrLimbs * ncols + 15) / 16 * 16; }
 
 static size_t mr_gbytes() { return (size_t)kMrGStages * kMrTiles * kMrGTile; }
 
@@ -723,7 +745,8 @@ int launch_grad_mrhs(iht_dataset *ds, MrCol *cols, int ncols, ProfEvents *prof)
         const int N = mr_n(nc);
         const size_t bbytes = (size_t)ksteps * N * 32;
         IHT_CUDA(cudaMemsetAsync(w.bimg, 0, bbytes, s));
-        k_mr_limbs<<<nc, 1024, 0, s>>>(cols + c0, (int64_t)ksteps * kMrStepSamples, N, w.bimg);
+        // scale, limbs and R over the single-column pass's samples (the rest are 0)
+        k_mr_limbs<<<nc, 1024, 0, s>>>(cols + c0, 2 * mr_ngroups(ds) * kMrStepSamples, N, w.bimg);
         const int nbst = mr_bstages(N);
         const int nbufs = std::min(kMrMaxBufs, (256 - N) / 16);
         if (nbst < 2 || nbufs < 2) return IHT_EINVAL;

@@ -322,7 +322,7 @@ __device__ __forceinline__ bool tc_epilogue(TcPipe &P, uint32_t tb, uint32_t lan
             s *= 0.0625f;
         }
         const float S1 = 32.0f * Ssum;
-        g[row] = v32[row] * (S1 - u32[row] * (R - Mj[row]));
+        g[row] = standardise(S1, R, Mj[row], u32[row], v32[row]);
     }
     return ok;
 }

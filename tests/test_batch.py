@@ -89,7 +89,7 @@ def test_gradient_batch_parity(iht, ctx, impl, n, p, b):
 
 
 def test_gradient_batch_two_passes(iht, ctx):
-    """More columns than one pass holds (112): the passes split and agree."""
+    """More columns than one pass holds (44): the passes split and agree."""
     torch = _torch()
     rng = np.random.default_rng(77)
     n, p, b = 700, 900, 130
@@ -98,22 +98,26 @@ def test_gradient_batch_two_passes(iht, ctx):
     R = rng.normal(size=(b, n)).astype(np.float32)
     Gd = iht.iht_gradient_batch(ds, [torch.from_numpy(R[c]).cuda() for c in range(b)],
                                 impl=2).cpu().numpy()
-    for c in (0, 1, 57, 111, 112, 129):
+    for c in (0, 1, 43, 44, 57, 87, 88, 111, 112, 129):
         assert rel_err(Gd[c], oracle.gradient(G, R[c].astype(np.float64))) <= GTOL
 
 
 def test_gradient_batch_matches_single_column(iht, ctx):
-    """One column of the multi-column pass against the same column alone."""
+    """One column of the multi-column pass against the same column alone: the
+    passes share the limb representation, the K order and the rounding of every
+    step, so the column is bit-identical to the single-column pass."""
     torch = _torch()
     rng = np.random.default_rng(5)
     G, _ = random_geno(rng, 1500, 700, miss=0.02)
     ds = load(iht, ctx, G)
     r = rng.normal(size=1500).astype(np.float32)
     g1 = iht.iht_gradient(ds, torch.from_numpy(r).cuda(), impl=1).cpu().numpy()
+    g2 = iht.iht_gradient(ds, torch.from_numpy(r).cuda(), impl=2).cpu().numpy()
     others = [torch.from_numpy(rng.normal(size=1500).astype(np.float32)).cuda() for _ in range(20)]
     gb = iht.iht_gradient_batch(ds, others[:7] + [torch.from_numpy(r).cuda()] + others[7:],
                                 impl=2).cpu().numpy()
     assert rel_err(gb[7], g1) <= GTOL
+    assert np.array_equal(gb[7], g2)
 
 
 def _signal_panel(seed, n, p, k_star, effect=0.6, miss=0.02):
@@ -215,21 +219,22 @@ def test_fit_batch_status_and_io(iht, ctx):
 
 
 def test_fit_batch_matches_single_solves(iht, ctx):
-    """A solve in a batch and the same solve alone (single-column path) agree
-    on every certified solve."""
-    n, p = 1200, 3000
+    """A solve in a batch and the same solve alone through iht_fit: the same
+    arithmetic step for step, so the same support, beta bit for bit and the
+    same iteration count, whatever else is in the batch."""
+    n, p = 1200, 3001
     G, codes, y, _, rng = _signal_panel(12, n, p, 5, effect=0.5)
     ds = load(iht, ctx, G)
     rows = np.sort(rng.choice(n, size=1000, replace=False)).astype(np.int32)
-    probs = [(y, 5, None), (y[rows], 5, rows), (y, 10, None)]
+    y2 = rng.normal(size=n)
+    probs = [(y, 5, None), (y[rows], 5, rows), (y, 10, None), (y2, 3, None), (y2[rows], 40, rows)]
     res = iht.iht_fit_batch(ds, probs)
     for (yy, k, rr), fb in zip(probs, res):
-        fo = oracle.iht(G, yy, k, rows=rr)
-        if certified(fo):
-            fs = iht.iht_fit(ds, yy, k, rows=rr)
-            assert np.array_equal(fs.support, fb.support)
-            assert rel_err(fb.beta, fs.beta) <= BTOL
-            assert fs.iterations == fb.iterations
+        fs = iht.iht_fit(ds, yy, k, rows=rr)
+        assert np.array_equal(fs.support, fb.support)
+        assert np.array_equal(fs.beta, fb.beta)
+        assert fs.iterations == fb.iterations and fs.status == fb.status
+        assert fs.objective == fb.objective
 
 
 def test_fit_batch_odd_p(iht, ctx):
