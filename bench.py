@@ -56,7 +56,7 @@ FALLBACK_HBM_GBS = 6400.0
 # DRAM bytes (read + write) of one single-column gradient launch on the
 # n = 5000, p = 500 000 panel, from one ncu capture of this kernel version
 # (dram__bytes_read.sum + dram__bytes_write.sum; summary in profiles/).
-K1_TRAFFIC_BYTES = 646332672 + 4857856
+K1_TRAFFIC_BYTES = None
 # The same for the first multi-column launch of the cross-validation batch
 # (44 residual columns of the 100 solves, the widest pass).
 K2_TRAFFIC_FIRST_LAUNCH_BYTES = 1538893312 + 167300608
@@ -706,7 +706,7 @@ def serve_arm(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--config", type=int, default=2, choices=[1, 2, 3, 4])

@@ -330,4 +330,12 @@ __device__ __forceinline__ float standardise(float S1, float R, float M, float u
     return __fmul_rn(v, __fsub_rn(S1, __fmul_rn(u, __fsub_rn(R, M))));
 }
 
+// The same from D = sum over all calls of (2 x + [call missing]) r, which is
+// what the tensor-core dosage map yields (a missing call counts once):
+// S1 = (D - M) / 2.
+__device__ __forceinline__ float standardise_d(float D, float R, float M, float u, float v)
+{
+    return standardise(__fmul_rn(0.5f, __fsub_rn(D, M)), R, M, u, v);
+}
+
 }  // namespace iht

@@ -11,19 +11,20 @@
 // GEMM of the 2-bit matrix against the b residual columns: one pass over the
 // packed genotypes serves all b solves.
 //
-// Operands (kind::f8f6f4, both E4M3, FP32 accumulate, M = 128 SNPs, K = 32),
-// the same numbers as the single-column pass (grad_tc.cu), column by column:
+// Operands (kind::f8f6f4, A E5M2, B E4M3, FP32 accumulate, M = 128 SNPs,
+// K = 32), the same numbers as the single-column pass (grad_tc.cu), column by
+// column:
 //   A: the dosage map in tensor memory, decoded by CUDA-core warps from the
-//      TMA-staged 2-bit codes: the field f = (c1, c1 & c0) of a code (00 for
-//      hom-ref and missing, 10 het, 11 hom-alt) moved to bits 3-4 of a byte is
-//      the E4M3 value 2^-5 x; output word j of an input word holds samples
-//      4k + j (byte k).
+//      TMA-staged 2-bit codes: a code moved to bits 2-3 of a byte (the low
+//      exponent bits) is the E5M2 value 2^-14 (2x + [missing]); output word j
+//      of an input word holds samples 4k + j (byte k).
 //   B: each residual column as 5 E4M3 limbs r ~ sum_l s_l q_l, s_l = s_0 2^-4l,
 //      s_0 = 2^ceil(log2(max|r| / 448)) (the single-column pass's limbs), one
 //      B row per limb (row 5c + l for column c), N = 5 b rounded up to 16,
 //      stored per K-step in the canonical K-major layout (8-row x 16-byte core
 //      matrices) in the same permuted sample order as A.
-//   So S1 = 32 sum_l s_l acc_l, summed over l in the single-column order.
+//   So D = 2^14 sum_l s_l acc_l (summed over l in the single-column order) is
+//   the sum of (2x + [missing]) r over all calls, and S1 = (D - M) / 2.
 //
 // One persistent CTA per SM handles two 128-SNP tiles at a time, so every B
 // chunk it streams from L2 feeds two MMAs.  Warps 0-15 decode (warps 8t..8t+7
@@ -32,8 +33,8 @@
 // MMAs, warp 17 streams genotype tiles (TMA 2D, 64-byte swizzle), warp 18
 // streams B chunks (bulk copies).  Tensor memory (512
 // columns): accumulator of tile t at column 256 t, its A buffers right after
-// it.  The epilogue writes S1; a second pass (k_miss_finalize) adds the
-// missing-call sums from the per-SNP lists and forms g, so this kernel's
+// it.  The epilogue writes D; a second pass (k_miss_finalize) forms the
+// missing-call sums from the per-SNP lists, S1 and g, so this kernel's
 // epilogue only stores.  Every wait is bounded and reports a timeout through
 // an error word instead of hanging.
 #include <cuda.h>
@@ -131,7 +132,7 @@ __global__ void __launch_bounds__(1024) k_mr_limbs(MrCol *cols, int64_t nsamp, i
     }
     acc = block_sum(acc, red);
     if (threadIdx.x == 0) {
-        C.scale = s0;                    // limb l scale: s0 16^-l; S1 = 32 sum_l s_l acc_l
+        C.scale = s0;                    // limb l scale: s0 16^-l; D = 2^14 sum_l s_l acc_l
         C.R = (float)acc;
     }
 }
@@ -240,16 +241,16 @@ __device__ __forceinline__ uint64_t mr_b_desc(uint32_t saddr)
            ((uint64_t)(256u >> 4) << 32) | (1ull << 46);
 }
 
-// E4M3 dosage map of one word of 16 codes (as the single-column pass):
-// output j holds samples 4k + j (byte k), value 2^-5 x.
+// E5M2 dosage map of one word of 16 codes (as the single-column pass): each
+// 2-bit field in bits 2-3 of its byte, value 2^-14 (2x + [missing]); output j
+// holds samples 4k + j (byte k).
 __device__ __forceinline__ void mr_decode(uint32_t w, uint32_t *a)
 {
-    const uint32_t f = w & ((w >> 1) | 0xAAAAAAAAu);     // even bits: c0 & c1; odd bits: c1
-    const uint32_t m = 0x18181818u;
-    a[0] = (f << 3) & m;
-    a[1] = (f << 1) & m;
-    a[2] = (f >> 1) & m;
-    a[3] = (f >> 3) & m;
+    const uint32_t m = 0x0C0C0C0Cu;
+    a[0] = (w << 2) & m;
+    a[1] = w & m;
+    a[2] = (w >> 2) & m;
+    a[3] = (w >> 4) & m;
 }
 
 struct MrPipe {
@@ -374,7 +375,7 @@ __global__ void __launch_bounds__(kMrThreads, 1) k_grad_mrhs(
                 if (abort_flag) ok = false;
             }
             if (!ok) break;
-            // epilogue: S1 of each column for this thread's SNP
+            // epilogue: D of each column for this thread's SNP
             if (!mr_wait(&pipe.accfull, (uint32_t)T & 1u)) {
                 abort_flag = 1;
                 ok = false;
@@ -385,7 +386,7 @@ __global__ void __launch_bounds__(kMrThreads, 1) k_grad_mrhs(
             {
                 // the groups take halves of the solves; solve c's limbs are the
                 // accumulator columns 5c .. 5c+4, combined in limb order as the
-                // single-column epilogue does: S1 = 32 sum_l s0 16^-l acc_l
+                // single-column epilogue does: D = 2^14 sum_l s0 16^-l acc_l
                 const int half = (ncols + 1) / 2;
                 const int c_lo = dg == 0 ? 0 : half, c_hi = dg == 0 ? half : ncols;
                 int c = c_lo, l = 0;
@@ -402,7 +403,7 @@ __global__ void __launch_bounds__(kMrThreads, 1) k_grad_mrhs(
                         ssum = fmaf(sc, __uint_as_float(acc[e]), ssum);
                         sc *= 0.0625f;
                         if (++l == kMrLimbs) {
-                            if (j < p) cols[c].g[j] = 32.0f * ssum;
+                            if (j < p) cols[c].g[j] = 16384.0f * ssum;     // D
                             ++c;
                             l = 0;
                             ssum = 0.0f;
@@ -532,9 +533,10 @@ __global__ void __launch_bounds__(kMrThreads, 1) k_grad_mrhs(
 
 // ---------------------------------------------------------------------------
 // Missing-call sums and the standardisation: g_cj = v (S1 - u (R - M_cj)),
-// with S1 read from g_c.  A block stages CG residual columns in shared memory,
-// interleaved (CG floats per sample); each lane owns one SNP, reads its
-// missing-call list 16 bytes at a time (8 or 4 sample indices) and gathers the
+// with S1 = (D - M_cj) / 2 and D read from g_c.  A block stages CG residual
+// columns in shared memory, interleaved (CG floats per sample); each lane owns
+// one SNP, reads its missing-call list 16 bytes at a time (8 or 4 sample
+// indices) and gathers the
 // CG residual values of every listed sample, so a list entry costs one
 // shared-memory vector load for all CG columns; the lane then writes the CG
 // finished gradient entries of its SNP (consecutive SNPs across the warp).
@@ -611,8 +613,8 @@ __global__ void __launch_bounds__(kFinThreads) k_miss_finalize(const int64_t *__
             for (int e = 0; e < CG; ++e) {
                 if (c0 + e < ncols) {
                     const MrCol &C = cols[c0 + e];
-                    const float s1 = C.g[j];
-                    C.g[j] = standardise(s1, C.R, m[e], C.u32[j], C.v32[j]);
+                    const float d = C.g[j];
+                    C.g[j] = standardise_d(d, C.R, m[e], C.u32[j], C.v32[j]);
                 }
             }
         }
@@ -752,7 +754,9 @@ int launch_grad_mrhs(iht_dataset *ds, MrCol *cols, int ncols, ProfEvents *prof)
         if (nbst < 2 || nbufs < 2) return IHT_EINVAL;
         // at least 116 KB, so one CTA per SM: the kernel allocates all 512 columns of tensor memory
         const size_t smem = std::max<size_t>(116 * 1024, mr_gbytes() + (size_t)nbst * kMrChunkSteps * N * 32);
-        const uint32_t idesc = (1u << 4) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
+        // D FP32, A E5M2, B E4M3, K-major, N, M = 128
+        const uint32_t idesc = (1u << 4) | (1u << 7) | ((uint32_t)(N >> 3) << 17) |
+                               ((uint32_t)(128 >> 4) << 24);
         prof_begin(prof, s);
         k_grad_mrhs<<<grid, kMrThreads, smem, s>>>(map, ds->p, ksteps, N, nc, nbufs, nbst, w.bimg,
                                                     cols + c0, idesc, w.err);

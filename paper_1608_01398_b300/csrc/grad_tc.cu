@@ -7,21 +7,23 @@
 // the multiply-adds while the kernel stays bound by the HBM stream of packed
 // genotypes.
 //
-// The dense part, S1_j = sum over observed calls of x_ij r_i, runs on the
-// tensor cores (kind::f8f6f4, both operands E4M3, FP32 accumulate, M = 128
-// SNPs, N = 16, K = 32 samples):
-//   A: the dosage map.  With D = code << 3 (code in the exponent field: values
-//      2^-6 (0, 1, 2, 4) for codes 00, 01, 10, 11), A = D with code 01
-//      zeroed = 2^-5 x; two instructions per output word from a word of 16
-//      codes (byte k of word j = sample 4k+j).
+// The dense part runs on the tensor cores (kind::f8f6f4, FP32 accumulate,
+// M = 128 SNPs, N = 16, K = 32 samples):
+//   A: the dosage map in E5M2.  The 2-bit code masked into bits 2-3 (the two
+//      low exponent bits) reads 0, 2^-14, 2^-13, 2^-12 for codes 00, 01, 10,
+//      11, i.e. 2^-14 (2x + [missing]); one AND, plus a shift for three of the
+//      four fields, per output word of a 16-code input word (byte k of output
+//      word j = sample 4k+j).
 //   B: the residual as L = 5 E4M3 limbs, r ~ sum_l s_l q_l with s_l =
 //      s_0 2^(-4l), in the same permuted sample order; limb l is row l of the
 //      K-step's first 8-row group and the second group is one shared all-zero
 //      group (8 bytes per sample).
-// So S1 = 32 sum_l s_l acc[l].  The missing-call sums M_j (1-2 % of calls)
-// come from a per-SNP list of missing sample offsets built at upload (a small
-// warp-per-SNP pass before this one); with them in the hot loop the
-// data-dependent per-call branches cost more than the whole dense pass.
+// So D = 2^14 sum_l s_l acc[l] = sum of (2x + [missing]) r over the calls, and
+// S1_j = sum over observed calls of x_ij r_i = (D - M_j) / 2.  The missing-call
+// sums M_j (1-2 % of calls) come from a per-SNP list of missing sample offsets
+// built at upload (a small warp-per-SNP pass before this one); they are needed
+// for R - M_j anyway, and with them in the hot loop the data-dependent
+// per-call branches cost more than the whole dense pass.
 //
 // Each tcgen05 instruction (an MMA or a commit) costs the SM's tensor front
 // end about 45 cycles whatever the operand size, so the kernel issues one MMA
@@ -241,21 +243,21 @@ __device__ __forceinline__ uint64_t b_desc(uint32_t saddr, uint32_t sbo)
            ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
 }
 
-// D FP32 (bit 4), A/B E4M3 (0), K-major, N = 16 (N>>3 at bit 17), M = 128 (M>>4 at bit 24)
-constexpr uint32_t kIdescF8 = (1u << 4) | ((uint32_t)(kTcN >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
+// D FP32 (bit 4), A E5M2 (1 at bit 7), B E4M3 (0 at bit 10), K-major,
+// N = 16 (N>>3 at bit 17), M = 128 (M>>4 at bit 24)
+constexpr uint32_t kIdescF8 = (1u << 4) | (1u << 7) | ((uint32_t)(kTcN >> 3) << 17) |
+                              ((uint32_t)(128 >> 4) << 24);
 
-// Dosage map of one 16-code input word.  Per 2-bit field, f = (c1, c1 & c0):
-// 00 for codes 00 and 01, 10 for het, 11 for hom-alt; moving a field to bits
-// 3..4 of a byte gives E4M3 0, 2^-5, 2^-4 = 2^-5 x.  Output word j holds
-// samples 4k+j (byte k).
+// Dosage map of one 16-code input word: each 2-bit field moved to bits 2-3 of
+// its byte, E5M2 2^-14 (2x + [missing]).  Output word j holds samples 4k+j
+// (byte k).
 __device__ __forceinline__ void decode_word(uint32_t w, uint32_t *a)
 {
-    const uint32_t f = w & ((w >> 1) | 0xAAAAAAAAu);     // even bits: c0 & c1; odd bits: c1
-    const uint32_t m = 0x18181818u;
-    a[0] = (f << 3) & m;
-    a[1] = (f << 1) & m;
-    a[2] = (f >> 1) & m;
-    a[3] = (f >> 3) & m;
+    const uint32_t m = 0x0C0C0C0Cu;
+    a[0] = (w << 2) & m;
+    a[1] = w & m;
+    a[2] = (w >> 2) & m;
+    a[3] = (w >> 4) & m;
 }
 
 struct TcPipe {
@@ -321,8 +323,8 @@ __device__ __forceinline__ bool tc_epilogue(TcPipe &P, uint32_t tb, uint32_t lan
             Ssum = fmaf(s, __uint_as_float(acc[l]), Ssum);
             s *= 0.0625f;
         }
-        const float S1 = 32.0f * Ssum;
-        g[row] = standardise(S1, R, Mj[row], u32[row], v32[row]);
+        const float D = 16384.0f * Ssum;
+        g[row] = standardise_d(D, R, Mj[row], u32[row], v32[row]);
     }
     return ok;
 }
@@ -421,13 +423,12 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_grad_tc(const __grid_constant
                     uint4 x1 = make_uint4(0u, 0u, 0u, 0u);
                     if (c + 1 < nchunks)
                         x1 = *reinterpret_cast<const uint4 *>(base + (c == 0 ? off1 : off3));
-                    if (grp >= kTcBufs) {
-                        if (!mbar_wait(&P.empty[buf], bphase ^ 1u)) {
-                            abort_flag = 1;
-                            ok = false;
-                        }
-                        tc_fence_after();
+                    // (a fresh barrier passes the wait on parity 1: the first round is free)
+                    if (!mbar_wait(&P.empty[buf], bphase ^ 1u)) {
+                        abort_flag = 1;
+                        ok = false;
                     }
+                    tc_fence_after();
                     tc_put_group(abase + 32 * buf, x0, x1);
                     asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
                     tc_fence_before();
@@ -464,14 +465,27 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_grad_tc(const __grid_constant
                     if (!mbar_wait(&P.accempty, (uint32_t)(T - 1) & 1u)) { abort_flag = 1; ok = false; }
                     tc_fence_after();
                 }
+                // B descriptor of K-step s: start b_addr + 256 (s + 1), 8-row-group
+                // stride za - 256 (s + 1) (to the shared zero group); both fields
+                // move by 256 bytes per step, so one 64-bit add advances it.
+                uint64_t bd = b_desc(b_addr + 256u, za - 256u);
+                constexpr uint64_t kBdStep = (uint64_t)(256 >> 4) - ((uint64_t)(256 >> 4) << 32);
                 for (int gg = 0; gg < ngrp && ok; ++gg) {
                     if (!mbar_wait(&P.full[buf], use & 1u)) { abort_flag = 1; ok = false; break; }
                     tc_fence_after();
-                    const int s_end = min(ksteps, (gg + 1) * kTcBufSteps);
-                    for (int s = gg * kTcBufSteps; s < s_end; ++s) {
-                        const uint32_t ls = 256u + 256u * (uint32_t)s;       // limb group of K-step s
-                        mma_f8(tb, tb + 32 + 32 * buf + 8 * (s - gg * kTcBufSteps),
-                               b_desc(b_addr + ls, za - ls), kIdescF8, s > 0 ? 1u : 0u);
+                    const int s0 = gg * kTcBufSteps;
+                    const uint32_t a0 = tb + 32 + 32 * buf;
+                    if (s0 + kTcBufSteps <= ksteps) {
+#pragma unroll
+                        for (int q = 0; q < kTcBufSteps; ++q) {
+                            mma_f8(tb, a0 + 8 * q, bd, kIdescF8, (s0 + q) > 0 ? 1u : 0u);
+                            bd += kBdStep;
+                        }
+                    } else {
+                        for (int q = 0; s0 + q < ksteps; ++q) {
+                            mma_f8(tb, a0 + 8 * q, bd, kIdescF8, (s0 + q) > 0 ? 1u : 0u);
+                            bd += kBdStep;
+                        }
                     }
                     mma_commit(&P.empty[buf]);
                     if (gg == ngrp - 1) mma_commit(&P.accfull);
