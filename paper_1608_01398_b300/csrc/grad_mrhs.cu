@@ -621,6 +621,75 @@ __global__ void __launch_bounds__(kFinThreads) k_miss_finalize(const int64_t *__
     }
 }
 
+// Eight columns per block: sample i's eight residual values form one 32-byte
+// row of the shared table, and a pair of lanes owns one SNP, lane h of the pair
+// reading half h (columns 4h .. 4h+3) of every listed row, so a quarter-warp's
+// 16-byte loads touch four rows instead of eight.  List positions outside the
+// SNP's range in its first and last 16-byte piece read an all-zero row (index
+// n_pad); every sum still runs over the SNP's list in order from 0.0f.
+constexpr int kFin8Threads = 1024;
+
+template <typename IdxT>
+__global__ void __launch_bounds__(kFin8Threads) k_miss_finalize8(const int64_t *__restrict__ off,
+                                                                 const IdxT *__restrict__ idx, int64_t p,
+                                                                 int64_t n_pad,
+                                                                 const MrCol *__restrict__ cols,
+                                                                 int ncols)
+{
+    constexpr int kPer = 16 / (int)sizeof(IdxT);               // indices per 16-byte load
+    extern __shared__ __align__(16) unsigned char mr_sh[];
+    float4 *rs = reinterpret_cast<float4 *>(mr_sh);            // 2 (n_pad + 1) float4
+    const int c0 = blockIdx.y * 8;
+    for (int64_t i = threadIdx.x; i <= n_pad; i += blockDim.x) {
+        float v[8];
+#pragma unroll
+        for (int e = 0; e < 8; ++e) v[e] = (i < n_pad && c0 + e < ncols) ? cols[c0 + e].r32[i] : 0.0f;
+        rs[2 * i] = make_float4(v[0], v[1], v[2], v[3]);
+        rs[2 * i + 1] = make_float4(v[4], v[5], v[6], v[7]);
+    }
+    __syncthreads();
+    const int lane = threadIdx.x & 31, h = lane & 1;
+    const uint32_t zrow = (uint32_t)n_pad;
+    const uint4 *__restrict__ idx4 = reinterpret_cast<const uint4 *>(idx);
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t base = warp * 16; base < p; base += nwarps * 16) {
+        const int64_t j = base + (lane >> 1);
+        const bool live = j < p;
+        const int64_t e0 = live ? off[j] : 0, e1 = live ? off[j + 1] : 0;
+        const int64_t a0 = e0 & ~(int64_t)(kPer - 1);
+        const int lo = (int)(e0 - a0), hi = (int)(e1 - a0);   // valid positions [lo, hi) from a0
+        const uint4 *__restrict__ src = idx4 + a0 / kPer;
+        float m0 = 0.0f, m1 = 0.0f, m2 = 0.0f, m3 = 0.0f;
+        for (int q = 0; q * kPer < hi; ++q) {
+            const uint4 w = src[q];
+            const IdxT *ent = reinterpret_cast<const IdxT *>(&w);
+#pragma unroll
+            for (int t = 0; t < kPer; ++t) {
+                const int pos = q * kPer + t;
+                const uint32_t row = (pos >= lo && pos < hi) ? (uint32_t)ent[t] : zrow;
+                const float4 x = rs[2 * row + h];
+                m0 += x.x;
+                m1 += x.y;
+                m2 += x.z;
+                m3 += x.w;
+            }
+        }
+        if (live) {
+            const float m[4] = {m0, m1, m2, m3};
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const int c = c0 + 4 * h + e;
+                if (c < ncols) {
+                    const MrCol &C = cols[c];
+                    const float d = C.g[j];
+                    C.g[j] = standardise_d(d, C.R, m[e], C.u32[j], C.v32[j]);
+                }
+            }
+        }
+    }
+}
+
 // ---------------------------------------------------------------------------
 
 struct MrWork {
@@ -699,9 +768,29 @@ static int mr_launch_finalize(iht_dataset *ds, const MrCol *cols, int ncols, siz
     return IHT_OK;
 }
 
+constexpr size_t kFin8SmemMax = 220 * 1024;
+
+template <typename IdxT>
+static int mr_launch_finalize8(iht_dataset *ds, const MrCol *cols, int ncols, size_t smem)
+{
+    auto kern = k_miss_finalize8<IdxT>;
+    IHT_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    const int groups = (ncols + 7) / 8;
+    // one wave: one block per SM (the table takes most of shared memory)
+    const int gx = (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(ds->p, kFin8Threads / 2),
+                                                               (int64_t)ds->ctx->num_sms / groups));
+    kern<<<dim3(gx, groups), kFin8Threads, smem, ds->ctx->stream>>>(ds->miss_off, (const IdxT *)ds->miss_idx,
+                                                                    ds->p, ds->n_pad, cols, ncols);
+    note_launch();
+    IHT_CUDA(cudaGetLastError());
+    return IHT_OK;
+}
+
 template <typename IdxT>
 static int mr_finalize(iht_dataset *ds, const MrCol *cols, int ncols)
 {
+    const size_t f8 = 32 * ((size_t)ds->n_pad + 1);
+    if (ncols > 4 && f8 <= kFin8SmemMax) return mr_launch_finalize8<IdxT>(ds, cols, ncols, f8);
     const size_t f = sizeof(float) * (size_t)ds->n_pad;
     if (4 * f <= 200 * 1024) return mr_launch_finalize<4, IdxT, true>(ds, cols, ncols, 4 * f);
     if (2 * f <= 200 * 1024) return mr_launch_finalize<2, IdxT, true>(ds, cols, ncols, 2 * f);
