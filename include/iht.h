@@ -162,14 +162,15 @@ int iht_topk(iht_ctx *ctx, const float *w, int64_t p, int32_t k, int32_t *idx_ou
  *   device  : CUDA device the pointers belong to.
  *   stream  : cudaStream_t to order the work on (NULL = legacy default stream).
  *   w       : device float[p];  idx_out: device int32[k].
- * The selection's scratch is a static device array in the library, sized for
- * p <= 16 777 216 (about 24 KB, held on every GPU that loads the library until
- * the process exits); larger p returns IHT_EINVAL without launching anything.
- * The first call on a device looks the array's address up with
- * cudaGetSymbolAddress; make that first call before any stream capture.  The
- * call only enqueues work on `stream` (it does not synchronise); all calls on a
- * device share the scratch, so calls that overlap on the GPU (other streams or
- * other host threads) race.  Never calls cudaMalloc or cudaFree. */
+ * The selection's scratch is a static device array in the library (about
+ * 41 KB, held on every GPU that loads the library until the process exits);
+ * p is limited to 16 777 216, larger p returns IHT_EINVAL without launching
+ * anything.  The first call on a device looks the array's address up with
+ * cudaGetSymbolAddress and clears it with cudaMemsetAsync on `stream`; make
+ * that first call before any stream capture.  The call only enqueues work on
+ * `stream` (it does not synchronise); all calls on a device share the scratch,
+ * so calls that overlap on the GPU (other streams or other host threads) race.
+ * Never calls cudaMalloc or cudaFree. */
 int iht_topk_noalloc(int device, void *stream, const float *w, int64_t p, int32_t k,
                      int32_t *idx_out);
 
@@ -248,7 +249,7 @@ int iht_gradient_batch(iht_dataset *ds, int32_t b, const int32_t *const *rows_li
  * pointers, copied at submission) arrive at any time.  A worker thread owned
  * by the server admits a pending request when a slot is free and its device
  * footprint (per-SNP statistics, gradient, residuals and scratch of one solve,
- * about 28 p + 56 n bytes plus a few kB) fits in hbm_budget, then runs
+ * about 28 p + 56 n bytes plus about 130 kB) fits in hbm_budget, then runs
  * every admitted solve together: one iteration per tick, one multi-column
  * gradient pass over the packed genotypes for all active solves (each solve is
  * a column), the O(nk) steps batched.  A solve retires when it stops (same

@@ -220,7 +220,7 @@ int iht_destroy(iht_ctx *ctx)
     cudaStreamSynchronize(ctx->stream);
     if (ctx->sel.hist) cudaFree(ctx->sel.hist);
     if (ctx->sel.st) cudaFree(ctx->sel.st);
-    if (ctx->sel.chunk_eq) cudaFree(ctx->sel.chunk_eq);
+    if (ctx->sel.cand) cudaFree(ctx->sel.cand);
     delete ctx;
     return IHT_OK;
 }

@@ -28,7 +28,8 @@ struct BatchWork {
     int32_t *S = nullptr, *Sp = nullptr, *cand = nullptr;
     double *bS = nullptr, *bSp = nullptr, *coef = nullptr, *partials = nullptr;
     SelState *st = nullptr;
-    uint32_t *hist = nullptr, *chunk_eq = nullptr;
+    uint32_t *hist = nullptr;
+    unsigned long long *selcand = nullptr;
     BSolve *bs = nullptr, *bs_host = nullptr;
     SelJob *jobs = nullptr, *jobs_host = nullptr;     // 2 nb: top-k then candidates
     MrCol *cols = nullptr, *cols_host = nullptr;
@@ -46,7 +47,7 @@ void free_batchwork(BatchWork *w)
 {
     if (!w) return;
     void *dev[] = {w->sc, w->y64, w->r64, w->rc64, w->zv, w->r32, w->g, w->S, w->Sp, w->cand,
-                   w->bS, w->bSp, w->coef, w->partials, w->st, w->hist, w->chunk_eq,
+                   w->bS, w->bSp, w->coef, w->partials, w->st, w->hist, w->selcand,
                    w->bs, w->jobs, w->cols, w->set_used, w->set_err, w->set_rowmask, w->set_u64,
                    w->set_v64, w->set_u32, w->set_v32, w->rows_dev, w->ybuf};
     for (void *p : dev)
@@ -81,7 +82,6 @@ static int ensure_batchwork(iht_dataset *ds, int nb, int kcap, int nsets, int64_
     BatchWork *x = new (std::nothrow) BatchWork();
     if (!x) return IHT_ENOMEM;
     const size_t np = (size_t)ds->n_pad, p = (size_t)ds->p, B = (size_t)nb, K = (size_t)kcap;
-    const size_t nch = (size_t)sel_nchunks(ds->p);
     cudaError_t e = cudaSuccess;
 #define BALLOC(field, bytes) \
     if (e == cudaSuccess) e = cudaMalloc((void **)&x->field, std::max<size_t>(16, (size_t)(bytes)));
@@ -101,7 +101,7 @@ static int ensure_batchwork(iht_dataset *ds, int nb, int kcap, int nsets, int64_
     BALLOC(partials, sizeof(double) * B * 3 * kPartials);
     BALLOC(st, sizeof(SelState) * 2 * B);
     BALLOC(hist, sizeof(uint32_t) * 2 * B * kSelBins);
-    BALLOC(chunk_eq, sizeof(uint32_t) * 2 * B * nch);
+    BALLOC(selcand, sizeof(unsigned long long) * 2 * B * kSelCap);
     BALLOC(bs, sizeof(BSolve) * B);
     BALLOC(jobs, sizeof(SelJob) * 2 * B);
     BALLOC(cols, sizeof(MrCol) * B);
@@ -120,6 +120,9 @@ static int ensure_batchwork(iht_dataset *ds, int nb, int kcap, int nsets, int64_
     if (e == cudaSuccess) e = cudaMallocHost((void **)&x->jobs_host, sizeof(SelJob) * 2 * B);
     if (e == cudaSuccess) e = cudaMallocHost((void **)&x->cols_host, sizeof(MrCol) * B);
     if (e == cudaSuccess) e = cudaMallocHost((void **)&x->set_err_host, sizeof(int32_t) * nsets);
+    // selection scratch starts zeroed; every selection leaves it so
+    if (e == cudaSuccess) e = cudaMemsetAsync(x->st, 0, sizeof(SelState) * 2 * B, ds->ctx->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(x->hist, 0, sizeof(uint32_t) * 2 * B * kSelBins, ds->ctx->stream);
     if (e != cudaSuccess) {
         set_cuda_error(e, "batch workspace allocation");
         free_batchwork(x);
@@ -309,7 +312,6 @@ int iht_fit_batch(iht_dataset *ds, int32_t b, const iht_solve_desc *solves,
     if ((rc = build_sets(ds, w, sets, opt.in_mem, set_rows))) return rc;
 
     const size_t np = (size_t)ds->n_pad, p = (size_t)ds->p, K = (size_t)w->kcap;
-    const size_t nch = (size_t)sel_nchunks(ds->p);
     const int npart = zmul_blocks(ds);
 
     // phenotypes, finite check, per-solve state
@@ -373,7 +375,7 @@ int iht_fit_batch(iht_dataset *ds, int32_t b, const iht_solve_desc *solves,
             J.out = t == 0 ? B.S : B.cand;
             J.st = w->st + t * b + c;
             J.hist = w->hist + (size_t)(t * b + c) * kSelBins;
-            J.chunk_eq = w->chunk_eq + (size_t)(t * b + c) * nch;
+            J.cand = w->selcand + (size_t)(t * b + c) * kSelCap;
             J.done = &w->sc[c].done;
             J.K = (uint32_t)(t == 0 ? B.k : B.K);
         }

@@ -26,6 +26,7 @@ namespace iht {
 constexpr int kMaxK = 1024;            // largest sparsity level accepted
 constexpr int kMaxCand = 2 * kMaxK;    // candidate list of the projection
 constexpr int kSelBins = 2048;         // radix-select histogram bins
+constexpr int kSelCap = 4096;          // keys at or above the boundary bin the fast finish sorts
 constexpr int kPartials = 2048;        // max blocks of per-block partial sums (3 values each)
 
 struct Scalars {                       // device-resident state of one solve
@@ -85,9 +86,12 @@ inline void prof_end(ProfEvents *pe, cudaStream_t s)
     }
 }
 
-struct SelState {                      // radix select progress
+struct SelState {                      // top-K selection progress (zero between calls)
     uint32_t prefix, mask, need, count_gt;
     uint32_t n_gt, err;
+    uint32_t ticket_a, ticket_b;       // blocks done in launch A / B
+    uint32_t ncand;                    // keys at or above the boundary bin
+    uint32_t pad[3];
 };
 
 // Host-side handles -------------------------------------------------------
@@ -113,8 +117,7 @@ struct DeviceGuard {
 
 struct SelWork {                       // radix-select scratch, one per context
     uint32_t *hist = nullptr;          // kSelBins
-    uint32_t *chunk_eq = nullptr;      // per-chunk counts of keys equal to the threshold
-    int64_t nchunks_cap = 0;
+    unsigned long long *cand = nullptr;    // kSelCap candidate words
     SelState *st = nullptr;
 };
 
@@ -251,11 +254,10 @@ struct SelJob {                        // one problem of a batched top-K
     int32_t *out;
     SelState *st;
     uint32_t *hist;                    // kSelBins
-    uint32_t *chunk_eq;                // sel_nchunks(p)
+    unsigned long long *cand;          // kSelCap candidate words
     const int32_t *done;               // skip the problem when *done (may be null)
     uint32_t K;
 };
-int64_t sel_nchunks(int64_t p);
 int select_topk_batch(iht_ctx *ctx, const SelJob *jobs, int nb, int64_t p);
 int ensure_selwork(iht_ctx *ctx, int64_t p);
 int select_topk(iht_ctx *ctx, const float *key_src, int64_t p, int32_t K, int32_t *out_idx,

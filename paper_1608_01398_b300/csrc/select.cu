@@ -2,16 +2,21 @@
 // projection P_{S_k}; the paper only asks for a fast sort, the tie rule is
 // this library's reading).
 //
-// Radix select on the IEEE bits of |x| (for non-negative floats the unsigned
-// bit pattern is monotone in the value):
-//   pass 0 histograms bits 30..20 (2048 bins), pass 1 bits 19..10, pass 2
-//   bits 9..0, each restricted to keys matching the digits fixed so far; a
-//   single-CTA scan after each pass picks the digit where the running count
-//   from the top reaches K.  The result is the K-th largest key T, the number
-//   of keys above it, and how many keys equal to T are still needed.
-// Collection writes every key > T (unordered) and the lowest-index keys == T
-// (ordered by a per-chunk count and an exclusive scan), then one CTA sorts the
-// K indices ascending.  NaN keys set SelState::err bit 0.
+// Two launches per call (per problem in the batched form), no host round trip:
+//   A  histograms bits 30..20 of |x| (2048 bins; for non-negative floats the
+//      unsigned bit pattern is monotone in the value).  The last block to
+//      finish (an atomic ticket) scans the bins from the top for the boundary
+//      bin b: fewer than K keys lie above it, at least K at or above it.
+//   B  copies every key in bin b or above -- typically a few hundred -- as the
+//      64-bit word (key << 32 | ~index) into a candidate buffer; the last block
+//      sorts the words descending (larger key first, lower index first among
+//      equal keys), takes the first K indices and sorts them ascending.
+// When more than kSelCap keys lie in or above the boundary bin (heavy ties),
+// B's last block finishes alone with the exact radix select: bits 19..10 and
+// 9..0 within the boundary bin give the K-th key T, then every key > T and the
+// lowest-index keys == T.  The tickets, the histogram and the candidate count
+// are zero again when a call ends (the scratch is zeroed once when allocated).
+// NaN keys set SelState::err bit 0 (sticky).
 #include <mutex>
 
 #include "common.cuh"
@@ -20,84 +25,15 @@ namespace iht {
 
 __device__ __forceinline__ uint32_t sel_key(float x) { return __float_as_uint(x) & 0x7fffffffu; }
 
-constexpr int kSelThreads = 256;
-constexpr int kSelItems = 16;                          // consecutive indices per thread
-constexpr int kSelChunk = kSelThreads * kSelItems;     // indices per collection block
+constexpr int kSelAThreads = 256;
+constexpr int kSelBThreads = 512;
+constexpr int kSelKeysPerBlock = 4096;     // keys per block of A and B (fewer blocks: fewer atomics)
 
-__device__ __forceinline__ void sel_init_body(SelState *st, uint32_t K, uint32_t *hist)
+// Exclusive scan of x over the block (blockDim.x <= 1024); wsum: 32 words.
+__device__ __forceinline__ uint32_t sel_excl_scan(uint32_t x, uint32_t *wsum, uint32_t *total = nullptr)
 {
-    if (threadIdx.x == 0) {
-        st->prefix = 0;
-        st->mask = 0;
-        st->need = K;
-        st->count_gt = 0;
-        st->n_gt = 0;
-        st->err = 0;
-    }
-    for (int b = threadIdx.x; b < kSelBins; b += blockDim.x) hist[b] = 0;
-}
-
-__global__ void k_sel_init(SelState *st, uint32_t K, uint32_t *hist, const int32_t *done)
-{
-    if (done && *done) return;
-    sel_init_body(st, K, hist);
-}
-
-// Histogram pass over keys[0..p) with the digits fixed so far; blockIdx.x
-// strides over the keys.
-__device__ __forceinline__ void sel_hist_body(const float *__restrict__ keys, int64_t p,
-                                              SelState *st, uint32_t *hist, int shift,
-                                              uint32_t dmask)
-{
-    __shared__ uint32_t sh[kSelBins];
-    for (int b = threadIdx.x; b < kSelBins; b += blockDim.x) sh[b] = 0;
-    __syncthreads();
-    const uint32_t prefix = st->prefix, mask = st->mask;
-    bool nan = false;
-    // 16-byte loads, two in flight per thread, over the 16-byte aligned middle of
-    // keys; the (at most 3 + 3) keys before and after it one at a time
-    auto one = [&](float x) {
-        const uint32_t k = sel_key(x);
-        nan |= k > 0x7f800000u;
-        if ((k & mask) == prefix) atomicAdd(&sh[(k >> shift) & dmask], 1u);
-    };
-    const int64_t head = std::min<int64_t>(p, (int64_t)((16u - ((uintptr_t)keys & 15u)) & 15u) >> 2);
-    const float4 *k4 = reinterpret_cast<const float4 *>(keys + head);
-    const int64_t n4 = (p - head) >> 2, step = (int64_t)gridDim.x * blockDim.x;
-    const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    int64_t q = tid;
-    for (; q + step < n4; q += 2 * step) {
-        const float4 a = k4[q], b = k4[q + step];
-        one(a.x); one(a.y); one(a.z); one(a.w);
-        one(b.x); one(b.y); one(b.z); one(b.w);
-    }
-    if (q < n4) {
-        const float4 a = k4[q];
-        one(a.x); one(a.y); one(a.z); one(a.w);
-    }
-    if (tid < head) one(keys[tid]);
-    const int64_t t = head + (n4 << 2) + tid;
-    if (t < p) one(keys[t]);
-    if (nan && shift == 20) atomicOr(&st->err, 1u);
-    __syncthreads();
-    for (int b = threadIdx.x; b < kSelBins; b += blockDim.x)
-        if (sh[b]) atomicAdd(&hist[b], sh[b]);
-}
-
-__global__ void __launch_bounds__(kSelThreads) k_sel_hist(const float *__restrict__ keys, int64_t p,
-                                                          SelState *st, uint32_t *hist, int shift,
-                                                          uint32_t dmask, const int32_t *done)
-{
-    if (done && *done) return;
-    sel_hist_body(keys, p, st, hist, shift, dmask);
-}
-
-// Inclusive scan over a block of 1024 threads, 2 items per thread (fixed order).
-__device__ __forceinline__ void scan2(uint32_t &a, uint32_t &b, uint32_t *wsum)
-{
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    b += a;
-    uint32_t t = b;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    uint32_t t = x;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
         const uint32_t v = __shfl_up_sync(0xffffffffu, t, o);
@@ -106,162 +42,169 @@ __device__ __forceinline__ void scan2(uint32_t &a, uint32_t &b, uint32_t *wsum)
     if (lane == 31) wsum[wid] = t;
     __syncthreads();
     if (wid == 0) {
-        uint32_t s = wsum[lane];
+        uint32_t q = lane < nw ? wsum[lane] : 0u;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
-            const uint32_t v = __shfl_up_sync(0xffffffffu, s, o);
-            if (lane >= o) s += v;
+            const uint32_t v = __shfl_up_sync(0xffffffffu, q, o);
+            if (lane >= o) q += v;
         }
-        wsum[lane] = s;
+        wsum[lane] = q;
     }
     __syncthreads();
-    const uint32_t off = (t - b) + (wid ? wsum[wid - 1] : 0u);
-    a += off;
-    b += off;
+    const uint32_t r = t - x + (wid ? wsum[wid - 1] : 0u);
+    if (total) *total = wsum[nw - 1];
     __syncthreads();
+    return r;
 }
 
-// Single block of 1024 threads: bins scanned from the top.
-__device__ __forceinline__ void sel_scan_body(SelState *st, uint32_t *hist, int shift, uint32_t dmask,
-                                              int nbins)
+// Bins h[0..nbins) (shared) scanned from the top: res = {bin, keys above it,
+// keys in it} for the bin where the running count reaches need.
+__device__ __forceinline__ void sel_find(const uint32_t *h, int nbins, uint32_t need, uint32_t *wsum,
+                                         uint32_t *res)
 {
-    __shared__ uint32_t wsum[32];
+    const int per = nbins / (int)blockDim.x;
     const int t = threadIdx.x;
-    // reversed order: position q holds bin nbins-1-q
-    const int q0 = 2 * t, q1 = 2 * t + 1;
-    const uint32_t h0 = q0 < nbins ? hist[nbins - 1 - q0] : 0u;
-    const uint32_t h1 = q1 < nbins ? hist[nbins - 1 - q1] : 0u;
-    uint32_t c0 = h0, c1 = h1;
-    scan2(c0, c1, wsum);     // inclusive cumulative counts from the top
-    const uint32_t need = st->need;
-    __syncthreads();
-    int hit = -1;
-    uint32_t above = 0;
-    if (q0 < nbins && c0 >= need && c0 - h0 < need) { hit = nbins - 1 - q0; above = c0 - h0; }
-    if (q1 < nbins && c1 >= need && c1 - h1 < need) { hit = nbins - 1 - q1; above = c1 - h1; }
-    if (hit >= 0) {
-        st->count_gt += above;
-        st->need = need - above;
-        st->prefix |= (uint32_t)hit << shift;
-        st->mask |= dmask << shift;
+    if (t == 0) res[0] = res[1] = res[2] = 0;
+    uint32_t tot = 0;
+    for (int i = 0; i < per; ++i) tot += h[nbins - 1 - (per * t + i)];
+    uint32_t before = sel_excl_scan(tot, wsum);
+    for (int i = 0; i < per; ++i) {
+        const int bin = nbins - 1 - (per * t + i);
+        const uint32_t c = h[bin];
+        if (before < need && before + c >= need) {
+            res[0] = (uint32_t)bin;
+            res[1] = before;
+            res[2] = c;
+        }
+        before += c;
     }
-    if (q0 < nbins) hist[nbins - 1 - q0] = 0;
-    if (q1 < nbins) hist[nbins - 1 - q1] = 0;
-}
-
-__global__ void __launch_bounds__(1024) k_sel_scan(SelState *st, uint32_t *hist, int shift,
-                                                   uint32_t dmask, int nbins, const int32_t *done)
-{
-    if (done && *done) return;
-    sel_scan_body(st, hist, shift, dmask, nbins);
-}
-
-// Keys > T go to out[0..count_gt) in any order; per-chunk counts of keys == T
-// (chunk = blockIdx.x).
-__device__ __forceinline__ void sel_collect_gt_body(const float *__restrict__ keys, int64_t p,
-                                                    SelState *st, int32_t *__restrict__ out,
-                                                    uint32_t *__restrict__ chunk_eq)
-{
-    __shared__ uint32_t sh_eq;
-    if (threadIdx.x == 0) sh_eq = 0;
     __syncthreads();
-    const uint32_t T = st->prefix;
-    const int64_t base = (int64_t)blockIdx.x * kSelChunk;
-    uint32_t eq = 0;
-    for (int it = 0; it < kSelItems; ++it) {
-        const int64_t j = base + it * kSelThreads + threadIdx.x;
-        if (j < p) {
+}
+
+// Calls f(key, index) for every key; 16-byte loads, two in flight per thread,
+// over the 16-byte aligned middle, the (at most 3 + 3) keys around it one at a
+// time.
+template <typename F>
+__device__ __forceinline__ void sel_each(const float *__restrict__ keys, int64_t p, F &&f)
+{
+    const int64_t head = std::min<int64_t>(p, (int64_t)((16u - ((uintptr_t)keys & 15u)) & 15u) >> 2);
+    const float4 *k4 = reinterpret_cast<const float4 *>(keys + head);
+    const int64_t n4 = (p - head) >> 2, step = (int64_t)gridDim.x * blockDim.x;
+    const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    int64_t q = tid;
+    for (; q + step < n4; q += 2 * step) {
+        const float4 a = k4[q], b = k4[q + step];
+        const int64_t ja = head + 4 * q, jb = head + 4 * (q + step);
+        f(a.x, ja); f(a.y, ja + 1); f(a.z, ja + 2); f(a.w, ja + 3);
+        f(b.x, jb); f(b.y, jb + 1); f(b.z, jb + 2); f(b.w, jb + 3);
+    }
+    if (q < n4) {
+        const float4 a = k4[q];
+        const int64_t ja = head + 4 * q;
+        f(a.x, ja); f(a.y, ja + 1); f(a.z, ja + 2); f(a.w, ja + 3);
+    }
+    if (tid < head) f(keys[tid], tid);
+    const int64_t t = head + (n4 << 2) + tid;
+    if (t < p) f(keys[t], t);
+}
+
+// Launch A: histogram of bits 30..20; the last block finds the boundary bin.
+__device__ __forceinline__ void sel_count_body(const float *__restrict__ keys, int64_t p, SelState *st,
+                                               uint32_t *hist, uint32_t K)
+{
+    __shared__ uint32_t sh[kSelBins];
+    __shared__ uint32_t wsum[32];
+    __shared__ uint32_t res[3];
+    __shared__ int last;
+    for (int b = threadIdx.x; b < kSelBins; b += blockDim.x) sh[b] = 0;
+    __syncthreads();
+    bool nan = false;
+    sel_each(keys, p, [&](float x, int64_t) {
+        const uint32_t k = sel_key(x);
+        nan |= k > 0x7f800000u;
+        atomicAdd(&sh[k >> 20], 1u);
+    });
+    if (nan) atomicOr(&st->err, 1u);
+    __syncthreads();
+    for (int b = threadIdx.x; b < kSelBins; b += blockDim.x)
+        if (sh[b]) atomicAdd(&hist[b], sh[b]);
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) last = atomicAdd(&st->ticket_a, 1u) == gridDim.x - 1;
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    for (int b = threadIdx.x; b < kSelBins; b += blockDim.x) {
+        sh[b] = __ldcg(&hist[b]);
+        hist[b] = 0;                                  // clean for the next call
+    }
+    __syncthreads();
+    sel_find(sh, kSelBins, K, wsum, res);
+    if (threadIdx.x == 0) {
+        st->prefix = res[0] << 20;
+        st->mask = 0x7ffu << 20;
+        st->count_gt = res[1];
+        st->need = K - res[1];
+        st->ncand = res[1] + res[2];
+        st->n_gt = 0;
+        st->ticket_a = 0;
+    }
+}
+
+// Exact finish in one block (keys in or above the boundary bin > kSelCap):
+// the other two digits of the K-th key T, then every key > T in any order and
+// the lowest-index keys == T in index order after them.
+__device__ void sel_exact_block(const float *__restrict__ keys, int64_t p, const SelState *st,
+                                int32_t *out, uint32_t K, uint32_t *wsum)
+{
+    __shared__ uint32_t h[1024];
+    __shared__ uint32_t res[3];
+    __shared__ uint32_t s_prefix, s_mask, s_need, s_gt, s_cnt;
+    const int tid = threadIdx.x;
+    if (tid == 0) {
+        s_prefix = st->prefix;
+        s_mask = st->mask;
+        s_need = st->need;
+        s_gt = st->count_gt;
+        s_cnt = 0;
+    }
+    __syncthreads();
+    for (int ps = 0; ps < 2; ++ps) {
+        const int shift = ps == 0 ? 10 : 0;
+        for (int b = tid; b < 1024; b += blockDim.x) h[b] = 0;
+        __syncthreads();
+        const uint32_t prefix = s_prefix, mask = s_mask;
+        for (int64_t j = tid; j < p; j += blockDim.x) {
             const uint32_t k = sel_key(keys[j]);
-            if (k > T) out[atomicAdd(&st->n_gt, 1u)] = (int32_t)j;
-            eq += k == T;
+            if ((k & mask) == prefix) atomicAdd(&h[(k >> shift) & 0x3ffu], 1u);
+        }
+        __syncthreads();
+        sel_find(h, 1024, s_need, wsum, res);
+        if (tid == 0) {
+            s_prefix |= res[0] << shift;
+            s_mask |= 0x3ffu << shift;
+            s_gt += res[1];
+            s_need -= res[1];
+        }
+        __syncthreads();
+    }
+    const uint32_t T = s_prefix, gt = s_gt, need = s_need;
+    for (int64_t j = tid; j < p; j += blockDim.x) {
+        if (sel_key(keys[j]) > T) {
+            const uint32_t slot = atomicAdd(&s_cnt, 1u);
+            if (slot < K) out[slot] = (int32_t)j;
         }
     }
-    if (eq) atomicAdd(&sh_eq, eq);
+    uint32_t taken = 0;
+    for (int64_t base = 0; base < p && taken < need; base += blockDim.x) {
+        const int64_t j = base + tid;
+        const uint32_t f = (j < p && sel_key(keys[j]) == T) ? 1u : 0u;
+        uint32_t tot = 0;
+        const uint32_t r = sel_excl_scan(f, wsum, &tot);
+        if (f && taken + r < need && gt + taken + r < K) out[gt + taken + r] = (int32_t)j;
+        taken += tot;
+    }
     __syncthreads();
-    if (threadIdx.x == 0) chunk_eq[blockIdx.x] = sh_eq;
-}
-
-__global__ void __launch_bounds__(kSelThreads) k_sel_collect_gt(const float *__restrict__ keys,
-                                                                int64_t p, SelState *st,
-                                                                int32_t *__restrict__ out,
-                                                                uint32_t *__restrict__ chunk_eq,
-                                                                const int32_t *done)
-{
-    if (done && *done) return;
-    sel_collect_gt_body(keys, p, st, out, chunk_eq);
-}
-
-// Exclusive scan of chunk_eq in place (single block of 1024 threads).
-__device__ __forceinline__ void sel_scan_chunks_body(uint32_t *chunk_eq, int64_t nchunks)
-{
-    __shared__ uint32_t wsum[32];
-    __shared__ uint32_t carry;
-    if (threadIdx.x == 0) carry = 0;
-    __syncthreads();
-    for (int64_t base = 0; base < nchunks; base += 2048) {
-        const int64_t i0 = base + 2 * threadIdx.x, i1 = i0 + 1;
-        const uint32_t h0 = i0 < nchunks ? chunk_eq[i0] : 0u;
-        const uint32_t h1 = i1 < nchunks ? chunk_eq[i1] : 0u;
-        uint32_t c0 = h0, c1 = h1;
-        scan2(c0, c1, wsum);
-        const uint32_t cr = carry;
-        if (i0 < nchunks) chunk_eq[i0] = cr + c0 - h0;
-        if (i1 < nchunks) chunk_eq[i1] = cr + c1 - h1;
-        __syncthreads();
-        if (threadIdx.x == blockDim.x - 1) carry = cr + c1;
-        __syncthreads();
-    }
-}
-
-__global__ void __launch_bounds__(1024) k_sel_scan_chunks(uint32_t *chunk_eq, int64_t nchunks,
-                                                          const int32_t *done)
-{
-    if (done && *done) return;
-    sel_scan_chunks_body(chunk_eq, nchunks);
-}
-
-// The lowest-index keys == T, in index order, after the keys > T.
-__device__ __forceinline__ void sel_collect_eq_body(const float *__restrict__ keys, int64_t p,
-                                                    const SelState *st, int32_t *__restrict__ out,
-                                                    const uint32_t *__restrict__ chunk_off)
-{
-    __shared__ uint32_t wsum[kSelThreads / 32];
-    const uint32_t T = st->prefix, need = st->need, gt = st->count_gt;
-    const uint32_t off0 = chunk_off[blockIdx.x];
-    if (off0 >= need) return;                 // uniform over the block
-    const int64_t base = (int64_t)blockIdx.x * kSelChunk + (int64_t)threadIdx.x * kSelItems;
-    uint32_t mine = 0;
-    for (int it = 0; it < kSelItems; ++it) {
-        const int64_t j = base + it;
-        mine += (j < p) && sel_key(keys[j]) == T;
-    }
-    // exclusive scan of `mine` over the block
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    uint32_t t = mine;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const uint32_t v = __shfl_up_sync(0xffffffffu, t, o);
-        if (lane >= o) t += v;
-    }
-    if (lane == 31) wsum[wid] = t;
-    __syncthreads();
-    uint32_t woff = 0;
-    for (int w = 0; w < wid; ++w) woff += wsum[w];
-    uint32_t rank = off0 + woff + t - mine;
-    for (int it = 0; it < kSelItems && rank < need; ++it) {
-        const int64_t j = base + it;
-        if (j < p && sel_key(keys[j]) == T) out[gt + rank++] = (int32_t)j;
-    }
-}
-
-__global__ void __launch_bounds__(kSelThreads) k_sel_collect_eq(const float *__restrict__ keys,
-                                                                int64_t p, const SelState *st,
-                                                                int32_t *__restrict__ out,
-                                                                const uint32_t *__restrict__ chunk_off,
-                                                                const int32_t *done)
-{
-    if (done && *done) return;
-    sel_collect_eq_body(keys, p, st, out, chunk_off);
 }
 
 // Sort K (<= kMaxCand) indices ascending in one block (bitonic in shared memory).
@@ -291,109 +234,128 @@ __device__ __forceinline__ void sort_idx_body(int32_t *idx, int K)
     for (int i = threadIdx.x; i < K; i += blockDim.x) idx[i] = s[i];
 }
 
-__global__ void __launch_bounds__(1024) k_sort_idx(int32_t *idx, int K, const int32_t *done)
+// Launch B: candidates at or above the boundary bin; the last block finishes.
+__device__ __forceinline__ void sel_pick_body(const float *__restrict__ keys, int64_t p, SelState *st,
+                                              unsigned long long *cand, int32_t *out, uint32_t K)
+{
+    __shared__ unsigned long long sk[kSelCap];
+    __shared__ uint32_t wsum[32];
+    __shared__ int last;
+    const uint32_t ncand = st->ncand;
+    const bool fast = ncand <= (uint32_t)kSelCap;
+    if (fast) {
+        const uint32_t lo = st->prefix;               // bin b << 20: keys >= lo are the candidates
+        sel_each(keys, p, [&](float x, int64_t j) {
+            const uint32_t k = sel_key(x);
+            if (k >= lo) {
+                const uint32_t slot = atomicAdd(&st->n_gt, 1u);
+                if (slot < (uint32_t)kSelCap)
+                    cand[slot] = ((unsigned long long)k << 32) | (unsigned long long)(~(uint32_t)j);
+            }
+        });
+    }
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) last = atomicAdd(&st->ticket_b, 1u) == gridDim.x - 1;
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    if (fast) {
+        int P = 1;
+        while (P < (int)ncand) P <<= 1;
+        for (int i = threadIdx.x; i < P; i += blockDim.x) sk[i] = i < (int)ncand ? __ldcg(&cand[i]) : 0ull;
+        __syncthreads();
+        for (int size = 2; size <= P; size <<= 1) {               // bitonic, descending
+            for (int stride = size >> 1; stride > 0; stride >>= 1) {
+                for (int i = threadIdx.x; i < P; i += blockDim.x) {
+                    const int jx = i ^ stride;
+                    if (jx > i) {
+                        const bool up = (i & size) == 0;
+                        const unsigned long long a = sk[i], b = sk[jx];
+                        if ((a < b) == up) {
+                            sk[i] = b;
+                            sk[jx] = a;
+                        }
+                    }
+                }
+                __syncthreads();
+            }
+        }
+        for (int i = threadIdx.x; i < (int)K; i += blockDim.x)
+            out[i] = (int32_t)(~(uint32_t)(sk[i] & 0xffffffffull));
+        __syncthreads();
+    } else {
+        sel_exact_block(keys, p, st, out, K, wsum);
+    }
+    sort_idx_body(out, (int)K);
+    if (threadIdx.x == 0) {
+        st->n_gt = 0;
+        st->ticket_b = 0;
+    }
+}
+
+__global__ void __launch_bounds__(kSelAThreads) k_sel_count(const float *__restrict__ keys, int64_t p,
+                                                            SelState *st, uint32_t *hist, uint32_t K,
+                                                            const int32_t *done)
 {
     if (done && *done) return;
-    sort_idx_body(idx, K);
+    sel_count_body(keys, p, st, hist, K);
 }
 
-// ---------------------------------------------------------------------------
-// Batched selection: blockIdx.y (or blockIdx.x for the single-block steps)
-// indexes the problem; each problem has its own keys, K, output and scratch.
-
-__global__ void k_bsel_init(const SelJob *jobs)
+__global__ void __launch_bounds__(kSelBThreads) k_sel_pick(const float *__restrict__ keys, int64_t p,
+                                                           SelState *st, unsigned long long *cand,
+                                                           int32_t *out, uint32_t K, const int32_t *done)
 {
-    const SelJob &J = jobs[blockIdx.x];
-    if (J.done && *J.done) return;
-    sel_init_body(J.st, J.K, J.hist);
+    if (done && *done) return;
+    sel_pick_body(keys, p, st, cand, out, K);
 }
 
-__global__ void __launch_bounds__(kSelThreads) k_bsel_hist(const SelJob *jobs, int64_t p, int shift,
-                                                           uint32_t dmask)
+// Batched selection: blockIdx.y indexes the problem; each problem has its own
+// keys, K, output and scratch.
+__global__ void __launch_bounds__(kSelAThreads) k_bsel_count(const SelJob *jobs, int64_t p)
 {
     const SelJob &J = jobs[blockIdx.y];
     if (J.done && *J.done) return;
-    sel_hist_body(J.keys, p, J.st, J.hist, shift, dmask);
+    sel_count_body(J.keys, p, J.st, J.hist, J.K);
 }
 
-__global__ void __launch_bounds__(1024) k_bsel_scan(const SelJob *jobs, int shift, uint32_t dmask,
-                                                    int nbins)
-{
-    const SelJob &J = jobs[blockIdx.x];
-    if (J.done && *J.done) return;
-    sel_scan_body(J.st, J.hist, shift, dmask, nbins);
-}
-
-__global__ void __launch_bounds__(kSelThreads) k_bsel_collect_gt(const SelJob *jobs, int64_t p)
+__global__ void __launch_bounds__(kSelBThreads) k_bsel_pick(const SelJob *jobs, int64_t p)
 {
     const SelJob &J = jobs[blockIdx.y];
     if (J.done && *J.done) return;
-    sel_collect_gt_body(J.keys, p, J.st, J.out, J.chunk_eq);
+    sel_pick_body(J.keys, p, J.st, J.cand, J.out, J.K);
 }
 
-__global__ void __launch_bounds__(1024) k_bsel_scan_chunks(const SelJob *jobs, int64_t nchunks)
+static int sel_blocks(int64_t p, int num_sms, int nb)
 {
-    const SelJob &J = jobs[blockIdx.x];
-    if (J.done && *J.done) return;
-    sel_scan_chunks_body(J.chunk_eq, nchunks);
+    return (int)std::max<int64_t>(1, std::min<int64_t>((p + kSelKeysPerBlock - 1) / kSelKeysPerBlock,
+                                                        ((int64_t)num_sms * 2 + nb - 1) / nb));
 }
 
-__global__ void __launch_bounds__(kSelThreads) k_bsel_collect_eq(const SelJob *jobs, int64_t p)
-{
-    const SelJob &J = jobs[blockIdx.y];
-    if (J.done && *J.done) return;
-    sel_collect_eq_body(J.keys, p, J.st, J.out, J.chunk_eq);
-}
-
-__global__ void __launch_bounds__(1024) k_bsort_idx(const SelJob *jobs)
-{
-    const SelJob &J = jobs[blockIdx.x];
-    if (J.done && *J.done) return;
-    sort_idx_body(J.out, (int)J.K);
-}
-
-int64_t sel_nchunks(int64_t p) { return (p + kSelChunk - 1) / kSelChunk; }
-
-// Top-K of |keys| for nb problems at once (jobs: device array of nb SelJob;
-// every job's chunk_eq holds sel_nchunks(p) counts).
+// Top-K of |keys| for nb problems at once (jobs: device array of nb SelJob
+// whose scratch was zeroed when allocated).
 int select_topk_batch(iht_ctx *ctx, const SelJob *jobs, int nb, int64_t p)
 {
     if (nb < 1) return IHT_OK;
     cudaStream_t s = ctx->stream;
-    const int64_t nchunks = (p + kSelChunk - 1) / kSelChunk;
-    const int hblocks = (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(p, kSelThreads),
-                                                                     ((int64_t)ctx->num_sms * 4 + nb - 1) / nb));
-    k_bsel_init<<<nb, 256, 0, s>>>(jobs);
-    const int shifts[3] = {20, 10, 0};
-    const uint32_t dmasks[3] = {0x7ffu, 0x3ffu, 0x3ffu};
-    for (int ps = 0; ps < 3; ++ps) {
-        k_bsel_hist<<<dim3(hblocks, nb), kSelThreads, 0, s>>>(jobs, p, shifts[ps], dmasks[ps]);
-        k_bsel_scan<<<nb, 1024, 0, s>>>(jobs, shifts[ps], dmasks[ps], (int)dmasks[ps] + 1);
-    }
-    k_bsel_collect_gt<<<dim3((unsigned)nchunks, nb), kSelThreads, 0, s>>>(jobs, p);
-    k_bsel_scan_chunks<<<nb, 1024, 0, s>>>(jobs, nchunks);
-    k_bsel_collect_eq<<<dim3((unsigned)nchunks, nb), kSelThreads, 0, s>>>(jobs, p);
-    k_bsort_idx<<<nb, 1024, 0, s>>>(jobs);
-    note_launch(11);
+    const int blocks = sel_blocks(p, ctx->num_sms, nb);
+    k_bsel_count<<<dim3(blocks, nb), kSelAThreads, 0, s>>>(jobs, p);
+    k_bsel_pick<<<dim3(blocks, nb), kSelBThreads, 0, s>>>(jobs, p);
+    note_launch(2);
     IHT_CUDA(cudaGetLastError());
     return IHT_OK;
 }
 
 int ensure_selwork(iht_ctx *ctx, int64_t p)
 {
+    (void)p;
     SelWork &w = ctx->sel;
-    const int64_t nchunks = (p + kSelChunk - 1) / kSelChunk;
     if (!w.hist) {
         IHT_CUDA(cudaMalloc(&w.hist, sizeof(uint32_t) * kSelBins));
         IHT_CUDA(cudaMalloc(&w.st, sizeof(SelState)));
+        IHT_CUDA(cudaMalloc(&w.cand, sizeof(unsigned long long) * kSelCap));
         IHT_CUDA(cudaMemsetAsync(w.hist, 0, sizeof(uint32_t) * kSelBins, ctx->stream));
-    }
-    if (nchunks > w.nchunks_cap) {
-        if (w.chunk_eq) cudaFree(w.chunk_eq);
-        w.chunk_eq = nullptr;
-        w.nchunks_cap = 0;
-        IHT_CUDA(cudaMalloc(&w.chunk_eq, sizeof(uint32_t) * nchunks));
-        w.nchunks_cap = nchunks;
+        IHT_CUDA(cudaMemsetAsync(w.st, 0, sizeof(SelState), ctx->stream));
     }
     return IHT_OK;
 }
@@ -403,24 +365,11 @@ int select_topk(iht_ctx *ctx, const float *keys, int64_t p, int32_t K, int32_t *
 {
     SelWork *ws = &ctx->sel;
     cudaStream_t s = ctx->stream;
-    if (K < 1 || K > p || K > kMaxCand) return IHT_EINVAL;
-    const int64_t nchunks = (p + kSelChunk - 1) / kSelChunk;
-    if (nchunks > ws->nchunks_cap) return IHT_EINVAL;
-    const int hblocks = (int)std::min<int64_t>(ceil_div(p, kSelThreads), (int64_t)ctx->num_sms * 4);
-    k_sel_init<<<1, 256, 0, s>>>(ws->st, (uint32_t)K, ws->hist, done);
-    const int shifts[3] = {20, 10, 0};
-    const uint32_t dmasks[3] = {0x7ffu, 0x3ffu, 0x3ffu};
-    for (int ps = 0; ps < 3; ++ps) {
-        k_sel_hist<<<hblocks, kSelThreads, 0, s>>>(keys, p, ws->st, ws->hist, shifts[ps], dmasks[ps],
-                                                   done);
-        k_sel_scan<<<1, 1024, 0, s>>>(ws->st, ws->hist, shifts[ps], dmasks[ps],
-                                      (int)dmasks[ps] + 1, done);
-    }
-    k_sel_collect_gt<<<(int)nchunks, kSelThreads, 0, s>>>(keys, p, ws->st, out, ws->chunk_eq, done);
-    k_sel_scan_chunks<<<1, 1024, 0, s>>>(ws->chunk_eq, nchunks, done);
-    k_sel_collect_eq<<<(int)nchunks, kSelThreads, 0, s>>>(keys, p, ws->st, out, ws->chunk_eq, done);
-    k_sort_idx<<<1, 1024, 0, s>>>(out, K, done);
-    note_launch(11);
+    if (K < 1 || K > p || K > kMaxCand || !ws->hist) return IHT_EINVAL;
+    const int blocks = sel_blocks(p, ctx->num_sms, 1);
+    k_sel_count<<<blocks, kSelAThreads, 0, s>>>(keys, p, ws->st, ws->hist, (uint32_t)K, done);
+    k_sel_pick<<<blocks, kSelBThreads, 0, s>>>(keys, p, ws->st, ws->cand, out, (uint32_t)K, done);
+    note_launch(2);
     IHT_CUDA(cudaGetLastError());
     return IHT_OK;
 }
@@ -429,19 +378,18 @@ int select_topk(iht_ctx *ctx, const float *keys, int64_t p, int32_t K, int32_t *
 // Allocation-free top-k (iht_topk_noalloc).
 //
 // For callers that must not allocate device memory: the scratch of the
-// selection (radix histogram, selection state, per-chunk tie counts) lives in
-// this file-scope device array, sized for p <= kNoAllocMaxP.  Every GPU that
-// loads the library holds it (about 24 KB) until the process exits.  The array
-// is shared by all calls on a device and keeps the last call's contents; the
-// first kernel of each call clears the histogram and the state, and the chunk
-// counts are written in full before they are read.  Calls that overlap on the
-// GPU (different streams, or several host threads) race on it.
+// selection (histogram, selection state, candidate buffer) lives in this
+// file-scope device array.  Every GPU that loads the library holds it (about
+// 41 KB) until the process exits.  The first call on a device clears it on the
+// caller's stream (cudaMemsetAsync, ahead of its kernels), and every call
+// leaves it clean again.  The array is shared by all calls on a device: calls
+// that overlap on the GPU (different streams, or several host threads) race on
+// it.
 
 constexpr int64_t kNoAllocMaxP = int64_t(1) << 24;                 // 16 777 216 entries
-constexpr int64_t kNoAllocChunks = kNoAllocMaxP / kSelChunk;      // 4096 tie-count chunks
 constexpr size_t kNoAllocHist = sizeof(uint32_t) * kSelBins;      // 8 KB
 constexpr size_t kNoAllocState = 256;                             // SelState, padded
-constexpr size_t kNoAllocBytes = kNoAllocHist + kNoAllocState + sizeof(uint32_t) * kNoAllocChunks;
+constexpr size_t kNoAllocBytes = kNoAllocHist + kNoAllocState + sizeof(unsigned long long) * kSelCap;
 
 static __device__ __align__(256) unsigned char g_topk_scratch[kNoAllocBytes];
 
@@ -452,7 +400,11 @@ static int g_noalloc_sms[kNoAllocMaxDevices] = {};
 
 // Device address of the scratch array on `device` (looked up once per device,
 // with that device current; the caller's current device is restored).
-static int noalloc_scratch(int device, unsigned char **addr, int *num_sms)
+static bool g_noalloc_cleared[kNoAllocMaxDevices] = {};
+
+// first: set when this call is the first on the device (the caller clears the
+// scratch on its stream before using it).
+static int noalloc_scratch(int device, unsigned char **addr, int *num_sms, bool *first)
 {
     if (device < 0 || device >= kNoAllocMaxDevices) return IHT_EINVAL;
     std::lock_guard<std::mutex> lock(g_noalloc_mu);
@@ -474,6 +426,8 @@ static int noalloc_scratch(int device, unsigned char **addr, int *num_sms)
     }
     *addr = g_noalloc_addr[device];
     *num_sms = g_noalloc_sms[device];
+    *first = !g_noalloc_cleared[device];
+    g_noalloc_cleared[device] = true;
     return IHT_OK;
 }
 
@@ -487,29 +441,28 @@ extern "C" int iht_topk_noalloc(int device, void *stream, const float *w, int64_
     if (p > kNoAllocMaxP) return IHT_EINVAL;   // beyond the size of the static scratch
     unsigned char *scratch = nullptr;
     int sms = 0;
-    int rc = noalloc_scratch(device, &scratch, &sms);
+    bool first = false;
+    int rc = noalloc_scratch(device, &scratch, &sms, &first);
     if (rc) return rc;
     int prev = -1;
     IHT_CUDA(cudaGetDevice(&prev));
     if (prev != device) IHT_CUDA(cudaSetDevice(device));
+    if (first) {
+        const cudaError_t ce = cudaMemsetAsync(scratch, 0, kNoAllocBytes, (cudaStream_t)stream);
+        if (ce != cudaSuccess) {
+            if (prev != device) cudaSetDevice(prev);
+            set_cuda_error(ce, "iht_topk_noalloc scratch clear");
+            return IHT_ECUDA;
+        }
+    }
     uint32_t *hist = reinterpret_cast<uint32_t *>(scratch);
     SelState *st = reinterpret_cast<SelState *>(scratch + kNoAllocHist);
-    uint32_t *chunk_eq = reinterpret_cast<uint32_t *>(scratch + kNoAllocHist + kNoAllocState);
+    unsigned long long *cand = reinterpret_cast<unsigned long long *>(scratch + kNoAllocHist + kNoAllocState);
     cudaStream_t s = (cudaStream_t)stream;
-    const int64_t nchunks = (p + kSelChunk - 1) / kSelChunk;
-    const int hblocks = (int)std::min<int64_t>(ceil_div(p, kSelThreads), (int64_t)sms * 4);
-    k_sel_init<<<1, 256, 0, s>>>(st, (uint32_t)k, hist, nullptr);
-    const int shifts[3] = {20, 10, 0};
-    const uint32_t dmasks[3] = {0x7ffu, 0x3ffu, 0x3ffu};
-    for (int ps = 0; ps < 3; ++ps) {
-        k_sel_hist<<<hblocks, kSelThreads, 0, s>>>(w, p, st, hist, shifts[ps], dmasks[ps], nullptr);
-        k_sel_scan<<<1, 1024, 0, s>>>(st, hist, shifts[ps], dmasks[ps], (int)dmasks[ps] + 1, nullptr);
-    }
-    k_sel_collect_gt<<<(int)nchunks, kSelThreads, 0, s>>>(w, p, st, idx_out, chunk_eq, nullptr);
-    k_sel_scan_chunks<<<1, 1024, 0, s>>>(chunk_eq, nchunks, nullptr);
-    k_sel_collect_eq<<<(int)nchunks, kSelThreads, 0, s>>>(w, p, st, idx_out, chunk_eq, nullptr);
-    k_sort_idx<<<1, 1024, 0, s>>>(idx_out, k, nullptr);
-    note_launch(11);
+    const int blocks = sel_blocks(p, sms, 1);
+    k_sel_count<<<blocks, kSelAThreads, 0, s>>>(w, p, st, hist, (uint32_t)k, nullptr);
+    k_sel_pick<<<blocks, kSelBThreads, 0, s>>>(w, p, st, cand, idx_out, (uint32_t)k, nullptr);
+    note_launch(2);
     const cudaError_t e = cudaGetLastError();
     if (prev != device) cudaSetDevice(prev);
     if (e != cudaSuccess) {

@@ -58,7 +58,8 @@ struct SlotMem {
     int32_t *S, *Sp, *cand;
     double *bS, *bSp, *coef, *partials;
     SelState *st;
-    uint32_t *hist, *chunk_eq;
+    uint32_t *hist;
+    unsigned long long *selcand;
     int32_t *rows;
     double *ystage;
 };
@@ -82,7 +83,6 @@ static size_t slot_layout(const iht_dataset *ds, int k, int64_t n_rows, char *ba
 {
     const size_t np = (size_t)ds->n_pad, p = (size_t)ds->p;
     const size_t K = (size_t)std::min<int64_t>(2 * (int64_t)k, ds->p);
-    const size_t nch = (size_t)sel_nchunks(ds->p);
     size_t off = 0;
     auto take = [&](size_t bytes) -> char * {
         char *q = base ? base + off : nullptr;
@@ -112,7 +112,7 @@ static size_t slot_layout(const iht_dataset *ds, int k, int64_t n_rows, char *ba
     t.partials = (double *)take(sizeof(double) * 3 * kPartials);
     t.st = (SelState *)take(sizeof(SelState) * 2);
     t.hist = (uint32_t *)take(sizeof(uint32_t) * 2 * kSelBins);
-    t.chunk_eq = (uint32_t *)take(sizeof(uint32_t) * 2 * nch);
+    t.selcand = (unsigned long long *)take(sizeof(unsigned long long) * 2 * kSelCap);
     t.rows = (int32_t *)take(sizeof(int32_t) * (size_t)n_rows);
     t.ystage = (double *)take(sizeof(double) * (size_t)n_rows);
     if (m) *m = t;
@@ -195,6 +195,9 @@ static int srv_admit_setup(iht_server *S, const std::vector<int> &fresh, std::ve
                                  cudaMemcpyHostToDevice, s));
         IHT_CUDA(cudaMemsetAsync(m.S, 0xFF, sizeof(int32_t) * q.k, s));
         IHT_CUDA(cudaMemsetAsync(m.bS, 0, sizeof(double) * q.k, s));
+        // selection scratch starts zeroed; every selection leaves it so
+        IHT_CUDA(cudaMemsetAsync(m.st, 0, sizeof(SelState) * 2, s));
+        IHT_CUDA(cudaMemsetAsync(m.hist, 0, sizeof(uint32_t) * 2 * kSelBins, s));
         const int32_t *rows_dev = q.all_rows ? nullptr : m.rows;
         int rc;
         if ((rc = setup_rowset(ds, rows_dev, q.n_rows, m.rs, &S->sc[c].err))) return rc;
@@ -229,7 +232,7 @@ static int srv_admit_setup(iht_server *S, const std::vector<int> &fresh, std::ve
         J.out = m.cand;
         J.st = m.st + 1;
         J.hist = m.hist + kSelBins;
-        J.chunk_eq = m.chunk_eq + sel_nchunks(ds->p);
+        J.cand = m.selcand + kSelCap;
         J.done = &S->sc[c].done;
         J.K = (uint32_t)sl.K;
         IHT_CUDA(cudaMemcpyAsync(S->jobs_c + c, &J, sizeof(SelJob), cudaMemcpyHostToDevice, s));
@@ -297,7 +300,7 @@ static int srv_tick(iht_server *S, const std::vector<int> &fresh)
             J.out = m.S;
             J.st = m.st;
             J.hist = m.hist;
-            J.chunk_eq = m.chunk_eq;
+            J.cand = m.selcand;
             J.done = &S->sc[c].done;
             J.K = (uint32_t)S->slots[c].k;
         }
@@ -445,7 +448,7 @@ static void srv_free(iht_server *S)
         if (p) cudaFreeHost(p);
     if (S->ctx.sel.hist) cudaFree(S->ctx.sel.hist);
     if (S->ctx.sel.st) cudaFree(S->ctx.sel.st);
-    if (S->ctx.sel.chunk_eq) cudaFree(S->ctx.sel.chunk_eq);
+    if (S->ctx.sel.cand) cudaFree(S->ctx.sel.cand);
     if (S->ctx.stream) cudaStreamDestroy(S->ctx.stream);
     delete S;
 }

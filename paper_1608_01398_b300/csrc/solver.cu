@@ -75,13 +75,16 @@ __global__ void __launch_bounds__(1024) k_gather_gS(const float *__restrict__ g,
 // out_i = base_i + sum_c a_c (x_i,col_c - u_col_c), a_c = sign coef_c v_col_c, over
 // the observed calls (Z[:, cols] coef, Sec. 2.3.2-2.3.3), on used rows (0
 // elsewhere); per-block sums of out, out^2 and (out - prev)^2 (0 without
-// prev) go to partials[3 b .. 3 b + 2].  One thread per sample, kZmulThreads
-// samples per block; each column's three possible terms a (x - u) for
-// x = 0, 1, 2 are staged in shared memory kZmulChunk columns at a time, so a
-// term costs one FP64 add (FP64 issue is the scarce resource here), added in
-// column order.
+// prev) go to partials[3 b .. 3 b + 2].  One thread per sample, blockDim.x
+// samples per block (as few as the partials table allows, so the small
+// product spreads over the SMs); each column's three possible terms a (x - u)
+// for x = 0, 1, 2 are staged in shared memory kZmulChunk columns at a time, so
+// a term costs one FP64 add (FP64 issue is the scarce resource here), added in
+// column order; a thread issues the byte loads of kZmulBatch columns before
+// their adds.
 constexpr int kZmulChunk = 256;
-constexpr int kZmulThreads = 128;
+constexpr int kZmulThreads = 128;           // largest block
+constexpr int kZmulBatch = 16;
 
 __device__ __forceinline__ void zmul_body(const uint8_t *__restrict__ G, int64_t stride,
                                           int64_t rowb, const int32_t *__restrict__ cols, int m,
@@ -117,6 +120,13 @@ __device__ __forceinline__ void zmul_body(const uint8_t *__restrict__ G, int64_t
         __syncthreads();
         if (inb) {
             int c = 0;
+            for (; c + kZmulBatch <= mc; c += kZmulBatch) {
+                uint32_t b[kZmulBatch];
+#pragma unroll
+                for (int q = 0; q < kZmulBatch; ++q) b[q] = __ldg(srow[c + q] + byte);
+#pragma unroll
+                for (int q = 0; q < kZmulBatch; ++q) acc += term[c + q][(b[q] >> shift) & 3u];
+            }
             for (; c + 4 <= mc; c += 4) {
                 uint32_t b[4];
 #pragma unroll
@@ -158,7 +168,16 @@ __global__ void __launch_bounds__(kZmulThreads) k_zmul(const uint8_t *__restrict
     zmul_body(G, stride, rowb, cols, m, coef, sign, u64, v64, used, base, prev, out, partials, n_pad);
 }
 
-int zmul_blocks(const iht_dataset *ds) { return ceil_div(ds->n_pad, kZmulThreads); }
+// 32, 64 or 128 samples per block: the smallest whose block count fits the
+// partials table.
+static int zmul_threads(const iht_dataset *ds)
+{
+    for (int t = 32; t < kZmulThreads; t *= 2)
+        if (ceil_div(ds->n_pad, t) <= kPartials) return t;
+    return kZmulThreads;
+}
+
+int zmul_blocks(const iht_dataset *ds) { return ceil_div(ds->n_pad, zmul_threads(ds)); }
 
 // out = base + sign * Z[:, cols] coef (device, stream-ordered); partials get
 // zmul_blocks() triples (sum, sum of squares, sum of (out - prev)^2) when not
@@ -167,7 +186,7 @@ int zmul_run(iht_dataset *ds, const int32_t *cols, int m, const double *coef, do
              const double *u, const double *v, const int32_t *used, const double *base,
              double *out, double *partials, const int32_t *done, const double *prev = nullptr)
 {
-    k_zmul<<<zmul_blocks(ds), kZmulThreads, 0, ds->ctx->stream>>>(ds->G, ds->stride, ds->rowb, cols, m, coef,
+    k_zmul<<<zmul_blocks(ds), zmul_threads(ds), 0, ds->ctx->stream>>>(ds->G, ds->stride, ds->rowb, cols, m, coef,
                                                          sign, u, v, used, base, prev, out, partials,
                                                          ds->n_pad, done);
     note_launch();
@@ -940,7 +959,7 @@ int launch_gather_gS_batch(iht_dataset *ds, const BSolve *bs, int nb)
 
 int launch_zmul_batch(iht_dataset *ds, const BSolve *bs, int nb, int, ZmulWhich which)
 {
-    k_zmul_b<<<dim3(zmul_blocks(ds), nb), kZmulThreads, 0, ds->ctx->stream>>>(ds->G, ds->stride, ds->rowb, bs,
+    k_zmul_b<<<dim3(zmul_blocks(ds), nb), zmul_threads(ds), 0, ds->ctx->stream>>>(ds->G, ds->stride, ds->rowb, bs,
                                                                    (int)which, ds->n_pad);
     note_launch();
     IHT_CUDA(cudaGetLastError());
