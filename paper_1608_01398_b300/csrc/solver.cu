@@ -75,15 +75,19 @@ __global__ void __launch_bounds__(1024) k_gather_gS(const float *__restrict__ g,
 // out_i = base_i + sum_c a_c (x_i,col_c - u_col_c), a_c = sign coef_c v_col_c, over
 // the observed calls (Z[:, cols] coef, Sec. 2.3.2-2.3.3), on used rows (0
 // elsewhere); per-block sums of out, out^2 and (out - prev)^2 (0 without
-// prev) go to partials[3 b .. 3 b + 2].  One thread per sample, blockDim.x
-// samples per block (as few as the partials table allows, so the small
-// product spreads over the SMs); each column's three possible terms a (x - u)
+// prev) go to partials[3 b .. 3 b + 2].  One thread per sample, 128 samples
+// per block (FP64 issue, not parallelism, bounds this product: smaller blocks
+// only multiply the partial triples every consumer sums); each column's three
+// possible terms a (x - u)
 // for x = 0, 1, 2 are staged in shared memory kZmulChunk columns at a time, so
 // a term costs one FP64 add (FP64 issue is the scarce resource here), added in
-// column order; a thread issues the byte loads of kZmulBatch columns before
-// their adds.
+// column order.  A thread loads the genotype bytes of a chunk's first
+// kZmulFirst columns (column index, then byte) while the block stages the
+// terms, and the rest kZmulBatch columns at a time, so the latency of a chunk
+// is about two dependent loads.
 constexpr int kZmulChunk = 256;
 constexpr int kZmulThreads = 128;           // largest block
+constexpr int kZmulFirst = 64;
 constexpr int kZmulBatch = 16;
 
 __device__ __forceinline__ void zmul_body(const uint8_t *__restrict__ G, int64_t stride,
@@ -106,6 +110,13 @@ __device__ __forceinline__ void zmul_body(const uint8_t *__restrict__ G, int64_t
     double acc = 0.0;
     for (int c0 = 0; c0 < m; c0 += kZmulChunk) {
         const int mc = min(kZmulChunk, m - c0);
+        const int mf = min(mc, kZmulFirst);
+        uint32_t bf[kZmulFirst];
+        if (inb) {
+#pragma unroll
+            for (int q = 0; q < kZmulFirst; ++q)
+                if (q < mf) bf[q] = __ldg(G + (int64_t)__ldg(cols + c0 + q) * stride + byte);
+        }
         __syncthreads();
         for (int c = threadIdx.x; c < mc; c += blockDim.x) {
             const int col = cols[c0 + c];
@@ -119,7 +130,10 @@ __device__ __forceinline__ void zmul_body(const uint8_t *__restrict__ G, int64_t
         }
         __syncthreads();
         if (inb) {
-            int c = 0;
+#pragma unroll
+            for (int q = 0; q < kZmulFirst; ++q)
+                if (q < mf) acc += term[q][(bf[q] >> shift) & 3u];
+            int c = mf;
             for (; c + kZmulBatch <= mc; c += kZmulBatch) {
                 uint32_t b[kZmulBatch];
 #pragma unroll
@@ -168,14 +182,7 @@ __global__ void __launch_bounds__(kZmulThreads) k_zmul(const uint8_t *__restrict
     zmul_body(G, stride, rowb, cols, m, coef, sign, u64, v64, used, base, prev, out, partials, n_pad);
 }
 
-// 32, 64 or 128 samples per block: the smallest whose block count fits the
-// partials table.
-static int zmul_threads(const iht_dataset *ds)
-{
-    for (int t = 32; t < kZmulThreads; t *= 2)
-        if (ceil_div(ds->n_pad, t) <= kPartials) return t;
-    return kZmulThreads;
-}
+static int zmul_threads(const iht_dataset *) { return kZmulThreads; }
 
 int zmul_blocks(const iht_dataset *ds) { return ceil_div(ds->n_pad, zmul_threads(ds)); }
 
@@ -224,6 +231,9 @@ constexpr int kMergeSort = 4 * kMaxK;   // power of two >= kMergeU
 constexpr int kMergeRank = 768;         // up to this many candidates: selection by rank
 
 struct MergeShared {
+    int32_t sS[kMaxK];            // S, beta_S and the candidates, staged once
+    double sbS[kMaxK];
+    int32_t scand[kMaxCand];
     int32_t uidx[kMergeU];
     double ubeta[kMergeU];
     double ug[kMergeU];
@@ -298,6 +308,11 @@ __device__ __forceinline__ void merge_body(const MergeArgs &A)
     MergeShared &sh = *reinterpret_cast<MergeShared *>(smem_raw);
     Scalars *sc = A.sc;
     const int k = sc->k;
+    for (int i = threadIdx.x; i < k; i += blockDim.x) {
+        sh.sS[i] = A.S[i];
+        sh.sbS[i] = A.bS[i];
+    }
+    for (int i = threadIdx.x; i < A.K; i += blockDim.x) sh.scand[i] = A.cand[i];
 
     double den = 0.0;
     if (A.first && threadIdx.x < 32) {
@@ -331,12 +346,12 @@ __device__ __forceinline__ void merge_body(const MergeArgs &A)
     // U = C (ascending) followed by S \ C (in S order)
     const int K = A.K;
     for (int b = threadIdx.x; b < K; b += blockDim.x) {
-        const int32_t j = A.cand[b];
-        const int pos = lower_bound_i32(A.S, k, j);
-        const bool on = pos < k && A.S[pos] == j;
+        const int32_t j = sh.scand[b];
+        const int pos = lower_bound_i32(sh.sS, k, j);
+        const bool on = pos < k && sh.sS[pos] == j;
         sh.uidx[b] = j;
         sh.inS[b] = on;
-        sh.ubeta[b] = on ? A.bS[pos] : 0.0;
+        sh.ubeta[b] = on ? sh.sbS[pos] : 0.0;
         sh.ug[b] = (double)A.g[j];
     }
     {
@@ -344,9 +359,9 @@ __device__ __forceinline__ void merge_body(const MergeArgs &A)
         int32_t j = 0;
         bool extra = false;
         if (a < k) {
-            j = A.S[a];
-            const int pos = lower_bound_i32(A.cand, K, j);
-            extra = !(pos < K && A.cand[pos] == j);
+            j = sh.sS[a];
+            const int pos = lower_bound_i32(sh.scand, K, j);
+            extra = !(pos < K && sh.scand[pos] == j);
         }
         const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
         const unsigned bal = __ballot_sync(0xffffffffu, extra);
@@ -359,7 +374,7 @@ __device__ __forceinline__ void merge_body(const MergeArgs &A)
             const int u = K + off;
             sh.uidx[u] = j;
             sh.inS[u] = 1;
-            sh.ubeta[u] = A.bS[a];
+            sh.ubeta[u] = sh.sbS[a];
             sh.ug[u] = (double)A.g[j];
         }
         if (threadIdx.x == blockDim.x - 1) sh.nS_extra = off + (extra ? 1 : 0);
@@ -392,17 +407,22 @@ __device__ __forceinline__ void merge_body(const MergeArgs &A)
         for (int r = threadIdx.x; r < k; r += blockDim.x) sh.inSp[sh.spos[r]] = 1;
         __syncthreads();
     }
+    // ||beta+ - beta||^2, ||beta||^2 and |S n S+| by one warp (FP64 issue is
+    // scarce: a block-wide reduction would spend it on empty threads); only
+    // thread 0 uses them
     int kept = 0;
     double dd = 0.0, bb = 0.0;
-    for (int u = threadIdx.x; u < nU; u += blockDim.x) {
-        kept += sh.inS[u] && sh.inSp[u];
-        const double d = (sh.inSp[u] ? sh.uw[u] : 0.0) - sh.ubeta[u];
-        dd += d * d;
-        bb += sh.ubeta[u] * sh.ubeta[u];
+    if (threadIdx.x < 32) {
+        for (int u = threadIdx.x; u < nU; u += 32) {
+            kept += sh.inS[u] && sh.inSp[u];
+            const double d = (sh.inSp[u] ? sh.uw[u] : 0.0) - sh.ubeta[u];
+            dd += d * d;
+            bb += sh.ubeta[u] * sh.ubeta[u];
+        }
+        kept = __reduce_add_sync(0xffffffffu, kept);
+        dd = warp_sum(dd);
+        bb = warp_sum(bb);
     }
-    kept = (int)block_sum((double)kept, sh.red);
-    dd = block_sum(dd, sh.red);
-    bb = block_sum(bb, sh.red);
 
     // S+ in index order with beta+
     if (small) {
