@@ -14,7 +14,8 @@ namespace iht {
 static thread_local char g_last_cuda[256] = "";
 static std::atomic<uint64_t> g_launches{0};
 
-void note_launch(int n) { g_launches.fetch_add((uint64_t)n, std::memory_order_relaxed); }
+void note_launch(int n) { g_launches.fetch_add((uint64_t)(int64_t)n, std::memory_order_relaxed); }
+uint64_t launches_noted() { return g_launches.load(std::memory_order_relaxed); }
 
 void set_cuda_error(cudaError_t e, const char *where)
 {
@@ -35,6 +36,10 @@ void free_workspace(Workspace *ws)
     free_batchwork(ws->bw);
     for (cudaEvent_t e : ws->prof_ev)
         if (e) cudaEventDestroy(e);
+    for (cudaEvent_t e : ws->gev)
+        if (e) cudaEventDestroy(e);
+    if (ws->iter_exec) cudaGraphExecDestroy(ws->iter_exec);
+    if (ws->cap_stream) cudaStreamDestroy(ws->cap_stream);
     delete ws;
 }
 

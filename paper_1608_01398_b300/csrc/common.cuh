@@ -51,6 +51,8 @@ struct Scalars {                       // device-resident state of one solve
     int32_t err;                       // bit 0: non-finite input, bit 1: bad rows
     int32_t live;                      // batched solves: takes part in the current attempt
     int32_t fresh;                     // batched solves: beta = 0 set-up still to run
+    int32_t skip1;                     // 1: no further attempt this iteration (accepted or stopped)
+    int32_t skip2;                     // 1: no next gradient yet (stopped, or still rejecting)
 };
 
 // Device descriptor of one solve of a batch (all pointers device memory).
@@ -177,6 +179,12 @@ struct Workspace {
     cudaEvent_t prof_ev[2 * 256] = {};
     int nprof = 0;
     double prof_ms = 0.0;
+    // one iteration of a solve as a CUDA graph, replayed while its key matches
+    cudaGraphExec_t iter_exec = nullptr;
+    cudaStream_t cap_stream = nullptr;     // private stream the iteration is captured on
+    uint64_t iter_key[8] = {};
+    int iter_launches = 0;                 // kernel launches per replay
+    cudaEvent_t gev[2] = {};               // around the gradient pass inside the graph
     BatchWork *bw = nullptr;               // batched solves (batch.cu)
 };
 constexpr int kProfEvents = 256;
@@ -184,6 +192,7 @@ constexpr int kProfEvents = 256;
 // error helpers -----------------------------------------------------------
 void set_cuda_error(cudaError_t e, const char *where);
 void note_launch(int n = 1);           // kernel launches issued (iht_kernel_launches)
+uint64_t launches_noted();
 #define IHT_CUDA(call)                                                  \
     do {                                                                \
         cudaError_t e_ = (call);                                        \
@@ -231,6 +240,7 @@ int prepare_grad_tc_to(iht_dataset *ds, const float *r32, float *Mj, const int32
 int launch_grad_tc_main_with(iht_dataset *ds, const float *r32, float *g, const float *u32,
                              const float *v32, const float *Mj, const int32_t *done);
 void grad_tc_release_thread();
+uint64_t grad_tc_scratch_id();
 int grad_tc_status(iht_dataset *ds, int *timed_out);
 // impl: 0 default (tensor cores when supported), 1 CUDA cores, 2 tensor cores
 int launch_grad_impl(iht_dataset *ds, int impl, const float *r32, float *g, const int32_t *done);

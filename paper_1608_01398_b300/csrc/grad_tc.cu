@@ -672,6 +672,12 @@ int launch_grad_tc_main(iht_dataset *ds, const float *r32, float *g, const int32
     return launch_grad_tc_main_with(ds, r32, g, ds->ws->u32, ds->ws->v32, ds->ws->Mj, done);
 }
 
+// Identifies the calling thread's pass scratch (changes when it is reallocated).
+uint64_t grad_tc_scratch_id()
+{
+    return (uint64_t)(uintptr_t)g_tc.bimg ^ ((uint64_t)(uintptr_t)g_tc.prm << 1);
+}
+
 // Frees the calling thread's pass scratch (a server's worker before it exits).
 void grad_tc_release_thread()
 {

@@ -220,6 +220,7 @@ struct MergeArgs {
     const double *partials;   // ||Z_S g_S||^2 pieces (first attempt)
     int npart;
     int first;                // 1: compute mu from num / den
+    const int32_t *skip;      // not null: return when *skip (a speculative attempt not needed)
     int32_t *Sp;
     double *bSp;
     Scalars *sc;
@@ -329,10 +330,12 @@ __device__ __forceinline__ void merge_body(const MergeArgs &A)
             if (num == 0.0) {
                 sc->status = IHT_OK;            // g_S = 0: fixed point
                 sc->done = 1;
+                sc->skip1 = sc->skip2 = 1;
                 sh.stop = 1;
             } else if (!(den > 0.0) || !isfinite(den) || !isfinite(num)) {
                 sc->status = IHT_ENUMERIC;
                 sc->done = 1;
+                sc->skip1 = sc->skip2 = 1;
                 sh.stop = 1;
             } else {
                 sc->mu = num / den;
@@ -480,7 +483,7 @@ __device__ __forceinline__ void merge_body(const MergeArgs &A)
 
 __global__ void __launch_bounds__(kMergeThreads) k_merge(MergeArgs A)
 {
-    const int d = A.sc->done;
+    const int d = A.sc->done || (A.skip && *A.skip);
     __syncthreads();   // every thread has read the flag before thread 0 may set it
     if (d) return;
     merge_body(A);
@@ -528,7 +531,13 @@ __device__ __forceinline__ void decide_body(Scalars *sc, const double *partials,
         }
     }
     __syncthreads();
-    if (!accept) return;
+    if (!accept) {
+        if (threadIdx.x == 0) {
+            sc->skip1 = 0;                     // another attempt with the shrunk mu
+            sc->skip2 = 1;
+        }
+        return;
+    }
     const int it = sc->iter;
     for (int c = threadIdx.x; c < k; c += blockDim.x) {
         S[c] = Sp[c];
@@ -546,14 +555,16 @@ __device__ __forceinline__ void decide_body(Scalars *sc, const double *partials,
             sc->status = IHT_ENOTCONV;
             sc->done = 1;
         }
+        sc->skip1 = 1;                         // accepted: no further attempt
+        sc->skip2 = sc->done;                  // the next gradient unless stopped
     }
 }
 
 __global__ void __launch_bounds__(256) k_decide(Scalars *sc, const double *partials, int npart,
                                                 int32_t *S, double *bS, const int32_t *Sp,
-                                                const double *bSp, TraceDev tr)
+                                                const double *bSp, TraceDev tr, const int32_t *skip)
 {
-    if (sc->done) return;
+    if (sc->done || (skip && *skip)) return;
     decide_body(sc, partials, npart, S, bS, Sp, bSp, tr);
 }
 
@@ -606,7 +617,16 @@ __global__ void k_check_finite(const double *__restrict__ y, int64_t n, Scalars 
 // ---------------------------------------------------------------------------
 // Host orchestration of one solve.
 
-int launch_merge(iht_dataset *ds, int K, int first)
+static void configure_merge(iht_dataset *ds)
+{
+    static thread_local int configured_dev = -1;
+    if (configured_dev != ds->ctx->device) {
+        cudaFuncSetAttribute(k_merge, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(MergeShared));
+        configured_dev = ds->ctx->device;
+    }
+}
+
+int launch_merge(iht_dataset *ds, int K, int first, const int32_t *skip = nullptr)
 {
     static thread_local int configured_dev = -1;
     const int smem = (int)sizeof(MergeShared);
@@ -624,6 +644,7 @@ int launch_merge(iht_dataset *ds, int K, int first)
     A.partials = ws->partials;
     A.npart = zmul_blocks(ds);
     A.first = first;
+    A.skip = skip;
     A.Sp = ws->Sp;
     A.bSp = ws->bSp;
     A.sc = ws->sc;
@@ -633,21 +654,130 @@ int launch_merge(iht_dataset *ds, int K, int first)
     return IHT_OK;
 }
 
-int launch_grad(iht_dataset *ds, int impl, const int32_t *done, bool profile)
+// The gradient pass; e0/e1 (optional) are recorded around its main kernel.
+static int launch_grad_ev(iht_dataset *ds, int impl, const int32_t *done, cudaEvent_t e0, cudaEvent_t e1)
 {
     Workspace *ws = ds->ws;
     cudaStream_t s = ds->ctx->stream;
-    const bool rec = profile && ws->nprof < kProfEvents;
     const bool tc = impl == 2 || (impl == 0 && grad_tc_supported(ds));
     int rc;
     if (tc && (rc = prepare_grad_tc(ds, ws->r32, done))) return rc;
-    if (rec) IHT_CUDA(cudaEventRecord(ws->prof_ev[2 * ws->nprof], s));
+    // inside a stream capture the records must be external to become event nodes of the graph
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (e0 || e1) IHT_CUDA(cudaStreamIsCapturing(s, &cap));
+    const unsigned flags = cap == cudaStreamCaptureStatusActive ? cudaEventRecordExternal : cudaEventRecordDefault;
+    if (e0) IHT_CUDA(cudaEventRecordWithFlags(e0, s, flags));
     rc = tc ? launch_grad_tc_main(ds, ws->r32, ws->g, done) : launch_grad_simt(ds, ws->r32, ws->g, done);
     if (rc) return rc;
-    if (rec) {
-        IHT_CUDA(cudaEventRecord(ws->prof_ev[2 * ws->nprof + 1], s));
-        ++ws->nprof;
+    if (e1) IHT_CUDA(cudaEventRecordWithFlags(e1, s, flags));
+    return IHT_OK;
+}
+
+int launch_grad(iht_dataset *ds, int impl, const int32_t *done, bool profile)
+{
+    Workspace *ws = ds->ws;
+    const bool rec = profile && ws->nprof < kProfEvents;
+    const int rc = launch_grad_ev(ds, impl, done, rec ? ws->prof_ev[2 * ws->nprof] : nullptr,
+                                  rec ? ws->prof_ev[2 * ws->nprof + 1] : nullptr);
+    if (rc) return rc;
+    if (rec) ++ws->nprof;
+    return IHT_OK;
+}
+
+// One backtracking attempt: projection, candidate residual, decision, centring.
+// skip (not null): every kernel returns at once when *skip (an attempt
+// enqueued before it was known to be needed).
+static int enqueue_attempt(iht_dataset *ds, int k, int K, int first, const int32_t *skip,
+                           const TraceDev &tr)
+{
+    Workspace *ws = ds->ws;
+    cudaStream_t s = ds->ctx->stream;
+    int rc;
+    if ((rc = launch_merge(ds, K, first, skip))) return rc;
+    if ((rc = zmul_run(ds, ws->Sp, k, ws->bSp, -1.0, ws->u64, ws->v64, ws->used, ws->y64, ws->rc64,
+                       ws->partials, skip ? skip : &ws->sc->done, ws->r64)))
+        return rc;
+    k_decide<<<1, 256, 0, s>>>(ws->sc, ws->partials, zmul_blocks(ds), ws->S, ws->bS, ws->Sp, ws->bSp, tr,
+                               skip);
+    k_center<<<ceil_div(ds->n_pad, 256), 256, 0, s>>>(ws->rc64, ws->r64, ws->used, ds->n_pad, ws->sc,
+                                                      ws->r32);
+    note_launch(2);
+    IHT_CUDA(cudaGetLastError());
+    return IHT_OK;
+}
+
+// One iteration from the current gradient: candidates, step size, two
+// attempts (the second returns at once unless the first was rejected), and the
+// next gradient (returns at once if the solve stopped or the second attempt
+// was rejected too).
+static int enqueue_iteration(iht_dataset *ds, int k, int K, int impl, cudaEvent_t e0, cudaEvent_t e1)
+{
+    Workspace *ws = ds->ws;
+    cudaStream_t s = ds->ctx->stream;
+    const int32_t *done = &ws->sc->done;
+    int rc;
+    if ((rc = select_topk(ds->ctx, ws->g, ds->p, K, ws->cand, done))) return rc;
+    k_gather_gS<<<1, 1024, 0, s>>>(ws->g, ws->S, k, ws->coef, ws->sc);
+    note_launch();
+    if ((rc = zmul_run(ds, ws->S, k, ws->coef, 1.0, ws->u64, ws->v64, ws->used, nullptr, ws->zv,
+                       ws->partials, done)))
+        return rc;
+    if ((rc = enqueue_attempt(ds, k, K, 1, nullptr, TraceDev{}))) return rc;
+    if ((rc = enqueue_attempt(ds, k, K, 0, &ws->sc->skip1, TraceDev{}))) return rc;
+    return launch_grad_ev(ds, impl, &ws->sc->skip2, e0, e1);
+}
+
+// The iteration as a CUDA graph (captured on a private stream: the caller's
+// stream may be the legacy default stream), cached in the workspace while the
+// key (sizes, gradient kernel, profiling, and every scratch address the
+// kernels were captured with) is unchanged.
+static int iteration_graph(iht_dataset *ds, int k, int K, int impl, bool prof, cudaGraphExec_t *exec)
+{
+    Workspace *ws = ds->ws;
+    const uint64_t key[8] = {(uint64_t)k, (uint64_t)K, (uint64_t)impl, (uint64_t)prof,
+                             (uint64_t)(uintptr_t)ws->S, (uint64_t)(uintptr_t)ws->cand,
+                             grad_tc_scratch_id(), (uint64_t)(uintptr_t)ds->ctx->sel.cand};
+    if (ws->iter_exec && std::equal(key, key + 8, ws->iter_key)) {
+        *exec = ws->iter_exec;
+        return IHT_OK;
     }
+    if (ws->iter_exec) {
+        cudaGraphExecDestroy(ws->iter_exec);
+        ws->iter_exec = nullptr;
+    }
+    if (!ws->cap_stream) IHT_CUDA(cudaStreamCreateWithFlags(&ws->cap_stream, cudaStreamNonBlocking));
+    if (prof && !ws->gev[0])
+        for (cudaEvent_t &e : ws->gev) IHT_CUDA(cudaEventCreate(&e));
+    configure_merge(ds);
+    cudaStream_t user = ds->ctx->stream;
+    ds->ctx->stream = ws->cap_stream;
+    const uint64_t before = launches_noted();
+    cudaError_t e = cudaStreamBeginCapture(ws->cap_stream, cudaStreamCaptureModeThreadLocal);
+    int rc = IHT_OK;
+    if (e == cudaSuccess)
+        rc = enqueue_iteration(ds, k, K, impl, prof ? ws->gev[0] : nullptr, prof ? ws->gev[1] : nullptr);
+    cudaGraph_t graph = nullptr;
+    const cudaError_t e2 = e == cudaSuccess ? cudaStreamEndCapture(ws->cap_stream, &graph) : e;
+    ds->ctx->stream = user;
+    const int n = (int)(launches_noted() - before);
+    note_launch(-n);                                   // captured, not run
+    if (rc == IHT_OK && e2 != cudaSuccess) {
+        set_cuda_error(e2, "iteration capture");
+        rc = IHT_ECUDA;
+    }
+    if (rc == IHT_OK) {
+        e = cudaGraphInstantiate(&ws->iter_exec, graph, 0);
+        if (e != cudaSuccess) {
+            set_cuda_error(e, "iteration graph instantiate");
+            ws->iter_exec = nullptr;
+            rc = IHT_ECUDA;
+        }
+    }
+    if (graph) cudaGraphDestroy(graph);
+    if (rc) return rc;
+    std::copy(key, key + 8, ws->iter_key);
+    ws->iter_launches = n;
+    *exec = ws->iter_exec;
     return IHT_OK;
 }
 
@@ -696,7 +826,41 @@ int run_solve(iht_dataset *ds, int k, const iht_options *opt, int n_rows, const 
     if ((rc = select_topk(ds->ctx, ws->g, ds->p, k, ws->S, done))) return rc;
     IHT_CUDA(cudaMemsetAsync(ws->bS, 0, sizeof(double) * k, s));
 
-    for (int it = 0; it < opt->max_iter; ++it) {
+    const bool traced = tr.objective || tr.mu || tr.backtracks || tr.changed || tr.supp || tr.beta;
+    double graph_ms = 0.0;
+    int graph_n = 0;
+    if (!traced) {
+        // one graph replay and one host synchronisation per iteration
+        cudaGraphExec_t exec = nullptr;
+        if ((rc = iteration_graph(ds, k, K, opt->grad_impl, prof, &exec))) return rc;
+        for (int it = 0; it < opt->max_iter; ++it) {
+            IHT_CUDA(cudaGraphLaunch(exec, s));
+            note_launch(ws->iter_launches);
+            IHT_CUDA(cudaMemcpyAsync(&ws->sc_host->done, &ws->sc->done, 2 * sizeof(int32_t),
+                                     cudaMemcpyDeviceToHost, s));
+            IHT_CUDA(cudaStreamSynchronize(s));
+            int32_t dn = ws->sc_host->done, rt = ws->sc_host->retry;
+            if (!dn && rt) {
+                // rejected twice: further attempts one at a time, then the next gradient
+                while (!dn && rt) {
+                    if ((rc = enqueue_attempt(ds, k, K, 0, nullptr, tr))) return rc;
+                    IHT_CUDA(cudaMemcpyAsync(&ws->sc_host->done, &ws->sc->done, 2 * sizeof(int32_t),
+                                             cudaMemcpyDeviceToHost, s));
+                    IHT_CUDA(cudaStreamSynchronize(s));
+                    dn = ws->sc_host->done;
+                    rt = ws->sc_host->retry;
+                }
+                if (!dn && (rc = launch_grad(ds, opt->grad_impl, done, prof))) return rc;
+            } else if (prof && !dn) {
+                float ms = 0.0f;                       // the graph's gradient pass ran
+                IHT_CUDA(cudaEventElapsedTime(&ms, ws->gev[0], ws->gev[1]));
+                graph_ms += ms;
+                ++graph_n;
+            }
+            if (dn) break;
+        }
+    }
+    for (int it = 0; traced && it < opt->max_iter; ++it) {
         if (it > 0 && (rc = launch_grad(ds, opt->grad_impl, done, prof))) return rc;
         if ((rc = select_topk(ds->ctx, ws->g, ds->p, K, ws->cand, done))) return rc;
         k_gather_gS<<<1, 1024, 0, s>>>(ws->g, ws->S, k, ws->coef, ws->sc);
@@ -705,15 +869,7 @@ int run_solve(iht_dataset *ds, int k, const iht_options *opt, int n_rows, const 
                            ws->partials, done)))
             return rc;
         for (int attempt = 0;; ++attempt) {
-            if ((rc = launch_merge(ds, K, attempt == 0))) return rc;
-            if ((rc = zmul_run(ds, ws->Sp, k, ws->bSp, -1.0, ws->u64, ws->v64, ws->used, ws->y64,
-                               ws->rc64, ws->partials, done, ws->r64)))
-                return rc;
-            k_decide<<<1, 256, 0, s>>>(ws->sc, ws->partials, npart, ws->S, ws->bS, ws->Sp, ws->bSp, tr);
-            k_center<<<ceil_div(ds->n_pad, 256), 256, 0, s>>>(ws->rc64, ws->r64, ws->used, ds->n_pad,
-                                                              ws->sc, ws->r32);
-            note_launch(2);
-            IHT_CUDA(cudaGetLastError());
+            if ((rc = enqueue_attempt(ds, k, K, attempt == 0, nullptr, tr))) return rc;
             IHT_CUDA(cudaMemcpyAsync(&ws->sc_host->done, &ws->sc->done, 2 * sizeof(int32_t),
                                      cudaMemcpyDeviceToHost, s));
             IHT_CUDA(cudaStreamSynchronize(s));
@@ -723,12 +879,13 @@ int run_solve(iht_dataset *ds, int k, const iht_options *opt, int n_rows, const 
     }
     IHT_CUDA(cudaMemcpyAsync(ws->sc_host, ws->sc, sizeof(Scalars), cudaMemcpyDeviceToHost, s));
     IHT_CUDA(cudaStreamSynchronize(s));
-    ws->prof_ms = 0.0;
+    ws->prof_ms = graph_ms;
     for (int e = 0; prof && e < ws->nprof; ++e) {
         float ms = 0.0f;
         IHT_CUDA(cudaEventElapsedTime(&ms, ws->prof_ev[2 * e], ws->prof_ev[2 * e + 1]));
         ws->prof_ms += ms;
     }
+    ws->nprof += graph_n;
     return IHT_OK;
 }
 
@@ -906,6 +1063,7 @@ __global__ void __launch_bounds__(kMergeThreads) k_merge_b(const BSolve *bs, int
     A.partials = B.partials;
     A.npart = npart;
     A.first = first;
+    A.skip = nullptr;
     A.Sp = B.Sp;
     A.bSp = B.bSp;
     A.sc = sc;
