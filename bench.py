@@ -71,6 +71,30 @@ def dist_env():
     return int(os.environ.get("RANK", "0")), int(os.environ.get("LOCAL_RANK", "0")), ws
 
 
+def gather_rows(vals, world):
+    """Every rank's row of per-rank figures, stacked [world, len] in rank order.
+
+    With world > 1 this is an all-gather over the initialised process group
+    (NCCL on the GPUs, gloo on the host); every rank gets the same array.
+    """
+    row = np.asarray(vals, dtype=np.float64)
+    if world <= 1:
+        return row[None, :]
+    import torch
+    import torch.distributed as dist
+    dev = (torch.device("cuda", torch.cuda.current_device()) if dist.get_backend() == "nccl"
+           else torch.device("cpu"))
+    t = torch.tensor(row, device=dev)
+    out = [torch.zeros_like(t) for _ in range(world)]
+    dist.all_gather(out, t)
+    return torch.stack(out).cpu().numpy()
+
+
+def weak_rate(rows, units, seconds):
+    """Whole-job throughput of replicas: units summed over ranks / the slowest rank's time."""
+    return float(rows[:, units].sum()) / float(rows[:, seconds].max())
+
+
 def measured_peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -204,7 +228,7 @@ def ours_arm(args):
     t0 = time.perf_counter()
     pn = synth.config_panel(cfg)
     bed = pn.bed()
-    y, causal, _ = synth.config_phenotype(cfg, pn)
+    y, causal, _ = synth.config_phenotype(cfg, pn, which=rank)    # replicas: own phenotype
     log(f"[bench] rank {rank}: generated {bed.nbytes / 1e6:.0f} MB panel in "
         f"{time.perf_counter() - t0:.1f}s")
 
@@ -265,19 +289,11 @@ def ours_arm(args):
     beta_host, supp_host = r.beta, r.support
 
     # ---- aggregate over ranks --------------------------------------------------
-    vals = torch.tensor([its, elapsed, e2e_its, e2e_wall, grad_ms, grad_n], dtype=torch.float64,
-                        device=f"cuda:{dev}")
-    if world > 1:
-        gathered = [torch.zeros_like(vals) for _ in range(world)]
-        torch.distributed.all_gather(gathered, vals)
-        allv = torch.stack(gathered).cpu().numpy()
-    else:
-        allv = vals.cpu().numpy()[None, :]
+    allv = gather_rows([its, elapsed, e2e_its, e2e_wall, grad_ms, grad_n], world)
     if rank == 0:
-        tot_its = float(allv[:, 0].sum())
         max_el = float(allv[:, 1].max())
-        value = tot_its / max_el
-        e2e_value = float(allv[:, 2].sum()) / float(allv[:, 3].max())
+        value = weak_rate(allv, 0, 1)
+        e2e_value = weak_rate(allv, 2, 3)
         hbm_peak, peak_kind = measured_peaks()
         alg_bytes = p * ((n + 3) // 4) + 12 * p + 4 * n      # packed genotypes + u, v, g + r
         per_launch_ms = grad_ms / max(grad_n, 1)
@@ -333,12 +349,13 @@ def measured_tensor_peak():
         return FP8_OVER_BF16 * FALLBACK_TFLOPS, "fallback bf16 sustained x 2"
 
 
-def cv_setup(cfg):
+def cv_setup(cfg, rank=0):
+    """The panel, a phenotype and the folds; replicas (rank > 0) draw their own phenotype and folds."""
     c = synth.CONFIGS[cfg]
     pn = synth.config_panel(cfg)
     bed = pn.bed()
-    y, _, _ = synth.config_phenotype(cfg, pn)
-    lab = synth.cv_folds(pn.n, c["folds"], synth.BASE_SEED + 1000 * cfg + 7)
+    y, _, _ = synth.config_phenotype(cfg, pn, which=rank)
+    lab = synth.cv_folds(pn.n, c["folds"], synth.BASE_SEED + 1000 * cfg + 7 + 101 * rank)
     train = [np.flatnonzero(lab != f).astype(np.int32) for f in range(c["folds"])]
     return c, pn, bed, y, train
 
@@ -396,7 +413,7 @@ def cv_arm(args):
     torch.cuda.set_device(local_rank)
     dev = local_rank
     t0 = time.perf_counter()
-    c, pn, bed, y, train = cv_setup(3)
+    c, pn, bed, y, train = cv_setup(3, rank)
     n, p = c["n"], c["p"]
     log(f"[bench] rank {rank}: generated {bed.nbytes / 1e6:.0f} MB panel in "
         f"{time.perf_counter() - t0:.1f}s")
@@ -468,17 +485,10 @@ def cv_arm(args):
     torch.cuda.synchronize(dev)
     e2e_wall = time.perf_counter() - w0
 
-    vals = torch.tensor([solves, elapsed, args.steps * b, e2e_wall], dtype=torch.float64,
-                        device=cuda)
-    if world > 1:
-        gathered = [torch.zeros_like(vals) for _ in range(world)]
-        torch.distributed.all_gather(gathered, vals)
-        allv = torch.stack(gathered).cpu().numpy()
-    else:
-        allv = vals.cpu().numpy()[None, :]
+    allv = gather_rows([solves, elapsed, args.steps * b, e2e_wall], world)
     if rank == 0:
-        value = float(allv[:, 0].sum()) / float(allv[:, 1].max())
-        e2e_value = float(allv[:, 2].sum()) / float(allv[:, 3].max())
+        value = weak_rate(allv, 0, 1)
+        e2e_value = weak_rate(allv, 2, 3)
         peak, peak_kind = measured_tensor_peak()
         n_k = 4 * ((((n + 3) // 4) + 15) // 16) * 16     # samples of the contraction (K-steps x 16)
         flops = 2.0 * n * p * MR_LIMBS * cols              # X0^T [limbs of r] over all passes
@@ -527,12 +537,13 @@ def cv_arm(args):
     return 0
 
 
-def serve_setup(args):
+def serve_setup(args, rank=0):
+    """The panel and the request stream (replicas draw their own requests)."""
     cfg = 4
     c = synth.CONFIGS[cfg]
     pn = synth.config_panel(cfg)
     bed = pn.bed()
-    reqs = synth.serving_requests(pn, args.requests, synth.BASE_SEED + 1000 * cfg + 11,
+    reqs = synth.serving_requests(pn, args.requests, synth.BASE_SEED + 1000 * cfg + 11 + 101 * rank,
                                   workers=min(16, os.cpu_count() or 1))
     return c, pn, bed, reqs
 
@@ -613,7 +624,7 @@ def serve_arm(args):
 
     rank, local_rank, world = dist_env()
     t0 = time.perf_counter()
-    c, pn, bed, reqs = serve_setup(args)          # before any CUDA work (spawned workers)
+    c, pn, bed, reqs = serve_setup(args, rank)    # before any CUDA work (spawned workers)
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device(f"cuda:{local_rank}"))
@@ -642,6 +653,8 @@ def serve_arm(args):
     clocks = ClockSampler(gpu_uuid(torch, dev))
     clocks.start()
     time.sleep(0.3)
+    if world > 1:
+        torch.distributed.barrier()
     l0 = iht.iht_kernel_launches()
     cap_walls, lat_all, iters = [], [], []
     for _ in range(args.steps):
@@ -649,10 +662,12 @@ def serve_arm(args):
         cap_walls.append(wall)
         lat_all.append(lat)
         iters += [r.iterations for r in out]
+    if world > 1:
+        torch.distributed.barrier()
     launches = iht.iht_kernel_launches() - l0
     clk = clocks.stop()
     st = srv.stats()
-    value = len(reqs) * args.steps / sum(cap_walls)
+    value = weak_rate(gather_rows([len(reqs) * args.steps, sum(cap_walls)], world), 0, 1)
     rng = np.random.Generator(np.random.PCG64(synth.BASE_SEED + 4099))
     poisson = {}
     for mult in (0.5, 1.2):
