@@ -186,9 +186,11 @@ def reference_arm(args):
     pn = synth.config_panel(cfg)
     bed = pn.bed()
     y, _, _ = synth.config_phenotype(cfg, pn)
-    cap = args.oracle_iters
+    # iterations per step: the bounded sample shrinks with the step count so any
+    # --steps finishes in about a minute of host time
+    cap = max(1, min(args.oracle_iters, 50 // max(args.steps, 1)))
     for _ in range(args.warmup):
-        run_oracle_sample(cfg, cap, pn, bed, y)
+        run_oracle_sample(cfg, 1, pn, bed, y)         # the oracle has no warm state
     its, secs = 0, 0.0
     threads = 1
     for _ in range(args.steps):
@@ -721,7 +723,8 @@ def serve_arm(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--steps", type=int, default=None,
+                    help="timed steps (default: 50 single solves, 3 CV batches, 1 serving pass)")
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--config", type=int, default=2, choices=[1, 2, 3, 4])
@@ -734,6 +737,8 @@ def main():
     ap.add_argument("--oracle-iters", type=int, default=10)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
+    if args.steps is None:
+        args.steps = {3: 3, 4: 1}.get(args.config, 50)
     if args.config == 3:
         return cv_reference_arm(args) if args.impl == "reference" else cv_arm(args)
     if args.config == 4:
