@@ -328,6 +328,16 @@ def ours_arm(args):
                 "value": iters / secs, "unit": "iter/s", "cores": threads, "kind": "oracle",
                 "sample": f"FP64 oracle IHT on {c['name']}, first {iters} iterations "
                           f"(incl. setup), {secs:.1f}s"}
+            # the same oracle on one host thread (its column-parallel loops serial)
+            import oracle
+            oracle.set_threads(1)
+            try:
+                i1, s1, _ = run_oracle_sample(cfg, 1, pn, bed, y)
+            finally:
+                oracle.set_threads(threads)
+            out["cpu_baseline"]["single_thread"] = {
+                "value": i1 / s1, "unit": "iter/s", "cores": 1,
+                "sample": f"first {i1} iteration (incl. setup), {s1:.1f}s"}
         print(json.dumps(out), flush=True)
     del ds, ctx
     if world > 1:

@@ -201,6 +201,44 @@ int iht_fit_trace(iht_dataset *ds, const int32_t *rows, int64_t n_rows, const do
                   int32_t k, const iht_options *opt, double *beta_out, int32_t *support_out,
                   iht_result *info, iht_trace *trace);
 
+/* Checkpoint / resume.  Between iterations the method carries only the support
+ * S, beta on S and its counters (Sec. 2.2: the residual, the gradient and the
+ * step size are recomputed from them), so a solve stopped after m iterations
+ * (max_iter = m, status ENOTCONV) and resumed from its state takes exactly the
+ * iterations the uninterrupted solve takes: same supports, same beta bit for
+ * bit, same count.
+ *
+ * The state image is a host byte string, little-endian: "IHTSTATE", version 1
+ * (uint32), header size 80 (uint32), n, p, n_rows (int64), k, iterations,
+ * backtracks, status (int32), objective, mu (double), an FNV-1a 64-bit
+ * checksum of the image taken with this field zero (uint64), then support[k]
+ * (int32, strictly ascending in [0, p)) and beta_s[k] (double, finite).
+ * No device work and no CUDA device needed for these three:
+ *   iht_state_bytes: image size for k (1 <= k <= 1024).
+ *   iht_state_save : image of a solve's outputs -- host support_out, beta_out
+ *                    on the support and info of iht_fit -- fitted on n_rows of a
+ *                    dataset of shape (n, p) into buf.  EINVAL when buf_bytes is
+ *                    too small or the support / values are not as above.
+ *   iht_state_load : parses an image.  With support, beta_s and info all NULL
+ *                    only the shape (n, p, n_rows, k) is returned; otherwise
+ *                    support and beta_s receive k entries (k <= k_cap) and info
+ *                    (optional) the counters.  EINVAL when the magic, version,
+ *                    size or checksum is wrong, or the contents are invalid.
+ * iht_fit_resume: iht_fit that starts from the image (state, state_bytes,
+ * host memory) instead of beta = 0.  k is the image's; the image's n and p must
+ * be the dataset's and its n_rows the rows given (EINVAL otherwise).  The
+ * iteration count continues from the image's, so opt->max_iter caps the total
+ * and info->iterations / backtracks are totals. */
+int iht_state_bytes(int32_t k, size_t *bytes);
+int iht_state_save(int64_t n, int64_t p, int64_t n_rows, int32_t k, const int32_t *support,
+                   const double *beta_s, const iht_result *info, void *buf, size_t buf_bytes);
+int iht_state_load(const void *buf, size_t buf_bytes, int32_t k_cap, int64_t *n, int64_t *p,
+                   int64_t *n_rows, int32_t *k, int32_t *support, double *beta_s,
+                   iht_result *info);
+int iht_fit_resume(iht_dataset *ds, const int32_t *rows, int64_t n_rows, const double *y,
+                   const void *state, size_t state_bytes, const iht_options *opt,
+                   double *beta_out, int32_t *support_out, iht_result *info);
+
 /* One solve of a batch: its row set (a CV training fold, a phenotype's
  * non-missing subjects, a serving request's subset), phenotype and k. */
 typedef struct iht_solve_desc {

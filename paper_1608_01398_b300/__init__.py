@@ -27,7 +27,8 @@ EXPORTED = ["iht_default_options", "iht_strerror", "iht_last_cuda_error", "iht_k
             "iht_gradient", "iht_topk", "iht_topk_noalloc", "iht_zmul", "iht_fit",
             "iht_fit_trace", "iht_fit_batch", "iht_gradient_batch", "iht_server_default_options",
             "iht_server_create", "iht_server_submit", "iht_server_poll", "iht_server_get_stats",
-            "iht_server_destroy"]
+            "iht_server_destroy", "iht_state_bytes", "iht_state_save", "iht_state_load",
+            "iht_fit_resume"]
 
 
 class IhtError(RuntimeError):
@@ -131,6 +132,14 @@ def _lib(build_if_stale: bool = True):
                                            ctypes.POINTER(ctypes.c_double)]),
         "iht_server_get_stats": (ctypes.c_int, [P, ctypes.POINTER(iht_server_stats)]),
         "iht_server_destroy": (ctypes.c_int, [P]),
+        "iht_state_bytes": (ctypes.c_int, [i32, ctypes.POINTER(sz)]),
+        "iht_state_save": (ctypes.c_int, [i64, i64, i64, i32, P, P, ctypes.POINTER(iht_result), P,
+                                          sz]),
+        "iht_state_load": (ctypes.c_int, [P, sz, i32, ctypes.POINTER(i64), ctypes.POINTER(i64),
+                                          ctypes.POINTER(i64), ctypes.POINTER(i32), P, P,
+                                          ctypes.POINTER(iht_result)]),
+        "iht_fit_resume": (ctypes.c_int, [P, P, i64, P, P, sz, ctypes.POINTER(iht_options), P, P,
+                                          ctypes.POINTER(iht_result)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -315,7 +324,7 @@ class FitResult:
     beta_s: object = None
 
 
-def _fit(ds: Dataset, y, k: int, rows, opts: iht_options, trace: bool):
+def _fit(ds: Dataset, y, k: int, rows, opts: iht_options, trace: bool, state: bytes = None):
     torch = _torch()
     dev_in = isinstance(y, torch.Tensor)
     if dev_in:
@@ -342,7 +351,12 @@ def _fit(ds: Dataset, y, k: int, rows, opts: iht_options, trace: bool):
         bp, sp = beta.ctypes.data, supp.ctypes.data
     res = iht_result()
     tr = None
-    if trace:
+    if state is not None:
+        buf = ctypes.create_string_buffer(bytes(state), len(state))
+        rc = _lib().iht_fit_resume(ds.h, None if rp is None else ctypes.c_void_p(rp), nr,
+                                   ctypes.c_void_p(yp), buf, len(state), ctypes.byref(opts),
+                                   ctypes.c_void_p(bp), ctypes.c_void_p(sp), ctypes.byref(res))
+    elif trace:
         T = max(opts.max_iter, 1)
         tr = dict(objective=np.full(T, np.nan), mu=np.full(T, np.nan),
                   backtracks=np.zeros(T, np.int32), changed=np.zeros(T, np.int32),
@@ -369,6 +383,71 @@ def iht_fit(ds: Dataset, y, k: int, rows=None, **opt) -> FitResult:
     o = iht_default_options(**opt)
     o.out_mem = IHT_DEVICE if out_device else IHT_HOST
     return _fit(ds, y, k, rows, o, trace=False)
+
+
+@dataclass
+class SolveState:
+    """A parsed solve-state image (see save_state / iht_fit_resume)."""
+    n: int
+    p: int
+    n_rows: int
+    k: int
+    support: np.ndarray
+    beta_s: np.ndarray
+    iterations: int
+    backtracks: int
+    status: int
+    objective: float
+    mu: float
+
+
+def save_state(shape, n_rows: int, fit: FitResult) -> bytes:
+    """Checkpoint image of a stopped solve (iht_state_save; no device work).
+
+    shape: (n, p) of the dataset (or the Dataset); n_rows: rows the solve used.
+    """
+    n, p = (shape.n, shape.p) if isinstance(shape, Dataset) else shape
+
+    def host(a):                                   # device tensors come back; no device needed
+        return a.cpu().numpy() if hasattr(a, "cpu") else np.asarray(a)
+
+    supp = np.ascontiguousarray(host(fit.support), dtype=np.int32)
+    bs = host(fit.beta_s) if fit.beta_s is not None else host(fit.beta)[supp]
+    bs = np.ascontiguousarray(bs, dtype=np.float64)
+    k = supp.size
+    nbytes = ctypes.c_size_t()
+    _check(_lib().iht_state_bytes(k, ctypes.byref(nbytes)), "iht_state_bytes")
+    info = iht_result(iterations=fit.iterations, status=fit.status, backtracks=fit.backtracks,
+                      objective=fit.objective, mu=fit.mu)
+    buf = ctypes.create_string_buffer(nbytes.value)
+    _check(_lib().iht_state_save(n, p, n_rows, k, supp.ctypes.data, bs.ctypes.data,
+                                 ctypes.byref(info), buf, nbytes.value), "iht_state_save")
+    return buf.raw
+
+
+def load_state(image: bytes) -> SolveState:
+    """Parse a solve-state image (iht_state_load; raises IhtError when it is malformed)."""
+    L = _lib()
+    buf = ctypes.create_string_buffer(bytes(image), len(image))
+    n, p, nr, k = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int32()
+    _check(L.iht_state_load(buf, len(image), 0, ctypes.byref(n), ctypes.byref(p), ctypes.byref(nr),
+                            ctypes.byref(k), None, None, None), "iht_state_load")
+    supp = np.empty(k.value, np.int32)
+    bs = np.empty(k.value)
+    info = iht_result()
+    _check(L.iht_state_load(buf, len(image), k.value, ctypes.byref(n), ctypes.byref(p),
+                            ctypes.byref(nr), ctypes.byref(k), supp.ctypes.data, bs.ctypes.data,
+                            ctypes.byref(info)), "iht_state_load")
+    return SolveState(n.value, p.value, nr.value, k.value, supp, bs, info.iterations,
+                      info.backtracks, info.status, info.objective, info.mu)
+
+
+def iht_fit_resume(ds: Dataset, y, state: bytes, rows=None, **opt) -> FitResult:
+    """iht_fit continued from a checkpoint image; max_iter caps the total iterations."""
+    out_device = opt.pop("out_device", False)
+    o = iht_default_options(**opt)
+    o.out_mem = IHT_DEVICE if out_device else IHT_HOST
+    return _fit(ds, y, load_state(state).k, rows, o, trace=False, state=state)
 
 
 def iht_fit_trace(ds: Dataset, y, k: int, rows=None, **opt) -> FitResult:

@@ -6,6 +6,7 @@
 
 #include <atomic>
 #include <new>
+#include <vector>
 
 #include "common.cuh"
 
@@ -393,7 +394,7 @@ int iht_zmul(iht_dataset *ds, const int32_t *rows, int64_t n_rows, const double 
 
 static int fit_impl(iht_dataset *ds, const int32_t *rows, int64_t n_rows, const double *y,
                     int32_t k, const iht_options *opt_in, double *beta_out, int32_t *support_out,
-                    iht_result *info, iht_trace *trace)
+                    iht_result *info, iht_trace *trace, const SolveInit *init = nullptr)
 {
     iht_options opt;
     if (opt_in)
@@ -423,7 +424,7 @@ static int fit_impl(iht_dataset *ds, const int32_t *rows, int64_t n_rows, const 
     }
     if ((rc = check_finite_y(ds, n_rows, y_dev))) return rc;
     if ((rc = scatter_rows_f64(ds, rows_dev, n_rows, y_dev, ws->y64))) return rc;
-    rc = run_solve_host(ds, k, &opt, (int)n_rows, trace, opt.max_iter);
+    rc = run_solve_host(ds, k, &opt, (int)n_rows, trace, opt.max_iter, init);
     if (rc) return rc;
     const Scalars &h = *ws->sc_host;
     if (opt.out_mem == IHT_DEVICE) {
@@ -472,6 +473,27 @@ int iht_fit_trace(iht_dataset *ds, const int32_t *rows, int64_t n_rows, const do
                   iht_result *info, iht_trace *trace)
 {
     return fit_impl(ds, rows, n_rows, y, k, opt, beta_out, support_out, info, trace);
+}
+
+int iht_fit_resume(iht_dataset *ds, const int32_t *rows, int64_t n_rows, const double *y,
+                   const void *state, size_t state_bytes, const iht_options *opt,
+                   double *beta_out, int32_t *support_out, iht_result *info)
+{
+    if (!ds || !state) return IHT_EINVAL;
+    int64_t n = 0, p = 0, nr = 0;
+    int32_t k = 0;
+    int rc = iht_state_load(state, state_bytes, kMaxK, &n, &p, &nr, &k, nullptr, nullptr, nullptr);
+    if (rc) return rc;
+    if (!rows) n_rows = ds->n;
+    if (n != ds->n || p != ds->p || nr != n_rows) return IHT_EINVAL;
+    std::vector<int32_t> S((size_t)k);
+    std::vector<double> b((size_t)k);
+    iht_result st{};
+    if ((rc = iht_state_load(state, state_bytes, kMaxK, &n, &p, &nr, &k, S.data(), b.data(), &st)))
+        return rc;
+    SolveInit init{S.data(), b.data(), st.iterations, st.backtracks};
+    if (init.iter < 0 || init.backtracks < 0) return IHT_EINVAL;
+    return fit_impl(ds, rows, n_rows, y, k, opt, beta_out, support_out, info, nullptr, &init);
 }
 
 }  // extern "C"

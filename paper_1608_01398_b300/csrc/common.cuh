@@ -281,8 +281,13 @@ int gather_rows_f64(iht_dataset *ds, const int32_t *rows_dev, int64_t n_rows, co
                     double *dst);
 int check_finite_y(iht_dataset *ds, int64_t n_rows, const double *y_dev);
 int check_finite_y_sc(iht_dataset *ds, int64_t n_rows, const double *y_dev, Scalars *sc);
+struct SolveInit {                     // resume a solve from its state (host arrays)
+    const int32_t *S;                  // k, strictly ascending
+    const double *bS;                  // beta on S
+    int32_t iter, backtracks;          // counters so far
+};
 int run_solve_host(iht_dataset *ds, int k, const iht_options *opt, int n_rows, iht_trace *trace,
-                   int max_iter);
+                   int max_iter, const SolveInit *init = nullptr);
 int write_beta_device(iht_dataset *ds, int k, double *beta_out);
 // batched tails (blockIdx selects the solve; finished solves return at once)
 enum ZmulWhich { kZmulInit = 0, kZmulStep = 1, kZmulResidual = 2 };

@@ -782,7 +782,8 @@ static int iteration_graph(iht_dataset *ds, int k, int K, int impl, bool prof, c
 }
 
 // y64 and the row set are in place; runs the solve, leaves S/bS and scalars.
-int run_solve(iht_dataset *ds, int k, const iht_options *opt, int n_rows, const TraceDev &tr)
+int run_solve(iht_dataset *ds, int k, const iht_options *opt, int n_rows, const TraceDev &tr,
+              const SolveInit *init)
 {
     Workspace *ws = ds->ws;
     cudaStream_t s = ds->ctx->stream;
@@ -799,7 +800,9 @@ int run_solve(iht_dataset *ds, int k, const iht_options *opt, int n_rows, const 
     h.k = k;
     h.n_rows = n_rows;
     h.status = IHT_ENOTCONV;
-    h.done = opt->max_iter <= 0 ? 1 : 0;
+    h.iter = init ? init->iter : 0;
+    h.bt_total = init ? init->backtracks : 0;
+    h.done = opt->max_iter <= h.iter ? 1 : 0;
     IHT_CUDA(cudaMemcpyAsync(ws->sc_host, ws->sc, sizeof(Scalars), cudaMemcpyDeviceToHost, s));
     IHT_CUDA(cudaStreamSynchronize(s));
     h.err = ws->sc_host->err;        // row / input flags from the set-up kernels
@@ -807,9 +810,17 @@ int run_solve(iht_dataset *ds, int k, const iht_options *opt, int n_rows, const 
     *ws->sc_host = h;
     IHT_CUDA(cudaMemcpyAsync(ws->sc, ws->sc_host, sizeof(Scalars), cudaMemcpyHostToDevice, s));
 
-    // beta = 0: r = y, objective, centred residual, g^0, S^0 = top-k |g^0|
-    if ((rc = zmul_run(ds, ws->cols, 0, ws->coef, -1.0, ws->u64, ws->v64, ws->used, ws->y64,
-                       ws->r64, ws->partials, nullptr)))
+    // beta = 0: r = y, objective, centred residual, g^0, S^0 = top-k |g^0|.  A
+    // resumed solve starts from its S and beta_S instead: r = y - Z_S beta_S by the
+    // same product the accepted step of the interrupted solve used.
+    if (init) {
+        IHT_CUDA(cudaMemcpyAsync(ws->S, init->S, sizeof(int32_t) * k, cudaMemcpyHostToDevice, s));
+        IHT_CUDA(cudaMemcpyAsync(ws->bS, init->bS, sizeof(double) * k, cudaMemcpyHostToDevice, s));
+    }
+    if ((rc = init ? zmul_run(ds, ws->S, k, ws->bS, -1.0, ws->u64, ws->v64, ws->used, ws->y64,
+                              ws->r64, ws->partials, nullptr)
+                   : zmul_run(ds, ws->cols, 0, ws->coef, -1.0, ws->u64, ws->v64, ws->used, ws->y64,
+                              ws->r64, ws->partials, nullptr)))
         return rc;
     k_init_objective<<<1, 32, 0, s>>>(ws->sc, ws->partials, npart);
     k_center<<<ceil_div(ds->n_pad, 256), 256, 0, s>>>(ws->r64, ws->r64, ws->used, ds->n_pad, ws->sc,
@@ -823,8 +834,10 @@ int run_solve(iht_dataset *ds, int k, const iht_options *opt, int n_rows, const 
         for (int e = 0; e < 2 * kProfEvents; ++e) IHT_CUDA(cudaEventCreate(&ws->prof_ev[e]));
     }
     if ((rc = launch_grad(ds, opt->grad_impl, done, prof))) return rc;
-    if ((rc = select_topk(ds->ctx, ws->g, ds->p, k, ws->S, done))) return rc;
-    IHT_CUDA(cudaMemsetAsync(ws->bS, 0, sizeof(double) * k, s));
+    if (!init) {
+        if ((rc = select_topk(ds->ctx, ws->g, ds->p, k, ws->S, done))) return rc;
+        IHT_CUDA(cudaMemsetAsync(ws->bS, 0, sizeof(double) * k, s));
+    }
 
     const bool traced = tr.objective || tr.mu || tr.backtracks || tr.changed || tr.supp || tr.beta;
     double graph_ms = 0.0;
@@ -890,7 +903,7 @@ int run_solve(iht_dataset *ds, int k, const iht_options *opt, int n_rows, const 
 }
 
 int run_solve_host(iht_dataset *ds, int k, const iht_options *opt, int n_rows, iht_trace *trace,
-                   int max_iter)
+                   int max_iter, const SolveInit *init)
 {
     TraceDev tr{};
     void *buf = nullptr;
@@ -907,7 +920,7 @@ int run_solve_host(iht_dataset *ds, int k, const iht_options *opt, int n_rows, i
         tr.changed = (int32_t *)p; p += T * sizeof(int32_t);
         tr.supp = (int32_t *)p;
     }
-    int rc = run_solve(ds, k, opt, n_rows, tr);
+    int rc = run_solve(ds, k, opt, n_rows, tr, init);
     if (rc == IHT_OK && trace) {
         cudaStream_t s = ds->ctx->stream;
         const int it = ds->ws->sc_host->iter;

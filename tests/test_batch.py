@@ -249,3 +249,39 @@ def test_fit_batch_odd_p(iht, ctx):
         s = iht.iht_fit(ds, yy, k, rows=rows)
         if certified(oracle.iht(G, yy, k, rows=rows)):
             assert np.array_equal(s.support, fg.support)
+
+
+@pytest.mark.parametrize("cfg,b", [(3, 44), (4, 64), (5, 32)])
+def test_fullsize_gradient_batch_sampled(iht, ctx, cfg, b):
+    """The full panels of the batched workloads (CV n=6000 p=1M, serving n=10000
+    p=1M, large n=20000 p=4M) in the multi-column launch shape their loops use
+    (one 44-column pass over the five training folds; 64 request-sized subsets,
+    two passes; 32 phenotypes on all rows): every column on sampled SNPs against
+    the oracle."""
+    torch = _torch()
+    pn = synth.config_panel(cfg)
+    bed = pn.bed()
+    ds = iht.Dataset(ctx, bed, pn.n, pn.p)
+    rng = np.random.default_rng(100 + cfg)
+    if cfg == 3:
+        lab = synth.cv_folds(pn.n, 5, 7)
+        sets = [np.flatnonzero(lab != f).astype(np.int32) for f in range(5)]
+    elif cfg == 4:
+        sets = [np.sort(rng.choice(pn.n, size=int(rng.integers(2000, pn.n + 1)), replace=False))
+                .astype(np.int32) for _ in range(8)]
+    else:
+        sets = [None]
+    rows = [sets[c % len(sets)] for c in range(b)]
+    R = [rng.normal(size=pn.n if r is None else r.size).astype(np.float32) for r in rows]
+    dev_rows = {id(r): torch.from_numpy(r).cuda() for r in sets if r is not None}
+    Gd = iht.iht_gradient_batch(ds, [torch.from_numpy(x).cuda() for x in R],
+                                [None if r is None else dev_rows[id(r)] for r in rows])
+    snps = np.sort(rng.choice(pn.p, size=1500, replace=False))
+    Gs = oracle.Geno(bed[3:].reshape(pn.p, pn.bed_row_bytes)[snps].ravel(), pn.n, snps.size,
+                     pn.bed_row_bytes)
+    Gh = Gd[:, torch.from_numpy(snps).cuda()].cpu().numpy()
+    for c in range(b):
+        go = oracle.gradient(Gs, R[c].astype(np.float64), rows[c])
+        assert rel_err(Gh[c], go) <= GTOL, f"column {c}"
+    assert bool(torch.isfinite(Gd).all())
+    del Gd, ds, bed
