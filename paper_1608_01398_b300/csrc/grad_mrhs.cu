@@ -29,9 +29,11 @@
 // One persistent CTA per SM handles two 128-SNP tiles at a time, so every B
 // chunk it streams from L2 feeds two MMAs.  Warps 0-15 decode (warps 8t..8t+7
 // own tile t, thread = SNP row = tensor-memory lane; two groups of four per
-// tile take alternate A buffers) and run the epilogue, warp 16 issues the
-// MMAs, warp 17 streams genotype tiles (TMA 2D, 64-byte swizzle), warp 18
-// streams B chunks (bulk copies).  Tensor memory (512
+// tile take alternate A buffers) and run the epilogue, warps 16 and 17 issue
+// the MMAs of tiles 0 and 1 (one issuing warp per tile: with a single one,
+// passes of few columns were bound by its MMA issue), warp 18 streams genotype
+// tiles (TMA 2D, 64-byte swizzle), warp 19 streams B chunks (bulk copies; a
+// chunk is free again once both tiles' MMAs reading it have completed).  Tensor memory (512
 // columns): accumulator of tile t at column 256 t, its A buffers right after
 // it.  The epilogue writes D; a second pass (k_miss_finalize) forms the
 // missing-call sums from the per-SNP lists, S1 and g, so this kernel's
@@ -47,11 +49,11 @@ namespace iht {
 constexpr int kMrTiles = 2;                 // 128-SNP tiles per CTA tile
 constexpr int kMrDecGroups = 2;             // decoder groups per tile (alternate A buffers)
 constexpr int kMrDecoders = 128 * kMrTiles * kMrDecGroups;   // decoder / epilogue threads
-constexpr int kMrBufArrivals = 128 * kMrTiles;               // decoders that fill one A buffer
-constexpr int kMrMmaWarp = kMrDecoders / 32;
-constexpr int kMrGWarp = kMrMmaWarp + 1;
-constexpr int kMrBWarp = kMrMmaWarp + 2;
-constexpr int kMrThreads = kMrDecoders + 96;
+constexpr int kMrBufArrivals = 128;                          // decoders that fill one tile's A buffer
+constexpr int kMrMmaWarp = kMrDecoders / 32;                 // MMA warps kMrMmaWarp + t, one per tile
+constexpr int kMrGWarp = kMrMmaWarp + kMrTiles;
+constexpr int kMrBWarp = kMrGWarp + 1;
+constexpr int kMrThreads = kMrDecoders + 32 * (kMrTiles + 2);
 constexpr int kMrStepSamples = 32;          // K of one MMA
 constexpr int kMrLimbs = 5;                 // E4M3 limbs per residual column
 constexpr int kMrGStageBytes = 64;          // packed bytes per row per TMA stage (256 samples)
@@ -255,9 +257,9 @@ __device__ __forceinline__ void mr_decode(uint32_t w, uint32_t *a)
 
 struct MrPipe {
     uint64_t gfull[kMrGStages], gempty[kMrGStages];
-    uint64_t bfull[kMrMaxBStages], bempty[kMrMaxBStages];
-    uint64_t afull[kMrMaxBufs], aempty[kMrMaxBufs];
-    uint64_t accfull, accempty;
+    uint64_t bfull[kMrMaxBStages], bempty[kMrMaxBStages];   // B chunks: shared by the tiles
+    uint64_t afull[kMrTiles][kMrMaxBufs], aempty[kMrTiles][kMrMaxBufs];
+    uint64_t accfull[kMrTiles], accempty[kMrTiles];
 };
 
 __global__ void __launch_bounds__(kMrThreads, 1) k_grad_mrhs(
@@ -283,14 +285,16 @@ __global__ void __launch_bounds__(kMrThreads, 1) k_grad_mrhs(
         }
         for (int s = 0; s < nbst; ++s) {
             mr_bar_init(&pipe.bfull[s], 1);
-            mr_bar_init(&pipe.bempty[s], 1);
+            mr_bar_init(&pipe.bempty[s], kMrTiles);           // one commit per tile's MMA warp
         }
-        for (int b = 0; b < nbufs; ++b) {
-            mr_bar_init(&pipe.afull[b], kMrBufArrivals);
-            mr_bar_init(&pipe.aempty[b], 1);
+        for (int t = 0; t < kMrTiles; ++t) {
+            for (int b = 0; b < nbufs; ++b) {
+                mr_bar_init(&pipe.afull[t][b], kMrBufArrivals);
+                mr_bar_init(&pipe.aempty[t][b], 1);
+            }
+            mr_bar_init(&pipe.accfull[t], 1);
+            mr_bar_init(&pipe.accempty[t], kMrDecoders / kMrTiles);
         }
-        mr_bar_init(&pipe.accfull, 1);
-        mr_bar_init(&pipe.accempty, kMrDecoders);
         abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -342,7 +346,7 @@ __global__ void __launch_bounds__(kMrThreads, 1) k_grad_mrhs(
                 // group dg fills the buffers whose sequence number has parity dg
                 for (int q4 = (int)((uint32_t)dg - gseq) & 1; q4 < nb; q4 += kMrDecGroups) {
                     if (aseq >= (uint32_t)nbufs) {
-                        if (!mr_wait(&pipe.aempty[aslot], aphase ^ 1u)) {
+                        if (!mr_wait(&pipe.aempty[t][aslot], aphase ^ 1u)) {
                             abort_flag = 1;
                             ok = false;
                             break;
@@ -358,7 +362,7 @@ __global__ void __launch_bounds__(kMrThreads, 1) k_grad_mrhs(
                     mr_st16(abase + 16u * aslot, v);
                     asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
                     mr_fence_before();
-                    mr_arrive(&pipe.afull[aslot]);
+                    mr_arrive(&pipe.afull[t][aslot]);
                     aseq += kMrDecGroups;
                     aslot += kMrDecGroups;
                     while (aslot >= (uint32_t)nbufs) {       // at most twice (nbufs >= 2)
@@ -376,7 +380,7 @@ __global__ void __launch_bounds__(kMrThreads, 1) k_grad_mrhs(
             }
             if (!ok) break;
             // epilogue: D of each column for this thread's SNP
-            if (!mr_wait(&pipe.accfull, (uint32_t)T & 1u)) {
+            if (!mr_wait(&pipe.accfull[t], (uint32_t)T & 1u)) {
                 abort_flag = 1;
                 ok = false;
                 break;
@@ -413,18 +417,20 @@ __global__ void __launch_bounds__(kMrThreads, 1) k_grad_mrhs(
                 }
             }
             mr_fence_before();
-            mr_arrive(&pipe.accempty);
+            mr_arrive(&pipe.accempty[t]);
         }
-    } else if (warp == kMrMmaWarp) {
-        // ------------------------------------------------------- MMA issuer
+    } else if (warp < kMrGWarp) {
+        // ------------------------------------------------------- MMA issuers (one per tile)
+        const int t = warp - kMrMmaWarp;
         if (lane == 0) {
             uint32_t aslot = 0, aphase = 0, bslot = 0, bphase = 0;
             int T = 0;
             bool ok = true;
             const uint32_t b0 = mr_smem(bst);
+            const uint32_t tb = tmem_base + (uint32_t)(256 * t);
             for (int64_t tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x, ++T) {
                 if (T >= 1) {
-                    if (!mr_wait(&pipe.accempty, (uint32_t)(T - 1) & 1u)) { abort_flag = 1; break; }
+                    if (!mr_wait(&pipe.accempty[t], (uint32_t)(T - 1) & 1u)) { abort_flag = 1; break; }
                     mr_fence_after();
                 }
                 for (int ch = 0; ch < cpt && ok; ++ch) {
@@ -432,21 +438,16 @@ __global__ void __launch_bounds__(kMrThreads, 1) k_grad_mrhs(
                     uint32_t baddr = b0 + bslot * chunk_bytes;
 #pragma unroll
                     for (int h = 0; h < kMrChunkSteps / 2; ++h) {     // two A buffers per chunk
-                        if (!mr_wait(&pipe.afull[aslot], aphase)) { abort_flag = 1; ok = false; break; }
+                        if (!mr_wait(&pipe.afull[t][aslot], aphase)) { abort_flag = 1; ok = false; break; }
                         mr_fence_after();
 #pragma unroll
                         for (int s2 = 0; s2 < 2; ++s2) {
-                            const uint64_t bd = mr_b_desc(baddr);
                             const uint32_t acc = (ch | h | s2) ? 1u : 0u;
-#pragma unroll
-                            for (int t = 0; t < kMrTiles; ++t) {
-                                const uint32_t tb = tmem_base + (uint32_t)(256 * t);
-                                mr_mma(tb, tb + (uint32_t)N + 16u * aslot + 8u * (uint32_t)s2, bd, idesc,
-                                       acc);
-                            }
+                            mr_mma(tb, tb + (uint32_t)N + 16u * aslot + 8u * (uint32_t)s2, mr_b_desc(baddr),
+                                   idesc, acc);
                             baddr += step_bytes;
                         }
-                        mr_commit(&pipe.aempty[aslot]);
+                        mr_commit(&pipe.aempty[t][aslot]);
                         if (++aslot == (uint32_t)nbufs) {
                             aslot = 0;
                             aphase ^= 1u;
@@ -460,7 +461,7 @@ __global__ void __launch_bounds__(kMrThreads, 1) k_grad_mrhs(
                     }
                 }
                 if (!ok) break;
-                mr_commit(&pipe.accfull);
+                mr_commit(&pipe.accfull[t]);
                 if (abort_flag) ok = false;
             }
         }
