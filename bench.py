@@ -59,7 +59,7 @@ FALLBACK_HBM_GBS = 6400.0
 K1_TRAFFIC_BYTES = 646168832 + 4421120
 # The same for the first multi-column launch of the cross-validation batch
 # (44 residual columns of the 100 solves, the widest pass).
-K2_TRAFFIC_FIRST_LAUNCH_BYTES = 1538893312 + 167300608
+K2_TRAFFIC_FIRST_LAUNCH_BYTES = 1538364416 + 167354112
 
 
 def log(*a):

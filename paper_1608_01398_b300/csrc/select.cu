@@ -329,7 +329,7 @@ __global__ void __launch_bounds__(kSelBThreads) k_bsel_pick(const SelJob *jobs, 
 static int sel_blocks(int64_t p, int num_sms, int nb)
 {
     return (int)std::max<int64_t>(1, std::min<int64_t>((p + kSelKeysPerBlock - 1) / kSelKeysPerBlock,
-                                                        ((int64_t)num_sms * 2 + nb - 1) / nb));
+                                                        ((int64_t)num_sms * 8 + nb - 1) / nb));
 }
 
 // Top-K of |keys| for nb problems at once (jobs: device array of nb SelJob
