@@ -140,7 +140,10 @@ struct iht_dataset {
     int64_t n_pad;       // 4 * stride samples
     uint8_t *G;
     // missing calls (code 01), built once at upload: sample offsets of SNP j
-    // are miss_idx[miss_off[j] .. miss_off[j+1]) (uint16 when n <= 65536)
+    // are miss_idx[miss_off[j] .. miss_off[j+1]) (uint16 when n <= 65536), in
+    // residue classes (i - j) mod 8 = 0, 1, .., 7, ascending within a class (the
+    // order every kernel sums them in: adjacent SNPs start on different shared-
+    // memory banks when their lanes gather staged residuals)
     int64_t *miss_off;
     void *miss_idx;
     int64_t miss_total;

@@ -446,9 +446,14 @@ __global__ void __launch_bounds__(256) k_miss_fill(const uint8_t *__restrict__ G
     for (int64_t j = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); j < p; j += nwarps) {
         const uint32_t *row = reinterpret_cast<const uint32_t *>(G + j * stride);
         int64_t pos = off[j];
+        // residue classes (i - j) mod 8 in turn, ascending within a class: the
+        // samples of class rho are fields rho and rho + 8 of every 16-sample word
+        for (int cls = 0; cls < 8; ++cls)
         for (int64_t base = 0; base < nw; base += 32) {
+            const int rho = (int)((j + cls) & 7);
+            const uint32_t cmask = (1u << (2 * rho)) | (1u << (2 * rho + 16));
             const int64_t w = base + lane;
-            uint32_t mm = w < nw ? missing_mask(__ldg(row + w), w, n) : 0u;
+            uint32_t mm = w < nw ? missing_mask(__ldg(row + w), w, n) & cmask : 0u;
             const int c = __popc(mm);
             int x = c;   // inclusive warp scan
 #pragma unroll
