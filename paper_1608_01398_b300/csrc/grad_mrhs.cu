@@ -58,7 +58,7 @@ constexpr int kMrStepSamples = 32;          // K of one MMA
 constexpr int kMrLimbs = 5;                 // E4M3 limbs per residual column
 constexpr int kMrGStageBytes = 64;          // packed bytes per row per TMA stage (256 samples)
 constexpr int kMrGTile = 128 * kMrGStageBytes;
-constexpr int kMrGStages = 4;
+constexpr int kMrMaxGStages = 8;          // genotype stages (launch parameter ngs <= this)
 constexpr int kMrChunkSteps = 4;            // K-steps per B chunk
 constexpr int kMrMaxBStages = 6;
 constexpr int kMrMaxBufs = 8;               // A buffers of 2 K-steps
@@ -197,6 +197,18 @@ __device__ __forceinline__ void mr_bulk(void *dst, const void *src, uint32_t byt
 __device__ __forceinline__ void mr_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void mr_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
+__device__ __forceinline__ void mr_st32(uint32_t taddr, const uint32_t (&v)[32])
+{
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,"
+        "%13,%14,%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31,%32};" ::"r"(taddr),
+        "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7]),
+        "r"(v[8]), "r"(v[9]), "r"(v[10]), "r"(v[11]), "r"(v[12]), "r"(v[13]), "r"(v[14]), "r"(v[15]),
+        "r"(v[16]), "r"(v[17]), "r"(v[18]), "r"(v[19]), "r"(v[20]), "r"(v[21]), "r"(v[22]), "r"(v[23]),
+        "r"(v[24]), "r"(v[25]), "r"(v[26]), "r"(v[27]), "r"(v[28]), "r"(v[29]), "r"(v[30]), "r"(v[31])
+        : "memory");
+}
+
 __device__ __forceinline__ void mr_st16(uint32_t taddr, const uint32_t (&v)[16])
 {
     asm volatile(
@@ -256,16 +268,17 @@ __device__ __forceinline__ void mr_decode(uint32_t w, uint32_t *a)
 }
 
 struct MrPipe {
-    uint64_t gfull[kMrGStages], gempty[kMrGStages];
+    uint64_t gfull[kMrMaxGStages], gempty[kMrMaxGStages];
     uint64_t bfull[kMrMaxBStages], bempty[kMrMaxBStages];   // B chunks: shared by the tiles
     uint64_t afull[kMrTiles][kMrMaxBufs], aempty[kMrTiles][kMrMaxBufs];
     uint64_t accfull[kMrTiles], accempty[kMrTiles];
 };
 
+template <bool kPairs>
 __global__ void __launch_bounds__(kMrThreads, 1) k_grad_mrhs(
     const __grid_constant__ CUtensorMap gmap, int64_t p, int ksteps, int N, int ncols, int nbufs,
-    int nbst, const uint8_t *__restrict__ bimg, const MrCol *__restrict__ cols, uint32_t idesc,
-    int *err)
+    int nbst, int ngs, const uint8_t *__restrict__ bimg, const MrCol *__restrict__ cols,
+    uint32_t idesc, int *err)
 {
     extern __shared__ __align__(1024) uint8_t smem[];
     __shared__ MrPipe pipe;
@@ -273,13 +286,13 @@ __global__ void __launch_bounds__(kMrThreads, 1) k_grad_mrhs(
     __shared__ volatile int abort_flag;
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    uint8_t *gst = smem;                                        // kMrGStages x 2 tiles x 8 KB
-    uint8_t *bst = smem + kMrGStages * kMrTiles * kMrGTile;     // nbst x chunk
+    uint8_t *gst = smem;                                        // ngs x 2 tiles x 8 KB
+    uint8_t *bst = smem + ngs * kMrTiles * kMrGTile;            // nbst x chunk
     const uint32_t chunk_bytes = (uint32_t)kMrChunkSteps * (uint32_t)N * 32u;
     const uint32_t step_bytes = (uint32_t)N * 32u;
 
     if (tid == 0) {
-        for (int s = 0; s < kMrGStages; ++s) {
+        for (int s = 0; s < ngs; ++s) {
             mr_bar_init(&pipe.gfull[s], 1);
             mr_bar_init(&pipe.gempty[s], kMrDecoders);
         }
@@ -327,8 +340,10 @@ __global__ void __launch_bounds__(kMrThreads, 1) k_grad_mrhs(
         const int swz = (r >> 1) & 3;
         uint32_t gslot = 0, gphase = 0;           // genotype stage ring
         // A buffer ring position of this group's next buffer (sequence number aseq)
-        uint32_t aslot = (uint32_t)dg % (uint32_t)nbufs, aphase = (uint32_t)dg / (uint32_t)nbufs;
-        uint32_t aseq = (uint32_t)dg;
+        // (pairs: group dg's first pair is pair dg, buffers 2 dg and 2 dg + 1)
+        const uint32_t first = kPairs ? 2u * (uint32_t)dg : (uint32_t)dg;
+        uint32_t aslot = first % (uint32_t)nbufs, aphase = first / (uint32_t)nbufs;
+        uint32_t aseq = first;
         int T = 0;
         bool ok = true;
         uint32_t gseq = 0;                         // sequence number of the stage's first buffer
@@ -343,6 +358,45 @@ __global__ void __launch_bounds__(kMrThreads, 1) k_grad_mrhs(
                 const uint8_t *rowp = gst + (gslot * kMrTiles + t) * kMrGTile + r * kMrGStageBytes;
                 const int nb = min(4, left);
                 left -= nb;
+                if (kPairs) {
+                    // group dg fills the buffer pairs (2 adjacent buffers, 128
+                    // samples, one 32-column store) whose pair number has parity
+                    // dg; buffers per tile and per stage are even, so no pair
+                    // straddles a stage or the ring's end (nbufs even)
+                    for (int q2 = (int)((uint32_t)dg - (gseq >> 1)) & 1; 2 * q2 < nb; q2 += kMrDecGroups) {
+                        if (aseq >= (uint32_t)nbufs) {
+                            if (!mr_wait(&pipe.aempty[t][aslot], aphase ^ 1u) ||
+                                !mr_wait(&pipe.aempty[t][aslot + 1], aphase ^ 1u)) {
+                                abort_flag = 1;
+                                ok = false;
+                                break;
+                            }
+                            mr_fence_after();
+                        }
+                        const uint4 x0 = *reinterpret_cast<const uint4 *>(rowp + (((2 * q2) ^ swz) << 4));
+                        const uint4 x1 = *reinterpret_cast<const uint4 *>(rowp + (((2 * q2 + 1) ^ swz) << 4));
+                        uint32_t v[32];
+                        mr_decode(x0.x, &v[0]);
+                        mr_decode(x0.y, &v[4]);
+                        mr_decode(x0.z, &v[8]);
+                        mr_decode(x0.w, &v[12]);
+                        mr_decode(x1.x, &v[16]);
+                        mr_decode(x1.y, &v[20]);
+                        mr_decode(x1.z, &v[24]);
+                        mr_decode(x1.w, &v[28]);
+                        mr_st32(abase + 16u * aslot, v);
+                        asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+                        mr_fence_before();
+                        mr_arrive(&pipe.afull[t][aslot]);
+                        mr_arrive(&pipe.afull[t][aslot + 1]);
+                        aseq += 2 * kMrDecGroups;
+                        aslot += 2 * kMrDecGroups;
+                        while (aslot >= (uint32_t)nbufs) {
+                            aslot -= (uint32_t)nbufs;
+                            aphase ^= 1u;
+                        }
+                    }
+                } else
                 // group dg fills the buffers whose sequence number has parity dg
                 for (int q4 = (int)((uint32_t)dg - gseq) & 1; q4 < nb; q4 += kMrDecGroups) {
                     if (aseq >= (uint32_t)nbufs) {
@@ -372,7 +426,7 @@ __global__ void __launch_bounds__(kMrThreads, 1) k_grad_mrhs(
                 }
                 gseq += (uint32_t)nb;
                 mr_arrive(&pipe.gempty[gslot]);
-                if (++gslot == kMrGStages) {
+                if (++gslot == (uint32_t)ngs) {
                     gslot = 0;
                     gphase ^= 1u;
                 }
@@ -475,7 +529,7 @@ __global__ void __launch_bounds__(kMrThreads, 1) k_grad_mrhs(
             for (int64_t tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
                 const int y0 = (int)(tile * (128 * kMrTiles));
                 for (int st = 0; st < spt; ++st, ++issued) {
-                    if (abort_flag || (issued >= kMrGStages && !mr_wait(&pipe.gempty[slot], phase ^ 1u))) {
+                    if (abort_flag || (issued >= ngs && !mr_wait(&pipe.gempty[slot], phase ^ 1u))) {
                         abort_flag = 1;
                         ok = false;
                         break;
@@ -485,15 +539,15 @@ __global__ void __launch_bounds__(kMrThreads, 1) k_grad_mrhs(
                     for (int t = 0; t < kMrTiles; ++t)
                         mr_tma_2d(gst + (slot * kMrTiles + t) * kMrGTile, &gmap, st * kMrGStageBytes,
                                   y0 + 128 * t, &pipe.gfull[slot]);
-                    if (++slot == kMrGStages) {
+                    if (++slot == (uint32_t)ngs) {
                         slot = 0;
                         phase ^= 1u;
                     }
                 }
             }
             // copies still in flight after an abort: wait for them (bounded)
-            for (int64_t q = issued - kMrGStages; q < issued; ++q)
-                if (q >= 0) mr_wait(&pipe.gfull[q % kMrGStages], (uint32_t)(q / kMrGStages) & 1u);
+            for (int64_t q = issued - ngs; q < issued; ++q)
+                if (q >= 0) mr_wait(&pipe.gfull[q % ngs], (uint32_t)(q / ngs) & 1u);
         }
         __syncwarp();
     } else {
@@ -713,12 +767,17 @@ static int mr_ksteps(const iht_dataset *ds)
 
 static int mr_n(int ncols) { return (kMrLimbs * ncols + 15) / 16 * 16; }
 
-static size_t mr_gbytes() { return (size_t)kMrGStages * kMrTiles * kMrGTile; }
+// Genotype stages: with few accumulator columns the pass streams genotypes as
+// fast as it decodes them and wants many bytes in flight; with many, B chunks
+// need the room (the pass is tensor-bound there).
+static int mr_gstages(int N) { return N <= 96 ? kMrMaxGStages : 4; }
+
+static size_t mr_gbytes(int N) { return (size_t)mr_gstages(N) * kMrTiles * kMrGTile; }
 
 static int mr_bstages(int N)
 {
     const size_t chunk = (size_t)kMrChunkSteps * N * 32;
-    const size_t room = kMrSmemMax - mr_gbytes();
+    const size_t room = kMrSmemMax - mr_gbytes(N);
     return (int)std::min<size_t>(kMrMaxBStages, room / chunk);
 }
 
@@ -826,7 +885,9 @@ int launch_grad_mrhs(iht_dataset *ds, MrCol *cols, int ncols, ProfEvents *prof)
     if (rc) return rc;
     static thread_local int cfg = -1;
     if (cfg != ds->ctx->device) {
-        IHT_CUDA(cudaFuncSetAttribute(k_grad_mrhs, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        IHT_CUDA(cudaFuncSetAttribute(k_grad_mrhs<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)kMrSmemMax));
+        IHT_CUDA(cudaFuncSetAttribute(k_grad_mrhs<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       (int)kMrSmemMax));
         cfg = ds->ctx->device;
     }
@@ -840,16 +901,20 @@ int launch_grad_mrhs(iht_dataset *ds, MrCol *cols, int ncols, ProfEvents *prof)
         // scale, limbs and R over the single-column pass's samples (the rest are 0)
         k_mr_limbs<<<nc, 1024, 0, s>>>(cols + c0, 2 * mr_ngroups(ds) * kMrStepSamples, N, w.bimg);
         const int nbst = mr_bstages(N);
-        const int nbufs = std::min(kMrMaxBufs, (256 - N) / 16);
+        int nbufs = std::min(kMrMaxBufs, (256 - N) / 16);
+        // with four or more A buffers a decoder step fills two (one 32-column store)
+        const bool pairs = nbufs >= 4;
+        if (pairs) nbufs &= ~1;
         if (nbst < 2 || nbufs < 2) return IHT_EINVAL;
         // at least 116 KB, so one CTA per SM: the kernel allocates all 512 columns of tensor memory
-        const size_t smem = std::max<size_t>(116 * 1024, mr_gbytes() + (size_t)nbst * kMrChunkSteps * N * 32);
+        const size_t smem = std::max<size_t>(116 * 1024, mr_gbytes(N) + (size_t)nbst * kMrChunkSteps * N * 32);
         // D FP32, A E5M2, B E4M3, K-major, N, M = 128
         const uint32_t idesc = (1u << 4) | (1u << 7) | ((uint32_t)(N >> 3) << 17) |
                                ((uint32_t)(128 >> 4) << 24);
         prof_begin(prof, s);
-        k_grad_mrhs<<<grid, kMrThreads, smem, s>>>(map, ds->p, ksteps, N, nc, nbufs, nbst, w.bimg,
-                                                    cols + c0, idesc, w.err);
+        auto kern = pairs ? k_grad_mrhs<true> : k_grad_mrhs<false>;
+        kern<<<grid, kMrThreads, smem, s>>>(map, ds->p, ksteps, N, nc, nbufs, nbst, mr_gstages(N), w.bimg,
+                                            cols + c0, idesc, w.err);
         prof_end(prof, s);
         note_launch(2);
         IHT_CUDA(cudaGetLastError());
