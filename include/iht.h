@@ -277,7 +277,9 @@ int iht_fit_batch(iht_dataset *ds, int32_t b, const iht_solve_desc *solves,
  *   n_rows    : host int64[b]
  *   R         : device float, column c at R + c * n (aligned with its rows)
  *   G_out     : device float[b][p]
- *   impl      : 0 default, 1 one CUDA-core pass per column, 2 multi-RHS tensor cores. */
+ *   impl      : 0 default (tensor cores; a single column runs the single-column
+ *               pass, which gives the same bits), 1 one CUDA-core pass per
+ *               column, 2 the multi-column tensor-core pass always. */
 int iht_gradient_batch(iht_dataset *ds, int32_t b, const int32_t *const *rows_list,
                        const int64_t *n_rows, const float *R, float *G_out, int impl);
 

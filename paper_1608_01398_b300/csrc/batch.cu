@@ -253,7 +253,7 @@ static int batch_grad(iht_dataset *ds, BatchWork *w, const std::vector<int> &act
     }
     IHT_CUDA(cudaMemcpyAsync(w->cols, w->cols_host, sizeof(MrCol) * act.size(),
                              cudaMemcpyHostToDevice, s));
-    return launch_grad_mrhs(ds, w->cols, (int)act.size(), prof);
+    return launch_grad_mrhs(ds, w->cols, (int)act.size(), prof, impl == 2 ? nullptr : w->cols_host);
 }
 
 }  // namespace iht

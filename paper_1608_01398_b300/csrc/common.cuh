@@ -258,7 +258,8 @@ struct MrCol {
 };
 int mrhs_max_cols();
 bool grad_mrhs_supported(const iht_dataset *ds);
-int launch_grad_mrhs(iht_dataset *ds, MrCol *cols_dev, int ncols, ProfEvents *prof = nullptr);
+int launch_grad_mrhs(iht_dataset *ds, MrCol *cols_dev, int ncols, ProfEvents *prof = nullptr,
+                     const MrCol *cols_host = nullptr);
 int grad_mrhs_status(iht_dataset *ds, int *timed_out);
 void grad_mrhs_release_thread();
 // select.cu

@@ -752,6 +752,9 @@ struct MrWork {
     size_t bbytes = 0;
     int *err = nullptr;
     int dev = -1;
+    float *mj = nullptr;                   // missing-call sums of a one-column pass (p)
+    int64_t mj_cap = 0;
+    int mj_dev = -1;
 };
 static thread_local MrWork g_mr;
 
@@ -859,12 +862,33 @@ static int mr_finalize(iht_dataset *ds, const MrCol *cols, int ncols)
 }
 
 // G of ncols residual columns (cols: device array; r32, u32, v32 and g set by
-// the caller).  Passes of at most kMrMaxCols columns.
-int launch_grad_mrhs(iht_dataset *ds, MrCol *cols, int ncols, ProfEvents *prof)
+// the caller; cols_host, optional, the same descriptors on the host).  Passes
+// of at most kMrMaxCols columns.  A single column with its host descriptor goes
+// through the single-column pass instead (same arithmetic, so the same bits,
+// at about half the cost of a one-column multi-column pass).
+int launch_grad_mrhs(iht_dataset *ds, MrCol *cols, int ncols, ProfEvents *prof, const MrCol *cols_host)
 {
     if (ncols <= 0) return IHT_OK;
     if (!grad_mrhs_supported(ds)) return IHT_EINVAL;
     cudaStream_t s = ds->ctx->stream;
+    if (ncols == 1 && cols_host && grad_tc_supported(ds)) {
+        MrWork &w = g_mr;
+        if (w.mj_dev != ds->ctx->device || w.mj_cap < ds->p) {
+            if (w.mj) cudaFree(w.mj);
+            w.mj = nullptr;
+            w.mj_cap = 0;
+            IHT_CUDA(cudaMalloc(&w.mj, sizeof(float) * (size_t)ds->p));
+            w.mj_cap = ds->p;
+            w.mj_dev = ds->ctx->device;
+        }
+        const MrCol &C = cols_host[0];
+        int rc = prepare_grad_tc_to(ds, C.r32, w.mj, nullptr);
+        if (rc) return rc;
+        prof_begin(prof, s);
+        rc = launch_grad_tc_main_with(ds, C.r32, C.g, C.u32, C.v32, w.mj, nullptr);
+        prof_end(prof, s);
+        return rc;
+    }
     const int ksteps = mr_ksteps(ds);
     const size_t need = (size_t)ksteps * mr_n(kMrMaxCols) * 32;
     MrWork &w = g_mr;
@@ -931,6 +955,7 @@ void grad_mrhs_release_thread()
     MrWork &w = g_mr;
     if (w.bimg) cudaFree(w.bimg);
     if (w.err) cudaFree(w.err);
+    if (w.mj) cudaFree(w.mj);
     w = MrWork();
 }
 

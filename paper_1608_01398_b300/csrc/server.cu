@@ -289,7 +289,7 @@ static int srv_tick(iht_server *S, const std::vector<int> &fresh)
         }
         IHT_CUDA(cudaMemcpyAsync(S->cols, S->cols_host, sizeof(MrCol) * act.size(),
                                  cudaMemcpyHostToDevice, s));
-        if ((rc = launch_grad_mrhs(ds, S->cols, (int)act.size()))) return rc;
+        if ((rc = launch_grad_mrhs(ds, S->cols, (int)act.size(), nullptr, S->cols_host))) return rc;
     }
     if (!fresh.empty()) {
         int nf = 0;
