@@ -274,8 +274,11 @@ struct SelJob {                        // one problem of a batched top-K
 };
 int select_topk_batch(iht_ctx *ctx, const SelJob *jobs, int nb, int64_t p);
 int ensure_selwork(iht_ctx *ctx, int64_t p);
+// gS .. gsc (optional): also form g_S and ||g_S||^2 of support gS (k = gk) in
+// the selection's last block (gather_gS_body).
 int select_topk(iht_ctx *ctx, const float *key_src, int64_t p, int32_t K, int32_t *out_idx,
-                const int32_t *done);
+                const int32_t *done, const int32_t *gS = nullptr, int gk = 0,
+                double *gcoef = nullptr, Scalars *gsc = nullptr);
 // solver.cu
 int zmul_blocks(const iht_dataset *ds);
 int launch_zmul(iht_dataset *ds, const int32_t *cols, int32_t m, const double *coef,
@@ -349,6 +352,26 @@ inline int ceil_div(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
 __device__ __forceinline__ float standardise(float S1, float R, float M, float u, float v)
 {
     return __fmul_rn(v, __fsub_rn(S1, __fmul_rn(u, __fsub_rn(R, M))));
+}
+
+// g_S (coef) and ||g_S||^2 (sc->num) for the step size: the first warp of the
+// block, lanes strided over S then a shuffle tree, so the sum's order does not
+// depend on the block size (the single-solve selection's last block and the
+// batched kernel give the same bits).
+__device__ __forceinline__ void gather_gS_body(const float *__restrict__ g,
+                                               const int32_t *__restrict__ S, int k,
+                                               double *__restrict__ coef, Scalars *sc)
+{
+    if (threadIdx.x >= 32) return;
+    double s = 0.0;
+    for (int c = threadIdx.x; c < k; c += 32) {
+        const double x = (double)g[S[c]];
+        coef[c] = x;
+        s += x * x;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (threadIdx.x == 0) sc->num = s;
 }
 
 // The same from D = sum over all calls of (2 x + [call missing]) r, which is

@@ -235,8 +235,12 @@ __device__ __forceinline__ void sort_idx_body(int32_t *idx, int K)
 }
 
 // Launch B: candidates at or above the boundary bin; the last block finishes.
+// gS (optional): the single solve's support; the last block then also forms
+// g_S and ||g_S||^2 (gather_gS_body) for the step size, saving a launch.
 __device__ __forceinline__ void sel_pick_body(const float *__restrict__ keys, int64_t p, SelState *st,
-                                              unsigned long long *cand, int32_t *out, uint32_t K)
+                                              unsigned long long *cand, int32_t *out, uint32_t K,
+                                              const int32_t *gS = nullptr, int gk = 0,
+                                              double *gcoef = nullptr, Scalars *gsc = nullptr)
 {
     __shared__ unsigned long long sk[kSelCap];
     __shared__ uint32_t wsum[32];
@@ -292,6 +296,7 @@ __device__ __forceinline__ void sel_pick_body(const float *__restrict__ keys, in
         st->n_gt = 0;
         st->ticket_b = 0;
     }
+    if (gS) gather_gS_body(keys, gS, gk, gcoef, gsc);
 }
 
 __global__ void __launch_bounds__(kSelAThreads) k_sel_count(const float *__restrict__ keys, int64_t p,
@@ -304,10 +309,12 @@ __global__ void __launch_bounds__(kSelAThreads) k_sel_count(const float *__restr
 
 __global__ void __launch_bounds__(kSelBThreads) k_sel_pick(const float *__restrict__ keys, int64_t p,
                                                            SelState *st, unsigned long long *cand,
-                                                           int32_t *out, uint32_t K, const int32_t *done)
+                                                           int32_t *out, uint32_t K, const int32_t *done,
+                                                           const int32_t *gS, int gk, double *gcoef,
+                                                           Scalars *gsc)
 {
     if (done && *done) return;
-    sel_pick_body(keys, p, st, cand, out, K);
+    sel_pick_body(keys, p, st, cand, out, K, gS, gk, gcoef, gsc);
 }
 
 // Batched selection: blockIdx.y indexes the problem; each problem has its own
@@ -361,14 +368,15 @@ int ensure_selwork(iht_ctx *ctx, int64_t p)
 }
 
 int select_topk(iht_ctx *ctx, const float *keys, int64_t p, int32_t K, int32_t *out,
-                const int32_t *done)
+                const int32_t *done, const int32_t *gS, int gk, double *gcoef, Scalars *gsc)
 {
     SelWork *ws = &ctx->sel;
     cudaStream_t s = ctx->stream;
     if (K < 1 || K > p || K > kMaxCand || !ws->hist) return IHT_EINVAL;
     const int blocks = sel_blocks(p, ctx->num_sms, 1);
     k_sel_count<<<blocks, kSelAThreads, 0, s>>>(keys, p, ws->st, ws->hist, (uint32_t)K, done);
-    k_sel_pick<<<blocks, kSelBThreads, 0, s>>>(keys, p, ws->st, ws->cand, out, (uint32_t)K, done);
+    k_sel_pick<<<blocks, kSelBThreads, 0, s>>>(keys, p, ws->st, ws->cand, out, (uint32_t)K, done, gS, gk,
+                                               gcoef, gsc);
     note_launch(2);
     IHT_CUDA(cudaGetLastError());
     return IHT_OK;
@@ -461,7 +469,8 @@ extern "C" int iht_topk_noalloc(int device, void *stream, const float *w, int64_
     cudaStream_t s = (cudaStream_t)stream;
     const int blocks = sel_blocks(p, sms, 1);
     k_sel_count<<<blocks, kSelAThreads, 0, s>>>(w, p, st, hist, (uint32_t)k, nullptr);
-    k_sel_pick<<<blocks, kSelBThreads, 0, s>>>(w, p, st, cand, idx_out, (uint32_t)k, nullptr);
+    k_sel_pick<<<blocks, kSelBThreads, 0, s>>>(w, p, st, cand, idx_out, (uint32_t)k, nullptr, nullptr, 0,
+                                               nullptr, nullptr);
     note_launch(2);
     const cudaError_t e = cudaGetLastError();
     if (prev != device) cudaSetDevice(prev);

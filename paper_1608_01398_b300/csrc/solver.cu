@@ -49,20 +49,6 @@ __device__ __forceinline__ void warp_partials(const double *__restrict__ partial
     d2 = warp_sum(d2);
 }
 
-__device__ __forceinline__ void gather_gS_body(const float *__restrict__ g,
-                                               const int32_t *__restrict__ S, int k,
-                                               double *__restrict__ coef, Scalars *sc)
-{
-    __shared__ double red[32];
-    double s = 0.0;
-    for (int c = threadIdx.x; c < k; c += blockDim.x) {
-        const double x = (double)g[S[c]];
-        coef[c] = x;
-        s += x * x;
-    }
-    s = block_sum(s, red);
-    if (threadIdx.x == 0) sc->num = s;
-}
 
 __global__ void __launch_bounds__(1024) k_gather_gS(const float *__restrict__ g,
                                                     const int32_t *__restrict__ S, int k,
@@ -716,9 +702,9 @@ static int enqueue_iteration(iht_dataset *ds, int k, int K, int impl, cudaEvent_
     cudaStream_t s = ds->ctx->stream;
     const int32_t *done = &ws->sc->done;
     int rc;
-    if ((rc = select_topk(ds->ctx, ws->g, ds->p, K, ws->cand, done))) return rc;
-    k_gather_gS<<<1, 1024, 0, s>>>(ws->g, ws->S, k, ws->coef, ws->sc);
-    note_launch();
+    // candidates, and g_S with ||g_S||^2 in the same launch's last block
+    if ((rc = select_topk(ds->ctx, ws->g, ds->p, K, ws->cand, done, ws->S, k, ws->coef, ws->sc)))
+        return rc;
     if ((rc = zmul_run(ds, ws->S, k, ws->coef, 1.0, ws->u64, ws->v64, ws->used, nullptr, ws->zv,
                        ws->partials, done)))
         return rc;
