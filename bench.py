@@ -66,6 +66,20 @@ def log(*a):
     print(*a, file=sys.stderr, flush=True)
 
 
+# The paper's own timings (Sec. 3, Tables 1 and 2): context for the lines below,
+# not a baseline -- another machine, FP64 OpenCL, no iteration counts or rates.
+PAPER_CONTEXT = {
+    "hardware": "1 six-core 2.67 GHz Xeon + 1 NVIDIA Tesla C2050 (Fermi, OpenCL), FP64",
+    "path_time_packed_multicore_gpu_s": 65.48,
+    "path_time_packed_multicore_s": 141.28,
+    "path_time_float_single_core_s": 8.27,
+    "path_workload": "NFBC1966 chromosome 1: 23,695 SNPs, n about 5.1k, k = 5..100 in steps of 5",
+    "cv5_k1to50_with_refit_hours": {"BMI": 1.12, "HDL": 1.28, "LDL": 1.32, "TG": 1.49},
+    "cv_workload": "NFBC1966 n about 4.7-5.1k, p about 333.7k, 5-fold CV over k = 1..50 and a refit",
+    "note": "the paper reports no iteration counts, per-iteration times or GB/s",
+}
+
+
 def dist_env():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     return int(os.environ.get("RANK", "0")), int(os.environ.get("LOCAL_RANK", "0")), ws
@@ -305,7 +319,8 @@ def ours_arm(args):
         out = {
             "metric": "IHT iterations/sec", "value": value, "unit": "iter/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * max_el / args.steps,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "paper_context": PAPER_CONTEXT,
+            "dtype": "f32",
             "data": "synthetic",
             "config": {"workload": c["name"], "n": n, "p": p, "k": k,
                        "packed_bytes": p * ((n + 3) // 4), "iterations_per_solve": iters_mean,
@@ -512,7 +527,7 @@ def cv_arm(args):
             "metric": "batched IHT solves/sec", "value": value, "unit": "solves/s",
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * float(allv[:, 1].max()) / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None,
+            "scaling": "weak", "vs_baseline": None, "paper_context": PAPER_CONTEXT,
             "dtype": "e4m3 operands (exact dosage, residual in 5 limbs), f32 accumulate, f64 scalars",
             "data": "synthetic",
             "config": {"workload": c["name"], "n": n, "p": p, "folds": c["folds"],
@@ -542,6 +557,134 @@ def cv_arm(args):
         }
         if not args.no_cpu_baseline and world == 1:
             out["cpu_baseline"] = cv_reference(args, c, pn, bed, y, train, its / max(solves, 1))
+        print(json.dumps(out), flush=True)
+    del ds, ctx
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def panel_arm(args):
+    """Large panel (n = 20 000, p = 4 M, 20 GB packed): the phenotypes in one batch."""
+    import torch
+    import paper_1608_01398_b300 as iht
+
+    rank, local_rank, world = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device(f"cuda:{local_rank}"))
+    torch.cuda.set_device(local_rank)
+    dev = local_rank
+    cfg = 5
+    c = synth.CONFIGS[cfg]
+    t0 = time.perf_counter()
+    pn = synth.config_panel(cfg)
+    bed = pn.bed()
+    ys = [synth.config_phenotype(cfg, pn, which=rank * c["phenotypes"] + i)[0]
+          for i in range(c["phenotypes"])]
+    n, p, k = pn.n, pn.p, c["k"]
+    log(f"[bench] rank {rank}: generated {bed.nbytes / 1e9:.1f} GB panel in {time.perf_counter() - t0:.1f}s")
+    stream = torch.cuda.current_stream(dev)
+    ctx = iht.Context(dev, stream)
+    ds = iht.Dataset(ctx, bed, n, p)
+    cuda = f"cuda:{dev}"
+    y_dev = [torch.from_numpy(y).to(cuda) for y in ys]
+    probs = [(yy, k, None) for yy in y_dev]
+    b = len(probs)
+    kw = dict(out_device=True, dense=False, grad_impl=args.grad_impl, tol=c["tol"], max_iter=c["max_iter"])
+    for _ in range(max(args.warmup, 0)):
+        iht.iht_fit_batch(ds, probs, **kw)
+    torch.cuda.synchronize(dev)
+    clocks = ClockSampler(gpu_uuid(torch, dev))
+    clocks.start()
+    time.sleep(0.3)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize(dev)
+    l0 = iht.iht_kernel_launches()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    solves, its, cols, grad_ms, grad_n, statuses = 0, 0, 0, 0.0, 0, []
+    for _ in range(args.steps):
+        res = iht.iht_fit_batch(ds, probs, profile=1, **kw)
+        solves += b
+        its += sum(r.iterations for r in res)
+        cols += sum(max(r.iterations, 1) for r in res)
+        grad_ms += res[0].grad_ms
+        grad_n += res[0].grad_launches
+        statuses += [r.status for r in res]
+    ev1.record(stream)
+    torch.cuda.synchronize(dev)
+    if world > 1:
+        torch.distributed.barrier()
+    launches = iht.iht_kernel_launches() - l0
+    clk = clocks.stop()
+    elapsed = ev0.elapsed_time(ev1) / 1e3
+
+    # the same solves one at a time through iht_fit (single-column path)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for (yy, kk, _) in probs:
+        iht.iht_fit(ds, yy, kk, out_device=True, grad_impl=args.grad_impl, tol=c["tol"],
+                    max_iter=c["max_iter"])
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    plain_s = e0.elapsed_time(e1) / 1e3
+
+    # end to end through host buffers
+    w0 = time.perf_counter()
+    for _ in range(args.steps):
+        iht.iht_fit_batch(ds, [(y, k, None) for y in ys], dense=False, grad_impl=args.grad_impl,
+                          tol=c["tol"], max_iter=c["max_iter"])
+    torch.cuda.synchronize(dev)
+    e2e_wall = time.perf_counter() - w0
+
+    allv = gather_rows([solves, elapsed, args.steps * b, e2e_wall], world)
+    if rank == 0:
+        value = weak_rate(allv, 0, 1)
+        peak, peak_kind = measured_tensor_peak()
+        achieved = 2.0 * n * p * MR_LIMBS * cols / (grad_ms / 1e3) / 1e12 if grad_ms > 0 else None
+        out = {
+            "metric": "batched IHT solves/sec", "value": value, "unit": "solves/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * float(allv[:, 1].max()) / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "paper_context": PAPER_CONTEXT,
+            "dtype": "e4m3 operands (exact dosage, residual in 5 limbs), f32 accumulate, f64 scalars",
+            "data": "synthetic",
+            "config": {"workload": c["name"], "n": n, "p": p, "k": k, "phenotypes": b,
+                       "iterations_per_solve": its / max(solves, 1), "grad_impl": args.grad_impl,
+                       "l2": "inputs larger than L2 (no flush)",
+                       "parallelism": "replicas" if world > 1 else "single"},
+            "plain": {"value": b / plain_s, "unit": "solves/s",
+                      "what": f"the same {b} solves one at a time through iht_fit"},
+            "speedup_vs_plain": value / (b / plain_s),
+            "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                         "frac": (achieved / peak) if achieved else None, "traffic": None,
+                         "kernel": "multi-column gradient pass (k_grad_mrhs)", "peak_source": peak_kind,
+                         "algorithmic_flops": "2 n p per residual limb column, five E4M3 limb "
+                                              "columns per solve column",
+                         "columns_total": cols, "launches": grad_n,
+                         "ms_per_launch": grad_ms / max(grad_n, 1)},
+            "e2e": {"value": weak_rate(allv, 2, 3), "unit": "solves/s",
+                    "h2d_bytes_per_step": 8 * n * b, "d2h_bytes_per_step": 12 * k * b},
+            "gpu_launches": int(launches), "clocks": clk,
+            "statuses": sorted(set(int(s) for s in statuses)),
+        }
+        if not args.no_cpu_baseline and world == 1:
+            import oracle
+            G = oracle.Geno.from_bed(bed, n, p)
+            t1 = time.perf_counter()
+            f = oracle.iht(G, ys[0], k, max_iter=1, tol=c["tol"], trace=False)
+            dt = time.perf_counter() - t1
+            ips = its / max(solves, 1)
+            out["cpu_baseline"] = {
+                "value": 1.0 / (dt / max(f.iterations, 1) * ips), "unit": "solves/s",
+                "cores": oracle.max_threads(), "kind": "oracle",
+                "sample": f"FP64 oracle, phenotype 0 on {c['name']}, {f.iterations} iteration "
+                          f"(incl. setup) in {dt:.1f}s; solves/s extrapolated at {ips:.1f} "
+                          f"iterations per solve"}
         print(json.dumps(out), flush=True)
     del ds, ctx
     if world > 1:
@@ -704,7 +847,7 @@ def serve_arm(args):
             "metric": "served IHT solves/sec", "value": value, "unit": "solves/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * sum(cap_walls) / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None,
+            "scaling": "weak", "vs_baseline": None, "paper_context": PAPER_CONTEXT,
             "dtype": "e4m3 operands (exact dosage, residual in 5 limbs), f32 accumulate, f64 scalars",
             "data": "synthetic",
             "config": {"workload": c["name"], "n": pn.n, "p": pn.p, "requests_per_step": len(reqs),
@@ -737,7 +880,7 @@ def main():
                     help="timed steps (default: 50 single solves, 3 CV batches, 1 serving pass)")
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--config", type=int, default=2, choices=[1, 2, 3, 4])
+    ap.add_argument("--config", type=int, default=2, choices=[1, 2, 3, 4, 5])
     ap.add_argument("--requests", type=int, default=2000)
     ap.add_argument("--plain-requests", type=int, default=40)
     ap.add_argument("--poisson-requests", type=int, default=300)
@@ -748,11 +891,17 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     if args.steps is None:
-        args.steps = {3: 3, 4: 1}.get(args.config, 50)
+        args.steps = {3: 3, 4: 1, 5: 1}.get(args.config, 50)
     if args.config == 3:
         return cv_reference_arm(args) if args.impl == "reference" else cv_arm(args)
     if args.config == 4:
         return serve_reference_arm(args) if args.impl == "reference" else serve_arm(args)
+    if args.config == 5:
+        if args.impl == "reference":
+            print(json.dumps({"impl": "reference", "unavailable": "the large panel's oracle "
+                              "reference is the cpu_baseline sample of the --config 5 line"}))
+            return 0
+        return panel_arm(args)
     if args.impl == "reference":
         return reference_arm(args)
     return ours_arm(args)
