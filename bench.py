@@ -272,13 +272,14 @@ def ours_arm(args):
     ev0 = torch.cuda.Event(enable_timing=True)
     ev1 = torch.cuda.Event(enable_timing=True)
     ev0.record(stream)
-    its, grad_ms, grad_n = 0, 0.0, 0
+    its, grad_ms, grad_n, replays = 0, 0.0, 0, 0
     statuses = []
     for _ in range(args.steps):
         r = iht.iht_fit(ds, y_dev, k, profile=1, **fit_kw)
         its += r.iterations
         grad_ms += r.grad_ms
         grad_n += r.grad_launches
+        replays += r.graph_replays
         statuses.append(r.status)
     ev1.record(stream)
     torch.cuda.synchronize(dev)
@@ -336,6 +337,8 @@ def ours_arm(args):
                     "d2h_bytes_per_step": int(12 * k + ctl)},
             "gpu_launches": int(launches), "clocks": clk,
             "statuses": sorted(set(int(s) for s in statuses)),
+            "graph_replays_per_step": replays / max(args.steps, 1),
+            "pass_shapes": iht.tuning_summary().strip().splitlines(),
         }
         if not args.no_cpu_baseline and world == 1:
             iters, secs, threads = run_oracle_sample(cfg, args.oracle_iters, pn, bed, y)
@@ -471,7 +474,7 @@ def cv_arm(args):
     ev0 = torch.cuda.Event(enable_timing=True)
     ev1 = torch.cuda.Event(enable_timing=True)
     ev0.record(stream)
-    solves, its, cols, grad_ms, grad_n, statuses = 0, 0, 0, 0.0, 0, []
+    solves, its, cols, grad_ms, grad_n, statuses, replays = 0, 0, 0, 0.0, 0, [], 0
     for _ in range(args.steps):
         res = iht.iht_fit_batch(ds, probs, profile=1, **kw)
         solves += b
@@ -479,6 +482,7 @@ def cv_arm(args):
         cols += sum(max(r.iterations, 1) for r in res)
         grad_ms += res[0].grad_ms
         grad_n += res[0].grad_launches
+        replays += res[0].graph_replays
         statuses += [r.status for r in res]
     ev1.record(stream)
     torch.cuda.synchronize(dev)
@@ -554,6 +558,8 @@ def cv_arm(args):
                     "d2h_bytes_per_step": int(12 * ktot)},
             "gpu_launches": int(launches), "clocks": clk,
             "statuses": sorted(set(int(s) for s in statuses)),
+            "graph_replays_per_step": replays / max(args.steps, 1),
+            "pass_shapes": iht.tuning_summary().strip().splitlines(),
         }
         if not args.no_cpu_baseline and world == 1:
             out["cpu_baseline"] = cv_reference(args, c, pn, bed, y, train, its / max(solves, 1))
@@ -605,7 +611,7 @@ def panel_arm(args):
     ev0 = torch.cuda.Event(enable_timing=True)
     ev1 = torch.cuda.Event(enable_timing=True)
     ev0.record(stream)
-    solves, its, cols, grad_ms, grad_n, statuses = 0, 0, 0, 0.0, 0, []
+    solves, its, cols, grad_ms, grad_n, statuses, replays = 0, 0, 0, 0.0, 0, [], 0
     for _ in range(args.steps):
         res = iht.iht_fit_batch(ds, probs, profile=1, **kw)
         solves += b
@@ -613,6 +619,7 @@ def panel_arm(args):
         cols += sum(max(r.iterations, 1) for r in res)
         grad_ms += res[0].grad_ms
         grad_n += res[0].grad_launches
+        replays += res[0].graph_replays
         statuses += [r.status for r in res]
     ev1.record(stream)
     torch.cuda.synchronize(dev)
@@ -671,6 +678,8 @@ def panel_arm(args):
                     "h2d_bytes_per_step": 8 * n * b, "d2h_bytes_per_step": 12 * k * b},
             "gpu_launches": int(launches), "clocks": clk,
             "statuses": sorted(set(int(s) for s in statuses)),
+            "graph_replays_per_step": replays / max(args.steps, 1),
+            "pass_shapes": iht.tuning_summary().strip().splitlines(),
         }
         if not args.no_cpu_baseline and world == 1:
             import oracle

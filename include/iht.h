@@ -71,7 +71,7 @@ typedef struct iht_result {
     double mu;             /* last accepted step size                          */
     double grad_ms;        /* total device time of the gradient launches (profile = 1) */
     int32_t grad_launches; /* gradient launches timed                          */
-    int32_t reserved2;
+    int32_t graph_replays; /* iterations run as one CUDA graph replay          */
 } iht_result;
 
 /* Optional per-iteration record of iht_fit_trace (host arrays; any may be NULL).
@@ -282,6 +282,51 @@ int iht_fit_batch(iht_dataset *ds, int32_t b, const iht_solve_desc *solves,
  *               column, 2 the multi-column tensor-core pass always. */
 int iht_gradient_batch(iht_dataset *ds, int32_t b, const int32_t *const *rows_list,
                        const int64_t *n_rows, const float *R, float *G_out, int impl);
+
+/* Launch shapes of the gradient passes and their autotuner.
+ *
+ * The tensor-core gradient passes (Sec. 2.2's g = Z^T r, one or many residual
+ * columns) have staging knobs that change how genotype and residual tiles are
+ * buffered, never the arithmetic or its order, so every shape writes the same
+ * bits.  The first pass of a kind on a dataset shape (device, padded samples,
+ * SNPs; for the multi-column pass also the accumulator-width bucket, 16..64,
+ * 80..128, 144..192 or 208..224 accumulator columns, 5 per residual column)
+ * runs every candidate shape on its real inputs, timed with CUDA events, and
+ * caches the fastest for the life of the process; later passes, including
+ * those captured into CUDA graphs, use the cached shape.  A pass launched
+ * while its stream is being captured, or with tuning off, uses the cached
+ * shape or else a fixed default.
+ *
+ * kind IHT_PASS_SINGLE (one residual column), params[0]: TMA stages per
+ * warpgroup, 2 .. as many as shared memory holds beside the residual image.
+ * kind IHT_PASS_MULTI (ncols residual columns in one pass), params[0]:
+ * genotype stages 2..8; params[1]: 1 = each decoder step fills a pair of A
+ * buffers (needs four or more buffers: 192 accumulator columns at most);
+ * params[2]: 1 = missing-call finalisation over 8 columns per block (when
+ * more than 4 columns and shared memory holds 32 (n_pad + 1) bytes). */
+enum { IHT_PASS_SINGLE = 0, IHT_PASS_MULTI = 1 };
+
+/* Tuning on (default) or off; IHT_AUTOTUNE=0 in the environment starts it off. */
+void iht_set_autotune(int on);
+
+/* Forgets every cached shape. */
+void iht_tune_clear(void);
+
+/* Pins the shape of passes of `kind` over ncols columns on this dataset
+ * (params: host int32[nparams], nparams 1 for SINGLE, 3 for MULTI).  EINVAL for
+ * a shape that does not fit the pass or an unknown kind. */
+int iht_tune_pin(const iht_dataset *ds, int32_t kind, int32_t ncols, const int32_t *params,
+                 int32_t nparams);
+
+/* Cached shape of passes of `kind` over ncols columns on this dataset into
+ * params (host int32[nparams]); EAGAIN when none is cached yet. */
+int iht_tune_query(const iht_dataset *ds, int32_t kind, int32_t ncols, int32_t *params,
+                   int32_t nparams);
+
+/* Text listing of the cache, one line per entry.  buf NULL: returns the bytes
+ * needed (with the terminating 0); otherwise writes at most buf_bytes bytes
+ * (truncated, 0-terminated) and returns OK. */
+int iht_tuning_summary(char *buf, size_t buf_bytes);
 
 /* a8 -- continuous-batching IHT server on one dataset.
  *

@@ -20,6 +20,7 @@ LIB_PATH = os.path.join(_HERE, "libiht.so")
 IHT_OK, IHT_EINVAL, IHT_ENOMEM, IHT_ENOTCONV, IHT_ENUMERIC, IHT_ETIMEOUT, IHT_ECUDA, IHT_EAGAIN = \
     range(8)
 IHT_HOST, IHT_DEVICE = 0, 1
+IHT_PASS_SINGLE, IHT_PASS_MULTI = 0, 1
 
 EXPORTED = ["iht_default_options", "iht_strerror", "iht_last_cuda_error", "iht_kernel_launches",
             "iht_create",
@@ -28,7 +29,8 @@ EXPORTED = ["iht_default_options", "iht_strerror", "iht_last_cuda_error", "iht_k
             "iht_fit_trace", "iht_fit_batch", "iht_gradient_batch", "iht_server_default_options",
             "iht_server_create", "iht_server_submit", "iht_server_poll", "iht_server_get_stats",
             "iht_server_destroy", "iht_state_bytes", "iht_state_save", "iht_state_load",
-            "iht_fit_resume"]
+            "iht_fit_resume", "iht_set_autotune", "iht_tune_clear", "iht_tune_pin", "iht_tune_query",
+            "iht_tuning_summary"]
 
 
 class IhtError(RuntimeError):
@@ -52,7 +54,7 @@ class iht_result(ctypes.Structure):
                 ("backtracks", ctypes.c_int32), ("reserved", ctypes.c_int32),
                 ("objective", ctypes.c_double), ("mu", ctypes.c_double),
                 ("grad_ms", ctypes.c_double), ("grad_launches", ctypes.c_int32),
-                ("reserved2", ctypes.c_int32)]
+                ("graph_replays", ctypes.c_int32)]
 
 
 class iht_trace(ctypes.Structure):
@@ -140,6 +142,11 @@ def _lib(build_if_stale: bool = True):
                                           ctypes.POINTER(iht_result)]),
         "iht_fit_resume": (ctypes.c_int, [P, P, i64, P, P, sz, ctypes.POINTER(iht_options), P, P,
                                           ctypes.POINTER(iht_result)]),
+        "iht_set_autotune": (None, [ctypes.c_int]),
+        "iht_tune_clear": (None, []),
+        "iht_tune_pin": (ctypes.c_int, [P, i32, i32, P, i32]),
+        "iht_tune_query": (ctypes.c_int, [P, i32, i32, P, i32]),
+        "iht_tuning_summary": (ctypes.c_int, [P, sz]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -322,6 +329,7 @@ class FitResult:
     grad_ms: float = 0.0
     grad_launches: int = 0
     beta_s: object = None
+    graph_replays: int = 0
 
 
 def _fit(ds: Dataset, y, k: int, rows, opts: iht_options, trace: bool, state: bytes = None):
@@ -374,7 +382,7 @@ def _fit(ds: Dataset, y, k: int, rows, opts: iht_options, trace: bool, state: by
     if tr is not None:
         tr = {f: a[:res.iterations] for f, a in tr.items()}
     return FitResult(beta, supp, res.iterations, rc, res.backtracks, res.objective, res.mu, tr,
-                     res.grad_ms, res.grad_launches)
+                     res.grad_ms, res.grad_launches, None, res.graph_replays)
 
 
 def iht_fit(ds: Dataset, y, k: int, rows=None, **opt) -> FitResult:
@@ -448,6 +456,45 @@ def iht_fit_resume(ds: Dataset, y, state: bytes, rows=None, **opt) -> FitResult:
     o = iht_default_options(**opt)
     o.out_mem = IHT_DEVICE if out_device else IHT_HOST
     return _fit(ds, y, load_state(state).k, rows, o, trace=False, state=state)
+
+
+def set_autotune(on: bool) -> None:
+    """Turn the gradient passes' shape tuning on or off (iht_set_autotune)."""
+    _lib().iht_set_autotune(1 if on else 0)
+
+
+def tune_clear() -> None:
+    """Forget every cached pass shape (iht_tune_clear)."""
+    _lib().iht_tune_clear()
+
+
+def _nparams(kind: int) -> int:
+    return 1 if kind == IHT_PASS_SINGLE else 3
+
+
+def tune_pin(ds: Dataset, kind: int, ncols: int, params) -> None:
+    """Pin the launch shape of passes of `kind` over ncols columns (iht_tune_pin)."""
+    a = np.ascontiguousarray(params, dtype=np.int32)
+    _check(_lib().iht_tune_pin(ds.h, kind, ncols, a.ctypes.data, a.size), "iht_tune_pin")
+
+
+def tune_query(ds: Dataset, kind: int, ncols: int):
+    """Cached shape of passes of `kind` over ncols columns as a tuple, or None."""
+    a = np.zeros(_nparams(kind), np.int32)
+    rc = _lib().iht_tune_query(ds.h, kind, ncols, a.ctypes.data, a.size)
+    if rc == IHT_EAGAIN:
+        return None
+    _check(rc, "iht_tune_query")
+    return tuple(int(v) for v in a)
+
+
+def tuning_summary() -> str:
+    """The tuned / pinned shapes of this process, one line each (iht_tuning_summary)."""
+    L = _lib()
+    need = L.iht_tuning_summary(None, 0)
+    buf = ctypes.create_string_buffer(max(need, 1))
+    _check(L.iht_tuning_summary(buf, len(buf)), "iht_tuning_summary")
+    return buf.value.decode()
 
 
 def iht_fit_trace(ds: Dataset, y, k: int, rows=None, **opt) -> FitResult:
@@ -526,7 +573,7 @@ def iht_fit_batch(ds: Dataset, problems, out_device: bool = False, dense: bool =
         r = infos[c]
         out.append(FitResult(None if betas is None else betas[c], supp[off:off + ks[c]],
                              r.iterations, r.status, r.backtracks, r.objective, r.mu, None,
-                             r.grad_ms, r.grad_launches, bsv[off:off + ks[c]]))
+                             r.grad_ms, r.grad_launches, bsv[off:off + ks[c]], r.graph_replays))
         off += ks[c]
     return out
 

@@ -457,7 +457,7 @@ static int fit_impl(iht_dataset *ds, const int32_t *rows, int64_t n_rows, const 
         info->mu = h.mu;
         info->grad_ms = opt.profile ? ws->prof_ms : 0.0;
         info->grad_launches = opt.profile ? ws->nprof : 0;
-        info->reserved2 = 0;
+        info->graph_replays = ws->graph_replays;
     }
     return h.status;
 }

@@ -9,15 +9,27 @@
 // blocks of the tail kernels return at once.  Row sets shared by several
 // solves (a cross-validation fold used along a path of model sizes) have
 // their per-SNP statistics computed once (Sec. 2.3.2).
+//
+// An iteration whose active solves are those of the previous iteration is one
+// replay of a CUDA graph (the gradient pass, candidates, g_S, Z_S g_S and two
+// attempts; the second attempt's kernels return at once for every solve whose
+// first step was accepted), with one host synchronisation.  Graphs are cached
+// per active set, so the replays of a repeated batch start at its second
+// iteration; an iteration after a solve retires runs as direct launches.
 #include <stdlib.h>
 #include <string.h>
 
 #include <new>
+#include <string>
+#include <unordered_map>
 #include <vector>
 
 #include "common.cuh"
 
 namespace iht {
+
+constexpr int kBatchGraphPairs = 32;       // gradient passes timed per replay (1408 columns)
+constexpr size_t kBatchGraphs = 64;        // cached iteration graphs per workspace
 
 struct BatchWork {
     int nb = 0, kcap = 0, nsets = 0;       // capacities
@@ -41,6 +53,17 @@ struct BatchWork {
     int32_t *rows_dev = nullptr;           // staged host row lists
     double *ybuf = nullptr;                // staged host phenotypes
     cudaEvent_t ev[2 * kProfEvents] = {};
+    // iteration graphs, keyed by sizes, scratch identities and the active set
+    struct Graph {
+        cudaGraphExec_t exec = nullptr;
+        int launches = 0;                  // kernels per replay
+        int pairs = 0;                     // gradient event pairs per replay
+        uint64_t used = 0;                 // last use (least recently used is replaced)
+    };
+    std::unordered_map<std::string, Graph> graphs;
+    uint64_t graph_clock = 0;
+    cudaStream_t cap_stream = nullptr;
+    cudaEvent_t gev[2 * kBatchGraphPairs] = {};
 };
 
 void free_batchwork(BatchWork *w)
@@ -57,6 +80,11 @@ void free_batchwork(BatchWork *w)
         if (p) cudaFreeHost(p);
     for (cudaEvent_t e : w->ev)
         if (e) cudaEventDestroy(e);
+    for (auto &kv : w->graphs)
+        if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
+    for (cudaEvent_t e : w->gev)
+        if (e) cudaEventDestroy(e);
+    if (w->cap_stream) cudaStreamDestroy(w->cap_stream);
     delete w;
 }
 
@@ -222,6 +250,27 @@ static int build_sets(iht_dataset *ds, BatchWork *w, const std::vector<SetKey> &
     return IHT_OK;
 }
 
+// Column descriptors of the listed solves, uploaded for the multi-column pass.
+static int batch_cols(iht_dataset *ds, BatchWork *w, const std::vector<int> &act,
+                      const std::vector<int> &set_of)
+{
+    const size_t np = (size_t)ds->n_pad, p = (size_t)ds->p;
+    for (size_t a = 0; a < act.size(); ++a) {
+        const int c = act[a];
+        const RowSet rs = batch_rowset(ds, w, set_of[c]);
+        MrCol &C = w->cols_host[a];
+        C.r32 = w->r32 + c * np;
+        C.u32 = rs.u32;
+        C.v32 = rs.v32;
+        C.g = w->g + c * p;
+        C.scale = 0.0f;
+        C.R = 0.0f;
+    }
+    IHT_CUDA(cudaMemcpyAsync(w->cols, w->cols_host, sizeof(MrCol) * act.size(), cudaMemcpyHostToDevice,
+                             ds->ctx->stream));
+    return IHT_OK;
+}
+
 // Gradient of the listed solves (impl 0/2: one multi-column pass; 1: one
 // CUDA-core pass per solve).
 static int batch_grad(iht_dataset *ds, BatchWork *w, const std::vector<int> &act,
@@ -240,20 +289,103 @@ static int batch_grad(iht_dataset *ds, BatchWork *w, const std::vector<int> &act
         }
         return IHT_OK;
     }
-    for (size_t a = 0; a < act.size(); ++a) {
-        const int c = act[a];
-        const RowSet rs = batch_rowset(ds, w, set_of[c]);
-        MrCol &C = w->cols_host[a];
-        C.r32 = w->r32 + c * np;
-        C.u32 = rs.u32;
-        C.v32 = rs.v32;
-        C.g = w->g + c * p;
-        C.scale = 0.0f;
-        C.R = 0.0f;
-    }
-    IHT_CUDA(cudaMemcpyAsync(w->cols, w->cols_host, sizeof(MrCol) * act.size(),
-                             cudaMemcpyHostToDevice, s));
+    int rc = batch_cols(ds, w, act, set_of);
+    if (rc) return rc;
     return launch_grad_mrhs(ds, w->cols, (int)act.size(), prof, impl == 2 ? nullptr : w->cols_host);
+}
+
+// One backtracking attempt of every solve that takes part (first: the
+// iteration's first attempt; else only solves whose last candidate was
+// rejected): projection, candidate residual, decision, centring.
+static int batch_attempt(iht_dataset *ds, BatchWork *w, int b, int kmax, bool first)
+{
+    int rc;
+    if ((rc = launch_merge_batch(ds, w->bs, b, first))) return rc;
+    if ((rc = launch_zmul_batch(ds, w->bs, b, kmax, kZmulResidual))) return rc;
+    if ((rc = launch_decide_batch(ds, w->bs, b))) return rc;
+    return launch_center_batch(ds, w->bs, b, false);
+}
+
+// Candidates, g_S and Z_S g_S after the gradient.
+static int batch_step(iht_dataset *ds, BatchWork *w, int b, int kmax)
+{
+    int rc;
+    if ((rc = select_topk_batch(ds->ctx, w->jobs + b, b, ds->p))) return rc;
+    if ((rc = launch_gather_gS_batch(ds, w->bs, b))) return rc;
+    return launch_zmul_batch(ds, w->bs, b, kmax, kZmulStep);
+}
+
+// The graph of one iteration over the active solves act (multi-column
+// gradient; w->cols uploaded by the caller before every replay), captured on
+// the workspace's private stream (the caller's may be the legacy default
+// stream) and cached under a key of everything its launches were captured
+// with: sizes, options, the thread's pass scratch and, per active solve, its
+// index and the column pointers the single-column pass takes from the host.
+static int batch_graph(iht_dataset *ds, BatchWork *w, int b, int kmax, int impl, bool prof,
+                       const std::vector<int> &act, BatchWork::Graph **out)
+{
+    std::vector<uint64_t> key = {(uint64_t)b, (uint64_t)kmax, (uint64_t)impl, (uint64_t)prof,
+                                 grad_mrhs_scratch_id(), grad_tc_scratch_id(), act.size()};
+    for (size_t a = 0; a < act.size(); ++a) {
+        const MrCol &C = w->cols_host[a];
+        key.insert(key.end(), {(uint64_t)act[a], (uint64_t)(uintptr_t)C.r32, (uint64_t)(uintptr_t)C.u32,
+                               (uint64_t)(uintptr_t)C.v32, (uint64_t)(uintptr_t)C.g});
+    }
+    std::string k(reinterpret_cast<const char *>(key.data()), key.size() * sizeof(uint64_t));
+    auto it = w->graphs.find(k);
+    if (it != w->graphs.end()) {
+        it->second.used = ++w->graph_clock;
+        *out = &it->second;
+        return IHT_OK;
+    }
+    if (w->graphs.size() >= kBatchGraphs) {        // replace the least recently used
+        auto lru = w->graphs.begin();
+        for (auto g = w->graphs.begin(); g != w->graphs.end(); ++g)
+            if (g->second.used < lru->second.used) lru = g;
+        cudaGraphExecDestroy(lru->second.exec);
+        w->graphs.erase(lru);
+    }
+    if (!w->cap_stream) IHT_CUDA(cudaStreamCreateWithFlags(&w->cap_stream, cudaStreamNonBlocking));
+    if (prof && !w->gev[0])
+        for (cudaEvent_t &e : w->gev) IHT_CUDA(cudaEventCreate(&e));
+    ProfEvents pe;
+    pe.ev = w->gev;
+    pe.cap = prof ? kBatchGraphPairs : 0;
+    cudaStream_t user = ds->ctx->stream;
+    ds->ctx->stream = w->cap_stream;
+    const uint64_t before = launches_noted();
+    cudaError_t e = cudaStreamBeginCapture(w->cap_stream, cudaStreamCaptureModeThreadLocal);
+    int rc = IHT_OK;
+    if (e == cudaSuccess) {
+        rc = launch_grad_mrhs(ds, w->cols, (int)act.size(), prof ? &pe : nullptr,
+                              impl == 2 ? nullptr : w->cols_host);
+        if (!rc) rc = batch_step(ds, w, b, kmax);
+        for (int attempt = 0; !rc && attempt < 2; ++attempt) rc = batch_attempt(ds, w, b, kmax, attempt == 0);
+    }
+    cudaGraph_t graph = nullptr;
+    const cudaError_t e2 = e == cudaSuccess ? cudaStreamEndCapture(w->cap_stream, &graph) : e;
+    ds->ctx->stream = user;
+    const int n = (int)(launches_noted() - before);
+    note_launch(-n);                                  // captured, not run
+    if (rc == IHT_OK && e2 != cudaSuccess) {
+        set_cuda_error(e2, "batch iteration capture");
+        rc = IHT_ECUDA;
+    }
+    BatchWork::Graph g;
+    if (rc == IHT_OK) {
+        e = cudaGraphInstantiate(&g.exec, graph, 0);
+        if (e != cudaSuccess) {
+            set_cuda_error(e, "batch iteration graph instantiate");
+            rc = IHT_ECUDA;
+        }
+    }
+    if (graph) cudaGraphDestroy(graph);
+    if (rc) return rc;
+    g.launches = n;
+    g.pairs = pe.n;
+    g.used = ++w->graph_clock;
+    *out = &(w->graphs[k] = g);
+    return IHT_OK;
 }
 
 }  // namespace iht
@@ -411,31 +543,47 @@ int iht_fit_batch(iht_dataset *ds, int32_t b, const iht_solve_desc *solves,
     if ((rc = select_topk_batch(ds->ctx, w->jobs, b, ds->p))) return rc;
     IHT_CUDA(cudaMemsetAsync(w->bS, 0, sizeof(double) * b * K, s));
 
+    double graph_ms = 0.0;
+    int graph_pairs = 0, replays = 0;
+    std::vector<int> prev;
     for (int it = 0; it < opt.max_iter && !act.empty(); ++it) {
-        if (it > 0 && (rc = grad(act))) return rc;
-        if ((rc = select_topk_batch(ds->ctx, w->jobs + b, b, ds->p))) return rc;
-        if ((rc = launch_gather_gS_batch(ds, w->bs, b))) return rc;
-        if ((rc = launch_zmul_batch(ds, w->bs, b, kmax, kZmulStep))) return rc;
-        for (int attempt = 0;; ++attempt) {
-            if ((rc = launch_merge_batch(ds, w->bs, b, attempt == 0))) return rc;
-            if ((rc = launch_zmul_batch(ds, w->bs, b, kmax, kZmulResidual))) return rc;
-            if ((rc = launch_decide_batch(ds, w->bs, b))) return rc;
-            if ((rc = launch_center_batch(ds, w->bs, b, false))) return rc;
+        BatchWork::Graph *gr = nullptr;
+        if (it > 0 && opt.grad_impl != 1 && act == prev) {
+            // same active solves as the last iteration: one replay
+            if ((rc = batch_cols(ds, w, act, set_of))) return rc;
+            if ((rc = batch_graph(ds, w, b, kmax, opt.grad_impl, prof, act, &gr))) return rc;
+            IHT_CUDA(cudaGraphLaunch(gr->exec, s));
+            note_launch(gr->launches);
+            ++replays;
+        } else {
+            if (it > 0 && (rc = grad(act))) return rc;
+            if ((rc = batch_step(ds, w, b, kmax))) return rc;
+            if ((rc = batch_attempt(ds, w, b, kmax, true))) return rc;
+        }
+        for (;;) {
             IHT_CUDA(cudaMemcpyAsync(w->sc_host, w->sc, sizeof(Scalars) * b, cudaMemcpyDeviceToHost, s));
             IHT_CUDA(cudaStreamSynchronize(s));
             bool again = false;
             for (int c : act) again |= !w->sc_host[c].done && w->sc_host[c].live && w->sc_host[c].retry;
             if (!again) break;
+            if ((rc = batch_attempt(ds, w, b, kmax, false))) return rc;
         }
+        for (int e = 0; gr && prof && e < gr->pairs; ++e) {     // the replay's gradient passes
+            float ms = 0.0f;
+            IHT_CUDA(cudaEventElapsedTime(&ms, w->gev[2 * e], w->gev[2 * e + 1]));
+            graph_ms += ms;
+            ++graph_pairs;
+        }
+        prev = act;
         active();
     }
     int timed_out = 0, tc_timed_out = 0;
     if (opt.grad_impl != 1 && (rc = grad_mrhs_status(ds, &timed_out))) return rc;
     if (opt.grad_impl == 0 && (rc = grad_tc_status(ds, &tc_timed_out))) return rc;
     if (timed_out || tc_timed_out) return IHT_ETIMEOUT;
-    double grad_ms = 0.0;
-    const int nprof = pe.n;
-    for (int e = 0; prof && e < nprof; ++e) {
+    double grad_ms = graph_ms;
+    const int nprof = pe.n + graph_pairs;
+    for (int e = 0; prof && e < pe.n; ++e) {
         float ms = 0.0f;
         IHT_CUDA(cudaEventElapsedTime(&ms, w->ev[2 * e], w->ev[2 * e + 1]));
         grad_ms += ms;
@@ -483,7 +631,7 @@ int iht_fit_batch(iht_dataset *ds, int32_t b, const iht_solve_desc *solves,
             r.mu = h.mu;
             r.grad_ms = prof ? grad_ms : 0.0;
             r.grad_launches = prof ? nprof : 0;
-            r.reserved2 = 0;
+            r.graph_replays = replays;
         }
     }
     return IHT_OK;

@@ -15,6 +15,7 @@
 //   g        float[p]           standardised gradient Z^T r.
 #pragma once
 #include <cuda_runtime.h>
+#include <vector>
 #include <stdint.h>
 
 #include <algorithm>
@@ -76,14 +77,23 @@ struct ProfEvents {
     int cap = 0;                       // pairs available
     int n = 0;                         // pairs recorded
 };
+// Inside a stream capture the records are external, so they become event
+// nodes of the graph (recorded again on every replay).
+inline unsigned prof_flags(cudaStream_t s)
+{
+    cudaStreamCaptureStatus st = cudaStreamCaptureStatusNone;
+    return cudaStreamIsCapturing(s, &st) == cudaSuccess && st == cudaStreamCaptureStatusActive
+               ? cudaEventRecordExternal
+               : cudaEventRecordDefault;
+}
 inline void prof_begin(ProfEvents *pe, cudaStream_t s)
 {
-    if (pe && pe->n < pe->cap) cudaEventRecord(pe->ev[2 * pe->n], s);
+    if (pe && pe->n < pe->cap) cudaEventRecordWithFlags(pe->ev[2 * pe->n], s, prof_flags(s));
 }
 inline void prof_end(ProfEvents *pe, cudaStream_t s)
 {
     if (pe && pe->n < pe->cap) {
-        cudaEventRecord(pe->ev[2 * pe->n + 1], s);
+        cudaEventRecordWithFlags(pe->ev[2 * pe->n + 1], s, prof_flags(s));
         ++pe->n;
     }
 }
@@ -188,6 +198,7 @@ struct Workspace {
     uint64_t iter_key[8] = {};
     int iter_launches = 0;                 // kernel launches per replay
     cudaEvent_t gev[2] = {};               // around the gradient pass inside the graph
+    int graph_replays = 0;                 // iterations of the last solve run as replays
     BatchWork *bw = nullptr;               // batched solves (batch.cu)
 };
 constexpr int kProfEvents = 256;
@@ -262,6 +273,39 @@ int launch_grad_mrhs(iht_dataset *ds, MrCol *cols_dev, int ncols, ProfEvents *pr
                      const MrCol *cols_host = nullptr);
 int grad_mrhs_status(iht_dataset *ds, int *timed_out);
 void grad_mrhs_release_thread();
+uint64_t grad_mrhs_scratch_id();
+// tune.cu: cached launch shapes of the gradient passes (kind IHT_PASS_SINGLE /
+// IHT_PASS_MULTI; bucket 0 for the single-column pass, else the largest
+// accumulator width of the multi-column bucket)
+constexpr int kTuneParams = 4;
+bool autotune_enabled();
+bool tune_lookup(const iht_dataset *ds, int kind, int bucket, int *params);
+void tune_store(const iht_dataset *ds, int kind, int bucket, const int *params, double ms, int candidates);
+bool stream_capturing(cudaStream_t s);
+bool grad_tc_shape_fits(const iht_dataset *ds, const int *params);
+bool grad_mrhs_shape_fits(int ncols, const int *params);
+int grad_mrhs_bucket(int ncols);
+// Events of one tuning run, destroyed with the set.
+struct TuneEvents {
+    std::vector<cudaEvent_t> ev;
+    explicit TuneEvents(size_t n) : ev(n, nullptr) {}
+    ~TuneEvents()
+    {
+        for (cudaEvent_t e : ev)
+            if (e) cudaEventDestroy(e);
+    }
+    cudaError_t create()
+    {
+        for (cudaEvent_t &e : ev)
+            if (cudaError_t r = cudaEventCreate(&e)) return r;
+        return cudaSuccess;
+    }
+    float ms(size_t a, size_t b) const
+    {
+        float t = 0.0f;
+        return cudaEventElapsedTime(&t, ev[a], ev[b]) == cudaSuccess ? t : 1e30f;
+    }
+};
 // select.cu
 struct SelJob {                        // one problem of a batched top-K
     const float *keys;

@@ -770,18 +770,65 @@ static int mr_ksteps(const iht_dataset *ds)
 
 static int mr_n(int ncols) { return (kMrLimbs * ncols + 15) / 16 * 16; }
 
-// Genotype stages: with few accumulator columns the pass streams genotypes as
-// fast as it decodes them and wants many bytes in flight; with many, B chunks
-// need the room (the pass is tensor-bound there).
-static int mr_gstages(int N) { return N <= 96 ? kMrMaxGStages : 4; }
+// Launch shape of a pass: staging only, so every shape writes the same bits.
+struct MrShape {
+    int ngs;      // genotype stages (2 tiles x 8 KB each)
+    int pairs;    // 1: each decoder step fills a pair of A buffers
+    int fin8;     // 1: missing-call finalisation over 8 columns per block
+};
 
-static size_t mr_gbytes(int N) { return (size_t)mr_gstages(N) * kMrTiles * kMrGTile; }
-
-static int mr_bstages(int N)
+// B stages and A buffers of shape sh at N accumulator columns (false: it does
+// not fit).  B stages: as many chunks as shared memory holds beside the
+// genotype stages, up to kMrMaxBStages.
+static bool mr_shape_launch(int N, const MrShape &sh, int *nbst, int *nbufs)
 {
+    if (sh.ngs < 2 || sh.ngs > kMrMaxGStages || sh.pairs < 0 || sh.pairs > 1 || sh.fin8 < 0 || sh.fin8 > 1)
+        return false;
+    const size_t gb = (size_t)sh.ngs * kMrTiles * kMrGTile;
     const size_t chunk = (size_t)kMrChunkSteps * N * 32;
-    const size_t room = kMrSmemMax - mr_gbytes(N);
-    return (int)std::min<size_t>(kMrMaxBStages, room / chunk);
+    if (gb + 2 * chunk > kMrSmemMax) return false;
+    int nb = std::min(kMrMaxBufs, (256 - N) / 16);
+    if (sh.pairs) {
+        if (nb < 4) return false;
+        nb &= ~1;
+    }
+    if (nb < 2) return false;
+    *nbst = (int)std::min<size_t>(kMrMaxBStages, (kMrSmemMax - gb) / chunk);
+    *nbufs = nb;
+    return true;
+}
+
+// Default shape: with few accumulator columns the pass streams genotypes as
+// fast as it decodes them and wants many bytes in flight; with many, B chunks
+// need the room (the pass is tensor-bound there).  Pairs whenever there are
+// four or more A buffers.
+static MrShape mr_default_shape(int N) { return MrShape{N <= 96 ? kMrMaxGStages : 4, 1, 1}; }
+
+// A cached shape made to fit N (pairs dropped when there are too few buffers;
+// the default when the stages do not fit).
+static MrShape mr_fit_shape(int N, MrShape sh, int *nbst, int *nbufs)
+{
+    if (mr_shape_launch(N, sh, nbst, nbufs)) return sh;
+    sh.pairs = 0;
+    if (mr_shape_launch(N, sh, nbst, nbufs)) return sh;
+    sh = mr_default_shape(N);
+    if (mr_shape_launch(N, sh, nbst, nbufs)) return sh;
+    sh.pairs = 0;
+    mr_shape_launch(N, sh, nbst, nbufs);             // 4 stages + 2 chunks fit at any N <= kMrMaxN
+    return sh;
+}
+
+// Tuning buckets of accumulator widths: 16..64, 80..128, 144..192 (pairs
+// possible) and 208..224.
+static int mr_bucket_of(int N) { return N <= 64 ? 64 : N <= 128 ? 128 : N <= 192 ? 192 : kMrMaxN; }
+
+int grad_mrhs_bucket(int ncols) { return mr_bucket_of(mr_n(std::min(ncols, kMrMaxCols))); }
+
+bool grad_mrhs_shape_fits(int ncols, const int *params)
+{
+    int nbst, nbufs;
+    return mr_shape_launch(mr_n(std::min(ncols, kMrMaxCols)), MrShape{params[0], params[1], params[2]}, &nbst,
+                           &nbufs);
 }
 
 int mrhs_max_cols() { return kMrMaxCols; }
@@ -818,7 +865,11 @@ template <int CG, typename IdxT, bool kStage>
 static int mr_launch_finalize(iht_dataset *ds, const MrCol *cols, int ncols, size_t smem)
 {
     auto kern = k_miss_finalize<CG, IdxT, kStage>;
-    if (smem > 48 * 1024) IHT_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    static thread_local int configured_dev = -1;          // limit raised once (not during a capture)
+    if (configured_dev != ds->ctx->device) {
+        IHT_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+        configured_dev = ds->ctx->device;
+    }
     const int groups = (ncols + CG - 1) / CG;
     const int per_sm = smem > 110 * 1024 ? 1 : 2;
     // one wave: at most per_sm resident blocks on every SM
@@ -837,7 +888,11 @@ template <typename IdxT>
 static int mr_launch_finalize8(iht_dataset *ds, const MrCol *cols, int ncols, size_t smem)
 {
     auto kern = k_miss_finalize8<IdxT>;
-    IHT_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    static thread_local int configured_dev = -1;
+    if (configured_dev != ds->ctx->device) {
+        IHT_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFin8SmemMax));
+        configured_dev = ds->ctx->device;
+    }
     const int groups = (ncols + 7) / 8;
     // one wave: one block per SM (the table takes most of shared memory)
     const int gx = (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(ds->p, kFin8Threads / 2),
@@ -850,10 +905,10 @@ static int mr_launch_finalize8(iht_dataset *ds, const MrCol *cols, int ncols, si
 }
 
 template <typename IdxT>
-static int mr_finalize(iht_dataset *ds, const MrCol *cols, int ncols)
+static int mr_finalize(iht_dataset *ds, const MrCol *cols, int ncols, bool fin8)
 {
     const size_t f8 = 32 * ((size_t)ds->n_pad + 1);
-    if (ncols > 4 && f8 <= kFin8SmemMax) return mr_launch_finalize8<IdxT>(ds, cols, ncols, f8);
+    if (fin8 && ncols > 4 && f8 <= kFin8SmemMax) return mr_launch_finalize8<IdxT>(ds, cols, ncols, f8);
     const size_t f = sizeof(float) * (size_t)ds->n_pad;
     if (4 * f <= 200 * 1024) return mr_launch_finalize<4, IdxT, true>(ds, cols, ncols, 4 * f);
     if (2 * f <= 200 * 1024) return mr_launch_finalize<2, IdxT, true>(ds, cols, ncols, 2 * f);
@@ -861,11 +916,86 @@ static int mr_finalize(iht_dataset *ds, const MrCol *cols, int ncols)
     return mr_launch_finalize<1, IdxT, false>(ds, cols, ncols, 0);
 }
 
+// One pass of nc <= kMrMaxCols columns after its limbs are staged.
+struct MrPass {
+    iht_dataset *ds;
+    const CUtensorMap *map;
+    int grid, ksteps, N, nc;
+    MrCol *cols;
+};
+
+// The multi-column pass and its finalisation in shape sh; with events, ev[e0],
+// ev[e0 + 1] bracket the pass and ev[e0 + 2], ev[e0 + 3] the finalisation.
+static int mr_pass(const MrPass &P, MrShape sh, const TuneEvents *te, size_t e0, ProfEvents *prof)
+{
+    cudaStream_t s = P.ds->ctx->stream;
+    int nbst = 0, nbufs = 0;
+    sh = mr_fit_shape(P.N, sh, &nbst, &nbufs);
+    // at least 116 KB, so one CTA per SM: the kernel allocates all 512 columns of tensor memory
+    const size_t smem = std::max<size_t>(116 * 1024, (size_t)sh.ngs * kMrTiles * kMrGTile +
+                                                         (size_t)nbst * kMrChunkSteps * P.N * 32);
+    // D FP32, A E5M2, B E4M3, K-major, N, M = 128
+    const uint32_t idesc = (1u << 4) | (1u << 7) | ((uint32_t)(P.N >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
+    if (te) IHT_CUDA(cudaEventRecord(te->ev[e0], s));
+    prof_begin(prof, s);
+    auto kern = sh.pairs ? k_grad_mrhs<true> : k_grad_mrhs<false>;
+    kern<<<P.grid, kMrThreads, smem, s>>>(*P.map, P.ds->p, P.ksteps, P.N, P.nc, nbufs, nbst, sh.ngs, g_mr.bimg,
+                                          P.cols, idesc, g_mr.err);
+    note_launch();
+    IHT_CUDA(cudaGetLastError());
+    prof_end(prof, s);
+    if (te) IHT_CUDA(cudaEventRecord(te->ev[e0 + 1], s));
+    if (te) IHT_CUDA(cudaEventRecord(te->ev[e0 + 2], s));
+    const int rc = P.ds->miss_idx16 ? mr_finalize<uint16_t>(P.ds, P.cols, P.nc, sh.fin8 != 0)
+                                    : mr_finalize<int32_t>(P.ds, P.cols, P.nc, sh.fin8 != 0);
+    if (rc) return rc;
+    if (te) IHT_CUDA(cudaEventRecord(te->ev[e0 + 3], s));
+    return IHT_OK;
+}
+
+// First pass of a bucket: the pass and its finalisation once per candidate
+// shape (genotype stages 4, 6, 8 x pairs on, off; finalisation widths
+// alternating), each run writing the same g (the finalisation reads the pass's
+// output in place, so each candidate runs both).  The fastest pass shape and
+// the faster finalisation are cached.  prof brackets the first candidate's pass.
+static int mr_tune(const MrPass &P, ProfEvents *prof)
+{
+    std::vector<MrShape> cand;
+    for (int ngs : {4, 6, 8})
+        for (int pairs : {1, 0}) {
+            const MrShape sh{ngs, pairs, (int)(cand.size() % 2 == 0)};
+            int nbst, nbufs;
+            if (mr_shape_launch(P.N, sh, &nbst, &nbufs)) cand.push_back(sh);
+        }
+    TuneEvents te(4 * cand.size());
+    IHT_CUDA(te.create());
+    for (size_t c = 0; c < cand.size(); ++c)
+        if (int rc = mr_pass(P, cand[c], &te, 4 * c, c == 0 ? prof : nullptr)) return rc;
+    IHT_CUDA(cudaStreamSynchronize(P.ds->ctx->stream));
+    float best = 1e30f, fin_best[2] = {1e30f, 1e30f};
+    int prm[kTuneParams] = {0, 0, 1, 0};
+    for (size_t c = 0; c < cand.size(); ++c) {
+        const float k = te.ms(4 * c, 4 * c + 1), f = te.ms(4 * c + 2, 4 * c + 3);
+        if (k < best) {
+            best = k;
+            prm[0] = cand[c].ngs;
+            prm[1] = cand[c].pairs;
+        }
+        fin_best[cand[c].fin8] = std::min(fin_best[cand[c].fin8], f);
+    }
+    prm[2] = fin_best[0] < fin_best[1] ? 0 : 1;
+    tune_store(P.ds, IHT_PASS_MULTI, mr_bucket_of(P.N), prm, best + std::min(fin_best[0], fin_best[1]),
+               (int)cand.size());
+    return IHT_OK;
+}
+
 // G of ncols residual columns (cols: device array; r32, u32, v32 and g set by
 // the caller; cols_host, optional, the same descriptors on the host).  Passes
-// of at most kMrMaxCols columns.  A single column with its host descriptor goes
-// through the single-column pass instead (same arithmetic, so the same bits,
-// at about half the cost of a one-column multi-column pass).
+// of at most kMrMaxCols columns, each in its bucket's cached shape (tuned on
+// this call when none is cached, tuning is on and the stream is not being
+// captured; else the default shape).  A single column with its host descriptor
+// goes through the single-column pass instead (same arithmetic, so the same
+// bits, at about half the cost of a one-column multi-column pass).
 int launch_grad_mrhs(iht_dataset *ds, MrCol *cols, int ncols, ProfEvents *prof, const MrCol *cols_host)
 {
     if (ncols <= 0) return IHT_OK;
@@ -917,6 +1047,7 @@ int launch_grad_mrhs(iht_dataset *ds, MrCol *cols, int ncols, ProfEvents *prof, 
     }
     const int64_t tiles = (ds->p + 128 * kMrTiles - 1) / (128 * kMrTiles);
     const int grid = (int)std::min<int64_t>(tiles, ds->ctx->num_sms);
+    const bool may_tune = autotune_enabled() && !stream_capturing(s);
     for (int c0 = 0; c0 < ncols; c0 += kMrMaxCols) {
         const int nc = std::min(kMrMaxCols, ncols - c0);
         const int N = mr_n(nc);
@@ -924,29 +1055,26 @@ int launch_grad_mrhs(iht_dataset *ds, MrCol *cols, int ncols, ProfEvents *prof, 
         IHT_CUDA(cudaMemsetAsync(w.bimg, 0, bbytes, s));
         // scale, limbs and R over the single-column pass's samples (the rest are 0)
         k_mr_limbs<<<nc, 1024, 0, s>>>(cols + c0, 2 * mr_ngroups(ds) * kMrStepSamples, N, w.bimg);
-        const int nbst = mr_bstages(N);
-        int nbufs = std::min(kMrMaxBufs, (256 - N) / 16);
-        // with four or more A buffers a decoder step fills two (one 32-column store)
-        const bool pairs = nbufs >= 4;
-        if (pairs) nbufs &= ~1;
-        if (nbst < 2 || nbufs < 2) return IHT_EINVAL;
-        // at least 116 KB, so one CTA per SM: the kernel allocates all 512 columns of tensor memory
-        const size_t smem = std::max<size_t>(116 * 1024, mr_gbytes(N) + (size_t)nbst * kMrChunkSteps * N * 32);
-        // D FP32, A E5M2, B E4M3, K-major, N, M = 128
-        const uint32_t idesc = (1u << 4) | (1u << 7) | ((uint32_t)(N >> 3) << 17) |
-                               ((uint32_t)(128 >> 4) << 24);
-        prof_begin(prof, s);
-        auto kern = pairs ? k_grad_mrhs<true> : k_grad_mrhs<false>;
-        kern<<<grid, kMrThreads, smem, s>>>(map, ds->p, ksteps, N, nc, nbufs, nbst, mr_gstages(N), w.bimg,
-                                            cols + c0, idesc, w.err);
-        prof_end(prof, s);
-        note_launch(2);
+        note_launch();
         IHT_CUDA(cudaGetLastError());
-        rc = ds->miss_idx16 ? mr_finalize<uint16_t>(ds, cols + c0, nc)
-                            : mr_finalize<int32_t>(ds, cols + c0, nc);
+        const MrPass pass{ds, &map, grid, ksteps, N, nc, cols + c0};
+        int prm[kTuneParams];
+        if (tune_lookup(ds, IHT_PASS_MULTI, mr_bucket_of(N), prm))
+            rc = mr_pass(pass, MrShape{prm[0], prm[1], prm[2]}, nullptr, 0, prof);
+        else if (may_tune)
+            rc = mr_tune(pass, prof);
+        else
+            rc = mr_pass(pass, mr_default_shape(N), nullptr, 0, prof);
         if (rc) return rc;
     }
     return IHT_OK;
+}
+
+// Identifies the calling thread's pass scratch (changes when it is reallocated).
+uint64_t grad_mrhs_scratch_id()
+{
+    return (uint64_t)(uintptr_t)g_mr.bimg ^ ((uint64_t)(uintptr_t)g_mr.err << 1) ^
+           ((uint64_t)(uintptr_t)g_mr.mj << 2) ^ ((uint64_t)g_mr.bbytes << 3);
 }
 
 // Frees the calling thread's pass scratch (a server's worker before it exits).

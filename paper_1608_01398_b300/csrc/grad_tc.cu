@@ -640,8 +640,65 @@ int prepare_grad_tc(iht_dataset *ds, const float *r32, const int32_t *done)
     return prepare_grad_tc_to(ds, r32, ds->ws->Mj, done);
 }
 
+bool grad_tc_shape_fits(const iht_dataset *ds, const int *params)
+{
+    return params[0] >= 2 && params[0] <= tc_stages(ds);
+}
+
+static int tc_launch(iht_dataset *ds, const CUtensorMap &map, int nst, float *g, const float *u32,
+                     const float *v32, const float *Mj, const int32_t *done)
+{
+    const int64_t tiles = (ds->p + 127) / 128;
+    const int grid = (int)std::min<int64_t>((tiles + kTcNWG - 1) / kTcNWG, (int64_t)ds->ctx->num_sms);
+    const size_t smem = (size_t)kTcNWG * nst * kTcStageTile + tc_bbytes(ds);
+    k_grad_tc<<<grid, kTcThreads, smem, ds->ctx->stream>>>(map, ds->p, tc_ngroups(ds), nst, g_tc.bimg,
+                                                           (int)tc_bbytes(ds), Mj, u32, v32, g, g_tc.prm,
+                                                           done);
+    note_launch();
+    IHT_CUDA(cudaGetLastError());
+    return IHT_OK;
+}
+
+// First pass on a dataset shape: every stage count from 3 up to the most that
+// fit, twice in turn (each run writes the same g), timed with events; the
+// fastest is cached.  Nothing is cached when the solve had already stopped
+// (the runs returned at once and timed nothing).
+static int tc_tune(iht_dataset *ds, const CUtensorMap &map, float *g, const float *u32, const float *v32,
+                   const float *Mj, const int32_t *done)
+{
+    cudaStream_t s = ds->ctx->stream;
+    const int hi = tc_stages(ds), lo = std::min(3, hi);
+    const int nc = hi - lo + 1, rounds = 2;
+    TuneEvents te(2 * nc * rounds);
+    IHT_CUDA(te.create());
+    for (int r = 0; r < rounds; ++r)
+        for (int c = 0; c < nc; ++c) {
+            const int i = 2 * (r * nc + c);
+            IHT_CUDA(cudaEventRecord(te.ev[i], s));
+            if (int rc = tc_launch(ds, map, lo + c, g, u32, v32, Mj, done)) return rc;
+            IHT_CUDA(cudaEventRecord(te.ev[i + 1], s));
+        }
+    int32_t stopped = 0;
+    if (done) IHT_CUDA(cudaMemcpyAsync(&stopped, done, sizeof(stopped), cudaMemcpyDeviceToHost, s));
+    IHT_CUDA(cudaStreamSynchronize(s));
+    float best = 1e30f;
+    int prm[kTuneParams] = {hi, 0, 0, 0};
+    for (int r = 0; r < rounds; ++r)
+        for (int c = 0; c < nc; ++c) {
+            const float ms = te.ms(2 * (r * nc + c), 2 * (r * nc + c) + 1);
+            if (ms < best) {
+                best = ms;
+                prm[0] = lo + c;
+            }
+        }
+    if (!stopped) tune_store(ds, IHT_PASS_SINGLE, 0, prm, best, nc * rounds);
+    return IHT_OK;
+}
+
 // The gradient pass proper (after prepare_grad_tc on the same stream) with
-// explicit statistics and missing-call sums.
+// explicit statistics and missing-call sums.  The TMA stage count is the
+// cached tuned one (tuned on this call when none is cached, tuning is on and
+// the stream is not being captured), else the most that fit.
 int launch_grad_tc_main_with(iht_dataset *ds, const float *r32, float *g, const float *u32,
                              const float *v32, const float *Mj, const int32_t *done)
 {
@@ -649,22 +706,17 @@ int launch_grad_tc_main_with(iht_dataset *ds, const float *r32, float *g, const 
     CUtensorMap map;
     int rc = make_gmap(ds, &map);
     if (rc) return rc;
-    const int ngroups = tc_ngroups(ds);
-    const size_t bbytes = tc_bbytes(ds);
-    const int smem = (int)tc_smem(ds);
     static thread_local int cfg = -1;
     if (cfg != ds->ctx->device) {
         IHT_CUDA(cudaFuncSetAttribute(k_grad_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       220 * 1024));
         cfg = ds->ctx->device;
     }
-    const int64_t tiles = (ds->p + 127) / 128;
-    const int grid = (int)std::min<int64_t>((tiles + kTcNWG - 1) / kTcNWG, (int64_t)ds->ctx->num_sms);
-    k_grad_tc<<<grid, kTcThreads, smem, s>>>(map, ds->p, ngroups, tc_stages(ds), g_tc.bimg, (int)bbytes,
-                                              Mj, u32, v32, g, g_tc.prm, done);
-    note_launch();
-    IHT_CUDA(cudaGetLastError());
-    return IHT_OK;
+    int prm[kTuneParams];
+    if (tune_lookup(ds, IHT_PASS_SINGLE, 0, prm) && grad_tc_shape_fits(ds, prm))
+        return tc_launch(ds, map, prm[0], g, u32, v32, Mj, done);
+    if (autotune_enabled() && !stream_capturing(s)) return tc_tune(ds, map, g, u32, v32, Mj, done);
+    return tc_launch(ds, map, tc_stages(ds), g, u32, v32, Mj, done);
 }
 
 int launch_grad_tc_main(iht_dataset *ds, const float *r32, float *g, const int32_t *done)

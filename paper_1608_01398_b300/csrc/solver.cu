@@ -826,6 +826,7 @@ int run_solve(iht_dataset *ds, int k, const iht_options *opt, int n_rows, const 
     }
 
     const bool traced = tr.objective || tr.mu || tr.backtracks || tr.changed || tr.supp || tr.beta;
+    ws->graph_replays = 0;
     double graph_ms = 0.0;
     int graph_n = 0;
     if (!traced) {
@@ -835,6 +836,7 @@ int run_solve(iht_dataset *ds, int k, const iht_options *opt, int n_rows, const 
         for (int it = 0; it < opt->max_iter; ++it) {
             IHT_CUDA(cudaGraphLaunch(exec, s));
             note_launch(ws->iter_launches);
+            ++ws->graph_replays;
             IHT_CUDA(cudaMemcpyAsync(&ws->sc_host->done, &ws->sc->done, 2 * sizeof(int32_t),
                                      cudaMemcpyDeviceToHost, s));
             IHT_CUDA(cudaStreamSynchronize(s));

@@ -237,6 +237,35 @@ def test_fit_batch_matches_single_solves(iht, ctx):
         assert fs.objective == fb.objective
 
 
+def test_fit_batch_iteration_graphs(iht, ctx):
+    """An iteration whose active solves are those of the previous one replays a
+    cached CUDA graph of the same launches in the same order (gradient pass,
+    selection, step, two attempts), so a batch gives the same bits on its first
+    call, on a repeat that replays cached graphs, alone (a one-column batch runs
+    the single-column pass inside its graph) and through iht_fit."""
+    n, p = 1200, 3001
+    G, codes, y, _, rng = _signal_panel(12, n, p, 5, effect=0.5)
+    ds = load(iht, ctx, G)
+    y2 = rng.normal(size=n)
+    probs = [(y, 5, None), (y2, 3, None), (y, 10, None)]
+    first = iht.iht_fit_batch(ds, probs)
+    again = iht.iht_fit_batch(ds, probs)
+    assert first[0].graph_replays > 0
+    assert again[0].graph_replays == first[0].graph_replays
+    for (yy, k, rr), f, a in zip(probs, first, again):
+        one = iht.iht_fit_batch(ds, [(yy, k, rr)])[0]
+        s = iht.iht_fit(ds, yy, k, rows=rr)
+        assert f.iterations > 2 and one.graph_replays > 0 and s.graph_replays > 0
+        for r in (a, one, s):
+            assert np.array_equal(r.support, f.support) and np.array_equal(r.beta, f.beta)
+            assert (r.iterations, r.status, r.objective) == (f.iterations, f.status, f.objective)
+    # profiled: every gradient pass, direct or replayed, is timed (one per iteration)
+    pr = iht.iht_fit_batch(ds, probs, profile=1)
+    its = max(r.iterations for r in pr)
+    assert its - 1 <= pr[0].grad_launches <= its + 1 and pr[0].grad_ms > 0
+    assert all(np.array_equal(r.beta, f.beta) for r, f in zip(pr, first))
+
+
 def test_fit_batch_odd_p(iht, ctx):
     """p not a multiple of 4: per-solve gradient rows start off 16-byte boundaries."""
     n, p = 500, 1003
