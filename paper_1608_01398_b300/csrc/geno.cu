@@ -527,7 +527,9 @@ int build_missing_lists(iht_dataset *ds)
 
 // M_j = sum of r over the missing calls of SNP j.  The block stages r in
 // shared memory; each lane owns one SNP and reads its list 16 bytes (8 or 4
-// sample offsets) at a time, adding in list order.
+// sample offsets) at a time, adding in list order; the next 16-byte piece is
+// requested before the current one is summed, so one list latency is exposed
+// per SNP rather than one per piece.
 template <typename IdxT>
 __global__ void __launch_bounds__(512) k_missing_sum_smem(const int64_t *__restrict__ off,
                                                           const IdxT *__restrict__ idx, int64_t p,
@@ -544,13 +546,20 @@ __global__ void __launch_bounds__(512) k_missing_sum_smem(const int64_t *__restr
     for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < p;
          j += (int64_t)gridDim.x * blockDim.x) {
         const int64_t e0 = off[j], e1 = off[j + 1];
+        const int64_t a0 = e0 & ~(int64_t)(kPer - 1);
+        const int lo = (int)(e0 - a0), hi = (int)(e1 - a0);   // valid positions [lo, hi) from a0
+        const uint4 *__restrict__ src = idx4 + a0 / kPer;     // (lists end with 16 spare entries)
         float m = 0.0f;
-        for (int64_t a = e0 & ~(int64_t)(kPer - 1); a < e1; a += kPer) {
-            const uint4 w = idx4[a / kPer];
+        uint4 w = src[0];
+        for (int q = 0; q * kPer < hi; ++q) {
+            const uint4 wn = (q + 1) * kPer < hi ? src[q + 1] : w;
             const IdxT *ent = reinterpret_cast<const IdxT *>(&w);
 #pragma unroll
-            for (int t = 0; t < kPer; ++t)
-                if (a + t >= e0 && a + t < e1) m += rs_miss[ent[t]];
+            for (int t = 0; t < kPer; ++t) {
+                const int pos = q * kPer + t;
+                if (pos >= lo && pos < hi) m += rs_miss[ent[t]];
+            }
+            w = wn;
         }
         M[j] = m;
     }

@@ -649,19 +649,25 @@ __global__ void __launch_bounds__(kFinThreads) k_miss_finalize(const int64_t *__
         const int64_t j = base + lane;
         const bool live = j < p;
         const int64_t e0 = live ? off[j] : 0, e1 = live ? off[j + 1] : 0;
+        const int64_t a0 = e0 & ~(int64_t)(kPer - 1);
+        const int lo = (int)(e0 - a0), hi = (int)(e1 - a0);   // valid positions [lo, hi) from a0
+        const uint4 *__restrict__ src = idx4 + a0 / kPer;
         float m[CG];
 #pragma unroll
         for (int e = 0; e < CG; ++e) m[e] = 0.0f;
-        for (int64_t a = e0 & ~(int64_t)(kPer - 1); a < e1; a += kPer) {
-            const uint4 w = idx4[a / kPer];
+        uint4 w = src[0];                                      // next piece requested a step ahead
+        for (int q = 0; q * kPer < hi; ++q) {
+            const uint4 wn = (q + 1) * kPer < hi ? src[q + 1] : w;
             const IdxT *ent = reinterpret_cast<const IdxT *>(&w);
 #pragma unroll
             for (int t = 0; t < kPer; ++t) {
-                if (a + t >= e0 && a + t < e1) {
+                const int pos = q * kPer + t;
+                if (pos >= lo && pos < hi) {
                     if (kStage) mr_addv(m, rs[ent[t]]);
                     else m[0] += __ldg(rg + ent[t]);
                 }
             }
+            w = wn;
         }
         if (live) {
 #pragma unroll
@@ -716,8 +722,9 @@ __global__ void __launch_bounds__(kFin8Threads) k_miss_finalize8(const int64_t *
         const int lo = (int)(e0 - a0), hi = (int)(e1 - a0);   // valid positions [lo, hi) from a0
         const uint4 *__restrict__ src = idx4 + a0 / kPer;
         float m0 = 0.0f, m1 = 0.0f, m2 = 0.0f, m3 = 0.0f;
+        uint4 w = src[0];                                      // next piece requested a step ahead
         for (int q = 0; q * kPer < hi; ++q) {
-            const uint4 w = src[q];
+            const uint4 wn = (q + 1) * kPer < hi ? src[q + 1] : w;
             const IdxT *ent = reinterpret_cast<const IdxT *>(&w);
 #pragma unroll
             for (int t = 0; t < kPer; ++t) {
@@ -729,6 +736,7 @@ __global__ void __launch_bounds__(kFin8Threads) k_miss_finalize8(const int64_t *
                 m2 += x.z;
                 m3 += x.w;
             }
+            w = wn;
         }
         if (live) {
             const float m[4] = {m0, m1, m2, m3};
