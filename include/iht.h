@@ -303,7 +303,10 @@ int iht_gradient_batch(iht_dataset *ds, int32_t b, const int32_t *const *rows_li
  * genotype stages 2..8; params[1]: 1 = each decoder step fills a pair of A
  * buffers (needs four or more buffers: 192 accumulator columns at most);
  * params[2]: 1 = missing-call finalisation over 8 columns per block (when
- * more than 4 columns and shared memory holds 32 (n_pad + 1) bytes). */
+ * more than 4 columns and the 8-column residual table fits in shared
+ * memory); params[3]: 1 = finalisation over the padded missing-call lists
+ * (groups of 8 SNPs with common residue-class boundaries, built at upload
+ * when n is at most about 12 800; ignored otherwise). */
 enum { IHT_PASS_SINGLE = 0, IHT_PASS_MULTI = 1 };
 
 /* Tuning on (default) or off; IHT_AUTOTUNE=0 in the environment starts it off. */
@@ -313,7 +316,7 @@ void iht_set_autotune(int on);
 void iht_tune_clear(void);
 
 /* Pins the shape of passes of `kind` over ncols columns on this dataset
- * (params: host int32[nparams], nparams 1 for SINGLE, 3 for MULTI).  EINVAL for
+ * (params: host int32[nparams], nparams 1 for SINGLE, 4 for MULTI).  EINVAL for
  * a shape that does not fit the pass or an unknown kind. */
 int iht_tune_pin(const iht_dataset *ds, int32_t kind, int32_t ncols, const int32_t *params,
                  int32_t nparams);

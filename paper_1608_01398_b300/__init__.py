@@ -469,7 +469,7 @@ def tune_clear() -> None:
 
 
 def _nparams(kind: int) -> int:
-    return 1 if kind == IHT_PASS_SINGLE else 3
+    return 1 if kind == IHT_PASS_SINGLE else 4
 
 
 def tune_pin(ds: Dataset, kind: int, ncols: int, params) -> None:

@@ -288,6 +288,8 @@ int iht_load_bed(iht_ctx *ctx, const uint8_t *bed, size_t bed_bytes, int mem, in
         cudaFree(ds->G);
         if (ds->miss_off) cudaFree(ds->miss_off);
         if (ds->miss_idx) cudaFree(ds->miss_idx);
+        if (ds->miss_goff) cudaFree(ds->miss_goff);
+        if (ds->miss_gidx) cudaFree(ds->miss_gidx);
         delete ds;
         return rc;
     }
@@ -304,6 +306,8 @@ int iht_dataset_free(iht_dataset *ds)
     cudaFree(ds->G);
     if (ds->miss_off) cudaFree(ds->miss_off);
     if (ds->miss_idx) cudaFree(ds->miss_idx);
+    if (ds->miss_goff) cudaFree(ds->miss_goff);
+    if (ds->miss_gidx) cudaFree(ds->miss_gidx);
     delete ds;
     return IHT_OK;
 }

@@ -158,6 +158,15 @@ struct iht_dataset {
     void *miss_idx;
     int64_t miss_total;
     bool miss_idx16;
+    // the same lists padded for the multi-column finalisation (uint16, built
+    // when a 4-column residual table with 8 zero rows fits in shared memory):
+    // groups of kPadGroup consecutive SNPs; every SNP of group g has a sequence
+    // of the same length L_g with the same class boundaries (class c padded to
+    // the group's longest class c with zero-row indices n_pad + ((j + c) mod 8),
+    // then to a multiple of 8 with n_pad + (j mod 8)); SNP j's sequence starts
+    // at miss_goff[g] + (j mod 8) L_g, L_g = (miss_goff[g + 1] - miss_goff[g]) / 8
+    int64_t *miss_goff = nullptr;
+    uint16_t *miss_gidx = nullptr;
     iht::Workspace *ws;
 };
 
@@ -237,6 +246,8 @@ int launch_counts_rowset(iht_dataset *ds, int64_t n_rows, const RowSet &rs);
 int launch_counts_sets(iht_dataset *ds, const RowSet *sets, const int64_t *n_rows, int nsets);
 int launch_fix_padding(iht_dataset *ds);
 int build_missing_lists(iht_dataset *ds);
+constexpr int kPadGroup = 8;
+bool padded_lists_wanted(const iht_dataset *ds);
 int launch_missing_sums(iht_dataset *ds, const float *r32, float *M, const int32_t *done);
 int setup_rows(iht_dataset *ds, const int32_t *rows_dev, int64_t n_rows);
 int launch_counts(iht_dataset *ds, int64_t n_rows);
@@ -387,6 +398,39 @@ __device__ __forceinline__ double block_sum(double x, double *sh)
     t = sh[0];
     __syncthreads();
     return t;
+}
+
+// Three fixed-order block sums at once (each in the order block_sum uses);
+// `sh` needs 3 blockDim.x / 32 doubles.
+__device__ __forceinline__ void block_sum3(double &x, double &y, double &z, double *sh)
+{
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        x += __shfl_xor_sync(0xffffffffu, x, o);
+        y += __shfl_xor_sync(0xffffffffu, y, o);
+        z += __shfl_xor_sync(0xffffffffu, z, o);
+    }
+    __syncthreads();
+    if (lane == 0) {
+        sh[wid] = x;
+        sh[nw + wid] = y;
+        sh[2 * nw + wid] = z;
+    }
+    __syncthreads();
+    if (wid == 0) {
+        double a = lane < nw ? sh[lane] : 0.0, b = lane < nw ? sh[nw + lane] : 0.0,
+               c = lane < nw ? sh[2 * nw + lane] : 0.0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            a += __shfl_xor_sync(0xffffffffu, a, o);
+            b += __shfl_xor_sync(0xffffffffu, b, o);
+            c += __shfl_xor_sync(0xffffffffu, c, o);
+        }
+        x = a;
+        y = b;
+        z = c;
+    }
 }
 
 inline int ceil_div(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }

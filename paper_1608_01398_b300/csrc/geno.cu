@@ -472,6 +472,116 @@ __global__ void __launch_bounds__(256) k_miss_fill(const uint8_t *__restrict__ G
     }
 }
 
+// Padded lists (see iht_dataset): class counts of this lane's SNP j (0 past p)
+// and, over the lane's group of kPadGroup lanes, the longest count of every
+// class.  Called by all 32 lanes of a warp, j = 32 w + lane.
+__device__ __forceinline__ int pad_classes(const int64_t *__restrict__ off, const uint16_t *__restrict__ idx,
+                                           int64_t j, int64_t p, int (&cnt)[8], int (&len)[8])
+{
+#pragma unroll
+    for (int c = 0; c < 8; ++c) cnt[c] = 0;
+    if (j < p)
+        for (int64_t e = off[j]; e < off[j + 1]; ++e) {
+            const int cls = (int)(((int64_t)idx[e] - j) & 7);
+#pragma unroll
+            for (int c = 0; c < 8; ++c) cnt[c] += cls == c;
+        }
+    int L = 0;
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+        int t = cnt[c];
+#pragma unroll
+        for (int o = 1; o < kPadGroup; o <<= 1) t = max(t, __shfl_xor_sync(0xffffffffu, t, o));
+        len[c] = t;
+        L += t;
+    }
+    return (L + 7) & ~7;
+}
+
+__global__ void __launch_bounds__(256) k_pad_len(const int64_t *__restrict__ off, const uint16_t *__restrict__ idx,
+                                                 int64_t p, int32_t *__restrict__ glen)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t ngroups = (p + kPadGroup - 1) / kPadGroup;
+    const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t w = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); w * 32 < p; w += nwarps) {
+        const int64_t j = 32 * w + lane;
+        int cnt[8], len[8];
+        const int L = pad_classes(off, idx, j, p, cnt, len);
+        if ((lane & (kPadGroup - 1)) == 0 && j / kPadGroup < ngroups) glen[j / kPadGroup] = L;
+    }
+}
+
+__global__ void __launch_bounds__(256) k_pad_fill(const int64_t *__restrict__ off, const uint16_t *__restrict__ idx,
+                                                  int64_t p, int64_t n_pad, const int64_t *__restrict__ goff,
+                                                  uint16_t *__restrict__ gidx)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t ngroups = (p + kPadGroup - 1) / kPadGroup;
+    const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t w = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); w * 32 < p; w += nwarps) {
+        const int64_t j = 32 * w + lane;
+        int cnt[8], len[8];
+        const int L = pad_classes(off, idx, j, p, cnt, len);
+        const int64_t g = j / kPadGroup;
+        if (g >= ngroups) continue;
+        uint16_t *dst = gidx + goff[g] + (j % kPadGroup) * (int64_t)L;
+        int64_t e = j < p ? off[j] : 0;
+        int pos = 0;
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+            for (int t = 0; t < cnt[c]; ++t) dst[pos++] = idx[e++];
+            const uint16_t z = (uint16_t)(n_pad + ((j + c) & 7));
+            for (int t = cnt[c]; t < len[c]; ++t) dst[pos++] = z;
+        }
+        const uint16_t z = (uint16_t)(n_pad + (j & 7));
+        while (pos < L) dst[pos++] = z;
+    }
+}
+
+bool padded_lists_wanted(const iht_dataset *ds)
+{
+    return ds->miss_idx16 && 16 * ((size_t)ds->n_pad + 8) <= 200 * 1024;
+}
+
+static int build_padded_lists(iht_dataset *ds)
+{
+    cudaStream_t s = ds->ctx->stream;
+    const int64_t p = ds->p, ngroups = (p + kPadGroup - 1) / kPadGroup;
+    const int blocks = (int)std::min<int64_t>(ceil_div(p, 256), (int64_t)ds->ctx->num_sms * 8);
+    int32_t *glen = nullptr;
+    IHT_CUDA(cudaMalloc(&glen, sizeof(int32_t) * ngroups));
+    k_pad_len<<<blocks, 256, 0, s>>>(ds->miss_off, (const uint16_t *)ds->miss_idx, p, glen);
+    note_launch();
+    std::vector<int32_t> hl(ngroups);
+    std::vector<int64_t> ho(ngroups + 1);
+    cudaError_t e = cudaMemcpyAsync(hl.data(), glen, sizeof(int32_t) * ngroups, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    cudaFree(glen);
+    if (e != cudaSuccess) {
+        set_cuda_error(e, "padded list lengths");
+        return IHT_ECUDA;
+    }
+    ho[0] = 0;
+    for (int64_t g = 0; g < ngroups; ++g) ho[g + 1] = ho[g] + (int64_t)kPadGroup * hl[g];
+    e = cudaMalloc(&ds->miss_goff, sizeof(int64_t) * (ngroups + 1));
+    // 16 spare entries: readers request the next 16-byte piece before they know it is needed
+    if (e == cudaSuccess) e = cudaMalloc(&ds->miss_gidx, sizeof(uint16_t) * (ho[ngroups] + 16));
+    if (e == cudaSuccess) e = cudaMemsetAsync(ds->miss_gidx + ho[ngroups], 0, 16 * sizeof(uint16_t), s);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(ds->miss_goff, ho.data(), sizeof(int64_t) * (ngroups + 1), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) {
+        set_cuda_error(e, "padded lists");
+        return e == cudaErrorMemoryAllocation ? IHT_ENOMEM : IHT_ECUDA;
+    }
+    k_pad_fill<<<blocks, 256, 0, s>>>(ds->miss_off, (const uint16_t *)ds->miss_idx, p, ds->n_pad, ds->miss_goff,
+                                      ds->miss_gidx);
+    note_launch();
+    IHT_CUDA(cudaGetLastError());
+    return IHT_OK;
+}
+
 int build_missing_lists(iht_dataset *ds)
 {
     cudaStream_t s = ds->ctx->stream;
@@ -522,7 +632,7 @@ int build_missing_lists(iht_dataset *ds)
                                                     (int32_t *)ds->miss_idx);
     note_launch();
     IHT_CUDA(cudaGetLastError());
-    return IHT_OK;
+    return padded_lists_wanted(ds) ? build_padded_lists(ds) : IHT_OK;
 }
 
 // M_j = sum of r over the missing calls of SNP j.  The block stages r in

@@ -753,6 +753,78 @@ __global__ void __launch_bounds__(kFin8Threads) k_miss_finalize8(const int64_t *
     }
 }
 
+// The same two finalisations over the padded lists (groups of 8 SNPs with
+// common class boundaries, pads pointing at zero rows n_pad + ((j + c) mod 8)):
+// at every step the SNPs of a quarter-warp read rows of one residue class c,
+// (j + c) mod 8 for consecutive j, so their rows fall in distinct bank groups
+// (32-byte rows: 4 per 128 bytes; 16-byte rows: 8); no bounds tests.  Zero
+// rows add +0.0f, which leaves a sum that starts at 0.0f unchanged, so every
+// SNP's sum is the one the unpadded lists give.
+template <bool kWide>
+__global__ void __launch_bounds__(kWide ? kFin8Threads : kFinThreads) k_miss_finalize_pad(
+    const int64_t *__restrict__ goff, const uint16_t *__restrict__ gidx, int64_t p, int64_t n_pad,
+    const MrCol *__restrict__ cols, int ncols)
+{
+    constexpr int kCols = kWide ? 8 : 4;                       // columns per block
+    constexpr int kSnps = kWide ? 16 : 32;                     // SNPs per warp
+    extern __shared__ __align__(16) unsigned char mr_sh[];
+    float4 *rs = reinterpret_cast<float4 *>(mr_sh);            // (n_pad + 8) rows of kCols floats
+    const int c0 = blockIdx.y * kCols;
+    for (int64_t i = threadIdx.x; i < n_pad + 8; i += blockDim.x) {
+        float v[kCols];
+#pragma unroll
+        for (int e = 0; e < kCols; ++e) v[e] = (i < n_pad && c0 + e < ncols) ? cols[c0 + e].r32[i] : 0.0f;
+#pragma unroll
+        for (int h = 0; h < kCols / 4; ++h)
+            rs[(kCols / 4) * i + h] = make_float4(v[4 * h], v[4 * h + 1], v[4 * h + 2], v[4 * h + 3]);
+    }
+    __syncthreads();
+    const int lane = threadIdx.x & 31, h = kWide ? (lane & 1) : 0;
+    const int64_t ngroups = (p + kPadGroup - 1) / kPadGroup;
+    const uint4 *__restrict__ g4 = reinterpret_cast<const uint4 *>(gidx);
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t base = warp * kSnps; base < p; base += nwarps * kSnps) {
+        const int64_t j = base + (kWide ? (lane >> 1) : lane);
+        const int64_t g = j / kPadGroup;
+        int64_t start = 0, L = 0;
+        if (g < ngroups) {
+            const int64_t g0 = goff[g];
+            L = (goff[g + 1] - g0) / kPadGroup;
+            start = g0 + (j % kPadGroup) * L;
+        }
+        const uint4 *__restrict__ src = g4 + start / 8;
+        const int nq = (int)(L / 8);
+        float m0 = 0.0f, m1 = 0.0f, m2 = 0.0f, m3 = 0.0f;
+        uint4 w = src[0];                                      // next piece requested a step ahead
+        for (int q = 0; q < nq; ++q) {
+            const uint4 wn = q + 1 < nq ? src[q + 1] : w;
+            const uint16_t *ent = reinterpret_cast<const uint16_t *>(&w);
+#pragma unroll
+            for (int t = 0; t < 8; ++t) {
+                const float4 x = rs[(kCols / 4) * (uint32_t)ent[t] + h];
+                m0 += x.x;
+                m1 += x.y;
+                m2 += x.z;
+                m3 += x.w;
+            }
+            w = wn;
+        }
+        if (j < p) {
+            const float m[4] = {m0, m1, m2, m3};
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const int c = c0 + 4 * h + e;
+                if (c < ncols) {
+                    const MrCol &C = cols[c];
+                    const float d = C.g[j];
+                    C.g[j] = standardise_d(d, C.R, m[e], C.u32[j], C.v32[j]);
+                }
+            }
+        }
+    }
+}
+
 // ---------------------------------------------------------------------------
 
 struct MrWork {
@@ -783,6 +855,7 @@ struct MrShape {
     int ngs;      // genotype stages (2 tiles x 8 KB each)
     int pairs;    // 1: each decoder step fills a pair of A buffers
     int fin8;     // 1: missing-call finalisation over 8 columns per block
+    int padded;   // 1: finalisation over the padded lists (when the dataset has them)
 };
 
 // B stages and A buffers of shape sh at N accumulator columns (false: it does
@@ -790,7 +863,8 @@ struct MrShape {
 // genotype stages, up to kMrMaxBStages.
 static bool mr_shape_launch(int N, const MrShape &sh, int *nbst, int *nbufs)
 {
-    if (sh.ngs < 2 || sh.ngs > kMrMaxGStages || sh.pairs < 0 || sh.pairs > 1 || sh.fin8 < 0 || sh.fin8 > 1)
+    if (sh.ngs < 2 || sh.ngs > kMrMaxGStages || sh.pairs < 0 || sh.pairs > 1 || sh.fin8 < 0 || sh.fin8 > 1 ||
+        sh.padded < 0 || sh.padded > 1)
         return false;
     const size_t gb = (size_t)sh.ngs * kMrTiles * kMrGTile;
     const size_t chunk = (size_t)kMrChunkSteps * N * 32;
@@ -810,7 +884,7 @@ static bool mr_shape_launch(int N, const MrShape &sh, int *nbst, int *nbufs)
 // fast as it decodes them and wants many bytes in flight; with many, B chunks
 // need the room (the pass is tensor-bound there).  Pairs whenever there are
 // four or more A buffers.
-static MrShape mr_default_shape(int N) { return MrShape{N <= 96 ? kMrMaxGStages : 4, 1, 1}; }
+static MrShape mr_default_shape(int N) { return MrShape{N <= 96 ? kMrMaxGStages : 4, 1, 1, 1}; }
 
 // A cached shape made to fit N (pairs dropped when there are too few buffers;
 // the default when the stages do not fit).
@@ -835,8 +909,8 @@ int grad_mrhs_bucket(int ncols) { return mr_bucket_of(mr_n(std::min(ncols, kMrMa
 bool grad_mrhs_shape_fits(int ncols, const int *params)
 {
     int nbst, nbufs;
-    return mr_shape_launch(mr_n(std::min(ncols, kMrMaxCols)), MrShape{params[0], params[1], params[2]}, &nbst,
-                           &nbufs);
+    return mr_shape_launch(mr_n(std::min(ncols, kMrMaxCols)), MrShape{params[0], params[1], params[2], params[3]},
+                           &nbst, &nbufs);
 }
 
 int mrhs_max_cols() { return kMrMaxCols; }
@@ -912,9 +986,36 @@ static int mr_launch_finalize8(iht_dataset *ds, const MrCol *cols, int ncols, si
     return IHT_OK;
 }
 
-template <typename IdxT>
-static int mr_finalize(iht_dataset *ds, const MrCol *cols, int ncols, bool fin8)
+template <bool kWide>
+static int mr_launch_finalize_pad(iht_dataset *ds, const MrCol *cols, int ncols, size_t smem)
 {
+    auto kern = k_miss_finalize_pad<kWide>;
+    static thread_local int configured_dev = -1;
+    if (configured_dev != ds->ctx->device) {
+        IHT_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFin8SmemMax));
+        configured_dev = ds->ctx->device;
+    }
+    const int cg = kWide ? 8 : 4, threads = kWide ? kFin8Threads : kFinThreads;
+    const int groups = (ncols + cg - 1) / cg;
+    const int per_sm = kWide || smem > 110 * 1024 ? 1 : 2;
+    const int64_t per_block = kWide ? threads / 2 : threads;     // SNPs per block and sweep
+    const int gx = (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(ds->p, per_block),
+                                                               (int64_t)ds->ctx->num_sms * per_sm / groups));
+    kern<<<dim3(gx, groups), threads, smem, ds->ctx->stream>>>(ds->miss_goff, ds->miss_gidx, ds->p, ds->n_pad,
+                                                               cols, ncols);
+    note_launch();
+    IHT_CUDA(cudaGetLastError());
+    return IHT_OK;
+}
+
+template <typename IdxT>
+static int mr_finalize(iht_dataset *ds, const MrCol *cols, int ncols, bool fin8, bool padded)
+{
+    if (padded && ds->miss_gidx) {
+        const size_t p8 = 32 * ((size_t)ds->n_pad + 8), p4 = 16 * ((size_t)ds->n_pad + 8);
+        if (fin8 && ncols > 4 && p8 <= kFin8SmemMax) return mr_launch_finalize_pad<true>(ds, cols, ncols, p8);
+        if (p4 <= 200 * 1024) return mr_launch_finalize_pad<false>(ds, cols, ncols, p4);
+    }
     const size_t f8 = 32 * ((size_t)ds->n_pad + 1);
     if (fin8 && ncols > 4 && f8 <= kFin8SmemMax) return mr_launch_finalize8<IdxT>(ds, cols, ncols, f8);
     const size_t f = sizeof(float) * (size_t)ds->n_pad;
@@ -954,46 +1055,57 @@ static int mr_pass(const MrPass &P, MrShape sh, const TuneEvents *te, size_t e0,
     prof_end(prof, s);
     if (te) IHT_CUDA(cudaEventRecord(te->ev[e0 + 1], s));
     if (te) IHT_CUDA(cudaEventRecord(te->ev[e0 + 2], s));
-    const int rc = P.ds->miss_idx16 ? mr_finalize<uint16_t>(P.ds, P.cols, P.nc, sh.fin8 != 0)
-                                    : mr_finalize<int32_t>(P.ds, P.cols, P.nc, sh.fin8 != 0);
+    const int rc = P.ds->miss_idx16 ? mr_finalize<uint16_t>(P.ds, P.cols, P.nc, sh.fin8 != 0, sh.padded != 0)
+                                    : mr_finalize<int32_t>(P.ds, P.cols, P.nc, sh.fin8 != 0, sh.padded != 0);
     if (rc) return rc;
     if (te) IHT_CUDA(cudaEventRecord(te->ev[e0 + 3], s));
     return IHT_OK;
 }
 
-// First pass of a bucket: the pass and its finalisation once per candidate
-// shape (genotype stages 4, 6, 8 x pairs on, off; finalisation widths
-// alternating), each run writing the same g (the finalisation reads the pass's
-// output in place, so each candidate runs both).  The fastest pass shape and
-// the faster finalisation are cached.  prof brackets the first candidate's pass.
+// First pass of a bucket: the pass and its finalisation once per run, the
+// pass cycling through the candidate shapes (genotype stages 4, 6, 8 x pairs
+// on, off) and the finalisation through its variants (8 or 4 columns per
+// block x plain or padded lists), each run writing the same g (the
+// finalisation reads the pass's output in place, so each run does both).  The
+// fastest pass shape and the fastest finalisation are cached.  prof brackets
+// the first run's pass.
 static int mr_tune(const MrPass &P, ProfEvents *prof)
 {
     std::vector<MrShape> cand;
     for (int ngs : {4, 6, 8})
         for (int pairs : {1, 0}) {
-            const MrShape sh{ngs, pairs, (int)(cand.size() % 2 == 0)};
+            const MrShape sh{ngs, pairs, 1, 0};
             int nbst, nbufs;
             if (mr_shape_launch(P.N, sh, &nbst, &nbufs)) cand.push_back(sh);
         }
-    TuneEvents te(4 * cand.size());
+    const int fins[4][2] = {{1, 1}, {0, 1}, {1, 0}, {0, 0}};    // (fin8, padded)
+    const int nfin = P.ds->miss_gidx ? 4 : 2;
+    const size_t runs = std::max(cand.size(), (size_t)nfin);
+    TuneEvents te(4 * runs);
     IHT_CUDA(te.create());
-    for (size_t c = 0; c < cand.size(); ++c)
-        if (int rc = mr_pass(P, cand[c], &te, 4 * c, c == 0 ? prof : nullptr)) return rc;
-    IHT_CUDA(cudaStreamSynchronize(P.ds->ctx->stream));
-    float best = 1e30f, fin_best[2] = {1e30f, 1e30f};
-    int prm[kTuneParams] = {0, 0, 1, 0};
-    for (size_t c = 0; c < cand.size(); ++c) {
-        const float k = te.ms(4 * c, 4 * c + 1), f = te.ms(4 * c + 2, 4 * c + 3);
-        if (k < best) {
-            best = k;
-            prm[0] = cand[c].ngs;
-            prm[1] = cand[c].pairs;
-        }
-        fin_best[cand[c].fin8] = std::min(fin_best[cand[c].fin8], f);
+    for (size_t r = 0; r < runs; ++r) {
+        MrShape sh = cand[r % cand.size()];
+        sh.fin8 = fins[(P.ds->miss_gidx ? 0 : 2) + r % nfin][0];
+        sh.padded = fins[(P.ds->miss_gidx ? 0 : 2) + r % nfin][1];
+        if (int rc = mr_pass(P, sh, &te, 4 * r, r == 0 ? prof : nullptr)) return rc;
     }
-    prm[2] = fin_best[0] < fin_best[1] ? 0 : 1;
-    tune_store(P.ds, IHT_PASS_MULTI, mr_bucket_of(P.N), prm, best + std::min(fin_best[0], fin_best[1]),
-               (int)cand.size());
+    IHT_CUDA(cudaStreamSynchronize(P.ds->ctx->stream));
+    float best = 1e30f, fin_best = 1e30f;
+    int prm[kTuneParams] = {0, 0, 1, 0};
+    for (size_t r = 0; r < runs; ++r) {
+        const float k = te.ms(4 * r, 4 * r + 1), f = te.ms(4 * r + 2, 4 * r + 3);
+        if (r < cand.size() && k < best) {
+            best = k;
+            prm[0] = cand[r].ngs;
+            prm[1] = cand[r].pairs;
+        }
+        if (f < fin_best) {
+            fin_best = f;
+            prm[2] = fins[(P.ds->miss_gidx ? 0 : 2) + r % nfin][0];
+            prm[3] = fins[(P.ds->miss_gidx ? 0 : 2) + r % nfin][1];
+        }
+    }
+    tune_store(P.ds, IHT_PASS_MULTI, mr_bucket_of(P.N), prm, best + fin_best, (int)runs);
     return IHT_OK;
 }
 
@@ -1068,7 +1180,7 @@ int launch_grad_mrhs(iht_dataset *ds, MrCol *cols, int ncols, ProfEvents *prof, 
         const MrPass pass{ds, &map, grid, ksteps, N, nc, cols + c0};
         int prm[kTuneParams];
         if (tune_lookup(ds, IHT_PASS_MULTI, mr_bucket_of(N), prm))
-            rc = mr_pass(pass, MrShape{prm[0], prm[1], prm[2]}, nullptr, 0, prof);
+            rc = mr_pass(pass, MrShape{prm[0], prm[1], prm[2], prm[3]}, nullptr, 0, prof);
         else if (may_tune)
             rc = mr_tune(pass, prof);
         else

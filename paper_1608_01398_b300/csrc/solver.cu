@@ -62,15 +62,16 @@ __global__ void __launch_bounds__(1024) k_gather_gS(const float *__restrict__ g,
 // the observed calls (Z[:, cols] coef, Sec. 2.3.2-2.3.3), on used rows (0
 // elsewhere); per-block sums of out, out^2 and (out - prev)^2 (0 without
 // prev) go to partials[3 b .. 3 b + 2].  One thread per sample, 128 samples
-// per block (FP64 issue, not parallelism, bounds this product: smaller blocks
-// only multiply the partial triples every consumer sums); each column's three
-// possible terms a (x - u)
-// for x = 0, 1, 2 are staged in shared memory kZmulChunk columns at a time, so
-// a term costs one FP64 add (FP64 issue is the scarce resource here), added in
-// column order.  A thread loads the genotype bytes of a chunk's first
-// kZmulFirst columns (column index, then byte) while the block stages the
-// terms, and the rest kZmulBatch columns at a time, so the latency of a chunk
-// is about two dependent loads.
+// per block (smaller blocks only multiply the partial triples every consumer
+// sums); each column's three possible terms a (x - u) for x = 0, 1, 2 are
+// staged in shared memory kZmulChunk columns at a time, so a term costs one
+// FP64 add, added in column order.  The product is a chain of dependent steps
+// (global loads, FP64 adds, block reductions) on a few warps per SM, so the
+// body shortens the chain: the row values (used, base, prev) are requested
+// first; a thread loads the genotype bytes of a chunk's first kZmulFirst
+// columns (column index, then byte) while the block stages the terms, and the
+// rest kZmulBatch columns at a time; the three block sums share one
+// reduction.
 constexpr int kZmulChunk = 256;
 constexpr int kZmulThreads = 128;           // largest block
 constexpr int kZmulFirst = 64;
@@ -86,13 +87,17 @@ __device__ __forceinline__ void zmul_body(const uint8_t *__restrict__ G, int64_t
                                           const double *__restrict__ prev, double *__restrict__ out,
                                           double *__restrict__ partials, int64_t n_pad)
 {
-    __shared__ double red[8];
+    __shared__ double red[3 * (kZmulThreads / 32)];
     __shared__ double term[kZmulChunk][4];     // terms for codes 00, 01 (missing: 0), 10, 11
     __shared__ const uint8_t *srow[kZmulChunk];
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t byte = i >> 2;
     const int shift = 2 * (int)(i & 3);
     const bool inb = i < n_pad && byte < rowb;
+    const bool in = i < n_pad;
+    const int32_t ui = in ? used[i] : 0;
+    const double bi = in && base ? base[i] : 0.0;
+    const double pi = in && prev ? prev[i] : 0.0;
     double acc = 0.0;
     for (int c0 = 0; c0 < m; c0 += kZmulChunk) {
         const int mc = min(kZmulChunk, m - c0);
@@ -138,14 +143,13 @@ __device__ __forceinline__ void zmul_body(const uint8_t *__restrict__ G, int64_t
         }
     }
     double o = 0.0, d = 0.0;
-    if (i < n_pad) {
-        o = used[i] ? (base ? base[i] : 0.0) + acc : 0.0;
+    if (in) {
+        o = ui ? bi + acc : 0.0;
         out[i] = o;
-        if (prev) d = o - prev[i];
+        if (prev) d = o - pi;
     }
-    const double s = block_sum(o, red);
-    const double s2 = block_sum(o * o, red);
-    const double d2 = block_sum(d * d, red);
+    double s = o, s2 = o * o, d2 = d * d;
+    block_sum3(s, s2, d2, red);
     if (threadIdx.x == 0 && partials) {
         partials[3 * blockIdx.x] = s;
         partials[3 * blockIdx.x + 1] = s2;

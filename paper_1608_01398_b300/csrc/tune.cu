@@ -26,7 +26,7 @@ using Key = std::tuple<int, int64_t, int64_t, int, int>;   // device, n_pad, p, 
 struct Choice {
     int params[kTuneParams];
     double ms;          // time of the chosen shape (0: pinned)
-    int candidates;     // shapes timed (0: pinned)
+    int candidates;     // timed runs (0: pinned)
 };
 
 std::mutex g_tune_mu;
@@ -90,7 +90,7 @@ static int tune_bucket_checked(const iht_dataset *ds, int kind, int ncols, const
     return -1;
 }
 
-static int tune_nparams(int kind) { return kind == IHT_PASS_SINGLE ? 1 : 3; }
+static int tune_nparams(int kind) { return kind == IHT_PASS_SINGLE ? 1 : 4; }
 
 }  // namespace iht
 
@@ -146,15 +146,15 @@ int iht_tuning_summary(char *buf, size_t buf_bytes)
             const char *how = c.candidates ? "tuned" : "pinned";
             if (std::get<3>(k) == IHT_PASS_SINGLE)
                 snprintf(line, sizeof line,
-                         "single-column device %d n_pad %lld p %lld: tma_stages %d (%s, %.3f ms, %d shapes)\n",
+                         "single-column device %d n_pad %lld p %lld: tma_stages %d (%s, %.3f ms, %d runs)\n",
                          std::get<0>(k), (long long)std::get<1>(k), (long long)std::get<2>(k), c.params[0],
                          how, c.ms, c.candidates);
             else
                 snprintf(line, sizeof line,
                          "multi-column device %d n_pad %lld p %lld N<=%d: genotype_stages %d pairs %d "
-                         "finalise8 %d (%s, %.3f ms, %d shapes)\n",
+                         "finalise8 %d padded %d (%s, %.3f ms, %d runs)\n",
                          std::get<0>(k), (long long)std::get<1>(k), (long long)std::get<2>(k), std::get<4>(k),
-                         c.params[0], c.params[1], c.params[2], how, c.ms, c.candidates);
+                         c.params[0], c.params[1], c.params[2], c.params[3], how, c.ms, c.candidates);
             out += line;
         }
     }
