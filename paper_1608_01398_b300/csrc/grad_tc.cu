@@ -549,6 +549,8 @@ struct TcWork {
     size_t bbytes = 0;
     TcParams *prm = nullptr;
     int dev = -1;
+    cudaStream_t side = nullptr;            // missing-call sums beside the limb kernel
+    cudaEvent_t fork = nullptr, join = nullptr;
 };
 static thread_local TcWork g_tc;
 
@@ -620,19 +622,42 @@ int prepare_grad_tc_to(iht_dataset *ds, const float *r32, float *Mj, const int32
     if (w.dev != ds->ctx->device || w.bbytes < bbytes) {
         if (w.bimg) cudaFree(w.bimg);
         if (w.prm) cudaFree(w.prm);
+        if (w.dev != ds->ctx->device) {
+            if (w.side) cudaStreamDestroy(w.side);
+            if (w.fork) cudaEventDestroy(w.fork);
+            if (w.join) cudaEventDestroy(w.join);
+            w.side = nullptr;
+            w.fork = w.join = nullptr;
+        }
         w.bimg = nullptr;
         w.prm = nullptr;
         w.bbytes = 0;
         IHT_CUDA(cudaMalloc(&w.bimg, bbytes));
         IHT_CUDA(cudaMalloc(&w.prm, sizeof(TcParams)));
         IHT_CUDA(cudaMemsetAsync(w.bimg, 0, bbytes, s));   // zero groups and unused limb rows
+        if (!w.side) {
+            IHT_CUDA(cudaStreamCreateWithFlags(&w.side, cudaStreamNonBlocking));
+            IHT_CUDA(cudaEventCreateWithFlags(&w.fork, cudaEventDisableTiming));
+            IHT_CUDA(cudaEventCreateWithFlags(&w.join, cudaEventDisableTiming));
+        }
         w.bbytes = bbytes;
         w.dev = ds->ctx->device;
     }
+    // The limb kernel (one block) and the missing-call sums read the same
+    // residual and nothing of each other: the sums run on a side stream forked
+    // from and joined back to the caller's (two branches of a captured graph).
+    IHT_CUDA(cudaEventRecord(w.fork, s));
+    IHT_CUDA(cudaStreamWaitEvent(w.side, w.fork, 0));
+    ds->ctx->stream = w.side;
+    const int rc = launch_missing_sums(ds, r32, Mj, done);
+    ds->ctx->stream = s;
+    if (rc) return rc;
+    IHT_CUDA(cudaEventRecord(w.join, w.side));
     k_limbs<<<1, 1024, 0, s>>>(r32, (int64_t)ksteps * kTcStepSamples, w.bimg, w.prm, done);
     note_launch();
     IHT_CUDA(cudaGetLastError());
-    return launch_missing_sums(ds, r32, Mj, done);
+    IHT_CUDA(cudaStreamWaitEvent(s, w.join, 0));
+    return IHT_OK;
 }
 
 int prepare_grad_tc(iht_dataset *ds, const float *r32, const int32_t *done)
@@ -736,6 +761,9 @@ void grad_tc_release_thread()
     TcWork &w = g_tc;
     if (w.bimg) cudaFree(w.bimg);
     if (w.prm) cudaFree(w.prm);
+    if (w.side) cudaStreamDestroy(w.side);
+    if (w.fork) cudaEventDestroy(w.fork);
+    if (w.join) cudaEventDestroy(w.join);
     w = TcWork();
 }
 
