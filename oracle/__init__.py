@@ -215,3 +215,47 @@ def iht(G: Geno, y, k: int, rows=None, max_iter: int = 100, tol: float = 1e-4, c
         it = info.iterations
         tr = {nm: arr[:it] for nm, arr in tr.items()}
     return Fit(beta, supp, info.iterations, rc, info.backtracks, info.objective, info.mu, tr)
+
+
+@dataclass
+class CV:
+    mse: np.ndarray          # [nk]: out-of-fold MSE averaged over the q folds
+    mse_fold: np.ndarray     # [q, nk]: each fold's out-of-fold MSE
+    k_best: int
+    fit: Fit                 # the refit on all rows at k_best
+    fits: list               # fits[f][t]: fold f's fit at ks[t]
+
+
+def cv(G: Geno, y, fold, q: int, ks, max_iter: int = 100, tol: float = 1e-4, c: float = 0.01,
+       kappa: float = 2.0, max_backtrack: int = 50, lib=None) -> CV:
+    """q-fold cross-validation over the model sizes ks, then the refit (Sec. 2.4).
+
+    fold[i] in 0..q-1 is subject i's partition.  The path is fitted on the other
+    q - 1 partitions (statistics of those rows); partition f is the test set:
+    its MSE is the mean over its rows of (y_i - z_i^T beta)^2, z_i standardised
+    with the training rows' statistics (the reading the batched solves use).
+    The curve averages the q partitions' MSEs (the paper plots MSE averaged
+    over the cross-validation slices); k_best is the first model size in ks
+    with the least averaged MSE, and the model is refitted on all rows with
+    ||beta||_0 <= k_best.
+    """
+    y = np.ascontiguousarray(y, dtype=np.float64)
+    fold = np.asarray(fold)
+    ks = [int(k) for k in ks]
+    kw = dict(max_iter=max_iter, tol=tol, c=c, kappa=kappa, max_backtrack=max_backtrack, lib=lib)
+    mse_fold = np.zeros((q, len(ks)))
+    fits = []
+    for f in range(q):
+        train = np.flatnonzero(fold != f).astype(np.int32)
+        test = np.flatnonzero(fold == f).astype(np.int32)
+        _, ut, vt = counts(G, train, lib)
+        row = []
+        for t, k in enumerate(ks):
+            fit = iht(G, y[train], k, rows=train, trace=False, **kw)
+            pred = zmul(G, fit.support, fit.beta[fit.support], test, ut, vt, lib)
+            mse_fold[f, t] = np.mean((y[test] - pred) ** 2)
+            row.append(fit)
+        fits.append(row)
+    mse = mse_fold.mean(axis=0)
+    k_best = ks[int(np.argmin(mse))]
+    return CV(mse, mse_fold, k_best, iht(G, y, k_best, trace=False, **kw), fits)

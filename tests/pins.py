@@ -328,6 +328,40 @@ def pin_orientation(lib):
     assert np.allclose(a.beta, -b.beta, rtol=1e-9, atol=1e-12)
 
 
+def pin_cv(lib):
+    """Cross-validation (Sec. 2.4) against numpy: each partition's rows
+    standardised with the numpy statistics of the other partitions' rows,
+    predictions from the fold fits, each partition's MSE, their mean per model
+    size (unequal partitions, so a pooled MSE would differ), the first least
+    size and the refit on all rows."""
+    rng, G, codes = _panel(41, 150, 40, miss=0.03)
+    y = np_Z(codes)[:, [3, 17, 30]] @ np.array([0.8, -0.6, 0.7]) + rng.normal(size=G.n)
+    q, ks = 3, [1, 2, 3, 5]
+    fold = rng.permutation(np.repeat(np.arange(q), [40, 50, 60]))
+    res = oracle.cv(G, y, fold, q, ks, lib=lib)
+    d = np_dosage(codes)                                        # p x n, NaN = missing
+    want = np.zeros((q, len(ks)))
+    for f in range(q):
+        tr, te = fold != f, fold == f
+        with np.errstate(invalid="ignore", divide="ignore"):
+            m = np.nanmean(d[:, tr], axis=1)
+            s = np.nanstd(d[:, tr], axis=1, ddof=1)
+            zt = (d[:, te] - m[:, None]) / s[:, None]
+        zt[~np.isfinite(zt)] = 0.0
+        zt[(s == 0) | ~np.isfinite(s), :] = 0.0
+        for t, k in enumerate(ks):
+            fit = res.fits[f][t]
+            alone = oracle.iht(G, y[tr], k, rows=np.flatnonzero(tr).astype(np.int32), trace=False,
+                               lib=lib)
+            assert np.array_equal(fit.beta, alone.beta), "fold fit is the training-rows solve"
+            want[f, t] = np.mean((y[te] - zt.T @ fit.beta) ** 2)
+    assert np.allclose(res.mse_fold, want, rtol=1e-10, atol=0), "partition MSE"
+    assert np.allclose(res.mse, want.mean(axis=0), rtol=1e-10, atol=0), "MSE averaged over partitions"
+    assert res.k_best == ks[int(np.argmin(want.mean(axis=0)))], "least averaged MSE"
+    refit = oracle.iht(G, y, res.k_best, trace=False, lib=lib)
+    assert np.array_equal(res.fit.beta, refit.beta), "refit on all rows at k_best"
+
+
 ALL_PINS = [pin_decode, pin_counts_stats, pin_stats_exact, pin_gradient, pin_identity, pin_topk,
             pin_k1_marginal, pin_fixed_point, pin_full_ols, pin_noiseless, pin_bruteforce,
-            pin_invariants, pin_orientation]
+            pin_invariants, pin_orientation, pin_cv]
