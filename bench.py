@@ -387,7 +387,7 @@ def cv_setup(cfg, rank=0):
     y, _, _ = synth.config_phenotype(cfg, pn, which=rank)
     lab = synth.cv_folds(pn.n, c["folds"], synth.BASE_SEED + 1000 * cfg + 7 + 101 * rank)
     train = [np.flatnonzero(lab != f).astype(np.int32) for f in range(c["folds"])]
-    return c, pn, bed, y, train
+    return c, pn, bed, y, train, lab
 
 
 def cv_reference(args, c, pn, bed, y, train, iters_per_solve=None):
@@ -412,7 +412,7 @@ def cv_reference_arm(args):
     rank, _, world = dist_env()
     if rank != 0:
         return 0
-    c, pn, bed, y, train = cv_setup(3)
+    c, pn, bed, y, train, _ = cv_setup(3)
     for _ in range(args.warmup):
         pass     # the oracle has no warm state: each step is a fresh bounded sample
     vals = [cv_reference(args, c, pn, bed, y, train) for _ in range(max(args.steps, 1))]
@@ -443,7 +443,7 @@ def cv_arm(args):
     torch.cuda.set_device(local_rank)
     dev = local_rank
     t0 = time.perf_counter()
-    c, pn, bed, y, train = cv_setup(3, rank)
+    c, pn, bed, y, train, lab = cv_setup(3, rank)
     n, p = c["n"], c["p"]
     log(f"[bench] rank {rank}: generated {bed.nbytes / 1e6:.0f} MB panel in "
         f"{time.perf_counter() - t0:.1f}s")
@@ -516,6 +516,15 @@ def cv_arm(args):
     torch.cuda.synchronize(dev)
     e2e_wall = time.perf_counter() - w0
 
+    # the whole model selection through iht_cv (Sec. 2.4): the 5 x 20 fits,
+    # out-of-fold MSE on the device, k_best, the refit on all rows; host in and out
+    iht.iht_cv(ds, y, lab, c["ks"], tol=c["tol"], max_iter=c["max_iter"])      # warm (tuned, graphs)
+    torch.cuda.synchronize(dev)
+    w0 = time.perf_counter()
+    sel = iht.iht_cv(ds, y, lab, c["ks"], tol=c["tol"], max_iter=c["max_iter"])
+    torch.cuda.synchronize(dev)
+    sel_s = time.perf_counter() - w0
+
     allv = gather_rows([solves, elapsed, args.steps * b, e2e_wall], world)
     if rank == 0:
         value = weak_rate(allv, 0, 1)
@@ -542,6 +551,12 @@ def cv_arm(args):
             "plain": {"value": b / plain_s, "unit": "solves/s",
                       "what": "the same 100 solves one at a time through iht_fit (single-column path)",
                       "iterations": plain_its},
+            "model_selection": {"seconds": sel_s, "k_best": int(sel.k_best),
+                                "mse_at_k_best": float(sel.mse[list(c["ks"]).index(sel.k_best)]),
+                                "refit_iterations": int(sel.fit.iterations),
+                                "what": "iht_cv wall time: 5 folds x k = 1..20 as one batch, "
+                                        "out-of-fold MSE on the device, the refit at k_best; "
+                                        "host inputs and outputs"},
             "speedup_vs_plain": value / (b / plain_s),
             "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                          "frac": (achieved / peak) if achieved else None,

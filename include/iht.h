@@ -270,6 +270,31 @@ int iht_fit_batch(iht_dataset *ds, int32_t b, const iht_solve_desc *solves,
                   const iht_options *opt, double *betas, int32_t *supports, double *beta_s,
                   iht_result *infos);
 
+/* Model selection -- q-fold cross-validation over a path of model sizes, then
+ * the refit (Sec. 2.4).  Every (partition, size) pair is one solve of a single
+ * iht_fit_batch: partition f's path is fitted on the other partitions' rows
+ * (statistics of those rows); its mean squared error is taken on partition
+ * f's rows on the device, z standardised with the training rows' statistics;
+ * the errors are averaged over the q partitions, the first size in ks with the
+ * least average is chosen and the model is refitted on all n rows.
+ *   y           : host double[n]
+ *   fold        : host int32[n], subject i's partition in 0..q-1; every
+ *                 partition needs a row and its complement at least 2
+ *   q           : partitions, 2..64
+ *   ks, nk      : host int32[nk] model sizes, each in 1..min(p, 1024)
+ *   opt         : solver options (in_mem, out_mem ignored: host in and out)
+ *   mse         : host double[nk] averaged out-of-fold MSE, or NULL
+ *   mse_fold    : host double[q][nk] each partition's MSE, or NULL
+ *   k_best      : host int32, the chosen size, or NULL
+ *   beta_out    : host double[p] refit coefficients, or NULL
+ *   support_out : host int32[k_best] refit support (capacity max ks), or NULL
+ *   info        : host iht_result of the refit, or NULL
+ * Returns the refit's status (OK or ENOTCONV), or EINVAL, ENOMEM, ENUMERIC
+ * (non-finite y), ETIMEOUT, ECUDA. */
+int iht_cv(iht_dataset *ds, const double *y, const int32_t *fold, int32_t q, const int32_t *ks,
+           int32_t nk, const iht_options *opt, double *mse, double *mse_fold, int32_t *k_best,
+           double *beta_out, int32_t *support_out, iht_result *info);
+
 /* a7 -- multi-right-hand-side standardised gradient G = Z^T R for b residual
  * columns, each with its own row set and statistics (exposes the batched
  * gradient for tests).

@@ -30,7 +30,7 @@ EXPORTED = ["iht_default_options", "iht_strerror", "iht_last_cuda_error", "iht_k
             "iht_server_create", "iht_server_submit", "iht_server_poll", "iht_server_get_stats",
             "iht_server_destroy", "iht_state_bytes", "iht_state_save", "iht_state_load",
             "iht_fit_resume", "iht_set_autotune", "iht_tune_clear", "iht_tune_pin", "iht_tune_query",
-            "iht_tuning_summary"]
+            "iht_tuning_summary", "iht_cv"]
 
 
 class IhtError(RuntimeError):
@@ -147,6 +147,8 @@ def _lib(build_if_stale: bool = True):
         "iht_tune_pin": (ctypes.c_int, [P, i32, i32, P, i32]),
         "iht_tune_query": (ctypes.c_int, [P, i32, i32, P, i32]),
         "iht_tuning_summary": (ctypes.c_int, [P, sz]),
+        "iht_cv": (ctypes.c_int, [P, P, P, i32, P, i32, ctypes.POINTER(iht_options), P, P,
+                                  ctypes.POINTER(i32), P, P, ctypes.POINTER(iht_result)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -456,6 +458,41 @@ def iht_fit_resume(ds: Dataset, y, state: bytes, rows=None, **opt) -> FitResult:
     o = iht_default_options(**opt)
     o.out_mem = IHT_DEVICE if out_device else IHT_HOST
     return _fit(ds, y, load_state(state).k, rows, o, trace=False, state=state)
+
+
+@dataclass
+class CVResult:
+    mse: np.ndarray          # [nk] out-of-fold MSE averaged over the partitions
+    mse_fold: np.ndarray     # [q, nk]
+    k_best: int
+    fit: FitResult           # refit on all rows at k_best
+
+
+def iht_cv(ds: Dataset, y, fold, ks, q: int = None, **opt) -> CVResult:
+    """q-fold cross-validation over the model sizes ks and the refit (iht_cv).
+
+    y: host phenotype (n); fold: host partition label per subject (0..q-1).
+    """
+    y = np.ascontiguousarray(y, dtype=np.float64)
+    fold = np.ascontiguousarray(fold, dtype=np.int32)
+    ks = np.ascontiguousarray(ks, dtype=np.int32)
+    q = int(fold.max()) + 1 if q is None else int(q)
+    o = iht_default_options(**opt)
+    mse = np.empty(ks.size)
+    mse_fold = np.empty((q, ks.size))
+    kb = ctypes.c_int32()
+    beta = np.empty(ds.p)
+    supp = np.empty(int(ks.max()), np.int32)
+    info = iht_result()
+    rc = _lib().iht_cv(ds.h, y.ctypes.data, fold.ctypes.data, q, ks.ctypes.data, ks.size,
+                       ctypes.byref(o), mse.ctypes.data, mse_fold.ctypes.data, ctypes.byref(kb),
+                       beta.ctypes.data, supp.ctypes.data, ctypes.byref(info))
+    _check(rc, "iht_cv", ok=(IHT_OK, IHT_ENOTCONV))
+    k = kb.value
+    fit = FitResult(beta, supp[:k].copy(), info.iterations, rc, info.backtracks, info.objective,
+                    info.mu, None, info.grad_ms, info.grad_launches, beta[supp[:k]].copy(),
+                    info.graph_replays)
+    return CVResult(mse, mse_fold, k, fit)
 
 
 def set_autotune(on: bool) -> None:

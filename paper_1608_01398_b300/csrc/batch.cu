@@ -388,6 +388,25 @@ static int batch_graph(iht_dataset *ds, BatchWork *w, int b, int kmax, int impl,
     return IHT_OK;
 }
 
+// Device scratch of one cross-validation call, freed with the object.
+struct CvScratch {
+    std::vector<void *> p;
+    ~CvScratch()
+    {
+        for (void *x : p)
+            if (x) cudaFree(x);
+    }
+    template <typename T>
+    cudaError_t alloc(T **out, size_t count)
+    {
+        void *x = nullptr;
+        const cudaError_t e = cudaMalloc(&x, std::max<size_t>(16, sizeof(T) * count));
+        if (e == cudaSuccess) p.push_back(x);
+        *out = static_cast<T *>(x);
+        return e;
+    }
+};
+
 }  // namespace iht
 
 using namespace iht;
@@ -635,6 +654,151 @@ int iht_fit_batch(iht_dataset *ds, int32_t b, const iht_solve_desc *solves,
         }
     }
     return IHT_OK;
+}
+
+int iht_cv(iht_dataset *ds, const double *y, const int32_t *fold, int32_t q, const int32_t *ks, int32_t nk,
+           const iht_options *opt_in, double *mse, double *mse_fold, int32_t *k_best, double *beta_out,
+           int32_t *support_out, iht_result *info)
+{
+    if (!ds || !y || !fold || !ks || q < 2 || q > 64 || nk < 1) return IHT_EINVAL;
+    iht_options opt;
+    if (opt_in)
+        opt = *opt_in;
+    else
+        iht_default_options(&opt);
+    const int64_t n = ds->n, p = ds->p;
+    for (int t = 0; t < nk; ++t)
+        if (ks[t] < 1 || ks[t] > p || ks[t] > kMaxK) return IHT_EINVAL;
+    // partitions: test rows of f, training rows = the other partitions'
+    std::vector<std::vector<int32_t>> train(q), test(q);
+    for (int64_t i = 0; i < n; ++i) {
+        const int32_t f = fold[i];
+        if (f < 0 || f >= q) return IHT_EINVAL;
+        test[f].push_back((int32_t)i);
+    }
+    for (int f = 0; f < q; ++f) {
+        if (test[f].empty() || n - (int64_t)test[f].size() < 2) return IHT_EINVAL;
+        train[f].reserve(n - test[f].size());
+        for (int64_t i = 0; i < n; ++i)
+            if (fold[i] != f) train[f].push_back((int32_t)i);
+    }
+    std::vector<std::vector<double>> ytr(q);
+    for (int f = 0; f < q; ++f) {
+        ytr[f].resize(train[f].size());
+        for (size_t a = 0; a < train[f].size(); ++a) ytr[f][a] = y[train[f][a]];
+    }
+    const int nb = q * nk;
+    std::vector<iht_solve_desc> solves(nb);
+    int64_t ktot = 0;
+    std::vector<int64_t> koff(nb);
+    for (int f = 0; f < q; ++f)
+        for (int t = 0; t < nk; ++t) {
+            iht_solve_desc &d = solves[f * nk + t];
+            memset(&d, 0, sizeof(d));
+            d.rows = train[f].data();
+            d.n_rows = (int64_t)train[f].size();
+            d.y = ytr[f].data();
+            d.k = ks[t];
+            koff[f * nk + t] = ktot;
+            ktot += ks[t];
+        }
+    DeviceGuard g(ds->ctx->device);
+    if (!g.ok) return IHT_ECUDA;
+    cudaStream_t s = ds->ctx->stream;
+    CvScratch sc;
+    int32_t *sup_d = nullptr, *used_d = nullptr;
+    double *bs_d = nullptr, *y64_d = nullptr, *out_d = nullptr, *part_d = nullptr;
+    CvJob *jobs_d = nullptr;
+    const size_t np = (size_t)ds->n_pad;
+    const int nblk = zmul_blocks(ds);
+    IHT_CUDA(sc.alloc(&sup_d, ktot));
+    IHT_CUDA(sc.alloc(&bs_d, ktot));
+    IHT_CUDA(sc.alloc(&used_d, (size_t)q * np));
+    IHT_CUDA(sc.alloc(&y64_d, np));
+    IHT_CUDA(sc.alloc(&out_d, (size_t)nb * np));
+    IHT_CUDA(sc.alloc(&part_d, (size_t)nb * 3 * nblk));
+    IHT_CUDA(sc.alloc(&jobs_d, (size_t)nb));
+
+    // every (partition, size) fit as one batch, host inputs, device outputs
+    iht_options o = opt;
+    o.in_mem = IHT_HOST;
+    o.out_mem = IHT_DEVICE;
+    std::vector<iht_result> fits(nb);
+    int rc = iht_fit_batch(ds, nb, solves.data(), &o, nullptr, sup_d, bs_d, fits.data());
+    if (rc) return rc;
+    for (const iht_result &r : fits)
+        if (r.status == IHT_ENUMERIC) return IHT_ENUMERIC;
+
+    // out-of-fold residuals with the training rows' statistics (row set f of
+    // the batch: the solves list partition f's training rows first at f * nk)
+    BatchWork *w = ds->ws->bw;
+    std::vector<SetKey> sets;
+    std::vector<int> set_of;
+    {
+        std::vector<const int32_t *> rows(nb);
+        std::vector<int64_t> nrows(nb);
+        for (int c = 0; c < nb; ++c) {
+            rows[c] = solves[c].rows;
+            nrows[c] = solves[c].n_rows;
+        }
+        dedupe_sets(nb, rows.data(), nrows.data(), n, sets, set_of);
+    }
+    std::vector<int32_t> used_h((size_t)q * np, 0);
+    std::vector<double> y64_h(np, 0.0);
+    for (int f = 0; f < q; ++f)
+        for (int32_t i : test[f]) used_h[(size_t)f * np + i] = 1;
+    for (int64_t i = 0; i < n; ++i) y64_h[i] = y[i];
+    std::vector<CvJob> jobs(nb);
+    for (int f = 0; f < q; ++f)
+        for (int t = 0; t < nk; ++t) {
+            const int c = f * nk + t;
+            const RowSet rs = batch_rowset(ds, w, set_of[c]);
+            CvJob &J = jobs[c];
+            J.S = sup_d + koff[c];
+            J.bS = bs_d + koff[c];
+            J.k = ks[t];
+            J.used = used_d + (size_t)f * np;
+            J.u64 = rs.u64;
+            J.v64 = rs.v64;
+            J.y64 = y64_d;
+            J.out = out_d + (size_t)c * np;
+            J.partials = part_d + (size_t)c * 3 * nblk;
+        }
+    IHT_CUDA(cudaMemcpyAsync(used_d, used_h.data(), sizeof(int32_t) * used_h.size(), cudaMemcpyHostToDevice, s));
+    IHT_CUDA(cudaMemcpyAsync(y64_d, y64_h.data(), sizeof(double) * np, cudaMemcpyHostToDevice, s));
+    IHT_CUDA(cudaMemcpyAsync(jobs_d, jobs.data(), sizeof(CvJob) * nb, cudaMemcpyHostToDevice, s));
+    if ((rc = launch_cv_resid(ds, jobs_d, nb))) return rc;
+    std::vector<double> part_h((size_t)nb * 3 * nblk);
+    IHT_CUDA(cudaMemcpyAsync(part_h.data(), part_d, sizeof(double) * part_h.size(), cudaMemcpyDeviceToHost, s));
+    IHT_CUDA(cudaStreamSynchronize(s));
+
+    // MSE per partition and size (block sums in order), averaged over partitions
+    std::vector<double> mf((size_t)q * nk), mm(nk, 0.0);
+    for (int c = 0; c < nb; ++c) {
+        double ss = 0.0;
+        for (int b = 0; b < nblk; ++b) ss += part_h[(size_t)c * 3 * nblk + 3 * b + 1];
+        mf[c] = ss / (double)test[c / nk].size();
+    }
+    for (int t = 0; t < nk; ++t) {
+        double a = 0.0;
+        for (int f = 0; f < q; ++f) a += mf[f * nk + t];
+        mm[t] = a / q;
+    }
+    int best = 0;
+    for (int t = 1; t < nk; ++t)
+        if (mm[t] < mm[best]) best = t;
+    if (mse) memcpy(mse, mm.data(), sizeof(double) * nk);
+    if (mse_fold) memcpy(mse_fold, mf.data(), sizeof(double) * mf.size());
+    if (k_best) *k_best = ks[best];
+
+    // the refit on all rows at the chosen size
+    std::vector<double> bfull(beta_out ? 0 : (size_t)p);
+    std::vector<int32_t> sfull(support_out ? 0 : (size_t)ks[best]);
+    iht_options ro = opt;
+    ro.in_mem = IHT_HOST;
+    ro.out_mem = IHT_HOST;
+    return iht_fit(ds, nullptr, n, y, ks[best], &ro, beta_out ? beta_out : bfull.data(),
+                   support_out ? support_out : sfull.data(), info);
 }
 
 int iht_gradient_batch(iht_dataset *ds, int32_t b, const int32_t *const *rows_list,

@@ -285,6 +285,18 @@ int launch_grad_mrhs(iht_dataset *ds, MrCol *cols_dev, int ncols, ProfEvents *pr
 int grad_mrhs_status(iht_dataset *ds, int *timed_out);
 void grad_mrhs_release_thread();
 uint64_t grad_mrhs_scratch_id();
+// solver.cu: out-of-fold residuals of fitted solves (cross-validation)
+struct CvJob {
+    const int32_t *S;          // k support indices of the fit
+    const double *bS;          // beta on S
+    int32_t k;
+    const int32_t *used;       // n_pad, 1 on the partition's (test) rows
+    const double *u64, *v64;   // statistics of the fit's training rows
+    const double *y64;         // n_pad phenotype (all rows)
+    double *out;               // n_pad: y - Z_S beta_S on the test rows, 0 elsewhere
+    double *partials;          // 3 per block: sum, sum of squares, 0
+};
+int launch_cv_resid(iht_dataset *ds, const CvJob *jobs_dev, int njobs);
 // tune.cu: cached launch shapes of the gradient passes (kind IHT_PASS_SINGLE /
 // IHT_PASS_MULTI; bucket 0 for the single-column pass, else the largest
 // accumulator width of the multi-column bucket)

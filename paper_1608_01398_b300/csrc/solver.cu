@@ -1083,6 +1083,27 @@ __global__ void __launch_bounds__(256) k_decide_b(const BSolve *bs, int npart)
     decide_body(sc, B.partials, npart, B.S, B.bS, B.Sp, B.bSp, TraceDev{});
 }
 
+// Cross-validation (Sec. 2.4): the residual y - Z_S beta_S of each fitted
+// solve over its partition's rows, standardised with its training rows'
+// statistics (the sparse product above, one job per block row).
+__global__ void __launch_bounds__(kZmulThreads) k_cv_resid(const uint8_t *__restrict__ G, int64_t stride,
+                                                  int64_t rowb, const CvJob *jobs, int64_t n_pad)
+{
+    const CvJob &J = jobs[blockIdx.y];
+    zmul_body(G, stride, rowb, J.S, J.k, J.bS, -1.0, J.u64, J.v64, J.used, J.y64, nullptr, J.out, J.partials,
+              n_pad);
+}
+
+int launch_cv_resid(iht_dataset *ds, const CvJob *jobs_dev, int njobs)
+{
+    if (njobs <= 0) return IHT_OK;
+    k_cv_resid<<<dim3(zmul_blocks(ds), njobs), zmul_threads(ds), 0, ds->ctx->stream>>>(ds->G, ds->stride, ds->rowb,
+                                                                                    jobs_dev, ds->n_pad);
+    note_launch();
+    IHT_CUDA(cudaGetLastError());
+    return IHT_OK;
+}
+
 __global__ void k_scatter_beta_b(const BSolve *bs, int64_t p, double *__restrict__ betas)
 {
     const BSolve &B = bs[blockIdx.y];
