@@ -276,10 +276,12 @@ int iht_fit_batch(iht_dataset *ds, int32_t b, const iht_solve_desc *solves,
  * (statistics of those rows); its mean squared error is taken on partition
  * f's rows on the device, z standardised with the training rows' statistics;
  * the errors are averaged over the q partitions, the first size in ks with the
- * least average is chosen and the model is refitted on all n rows.
+ * least average is chosen and the model is refitted on all labelled rows.
  *   y           : host double[n]
- *   fold        : host int32[n], subject i's partition in 0..q-1; every
- *                 partition needs a row and its complement at least 2
+ *   fold        : host int32[n], subject i's partition in 0..q-1, or -1 for
+ *                 a subject outside both the selection and the refit (a
+ *                 held-out test set); every partition needs a row and its
+ *                 complement among the labelled subjects at least 2
  *   q           : partitions, 2..64
  *   ks, nk      : host int32[nk] model sizes, each in 1..min(p, 1024)
  *   opt         : solver options (in_mem, out_mem ignored: host in and out)

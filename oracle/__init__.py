@@ -230,14 +230,16 @@ def cv(G: Geno, y, fold, q: int, ks, max_iter: int = 100, tol: float = 1e-4, c: 
        kappa: float = 2.0, max_backtrack: int = 50, lib=None) -> CV:
     """q-fold cross-validation over the model sizes ks, then the refit (Sec. 2.4).
 
-    fold[i] in 0..q-1 is subject i's partition.  The path is fitted on the other
+    fold[i] in 0..q-1 is subject i's partition, -1 a subject outside the
+    selection and the refit (a held-out test set, as Sec. 3.1 keeps one apart
+    from the cross-validation).  The path is fitted on the other
     q - 1 partitions (statistics of those rows); partition f is the test set:
     its MSE is the mean over its rows of (y_i - z_i^T beta)^2, z_i standardised
     with the training rows' statistics (the reading the batched solves use).
     The curve averages the q partitions' MSEs (the paper plots MSE averaged
     over the cross-validation slices); k_best is the first model size in ks
-    with the least averaged MSE, and the model is refitted on all rows with
-    ||beta||_0 <= k_best.
+    with the least averaged MSE, and the model is refitted on all labelled rows
+    with ||beta||_0 <= k_best.
     """
     y = np.ascontiguousarray(y, dtype=np.float64)
     fold = np.asarray(fold)
@@ -246,7 +248,7 @@ def cv(G: Geno, y, fold, q: int, ks, max_iter: int = 100, tol: float = 1e-4, c: 
     mse_fold = np.zeros((q, len(ks)))
     fits = []
     for f in range(q):
-        train = np.flatnonzero(fold != f).astype(np.int32)
+        train = np.flatnonzero((fold != f) & (fold >= 0)).astype(np.int32)
         test = np.flatnonzero(fold == f).astype(np.int32)
         _, ut, vt = counts(G, train, lib)
         row = []
@@ -258,4 +260,7 @@ def cv(G: Geno, y, fold, q: int, ks, max_iter: int = 100, tol: float = 1e-4, c: 
         fits.append(row)
     mse = mse_fold.mean(axis=0)
     k_best = ks[int(np.argmin(mse))]
-    return CV(mse, mse_fold, k_best, iht(G, y, k_best, trace=False, **kw), fits)
+    inside = np.flatnonzero(fold >= 0).astype(np.int32)
+    refit = (iht(G, y, k_best, trace=False, **kw) if inside.size == fold.size
+             else iht(G, y[inside], k_best, rows=inside, trace=False, **kw))
+    return CV(mse, mse_fold, k_best, refit, fits)

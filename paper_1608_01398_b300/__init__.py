@@ -471,7 +471,8 @@ class CVResult:
 def iht_cv(ds: Dataset, y, fold, ks, q: int = None, **opt) -> CVResult:
     """q-fold cross-validation over the model sizes ks and the refit (iht_cv).
 
-    y: host phenotype (n); fold: host partition label per subject (0..q-1).
+    y: host phenotype (n); fold: host partition label per subject (0..q-1, or
+    -1 for a subject left out of the selection and the refit).
     """
     y = np.ascontiguousarray(y, dtype=np.float64)
     fold = np.ascontiguousarray(fold, dtype=np.int32)

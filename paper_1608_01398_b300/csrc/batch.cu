@@ -669,18 +669,23 @@ int iht_cv(iht_dataset *ds, const double *y, const int32_t *fold, int32_t q, con
     const int64_t n = ds->n, p = ds->p;
     for (int t = 0; t < nk; ++t)
         if (ks[t] < 1 || ks[t] > p || ks[t] > kMaxK) return IHT_EINVAL;
-    // partitions: test rows of f, training rows = the other partitions'
+    // partitions: test rows of f, training rows = the other partitions' (label
+    // -1: a subject outside the selection and the refit)
     std::vector<std::vector<int32_t>> train(q), test(q);
+    std::vector<int32_t> inside;
     for (int64_t i = 0; i < n; ++i) {
         const int32_t f = fold[i];
-        if (f < 0 || f >= q) return IHT_EINVAL;
+        if (f < -1 || f >= q) return IHT_EINVAL;
+        if (f < 0) continue;
         test[f].push_back((int32_t)i);
+        inside.push_back((int32_t)i);
     }
+    const int64_t n_in = (int64_t)inside.size();
     for (int f = 0; f < q; ++f) {
-        if (test[f].empty() || n - (int64_t)test[f].size() < 2) return IHT_EINVAL;
-        train[f].reserve(n - test[f].size());
-        for (int64_t i = 0; i < n; ++i)
-            if (fold[i] != f) train[f].push_back((int32_t)i);
+        if (test[f].empty() || n_in - (int64_t)test[f].size() < 2) return IHT_EINVAL;
+        train[f].reserve(n_in - test[f].size());
+        for (int32_t i : inside)
+            if (fold[i] != f) train[f].push_back(i);
     }
     std::vector<std::vector<double>> ytr(q);
     for (int f = 0; f < q; ++f) {
@@ -791,14 +796,17 @@ int iht_cv(iht_dataset *ds, const double *y, const int32_t *fold, int32_t q, con
     if (mse_fold) memcpy(mse_fold, mf.data(), sizeof(double) * mf.size());
     if (k_best) *k_best = ks[best];
 
-    // the refit on all rows at the chosen size
+    // the refit on all rows of the partitions at the chosen size
     std::vector<double> bfull(beta_out ? 0 : (size_t)p);
     std::vector<int32_t> sfull(support_out ? 0 : (size_t)ks[best]);
     iht_options ro = opt;
     ro.in_mem = IHT_HOST;
     ro.out_mem = IHT_HOST;
-    return iht_fit(ds, nullptr, n, y, ks[best], &ro, beta_out ? beta_out : bfull.data(),
-                   support_out ? support_out : sfull.data(), info);
+    const bool all = n_in == n;
+    std::vector<double> yin(all ? 0 : (size_t)n_in);
+    for (int64_t a = 0; !all && a < n_in; ++a) yin[a] = y[inside[a]];
+    return iht_fit(ds, all ? nullptr : inside.data(), n_in, all ? y : yin.data(), ks[best], &ro,
+                   beta_out ? beta_out : bfull.data(), support_out ? support_out : sfull.data(), info);
 }
 
 int iht_gradient_batch(iht_dataset *ds, int32_t b, const int32_t *const *rows_list,

@@ -171,6 +171,17 @@ def phenotype(pn: Panel, k_star: int, effect_var: float, noise_var: float, seed:
     return y, causal, beta
 
 
+def signal(pn: Panel, causal, beta, rows: np.ndarray | None = None) -> np.ndarray:
+    """Z_pop[rows, causal] @ beta: the noise-free part of ``phenotype``'s y."""
+    return _pop_standardised(pn, np.asarray(causal, dtype=np.int64), rows) @ np.asarray(beta)
+
+
+def sim_path(k_true: int, sizes: int = 100, step: int = 2) -> list:
+    """Model sizes k0, k0 + step, ... straddling k_true (Sec. 3.1: 100 sizes, step 2)."""
+    k0 = max(step, k_true - step * (sizes // 2 - 1))
+    return [k0 + step * i for i in range(sizes)]
+
+
 CONFIGS = {
     # tiny FP64 case the oracle finishes in seconds
     1: dict(name="iht_n1000_p10000_k10", n=1000, p=10000, maf=("uniform", 0.05, 0.5),
@@ -189,6 +200,14 @@ CONFIGS = {
     5: dict(name="panel_n20000_p4000000_32pheno", n=20000, p=4000000,
             maf=("beta", 0.5, 2.0, 0.01, 0.5), miss=0.02, k_star=100, effect_var=0.1,
             noise_var=1.0, phenotypes=32, k=100, tol=1e-4, max_iter=100),
+    # replay of the Sec. 3.1 simulation on a stand-in for its chromosome-1 matrix
+    # (5289 subjects x 23 695 SNPs): k_true in {100, 200, 300}, effects
+    # N(0, 0.01 / s) for SNR 100 / 50 / 10 / 5 % (s = 1, 2, 10, 20), noise
+    # N(0, 0.01), 289 subjects held out, 5-fold CV on the rest over 100 sizes
+    6: dict(name="sim_n5289_p23695_ktrue100to300", n=5289, p=23695,
+            maf=("beta", 0.5, 2.0, 0.01, 0.5), miss=0.01, k_true=[100, 200, 300],
+            snr_s=[1, 2, 10, 20], effect_var=0.01, noise_var=0.01, replicates=10, test=289,
+            folds=5, path=100, path_step=2, tol=1e-4, max_iter=100),
 }
 
 

@@ -333,16 +333,17 @@ def pin_cv(lib):
     standardised with the numpy statistics of the other partitions' rows,
     predictions from the fold fits, each partition's MSE, their mean per model
     size (unequal partitions, so a pooled MSE would differ), the first least
-    size and the refit on all rows."""
+    size and the refit on the labelled rows; subjects labelled -1 (a held-out
+    set) take part in nothing."""
     rng, G, codes = _panel(41, 150, 40, miss=0.03)
     y = np_Z(codes)[:, [3, 17, 30]] @ np.array([0.8, -0.6, 0.7]) + rng.normal(size=G.n)
     q, ks = 3, [1, 2, 3, 5]
-    fold = rng.permutation(np.repeat(np.arange(q), [40, 50, 60]))
+    fold = rng.permutation(np.repeat(np.arange(-1, q), [12, 40, 45, 53]))    # 12 held out
     res = oracle.cv(G, y, fold, q, ks, lib=lib)
     d = np_dosage(codes)                                        # p x n, NaN = missing
     want = np.zeros((q, len(ks)))
     for f in range(q):
-        tr, te = fold != f, fold == f
+        tr, te = (fold != f) & (fold >= 0), fold == f
         with np.errstate(invalid="ignore", divide="ignore"):
             m = np.nanmean(d[:, tr], axis=1)
             s = np.nanstd(d[:, tr], axis=1, ddof=1)
@@ -358,8 +359,9 @@ def pin_cv(lib):
     assert np.allclose(res.mse_fold, want, rtol=1e-10, atol=0), "partition MSE"
     assert np.allclose(res.mse, want.mean(axis=0), rtol=1e-10, atol=0), "MSE averaged over partitions"
     assert res.k_best == ks[int(np.argmin(want.mean(axis=0)))], "least averaged MSE"
-    refit = oracle.iht(G, y, res.k_best, trace=False, lib=lib)
-    assert np.array_equal(res.fit.beta, refit.beta), "refit on all rows at k_best"
+    inside = np.flatnonzero(fold >= 0).astype(np.int32)
+    refit = oracle.iht(G, y[inside], res.k_best, rows=inside, trace=False, lib=lib)
+    assert np.array_equal(res.fit.beta, refit.beta), "refit on the labelled rows at k_best"
 
 
 ALL_PINS = [pin_decode, pin_counts_stats, pin_stats_exact, pin_gradient, pin_identity, pin_topk,

@@ -80,15 +80,16 @@ def test_cv_against_oracle(ctx):
 
 @pytest.mark.gpu
 def test_cv_mse_of_its_own_fits(ctx):
-    """Unequal partitions, k = 1 and a size above the signal: the device MSE of
-    every (partition, size) fit against the FP64 MSE of the same fits, which a
-    batch of the same solves reproduces bit for bit."""
-    n, p, q, ks = 500, 1203, 3, (1, 3, 8)
+    """Unequal partitions, 40 held-out subjects (label -1), k = 1 and a size
+    above the signal: the device MSE of every (partition, size) fit against the
+    FP64 MSE of the same fits, which a batch of the same solves reproduces bit
+    for bit; the refit is iht_fit on the labelled rows."""
+    n, p, q, ks = 540, 1203, 3, (1, 3, 8)
     G, y, rng = _panel(17, n, p, 3)
     ds = _load(ctx, G)
-    fold = rng.permutation(np.repeat(np.arange(q), [120, 170, 210])).astype(np.int32)
+    fold = rng.permutation(np.repeat(np.arange(-1, q), [40, 120, 170, 210])).astype(np.int32)
     res = iht.iht_cv(ds, y, fold, ks)
-    train = [np.flatnonzero(fold != f).astype(np.int32) for f in range(q)]
+    train = [np.flatnonzero((fold != f) & (fold >= 0)).astype(np.int32) for f in range(q)]
     test = [np.flatnonzero(fold == f).astype(np.int32) for f in range(q)]
     fits = iht.iht_fit_batch(ds, [(y[train[f]], k, train[f]) for f in range(q) for k in ks])
     want = np.zeros((q, len(ks)))
@@ -101,6 +102,9 @@ def test_cv_mse_of_its_own_fits(ctx):
             want[f, t] = np.mean((y[test[f]] - pred) ** 2)
     assert np.allclose(res.mse_fold, want, rtol=1e-12, atol=0)
     assert res.k_best == ks[int(np.argmin(want.mean(axis=0)))]
+    inside = np.flatnonzero(fold >= 0).astype(np.int32)
+    alone = iht.iht_fit(ds, y[inside], res.k_best, rows=inside)
+    assert np.array_equal(alone.beta, res.fit.beta) and alone.iterations == res.fit.iterations
 
 
 @pytest.mark.gpu
