@@ -10,18 +10,19 @@
 // solves (a cross-validation fold used along a path of model sizes) have
 // their per-SNP statistics computed once (Sec. 2.3.2).
 //
-// An iteration whose active solves are those of the previous iteration is one
-// replay of a CUDA graph (the gradient pass, candidates, g_S, Z_S g_S and two
-// attempts; the second attempt's kernels return at once for every solve whose
-// first step was accepted), with one host synchronisation.  Graphs are cached
-// per active set, so the replays of a repeated batch start at its second
-// iteration; an iteration after a solve retires runs as direct launches.
+// An iteration is one replay of a CUDA graph (the gradient pass, candidates,
+// g_S, Z_S g_S and two attempts; the second attempt's kernels return at once
+// for every solve whose first step was accepted), with one host
+// synchronisation, once its number of active columns has been seen: a new
+// count runs once as direct launches and is captured when it comes again, in
+// the same call or a later one.
 #include <stdlib.h>
 #include <string.h>
 
 #include <new>
 #include <string>
 #include <unordered_map>
+#include <unordered_set>
 #include <vector>
 
 #include "common.cuh"
@@ -61,6 +62,7 @@ struct BatchWork {
         uint64_t used = 0;                 // last use (least recently used is replaced)
     };
     std::unordered_map<std::string, Graph> graphs;
+    std::unordered_set<std::string> graph_seen;   // keys run once as direct launches
     uint64_t graph_clock = 0;
     cudaStream_t cap_stream = nullptr;
     cudaEvent_t gev[2 * kBatchGraphPairs] = {};
@@ -315,29 +317,41 @@ static int batch_step(iht_dataset *ds, BatchWork *w, int b, int kmax)
     return launch_zmul_batch(ds, w->bs, b, kmax, kZmulStep);
 }
 
+// Key of the iteration graph over ncols active columns (w->cols_host filled).
+// Only the column count shapes the captured launches: the column descriptors
+// live in w->cols, uploaded before every replay, and every other kernel runs
+// over all b solves, each block gated by its solve's flags on the device; a
+// single column with impl 0 runs the single-column pass, whose pointers come
+// from the host and join the key.
+static std::string batch_graph_key(BatchWork *w, int b, int kmax, int impl, bool prof, int ncols)
+{
+    std::vector<uint64_t> key = {(uint64_t)b, (uint64_t)kmax, (uint64_t)impl, (uint64_t)prof,
+                                 grad_mrhs_scratch_id(), grad_tc_scratch_id(), (uint64_t)ncols};
+    if (ncols == 1 && impl != 2) {
+        const MrCol &C = w->cols_host[0];
+        key.insert(key.end(), {(uint64_t)(uintptr_t)C.r32, (uint64_t)(uintptr_t)C.u32, (uint64_t)(uintptr_t)C.v32,
+                               (uint64_t)(uintptr_t)C.g});
+    }
+    return std::string(reinterpret_cast<const char *>(key.data()), key.size() * sizeof(uint64_t));
+}
+
+// The cached graph under key k, or null.
+static BatchWork::Graph *batch_graph_find(BatchWork *w, const std::string &k)
+{
+    auto it = w->graphs.find(k);
+    if (it == w->graphs.end()) return nullptr;
+    it->second.used = ++w->graph_clock;
+    return &it->second;
+}
+
 // The graph of one iteration over the active solves act (multi-column
 // gradient; w->cols uploaded by the caller before every replay), captured on
 // the workspace's private stream (the caller's may be the legacy default
-// stream) and cached under a key of everything its launches were captured
-// with: sizes, options, the thread's pass scratch and, per active solve, its
-// index and the column pointers the single-column pass takes from the host.
+// stream) and cached under k (batch_graph_key).
 static int batch_graph(iht_dataset *ds, BatchWork *w, int b, int kmax, int impl, bool prof,
-                       const std::vector<int> &act, BatchWork::Graph **out)
+                       const std::vector<int> &act, const std::string &k, BatchWork::Graph **out)
 {
-    std::vector<uint64_t> key = {(uint64_t)b, (uint64_t)kmax, (uint64_t)impl, (uint64_t)prof,
-                                 grad_mrhs_scratch_id(), grad_tc_scratch_id(), act.size()};
-    for (size_t a = 0; a < act.size(); ++a) {
-        const MrCol &C = w->cols_host[a];
-        key.insert(key.end(), {(uint64_t)act[a], (uint64_t)(uintptr_t)C.r32, (uint64_t)(uintptr_t)C.u32,
-                               (uint64_t)(uintptr_t)C.v32, (uint64_t)(uintptr_t)C.g});
-    }
-    std::string k(reinterpret_cast<const char *>(key.data()), key.size() * sizeof(uint64_t));
-    auto it = w->graphs.find(k);
-    if (it != w->graphs.end()) {
-        it->second.used = ++w->graph_clock;
-        *out = &it->second;
-        return IHT_OK;
-    }
+    if ((*out = batch_graph_find(w, k))) return IHT_OK;
     if (w->graphs.size() >= kBatchGraphs) {        // replace the least recently used
         auto lru = w->graphs.begin();
         for (auto g = w->graphs.begin(); g != w->graphs.end(); ++g)
@@ -567,10 +581,20 @@ int iht_fit_batch(iht_dataset *ds, int32_t b, const iht_solve_desc *solves,
     std::vector<int> prev;
     for (int it = 0; it < opt.max_iter && !act.empty(); ++it) {
         BatchWork::Graph *gr = nullptr;
-        if (it > 0 && opt.grad_impl != 1 && act == prev) {
-            // same active solves as the last iteration: one replay
+        bool replay = false;
+        std::string key;
+        if (it > 0 && opt.grad_impl != 1) {
+            // a graph for this many active columns exists, or the count ran
+            // before (in this call or an earlier one: capture it now); a new
+            // count runs once as direct launches first (the tuner may time a
+            // new width)
             if ((rc = batch_cols(ds, w, act, set_of))) return rc;
-            if ((rc = batch_graph(ds, w, b, kmax, opt.grad_impl, prof, act, &gr))) return rc;
+            key = batch_graph_key(w, b, kmax, opt.grad_impl, prof, (int)act.size());
+            replay = batch_graph_find(w, key) != nullptr || act == prev || w->graph_seen.count(key);
+            if (!replay && w->graph_seen.size() < 64 * kBatchGraphs) w->graph_seen.insert(key);
+        }
+        if (replay) {
+            if ((rc = batch_graph(ds, w, b, kmax, opt.grad_impl, prof, act, key, &gr))) return rc;
             IHT_CUDA(cudaGraphLaunch(gr->exec, s));
             note_launch(gr->launches);
             ++replays;

@@ -238,11 +238,12 @@ def test_fit_batch_matches_single_solves(iht, ctx):
 
 
 def test_fit_batch_iteration_graphs(iht, ctx):
-    """An iteration whose active solves are those of the previous one replays a
-    cached CUDA graph of the same launches in the same order (gradient pass,
-    selection, step, two attempts), so a batch gives the same bits on its first
-    call, on a repeat that replays cached graphs, alone (a one-column batch runs
-    the single-column pass inside its graph) and through iht_fit."""
+    """An iteration replays a cached CUDA graph of the same launches in the same
+    order (gradient pass, selection, step, two attempts) once a graph for its
+    number of active columns exists, so a batch gives the same bits on its
+    first call, on a repeat that replays the cached graphs from its second
+    iteration on, alone (a one-column batch runs the single-column pass inside
+    its graph) and through iht_fit."""
     n, p = 1200, 3001
     G, codes, y, _, rng = _signal_panel(12, n, p, 5, effect=0.5)
     ds = load(iht, ctx, G)
@@ -251,7 +252,8 @@ def test_fit_batch_iteration_graphs(iht, ctx):
     first = iht.iht_fit_batch(ds, probs)
     again = iht.iht_fit_batch(ds, probs)
     assert first[0].graph_replays > 0
-    assert again[0].graph_replays == first[0].graph_replays
+    its = max(r.iterations for r in first)
+    assert first[0].graph_replays <= again[0].graph_replays <= its - 1
     for (yy, k, rr), f, a in zip(probs, first, again):
         one = iht.iht_fit_batch(ds, [(yy, k, rr)])[0]
         s = iht.iht_fit(ds, yy, k, rows=rr)
