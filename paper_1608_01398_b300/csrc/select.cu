@@ -399,19 +399,21 @@ constexpr size_t kNoAllocHist = sizeof(uint32_t) * kSelBins;      // 8 KB
 constexpr size_t kNoAllocState = 256;                             // SelState, padded
 constexpr size_t kNoAllocBytes = kNoAllocHist + kNoAllocState + sizeof(unsigned long long) * kSelCap;
 
+static_assert(sizeof(SelState) <= kNoAllocState, "selection state must fit its slot");
+
 static __device__ __align__(256) unsigned char g_topk_scratch[kNoAllocBytes];
 
 constexpr int kNoAllocMaxDevices = 64;
 static std::mutex g_noalloc_mu;
 static unsigned char *g_noalloc_addr[kNoAllocMaxDevices] = {};
 static int g_noalloc_sms[kNoAllocMaxDevices] = {};
+static bool g_noalloc_cleared[kNoAllocMaxDevices] = {};
 
 // Device address of the scratch array on `device` (looked up once per device,
 // with that device current; the caller's current device is restored).
-static bool g_noalloc_cleared[kNoAllocMaxDevices] = {};
-
 // first: set when this call is the first on the device (the caller clears the
-// scratch on its stream before using it).
+// scratch on its stream before using it, and calls noalloc_unclear if that
+// fails, so the next call clears it again).
 static int noalloc_scratch(int device, unsigned char **addr, int *num_sms, bool *first)
 {
     if (device < 0 || device >= kNoAllocMaxDevices) return IHT_EINVAL;
@@ -439,6 +441,12 @@ static int noalloc_scratch(int device, unsigned char **addr, int *num_sms, bool 
     return IHT_OK;
 }
 
+static void noalloc_unclear(int device)
+{
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    g_noalloc_cleared[device] = false;
+}
+
 }  // namespace iht
 
 extern "C" int iht_topk_noalloc(int device, void *stream, const float *w, int64_t p, int32_t k,
@@ -458,6 +466,7 @@ extern "C" int iht_topk_noalloc(int device, void *stream, const float *w, int64_
     if (first) {
         const cudaError_t ce = cudaMemsetAsync(scratch, 0, kNoAllocBytes, (cudaStream_t)stream);
         if (ce != cudaSuccess) {
+            noalloc_unclear(device);
             if (prev != device) cudaSetDevice(prev);
             set_cuda_error(ce, "iht_topk_noalloc scratch clear");
             return IHT_ECUDA;
