@@ -317,7 +317,8 @@ int iht_gradient_batch(iht_dataset *ds, int32_t b, const int32_t *const *rows_li
  * buffered, never the arithmetic or its order, so every shape writes the same
  * bits.  The first pass of a kind on a dataset shape (device, padded samples,
  * SNPs; for the multi-column pass also the accumulator-width bucket, 16..64,
- * 80..128, 144..192 or 208..224 accumulator columns, 5 per residual column)
+ * 80..96, 112..128, 144..192 or 208..224 accumulator columns, 5 per residual
+ * column)
  * runs every candidate shape on its real inputs, timed with CUDA events, and
  * caches the fastest for the life of the process; later passes, including
  * those captured into CUDA graphs, use the cached shape.  A pass launched
@@ -327,13 +328,16 @@ int iht_gradient_batch(iht_dataset *ds, int32_t b, const int32_t *const *rows_li
  * kind IHT_PASS_SINGLE (one residual column), params[0]: TMA stages per
  * warpgroup, 2 .. as many as shared memory holds beside the residual image.
  * kind IHT_PASS_MULTI (ncols residual columns in one pass), params[0]:
- * genotype stages 2..8; params[1]: 1 = each decoder step fills a pair of A
- * buffers (needs four or more buffers: 192 accumulator columns at most);
+ * genotype stages 2..8 (4 at most with 4 tiles); params[1]: 1 = each decoder
+ * step fills a pair of A buffers (needs four or more buffers: 192
+ * accumulator columns at most with 2 tiles, 64 with 4);
  * params[2]: 1 = missing-call finalisation over 8 columns per block (when
  * more than 4 columns and the 8-column residual table fits in shared
  * memory); params[3]: 1 = finalisation over the padded missing-call lists
  * (groups of 8 SNPs with common residue-class boundaries, built at upload
- * when n is at most about 12 800; ignored otherwise). */
+ * when n is at most about 12 800; ignored otherwise); params[4]: 128-SNP
+ * tiles per step of a CTA, each with its own MMA-issuing warp: 2, or 4 for
+ * accumulators of at most 96 columns (19 residual columns). */
 enum { IHT_PASS_SINGLE = 0, IHT_PASS_MULTI = 1 };
 
 /* Tuning on (default) or off; IHT_AUTOTUNE=0 in the environment starts it off. */
@@ -343,7 +347,7 @@ void iht_set_autotune(int on);
 void iht_tune_clear(void);
 
 /* Pins the shape of passes of `kind` over ncols columns on this dataset
- * (params: host int32[nparams], nparams 1 for SINGLE, 4 for MULTI).  EINVAL for
+ * (params: host int32[nparams], nparams 1 for SINGLE, 5 for MULTI).  EINVAL for
  * a shape that does not fit the pass or an unknown kind. */
 int iht_tune_pin(const iht_dataset *ds, int32_t kind, int32_t ncols, const int32_t *params,
                  int32_t nparams);

@@ -507,7 +507,7 @@ def tune_clear() -> None:
 
 
 def _nparams(kind: int) -> int:
-    return 1 if kind == IHT_PASS_SINGLE else 4
+    return 1 if kind == IHT_PASS_SINGLE else 5
 
 
 def tune_pin(ds: Dataset, kind: int, ncols: int, params) -> None:

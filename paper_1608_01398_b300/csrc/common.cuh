@@ -300,7 +300,7 @@ int launch_cv_resid(iht_dataset *ds, const CvJob *jobs_dev, int njobs);
 // tune.cu: cached launch shapes of the gradient passes (kind IHT_PASS_SINGLE /
 // IHT_PASS_MULTI; bucket 0 for the single-column pass, else the largest
 // accumulator width of the multi-column bucket)
-constexpr int kTuneParams = 4;
+constexpr int kTuneParams = 5;
 bool autotune_enabled();
 bool tune_lookup(const iht_dataset *ds, int kind, int bucket, int *params);
 void tune_store(const iht_dataset *ds, int kind, int bucket, const int *params, double ms, int candidates);

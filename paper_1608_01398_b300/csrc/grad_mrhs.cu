@@ -46,14 +46,17 @@
 
 namespace iht {
 
-constexpr int kMrTiles = 2;                 // 128-SNP tiles per CTA tile
-constexpr int kMrDecGroups = 2;             // decoder groups per tile (alternate A buffers)
-constexpr int kMrDecoders = 128 * kMrTiles * kMrDecGroups;   // decoder / epilogue threads
+// A CTA takes kTiles 128-SNP tiles per step, each with its own MMA-issuing
+// warp and its own kTiles-th of tensor memory, and kGroups decoder groups of
+// 128 threads per tile (512 decoders either way): 2 tiles x 2 groups, or, for
+// accumulators of at most 96 columns, 4 tiles x 1 group -- one MMA-issuing
+// warp sustains about one MMA per few hundred cycles, so with few columns the
+// pass is bound by the number of issuing warps per SM.
+constexpr int kMrMaxTiles = 4;
+constexpr int kMrDecoders = 512;                             // decoder / epilogue threads
 constexpr int kMrBufArrivals = 128;                          // decoders that fill one tile's A buffer
 constexpr int kMrMmaWarp = kMrDecoders / 32;                 // MMA warps kMrMmaWarp + t, one per tile
-constexpr int kMrGWarp = kMrMmaWarp + kMrTiles;
-constexpr int kMrBWarp = kMrGWarp + 1;
-constexpr int kMrThreads = kMrDecoders + 32 * (kMrTiles + 2);
+__host__ __device__ constexpr int mr_threads(int tiles) { return kMrDecoders + 32 * (tiles + 2); }
 constexpr int kMrStepSamples = 32;          // K of one MMA
 constexpr int kMrLimbs = 5;                 // E4M3 limbs per residual column
 constexpr int kMrGStageBytes = 64;          // packed bytes per row per TMA stage (256 samples)
@@ -270,12 +273,12 @@ __device__ __forceinline__ void mr_decode(uint32_t w, uint32_t *a)
 struct MrPipe {
     uint64_t gfull[kMrMaxGStages], gempty[kMrMaxGStages];
     uint64_t bfull[kMrMaxBStages], bempty[kMrMaxBStages];   // B chunks: shared by the tiles
-    uint64_t afull[kMrTiles][kMrMaxBufs], aempty[kMrTiles][kMrMaxBufs];
-    uint64_t accfull[kMrTiles], accempty[kMrTiles];
+    uint64_t afull[kMrMaxTiles][kMrMaxBufs], aempty[kMrMaxTiles][kMrMaxBufs];
+    uint64_t accfull[kMrMaxTiles], accempty[kMrMaxTiles];
 };
 
-template <bool kPairs>
-__global__ void __launch_bounds__(kMrThreads, 1) k_grad_mrhs(
+template <bool kPairs, int kTiles, int kGroups>
+__global__ void __launch_bounds__(mr_threads(kTiles), 1) k_grad_mrhs(
     const __grid_constant__ CUtensorMap gmap, int64_t p, int ksteps, int N, int ncols, int nbufs,
     int nbst, int ngs, const uint8_t *__restrict__ bimg, const MrCol *__restrict__ cols,
     uint32_t idesc, int *err)
@@ -285,9 +288,12 @@ __global__ void __launch_bounds__(kMrThreads, 1) k_grad_mrhs(
     __shared__ uint32_t tmem_base;
     __shared__ volatile int abort_flag;
 
+    static_assert(kTiles * kGroups * 128 == kMrDecoders && kTiles <= kMrMaxTiles, "decoder layout");
+    constexpr int kGWarp = kMrMmaWarp + kTiles;                // genotype TMA warp (B warp after it)
+    constexpr uint32_t kTmemPerTile = 512u / kTiles;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    uint8_t *gst = smem;                                        // ngs x 2 tiles x 8 KB
-    uint8_t *bst = smem + ngs * kMrTiles * kMrGTile;            // nbst x chunk
+    uint8_t *gst = smem;                                        // ngs x kTiles tiles x 8 KB
+    uint8_t *bst = smem + ngs * kTiles * kMrGTile;              // nbst x chunk
     const uint32_t chunk_bytes = (uint32_t)kMrChunkSteps * (uint32_t)N * 32u;
     const uint32_t step_bytes = (uint32_t)N * 32u;
 
@@ -298,15 +304,15 @@ __global__ void __launch_bounds__(kMrThreads, 1) k_grad_mrhs(
         }
         for (int s = 0; s < nbst; ++s) {
             mr_bar_init(&pipe.bfull[s], 1);
-            mr_bar_init(&pipe.bempty[s], kMrTiles);           // one commit per tile's MMA warp
+            mr_bar_init(&pipe.bempty[s], kTiles);             // one commit per tile's MMA warp
         }
-        for (int t = 0; t < kMrTiles; ++t) {
+        for (int t = 0; t < kTiles; ++t) {
             for (int b = 0; b < nbufs; ++b) {
                 mr_bar_init(&pipe.afull[t][b], kMrBufArrivals);
                 mr_bar_init(&pipe.aempty[t][b], 1);
             }
             mr_bar_init(&pipe.accfull[t], 1);
-            mr_bar_init(&pipe.accempty[t], kMrDecoders / kMrTiles);
+            mr_bar_init(&pipe.accempty[t], kMrDecoders / kTiles);
         }
         abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -320,7 +326,7 @@ __global__ void __launch_bounds__(kMrThreads, 1) k_grad_mrhs(
     __syncthreads();
     mr_fence_after();
 
-    const int64_t ntiles = (p + 128 * kMrTiles - 1) / (128 * kMrTiles);
+    const int64_t ntiles = (p + 128 * kTiles - 1) / (128 * kTiles);
     const int spt = (ksteps + 7) / 8;                   // genotype stages per tile (8 K-steps each)
     const int cpt = ksteps / kMrChunkSteps;             // B chunks per tile
 
@@ -329,13 +335,13 @@ __global__ void __launch_bounds__(kMrThreads, 1) k_grad_mrhs(
     // or modulo sits on their path.
     if (tid < kMrDecoders) {
         // ------------------------------------------------------- decoders + epilogue
-        // warps 8t .. 8t+7 serve tile t: group dg = 0 fills the even A buffers of
-        // the sequence, dg = 1 the odd ones, so two buffers are in flight per
-        // lane quarter and each group's latency chain (decode, tcgen05.st, wait,
-        // arrive) overlaps the other's
-        const int t = warp / (4 * kMrDecGroups), dg = (warp >> 2) % kMrDecGroups, r = tid & 127;
+        // warps 4 kGroups t .. serve tile t; with two groups, group dg = 0 fills
+        // the even A buffers of the sequence and dg = 1 the odd ones, so two
+        // buffers are in flight per lane quarter and each group's latency chain
+        // (decode, tcgen05.st, wait, arrive) overlaps the other's
+        const int t = warp / (4 * kGroups), dg = (warp >> 2) % kGroups, r = tid & 127;
         const uint32_t lane_off = (uint32_t)((warp & 3) * 32) << 16;
-        const uint32_t tb = tmem_base + (uint32_t)(256 * t) + lane_off;
+        const uint32_t tb = tmem_base + kTmemPerTile * (uint32_t)t + lane_off;
         const uint32_t abase = tb + (uint32_t)N;
         const int swz = (r >> 1) & 3;
         uint32_t gslot = 0, gphase = 0;           // genotype stage ring
@@ -355,7 +361,7 @@ __global__ void __launch_bounds__(kMrThreads, 1) k_grad_mrhs(
                     ok = false;
                     break;
                 }
-                const uint8_t *rowp = gst + (gslot * kMrTiles + t) * kMrGTile + r * kMrGStageBytes;
+                const uint8_t *rowp = gst + (gslot * kTiles + t) * kMrGTile + r * kMrGStageBytes;
                 const int nb = min(4, left);
                 left -= nb;
                 if (kPairs) {
@@ -363,7 +369,7 @@ __global__ void __launch_bounds__(kMrThreads, 1) k_grad_mrhs(
                     // samples, one 32-column store) whose pair number has parity
                     // dg; buffers per tile and per stage are even, so no pair
                     // straddles a stage or the ring's end (nbufs even)
-                    for (int q2 = (int)((uint32_t)dg - (gseq >> 1)) & 1; 2 * q2 < nb; q2 += kMrDecGroups) {
+                    for (int q2 = (int)(((uint32_t)dg - (gseq >> 1)) & (kGroups - 1)); 2 * q2 < nb; q2 += kGroups) {
                         if (aseq >= (uint32_t)nbufs) {
                             if (!mr_wait(&pipe.aempty[t][aslot], aphase ^ 1u) ||
                                 !mr_wait(&pipe.aempty[t][aslot + 1], aphase ^ 1u)) {
@@ -389,16 +395,16 @@ __global__ void __launch_bounds__(kMrThreads, 1) k_grad_mrhs(
                         mr_fence_before();
                         mr_arrive(&pipe.afull[t][aslot]);
                         mr_arrive(&pipe.afull[t][aslot + 1]);
-                        aseq += 2 * kMrDecGroups;
-                        aslot += 2 * kMrDecGroups;
+                        aseq += 2 * kGroups;
+                        aslot += 2 * kGroups;
                         while (aslot >= (uint32_t)nbufs) {
                             aslot -= (uint32_t)nbufs;
                             aphase ^= 1u;
                         }
                     }
                 } else
-                // group dg fills the buffers whose sequence number has parity dg
-                for (int q4 = (int)((uint32_t)dg - gseq) & 1; q4 < nb; q4 += kMrDecGroups) {
+                // group dg fills the buffers whose sequence number is dg mod kGroups
+                for (int q4 = (int)(((uint32_t)dg - gseq) & (kGroups - 1)); q4 < nb; q4 += kGroups) {
                     if (aseq >= (uint32_t)nbufs) {
                         if (!mr_wait(&pipe.aempty[t][aslot], aphase ^ 1u)) {
                             abort_flag = 1;
@@ -417,8 +423,8 @@ __global__ void __launch_bounds__(kMrThreads, 1) k_grad_mrhs(
                     asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
                     mr_fence_before();
                     mr_arrive(&pipe.afull[t][aslot]);
-                    aseq += kMrDecGroups;
-                    aslot += kMrDecGroups;
+                    aseq += kGroups;
+                    aslot += kGroups;
                     while (aslot >= (uint32_t)nbufs) {       // at most twice (nbufs >= 2)
                         aslot -= (uint32_t)nbufs;
                         aphase ^= 1u;
@@ -440,12 +446,12 @@ __global__ void __launch_bounds__(kMrThreads, 1) k_grad_mrhs(
                 break;
             }
             mr_fence_after();
-            const int64_t j = tile * (128 * kMrTiles) + 128 * t + r;
+            const int64_t j = tile * (128 * kTiles) + 128 * t + r;
             {
-                // the groups take halves of the solves; solve c's limbs are the
-                // accumulator columns 5c .. 5c+4, combined in limb order as the
-                // single-column epilogue does: D = 2^14 sum_l s0 16^-l acc_l
-                const int half = (ncols + 1) / 2;
+                // the groups take halves of the solves (one group: all); solve c's
+                // limbs are the accumulator columns 5c .. 5c+4, combined in limb
+                // order as the single-column epilogue does: D = 2^14 sum_l s0 16^-l acc_l
+                const int half = kGroups == 1 ? ncols : (ncols + 1) / 2;
                 const int c_lo = dg == 0 ? 0 : half, c_hi = dg == 0 ? half : ncols;
                 int c = c_lo, l = 0;
                 float ssum = 0.0f, sc = c < c_hi ? cols[c].scale : 0.0f;
@@ -473,7 +479,7 @@ __global__ void __launch_bounds__(kMrThreads, 1) k_grad_mrhs(
             mr_fence_before();
             mr_arrive(&pipe.accempty[t]);
         }
-    } else if (warp < kMrGWarp) {
+    } else if (warp < kGWarp) {
         // ------------------------------------------------------- MMA issuers (one per tile)
         const int t = warp - kMrMmaWarp;
         if (lane == 0) {
@@ -481,7 +487,7 @@ __global__ void __launch_bounds__(kMrThreads, 1) k_grad_mrhs(
             int T = 0;
             bool ok = true;
             const uint32_t b0 = mr_smem(bst);
-            const uint32_t tb = tmem_base + (uint32_t)(256 * t);
+            const uint32_t tb = tmem_base + kTmemPerTile * (uint32_t)t;
             for (int64_t tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x, ++T) {
                 if (T >= 1) {
                     if (!mr_wait(&pipe.accempty[t], (uint32_t)(T - 1) & 1u)) { abort_flag = 1; break; }
@@ -520,24 +526,24 @@ __global__ void __launch_bounds__(kMrThreads, 1) k_grad_mrhs(
             }
         }
         __syncwarp();
-    } else if (warp == kMrGWarp) {
+    } else if (warp == kGWarp) {
         // ------------------------------------------------------- genotype tiles (TMA)
         if (lane == 0) {
             uint32_t slot = 0, phase = 0;
             int64_t issued = 0;
             bool ok = true;
             for (int64_t tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
-                const int y0 = (int)(tile * (128 * kMrTiles));
+                const int y0 = (int)(tile * (128 * kTiles));
                 for (int st = 0; st < spt; ++st, ++issued) {
                     if (abort_flag || (issued >= ngs && !mr_wait(&pipe.gempty[slot], phase ^ 1u))) {
                         abort_flag = 1;
                         ok = false;
                         break;
                     }
-                    mr_expect_tx(&pipe.gfull[slot], (uint32_t)(kMrTiles * kMrGTile));
+                    mr_expect_tx(&pipe.gfull[slot], (uint32_t)(kTiles * kMrGTile));
 #pragma unroll
-                    for (int t = 0; t < kMrTiles; ++t)
-                        mr_tma_2d(gst + (slot * kMrTiles + t) * kMrGTile, &gmap, st * kMrGStageBytes,
+                    for (int t = 0; t < kTiles; ++t)
+                        mr_tma_2d(gst + (slot * kTiles + t) * kMrGTile, &gmap, st * kMrGStageBytes,
                                   y0 + 128 * t, &pipe.gfull[slot]);
                     if (++slot == (uint32_t)ngs) {
                         slot = 0;
@@ -852,24 +858,26 @@ static int mr_n(int ncols) { return (kMrLimbs * ncols + 15) / 16 * 16; }
 
 // Launch shape of a pass: staging only, so every shape writes the same bits.
 struct MrShape {
-    int ngs;      // genotype stages (2 tiles x 8 KB each)
+    int ngs;      // genotype stages (tiles x 8 KB each)
     int pairs;    // 1: each decoder step fills a pair of A buffers
     int fin8;     // 1: missing-call finalisation over 8 columns per block
     int padded;   // 1: finalisation over the padded lists (when the dataset has them)
+    int tiles;    // 128-SNP tiles per CTA step: 2 (two decoder groups each) or 4 (one)
 };
 
 // B stages and A buffers of shape sh at N accumulator columns (false: it does
 // not fit).  B stages: as many chunks as shared memory holds beside the
-// genotype stages, up to kMrMaxBStages.
+// genotype stages, up to kMrMaxBStages; A buffers: as many 16-column buffers
+// as a tile's share of tensor memory holds beside its accumulator.
 static bool mr_shape_launch(int N, const MrShape &sh, int *nbst, int *nbufs)
 {
     if (sh.ngs < 2 || sh.ngs > kMrMaxGStages || sh.pairs < 0 || sh.pairs > 1 || sh.fin8 < 0 || sh.fin8 > 1 ||
-        sh.padded < 0 || sh.padded > 1)
+        sh.padded < 0 || sh.padded > 1 || (sh.tiles != 2 && sh.tiles != 4))
         return false;
-    const size_t gb = (size_t)sh.ngs * kMrTiles * kMrGTile;
+    const size_t gb = (size_t)sh.ngs * sh.tiles * kMrGTile;
     const size_t chunk = (size_t)kMrChunkSteps * N * 32;
     if (gb + 2 * chunk > kMrSmemMax) return false;
-    int nb = std::min(kMrMaxBufs, (256 - N) / 16);
+    int nb = std::min(kMrMaxBufs, (512 / sh.tiles - N) / 16);
     if (sh.pairs) {
         if (nb < 4) return false;
         nb &= ~1;
@@ -880,14 +888,19 @@ static bool mr_shape_launch(int N, const MrShape &sh, int *nbst, int *nbufs)
     return true;
 }
 
-// Default shape: with few accumulator columns the pass streams genotypes as
-// fast as it decodes them and wants many bytes in flight; with many, B chunks
-// need the room (the pass is tensor-bound there).  Pairs whenever there are
-// four or more A buffers.
-static MrShape mr_default_shape(int N) { return MrShape{N <= 96 ? kMrMaxGStages : 4, 1, 1, 1}; }
+// Default shape: with at most 64 accumulator columns four tiles per step (four
+// MMA-issuing warps); above, two tiles, with many genotype stages in flight up
+// to 96 columns and B chunks given the room beyond (the pass is tensor-bound
+// there).  Pairs whenever there are four or more A buffers.
+static MrShape mr_default_shape(int N)
+{
+    if (N <= 64) return MrShape{4, 1, 1, 1, 4};
+    return MrShape{N <= 96 ? kMrMaxGStages : 4, 1, 1, 1, 2};
+}
 
 // A cached shape made to fit N (pairs dropped when there are too few buffers;
-// the default when the stages do not fit).
+// the default when the stages or tiles do not fit; last, two tiles, four
+// stages, no pairs, which fit at any N <= kMrMaxN).
 static MrShape mr_fit_shape(int N, MrShape sh, int *nbst, int *nbufs)
 {
     if (mr_shape_launch(N, sh, nbst, nbufs)) return sh;
@@ -895,22 +908,25 @@ static MrShape mr_fit_shape(int N, MrShape sh, int *nbst, int *nbufs)
     if (mr_shape_launch(N, sh, nbst, nbufs)) return sh;
     sh = mr_default_shape(N);
     if (mr_shape_launch(N, sh, nbst, nbufs)) return sh;
-    sh.pairs = 0;
-    mr_shape_launch(N, sh, nbst, nbufs);             // 4 stages + 2 chunks fit at any N <= kMrMaxN
+    sh = MrShape{4, 0, 1, 1, 2};
+    mr_shape_launch(N, sh, nbst, nbufs);
     return sh;
 }
 
-// Tuning buckets of accumulator widths: 16..64, 80..128, 144..192 (pairs
-// possible) and 208..224.
-static int mr_bucket_of(int N) { return N <= 64 ? 64 : N <= 128 ? 128 : N <= 192 ? 192 : kMrMaxN; }
+// Tuning buckets of accumulator widths: 16..64, 80..96 (four tiles possible),
+// 112..128, 144..192 (pairs possible) and 208..224.
+static int mr_bucket_of(int N)
+{
+    return N <= 64 ? 64 : N <= 96 ? 96 : N <= 128 ? 128 : N <= 192 ? 192 : kMrMaxN;
+}
 
 int grad_mrhs_bucket(int ncols) { return mr_bucket_of(mr_n(std::min(ncols, kMrMaxCols))); }
 
 bool grad_mrhs_shape_fits(int ncols, const int *params)
 {
     int nbst, nbufs;
-    return mr_shape_launch(mr_n(std::min(ncols, kMrMaxCols)), MrShape{params[0], params[1], params[2], params[3]},
-                           &nbst, &nbufs);
+    return mr_shape_launch(mr_n(std::min(ncols, kMrMaxCols)),
+                           MrShape{params[0], params[1], params[2], params[3], params[4]}, &nbst, &nbufs);
 }
 
 int mrhs_max_cols() { return kMrMaxCols; }
@@ -1029,7 +1045,7 @@ static int mr_finalize(iht_dataset *ds, const MrCol *cols, int ncols, bool fin8,
 struct MrPass {
     iht_dataset *ds;
     const CUtensorMap *map;
-    int grid, ksteps, N, nc;
+    int ksteps, N, nc;
     MrCol *cols;
 };
 
@@ -1041,15 +1057,18 @@ static int mr_pass(const MrPass &P, MrShape sh, const TuneEvents *te, size_t e0,
     int nbst = 0, nbufs = 0;
     sh = mr_fit_shape(P.N, sh, &nbst, &nbufs);
     // at least 116 KB, so one CTA per SM: the kernel allocates all 512 columns of tensor memory
-    const size_t smem = std::max<size_t>(116 * 1024, (size_t)sh.ngs * kMrTiles * kMrGTile +
+    const size_t smem = std::max<size_t>(116 * 1024, (size_t)sh.ngs * sh.tiles * kMrGTile +
                                                          (size_t)nbst * kMrChunkSteps * P.N * 32);
     // D FP32, A E5M2, B E4M3, K-major, N, M = 128
     const uint32_t idesc = (1u << 4) | (1u << 7) | ((uint32_t)(P.N >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
+    const int64_t ntiles = (P.ds->p + 128 * sh.tiles - 1) / (128 * sh.tiles);
+    const int grid = (int)std::min<int64_t>(ntiles, P.ds->ctx->num_sms);
     if (te) IHT_CUDA(cudaEventRecord(te->ev[e0], s));
     prof_begin(prof, s);
-    auto kern = sh.pairs ? k_grad_mrhs<true> : k_grad_mrhs<false>;
-    kern<<<P.grid, kMrThreads, smem, s>>>(*P.map, P.ds->p, P.ksteps, P.N, P.nc, nbufs, nbst, sh.ngs, g_mr.bimg,
-                                          P.cols, idesc, g_mr.err);
+    auto kern = sh.tiles == 4 ? (sh.pairs ? k_grad_mrhs<true, 4, 1> : k_grad_mrhs<false, 4, 1>)
+                              : (sh.pairs ? k_grad_mrhs<true, 2, 2> : k_grad_mrhs<false, 2, 2>);
+    kern<<<grid, mr_threads(sh.tiles), smem, s>>>(*P.map, P.ds->p, P.ksteps, P.N, P.nc, nbufs, nbst, sh.ngs,
+                                                  g_mr.bimg, P.cols, idesc, g_mr.err);
     note_launch();
     IHT_CUDA(cudaGetLastError());
     prof_end(prof, s);
@@ -1063,21 +1082,23 @@ static int mr_pass(const MrPass &P, MrShape sh, const TuneEvents *te, size_t e0,
 }
 
 // First pass of a bucket: the pass and its finalisation once per run, the
-// pass cycling through the candidate shapes (genotype stages 4, 6, 8 x pairs
-// on, off) and the finalisation through its variants (8 or 4 columns per
-// block x plain or padded lists), each run writing the same g (the
+// pass cycling through the candidate shapes (2 or 4 tiles per CTA step x
+// genotype stages 4, 6, 8 x pairs on, off, as they fit) and the finalisation
+// through its variants (8 or 4 columns per block x plain or padded lists),
+// each run writing the same g (the
 // finalisation reads the pass's output in place, so each run does both).  The
 // fastest pass shape and the fastest finalisation are cached.  prof brackets
 // the first run's pass.
 static int mr_tune(const MrPass &P, ProfEvents *prof)
 {
     std::vector<MrShape> cand;
-    for (int ngs : {4, 6, 8})
-        for (int pairs : {1, 0}) {
-            const MrShape sh{ngs, pairs, 1, 0};
-            int nbst, nbufs;
-            if (mr_shape_launch(P.N, sh, &nbst, &nbufs)) cand.push_back(sh);
-        }
+    for (int tiles : {2, 4})
+        for (int ngs : {4, 6, 8})
+            for (int pairs : {1, 0}) {
+                const MrShape sh{ngs, pairs, 1, 0, tiles};
+                int nbst, nbufs;
+                if (mr_shape_launch(P.N, sh, &nbst, &nbufs)) cand.push_back(sh);
+            }
     const int fins[4][2] = {{1, 1}, {0, 1}, {1, 0}, {0, 0}};    // (fin8, padded)
     const int nfin = P.ds->miss_gidx ? 4 : 2;
     const size_t runs = std::max(cand.size(), (size_t)nfin);
@@ -1091,13 +1112,14 @@ static int mr_tune(const MrPass &P, ProfEvents *prof)
     }
     IHT_CUDA(cudaStreamSynchronize(P.ds->ctx->stream));
     float best = 1e30f, fin_best = 1e30f;
-    int prm[kTuneParams] = {0, 0, 1, 0};
+    int prm[kTuneParams] = {0, 0, 1, 0, 2};
     for (size_t r = 0; r < runs; ++r) {
         const float k = te.ms(4 * r, 4 * r + 1), f = te.ms(4 * r + 2, 4 * r + 3);
         if (r < cand.size() && k < best) {
             best = k;
             prm[0] = cand[r].ngs;
             prm[1] = cand[r].pairs;
+            prm[4] = cand[r].tiles;
         }
         if (f < fin_best) {
             fin_best = f;
@@ -1159,14 +1181,11 @@ int launch_grad_mrhs(iht_dataset *ds, MrCol *cols, int ncols, ProfEvents *prof, 
     if (rc) return rc;
     static thread_local int cfg = -1;
     if (cfg != ds->ctx->device) {
-        IHT_CUDA(cudaFuncSetAttribute(k_grad_mrhs<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)kMrSmemMax));
-        IHT_CUDA(cudaFuncSetAttribute(k_grad_mrhs<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)kMrSmemMax));
+        for (auto kern : {k_grad_mrhs<true, 2, 2>, k_grad_mrhs<false, 2, 2>, k_grad_mrhs<true, 4, 1>,
+                          k_grad_mrhs<false, 4, 1>})
+            IHT_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMrSmemMax));
         cfg = ds->ctx->device;
     }
-    const int64_t tiles = (ds->p + 128 * kMrTiles - 1) / (128 * kMrTiles);
-    const int grid = (int)std::min<int64_t>(tiles, ds->ctx->num_sms);
     const bool may_tune = autotune_enabled() && !stream_capturing(s);
     for (int c0 = 0; c0 < ncols; c0 += kMrMaxCols) {
         const int nc = std::min(kMrMaxCols, ncols - c0);
@@ -1177,10 +1196,10 @@ int launch_grad_mrhs(iht_dataset *ds, MrCol *cols, int ncols, ProfEvents *prof, 
         k_mr_limbs<<<nc, 1024, 0, s>>>(cols + c0, 2 * mr_ngroups(ds) * kMrStepSamples, N, w.bimg);
         note_launch();
         IHT_CUDA(cudaGetLastError());
-        const MrPass pass{ds, &map, grid, ksteps, N, nc, cols + c0};
+        const MrPass pass{ds, &map, ksteps, N, nc, cols + c0};
         int prm[kTuneParams];
         if (tune_lookup(ds, IHT_PASS_MULTI, mr_bucket_of(N), prm))
-            rc = mr_pass(pass, MrShape{prm[0], prm[1], prm[2], prm[3]}, nullptr, 0, prof);
+            rc = mr_pass(pass, MrShape{prm[0], prm[1], prm[2], prm[3], prm[4]}, nullptr, 0, prof);
         else if (may_tune)
             rc = mr_tune(pass, prof);
         else

@@ -90,7 +90,7 @@ static int tune_bucket_checked(const iht_dataset *ds, int kind, int ncols, const
     return -1;
 }
 
-static int tune_nparams(int kind) { return kind == IHT_PASS_SINGLE ? 1 : 4; }
+static int tune_nparams(int kind) { return kind == IHT_PASS_SINGLE ? 1 : 5; }
 
 }  // namespace iht
 
@@ -151,10 +151,11 @@ int iht_tuning_summary(char *buf, size_t buf_bytes)
                          how, c.ms, c.candidates);
             else
                 snprintf(line, sizeof line,
-                         "multi-column device %d n_pad %lld p %lld N<=%d: genotype_stages %d pairs %d "
-                         "finalise8 %d padded %d (%s, %.3f ms, %d runs)\n",
+                         "multi-column device %d n_pad %lld p %lld N<=%d: tiles %d genotype_stages %d "
+                         "pairs %d finalise8 %d padded %d (%s, %.3f ms, %d runs)\n",
                          std::get<0>(k), (long long)std::get<1>(k), (long long)std::get<2>(k), std::get<4>(k),
-                         c.params[0], c.params[1], c.params[2], c.params[3], how, c.ms, c.candidates);
+                         c.params[4], c.params[0], c.params[1], c.params[2], c.params[3], how, c.ms,
+                         c.candidates);
             out += line;
         }
     }

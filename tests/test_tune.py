@@ -24,9 +24,9 @@ def test_tuning_api_on_the_host():
     assert L.iht_tuning_summary(None, 0) == 1
     iht.set_autotune(False)
     iht.set_autotune(True)
-    prm = np.array([4, 1, 1, 1], np.int32)
-    assert L.iht_tune_pin(None, iht.IHT_PASS_MULTI, 8, prm.ctypes.data, 4) == iht.IHT_EINVAL
-    assert L.iht_tune_query(None, iht.IHT_PASS_MULTI, 8, prm.ctypes.data, 4) == iht.IHT_EINVAL
+    prm = np.array([4, 1, 1, 1, 2], np.int32)
+    assert L.iht_tune_pin(None, iht.IHT_PASS_MULTI, 8, prm.ctypes.data, 5) == iht.IHT_EINVAL
+    assert L.iht_tune_query(None, iht.IHT_PASS_MULTI, 8, prm.ctypes.data, 5) == iht.IHT_EINVAL
 
 
 # --------------------------------------------------------------------------- GPU
@@ -79,20 +79,25 @@ def test_multi_column_shapes_give_the_same_bits(panel, ncols):
     iht.tune_clear()
     want = np.stack([_single(ds, R[c]) for c in range(ncols)])
     tried = 0
-    for ngs, pairs, fin8, padded in itertools.product((2, 4, 6, 8), (0, 1), (0, 1), (0, 1)):
+    for tiles, ngs, pairs, fin8, padded in itertools.product((2, 4), (2, 4, 6, 8), (0, 1), (0, 1), (0, 1)):
         try:
-            iht.tune_pin(ds, iht.IHT_PASS_MULTI, ncols, [ngs, pairs, fin8, padded])
-        except iht.IhtError:                   # pairs need four or more A buffers
-            assert pairs == 1 and ncols > 38
+            iht.tune_pin(ds, iht.IHT_PASS_MULTI, ncols, [ngs, pairs, fin8, padded, tiles])
+        except iht.IhtError:
+            # pairs need four or more A buffers; 4 tiles need N <= 96 and at most
+            # 6 genotype stages beside the B chunks
+            assert (pairs == 1 and ncols > 38) or (tiles == 4 and (ncols > 19 or ngs > 6 or
+                                                                   (pairs == 1 and ncols > 12)))
             continue
         got = iht.iht_gradient_batch(ds, R[:ncols], impl=2).cpu().numpy()
-        assert np.array_equal(got, want), (ngs, pairs, fin8, padded)
+        assert np.array_equal(got, want), (tiles, ngs, pairs, fin8, padded)
         tried += 1
     assert tried >= 16
     with pytest.raises(iht.IhtError):
-        iht.tune_pin(ds, iht.IHT_PASS_MULTI, ncols, [9, 0, 0, 0])
+        iht.tune_pin(ds, iht.IHT_PASS_MULTI, ncols, [9, 0, 0, 0, 2])
     with pytest.raises(iht.IhtError):
-        iht.tune_pin(ds, iht.IHT_PASS_MULTI, ncols, [4, 0, 0, 2])
+        iht.tune_pin(ds, iht.IHT_PASS_MULTI, ncols, [4, 0, 0, 2, 2])
+    with pytest.raises(iht.IhtError):
+        iht.tune_pin(ds, iht.IHT_PASS_MULTI, ncols, [4, 0, 0, 0, 3])
     iht.tune_clear()
 
 
@@ -110,9 +115,10 @@ def test_tuner_caches_a_shape_and_keeps_the_bits(panel):
     got = iht.iht_gradient_batch(ds, R[:20], impl=2).cpu().numpy()
     assert np.array_equal(got1, want1) and np.array_equal(got, want)
     nst, = iht.tune_query(ds, iht.IHT_PASS_SINGLE, 1)
-    ngs, pairs, fin8, padded = iht.tune_query(ds, iht.IHT_PASS_MULTI, 20)
+    ngs, pairs, fin8, padded, tiles = iht.tune_query(ds, iht.IHT_PASS_MULTI, 20)
     assert nst >= 2 and ngs in (4, 6, 8) and pairs in (0, 1) and fin8 in (0, 1) and padded in (0, 1)
-    assert iht.tune_query(ds, iht.IHT_PASS_MULTI, 21) == (ngs, pairs, fin8, padded)   # same bucket
+    assert tiles in (2, 4)
+    assert iht.tune_query(ds, iht.IHT_PASS_MULTI, 21) == (ngs, pairs, fin8, padded, tiles)  # same bucket
     assert iht.tune_query(ds, iht.IHT_PASS_MULTI, 40) is None                  # another bucket
     text = iht.tuning_summary()
     assert "single-column" in text and "multi-column" in text and "tuned" in text
