@@ -12,7 +12,12 @@ a planted mistake) and raises AssertionError when the oracle disagrees with:
     least squares on the support at a fixed point (Eq. normal_equations), OLS
     when k = p < n, exact recovery of noiseless sparse models, brute force over
     all k-subsets, a monotone objective, |supp beta| <= k, and the sign
-    symmetry of allele orientation.
+    symmetry of allele orientation;
+  * an iteration-by-iteration numpy replay of the step size, the backtracking
+    rule mu < omega = (1-c) ||d||^2 / ||Z d||^2 and the sufficient decrease it
+    implies (Sec. 2.3.1), on instances where the accept decisions depend on c;
+  * the stopping rule ||beta+ - beta|| / (||beta|| + 1) < tol recomputed from
+    the traced iterates at three scales of y.
 """
 from __future__ import annotations
 
@@ -364,6 +369,117 @@ def pin_cv(lib):
     assert np.array_equal(res.fit.beta, refit.beta), "refit on the labelled rows at k_best"
 
 
+
+def _np_topk(w, k):
+    """P_{S_k} by numpy: the k largest |w|, ties to the lower index, ascending."""
+    return np.sort(np.lexsort((np.arange(w.size), -np.abs(w)))[:k])
+
+
+def _np_iteration(Z, y, beta, S, k, c, kappa, max_bt):
+    """One IHT iteration in numpy (Sec. 2.2, 2.3.1): normalized step on S,
+    projection, and the backtracking rule shrink-while mu >= (1-c) rho,
+    rho = ||d||^2 / ||Z d||^2, applied when the support changes.  Returns
+    (S+, beta+, accepted mu, shrinks, decisions) where decisions lists
+    (mu, rho) for every omega check made."""
+    g = Z.T @ (y - Z @ beta)
+    mu = (g[S] @ g[S]) / np.sum((Z[:, S] @ g[S]) ** 2)
+    decisions = []
+    for j in range(max_bt + 1):
+        w = beta + mu * g
+        Sp = _np_topk(w, k)
+        bp = np.zeros_like(beta)
+        bp[Sp] = w[Sp]
+        if np.array_equal(Sp, S):
+            return Sp, bp, mu, j, decisions
+        d = bp - beta
+        rho = (d @ d) / np.sum((Z @ d) ** 2)
+        decisions.append((mu, rho))
+        if mu < (1 - c) * rho or j == max_bt:
+            return Sp, bp, mu, j, decisions
+        mu /= kappa
+    raise AssertionError("unreachable")
+
+
+def pin_backtracking_replay(lib):
+    """Every iteration replayed in numpy from the oracle's previous iterate: the
+    step size, each backtracking decision and the accepted support, beta and
+    shrink count agree, and the omega the oracle reports is (1-c) rho of its
+    accepted candidate (Sec. 2.3.1).  With c = 0.3 many decisions fall where
+    mu < (1-c) rho, mu < rho and mu < (1+c) rho disagree, so a dropped or
+    flipped (1-c) factor changes a decision; the pin asserts such decisions
+    occurred.  Accepted steps also satisfy the sufficient decrease that the
+    rule guarantees: f(beta) - f(beta+) > c ||d||^2 / (2 mu), from
+    g^T d >= ||d||^2 / (2 mu) (beta+ is the best k-sparse approximation of
+    beta + mu g) and ||Z d||^2 < (1-c) ||d||^2 / mu."""
+    cases = [(70, 12, 0.3), (71, 5, 0.3), (74, 12, 0.3), (70, 12, 0.01), (71, 12, 0.01)]
+    sensitive = 0
+    for seed, k, c in cases:
+        rng, G, codes = _panel(seed, 150, 300, miss=0.02)
+        Z = np_Z(codes)
+        causal = rng.choice(G.p, size=8, replace=False)
+        y = Z[:, causal] @ rng.normal(0, 0.5, size=8) + rng.normal(size=G.n)
+        f = oracle.iht(G, y, k, c=c, tol=1e-4, max_iter=200, lib=lib)
+        assert f.iterations >= 3
+        beta = np.zeros(G.p)
+        S = _np_topk(Z.T @ y, k)
+        for t in range(f.iterations):
+            Sp, bp, mu, bt, dec = _np_iteration(Z, y, beta, S, k, c, 2.0, 50)
+            assert np.array_equal(Sp, f.trace["supp"][t]), f"support at iteration {t}"
+            assert np.allclose(bp[Sp], f.trace["beta"][t], rtol=1e-9, atol=1e-12), f"beta at {t}"
+            assert bt == f.trace["backtracks"][t], f"shrinks at iteration {t}"
+            assert abs(mu - f.trace["mu"][t]) <= 1e-9 * mu, f"step size at iteration {t}"
+            if dec:
+                m_, rho = dec[-1]
+                assert abs(f.trace["omega"][t] - (1 - c) * rho) <= 1e-9 * rho, f"omega at {t}"
+                for m_, rho in dec:
+                    a = m_ < (1 - c) * rho
+                    sensitive += a != (m_ < rho) or a != (m_ < (1 + c) * rho)
+                if bt < 50:
+                    d = bp - beta
+                    f0 = 0.5 * np.sum((y - Z @ beta) ** 2)
+                    f1 = 0.5 * np.sum((y - Z @ bp) ** 2)
+                    assert f0 - f1 > c * (d @ d) / (2 * mu) * (1 - 1e-9), f"decrease at {t}"
+            beta, S = bp, Sp
+    assert sensitive >= 10, "instances must exercise decisions that depend on c"
+
+
+def pin_convergence_rule(lib):
+    """The solve stops at the first iteration with ||beta+ - beta|| / (||beta|| + 1)
+    < tol, recomputed in numpy from the traced iterates, and not before.  The
+    same problem is solved with y scaled by 1e-3, 1 and 1e3 (IHT's supports and
+    step sizes are scale-invariant; only the stopping test sees the scale): at
+    1e3 the stop happens while ||beta+ - beta|| itself is still >= tol, at 1e-3
+    while ||beta+ - beta|| / ||beta|| is still >= tol, so a test without the
+    +1 or with a plain relative denominator stops at another iteration."""
+    rng, G, codes = _panel(72, 150, 300, miss=0.02)
+    Z = np_Z(codes)
+    causal = rng.choice(G.p, size=8, replace=False)
+    y0 = Z[:, causal] @ rng.normal(0, 0.5, size=8) + rng.normal(size=G.n)
+    tol = 1e-4
+    stops = []
+    for s in (1e-3, 1.0, 1e3):
+        f = oracle.iht(G, s * y0, 12, tol=tol, max_iter=300, lib=lib)
+        assert f.status == oracle.OK
+        prev = np.zeros(G.p)
+        steps, dn, bn = [], [], []
+        for t in range(f.iterations):
+            cur = np.zeros(G.p)
+            cur[f.trace["supp"][t]] = f.trace["beta"][t]
+            dn.append(np.linalg.norm(cur - prev))
+            bn.append(np.linalg.norm(prev))
+            steps.append(dn[-1] / (bn[-1] + 1.0))
+            prev = cur
+        steps = np.array(steps)
+        assert np.all(steps[:-1] >= tol), f"scale {s}: stopped late"
+        assert steps[-1] < tol, f"scale {s}: stopped early"
+        stops.append((s, dn[-1], bn[-1]))
+    s, d, b = stops[2]
+    assert d >= tol, "the 1e3 instance must separate the +1 rule from an absolute test"
+    s, d, b = stops[0]
+    assert d / b >= tol, "the 1e-3 instance must separate the +1 rule from a relative test"
+
+
 ALL_PINS = [pin_decode, pin_counts_stats, pin_stats_exact, pin_gradient, pin_identity, pin_topk,
             pin_k1_marginal, pin_fixed_point, pin_full_ols, pin_noiseless, pin_bruteforce,
-            pin_invariants, pin_orientation, pin_cv]
+            pin_invariants, pin_orientation, pin_cv, pin_backtracking_replay,
+            pin_convergence_rule]

@@ -33,6 +33,13 @@ MUTANTS = {
     "backtrack_test_reversed": [("if (mu < omega || bt", "if (mu > omega || bt")],
     "residual_sign": [("r[a] = y[a] - zv[a];", "r[a] = y[a] + zv[a];")],
     "no_step_shrink": [("mu /= opt->kappa;", "mu *= 1.0;")],
+    "omega_without_1_minus_c": [("omega = (1.0 - opt->c) * dd / zz;", "omega = dd / zz;")],
+    "omega_with_1_plus_c": [("omega = (1.0 - opt->c) * dd / zz;",
+                             "omega = (1.0 + opt->c) * dd / zz;")],
+    "convergence_without_plus_one": [("double step = sqrt(dn) / (sqrt(bn) + 1.0);",
+                                      "double step = sqrt(dn);")],
+    "convergence_plain_relative": [("double step = sqrt(dn) / (sqrt(bn) + 1.0);",
+                                    "double step = sqrt(dn) / sqrt(bn);")],
 }
 
 
