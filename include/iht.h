@@ -98,6 +98,20 @@ const char *iht_last_cuda_error(void);
  * (all threads, all devices).  Host-only; lets callers count device work. */
 uint64_t iht_kernel_launches(void);
 
+/* Host-side fault injection, for testing how failures reach the caller (the
+ * paper has no counterpart).  No device fault is made and no kernel changes:
+ *   IHT_FAULT_ALLOC   : the next `count` device allocations made by the library
+ *                       fail as on an exhausted device (calls return ENOMEM and
+ *                       free what they had taken);
+ *   IHT_FAULT_TIMEOUT : the next `count` reads of a gradient pass's bounded-wait
+ *                       status find its error word set (the library writes it
+ *                       from the host before the read, as a device wait that
+ *                       gave up would have), so the call returns ETIMEOUT;
+ *   IHT_FAULT_NONE    : clears pending faults (count ignored).
+ * Process-wide, all threads.  EINVAL for another kind or count < 0. */
+enum { IHT_FAULT_NONE = 0, IHT_FAULT_ALLOC = 1, IHT_FAULT_TIMEOUT = 2 };
+int iht_fault_inject(int kind, int32_t count);
+
 /* Create a context on CUDA device `device` that orders all work on `stream`
  * (a cudaStream_t; NULL = the legacy default stream).  *out receives the
  * context.  EINVAL for a bad device, ECUDA if the device cannot be used. */
@@ -143,6 +157,7 @@ int iht_counts(iht_dataset *ds, const int32_t *rows, int64_t n_rows, int mem,
  *   r      : device float[n_rows], aligned with rows.
  *   g_out  : device float[p].
  *   impl   : 0 default, 1 CUDA-core kernel, 2 tensor-core kernel.
+ * ETIMEOUT when a bounded wait of the tensor-core pass gave up (g_out invalid).
  * Computed as g_j = v_j (S1_j - u_j (R - M_j)), S1 = sum of dosage * r over
  * observed calls, M = sum of r over missing calls, R = sum of r. */
 int iht_gradient(iht_dataset *ds, const int32_t *rows, int64_t n_rows, const float *r,
@@ -150,7 +165,8 @@ int iht_gradient(iht_dataset *ds, const int32_t *rows, int64_t n_rows, const flo
 
 /* a3 -- projection onto the k-sparse set (Eq. ihta): the k indices of the
  * largest |w_j|, ties to the lower index, returned ascending.
- *   w: device float[p]; idx_out: device int32[k].  EINVAL if k < 1 or k > p. */
+ *   w: device float[p]; idx_out: device int32[k].  EINVAL if k < 1 or k > p;
+ *   ENUMERIC if w holds a NaN (idx_out is still written: NaN ranks above +Inf). */
 int iht_topk(iht_ctx *ctx, const float *w, int64_t p, int32_t k, int32_t *idx_out);
 
 /* Allocation-free variant of iht_topk (the paper has no counterpart; this is
@@ -164,13 +180,16 @@ int iht_topk(iht_ctx *ctx, const float *w, int64_t p, int32_t k, int32_t *idx_ou
  *   w       : device float[p];  idx_out: device int32[k].
  * The selection's scratch is a static device array in the library (about
  * 41 KB, held on every GPU that loads the library until the process exits);
- * p is limited to 16 777 216, larger p returns IHT_EINVAL without launching
- * anything.  The first call on a device looks the array's address up with
- * cudaGetSymbolAddress and clears it with cudaMemsetAsync on `stream`; make
- * that first call before any stream capture.  The call only enqueues work on
- * `stream` (it does not synchronise); all calls on a device share the scratch,
- * so calls that overlap on the GPU (other streams or other host threads) race.
- * Never calls cudaMalloc or cudaFree. */
+ * p is limited to 16 777 216 (a fixed maximum of this entry point, not a
+ * bound set by the array, whose size does not depend on p); larger p returns
+ * IHT_EINVAL without launching anything.  The first call on a device looks the
+ * array's address up with cudaGetSymbolAddress and clears it with
+ * cudaMemsetAsync on `stream`; make that first call before any stream capture.
+ * The call only enqueues work on `stream` (it does not synchronise), so it
+ * cannot report NaN keys: they rank above +Inf and the call returns IHT_OK.
+ * All calls on a device share the scratch, so calls that overlap on the GPU
+ * (other streams or other host threads) race.  Never calls cudaMalloc or
+ * cudaFree. */
 int iht_topk_noalloc(int device, void *stream, const float *w, int64_t p, int32_t k,
                      int32_t *idx_out);
 
@@ -192,7 +211,9 @@ int iht_zmul(iht_dataset *ds, const int32_t *rows, int64_t n_rows, const double 
  *   support_out : int32[k], ascending.
  *   info        : host iht_result, may be NULL.
  * Starts from beta = 0 with S^0 = the top-k of |Z^T y|.  Returns the solve's
- * status: OK, ENOTCONV (results valid), ENUMERIC, EINVAL, ENOMEM, ECUDA. */
+ * status: OK, ENOTCONV (results valid), ENUMERIC, EINVAL, ENOMEM, ECUDA, or
+ * ETIMEOUT when a bounded wait of a tensor-core gradient pass gave up (the
+ * outputs are then not valid). */
 int iht_fit(iht_dataset *ds, const int32_t *rows, int64_t n_rows, const double *y, int32_t k,
             const iht_options *opt, double *beta_out, int32_t *support_out, iht_result *info);
 

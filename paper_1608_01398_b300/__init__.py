@@ -21,6 +21,7 @@ IHT_OK, IHT_EINVAL, IHT_ENOMEM, IHT_ENOTCONV, IHT_ENUMERIC, IHT_ETIMEOUT, IHT_EC
     range(8)
 IHT_HOST, IHT_DEVICE = 0, 1
 IHT_PASS_SINGLE, IHT_PASS_MULTI = 0, 1
+IHT_FAULT_NONE, IHT_FAULT_ALLOC, IHT_FAULT_TIMEOUT = 0, 1, 2
 
 EXPORTED = ["iht_default_options", "iht_strerror", "iht_last_cuda_error", "iht_kernel_launches",
             "iht_create",
@@ -30,7 +31,7 @@ EXPORTED = ["iht_default_options", "iht_strerror", "iht_last_cuda_error", "iht_k
             "iht_server_create", "iht_server_submit", "iht_server_poll", "iht_server_get_stats",
             "iht_server_destroy", "iht_state_bytes", "iht_state_save", "iht_state_load",
             "iht_fit_resume", "iht_set_autotune", "iht_tune_clear", "iht_tune_pin", "iht_tune_query",
-            "iht_tuning_summary", "iht_cv"]
+            "iht_tuning_summary", "iht_cv", "iht_fault_inject"]
 
 
 class IhtError(RuntimeError):
@@ -105,6 +106,7 @@ def _lib(build_if_stale: bool = True):
         "iht_strerror": (ctypes.c_char_p, [ctypes.c_int]),
         "iht_last_cuda_error": (ctypes.c_char_p, []),
         "iht_kernel_launches": (ctypes.c_uint64, []),
+        "iht_fault_inject": (ctypes.c_int, [ctypes.c_int, i32]),
         "iht_create": (ctypes.c_int, [ctypes.POINTER(P), ctypes.c_int, P]),
         "iht_destroy": (ctypes.c_int, [P]),
         "iht_load_bed": (ctypes.c_int, [P, P, sz, ctypes.c_int, i64, i64, ctypes.POINTER(P)]),
@@ -161,6 +163,11 @@ def _lib(build_if_stale: bool = True):
 def iht_kernel_launches() -> int:
     """Kernel launches issued by libiht in this process."""
     return int(_lib().iht_kernel_launches())
+
+
+def fault_inject(kind: int, count: int = 1) -> None:
+    """Host-side fault injection for error-path tests (iht_fault_inject)."""
+    _check(_lib().iht_fault_inject(int(kind), int(count)), "iht_fault_inject")
 
 
 def status_name(s: int) -> str:

@@ -18,6 +18,35 @@ static std::atomic<uint64_t> g_launches{0};
 void note_launch(int n) { g_launches.fetch_add((uint64_t)(int64_t)n, std::memory_order_relaxed); }
 uint64_t launches_noted() { return g_launches.load(std::memory_order_relaxed); }
 
+static std::atomic<int> g_fault[3];         // pending injected faults by kind
+
+bool fault_take(int kind)
+{
+    if (kind <= 0 || kind >= 3) return false;
+    int n = g_fault[kind].load(std::memory_order_relaxed);
+    while (n > 0)
+        if (g_fault[kind].compare_exchange_weak(n, n - 1, std::memory_order_relaxed)) return true;
+    return false;
+}
+
+cudaError_t dev_malloc_raw(void **ptr, size_t bytes)
+{
+    if (fault_take(IHT_FAULT_ALLOC)) {
+        *ptr = nullptr;
+        return cudaErrorMemoryAllocation;
+    }
+    return cudaMalloc(ptr, bytes);
+}
+
+cudaError_t dev_malloc_async_raw(void **ptr, size_t bytes, cudaStream_t s)
+{
+    if (fault_take(IHT_FAULT_ALLOC)) {
+        *ptr = nullptr;
+        return cudaErrorMemoryAllocation;
+    }
+    return cudaMallocAsync(ptr, bytes, s);
+}
+
 void set_cuda_error(cudaError_t e, const char *where)
 {
     snprintf(g_last_cuda, sizeof(g_last_cuda), "%s (%s) at %s", cudaGetErrorName(e),
@@ -53,7 +82,7 @@ int ensure_workspace(iht_dataset *ds, int)
     const int64_t p = ds->p, np = ds->n_pad;
     ws->p = p;
     ws->n_pad = np;
-    auto A = [](void **ptr, size_t bytes) { return cudaMalloc(ptr, bytes ? bytes : 16); };
+    auto A = [](void **ptr, size_t bytes) { return dev_malloc(ptr, bytes ? bytes : 16); };
     cudaError_t e = cudaSuccess;
 #define ALLOC(field, bytes)                                        \
     if (e == cudaSuccess) e = A((void **)&ws->field, (size_t)(bytes));
@@ -196,6 +225,18 @@ const char *iht_last_cuda_error(void) { return g_last_cuda; }
 
 uint64_t iht_kernel_launches(void) { return g_launches.load(std::memory_order_relaxed); }
 
+int iht_fault_inject(int kind, int32_t count)
+{
+    if (kind == IHT_FAULT_NONE) {
+        g_fault[IHT_FAULT_ALLOC].store(0);
+        g_fault[IHT_FAULT_TIMEOUT].store(0);
+        return IHT_OK;
+    }
+    if ((kind != IHT_FAULT_ALLOC && kind != IHT_FAULT_TIMEOUT) || count < 0) return IHT_EINVAL;
+    g_fault[kind].store(count);
+    return IHT_OK;
+}
+
 int iht_create(iht_ctx **out, int device, void *stream)
 {
     if (!out) return IHT_EINVAL;
@@ -262,7 +303,7 @@ int iht_load_bed(iht_ctx *ctx, const uint8_t *bed, size_t bed_bytes, int mem, in
     ds->miss_idx = nullptr;
     ds->miss_total = 0;
     ds->miss_idx16 = n <= 65536;
-    cudaError_t e = cudaMalloc(&ds->G, (size_t)(p * ds->stride));
+    cudaError_t e = dev_malloc(&ds->G, (size_t)(p * ds->stride));
     if (e != cudaSuccess) {
         set_cuda_error(e, "cudaMalloc(genotypes)");
         delete ds;
@@ -356,9 +397,11 @@ int iht_gradient(iht_dataset *ds, const int32_t *rows, int64_t n_rows, const flo
     const int32_t *rows_dev = nullptr;
     if ((rc = prepare_rows(ds, rows, n_rows, IHT_DEVICE, &rows_dev))) return rc;
     if ((rc = scatter_rows_f32(ds, rows_dev, n_rows, r, ds->ws->r32))) return rc;
+    if ((rc = grad_tc_reset_status(ds))) return rc;
     if ((rc = launch_grad_impl(ds, impl, ds->ws->r32, g_out, nullptr))) return rc;
-    IHT_CUDA(cudaStreamSynchronize(ds->ctx->stream));
-    return IHT_OK;
+    int timed_out = 0;
+    if ((rc = grad_tc_status(ds, &timed_out))) return rc;      // synchronises
+    return timed_out ? IHT_ETIMEOUT : IHT_OK;
 }
 
 int iht_topk(iht_ctx *ctx, const float *w, int64_t p, int32_t k, int32_t *idx_out)
@@ -369,9 +412,12 @@ int iht_topk(iht_ctx *ctx, const float *w, int64_t p, int32_t k, int32_t *idx_ou
     if (!g.ok) return IHT_ECUDA;
     int rc = ensure_selwork(ctx, p);
     if (rc) return rc;
+    IHT_CUDA(cudaMemsetAsync(&ctx->sel.st->err, 0, sizeof(uint32_t), ctx->stream));
     if ((rc = select_topk(ctx, w, p, k, idx_out, nullptr))) return rc;
+    uint32_t err = 0;
+    IHT_CUDA(cudaMemcpyAsync(&err, &ctx->sel.st->err, sizeof(err), cudaMemcpyDeviceToHost, ctx->stream));
     IHT_CUDA(cudaStreamSynchronize(ctx->stream));
-    return IHT_OK;
+    return (err & 1u) ? IHT_ENUMERIC : IHT_OK;
 }
 
 int iht_zmul(iht_dataset *ds, const int32_t *rows, int64_t n_rows, const double *u,

@@ -114,7 +114,7 @@ static int ensure_batchwork(iht_dataset *ds, int nb, int kcap, int nsets, int64_
     const size_t np = (size_t)ds->n_pad, p = (size_t)ds->p, B = (size_t)nb, K = (size_t)kcap;
     cudaError_t e = cudaSuccess;
 #define BALLOC(field, bytes) \
-    if (e == cudaSuccess) e = cudaMalloc((void **)&x->field, std::max<size_t>(16, (size_t)(bytes)));
+    if (e == cudaSuccess) e = dev_malloc((void **)&x->field, std::max<size_t>(16, (size_t)(bytes)));
     BALLOC(sc, sizeof(Scalars) * B);
     BALLOC(y64, sizeof(double) * B * np);
     BALLOC(r64, sizeof(double) * B * np);
@@ -414,7 +414,7 @@ struct CvScratch {
     cudaError_t alloc(T **out, size_t count)
     {
         void *x = nullptr;
-        const cudaError_t e = cudaMalloc(&x, std::max<size_t>(16, sizeof(T) * count));
+        const cudaError_t e = dev_malloc(&x, std::max<size_t>(16, sizeof(T) * count));
         if (e == cudaSuccess) p.push_back(x);
         *out = static_cast<T *>(x);
         return e;
@@ -480,6 +480,7 @@ int iht_fit_batch(iht_dataset *ds, int32_t b, const iht_solve_desc *solves,
     const int npart = zmul_blocks(ds);
 
     // phenotypes, finite check, per-solve state
+    if ((rc = grad_mrhs_reset_status(ds)) || (rc = grad_tc_reset_status(ds))) return rc;
     IHT_CUDA(cudaMemsetAsync(w->sc, 0, sizeof(Scalars) * b, s));
     int64_t yoff = 0, koff = 0;
     for (int c = 0; c < b; ++c) {
@@ -862,6 +863,7 @@ int iht_gradient_batch(iht_dataset *ds, int32_t b, const int32_t *const *rows_li
                                    R + (size_t)c * ds->n, w->r32 + c * np)))
             return rc;
     }
+    if ((rc = grad_mrhs_reset_status(ds)) || (rc = grad_tc_reset_status(ds))) return rc;
     if ((rc = batch_grad(ds, w, act, set_of, impl))) return rc;
     cudaStream_t s = ds->ctx->stream;
     IHT_CUDA(cudaMemcpyAsync(G_out, w->g, sizeof(float) * b * p, cudaMemcpyDeviceToDevice, s));

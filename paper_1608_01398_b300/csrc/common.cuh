@@ -214,6 +214,20 @@ constexpr int kProfEvents = 256;
 
 // error helpers -----------------------------------------------------------
 void set_cuda_error(cudaError_t e, const char *where);
+// Device allocations of the library go through these (host-side fault
+// injection, iht_fault_inject, can make them fail as an exhausted device would).
+cudaError_t dev_malloc_raw(void **ptr, size_t bytes);
+cudaError_t dev_malloc_async_raw(void **ptr, size_t bytes, cudaStream_t s);
+template <typename T> inline cudaError_t dev_malloc(T **ptr, size_t bytes)
+{
+    return dev_malloc_raw(reinterpret_cast<void **>(ptr), bytes);
+}
+template <typename T> inline cudaError_t dev_malloc_async(T **ptr, size_t bytes, cudaStream_t s)
+{
+    return dev_malloc_async_raw(reinterpret_cast<void **>(ptr), bytes, s);
+}
+// true (and one injected fault used up) when a fault of `kind` is pending
+bool fault_take(int kind);
 void note_launch(int n = 1);           // kernel launches issued (iht_kernel_launches)
 uint64_t launches_noted();
 #define IHT_CUDA(call)                                                  \
@@ -267,6 +281,7 @@ int launch_grad_tc_main_with(iht_dataset *ds, const float *r32, float *g, const 
 void grad_tc_release_thread();
 uint64_t grad_tc_scratch_id();
 int grad_tc_status(iht_dataset *ds, int *timed_out);
+int grad_tc_reset_status(iht_dataset *ds);
 // impl: 0 default (tensor cores when supported), 1 CUDA cores, 2 tensor cores
 int launch_grad_impl(iht_dataset *ds, int impl, const float *r32, float *g, const int32_t *done);
 int launch_grad_simt_stats(iht_dataset *ds, const float *r32, const float *u32, const float *v32,
@@ -283,6 +298,7 @@ bool grad_mrhs_supported(const iht_dataset *ds);
 int launch_grad_mrhs(iht_dataset *ds, MrCol *cols_dev, int ncols, ProfEvents *prof = nullptr,
                      const MrCol *cols_host = nullptr);
 int grad_mrhs_status(iht_dataset *ds, int *timed_out);
+int grad_mrhs_reset_status(iht_dataset *ds);
 void grad_mrhs_release_thread();
 uint64_t grad_mrhs_scratch_id();
 // solver.cu: out-of-fold residuals of fitted solves (cross-validation)

@@ -550,7 +550,7 @@ static int build_padded_lists(iht_dataset *ds)
     const int64_t p = ds->p, ngroups = (p + kPadGroup - 1) / kPadGroup;
     const int blocks = (int)std::min<int64_t>(ceil_div(p, 256), (int64_t)ds->ctx->num_sms * 8);
     int32_t *glen = nullptr;
-    IHT_CUDA(cudaMalloc(&glen, sizeof(int32_t) * ngroups));
+    IHT_CUDA(dev_malloc(&glen, sizeof(int32_t) * ngroups));
     k_pad_len<<<blocks, 256, 0, s>>>(ds->miss_off, (const uint16_t *)ds->miss_idx, p, glen);
     note_launch();
     std::vector<int32_t> hl(ngroups);
@@ -564,9 +564,9 @@ static int build_padded_lists(iht_dataset *ds)
     }
     ho[0] = 0;
     for (int64_t g = 0; g < ngroups; ++g) ho[g + 1] = ho[g] + (int64_t)kPadGroup * hl[g];
-    e = cudaMalloc(&ds->miss_goff, sizeof(int64_t) * (ngroups + 1));
+    e = dev_malloc(&ds->miss_goff, sizeof(int64_t) * (ngroups + 1));
     // 16 spare entries: readers request the next 16-byte piece before they know it is needed
-    if (e == cudaSuccess) e = cudaMalloc(&ds->miss_gidx, sizeof(uint16_t) * (ho[ngroups] + 16));
+    if (e == cudaSuccess) e = dev_malloc(&ds->miss_gidx, sizeof(uint16_t) * (ho[ngroups] + 16));
     if (e == cudaSuccess) e = cudaMemsetAsync(ds->miss_gidx + ho[ngroups], 0, 16 * sizeof(uint16_t), s);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(ds->miss_goff, ho.data(), sizeof(int64_t) * (ngroups + 1), cudaMemcpyHostToDevice, s);
@@ -587,7 +587,7 @@ int build_missing_lists(iht_dataset *ds)
     cudaStream_t s = ds->ctx->stream;
     const int64_t p = ds->p;
     int32_t *cnt = nullptr;
-    IHT_CUDA(cudaMalloc(&cnt, sizeof(int32_t) * p));
+    IHT_CUDA(dev_malloc(&cnt, sizeof(int32_t) * p));
     const int blocks = (int)std::min<int64_t>(ceil_div(p, 8), (int64_t)ds->ctx->num_sms * 16);
     k_miss_count<<<blocks, 256, 0, s>>>(ds->G, p, ds->stride, ds->n, cnt);
     note_launch();
@@ -612,10 +612,10 @@ int build_missing_lists(iht_dataset *ds)
     for (int64_t j = 0; j < p; ++j) ho[j + 1] = ho[j] + hc[j];
     free(hc);
     ds->miss_total = ho[p];
-    e = cudaMalloc(&ds->miss_off, sizeof(int64_t) * (p + 1));
+    e = dev_malloc(&ds->miss_off, sizeof(int64_t) * (p + 1));
     if (e == cudaSuccess)
         // 16 spare entries: readers load the lists in aligned 16-byte pieces
-        e = cudaMalloc(&ds->miss_idx, (ds->miss_total + 16) * (ds->miss_idx16 ? 2 : 4));
+        e = dev_malloc(&ds->miss_idx, (ds->miss_total + 16) * (ds->miss_idx16 ? 2 : 4));
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(ds->miss_off, ho, sizeof(int64_t) * (p + 1), cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);

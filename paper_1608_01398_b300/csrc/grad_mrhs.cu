@@ -484,6 +484,8 @@ __global__ void __launch_bounds__(mr_threads(kTiles), 1) k_grad_mrhs(
         const int t = warp - kMrMmaWarp;
         if (lane == 0) {
             uint32_t aslot = 0, aphase = 0, bslot = 0, bphase = 0;
+            uint64_t *last_bar = nullptr;           // barrier of the last commit, and its phase
+            uint32_t last_par = 0;
             int T = 0;
             bool ok = true;
             const uint32_t b0 = mr_smem(bst);
@@ -508,6 +510,8 @@ __global__ void __launch_bounds__(mr_threads(kTiles), 1) k_grad_mrhs(
                             baddr += step_bytes;
                         }
                         mr_commit(&pipe.aempty[t][aslot]);
+                        last_bar = &pipe.aempty[t][aslot];
+                        last_par = aphase;
                         if (++aslot == (uint32_t)nbufs) {
                             aslot = 0;
                             aphase ^= 1u;
@@ -524,6 +528,11 @@ __global__ void __launch_bounds__(mr_threads(kTiles), 1) k_grad_mrhs(
                 mr_commit(&pipe.accfull[t]);
                 if (abort_flag) ok = false;
             }
+            // MMAs still running after an abort write tensor memory: wait (bounded)
+            // for the last commit, which tracks every MMA issued before it, so the
+            // allocation is not released under them (on a normal exit it has
+            // completed long ago)
+            if (last_bar) mr_wait(last_bar, last_par);
         }
         __syncwarp();
     } else if (warp == kGWarp) {
@@ -1149,7 +1158,7 @@ int launch_grad_mrhs(iht_dataset *ds, MrCol *cols, int ncols, ProfEvents *prof, 
             if (w.mj) cudaFree(w.mj);
             w.mj = nullptr;
             w.mj_cap = 0;
-            IHT_CUDA(cudaMalloc(&w.mj, sizeof(float) * (size_t)ds->p));
+            IHT_CUDA(dev_malloc(&w.mj, sizeof(float) * (size_t)ds->p));
             w.mj_cap = ds->p;
             w.mj_dev = ds->ctx->device;
         }
@@ -1170,8 +1179,8 @@ int launch_grad_mrhs(iht_dataset *ds, MrCol *cols, int ncols, ProfEvents *prof, 
         w.bimg = nullptr;
         w.err = nullptr;
         w.bbytes = 0;
-        IHT_CUDA(cudaMalloc(&w.bimg, need));
-        IHT_CUDA(cudaMalloc(&w.err, sizeof(int)));
+        IHT_CUDA(dev_malloc(&w.bimg, need));
+        IHT_CUDA(dev_malloc(&w.err, sizeof(int)));
         IHT_CUDA(cudaMemsetAsync(w.err, 0, sizeof(int), s));
         w.bbytes = need;
         w.dev = ds->ctx->device;
@@ -1226,15 +1235,26 @@ void grad_mrhs_release_thread()
     w = MrWork();
 }
 
-// Bounded-wait status of the multi-column passes so far (1 = a wait timed out).
+// Bounded-wait status of the multi-column passes since the last reset (1 = a
+// wait timed out); synchronises the stream.  An injected timeout
+// (iht_fault_inject) writes the error word from the host first.
 int grad_mrhs_status(iht_dataset *ds, int *timed_out)
 {
     *timed_out = 0;
     if (!g_mr.err) return IHT_OK;
+    if (fault_take(IHT_FAULT_TIMEOUT))
+        IHT_CUDA(cudaMemsetAsync(g_mr.err, 0x01, sizeof(int), ds->ctx->stream));
     int h = 0;
     IHT_CUDA(cudaMemcpyAsync(&h, g_mr.err, sizeof(int), cudaMemcpyDeviceToHost, ds->ctx->stream));
     IHT_CUDA(cudaStreamSynchronize(ds->ctx->stream));
-    *timed_out = h;
+    *timed_out = h != 0;
+    return IHT_OK;
+}
+
+// Clears the error word of the calling thread's multi-column pass (stream-ordered).
+int grad_mrhs_reset_status(iht_dataset *ds)
+{
+    if (g_mr.err) IHT_CUDA(cudaMemsetAsync(g_mr.err, 0, sizeof(int), ds->ctx->stream));
     return IHT_OK;
 }
 

@@ -139,10 +139,9 @@ __global__ void __launch_bounds__(1024) k_limbs(const float *__restrict__ r32, i
     // the trailing zero group may hold limbs of an earlier, longer residual
     for (int64_t b = threadIdx.x; b < 256; b += blockDim.x) bimg[256 + 256 * (n_pad >> 5) + b] = 0;
     acc = block_sum(acc, red);
-    if (threadIdx.x == 0) {
+    if (threadIdx.x == 0) {             // (err is left as it is: set by a pass that timed out)
         prm->s0 = s0;
         prm->R = (float)acc;
-        prm->err = 0;
     }
 }
 
@@ -457,6 +456,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_grad_tc(const __grid_constant
         const uint32_t za = 256u + 256u * (uint32_t)ksteps;   // trailing zero group
         if (lane == 0) {
             uint32_t buf = 0, use = 0;                                   // A-buffer ring
+            uint64_t *last_bar = nullptr;            // barrier of the last commit, and its phase
+            uint32_t last_par = 0;
             int T = 0;
             bool ok = true;
             const int ngrp = (ngroups + 1) / 2;                          // A groups per tile
@@ -488,6 +489,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_grad_tc(const __grid_constant
                         }
                     }
                     mma_commit(&P.empty[buf]);
+                    last_bar = &P.empty[buf];
+                    last_par = use & 1u;
                     if (gg == ngrp - 1) mma_commit(&P.accfull);
                     if (++buf == kTcBufs) {
                         buf = 0;
@@ -496,6 +499,11 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_grad_tc(const __grid_constant
                 }
                 if (abort_flag) ok = false;
             }
+            // MMAs still running after an abort write tensor memory: wait (bounded)
+            // for the last commit, which tracks every MMA issued before it, so the
+            // allocation is not released under them (on a normal exit it has
+            // completed long ago)
+            if (last_bar) mbar_wait(last_bar, last_par);
         }
         __syncwarp();
     } else {
@@ -632,9 +640,10 @@ int prepare_grad_tc_to(iht_dataset *ds, const float *r32, float *Mj, const int32
         w.bimg = nullptr;
         w.prm = nullptr;
         w.bbytes = 0;
-        IHT_CUDA(cudaMalloc(&w.bimg, bbytes));
-        IHT_CUDA(cudaMalloc(&w.prm, sizeof(TcParams)));
+        IHT_CUDA(dev_malloc(&w.bimg, bbytes));
+        IHT_CUDA(dev_malloc(&w.prm, sizeof(TcParams)));
         IHT_CUDA(cudaMemsetAsync(w.bimg, 0, bbytes, s));   // zero groups and unused limb rows
+        IHT_CUDA(cudaMemsetAsync(w.prm, 0, sizeof(TcParams), s));
         if (!w.side) {
             IHT_CUDA(cudaStreamCreateWithFlags(&w.side, cudaStreamNonBlocking));
             IHT_CUDA(cudaEventCreateWithFlags(&w.fork, cudaEventDisableTiming));
@@ -774,15 +783,26 @@ int launch_grad_tc(iht_dataset *ds, const float *r32, float *g, const int32_t *d
     return launch_grad_tc_main(ds, r32, g, done);
 }
 
-// Bounded-wait status of the last tensor-core pass (1 = a wait timed out).
+// Bounded-wait status of the tensor-core passes since the last reset (1 = a
+// wait timed out); synchronises the stream.  An injected timeout
+// (iht_fault_inject) writes the error word from the host first.
 int grad_tc_status(iht_dataset *ds, int *timed_out)
 {
     *timed_out = 0;
     if (!g_tc.prm) return IHT_OK;
+    if (fault_take(IHT_FAULT_TIMEOUT))
+        IHT_CUDA(cudaMemsetAsync(&g_tc.prm->err, 0x01, sizeof(int), ds->ctx->stream));
     TcParams h;
     IHT_CUDA(cudaMemcpyAsync(&h, g_tc.prm, sizeof(h), cudaMemcpyDeviceToHost, ds->ctx->stream));
     IHT_CUDA(cudaStreamSynchronize(ds->ctx->stream));
-    *timed_out = h.err;
+    *timed_out = h.err != 0;
+    return IHT_OK;
+}
+
+// Clears the error word of the calling thread's tensor-core pass (stream-ordered).
+int grad_tc_reset_status(iht_dataset *ds)
+{
+    if (g_tc.prm) IHT_CUDA(cudaMemsetAsync(&g_tc.prm->err, 0, sizeof(int), ds->ctx->stream));
     return IHT_OK;
 }
 

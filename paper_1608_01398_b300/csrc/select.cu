@@ -16,7 +16,8 @@
 // 9..0 within the boundary bin give the K-th key T, then every key > T and the
 // lowest-index keys == T.  The tickets, the histogram and the candidate count
 // are zero again when a call ends (the scratch is zeroed once when allocated).
-// NaN keys set SelState::err bit 0 (sticky).
+// A NaN key sets SelState::err bit 0 (the bit stays set until a caller clears
+// it); its bit pattern orders above +Inf, so NaN keys are selected first.
 #include <mutex>
 
 #include "common.cuh"
@@ -358,9 +359,9 @@ int ensure_selwork(iht_ctx *ctx, int64_t p)
     (void)p;
     SelWork &w = ctx->sel;
     if (!w.hist) {
-        IHT_CUDA(cudaMalloc(&w.hist, sizeof(uint32_t) * kSelBins));
-        IHT_CUDA(cudaMalloc(&w.st, sizeof(SelState)));
-        IHT_CUDA(cudaMalloc(&w.cand, sizeof(unsigned long long) * kSelCap));
+        IHT_CUDA(dev_malloc(&w.hist, sizeof(uint32_t) * kSelBins));
+        IHT_CUDA(dev_malloc(&w.st, sizeof(SelState)));
+        IHT_CUDA(dev_malloc(&w.cand, sizeof(unsigned long long) * kSelCap));
         IHT_CUDA(cudaMemsetAsync(w.hist, 0, sizeof(uint32_t) * kSelBins, ctx->stream));
         IHT_CUDA(cudaMemsetAsync(w.st, 0, sizeof(SelState), ctx->stream));
     }
@@ -390,10 +391,15 @@ int select_topk(iht_ctx *ctx, const float *keys, int64_t p, int32_t K, int32_t *
 // file-scope device array.  Every GPU that loads the library holds it (about
 // 41 KB) until the process exits.  The first call on a device clears it on the
 // caller's stream (cudaMemsetAsync, ahead of its kernels), and every call
-// leaves it clean again.  The array is shared by all calls on a device: calls
-// that overlap on the GPU (different streams, or several host threads) race on
-// it.
+// leaves it clean again; a call whose clear or launches fail marks the device
+// so that the next call clears it again.  The array is shared by all calls on
+// a device: calls that overlap on the GPU (different streams, or several host
+// threads) race on it.  The call does not synchronise, so it cannot report NaN
+// keys: they rank above +Inf (their bit patterns are larger), and the NaN bit
+// of the selection state is cleared at the start of every call.
 
+// The entry point's chosen fixed maximum p.  It is not set by the array: the
+// histogram, the state and the candidate buffer have the same size for any p.
 constexpr int64_t kNoAllocMaxP = int64_t(1) << 24;                 // 16 777 216 entries
 constexpr size_t kNoAllocHist = sizeof(uint32_t) * kSelBins;      // 8 KB
 constexpr size_t kNoAllocState = 256;                             // SelState, padded
@@ -411,9 +417,8 @@ static bool g_noalloc_cleared[kNoAllocMaxDevices] = {};
 
 // Device address of the scratch array on `device` (looked up once per device,
 // with that device current; the caller's current device is restored).
-// first: set when this call is the first on the device (the caller clears the
-// scratch on its stream before using it, and calls noalloc_unclear if that
-// fails, so the next call clears it again).
+// first: set while no call on the device has enqueued the clear yet (the
+// caller clears the scratch on its stream, then calls noalloc_mark_cleared).
 static int noalloc_scratch(int device, unsigned char **addr, int *num_sms, bool *first)
 {
     if (device < 0 || device >= kNoAllocMaxDevices) return IHT_EINVAL;
@@ -437,14 +442,13 @@ static int noalloc_scratch(int device, unsigned char **addr, int *num_sms, bool 
     *addr = g_noalloc_addr[device];
     *num_sms = g_noalloc_sms[device];
     *first = !g_noalloc_cleared[device];
-    g_noalloc_cleared[device] = true;
     return IHT_OK;
 }
 
-static void noalloc_unclear(int device)
+static void noalloc_mark_cleared(int device, bool cleared)
 {
     std::lock_guard<std::mutex> lock(g_noalloc_mu);
-    g_noalloc_cleared[device] = false;
+    g_noalloc_cleared[device] = cleared;
 }
 
 }  // namespace iht
@@ -454,7 +458,7 @@ extern "C" int iht_topk_noalloc(int device, void *stream, const float *w, int64_
 {
     using namespace iht;
     if (!w || !idx_out || p < 1 || k < 1 || k > p || k > kMaxCand) return IHT_EINVAL;
-    if (p > kNoAllocMaxP) return IHT_EINVAL;   // beyond the size of the static scratch
+    if (p > kNoAllocMaxP) return IHT_EINVAL;   // above the entry point's fixed maximum
     unsigned char *scratch = nullptr;
     int sms = 0;
     bool first = false;
@@ -463,27 +467,30 @@ extern "C" int iht_topk_noalloc(int device, void *stream, const float *w, int64_
     int prev = -1;
     IHT_CUDA(cudaGetDevice(&prev));
     if (prev != device) IHT_CUDA(cudaSetDevice(device));
-    if (first) {
-        const cudaError_t ce = cudaMemsetAsync(scratch, 0, kNoAllocBytes, (cudaStream_t)stream);
-        if (ce != cudaSuccess) {
-            noalloc_unclear(device);
-            if (prev != device) cudaSetDevice(prev);
-            set_cuda_error(ce, "iht_topk_noalloc scratch clear");
-            return IHT_ECUDA;
-        }
-    }
+    cudaStream_t s = (cudaStream_t)stream;
     uint32_t *hist = reinterpret_cast<uint32_t *>(scratch);
     SelState *st = reinterpret_cast<SelState *>(scratch + kNoAllocHist);
     unsigned long long *cand = reinterpret_cast<unsigned long long *>(scratch + kNoAllocHist + kNoAllocState);
-    cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t e = first ? cudaMemsetAsync(scratch, 0, kNoAllocBytes, s)
+                          : cudaMemsetAsync(&st->err, 0, sizeof(st->err), s);
+    if (e != cudaSuccess) {
+        if (prev != device) cudaSetDevice(prev);
+        set_cuda_error(e, "iht_topk_noalloc scratch clear");
+        return IHT_ECUDA;
+    }
+    if (first) noalloc_mark_cleared(device, true);
     const int blocks = sel_blocks(p, sms, 1);
     k_sel_count<<<blocks, kSelAThreads, 0, s>>>(w, p, st, hist, (uint32_t)k, nullptr);
-    k_sel_pick<<<blocks, kSelBThreads, 0, s>>>(w, p, st, cand, idx_out, (uint32_t)k, nullptr, nullptr, 0,
-                                               nullptr, nullptr);
+    e = cudaGetLastError();
+    if (e == cudaSuccess) {
+        k_sel_pick<<<blocks, kSelBThreads, 0, s>>>(w, p, st, cand, idx_out, (uint32_t)k, nullptr,
+                                                   nullptr, 0, nullptr, nullptr);
+        e = cudaGetLastError();
+    }
     note_launch(2);
-    const cudaError_t e = cudaGetLastError();
     if (prev != device) cudaSetDevice(prev);
     if (e != cudaSuccess) {
+        noalloc_mark_cleared(device, false);   // the scratch may be left dirty: clear it next time
         set_cuda_error(e, "iht_topk_noalloc launch");
         return IHT_ECUDA;
     }

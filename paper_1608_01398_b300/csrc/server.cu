@@ -163,7 +163,7 @@ static int srv_admit_setup(iht_server *S, const std::vector<int> &fresh, std::ve
     for (size_t a = 0; a < fresh.size(); ++a) {
         Slot &sl = S->slots[fresh[a]];
         const SrvRequest &q = reqs[a];
-        IHT_CUDA(cudaMallocAsync(&sl.block, q.bytes, s));
+        IHT_CUDA(dev_malloc_async(&sl.block, q.bytes, s));
         slot_layout(ds, q.k, q.n_rows, (char *)sl.block, &sl.m);
         SlotMem &m = sl.m;
         sl.busy = true;
@@ -494,11 +494,11 @@ int iht_server_create(iht_dataset *ds, const iht_server_options *opt_in, iht_ser
     S->view.ctx = &S->ctx;
     S->view.ws = nullptr;
     const size_t B = (size_t)opt.max_slots;
-    if (e == cudaSuccess) e = cudaMalloc(&S->sc, sizeof(Scalars) * B);
-    if (e == cudaSuccess) e = cudaMalloc(&S->bs, sizeof(BSolve) * B);
-    if (e == cudaSuccess) e = cudaMalloc(&S->jobs_c, sizeof(SelJob) * B);
-    if (e == cudaSuccess) e = cudaMalloc(&S->jobs_s, sizeof(SelJob) * B);
-    if (e == cudaSuccess) e = cudaMalloc(&S->cols, sizeof(MrCol) * B);
+    if (e == cudaSuccess) e = dev_malloc(&S->sc, sizeof(Scalars) * B);
+    if (e == cudaSuccess) e = dev_malloc(&S->bs, sizeof(BSolve) * B);
+    if (e == cudaSuccess) e = dev_malloc(&S->jobs_c, sizeof(SelJob) * B);
+    if (e == cudaSuccess) e = dev_malloc(&S->jobs_s, sizeof(SelJob) * B);
+    if (e == cudaSuccess) e = dev_malloc(&S->cols, sizeof(MrCol) * B);
     if (e == cudaSuccess) e = cudaMallocHost(&S->sc_host, sizeof(Scalars) * B);
     if (e == cudaSuccess) e = cudaMallocHost(&S->bs_host, sizeof(BSolve) * B);
     if (e == cudaSuccess) e = cudaMallocHost(&S->jobs_c_host, sizeof(SelJob) * B);

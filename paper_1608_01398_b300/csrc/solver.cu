@@ -797,6 +797,7 @@ int run_solve(iht_dataset *ds, int k, const iht_options *opt, int n_rows, const 
     IHT_CUDA(cudaStreamSynchronize(s));
     h.err = ws->sc_host->err;        // row / input flags from the set-up kernels
     if (h.err) return (h.err & 1) ? IHT_ENUMERIC : IHT_EINVAL;
+    if ((rc = grad_tc_reset_status(ds))) return rc;
     *ws->sc_host = h;
     IHT_CUDA(cudaMemcpyAsync(ws->sc, ws->sc_host, sizeof(Scalars), cudaMemcpyHostToDevice, s));
 
@@ -883,7 +884,9 @@ int run_solve(iht_dataset *ds, int k, const iht_options *opt, int n_rows, const 
         if (ws->sc_host->done) break;
     }
     IHT_CUDA(cudaMemcpyAsync(ws->sc_host, ws->sc, sizeof(Scalars), cudaMemcpyDeviceToHost, s));
-    IHT_CUDA(cudaStreamSynchronize(s));
+    int timed_out = 0;
+    if ((rc = grad_tc_status(ds, &timed_out))) return rc;     // synchronises the stream
+    if (timed_out) return IHT_ETIMEOUT;                        // a pass gave up: g was not formed
     ws->prof_ms = graph_ms;
     for (int e = 0; prof && e < ws->nprof; ++e) {
         float ms = 0.0f;
@@ -903,7 +906,7 @@ int run_solve_host(iht_dataset *ds, int k, const iht_options *opt, int n_rows, i
     if (trace) {
         const size_t bytes = T * (2 * sizeof(double) + 2 * sizeof(int32_t)) +
                              T * k * (sizeof(int32_t) + sizeof(double));
-        IHT_CUDA(cudaMalloc(&buf, bytes));
+        IHT_CUDA(dev_malloc(&buf, bytes));
         char *p = (char *)buf;
         tr.objective = (double *)p; p += T * sizeof(double);
         tr.mu = (double *)p; p += T * sizeof(double);

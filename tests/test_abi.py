@@ -76,3 +76,13 @@ def test_server_entry_points_check_arguments():
     assert lib.iht_server_poll(None, 1, None, None, None, None) == iht.IHT_EINVAL
     assert lib.iht_server_get_stats(None, None) == iht.IHT_EINVAL
     assert lib.iht_server_destroy(None) == iht.IHT_EINVAL
+
+
+def test_fault_injection_arguments():
+    """Host-side fault injection checks its arguments and needs no device."""
+    lib = iht._lib()
+    assert lib.iht_fault_inject(iht.IHT_FAULT_NONE, 0) == iht.IHT_OK
+    assert lib.iht_fault_inject(3, 1) == iht.IHT_EINVAL
+    assert lib.iht_fault_inject(iht.IHT_FAULT_ALLOC, -1) == iht.IHT_EINVAL
+    assert lib.iht_fault_inject(iht.IHT_FAULT_TIMEOUT, 2) == iht.IHT_OK
+    assert lib.iht_fault_inject(iht.IHT_FAULT_NONE, 0) == iht.IHT_OK

@@ -274,3 +274,17 @@ def test_topk_unaligned_keys(iht, ctx, offset):
     idx = iht.iht_topk(ctx, wd, k).cpu().numpy()
     ww = w[offset:].astype(np.float64)
     assert np.array_equal(idx, np.sort(np.lexsort((np.arange(p), -np.abs(ww)))[:k]))
+
+
+def test_topk_nan_is_reported(iht, ctx):
+    """A NaN key: iht_topk reports ENUMERIC; the next clean call is OK again."""
+    torch = _torch()
+    rng = np.random.default_rng(12)
+    w = rng.normal(size=20000).astype(np.float32)
+    bad = w.copy()
+    bad[777] = np.nan
+    with pytest.raises(iht.IhtError) as e:
+        iht.iht_topk(ctx, torch.from_numpy(bad).cuda(), 10)
+    assert e.value.status == iht.IHT_ENUMERIC
+    idx = iht.iht_topk(ctx, torch.from_numpy(w).cuda(), 10).cpu().numpy()
+    assert np.array_equal(idx, np.sort(np.lexsort((np.arange(w.size), -np.abs(w.astype(np.float64))))[:10]))

@@ -45,6 +45,32 @@ def test_noalloc_topk_matches_iht_topk_twice(env):
         assert np.array_equal(got, ref)
 
 
+def test_noalloc_topk_on_a_side_stream_and_with_nan(env):
+    """The call orders its work on the stream it is given; a NaN key ranks above
+    +Inf (the call does not synchronise, so it returns no status for it)."""
+    torch, iht, ctx = env
+    rng = np.random.default_rng(5)
+    p, k = 200_003, 64
+    w = rng.normal(size=p).astype(np.float32)
+    side = torch.cuda.Stream()
+    for bad in (None, 1234):
+        ww = w.copy()
+        if bad is not None:
+            ww[bad] = np.nan
+        wd = torch.from_numpy(ww).cuda()
+        torch.cuda.synchronize()
+        out = torch.full((k,), -1, dtype=torch.int32, device="cuda")
+        with torch.cuda.stream(side):
+            iht.iht_topk_noalloc(wd, k, out, stream=side)
+        side.synchronize()
+        got = out.cpu().numpy()
+        key = np.abs(w.astype(np.float64))
+        order = np.lexsort((np.arange(p), -key))
+        if bad is not None:                      # the NaN first, then the rest by |w|
+            order = np.concatenate([[bad], order[order != bad]])
+        assert np.array_equal(got, np.sort(order[:k]))
+
+
 def test_noalloc_topk_refuses_oversize(env):
     torch, iht, ctx = env
     lib = iht._lib()
