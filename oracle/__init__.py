@@ -40,7 +40,11 @@ def build(force: bool = False, src: str = _SRC, out: str = _LIB, defines=()) -> 
 
 class _Opts(ctypes.Structure):
     _fields_ = [("max_iter", ctypes.c_int32), ("max_backtrack", ctypes.c_int32),
-                ("tol", ctypes.c_double), ("c", ctypes.c_double), ("kappa", ctypes.c_double)]
+                ("tol", ctypes.c_double), ("c", ctypes.c_double), ("kappa", ctypes.c_double),
+                ("variant", ctypes.c_int32), ("pad", ctypes.c_int32)]
+
+
+VARIANTS = {"iht": 0, "htp": 1}
 
 
 class _Info(ctypes.Structure):
@@ -69,13 +73,14 @@ def load(path: str = _LIB, build_first: bool = True):
     lib.oracle_gradient.argtypes = [P, i64, i64, i64, P, i64, P, P, P, P]
     lib.oracle_zmul.argtypes = [P, i64, i64, P, i64, P, P, P, i32, P, P]
     lib.oracle_topk.argtypes = [P, i64, i32, P]
-    lib.oracle_iht.argtypes = [P, i64, i64, i64, P, i64, P, i32, ctypes.POINTER(_Opts), P, P,
-                               ctypes.POINTER(_Info), ctypes.POINTER(_Trace)]
+    lib.oracle_iht.argtypes = [P, i64, i64, i64, P, i64, P, i32, ctypes.POINTER(_Opts), P, i64,
+                               P, P, ctypes.POINTER(_Info), ctypes.POINTER(_Trace)]
+    lib.oracle_cov_stats.argtypes = [P, i64, i64, P, i64, P, P]
     lib.oracle_set_threads.argtypes = [ctypes.c_int]
     lib.oracle_set_threads.restype = None
     lib.oracle_max_threads.restype = ctypes.c_int
     for f in ("oracle_decode", "oracle_counts", "oracle_gradient", "oracle_zmul",
-              "oracle_topk", "oracle_iht"):
+              "oracle_topk", "oracle_iht", "oracle_cov_stats"):
         getattr(lib, f).restype = ctypes.c_int
     if path == _LIB:
         _lib = lib
@@ -168,6 +173,27 @@ def zmul(G: Geno, cols, coef, rows=None, u=None, v=None, lib=None) -> np.ndarray
     return out
 
 
+def _cov(cov, n: int):
+    """Covariates as a contiguous (q, n) float64 array, or None."""
+    if cov is None:
+        return None
+    c = np.ascontiguousarray(np.atleast_2d(cov), dtype=np.float64)
+    if c.shape[1] != n:
+        raise ValueError("cov must have shape (q, n)")
+    return c
+
+
+def cov_stats(cov, n: int, rows=None, lib=None):
+    """Mean and inverse SD of each covariate over the rows (reading R13)."""
+    c = _cov(cov, n)
+    rows = _rows(rows)
+    nr = n if rows is None else rows.size
+    q = c.shape[0]
+    cu, cv = np.empty(q), np.empty(q)
+    _check((lib or load()).oracle_cov_stats(_p(c), n, q, _p(rows), nr, _p(cu), _p(cv)))
+    return cu, cv
+
+
 def topk(w, k: int, lib=None) -> np.ndarray:
     w = np.ascontiguousarray(w, dtype=np.float64)
     out = np.empty(k, dtype=np.int32)
@@ -188,12 +214,17 @@ class Fit:
 
 
 def iht(G: Geno, y, k: int, rows=None, max_iter: int = 100, tol: float = 1e-4, c: float = 0.01,
-        kappa: float = 2.0, max_backtrack: int = 50, trace: bool = True, lib=None) -> Fit:
+        kappa: float = 2.0, max_backtrack: int = 50, trace: bool = True, lib=None,
+        variant: str = "iht", cov=None) -> Fit:
+    """IHT (or HTP, variant="htp") on the SNPs and the optional covariates
+    cov (q, n); beta has p + q entries, covariate t at index p + t."""
     rows = _rows(rows)
     y = np.ascontiguousarray(y, dtype=np.float64)
-    beta = np.zeros(G.p)
+    cv = _cov(cov, G.n)
+    q = 0 if cv is None else cv.shape[0]
+    beta = np.zeros(G.p + q)
     supp = np.empty(k, dtype=np.int32)
-    opts = _Opts(max_iter, max_backtrack, tol, c, kappa)
+    opts = _Opts(max_iter, max_backtrack, tol, c, kappa, VARIANTS[variant], 0)
     info = _Info()
     T = max(max_iter, 1)
     tr = {}
@@ -207,8 +238,8 @@ def iht(G: Geno, y, k: int, rows=None, max_iter: int = 100, tol: float = 1e-4, c
         for nm, arr in tr.items():
             setattr(ct, nm, arr.ctypes.data)
     rc = (lib or load()).oracle_iht(_p(G.body), G.row_bytes, G.n, G.p, _p(rows), y.size, _p(y),
-                                    k, ctypes.byref(opts), _p(beta), _p(supp), ctypes.byref(info),
-                                    ctypes.byref(ct) if trace else None)
+                                    k, ctypes.byref(opts), _p(cv), q, _p(beta), _p(supp),
+                                    ctypes.byref(info), ctypes.byref(ct) if trace else None)
     if rc not in (OK, ENOTCONV, ENUMERIC):
         raise RuntimeError(f"oracle_iht status {rc}")
     if trace:

@@ -479,7 +479,159 @@ def pin_convergence_rule(lib):
     assert d / b >= tol, "the 1e-3 instance must separate the +1 rule from a relative test"
 
 
+
+def _np_htp_iteration(Z, y, beta, S, k, c, kappa, max_bt):
+    """One HTP iteration in numpy (Sec. 2.2 and the step-size reading R11):
+    the normalized step over Gamma = the k largest |g|, IHT's projection and
+    backtracking rule on the candidate, then least squares on S+ (numpy
+    lstsq).  Returns (S+, beta+, mu, shrinks)."""
+    g = Z.T @ (y - Z @ beta)
+    gam = _np_topk(g, k)
+    mu = (g[gam] @ g[gam]) / np.sum((Z[:, gam] @ g[gam]) ** 2)
+    for j in range(max_bt + 1):
+        w = beta + mu * g
+        Sp = _np_topk(w, k)
+        if np.array_equal(Sp, S):
+            break
+        bp = np.zeros_like(beta)
+        bp[Sp] = w[Sp]
+        d = bp - beta
+        rho = (d @ d) / np.sum((Z @ d) ** 2)
+        if mu < (1 - c) * rho or j == max_bt:
+            break
+        mu /= kappa
+    out = np.zeros_like(beta)
+    out[Sp] = np.linalg.lstsq(Z[:, Sp], y, rcond=None)[0]
+    return Sp, out, mu, j
+
+
+def pin_htp_replay(lib):
+    """HTP, iteration by iteration against numpy: the step over the k largest
+    |g| (after a refit g vanishes on S), the backtracking decisions on the
+    projected candidate, the support, beta+ = least squares on S+ (Eq.
+    normal_equations) and the stopping rule; the objective never increases."""
+    for seed, k, c in ((70, 5, 0.01), (71, 12, 0.01), (72, 12, 0.3), (74, 8, 0.3), (79, 5, 0.3)):
+        rng, G, codes = _panel(seed, 150, 300, miss=0.02)
+        Z = np_Z(codes)
+        causal = rng.choice(G.p, size=8, replace=False)
+        y = Z[:, causal] @ rng.normal(0, 0.5, size=8) + rng.normal(size=G.n)
+        f = oracle.iht(G, y, k, c=c, tol=1e-10, max_iter=100, variant="htp", lib=lib)
+        assert f.status == oracle.OK and f.iterations >= 2
+        beta = np.zeros(G.p)
+        S = _np_topk(Z.T @ y, k)
+        fprev = 0.5 * float(y @ y)
+        for t in range(f.iterations):
+            Sp, bp, mu, bt = _np_htp_iteration(Z, y, beta, S, k, c, 2.0, 50)
+            assert np.array_equal(Sp, f.trace["supp"][t]), f"support at iteration {t}"
+            assert np.allclose(bp[Sp], f.trace["beta"][t], rtol=1e-8, atol=1e-10), f"refit at {t}"
+            assert abs(mu - f.trace["mu"][t]) <= 1e-8 * mu, f"step size at iteration {t}"
+            assert bt == f.trace["backtracks"][t], f"shrinks at iteration {t}"
+            step = np.linalg.norm(bp - beta) / (np.linalg.norm(beta) + 1.0)
+            assert (step < 1e-10) == (t == f.iterations - 1), f"stopping rule at {t}"
+            fcur = 0.5 * float(np.sum((y - Z @ bp) ** 2))
+            assert abs(f.trace["objective"][t] - fcur) <= 1e-9 * fcur
+            assert fcur <= fprev * (1 + 1e-12), f"objective increased at {t}"
+            beta, S, fprev = bp, Sp, fcur
+
+
+def pin_htp_closed_forms(lib):
+    """HTP on tiny inputs: never below the best k-subset least-squares fit,
+    equal to it on strong signals; k = p < n gives OLS after one step and
+    stops at the next; a duplicated column and a monomorphic column among the
+    predictors leave the fitted values those of numpy's least squares, with
+    coefficient 0 on the later duplicate and on the constant column."""
+    for seed in (61, 62, 63):
+        rng, G, codes = _panel(seed, 40, 12, miss=0.0)
+        Z = np_Z(codes)
+        for k in (1, 2, 3):
+            for strong in (False, True):
+                if strong:
+                    S = rng.choice(G.p, size=k, replace=False)
+                    y = Z[:, S] @ (rng.choice([-1, 1], size=k) * rng.uniform(4, 6, size=k)) \
+                        + 0.3 * rng.normal(size=G.n)
+                else:
+                    y = rng.normal(size=G.n)
+                best = min(lstsq_obj(Z, y, cc)[1] for cc in itertools.combinations(range(G.p), k))
+                f = oracle.iht(G, y, k, tol=1e-12, max_iter=500, variant="htp", lib=lib)
+                assert f.objective >= best - 1e-9 * (1 + best), "HTP below the subset optimum"
+                if strong:
+                    assert abs(f.objective - best) <= 1e-9 * (1 + best), "strong signal: optimum"
+    rng, G, codes = _panel(41, 120, 6, miss=0.0)
+    Z = np_Z(codes)
+    y = Z @ rng.normal(size=6) + rng.normal(size=G.n)
+    f = oracle.iht(G, y, 6, tol=1e-12, max_iter=50, variant="htp", lib=lib)
+    coef, _ = lstsq_obj(Z, y, range(6))
+    assert np.allclose(f.trace["beta"][0], coef, rtol=1e-9, atol=1e-12), "k = p: OLS in one step"
+    assert f.iterations == 2 and f.status == oracle.OK
+    rng = np.random.default_rng(91)
+    _, codes = random_geno(rng, 90, 10, miss=0.0)
+    codes[7] = codes[2]                                   # column 7 duplicates column 2
+    codes[5] = 3                                          # column 5 is monomorphic
+    G = geno_from_codes(codes)
+    Z = np_Z(codes)
+    y = Z[:, [2, 4]] @ np.array([1.5, -1.0]) + 0.5 * rng.normal(size=G.n)
+    f = oracle.iht(G, y, 10, tol=1e-12, max_iter=50, variant="htp", lib=lib)
+    fit = Z @ f.beta
+    want = Z @ np.linalg.lstsq(Z, y, rcond=None)[0]
+    assert np.allclose(fit, want, rtol=1e-9, atol=1e-9), "fitted values of the full refit"
+    assert f.beta[7] == 0.0 and f.beta[5] == 0.0, "dependent and zero columns get 0"
+
+
+def _cov_panel(seed):
+    rng, G, codes = _panel(seed, 200, 60, miss=0.02)
+    cov = np.vstack([rng.normal(size=G.n), (rng.random(G.n) < 0.4).astype(float),
+                     rng.gamma(2.0, size=G.n), np.full(G.n, 3.0)])     # last one constant
+    return rng, G, codes, cov
+
+
+def _np_cov_z(cov, rows=None):
+    c = cov if rows is None else cov[:, rows]
+    m = c.mean(axis=1, keepdims=True)
+    s = c.std(axis=1, ddof=1, keepdims=True)
+    with np.errstate(invalid="ignore", divide="ignore"):
+        z = np.where(s > 0, (c - m) / s, 0.0)
+    return z.T
+
+
+def pin_cov_stats(lib):
+    """Covariate mean / inverse SD (reading R13) against numpy, with a row subset
+    and a constant column (inverse SD 0)."""
+    rng, G, codes, cov = _cov_panel(83)
+    for rows in (None, np.sort(rng.choice(G.n, size=77, replace=False))):
+        cu, cv = oracle.cov_stats(cov, G.n, rows, lib=lib)
+        c = cov if rows is None else cov[:, rows]
+        assert np.allclose(cu, c.mean(axis=1), rtol=1e-13, atol=1e-13)
+        sd = c.std(axis=1, ddof=1)
+        assert np.allclose(cv[:3], 1.0 / sd[:3], rtol=1e-12) and cv[3] == 0.0
+
+
+def pin_cov_design(lib):
+    """IHT with covariates is IHT on the design [Z | C_std] (covariates standardised
+    over the used rows, appended after the SNPs, counted in k): each iteration
+    replayed in numpy on that matrix; with a row subset too; and at a fixed
+    point beta solves the normal equations on its support."""
+    rng, G, codes, cov = _cov_panel(84)
+    for rows in (None, np.sort(rng.choice(G.n, size=170, replace=False))):
+        Z = np.hstack([np_Z(codes, rows), _np_cov_z(cov, rows)])
+        nr = Z.shape[0]
+        y = Z[:, [4, 11, G.p, G.p + 2]] @ np.array([0.8, -0.6, 1.5, 0.7]) + rng.normal(size=nr)
+        for k in (3, 6):
+            f = oracle.iht(G, y, k, rows=rows, cov=cov, tol=1e-4, max_iter=200, lib=lib)
+            assert np.any(f.support >= G.p), "a covariate enters the support"
+            beta = np.zeros(G.p + cov.shape[0])
+            S = _np_topk(Z.T @ y, k)
+            for t in range(f.iterations):
+                Sp, bp, mu, bt, _ = _np_iteration(Z, y, beta, S, k, 0.01, 2.0, 50)
+                assert np.array_equal(Sp, f.trace["supp"][t]), f"support at iteration {t}"
+                assert np.allclose(bp[Sp], f.trace["beta"][t], rtol=1e-9, atol=1e-12)
+                beta, S = bp, Sp
+        f = oracle.iht(G, y, 4, rows=rows, cov=cov, tol=1e-12, max_iter=5000, lib=lib)
+        coef, obj = lstsq_obj(Z, y, f.support)
+        assert np.allclose(f.beta[f.support], coef, rtol=1e-7, atol=1e-9), "normal equations"
+
+
 ALL_PINS = [pin_decode, pin_counts_stats, pin_stats_exact, pin_gradient, pin_identity, pin_topk,
             pin_k1_marginal, pin_fixed_point, pin_full_ols, pin_noiseless, pin_bruteforce,
             pin_invariants, pin_orientation, pin_cv, pin_backtracking_replay,
-            pin_convergence_rule]
+            pin_convergence_rule, pin_htp_replay, pin_htp_closed_forms, pin_cov_stats,
+            pin_cov_design]

@@ -40,6 +40,14 @@ MUTANTS = {
                                       "double step = sqrt(dn);")],
     "convergence_plain_relative": [("double step = sqrt(dn) / (sqrt(bn) + 1.0);",
                                     "double step = sqrt(dn) / sqrt(bn);")],
+    "htp_without_refit": [("if (htp) {\n            refit_ls(", "if (0) {\n            refit_ls(")],
+    "htp_step_over_support": [("stepset = gam;", "stepset = S;")],
+    "htp_refit_without_dependence_threshold": [("d > 1e-10 * gij ? sqrt(d) : 0.0", "d > 0.0 ? sqrt(d) : 0.0")],
+    "covariates_not_scaled": [("return D->cv[t] * (D->cov[t * D->n + row_of(D->rows, a)] - D->cu[t]);",
+                               "return (D->cov[t * D->n + row_of(D->rows, a)] - D->cu[t]);")],
+    "covariate_variance_over_n": [("const double var = ss / (double)(n_rows - 1);",
+                                   "const double var = ss / (double)n_rows;")],
+    "covariates_ignore_row_subset": [("m += c[row_of(rows, a)];", "m += c[a];")],
 }
 
 
