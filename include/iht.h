@@ -60,7 +60,23 @@ typedef struct iht_options {
     int32_t out_mem;       /* where beta_out and support_out live                    */
     int32_t grad_impl;     /* gradient kernel: 0 default, 1 CUDA-core, 2 tensor-core  */
     int32_t profile;       /* 1: time every gradient launch with CUDA events [0]     */
+    int32_t variant;       /* IHT_VARIANT_IHT [default] or IHT_VARIANT_HTP (below)   */
+    int32_t reserved;
 } iht_options;
+
+/* Solver variants (iht_options.variant).
+ *   IHT: the projected gradient step of Eq. ihta.
+ *   HTP: hard thresholding pursuit (Sec. 2.2: the projection is followed by a
+ *        least-squares solve of the normal equations, Eq. normal_equations, on
+ *        the active set).  After a refit the gradient vanishes on the support,
+ *        so the normalized step is taken over the k largest |g_j| (ties to the
+ *        lower index); the backtracking check applies to the projected
+ *        candidate, whose support S+ is then refitted by an FP64 Cholesky
+ *        solve in ascending index order, a column with pivot <= 1e-10 times its
+ *        diagonal entry (zero or dependent on earlier columns) getting 0.
+ *        Supported by iht_fit and iht_fit_trace; the batched calls, iht_cv,
+ *        the server and iht_fit_resume return EINVAL for it. */
+enum { IHT_VARIANT_IHT = 0, IHT_VARIANT_HTP = 1 };
 
 typedef struct iht_result {
     int32_t iterations;    /* updates performed                                */
@@ -138,6 +154,22 @@ int iht_dataset_free(iht_dataset *ds);
 /* Dataset shape: n, p and the repacked row stride in bytes (any may be NULL). */
 int iht_dataset_shape(const iht_dataset *ds, int64_t *n, int64_t *p, int64_t *stride);
 
+/* Nongenetic covariates (Sec. 3: the predictors are the SNPs and the
+ * covariates, and a model size k counts both).  Sets q dense columns that
+ * iht_fit and iht_fit_trace append to the SNPs as predictors p .. p+q-1:
+ * each is standardised over the rows of the solve (mean, (n_rows - 1)
+ * denominator, a constant column is inert) and competes in the projection
+ * like a SNP.  With covariates set, beta_out of those calls has p + q entries
+ * and support entries >= p name covariates.
+ *   cov : double[q][n], covariate t of subject i at cov[t * n + i], in memory
+ *         of kind `mem`; copied (the caller keeps ownership).
+ *   q   : 0..64; 0 removes the covariates.
+ * A non-finite value on a used row makes the fit return ENUMERIC.  The
+ * batched calls, iht_cv, the server and iht_fit_resume return EINVAL on a
+ * dataset with covariates.  EINVAL for q outside 0..64 or cov NULL with q > 0;
+ * ENOMEM if the copy does not fit. */
+int iht_set_covariates(iht_dataset *ds, const double *cov, int32_t q, int mem);
+
 /* a1 -- per-SNP code counts and the cached mean / inverse-SD vectors u, v of
  * Sec. 2.3.2, over a row set.
  *   rows       : n_rows distinct subject indices in [0, n), or NULL for all n.
@@ -204,10 +236,11 @@ int iht_zmul(iht_dataset *ds, const int32_t *rows, int64_t n_rows, const double 
 /* a2-a6 -- IHT least squares to convergence (Sec. 2.2-2.3.1).
  *   rows        : int32[n_rows] subjects the solve uses, or NULL for all n.
  *   y           : double[n_rows] phenotype aligned with rows.
- *   k           : sparsity level, 1 <= k <= p.
+ *   k           : sparsity level, 1 <= k <= p (+ q with covariates), k <= 1024.
  *   opt         : options (NULL = defaults).  rows and y live in opt->in_mem,
  *                 beta_out and support_out in opt->out_mem.
- *   beta_out    : double[p], written in full (zeros off the support).
+ *   beta_out    : double[p] (p + q with covariates), written in full (zeros
+ *                 off the support).
  *   support_out : int32[k], ascending.
  *   info        : host iht_result, may be NULL.
  * Starts from beta = 0 with S^0 = the top-k of |Z^T y|.  Returns the solve's

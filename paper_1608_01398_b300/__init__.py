@@ -22,6 +22,8 @@ IHT_OK, IHT_EINVAL, IHT_ENOMEM, IHT_ENOTCONV, IHT_ENUMERIC, IHT_ETIMEOUT, IHT_EC
 IHT_HOST, IHT_DEVICE = 0, 1
 IHT_PASS_SINGLE, IHT_PASS_MULTI = 0, 1
 IHT_FAULT_NONE, IHT_FAULT_ALLOC, IHT_FAULT_TIMEOUT = 0, 1, 2
+IHT_VARIANT_IHT, IHT_VARIANT_HTP = 0, 1
+VARIANTS = {"iht": IHT_VARIANT_IHT, "htp": IHT_VARIANT_HTP}
 
 EXPORTED = ["iht_default_options", "iht_strerror", "iht_last_cuda_error", "iht_kernel_launches",
             "iht_create",
@@ -31,7 +33,7 @@ EXPORTED = ["iht_default_options", "iht_strerror", "iht_last_cuda_error", "iht_k
             "iht_server_create", "iht_server_submit", "iht_server_poll", "iht_server_get_stats",
             "iht_server_destroy", "iht_state_bytes", "iht_state_save", "iht_state_load",
             "iht_fit_resume", "iht_set_autotune", "iht_tune_clear", "iht_tune_pin", "iht_tune_query",
-            "iht_tuning_summary", "iht_cv", "iht_fault_inject"]
+            "iht_tuning_summary", "iht_cv", "iht_fault_inject", "iht_set_covariates"]
 
 
 class IhtError(RuntimeError):
@@ -47,7 +49,8 @@ class iht_options(ctypes.Structure):
     _fields_ = [("max_iter", ctypes.c_int32), ("max_backtrack", ctypes.c_int32),
                 ("tol", ctypes.c_double), ("c", ctypes.c_double), ("kappa", ctypes.c_double),
                 ("in_mem", ctypes.c_int32), ("out_mem", ctypes.c_int32),
-                ("grad_impl", ctypes.c_int32), ("profile", ctypes.c_int32)]
+                ("grad_impl", ctypes.c_int32), ("profile", ctypes.c_int32),
+                ("variant", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 class iht_result(ctypes.Structure):
@@ -111,6 +114,7 @@ def _lib(build_if_stale: bool = True):
         "iht_destroy": (ctypes.c_int, [P]),
         "iht_load_bed": (ctypes.c_int, [P, P, sz, ctypes.c_int, i64, i64, ctypes.POINTER(P)]),
         "iht_dataset_free": (ctypes.c_int, [P]),
+        "iht_set_covariates": (ctypes.c_int, [P, P, i32, ctypes.c_int]),
         "iht_dataset_shape": (ctypes.c_int, [P, ctypes.POINTER(i64), ctypes.POINTER(i64),
                                              ctypes.POINTER(i64)]),
         "iht_counts": (ctypes.c_int, [P, P, i64, ctypes.c_int, P, P, P]),
@@ -238,6 +242,27 @@ class Dataset:
         n_, p_, s_ = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
         _lib().iht_dataset_shape(h, ctypes.byref(n_), ctypes.byref(p_), ctypes.byref(s_))
         self.n, self.p, self.stride = n_.value, p_.value, s_.value
+        self.q = 0
+
+    def set_covariates(self, cov) -> None:
+        """iht_set_covariates: cov (q, n) host array or CUDA float64 tensor; None
+        or q = 0 removes them.  Fits then have p + q coefficients."""
+        torch = _torch()
+        if cov is None:
+            _check(_lib().iht_set_covariates(self.h, None, 0, IHT_HOST), "iht_set_covariates")
+            self.q = 0
+            return
+        if isinstance(cov, torch.Tensor):
+            if cov.dim() != 2 or cov.shape[1] != self.n:
+                raise ValueError("cov must have shape (q, n)")
+            ptr, q, mem = _dptr(cov, torch.float64, "cov"), cov.shape[0], IHT_DEVICE
+        else:
+            cov = np.ascontiguousarray(np.atleast_2d(cov), dtype=np.float64)
+            if cov.shape[1] != self.n:
+                raise ValueError("cov must have shape (q, n)")
+            ptr, q, mem = cov.ctypes.data, cov.shape[0], IHT_HOST
+        _check(_lib().iht_set_covariates(self.h, ctypes.c_void_p(ptr), q, mem), "iht_set_covariates")
+        self.q = q
 
     def close(self):
         if getattr(self, "h", None):
@@ -257,6 +282,8 @@ def iht_default_options(**kw) -> iht_options:
     for k, v in kw.items():
         if not hasattr(o, k):
             raise AttributeError(k)
+        if k == "variant" and isinstance(v, str):
+            v = VARIANTS[v]
         setattr(o, k, v)
     return o
 
@@ -358,12 +385,13 @@ def _fit(ds: Dataset, y, k: int, rows, opts: iht_options, trace: bool, state: by
         opts.in_mem = IHT_HOST
     if rows is None and nr != ds.n:
         raise ValueError("y must have n entries when rows is None")
+    P = ds.p + ds.q                       # SNPs, then covariates
     if opts.out_mem == IHT_DEVICE:
-        beta = torch.empty(ds.p, dtype=torch.float64, device=f"cuda:{ds.ctx.device}")
+        beta = torch.empty(P, dtype=torch.float64, device=f"cuda:{ds.ctx.device}")
         supp = torch.empty(k, dtype=torch.int32, device=f"cuda:{ds.ctx.device}")
         bp, sp = beta.data_ptr(), supp.data_ptr()
     else:
-        beta = np.empty(ds.p)
+        beta = np.empty(P)
         supp = np.empty(k, dtype=np.int32)
         bp, sp = beta.ctypes.data, supp.ctypes.data
     res = iht_result()

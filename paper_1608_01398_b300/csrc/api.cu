@@ -59,7 +59,8 @@ void free_workspace(Workspace *ws)
     void *ptrs[] = {ws->used, ws->rowmask, ws->counts, ws->u64, ws->v64, ws->u32, ws->v32,
                     ws->y64, ws->r64, ws->zv, ws->rc64, ws->r32, ws->g, ws->Mj, ws->partials, ws->rows_dev,
                     ws->ybuf, ws->fbuf, ws->cand, ws->S, ws->Sp, ws->bS, ws->bSp, ws->coef,
-                    ws->cols, ws->sc};
+                    ws->cols, ws->sc, ws->cu64, ws->cv64, ws->zc, ws->gam, ws->zs, ws->gram,
+                    ws->chol, ws->hvec};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (ws->sc_host) cudaFreeHost(ws->sc_host);
@@ -98,7 +99,7 @@ int ensure_workspace(iht_dataset *ds, int)
     ALLOC(zv, sizeof(double) * np);
     ALLOC(rc64, sizeof(double) * np);
     ALLOC(r32, sizeof(float) * np);
-    ALLOC(g, sizeof(float) * p);
+    ALLOC(g, sizeof(float) * (p + kMaxCov));
     ALLOC(Mj, sizeof(float) * p);
     ALLOC(partials, sizeof(double) * 3 * kPartials);
     ALLOC(rows_dev, sizeof(int32_t) * np);
@@ -204,6 +205,8 @@ void iht_default_options(iht_options *o)
     o->out_mem = IHT_HOST;
     o->grad_impl = 0;
     o->profile = 0;
+    o->variant = IHT_VARIANT_IHT;
+    o->reserved = 0;
 }
 
 const char *iht_strerror(int s)
@@ -345,11 +348,41 @@ int iht_dataset_free(iht_dataset *ds)
     cudaStreamSynchronize(ds->ctx->stream);
     free_workspace(ds->ws);
     cudaFree(ds->G);
+    if (ds->cov) cudaFree(ds->cov);
     if (ds->miss_off) cudaFree(ds->miss_off);
     if (ds->miss_idx) cudaFree(ds->miss_idx);
     if (ds->miss_goff) cudaFree(ds->miss_goff);
     if (ds->miss_gidx) cudaFree(ds->miss_gidx);
     delete ds;
+    return IHT_OK;
+}
+
+int iht_set_covariates(iht_dataset *ds, const double *cov, int32_t q, int mem)
+{
+    if (!ds || q < 0 || q > kMaxCov || (q > 0 && !cov) || (mem != IHT_HOST && mem != IHT_DEVICE))
+        return IHT_EINVAL;
+    DeviceGuard g(ds->ctx->device);
+    if (!g.ok) return IHT_ECUDA;
+    cudaStream_t s = ds->ctx->stream;
+    IHT_CUDA(cudaStreamSynchronize(s));
+    if (ds->cov) cudaFree(ds->cov);
+    ds->cov = nullptr;
+    ds->q = 0;
+    if (q == 0) return IHT_OK;
+    double *d = nullptr;
+    IHT_CUDA(dev_malloc(&d, sizeof(double) * (size_t)q * ds->n_pad));
+    cudaError_t e = cudaMemsetAsync(d, 0, sizeof(double) * (size_t)q * ds->n_pad, s);
+    if (e == cudaSuccess)
+        e = cudaMemcpy2DAsync(d, sizeof(double) * ds->n_pad, cov, sizeof(double) * ds->n,
+                              sizeof(double) * ds->n, q, cudaMemcpyDefault, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) {
+        cudaFree(d);
+        set_cuda_error(e, "iht_set_covariates");
+        return IHT_ECUDA;
+    }
+    ds->cov = d;
+    ds->q = q;
     return IHT_OK;
 }
 
@@ -453,12 +486,15 @@ static int fit_impl(iht_dataset *ds, const int32_t *rows, int64_t n_rows, const 
         iht_default_options(&opt);
     if (!ds || !y || !beta_out || !support_out) return IHT_EINVAL;
     if (!rows) n_rows = ds->n;
-    if (n_rows < 2 || n_rows > ds->n || k < 1 || k > ds->p || k > kMaxK) return IHT_EINVAL;
+    const int64_t P = ds->p + ds->q;
+    if (n_rows < 2 || n_rows > ds->n || k < 1 || k > P || k > kMaxK) return IHT_EINVAL;
     if ((opt.in_mem != IHT_HOST && opt.in_mem != IHT_DEVICE) ||
         (opt.out_mem != IHT_HOST && opt.out_mem != IHT_DEVICE) || opt.max_iter < 0 ||
         opt.max_backtrack < 0 || !(opt.kappa > 1.0) || !(opt.c >= 0.0 && opt.c < 1.0) ||
-        !(opt.tol >= 0.0) || opt.grad_impl < 0 || opt.grad_impl > 2)
+        !(opt.tol >= 0.0) || opt.grad_impl < 0 || opt.grad_impl > 2 ||
+        (opt.variant != IHT_VARIANT_IHT && opt.variant != IHT_VARIANT_HTP))
         return IHT_EINVAL;
+    if (init && (ds->q > 0 || opt.variant != IHT_VARIANT_IHT)) return IHT_EINVAL;
     DeviceGuard g(ds->ctx->device);
     if (!g.ok) return IHT_ECUDA;
     int rc = ensure_workspace(ds, k);
@@ -474,6 +510,7 @@ static int fit_impl(iht_dataset *ds, const int32_t *rows, int64_t n_rows, const 
     }
     if ((rc = check_finite_y(ds, n_rows, y_dev))) return rc;
     if ((rc = scatter_rows_f64(ds, rows_dev, n_rows, y_dev, ws->y64))) return rc;
+    if ((rc = cov_setup(ds, n_rows))) return rc;
     rc = run_solve_host(ds, k, &opt, (int)n_rows, trace, opt.max_iter, init);
     if (rc) return rc;
     const Scalars &h = *ws->sc_host;
@@ -494,7 +531,7 @@ static int fit_impl(iht_dataset *ds, const int32_t *rows, int64_t n_rows, const 
             set_cuda_error(e, "iht_fit outputs");
             return IHT_ECUDA;
         }
-        memset(beta_out, 0, sizeof(double) * ds->p);
+        memset(beta_out, 0, sizeof(double) * P);
         for (int c = 0; c < k; ++c) beta_out[support_out[c]] = bS[c];
         free(bS);
     }

@@ -440,7 +440,8 @@ int iht_fit_batch(iht_dataset *ds, int32_t b, const iht_solve_desc *solves,
     if ((opt.in_mem != IHT_HOST && opt.in_mem != IHT_DEVICE) ||
         (opt.out_mem != IHT_HOST && opt.out_mem != IHT_DEVICE) || opt.max_iter < 0 ||
         opt.max_backtrack < 0 || !(opt.kappa > 1.0) || !(opt.c >= 0.0 && opt.c < 1.0) ||
-        !(opt.tol >= 0.0) || opt.grad_impl < 0 || opt.grad_impl > 2)
+        !(opt.tol >= 0.0) || opt.grad_impl < 0 || opt.grad_impl > 2 ||
+        opt.variant != IHT_VARIANT_IHT || ds->q > 0)
         return IHT_EINVAL;
     int kmax = 0;
     int64_t ytot = 0;
@@ -692,6 +693,7 @@ int iht_cv(iht_dataset *ds, const double *y, const int32_t *fold, int32_t q, con
     else
         iht_default_options(&opt);
     const int64_t n = ds->n, p = ds->p;
+    if (opt.variant != IHT_VARIANT_IHT || ds->q > 0) return IHT_EINVAL;
     for (int t = 0; t < nk; ++t)
         if (ks[t] < 1 || ks[t] > p || ks[t] > kMaxK) return IHT_EINVAL;
     // partitions: test rows of f, training rows = the other partitions' (label

@@ -29,6 +29,7 @@ constexpr int kMaxCand = 2 * kMaxK;    // candidate list of the projection
 constexpr int kSelBins = 2048;         // radix-select histogram bins
 constexpr int kSelCap = 4096;          // keys at or above the boundary bin the fast finish sorts
 constexpr int kPartials = 2048;        // max blocks of per-block partial sums (3 values each)
+constexpr int kMaxCov = 64;            // nongenetic covariates per dataset
 
 struct Scalars {                       // device-resident state of one solve
     double num;                        // ||g_S||^2
@@ -54,6 +55,8 @@ struct Scalars {                       // device-resident state of one solve
     int32_t fresh;                     // batched solves: beta = 0 set-up still to run
     int32_t skip1;                     // 1: no further attempt this iteration (accepted or stopped)
     int32_t skip2;                     // 1: no next gradient yet (stopped, or still rejecting)
+    int32_t htp;                       // 1: HTP (the accepted support is refitted by least squares)
+    int32_t pad_;
 };
 
 // Device descriptor of one solve of a batch (all pointers device memory).
@@ -167,6 +170,10 @@ struct iht_dataset {
     // at miss_goff[g] + (j mod 8) L_g, L_g = (miss_goff[g + 1] - miss_goff[g]) / 8
     int64_t *miss_goff = nullptr;
     uint16_t *miss_gidx = nullptr;
+    // nongenetic covariates (iht_set_covariates): q dense columns, predictors
+    // p .. p+q-1; cov[t * n_pad + i] = covariate t of subject i (0 on pad samples)
+    int64_t q = 0;
+    double *cov = nullptr;
     iht::Workspace *ws;
 };
 
@@ -183,8 +190,15 @@ struct Workspace {
     float *u32 = nullptr, *v32 = nullptr;
     double *y64 = nullptr, *r64 = nullptr, *zv = nullptr;
     double *rc64 = nullptr;                // residual of the candidate update
-    float *r32 = nullptr, *g = nullptr;
+    float *r32 = nullptr, *g = nullptr;    // g: p + kMaxCov entries (covariates after the SNPs)
     float *Mj = nullptr;                   // per-SNP sum of r over missing calls
+    // covariates over the current row set: mean, inverse SD, standardised
+    // values zc[t * n_pad + i] (0 off the used rows)
+    double *cu64 = nullptr, *cv64 = nullptr, *zc = nullptr;
+    // HTP refit scratch: Gamma, standardised support columns, Gram, Cholesky factor
+    int32_t *gam = nullptr;
+    double *zs = nullptr, *gram = nullptr, *chol = nullptr, *hvec = nullptr;
+    int htp_k = 0;                         // support size the refit scratch holds
     double *partials = nullptr;        // kPartials * 2
     int32_t *rows_dev = nullptr;       // int32[n]: host row lists copied here
     double *ybuf = nullptr;            // double[n]: host phenotypes copied here
@@ -379,6 +393,12 @@ struct SolveInit {                     // resume a solve from its state (host ar
 int run_solve_host(iht_dataset *ds, int k, const iht_options *opt, int n_rows, iht_trace *trace,
                    int max_iter, const SolveInit *init = nullptr);
 int write_beta_device(iht_dataset *ds, int k, double *beta_out);
+// htp.cu: covariates of the current row set, their gradient entries, and the
+// least-squares refit of HTP
+int cov_setup(iht_dataset *ds, int64_t n_rows);
+int launch_cov_grad(iht_dataset *ds, const float *r32, float *g, const int32_t *done);
+int htp_refit(iht_dataset *ds, int k, const int32_t *Sp, double *bSp, const int32_t *done);
+int ensure_htp_scratch(iht_dataset *ds, int k);
 // batched tails (blockIdx selects the solve; finished solves return at once)
 enum ZmulWhich { kZmulInit = 0, kZmulStep = 1, kZmulResidual = 2 };
 int launch_gather_gS_batch(iht_dataset *ds, const BSolve *bs, int nb);

@@ -297,7 +297,10 @@ __device__ __forceinline__ void sel_pick_body(const float *__restrict__ keys, in
         st->n_gt = 0;
         st->ticket_b = 0;
     }
-    if (gS) gather_gS_body(keys, gS, gk, gcoef, gsc);
+    if (gS) {
+        __syncthreads();          // gS may be the output just written (HTP's step set)
+        gather_gS_body(keys, gS, gk, gcoef, gsc);
+    }
 }
 
 __global__ void __launch_bounds__(kSelAThreads) k_sel_count(const float *__restrict__ keys, int64_t p,

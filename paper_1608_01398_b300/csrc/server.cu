@@ -477,7 +477,8 @@ int iht_server_create(iht_dataset *ds, const iht_server_options *opt_in, iht_ser
         iht_server_default_options(&opt);
     const iht_options &so = opt.solve;
     if (opt.max_slots < 1 || opt.max_slots > 1024 || so.max_iter < 0 || so.max_backtrack < 0 ||
-        !(so.kappa > 1.0) || !(so.c >= 0.0 && so.c < 1.0) || !(so.tol >= 0.0))
+        !(so.kappa > 1.0) || !(so.c >= 0.0 && so.c < 1.0) || !(so.tol >= 0.0) ||
+        so.variant != IHT_VARIANT_IHT || ds->q > 0)
         return IHT_EINVAL;
     if (!grad_mrhs_supported(ds) || zmul_blocks(ds) > kPartials) return IHT_EINVAL;
     DeviceGuard g(ds->ctx->device);

@@ -85,7 +85,8 @@ __device__ __forceinline__ void zmul_body(const uint8_t *__restrict__ G, int64_t
                                           const int32_t *__restrict__ used,
                                           const double *__restrict__ base,
                                           const double *__restrict__ prev, double *__restrict__ out,
-                                          double *__restrict__ partials, int64_t n_pad)
+                                          double *__restrict__ partials, int64_t n_pad,
+                                          int64_t psnp = 0, const double *__restrict__ zc = nullptr)
 {
     __shared__ double red[3 * (kZmulThreads / 32)];
     __shared__ double term[kZmulChunk][4];     // terms for codes 00, 01 (missing: 0), 10, 11
@@ -98,6 +99,11 @@ __device__ __forceinline__ void zmul_body(const uint8_t *__restrict__ G, int64_t
     const int32_t ui = in ? used[i] : 0;
     const double bi = in && base ? base[i] : 0.0;
     const double pi = in && prev ? prev[i] : 0.0;
+    // covariate columns (index >= psnp, with zc) sort after the SNPs of an
+    // ascending column list: the SNP loop takes the first msnp columns
+    const int mall = m;
+    if (zc)
+        while (m > 0 && cols[m - 1] >= psnp) --m;
     double acc = 0.0;
     for (int c0 = 0; c0 < m; c0 += kZmulChunk) {
         const int mc = min(kZmulChunk, m - c0);
@@ -142,6 +148,8 @@ __device__ __forceinline__ void zmul_body(const uint8_t *__restrict__ G, int64_t
             for (; c < mc; ++c) acc += term[c][((uint32_t)__ldg(srow[c] + byte) >> shift) & 3u];
         }
     }
+    if (in)
+        for (int c = m; c < mall; ++c) acc += (sign * coef[c]) * zc[(int64_t)(cols[c] - psnp) * n_pad + i];
     double o = 0.0, d = 0.0;
     if (in) {
         o = ui ? bi + acc : 0.0;
@@ -166,10 +174,12 @@ __global__ void __launch_bounds__(kZmulThreads) k_zmul(const uint8_t *__restrict
                                               const double *__restrict__ base,
                                               const double *__restrict__ prev,
                                               double *__restrict__ out, double *__restrict__ partials,
-                                              int64_t n_pad, const int32_t *__restrict__ done)
+                                              int64_t n_pad, const int32_t *__restrict__ done,
+                                              int64_t psnp, const double *__restrict__ zc)
 {
     if (done && *done) return;
-    zmul_body(G, stride, rowb, cols, m, coef, sign, u64, v64, used, base, prev, out, partials, n_pad);
+    zmul_body(G, stride, rowb, cols, m, coef, sign, u64, v64, used, base, prev, out, partials, n_pad,
+              psnp, zc);
 }
 
 static int zmul_threads(const iht_dataset *) { return kZmulThreads; }
@@ -179,13 +189,17 @@ int zmul_blocks(const iht_dataset *ds) { return ceil_div(ds->n_pad, zmul_threads
 // out = base + sign * Z[:, cols] coef (device, stream-ordered); partials get
 // zmul_blocks() triples (sum, sum of squares, sum of (out - prev)^2) when not
 // null.
+// cov: the columns may include covariates (indices p .. p+q-1, after the SNPs
+// of an ascending list), standardised over the solve's rows (workspace zc).
 int zmul_run(iht_dataset *ds, const int32_t *cols, int m, const double *coef, double sign,
              const double *u, const double *v, const int32_t *used, const double *base,
-             double *out, double *partials, const int32_t *done, const double *prev = nullptr)
+             double *out, double *partials, const int32_t *done, const double *prev = nullptr,
+             bool cov = true)
 {
+    const double *zc = cov && ds->q > 0 ? ds->ws->zc : nullptr;
     k_zmul<<<zmul_blocks(ds), zmul_threads(ds), 0, ds->ctx->stream>>>(ds->G, ds->stride, ds->rowb, cols, m, coef,
                                                          sign, u, v, used, base, prev, out, partials,
-                                                         ds->n_pad, done);
+                                                         ds->n_pad, done, ds->p, zc);
     note_launch();
     IHT_CUDA(cudaGetLastError());
     return IHT_OK;
@@ -195,7 +209,7 @@ int launch_zmul(iht_dataset *ds, const int32_t *cols, int32_t m, const double *c
                 const double *u, const double *v, const int32_t *used, const double *base,
                 double *out, double *partials)
 {
-    return zmul_run(ds, cols, m, coef, 1.0, u, v, used, base, out, partials, nullptr);
+    return zmul_run(ds, cols, m, coef, 1.0, u, v, used, base, out, partials, nullptr, nullptr, false);
 }
 
 // ---------------------------------------------------------------------------
@@ -507,7 +521,17 @@ __device__ __forceinline__ void decide_body(Scalars *sc, const double *partials,
             }
         }
         sc->retry = accept ? 0 : 1;
-        if (accept) {
+        if (accept && sc->htp) {
+            // HTP: the step is accepted; the refit on S+ and its residual give the
+            // objective and the stopping test (k_htp_finish)
+            const int it = sc->iter;
+            sc->bt_total += sc->bt_last;
+            if (tr.mu) tr.mu[it] = sc->mu;
+            if (tr.backtracks) tr.backtracks[it] = sc->bt_last;
+            if (tr.changed) tr.changed[it] = sc->changed;
+            sc->skip1 = 1;
+            sc->skip2 = 1;
+        } else if (accept) {
             const int it = sc->iter;
             sc->bt_total += sc->bt_last;
             sc->sum_r = s;
@@ -528,6 +552,7 @@ __device__ __forceinline__ void decide_body(Scalars *sc, const double *partials,
         }
         return;
     }
+    if (sc->htp) return;
     const int it = sc->iter;
     for (int c = threadIdx.x; c < k; c += blockDim.x) {
         S[c] = Sp[c];
@@ -556,6 +581,67 @@ __global__ void __launch_bounds__(256) k_decide(Scalars *sc, const double *parti
 {
     if (sc->done || (skip && *skip)) return;
     decide_body(sc, partials, npart, S, bS, Sp, bSp, tr);
+}
+
+// HTP: after the refit beta+ on S+ (bSp) and its residual (partials: sum r+,
+// sum r+^2): objective, the stopping test against beta on S, state copy, trace.
+// One block; thread 0 walks S and S+ (both ascending) in order.
+__global__ void __launch_bounds__(256) k_htp_finish(Scalars *sc, const double *partials, int npart,
+                                                    int32_t *S, double *bS, const int32_t *Sp,
+                                                    const double *bSp, TraceDev tr)
+{
+    if (sc->done) return;
+    const int k = sc->k;
+    double s = 0.0, s2 = 0.0, d2 = 0.0;
+    if (threadIdx.x < 32) warp_partials(partials, npart, s, s2, d2);
+    if (threadIdx.x == 0) {
+        double dd = 0.0, bb = 0.0;
+        int a = 0, b = 0;
+        while (a < k || b < k) {
+            const int32_t ja = a < k ? S[a] : 0x7fffffff, jb = b < k ? Sp[b] : 0x7fffffff;
+            double d;
+            if (ja == jb) {
+                d = bSp[b] - bS[a];
+                bb += bS[a] * bS[a];
+                ++a;
+                ++b;
+            } else if (ja < jb) {
+                d = -bS[a];
+                bb += bS[a] * bS[a];
+                ++a;
+            } else {
+                d = bSp[b];
+                ++b;
+            }
+            dd += d * d;
+        }
+        sc->sum_r = s;
+        sc->sumsq_r = s2;
+        sc->f = 0.5 * s2;
+        sc->dd = dd;
+        sc->bb = bb;
+        sc->step = sqrt(dd) / (sqrt(bb) + 1.0);
+        if (tr.objective) tr.objective[sc->iter] = sc->f;
+    }
+    __syncthreads();
+    const int it = sc->iter;
+    for (int c = threadIdx.x; c < k; c += blockDim.x) {
+        S[c] = Sp[c];
+        bS[c] = bSp[c];
+        if (tr.supp) tr.supp[(size_t)it * k + c] = Sp[c];
+        if (tr.beta) tr.beta[(size_t)it * k + c] = bSp[c];
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        sc->iter = it + 1;
+        if (sc->step < sc->tol) {
+            sc->status = IHT_OK;
+            sc->done = 1;
+        } else if (sc->iter >= sc->max_iter) {
+            sc->status = IHT_ENOTCONV;
+            sc->done = 1;
+        }
+    }
 }
 
 // Objective of beta = 0 (r = y) before the first iteration (one thread).
@@ -660,7 +746,7 @@ static int launch_grad_ev(iht_dataset *ds, int impl, const int32_t *done, cudaEv
     rc = tc ? launch_grad_tc_main(ds, ws->r32, ws->g, done) : launch_grad_simt(ds, ws->r32, ws->g, done);
     if (rc) return rc;
     if (e1) IHT_CUDA(cudaEventRecordWithFlags(e1, s, flags));
-    return IHT_OK;
+    return launch_cov_grad(ds, ws->r32, ws->g, done);       // covariate entries p .. p+q-1
 }
 
 int launch_grad(iht_dataset *ds, int impl, const int32_t *done, bool profile)
@@ -707,7 +793,7 @@ static int enqueue_iteration(iht_dataset *ds, int k, int K, int impl, cudaEvent_
     const int32_t *done = &ws->sc->done;
     int rc;
     // candidates, and g_S with ||g_S||^2 in the same launch's last block
-    if ((rc = select_topk(ds->ctx, ws->g, ds->p, K, ws->cand, done, ws->S, k, ws->coef, ws->sc)))
+    if ((rc = select_topk(ds->ctx, ws->g, ds->p + ds->q, K, ws->cand, done, ws->S, k, ws->coef, ws->sc)))
         return rc;
     if ((rc = zmul_run(ds, ws->S, k, ws->coef, 1.0, ws->u64, ws->v64, ws->used, nullptr, ws->zv,
                        ws->partials, done)))
@@ -724,8 +810,8 @@ static int enqueue_iteration(iht_dataset *ds, int k, int K, int impl, cudaEvent_
 static int iteration_graph(iht_dataset *ds, int k, int K, int impl, bool prof, cudaGraphExec_t *exec)
 {
     Workspace *ws = ds->ws;
-    const uint64_t key[8] = {(uint64_t)k, (uint64_t)K, (uint64_t)impl, (uint64_t)prof,
-                             (uint64_t)(uintptr_t)ws->S, (uint64_t)(uintptr_t)ws->cand,
+    const uint64_t key[8] = {(uint64_t)k | ((uint64_t)ds->q << 32), (uint64_t)K, (uint64_t)impl,
+                             (uint64_t)prof, (uint64_t)(uintptr_t)ws->S, (uint64_t)(uintptr_t)ws->cand,
                              grad_tc_scratch_id(), (uint64_t)(uintptr_t)ds->ctx->sel.cand};
     if (ws->iter_exec && std::equal(key, key + 8, ws->iter_key)) {
         *exec = ws->iter_exec;
@@ -778,10 +864,13 @@ int run_solve(iht_dataset *ds, int k, const iht_options *opt, int n_rows, const 
     Workspace *ws = ds->ws;
     cudaStream_t s = ds->ctx->stream;
     const int npart = zmul_blocks(ds);
-    const int K = (int)std::min<int64_t>(2 * (int64_t)k, ds->p);
+    const int64_t P = ds->p + ds->q;                  // SNPs, then covariates
+    const int K = (int)std::min<int64_t>(2 * (int64_t)k, P);
+    const bool htp = opt->variant == IHT_VARIANT_HTP;
     int rc;
 
     Scalars h{};
+    h.htp = htp ? 1 : 0;
     h.c = opt->c;
     h.kappa = opt->kappa;
     h.tol = opt->tol;
@@ -826,7 +915,7 @@ int run_solve(iht_dataset *ds, int k, const iht_options *opt, int n_rows, const 
     }
     if ((rc = launch_grad(ds, opt->grad_impl, done, prof))) return rc;
     if (!init) {
-        if ((rc = select_topk(ds->ctx, ws->g, ds->p, k, ws->S, done))) return rc;
+        if ((rc = select_topk(ds->ctx, ws->g, P, k, ws->S, done))) return rc;
         IHT_CUDA(cudaMemsetAsync(ws->bS, 0, sizeof(double) * k, s));
     }
 
@@ -834,7 +923,44 @@ int run_solve(iht_dataset *ds, int k, const iht_options *opt, int n_rows, const 
     ws->graph_replays = 0;
     double graph_ms = 0.0;
     int graph_n = 0;
-    if (!traced) {
+    if (htp) {
+        // HTP (Sec. 2.2), one host synchronisation per attempt: step over Gamma =
+        // the k largest |g| with g_Gamma and ||g_Gamma||^2 from the selection's last
+        // block, candidates, attempts on the projected candidate, then the
+        // least-squares refit on S+, its residual, the stopping test and centring.
+        if ((rc = ensure_htp_scratch(ds, k))) return rc;
+        for (int it = 0; it < opt->max_iter; ++it) {
+            if (it > 0 && (rc = launch_grad(ds, opt->grad_impl, done, prof))) return rc;
+            if ((rc = select_topk(ds->ctx, ws->g, P, k, ws->gam, done, ws->gam, k, ws->coef, ws->sc)))
+                return rc;
+            if ((rc = zmul_run(ds, ws->gam, k, ws->coef, 1.0, ws->u64, ws->v64, ws->used, nullptr,
+                               ws->zv, ws->partials, done)))
+                return rc;
+            if ((rc = select_topk(ds->ctx, ws->g, P, K, ws->cand, done))) return rc;
+            for (int attempt = 0;; ++attempt) {
+                if ((rc = enqueue_attempt(ds, k, K, attempt == 0, nullptr, tr))) return rc;
+                IHT_CUDA(cudaMemcpyAsync(&ws->sc_host->done, &ws->sc->done, 2 * sizeof(int32_t),
+                                         cudaMemcpyDeviceToHost, s));
+                IHT_CUDA(cudaStreamSynchronize(s));
+                if (ws->sc_host->done || !ws->sc_host->retry) break;
+            }
+            if (ws->sc_host->done) break;
+            if ((rc = htp_refit(ds, k, ws->Sp, ws->bSp, done))) return rc;
+            if ((rc = zmul_run(ds, ws->Sp, k, ws->bSp, -1.0, ws->u64, ws->v64, ws->used, ws->y64,
+                               ws->rc64, ws->partials, done)))
+                return rc;
+            k_htp_finish<<<1, 256, 0, s>>>(ws->sc, ws->partials, npart, ws->S, ws->bS, ws->Sp, ws->bSp, tr);
+            k_center<<<ceil_div(ds->n_pad, 256), 256, 0, s>>>(ws->rc64, ws->r64, ws->used, ds->n_pad,
+                                                              ws->sc, ws->r32);
+            note_launch(2);
+            IHT_CUDA(cudaGetLastError());
+            IHT_CUDA(cudaMemcpyAsync(&ws->sc_host->done, &ws->sc->done, sizeof(int32_t),
+                                     cudaMemcpyDeviceToHost, s));
+            IHT_CUDA(cudaStreamSynchronize(s));
+            if (ws->sc_host->done) break;
+        }
+    }
+    if (!traced && !htp) {
         // one graph replay and one host synchronisation per iteration
         cudaGraphExec_t exec = nullptr;
         if ((rc = iteration_graph(ds, k, K, opt->grad_impl, prof, &exec))) return rc;
@@ -866,9 +992,9 @@ int run_solve(iht_dataset *ds, int k, const iht_options *opt, int n_rows, const 
             if (dn) break;
         }
     }
-    for (int it = 0; traced && it < opt->max_iter; ++it) {
+    for (int it = 0; traced && !htp && it < opt->max_iter; ++it) {
         if (it > 0 && (rc = launch_grad(ds, opt->grad_impl, done, prof))) return rc;
-        if ((rc = select_topk(ds->ctx, ws->g, ds->p, K, ws->cand, done))) return rc;
+        if ((rc = select_topk(ds->ctx, ws->g, P, K, ws->cand, done))) return rc;
         k_gather_gS<<<1, 1024, 0, s>>>(ws->g, ws->S, k, ws->coef, ws->sc);
         note_launch();
         if ((rc = zmul_run(ds, ws->S, k, ws->coef, 1.0, ws->u64, ws->v64, ws->used, nullptr, ws->zv,
@@ -984,7 +1110,7 @@ __global__ void k_scatter_beta(const int32_t *__restrict__ S, const double *__re
 int write_beta_device(iht_dataset *ds, int k, double *beta_out)
 {
     cudaStream_t s = ds->ctx->stream;
-    IHT_CUDA(cudaMemsetAsync(beta_out, 0, sizeof(double) * ds->p, s));
+    IHT_CUDA(cudaMemsetAsync(beta_out, 0, sizeof(double) * (ds->p + ds->q), s));
     k_scatter_beta<<<ceil_div(k, 256), 256, 0, s>>>(ds->ws->S, ds->ws->bS, k, beta_out);
     note_launch();
     IHT_CUDA(cudaGetLastError());
