@@ -1241,7 +1241,10 @@ void grad_mrhs_release_thread()
 int grad_mrhs_status(iht_dataset *ds, int *timed_out)
 {
     *timed_out = 0;
-    if (!g_mr.err) return IHT_OK;
+    if (!g_mr.err) {                     // no multi-column pass yet: nothing to read
+        IHT_CUDA(cudaStreamSynchronize(ds->ctx->stream));
+        return IHT_OK;
+    }
     if (fault_take(IHT_FAULT_TIMEOUT))
         IHT_CUDA(cudaMemsetAsync(g_mr.err, 0x01, sizeof(int), ds->ctx->stream));
     int h = 0;

@@ -789,7 +789,10 @@ int launch_grad_tc(iht_dataset *ds, const float *r32, float *g, const int32_t *d
 int grad_tc_status(iht_dataset *ds, int *timed_out)
 {
     *timed_out = 0;
-    if (!g_tc.prm) return IHT_OK;
+    if (!g_tc.prm) {                     // no tensor-core pass yet: nothing to read
+        IHT_CUDA(cudaStreamSynchronize(ds->ctx->stream));
+        return IHT_OK;
+    }
     if (fault_take(IHT_FAULT_TIMEOUT))
         IHT_CUDA(cudaMemsetAsync(&g_tc.prm->err, 0x01, sizeof(int), ds->ctx->stream));
     TcParams h;
