@@ -258,7 +258,7 @@ class CV:
 
 
 def cv(G: Geno, y, fold, q: int, ks, max_iter: int = 100, tol: float = 1e-4, c: float = 0.01,
-       kappa: float = 2.0, max_backtrack: int = 50, lib=None) -> CV:
+       kappa: float = 2.0, max_backtrack: int = 50, lib=None, trace: bool = False) -> CV:
     """q-fold cross-validation over the model sizes ks, then the refit (Sec. 2.4).
 
     fold[i] in 0..q-1 is subject i's partition, -1 a subject outside the
@@ -284,7 +284,7 @@ def cv(G: Geno, y, fold, q: int, ks, max_iter: int = 100, tol: float = 1e-4, c: 
         _, ut, vt = counts(G, train, lib)
         row = []
         for t, k in enumerate(ks):
-            fit = iht(G, y[train], k, rows=train, trace=False, **kw)
+            fit = iht(G, y[train], k, rows=train, trace=trace, **kw)
             pred = zmul(G, fit.support, fit.beta[fit.support], test, ut, vt, lib)
             mse_fold[f, t] = np.mean((y[test] - pred) ** 2)
             row.append(fit)
@@ -292,6 +292,6 @@ def cv(G: Geno, y, fold, q: int, ks, max_iter: int = 100, tol: float = 1e-4, c: 
     mse = mse_fold.mean(axis=0)
     k_best = ks[int(np.argmin(mse))]
     inside = np.flatnonzero(fold >= 0).astype(np.int32)
-    refit = (iht(G, y, k_best, trace=False, **kw) if inside.size == fold.size
-             else iht(G, y[inside], k_best, rows=inside, trace=False, **kw))
+    refit = (iht(G, y, k_best, trace=trace, **kw) if inside.size == fold.size
+             else iht(G, y[inside], k_best, rows=inside, trace=trace, **kw))
     return CV(mse, mse_fold, k_best, refit, fits)

@@ -154,7 +154,9 @@ def test_fit_batch_cv_against_oracle(iht, ctx, impl):
             cols = np.flatnonzero(beta).astype(np.int32)
             pred = oracle.zmul(G, cols, beta[cols], test[f], ut, vt) if cols.size else 0.0
             acc[ks.index(k)] += np.mean((y[test[f]] - pred) ** 2) / folds
-    assert ncert >= 0.8 * len(probs)
+    print(f"[parity] CV batch: {ncert} of {len(probs)} certified, tie-ambiguous "
+          f"exclusion {1 - ncert / len(probs):.3f}")
+    assert ncert == len(probs)                         # every solve certified: all must match
     assert np.max(np.abs(mse_g - mse_o) / mse_o) <= BTOL
     assert ks[int(np.argmin(mse_g))] == ks[int(np.argmin(mse_o))]
 
@@ -175,7 +177,8 @@ def test_fit_batch_mixed_sizes_and_sets(iht, ctx):
         fo = oracle.iht(G, yy, k, rows=rows)
         ncert += check_solve(fo, fg)
         assert np.count_nonzero(fg.beta) <= k and len(fg.support) == k
-    assert ncert >= 4
+    print(f"[parity] mixed batch: {ncert} of {len(probs)} certified")
+    assert ncert == len(probs)
 
 
 def test_fit_batch_status_and_io(iht, ctx):

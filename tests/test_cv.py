@@ -130,3 +130,50 @@ def test_cv_edge_cases(ctx):
     bad[4] = np.nan
     with pytest.raises(iht.IhtError):
         iht.iht_cv(ds, bad, fold, [1, 2])
+
+
+@pytest.mark.gpu
+def test_cv_at_the_simulation_replay_shape(ctx):
+    """The Sec. 3.1 replay shape: n = 5289, p = 23 695 (Beta(0.5, 2) allele
+    frequencies, 1 % missing), 289 subjects held out (label -1), 5-fold CV on
+    the other 5000 over model sizes around the 100-350 of the paper's paths,
+    k_true = 200 at SNR 100 %.  Every fold fit the oracle certifies gives the
+    oracle's out-of-fold MSE within 1e-4 (11 of the 15 are certified here; the
+    other four have a k-th and (k+1)-th |w| closer than the FP32 gradient error
+    and are reported as excluded, held only to a sanity bound), the chosen size
+    agrees (the curve's minimum is well separated), and the refit is iht_fit on
+    the labelled rows."""
+    c = synth.CONFIGS[6]
+    pn = synth.config_panel(6)
+    bed = pn.bed()
+    G = oracle.Geno.from_bed(bed, pn.n, pn.p)
+    ds = iht.Dataset(ctx, bed, pn.n, pn.p)
+    y, causal, beta = synth.phenotype(pn, 200, c["effect_var"], c["noise_var"],
+                                      synth.BASE_SEED + 6000 + 17)
+    split = np.random.Generator(np.random.PCG64(synth.BASE_SEED + 6000 + 101))
+    test = np.sort(split.choice(pn.n, size=c["test"], replace=False)).astype(np.int32)
+    train = np.setdiff1d(np.arange(pn.n), test).astype(np.int32)
+    fold = np.full(pn.n, -1, np.int32)
+    fold[train] = synth.cv_folds(train.size, c["folds"], synth.BASE_SEED + 6007)
+    ks = (100, 200, 350)
+    res = iht.iht_cv(ds, y, fold, ks, tol=c["tol"], max_iter=c["max_iter"])
+    ref = oracle.cv(G, y, fold, c["folds"], ks, tol=c["tol"], max_iter=c["max_iter"], trace=True)
+    cert = np.array([[_certified(ref.fits[f][t]) for t in range(len(ks))] for f in range(c["folds"])])
+    print(f"[parity] replay-shape CV: {int(cert.sum())} of {cert.size} fold fits certified, "
+          f"tie-ambiguous exclusion {1 - cert.mean():.3f}")
+    assert int(cert.sum()) == 11
+    rel = np.abs(res.mse_fold - ref.mse_fold) / ref.mse_fold
+    print(f"[parity] certified fold MSE max rel err {np.max(rel[cert]):.2e}, "
+          f"excluded {np.max(rel[~cert]):.2e}")
+    assert np.max(rel[cert]) <= BTOL
+    assert np.max(rel[~cert]) <= 0.05
+    order = np.sort(ref.mse)
+    assert order[1] > 1.1 * order[0]                   # a well separated minimum
+    assert res.k_best == ref.k_best
+    if _certified(ref.fit):
+        assert np.array_equal(np.asarray(res.fit.support), ref.fit.support)
+        assert res.fit.iterations == ref.fit.iterations
+        assert np.max(np.abs(res.fit.beta - ref.fit.beta)) <= BTOL * np.max(np.abs(ref.fit.beta))
+    inside = np.flatnonzero(fold >= 0).astype(np.int32)
+    alone = iht.iht_fit(ds, y[inside], res.k_best, rows=inside, tol=c["tol"])
+    assert np.array_equal(alone.beta, res.fit.beta)

@@ -105,7 +105,9 @@ def test_served_results_match_oracle_and_alone(iht, panel):
             assert a.iterations == fo.iterations and a.status == fo.status
             assert np.array_equal(a.support, fo.support)
             assert rel_err(a.beta_s, fo.beta[fo.support]) <= BTOL
-    assert ncert >= len(reqs) // 2
+    print(f"[parity] served requests: {ncert} of {len(reqs)} certified, tie-ambiguous "
+          f"exclusion {1 - ncert / len(reqs):.3f}")
+    assert ncert == len(reqs)                          # the oracle certifies every request here
 
 
 def test_served_equals_batched_and_single(iht, panel):
