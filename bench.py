@@ -898,6 +898,17 @@ def serve_arm(args):
     return 0
 
 
+def replay_metrics(support, causal, signal, y):
+    """Sec. 3.1 diagnostics of one replicate: precision = |S n C| / |S| and recall
+    = |S n C| / |C| of the refit's support S against the causal set C, and
+    h^2 = sample variance of the noise-free signal X beta_true / sample variance
+    of y (the paper's approximation of narrow-sense heritability)."""
+    s = set(int(j) for j in np.asarray(support).ravel())
+    c = set(int(j) for j in causal)
+    hit = len(s & c)
+    return hit / max(len(s), 1), hit / max(len(c), 1), float(np.var(signal) / np.var(y))
+
+
 def sim_arm(args):
     """Replay of the Sec. 3.1 simulation (synthetic stand-in for its chromosome-1
     matrix): per replicate, a phenotype with k_true causal SNPs at one SNR, 5-fold
@@ -937,7 +948,7 @@ def sim_arm(args):
             seed = synth.BASE_SEED + 1000 * cfg + 100000 * rank + 1000 * ci + r
             y, causal, beta = synth.phenotype(pn, kt, c["effect_var"] / s, c["noise_var"], seed)
             sig = synth.signal(pn, causal, beta)
-            jobs.append((ci, kt, s, y, set(causal.tolist()), float(np.var(sig) / np.var(y))))
+            jobs.append((ci, kt, s, y, causal, sig))
     kw = dict(tol=c["tol"], max_iter=c["max_iter"], grad_impl=args.grad_impl)
     for _ in range(max(args.warmup, 0)):                       # tuning, graphs, allocations
         iht.iht_cv(ds, jobs[0][3], lab, synth.sim_path(jobs[0][1], c["path"], c["path_step"]), **kw)
@@ -953,14 +964,14 @@ def sim_arm(args):
     w0 = time.perf_counter()
     for _ in range(args.steps):
         rows = []
-        for ci, kt, s, y, causal, h2 in jobs:
+        for ci, kt, s, y, causal, sig in jobs:
             sel = iht.iht_cv(ds, y, lab, synth.sim_path(kt, c["path"], c["path_step"]), **kw)
             supp = np.asarray(sel.fit.support)
             sb = torch.from_numpy(np.ascontiguousarray(sel.fit.beta[supp])).to(cuda)
             pred = iht.iht_zmul(ds, torch.from_numpy(supp.astype(np.int32)).to(cuda), sb, rows=test_d,
                                 u=u_d, v=v_d).cpu().numpy()
-            hit = len(causal.intersection(supp.tolist()))
-            rows.append((ci, sel.k_best, hit / sel.k_best, hit / kt, float(np.mean((y[test] - pred) ** 2)), h2))
+            prec, rec, h2 = replay_metrics(supp, causal, sig, y)
+            rows.append((ci, sel.k_best, prec, rec, float(np.mean((y[test] - pred) ** 2)), h2))
     torch.cuda.synchronize(dev)
     wall = time.perf_counter() - w0
     launches = iht.iht_kernel_launches() - l0

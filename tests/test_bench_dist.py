@@ -76,3 +76,14 @@ def test_replicas_draw_their_own_inputs():
     y0, c0, _ = synth.config_phenotype(2, pn, which=0)
     y1, c1, _ = synth.config_phenotype(2, pn, which=1)
     assert not np.array_equal(c0, c1) and not np.allclose(y0, y1)
+
+
+def test_replay_metrics_hand_example():
+    """Sec. 3.1 diagnostics on a worked example: support {1,2,3,4} against causal
+    {2,4,9}: precision 2/4, recall 2/3; h^2 = var(signal) / var(y) with
+    signal (1,2,3) and y (2,4,6): (2/3) / (8/3) = 1/4."""
+    import bench
+    prec, rec, h2 = bench.replay_metrics(np.array([1, 2, 3, 4]), [2, 4, 9],
+                                         np.array([1.0, 2.0, 3.0]), np.array([2.0, 4.0, 6.0]))
+    assert prec == 0.5 and rec == 2 / 3 and abs(h2 - 0.25) < 1e-15
+    assert bench.replay_metrics([5], [5], np.ones(3) * 2, np.array([1.0, 2.0, 4.0]))[:2] == (1.0, 1.0)
