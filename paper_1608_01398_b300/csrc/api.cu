@@ -70,6 +70,7 @@ void free_workspace(Workspace *ws)
     for (cudaEvent_t e : ws->gev)
         if (e) cudaEventDestroy(e);
     if (ws->iter_exec) cudaGraphExecDestroy(ws->iter_exec);
+    free_fused(ws);
     if (ws->cap_stream) cudaStreamDestroy(ws->cap_stream);
     delete ws;
 }

@@ -111,6 +111,8 @@ struct SelState {                      // top-K selection progress (zero between
 
 // Host-side handles -------------------------------------------------------
 struct Workspace;
+struct TailWork;                       // fused per-iteration kernel's scratch (tail.cu)
+struct TcParams;                       // limb scale, residual sum, error word (limbs.cuh)
 struct BatchWork;
 void free_batchwork(BatchWork *w);
 
@@ -223,6 +225,12 @@ struct Workspace {
     cudaEvent_t gev[2] = {};               // around the gradient pass inside the graph
     int graph_replays = 0;                 // iterations of the last solve run as replays
     BatchWork *bw = nullptr;               // batched solves (batch.cu)
+    // a whole solve as one graph: a conditional while loop over the fused
+    // per-iteration kernel and the gradient pass (tail.cu)
+    TailWork *tail = nullptr;
+    cudaGraphExec_t fused_exec = nullptr;
+    uint64_t fused_key[10] = {};
+    int fused_launches = 0;                // kernels per loop trip
 };
 constexpr int kProfEvents = 256;
 
@@ -296,6 +304,7 @@ void grad_tc_release_thread();
 uint64_t grad_tc_scratch_id();
 int grad_tc_status(iht_dataset *ds, int *timed_out);
 int grad_tc_reset_status(iht_dataset *ds);
+int grad_tc_limb_buffers(iht_dataset *ds, uint8_t **bimg, TcParams **prm, int64_t *nlim);
 // impl: 0 default (tensor cores when supported), 1 CUDA cores, 2 tensor cores
 int launch_grad_impl(iht_dataset *ds, int impl, const float *r32, float *g, const int32_t *done);
 int launch_grad_simt_stats(iht_dataset *ds, const float *r32, const float *u32, const float *v32,
@@ -393,6 +402,12 @@ struct SolveInit {                     // resume a solve from its state (host ar
 int run_solve_host(iht_dataset *ds, int k, const iht_options *opt, int n_rows, iht_trace *trace,
                    int max_iter, const SolveInit *init = nullptr);
 int write_beta_device(iht_dataset *ds, int k, double *beta_out);
+// tail.cu: the rest of a solve after its first gradient pass as one graph
+// launch (no host synchronisation per iteration); false when the shape is not
+// supported (then the per-iteration graph runs)
+bool fused_supported(const iht_dataset *ds, int k, int impl);
+int run_fused_solve(iht_dataset *ds, int k, int K, int impl);
+void free_fused(Workspace *ws);
 // htp.cu: covariates of the current row set, their gradient entries, and the
 // least-squares refit of HTP
 int cov_setup(iht_dataset *ds, int64_t n_rows);

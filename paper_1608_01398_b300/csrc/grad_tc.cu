@@ -49,11 +49,10 @@
 #include <cuda.h>
 #include <cuda_fp8.h>
 
-#include "common.cuh"
+#include "limbs.cuh"
 
 namespace iht {
 
-constexpr int kTcLimbs = 5;
 constexpr int kTcN = 16;
 constexpr int kTcStepSamples = 32;                 // K of one MMA (bytes of FP8)
 constexpr int kTcGroupBytes = 16;                  // packed bytes per chunk = 2 K-steps
@@ -68,32 +67,12 @@ constexpr int kTcStageTile = 128 * kTcStageBytes;  // 8 KB
 
 constexpr uint32_t kTcSpin = 1u << 24;             // bounded waits (each poll may suspend up to 128 ns)
 
-struct TcParams {
-    float s0;        // scale of limb 0 (limb l: s0 * 2^-4l)
-    float R;         // sum of the residual over the samples
-    int err;         // 1: a bounded wait timed out
-    int pad;
-};
 
 __device__ __forceinline__ uint32_t smem_addr(const void *p)
 {
     return (uint32_t)__cvta_generic_to_shared(p);
 }
 
-// ---------------------------------------------------------------------------
-// Residual -> E4M3 limbs in the B image (permuted K order, canonical layout):
-// [256 unused bytes][K-step 0 (256 bytes)]...[K-step S-1][256 zero bytes].
-
-__device__ __forceinline__ int b_offset(int64_t i, int limb)
-{
-    const int64_t s = i >> 5;                       // K-step
-    const int ii = (int)(i & 31);
-    const int wi = ii >> 4, q = ii & 15;            // 16-sample word, position in it
-    const int k = q >> 2, j = q & 3;                // output byte k of decoded word j
-    const int c = 4 * wi + j;                       // TMEM column within the step
-    const int kpos = 4 * c + k;                     // K index within the step
-    return 256 + (int)(s * 256) + (kpos >> 4) * 128 + limb * 16 + (kpos & 15);
-}
 
 __global__ void __launch_bounds__(1024) k_limbs(const float *__restrict__ r32, int64_t n_pad,
                                                 uint8_t *__restrict__ bimg, TcParams *prm,
@@ -116,25 +95,12 @@ __global__ void __launch_bounds__(1024) k_limbs(const float *__restrict__ r32, i
     }
     __syncthreads();
     m = smax[0];
-    float s0 = 1.0f;
-    if (m > 0.0f) {
-        int e;
-        frexpf(m / 448.0f, &e);          // m/448 <= 2^e
-        s0 = ldexpf(1.0f, e);
-    }
+    const float s0 = limb_scale(m);
     double acc = 0.0;
     for (int64_t i = threadIdx.x; i < n_pad; i += blockDim.x) {
-        float res = r32[i];
-        float s = s0;
+        const float res = r32[i];
         acc += (double)res;
-#pragma unroll
-        for (int l = 0; l < kTcLimbs; ++l) {
-            const __nv_fp8_e4m3 q(res / s);
-            const float qf = (float)q;
-            bimg[b_offset(i, l)] = q.__x;
-            res -= s * qf;
-            s *= 0.0625f;
-        }
+        limb_encode(res, s0, bimg, i);
     }
     // the trailing zero group may hold limbs of an earlier, longer residual
     for (int64_t b = threadIdx.x; b < 256; b += blockDim.x) bimg[256 + 256 * (n_pad >> 5) + b] = 0;
@@ -618,13 +584,10 @@ static int make_gmap(const iht_dataset *ds, CUtensorMap *map)
     return r == CUDA_SUCCESS ? IHT_OK : IHT_ECUDA;
 }
 
-// Residual -> limb image (and its scale and sum) for the next tensor-core pass,
-// and the missing-call sums of r into Mj (p floats).
-int prepare_grad_tc_to(iht_dataset *ds, const float *r32, float *Mj, const int32_t *done)
+// The calling thread's limb image and parameter block, sized for this dataset.
+static int tc_ensure(iht_dataset *ds)
 {
-    if (!grad_tc_supported(ds)) return IHT_EINVAL;
     cudaStream_t s = ds->ctx->stream;
-    const int ksteps = 2 * tc_ngroups(ds);
     const size_t bbytes = tc_bbytes(ds);
     TcWork &w = g_tc;
     if (w.dev != ds->ctx->device || w.bbytes < bbytes) {
@@ -652,6 +615,28 @@ int prepare_grad_tc_to(iht_dataset *ds, const float *r32, float *Mj, const int32
         w.bbytes = bbytes;
         w.dev = ds->ctx->device;
     }
+    return IHT_OK;
+}
+
+int grad_tc_limb_buffers(iht_dataset *ds, uint8_t **bimg, TcParams **prm, int64_t *nlim)
+{
+    if (!grad_tc_supported(ds)) return IHT_EINVAL;
+    if (int rc = tc_ensure(ds)) return rc;
+    *bimg = g_tc.bimg;
+    *prm = g_tc.prm;
+    *nlim = (int64_t)2 * tc_ngroups(ds) * kTcStepSamples;
+    return IHT_OK;
+}
+
+// Residual -> limb image (and its scale and sum) for the next tensor-core pass,
+// and the missing-call sums of r into Mj (p floats).
+int prepare_grad_tc_to(iht_dataset *ds, const float *r32, float *Mj, const int32_t *done)
+{
+    if (!grad_tc_supported(ds)) return IHT_EINVAL;
+    cudaStream_t s = ds->ctx->stream;
+    const int ksteps = 2 * tc_ngroups(ds);
+    if (int rc = tc_ensure(ds)) return rc;
+    TcWork &w = g_tc;
     // The limb kernel (one block) and the missing-call sums read the same
     // residual and nothing of each other: the sums run on a side stream forked
     // from and joined back to the caller's (two branches of a captured graph).

@@ -20,94 +20,9 @@
 // it); its bit pattern orders above +Inf, so NaN keys are selected first.
 #include <mutex>
 
-#include "common.cuh"
+#include "select_bodies.cuh"
 
 namespace iht {
-
-__device__ __forceinline__ uint32_t sel_key(float x) { return __float_as_uint(x) & 0x7fffffffu; }
-
-constexpr int kSelAThreads = 256;
-constexpr int kSelBThreads = 512;
-constexpr int kSelKeysPerBlock = 4096;     // keys per block of A and B (fewer blocks: fewer atomics)
-
-// Exclusive scan of x over the block (blockDim.x <= 1024); wsum: 32 words.
-__device__ __forceinline__ uint32_t sel_excl_scan(uint32_t x, uint32_t *wsum, uint32_t *total = nullptr)
-{
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    uint32_t t = x;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const uint32_t v = __shfl_up_sync(0xffffffffu, t, o);
-        if (lane >= o) t += v;
-    }
-    if (lane == 31) wsum[wid] = t;
-    __syncthreads();
-    if (wid == 0) {
-        uint32_t q = lane < nw ? wsum[lane] : 0u;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const uint32_t v = __shfl_up_sync(0xffffffffu, q, o);
-            if (lane >= o) q += v;
-        }
-        wsum[lane] = q;
-    }
-    __syncthreads();
-    const uint32_t r = t - x + (wid ? wsum[wid - 1] : 0u);
-    if (total) *total = wsum[nw - 1];
-    __syncthreads();
-    return r;
-}
-
-// Bins h[0..nbins) (shared) scanned from the top: res = {bin, keys above it,
-// keys in it} for the bin where the running count reaches need.
-__device__ __forceinline__ void sel_find(const uint32_t *h, int nbins, uint32_t need, uint32_t *wsum,
-                                         uint32_t *res)
-{
-    const int per = nbins / (int)blockDim.x;
-    const int t = threadIdx.x;
-    if (t == 0) res[0] = res[1] = res[2] = 0;
-    uint32_t tot = 0;
-    for (int i = 0; i < per; ++i) tot += h[nbins - 1 - (per * t + i)];
-    uint32_t before = sel_excl_scan(tot, wsum);
-    for (int i = 0; i < per; ++i) {
-        const int bin = nbins - 1 - (per * t + i);
-        const uint32_t c = h[bin];
-        if (before < need && before + c >= need) {
-            res[0] = (uint32_t)bin;
-            res[1] = before;
-            res[2] = c;
-        }
-        before += c;
-    }
-    __syncthreads();
-}
-
-// Calls f(key, index) for every key; 16-byte loads, two in flight per thread,
-// over the 16-byte aligned middle, the (at most 3 + 3) keys around it one at a
-// time.
-template <typename F>
-__device__ __forceinline__ void sel_each(const float *__restrict__ keys, int64_t p, F &&f)
-{
-    const int64_t head = std::min<int64_t>(p, (int64_t)((16u - ((uintptr_t)keys & 15u)) & 15u) >> 2);
-    const float4 *k4 = reinterpret_cast<const float4 *>(keys + head);
-    const int64_t n4 = (p - head) >> 2, step = (int64_t)gridDim.x * blockDim.x;
-    const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    int64_t q = tid;
-    for (; q + step < n4; q += 2 * step) {
-        const float4 a = k4[q], b = k4[q + step];
-        const int64_t ja = head + 4 * q, jb = head + 4 * (q + step);
-        f(a.x, ja); f(a.y, ja + 1); f(a.z, ja + 2); f(a.w, ja + 3);
-        f(b.x, jb); f(b.y, jb + 1); f(b.z, jb + 2); f(b.w, jb + 3);
-    }
-    if (q < n4) {
-        const float4 a = k4[q];
-        const int64_t ja = head + 4 * q;
-        f(a.x, ja); f(a.y, ja + 1); f(a.z, ja + 2); f(a.w, ja + 3);
-    }
-    if (tid < head) f(keys[tid], tid);
-    const int64_t t = head + (n4 << 2) + tid;
-    if (t < p) f(keys[t], t);
-}
 
 // Launch A: histogram of bits 30..20; the last block finds the boundary bin.
 __device__ __forceinline__ void sel_count_body(const float *__restrict__ keys, int64_t p, SelState *st,
@@ -152,89 +67,6 @@ __device__ __forceinline__ void sel_count_body(const float *__restrict__ keys, i
     }
 }
 
-// Exact finish in one block (keys in or above the boundary bin > kSelCap):
-// the other two digits of the K-th key T, then every key > T in any order and
-// the lowest-index keys == T in index order after them.
-__device__ void sel_exact_block(const float *__restrict__ keys, int64_t p, const SelState *st,
-                                int32_t *out, uint32_t K, uint32_t *wsum)
-{
-    __shared__ uint32_t h[1024];
-    __shared__ uint32_t res[3];
-    __shared__ uint32_t s_prefix, s_mask, s_need, s_gt, s_cnt;
-    const int tid = threadIdx.x;
-    if (tid == 0) {
-        s_prefix = st->prefix;
-        s_mask = st->mask;
-        s_need = st->need;
-        s_gt = st->count_gt;
-        s_cnt = 0;
-    }
-    __syncthreads();
-    for (int ps = 0; ps < 2; ++ps) {
-        const int shift = ps == 0 ? 10 : 0;
-        for (int b = tid; b < 1024; b += blockDim.x) h[b] = 0;
-        __syncthreads();
-        const uint32_t prefix = s_prefix, mask = s_mask;
-        for (int64_t j = tid; j < p; j += blockDim.x) {
-            const uint32_t k = sel_key(keys[j]);
-            if ((k & mask) == prefix) atomicAdd(&h[(k >> shift) & 0x3ffu], 1u);
-        }
-        __syncthreads();
-        sel_find(h, 1024, s_need, wsum, res);
-        if (tid == 0) {
-            s_prefix |= res[0] << shift;
-            s_mask |= 0x3ffu << shift;
-            s_gt += res[1];
-            s_need -= res[1];
-        }
-        __syncthreads();
-    }
-    const uint32_t T = s_prefix, gt = s_gt, need = s_need;
-    for (int64_t j = tid; j < p; j += blockDim.x) {
-        if (sel_key(keys[j]) > T) {
-            const uint32_t slot = atomicAdd(&s_cnt, 1u);
-            if (slot < K) out[slot] = (int32_t)j;
-        }
-    }
-    uint32_t taken = 0;
-    for (int64_t base = 0; base < p && taken < need; base += blockDim.x) {
-        const int64_t j = base + tid;
-        const uint32_t f = (j < p && sel_key(keys[j]) == T) ? 1u : 0u;
-        uint32_t tot = 0;
-        const uint32_t r = sel_excl_scan(f, wsum, &tot);
-        if (f && taken + r < need && gt + taken + r < K) out[gt + taken + r] = (int32_t)j;
-        taken += tot;
-    }
-    __syncthreads();
-}
-
-// Sort K (<= kMaxCand) indices ascending in one block (bitonic in shared memory).
-__device__ __forceinline__ void sort_idx_body(int32_t *idx, int K)
-{
-    __shared__ int32_t s[kMaxCand];
-    int P = 1;
-    while (P < K) P <<= 1;
-    for (int i = threadIdx.x; i < P; i += blockDim.x) s[i] = i < K ? idx[i] : 0x7fffffff;
-    __syncthreads();
-    for (int size = 2; size <= P; size <<= 1) {
-        for (int stride = size >> 1; stride > 0; stride >>= 1) {
-            for (int i = threadIdx.x; i < P; i += blockDim.x) {
-                const int jx = i ^ stride;
-                if (jx > i) {
-                    const bool up = (i & size) == 0;
-                    const int32_t a = s[i], b = s[jx];
-                    if ((a > b) == up) {
-                        s[i] = b;
-                        s[jx] = a;
-                    }
-                }
-            }
-            __syncthreads();
-        }
-    }
-    for (int i = threadIdx.x; i < K; i += blockDim.x) idx[i] = s[i];
-}
-
 // Launch B: candidates at or above the boundary bin; the last block finishes.
 // gS (optional): the single solve's support; the last block then also forms
 // g_S and ||g_S||^2 (gather_gS_body) for the step size, saving a launch.
@@ -265,34 +97,7 @@ __device__ __forceinline__ void sel_pick_body(const float *__restrict__ keys, in
     __syncthreads();
     if (!last) return;
     __threadfence();
-    if (fast) {
-        int P = 1;
-        while (P < (int)ncand) P <<= 1;
-        for (int i = threadIdx.x; i < P; i += blockDim.x) sk[i] = i < (int)ncand ? __ldcg(&cand[i]) : 0ull;
-        __syncthreads();
-        for (int size = 2; size <= P; size <<= 1) {               // bitonic, descending
-            for (int stride = size >> 1; stride > 0; stride >>= 1) {
-                for (int i = threadIdx.x; i < P; i += blockDim.x) {
-                    const int jx = i ^ stride;
-                    if (jx > i) {
-                        const bool up = (i & size) == 0;
-                        const unsigned long long a = sk[i], b = sk[jx];
-                        if ((a < b) == up) {
-                            sk[i] = b;
-                            sk[jx] = a;
-                        }
-                    }
-                }
-                __syncthreads();
-            }
-        }
-        for (int i = threadIdx.x; i < (int)K; i += blockDim.x)
-            out[i] = (int32_t)(~(uint32_t)(sk[i] & 0xffffffffull));
-        __syncthreads();
-    } else {
-        sel_exact_block(keys, p, st, out, K, wsum);
-    }
-    sort_idx_body(out, (int)K);
+    sel_finish(keys, p, st, cand, ncand, out, K, sk, wsum);
     if (threadIdx.x == 0) {
         st->n_gt = 0;
         st->ticket_b = 0;

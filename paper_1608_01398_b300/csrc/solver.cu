@@ -20,34 +20,11 @@
 // k candidates lie on S, hence the top-k of |w| over all p lies in S u C.
 #include <math.h>
 
-#include "common.cuh"
+#include "bodies.cuh"
 
 namespace iht {
 
-__device__ __forceinline__ int dosage_of(uint32_t code)   // -1 = missing
-{
-    return code == 0u ? 0 : (code == 2u ? 1 : (code == 3u ? 2 : -1));
-}
 
-// Sums of the per-block partial triples (stride 3) by one full warp: lane l
-// adds blocks l, l + 32, ... in order, then a fixed shuffle tree; every lane
-// gets the totals (deterministic, and 32 loads in flight instead of one).
-__device__ __forceinline__ void warp_partials(const double *__restrict__ partials, int npart,
-                                              double &s, double &s2, double &d2)
-{
-    const int lane = threadIdx.x & 31;
-    s = 0.0;
-    s2 = 0.0;
-    d2 = 0.0;
-    for (int b = lane; b < npart; b += 32) {
-        s += partials[3 * b];
-        s2 += partials[3 * b + 1];
-        d2 += partials[3 * b + 2];
-    }
-    s = warp_sum(s);
-    s2 = warp_sum(s2);
-    d2 = warp_sum(d2);
-}
 
 
 __global__ void __launch_bounds__(1024) k_gather_gS(const float *__restrict__ g,
@@ -58,112 +35,6 @@ __global__ void __launch_bounds__(1024) k_gather_gS(const float *__restrict__ g,
     gather_gS_body(g, S, k, coef, sc);
 }
 
-// out_i = base_i + sum_c a_c (x_i,col_c - u_col_c), a_c = sign coef_c v_col_c, over
-// the observed calls (Z[:, cols] coef, Sec. 2.3.2-2.3.3), on used rows (0
-// elsewhere); per-block sums of out, out^2 and (out - prev)^2 (0 without
-// prev) go to partials[3 b .. 3 b + 2].  One thread per sample, 128 samples
-// per block (smaller blocks only multiply the partial triples every consumer
-// sums); each column's three possible terms a (x - u) for x = 0, 1, 2 are
-// staged in shared memory kZmulChunk columns at a time, so a term costs one
-// FP64 add, added in column order.  The product is a chain of dependent steps
-// (global loads, FP64 adds, block reductions) on a few warps per SM, so the
-// body shortens the chain: the row values (used, base, prev) are requested
-// first; a thread loads the genotype bytes of a chunk's first kZmulFirst
-// columns (column index, then byte) while the block stages the terms, and the
-// rest kZmulBatch columns at a time; the three block sums share one
-// reduction.
-constexpr int kZmulChunk = 256;
-constexpr int kZmulThreads = 128;           // largest block
-constexpr int kZmulFirst = 64;
-constexpr int kZmulBatch = 16;
-
-__device__ __forceinline__ void zmul_body(const uint8_t *__restrict__ G, int64_t stride,
-                                          int64_t rowb, const int32_t *__restrict__ cols, int m,
-                                          const double *__restrict__ coef, double sign,
-                                          const double *__restrict__ u64,
-                                          const double *__restrict__ v64,
-                                          const int32_t *__restrict__ used,
-                                          const double *__restrict__ base,
-                                          const double *__restrict__ prev, double *__restrict__ out,
-                                          double *__restrict__ partials, int64_t n_pad,
-                                          int64_t psnp = 0, const double *__restrict__ zc = nullptr)
-{
-    __shared__ double red[3 * (kZmulThreads / 32)];
-    __shared__ double term[kZmulChunk][4];     // terms for codes 00, 01 (missing: 0), 10, 11
-    __shared__ const uint8_t *srow[kZmulChunk];
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const int64_t byte = i >> 2;
-    const int shift = 2 * (int)(i & 3);
-    const bool inb = i < n_pad && byte < rowb;
-    const bool in = i < n_pad;
-    const int32_t ui = in ? used[i] : 0;
-    const double bi = in && base ? base[i] : 0.0;
-    const double pi = in && prev ? prev[i] : 0.0;
-    // covariate columns (index >= psnp, with zc) sort after the SNPs of an
-    // ascending column list: the SNP loop takes the first msnp columns
-    const int mall = m;
-    if (zc)
-        while (m > 0 && cols[m - 1] >= psnp) --m;
-    double acc = 0.0;
-    for (int c0 = 0; c0 < m; c0 += kZmulChunk) {
-        const int mc = min(kZmulChunk, m - c0);
-        const int mf = min(mc, kZmulFirst);
-        uint32_t bf[kZmulFirst];
-        if (inb) {
-#pragma unroll
-            for (int q = 0; q < kZmulFirst; ++q)
-                if (q < mf) bf[q] = __ldg(G + (int64_t)__ldg(cols + c0 + q) * stride + byte);
-        }
-        __syncthreads();
-        for (int c = threadIdx.x; c < mc; c += blockDim.x) {
-            const int col = cols[c0 + c];
-            const double a = sign * coef[c0 + c] * v64[col];
-            const double b = a * u64[col];
-            term[c][0] = a * 0.0 - b;
-            term[c][1] = 0.0;
-            term[c][2] = a * 1.0 - b;
-            term[c][3] = a * 2.0 - b;
-            srow[c] = G + (int64_t)col * stride;
-        }
-        __syncthreads();
-        if (inb) {
-#pragma unroll
-            for (int q = 0; q < kZmulFirst; ++q)
-                if (q < mf) acc += term[q][(bf[q] >> shift) & 3u];
-            int c = mf;
-            for (; c + kZmulBatch <= mc; c += kZmulBatch) {
-                uint32_t b[kZmulBatch];
-#pragma unroll
-                for (int q = 0; q < kZmulBatch; ++q) b[q] = __ldg(srow[c + q] + byte);
-#pragma unroll
-                for (int q = 0; q < kZmulBatch; ++q) acc += term[c + q][(b[q] >> shift) & 3u];
-            }
-            for (; c + 4 <= mc; c += 4) {
-                uint32_t b[4];
-#pragma unroll
-                for (int q = 0; q < 4; ++q) b[q] = __ldg(srow[c + q] + byte);
-#pragma unroll
-                for (int q = 0; q < 4; ++q) acc += term[c + q][(b[q] >> shift) & 3u];
-            }
-            for (; c < mc; ++c) acc += term[c][((uint32_t)__ldg(srow[c] + byte) >> shift) & 3u];
-        }
-    }
-    if (in)
-        for (int c = m; c < mall; ++c) acc += (sign * coef[c]) * zc[(int64_t)(cols[c] - psnp) * n_pad + i];
-    double o = 0.0, d = 0.0;
-    if (in) {
-        o = ui ? bi + acc : 0.0;
-        out[i] = o;
-        if (prev) d = o - pi;
-    }
-    double s = o, s2 = o * o, d2 = d * d;
-    block_sum3(s, s2, d2, red);
-    if (threadIdx.x == 0 && partials) {
-        partials[3 * blockIdx.x] = s;
-        partials[3 * blockIdx.x + 1] = s2;
-        partials[3 * blockIdx.x + 2] = d2;
-    }
-}
 
 __global__ void __launch_bounds__(kZmulThreads) k_zmul(const uint8_t *__restrict__ G, int64_t stride,
                                               int64_t rowb, const int32_t *__restrict__ cols, int m,
@@ -179,7 +50,7 @@ __global__ void __launch_bounds__(kZmulThreads) k_zmul(const uint8_t *__restrict
 {
     if (done && *done) return;
     zmul_body(G, stride, rowb, cols, m, coef, sign, u64, v64, used, base, prev, out, partials, n_pad,
-              psnp, zc);
+              psnp, zc, (int)blockIdx.x);
 }
 
 static int zmul_threads(const iht_dataset *) { return kZmulThreads; }
@@ -215,275 +86,6 @@ int launch_zmul(iht_dataset *ds, const int32_t *cols, int32_t m, const double *c
 // ---------------------------------------------------------------------------
 // Projection for one step size: one block of 1024 threads.
 
-struct MergeArgs {
-    const float *g;
-    const int32_t *S;     // k, ascending
-    const double *bS;     // beta on S
-    const int32_t *cand;  // K, ascending
-    int K;
-    const double *partials;   // ||Z_S g_S||^2 pieces (first attempt)
-    int npart;
-    int first;                // 1: compute mu from num / den
-    const int32_t *skip;      // not null: return when *skip (a speculative attempt not needed)
-    int32_t *Sp;
-    double *bSp;
-    Scalars *sc;
-};
-
-constexpr int kMergeThreads = 1024;
-constexpr int kMergeU = 3 * kMaxK;      // |S u C| <= k + 2k
-constexpr int kMergeSort = 4 * kMaxK;   // power of two >= kMergeU
-constexpr int kMergeRank = 768;         // up to this many candidates: selection by rank
-
-struct MergeShared {
-    int32_t sS[kMaxK];            // S, beta_S and the candidates, staged once
-    double sbS[kMaxK];
-    int32_t scand[kMaxCand];
-    int32_t uidx[kMergeU];
-    double ubeta[kMergeU];
-    double ug[kMergeU];
-    double uw[kMergeU];
-    uint8_t inS[kMergeU];
-    uint8_t inSp[kMergeU];
-    unsigned long long skey[kMergeSort];
-    int32_t spos[kMergeSort];
-    double red[32];
-    uint32_t wsum[32];
-    int nS_extra;
-    int stop;
-};
-
-__device__ __forceinline__ bool before(unsigned long long ka, int32_t ia, unsigned long long kb,
-                                       int32_t ib)
-{
-    return ka > kb || (ka == kb && ia < ib);
-}
-
-__device__ int lower_bound_i32(const int32_t *a, int n, int32_t x)
-{
-    int lo = 0, hi = n;
-    while (lo < hi) {
-        const int mid = (lo + hi) >> 1;
-        if (a[mid] < x) lo = mid + 1; else hi = mid;
-    }
-    return lo;
-}
-
-// Sort positions 0..nU-1 of U by (|w| descending, index ascending).
-__device__ void sort_by_w(MergeShared &sh, int nU)
-{
-    int P = 1;
-    while (P < nU) P <<= 1;
-    for (int i = threadIdx.x; i < P; i += blockDim.x) {
-        if (i < nU) {
-            sh.skey[i] = (unsigned long long)__double_as_longlong(fabs(sh.uw[i]));
-            sh.spos[i] = i;
-        } else {
-            sh.skey[i] = 0ull;
-            sh.spos[i] = -1;
-        }
-    }
-    __syncthreads();
-    for (int size = 2; size <= P; size <<= 1) {
-        for (int st = size >> 1; st > 0; st >>= 1) {
-            for (int i = threadIdx.x; i < P; i += blockDim.x) {
-                const int j = i ^ st;
-                if (j > i) {
-                    const bool up = (i & size) == 0;
-                    const unsigned long long ki = sh.skey[i], kj = sh.skey[j];
-                    const int32_t pi = sh.spos[i], pj = sh.spos[j];
-                    const int32_t xi = pi < 0 ? 0x7fffffff : sh.uidx[pi];
-                    const int32_t xj = pj < 0 ? 0x7fffffff : sh.uidx[pj];
-                    const bool swap = up ? before(kj, xj, ki, xi) : before(ki, xi, kj, xj);
-                    if (swap) {
-                        sh.skey[i] = kj; sh.skey[j] = ki;
-                        sh.spos[i] = pj; sh.spos[j] = pi;
-                    }
-                }
-            }
-            __syncthreads();
-        }
-    }
-}
-
-// The projection proper for a live solve (every thread of the block calls it).
-__device__ __forceinline__ void merge_body(const MergeArgs &A)
-{
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    MergeShared &sh = *reinterpret_cast<MergeShared *>(smem_raw);
-    Scalars *sc = A.sc;
-    const int k = sc->k;
-    for (int i = threadIdx.x; i < k; i += blockDim.x) {
-        sh.sS[i] = A.S[i];
-        sh.sbS[i] = A.bS[i];
-    }
-    for (int i = threadIdx.x; i < A.K; i += blockDim.x) sh.scand[i] = A.cand[i];
-
-    double den = 0.0;
-    if (A.first && threadIdx.x < 32) {
-        double s_, d2_;
-        warp_partials(A.partials, A.npart, s_, den, d2_);
-    }
-    if (threadIdx.x == 0) {
-        sh.stop = 0;
-        sh.nS_extra = 0;
-        if (A.first) {
-            // step size mu = ||g_S||^2 / ||Z_S g_S||^2 (reading of Sec. 2.3.1)
-            const double num = sc->num;
-            sc->bt_last = 0;
-            if (num == 0.0) {
-                sc->status = IHT_OK;            // g_S = 0: fixed point
-                sc->done = 1;
-                sc->skip1 = sc->skip2 = 1;
-                sh.stop = 1;
-            } else if (!(den > 0.0) || !isfinite(den) || !isfinite(num)) {
-                sc->status = IHT_ENUMERIC;
-                sc->done = 1;
-                sc->skip1 = sc->skip2 = 1;
-                sh.stop = 1;
-            } else {
-                sc->mu = num / den;
-            }
-        }
-    }
-    __syncthreads();
-    if (sh.stop) return;
-    const double mu = sc->mu;
-
-    // U = C (ascending) followed by S \ C (in S order)
-    const int K = A.K;
-    for (int b = threadIdx.x; b < K; b += blockDim.x) {
-        const int32_t j = sh.scand[b];
-        const int pos = lower_bound_i32(sh.sS, k, j);
-        const bool on = pos < k && sh.sS[pos] == j;
-        sh.uidx[b] = j;
-        sh.inS[b] = on;
-        sh.ubeta[b] = on ? sh.sbS[pos] : 0.0;
-        sh.ug[b] = (double)A.g[j];
-    }
-    {
-        const int a = threadIdx.x;
-        int32_t j = 0;
-        bool extra = false;
-        if (a < k) {
-            j = sh.sS[a];
-            const int pos = lower_bound_i32(sh.scand, K, j);
-            extra = !(pos < K && sh.scand[pos] == j);
-        }
-        const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-        const unsigned bal = __ballot_sync(0xffffffffu, extra);
-        if (lane == 0) sh.wsum[wid] = __popc(bal);
-        __syncthreads();
-        int off = 0;
-        for (int w = 0; w < wid; ++w) off += sh.wsum[w];
-        off += __popc(bal & ((1u << lane) - 1u));
-        if (extra) {
-            const int u = K + off;
-            sh.uidx[u] = j;
-            sh.inS[u] = 1;
-            sh.ubeta[u] = sh.sbS[a];
-            sh.ug[u] = (double)A.g[j];
-        }
-        if (threadIdx.x == blockDim.x - 1) sh.nS_extra = off + (extra ? 1 : 0);
-    }
-    __syncthreads();
-    const int nU = K + sh.nS_extra;
-
-    for (int u = threadIdx.x; u < nU; u += blockDim.x) {
-        sh.uw[u] = __dadd_rn(sh.ubeta[u], __dmul_rn(mu, sh.ug[u]));
-        sh.skey[u] = (unsigned long long)__double_as_longlong(fabs(sh.uw[u]));
-    }
-    __syncthreads();
-    const bool small = nU <= kMergeRank;
-    if (small) {
-        // S+ by rank: u is in S+ iff fewer than k entries come before it
-        // (|w| descending, index ascending); every thread reads the same v
-        // at the same time (shared-memory broadcast)
-        for (int u = threadIdx.x; u < nU; u += blockDim.x) {
-            const unsigned long long ku = sh.skey[u];
-            const int32_t iu = sh.uidx[u];
-            int rank = 0;
-            for (int v = 0; v < nU; ++v) rank += before(sh.skey[v], sh.uidx[v], ku, iu) ? 1 : 0;
-            sh.inSp[u] = rank < k ? 1 : 0;
-        }
-        __syncthreads();
-    } else {
-        sort_by_w(sh, nU);
-        for (int u = threadIdx.x; u < nU; u += blockDim.x) sh.inSp[u] = 0;
-        __syncthreads();
-        for (int r = threadIdx.x; r < k; r += blockDim.x) sh.inSp[sh.spos[r]] = 1;
-        __syncthreads();
-    }
-    // ||beta+ - beta||^2, ||beta||^2 and |S n S+| by one warp (FP64 issue is
-    // scarce: a block-wide reduction would spend it on empty threads); only
-    // thread 0 uses them
-    int kept = 0;
-    double dd = 0.0, bb = 0.0;
-    if (threadIdx.x < 32) {
-        for (int u = threadIdx.x; u < nU; u += 32) {
-            kept += sh.inS[u] && sh.inSp[u];
-            const double d = (sh.inSp[u] ? sh.uw[u] : 0.0) - sh.ubeta[u];
-            dd += d * d;
-            bb += sh.ubeta[u] * sh.ubeta[u];
-        }
-        kept = __reduce_add_sync(0xffffffffu, kept);
-        dd = warp_sum(dd);
-        bb = warp_sum(bb);
-    }
-
-    // S+ in index order with beta+
-    if (small) {
-        // position of u among the members of S+ = members with a lower index
-        for (int u = threadIdx.x; u < nU; u += blockDim.x) {
-            if (!sh.inSp[u]) continue;
-            const int32_t iu = sh.uidx[u];
-            int pos = 0;
-            for (int v = 0; v < nU; ++v) pos += (sh.inSp[v] && sh.uidx[v] < iu) ? 1 : 0;
-            A.Sp[pos] = iu;
-            A.bSp[pos] = sh.uw[u];
-        }
-        if (threadIdx.x == 0) {
-            sc->changed = kept < k ? 1 : 0;
-            sc->dd = dd;
-            sc->bb = bb;
-        }
-        return;
-    }
-    __syncthreads();
-    for (int r = threadIdx.x; r < kMergeSort; r += blockDim.x) sh.skey[r] = ~0ull;
-    __syncthreads();
-    for (int r = threadIdx.x; r < k; r += blockDim.x) {
-        const int u = sh.spos[r];
-        sh.skey[r] = ((unsigned long long)(uint32_t)sh.uidx[u] << 32) | (uint32_t)u;
-    }
-    __syncthreads();
-    {
-        int P = 1;
-        while (P < k) P <<= 1;
-        for (int size = 2; size <= P; size <<= 1)
-            for (int st = size >> 1; st > 0; st >>= 1) {
-                for (int i = threadIdx.x; i < P; i += blockDim.x) {
-                    const int j = i ^ st;
-                    if (j > i) {
-                        const bool up = (i & size) == 0;
-                        const unsigned long long a = sh.skey[i], b = sh.skey[j];
-                        if ((a > b) == up) { sh.skey[i] = b; sh.skey[j] = a; }
-                    }
-                }
-                __syncthreads();
-            }
-    }
-    for (int r = threadIdx.x; r < k; r += blockDim.x) {
-        const int u = (int)(uint32_t)(sh.skey[r] & 0xffffffffull);
-        A.Sp[r] = sh.uidx[u];
-        A.bSp[r] = sh.uw[u];
-    }
-    if (threadIdx.x == 0) {
-        sc->changed = kept < k ? 1 : 0;
-        sc->dd = dd;
-        sc->bb = bb;
-    }
-}
 
 __global__ void __launch_bounds__(kMergeThreads) k_merge(MergeArgs A)
 {
@@ -494,86 +96,6 @@ __global__ void __launch_bounds__(kMergeThreads) k_merge(MergeArgs A)
 }
 
 // ---------------------------------------------------------------------------
-struct TraceDev {
-    double *objective, *mu;
-    int32_t *backtracks, *changed, *supp;
-    double *beta;
-};
-
-// Backtracking decision for the candidate of k_merge, whose residual r+ the
-// preceding pass wrote (partials: sum r+, sum r+^2, sum (r+ - r)^2).
-__device__ __forceinline__ void decide_body(Scalars *sc, const double *partials, int npart,
-                                            int32_t *S, double *bS, const int32_t *Sp,
-                                            const double *bSp, const TraceDev &tr)
-{
-    __shared__ int accept;
-    const int k = sc->k;
-    double s = 0.0, s2 = 0.0, zz = 0.0;
-    if (threadIdx.x < 32) warp_partials(partials, npart, s, s2, zz);
-    if (threadIdx.x == 0) {
-        accept = 1;
-        if (sc->changed && zz > 0.0) {
-            const double omega = (1.0 - sc->c) * sc->dd / zz;
-            if (sc->mu >= omega && sc->bt_last < sc->max_backtrack) {
-                sc->mu = sc->mu / sc->kappa;
-                sc->bt_last += 1;
-                accept = 0;
-            }
-        }
-        sc->retry = accept ? 0 : 1;
-        if (accept && sc->htp) {
-            // HTP: the step is accepted; the refit on S+ and its residual give the
-            // objective and the stopping test (k_htp_finish)
-            const int it = sc->iter;
-            sc->bt_total += sc->bt_last;
-            if (tr.mu) tr.mu[it] = sc->mu;
-            if (tr.backtracks) tr.backtracks[it] = sc->bt_last;
-            if (tr.changed) tr.changed[it] = sc->changed;
-            sc->skip1 = 1;
-            sc->skip2 = 1;
-        } else if (accept) {
-            const int it = sc->iter;
-            sc->bt_total += sc->bt_last;
-            sc->sum_r = s;
-            sc->sumsq_r = s2;
-            sc->f = 0.5 * s2;
-            sc->step = sqrt(sc->dd) / (sqrt(sc->bb) + 1.0);
-            if (tr.objective) tr.objective[it] = sc->f;
-            if (tr.mu) tr.mu[it] = sc->mu;
-            if (tr.backtracks) tr.backtracks[it] = sc->bt_last;
-            if (tr.changed) tr.changed[it] = sc->changed;
-        }
-    }
-    __syncthreads();
-    if (!accept) {
-        if (threadIdx.x == 0) {
-            sc->skip1 = 0;                     // another attempt with the shrunk mu
-            sc->skip2 = 1;
-        }
-        return;
-    }
-    if (sc->htp) return;
-    const int it = sc->iter;
-    for (int c = threadIdx.x; c < k; c += blockDim.x) {
-        S[c] = Sp[c];
-        bS[c] = bSp[c];
-        if (tr.supp) tr.supp[(size_t)it * k + c] = Sp[c];
-        if (tr.beta) tr.beta[(size_t)it * k + c] = bSp[c];
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        sc->iter = it + 1;
-        if (sc->step < sc->tol) {
-            sc->status = IHT_OK;
-            sc->done = 1;
-        } else if (sc->iter >= sc->max_iter) {
-            sc->status = IHT_ENOTCONV;
-            sc->done = 1;
-        }
-        sc->skip1 = 1;                         // accepted: no further attempt
-        sc->skip2 = sc->done;                  // the next gradient unless stopped
-    }
-}
 
 __global__ void __launch_bounds__(256) k_decide(Scalars *sc, const double *partials, int npart,
                                                 int32_t *S, double *bS, const int32_t *Sp,
@@ -644,18 +166,6 @@ __global__ void __launch_bounds__(256) k_htp_finish(Scalars *sc, const double *p
     }
 }
 
-// Objective of beta = 0 (r = y) before the first iteration (one thread).
-// One full warp; lane 0 writes.
-__device__ __forceinline__ void init_objective_body(Scalars *sc, const double *partials, int npart)
-{
-    double s, s2, d2;
-    warp_partials(partials, npart, s, s2, d2);
-    if (threadIdx.x == 0) {
-        sc->sum_r = s;
-        sc->sumsq_r = s2;
-        sc->f = 0.5 * s2;
-    }
-}
 
 __global__ void k_init_objective(Scalars *sc, const double *partials, int npart)
 {
@@ -663,18 +173,6 @@ __global__ void k_init_objective(Scalars *sc, const double *partials, int npart)
     init_objective_body(sc, partials, npart);
 }
 
-// Accepted residual: r64 <- src, r32 <- src - mean on the used rows.
-__device__ __forceinline__ void center_body(const double *__restrict__ src, double *__restrict__ r64,
-                                            const int32_t *__restrict__ used, int64_t n_pad,
-                                            const Scalars *sc, float *__restrict__ r32)
-{
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n_pad) return;
-    const double mean = sc->sum_r / (double)sc->n_rows;
-    const double v = src[i];
-    if (src != r64) r64[i] = v;
-    r32[i] = used[i] ? (float)(v - mean) : 0.0f;
-}
 
 __global__ void k_center(const double *__restrict__ src, double *__restrict__ r64,
                          const int32_t *__restrict__ used, int64_t n_pad, const Scalars *sc,
@@ -960,7 +458,22 @@ int run_solve(iht_dataset *ds, int k, const iht_options *opt, int n_rows, const 
             if (ws->sc_host->done) break;
         }
     }
-    if (!traced && !htp) {
+    bool fused = false;
+    if (!traced && !htp && !prof && fused_supported(ds, k, opt->grad_impl)) {
+        // the rest of the solve as one graph launch: one host synchronisation
+        const int it0 = ws->sc_host->iter;
+        rc = run_fused_solve(ds, k, K, opt->grad_impl);
+        if (rc != IHT_EAGAIN) {
+            if (rc) return rc;
+            fused = true;
+            IHT_CUDA(cudaMemcpyAsync(&ws->sc_host->iter, &ws->sc->iter, sizeof(int32_t),
+                                     cudaMemcpyDeviceToHost, s));
+            IHT_CUDA(cudaStreamSynchronize(s));
+            ws->graph_replays = ws->sc_host->iter - it0;
+            note_launch(ws->fused_launches * std::max(ws->graph_replays, 1));
+        }
+    }
+    if (!traced && !htp && !fused) {
         // one graph replay and one host synchronisation per iteration
         cudaGraphExec_t exec = nullptr;
         if ((rc = iteration_graph(ds, k, K, opt->grad_impl, prof, &exec))) return rc;
@@ -1151,13 +664,13 @@ __global__ void __launch_bounds__(kZmulThreads) k_zmul_b(const uint8_t *__restri
     if (!zmul_gate(B, which)) return;
     if (which == kZmulInit)
         zmul_body(G, stride, rowb, nullptr, 0, nullptr, -1.0, B.u64, B.v64, B.used, B.y64, nullptr,
-                  B.r64, B.partials, n_pad);
+                  B.r64, B.partials, n_pad, 0, nullptr, (int)blockIdx.x);
     else if (which == kZmulStep)
         zmul_body(G, stride, rowb, B.S, B.k, B.coef, 1.0, B.u64, B.v64, B.used, nullptr, nullptr,
-                  B.zv, B.partials, n_pad);
+                  B.zv, B.partials, n_pad, 0, nullptr, (int)blockIdx.x);
     else
         zmul_body(G, stride, rowb, B.Sp, B.k, B.bSp, -1.0, B.u64, B.v64, B.used, B.y64, B.r64,
-                  B.rc64, B.partials, n_pad);
+                  B.rc64, B.partials, n_pad, 0, nullptr, (int)blockIdx.x);
 }
 
 __global__ void k_init_objective_b(const BSolve *bs, int npart)
@@ -1220,7 +733,7 @@ __global__ void __launch_bounds__(kZmulThreads) k_cv_resid(const uint8_t *__rest
 {
     const CvJob &J = jobs[blockIdx.y];
     zmul_body(G, stride, rowb, J.S, J.k, J.bS, -1.0, J.u64, J.v64, J.used, J.y64, nullptr, J.out, J.partials,
-              n_pad);
+              n_pad, 0, nullptr, (int)blockIdx.x);
 }
 
 int launch_cv_resid(iht_dataset *ds, const CvJob *jobs_dev, int njobs)

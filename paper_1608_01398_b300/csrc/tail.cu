@@ -1,0 +1,477 @@
+// One IHT iteration after its gradient pass as a single cooperative kernel,
+// and the rest of a solve as one CUDA graph launch.
+//
+// Between two gradient passes an iteration (Sec. 2.2-2.3.1) is a chain of small
+// dependent steps: the top-2k candidates of |g|, g_S and Z_S g_S for the step
+// size, the projection, the residual of the candidate, the backtracking test
+// (repeated while it rejects), the centred residual and its limb image for the
+// next tensor-core pass.  As separate launches each step costs a launch and a
+// drain of the GPU; here they are the phases of one kernel whose blocks meet at
+// grid barriers (a cooperative launch, so every block is resident; every wait
+// is bounded and a barrier that gives up stops the solve with an error word the
+// host reads).  Each phase runs the same device code as the separate kernels
+// (bodies.cuh, select_bodies.cuh, limbs.cuh), so a solve gives the same bits on
+// either path and in a batch.
+//
+// The solve graph is a conditional while node whose body is this kernel, the
+// missing-call sums and the gradient pass; the kernel clears the condition once
+// the solve has stopped, so the host synchronises once per solve.
+#include "bodies.cuh"
+#include "limbs.cuh"
+#include "select_bodies.cuh"
+
+namespace iht {
+
+constexpr int kTailThreads = kZmulThreads;    // one 128-sample block of the sparse product per pass
+constexpr int kTailKM = 256;                  // largest k of the fused path
+constexpr uint32_t kBarSpin = 1u << 24;       // bounded barrier waits (each poll may sleep ~64 ns)
+
+struct TailWork {                     // zeroed before every solve
+    unsigned int bar_count, bar_gen;  // grid barrier: arrivals, generation
+    int bar_err, pad;                 // 1: a barrier wait gave up
+    SelState st;                      // selection state (boundary bin, candidate count)
+    uint32_t hist[kSelBins];          // histogram of |g| bits 30..20
+    unsigned long long cand[kSelCap]; // candidate words (key << 32 | ~index)
+    float part_m[1024];               // limb prerequisites: max |r| and sum of r over
+    double part_acc[1024];            //   the samples i = t mod 1024 (the limb kernel's layout)
+};
+
+struct TailArgs {
+    const uint8_t *G;
+    int64_t stride, rowb, n_pad, p, P;   // P = p + covariates
+    const double *zc;                    // standardised covariates, or null
+    Scalars *sc;
+    const float *g;
+    int32_t *S, *Sp, *cand;
+    double *bS, *bSp, *coef;
+    const double *u64, *v64;
+    const int32_t *used;
+    const double *y64;
+    double *r64, *rc64, *zv;
+    float *r32;
+    double *partials;
+    int npart;                           // 128-sample blocks of the sparse product
+    int k, K;
+    TailWork *T;
+    uint8_t *bimg;                       // limb image of the next tensor-core pass
+    TcParams *prm;
+    int64_t nlim;                        // samples the limb image covers
+    cudaGraphConditionalHandle cond;
+};
+
+// Grid-wide barrier (sense by generation).  Thread 0 arrives after the
+// block's writes (block barrier, then a device-scope fence); the last block to
+// arrive resets the count and opens the next generation; the others poll the
+// generation with a bounded number of sleeps.  Returns false when this block
+// or another gave up.
+__device__ __forceinline__ bool grid_sync(TailWork *T)
+{
+    __shared__ int s_ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        volatile unsigned int *gen = &T->bar_gen;
+        const unsigned int g = *gen;
+        int ok = 1;
+        __threadfence();
+        if (atomicAdd(&T->bar_count, 1u) == gridDim.x - 1) {
+            atomicExch(&T->bar_count, 0u);
+            __threadfence();
+            atomicAdd(&T->bar_gen, 1u);
+        } else {
+            uint32_t it = 0;
+            while (*gen == g) {
+                if (++it > kBarSpin) {
+                    ok = 0;
+                    break;
+                }
+                __nanosleep(64);
+            }
+        }
+        __threadfence();
+        if (!ok) atomicExch(&T->bar_err, 1);
+        s_ok = ok && !*(volatile int *)&T->bar_err;
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
+__device__ __forceinline__ void tail_stop(const TailArgs &A)
+{
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        atomicExch(&A.T->bar_err, 1);
+        A.sc->done = 1;
+        cudaGraphSetConditional(A.cond, 0u);
+    }
+}
+
+__global__ void __launch_bounds__(kTailThreads) k_tail(const __grid_constant__ TailArgs A)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ uint32_t wsum[32];
+    __shared__ uint32_t res[3];
+    __shared__ double red[32];
+    __shared__ int s_state;
+    TailWork *T = A.T;
+    Scalars *sc = A.sc;
+    const int tid = threadIdx.x;
+    const bool b0 = blockIdx.x == 0;
+
+    if (tid == 0) s_state = *(volatile int32_t *)&sc->done;
+    __syncthreads();
+    if (s_state) {
+        if (b0 && tid == 0) cudaGraphSetConditional(A.cond, 0u);
+        return;
+    }
+
+    // A: g_S and ||g_S||^2 for the step size (block 0, first warp); histogram of |g|
+    if (b0) gather_gS_body(A.g, A.S, A.k, A.coef, sc);
+    {
+        uint32_t *hs = reinterpret_cast<uint32_t *>(smem_raw);
+        for (int b = tid; b < kSelBins; b += blockDim.x) hs[b] = 0;
+        __syncthreads();
+        bool nan = false;
+        sel_each(A.g, A.P, [&](float x, int64_t) {
+            const uint32_t key = sel_key(x);
+            nan |= key > 0x7f800000u;
+            atomicAdd(&hs[key >> 20], 1u);
+        });
+        if (nan) atomicOr(&T->st.err, 1u);
+        __syncthreads();
+        for (int b = tid; b < kSelBins; b += blockDim.x)
+            if (hs[b]) atomicAdd(&T->hist[b], hs[b]);
+    }
+    if (!grid_sync(T)) return tail_stop(A);
+
+    // B: the boundary bin (every block, from the whole histogram) and the keys
+    // in or above it as candidate words
+    {
+        uint32_t *hs = reinterpret_cast<uint32_t *>(smem_raw);
+        for (int b = tid; b < kSelBins; b += blockDim.x) hs[b] = __ldcg(&T->hist[b]);
+        __syncthreads();
+        sel_find(hs, kSelBins, (uint32_t)A.K, wsum, res);
+        const uint32_t lo = res[0] << 20, ncand = res[1] + res[2];
+        if (ncand <= (uint32_t)kSelCap)
+            sel_each(A.g, A.P, [&](float x, int64_t j) {
+                const uint32_t key = sel_key(x);
+                if (key >= lo) {
+                    const uint32_t slot = atomicAdd(&T->st.n_gt, 1u);
+                    if (slot < (uint32_t)kSelCap)
+                        T->cand[slot] = ((unsigned long long)key << 32) | (unsigned long long)(~(uint32_t)j);
+                }
+            });
+        if (b0 && tid == 0) {
+            T->st.prefix = res[0] << 20;
+            T->st.mask = 0x7ffu << 20;
+            T->st.count_gt = res[1];
+            T->st.need = (uint32_t)A.K - res[1];
+            T->st.ncand = ncand;
+        }
+    }
+    if (!grid_sync(T)) return tail_stop(A);
+
+    // C: block 0 sorts the candidates into the K indices (ascending) and cleans
+    // the selection scratch; the other blocks form Z_S g_S
+    if (b0) {
+        const uint32_t ncand = T->st.ncand;
+        sel_finish(A.g, A.P, &T->st, T->cand, ncand, A.cand, (uint32_t)A.K,
+                   reinterpret_cast<unsigned long long *>(smem_raw), wsum);
+        for (int b = tid; b < kSelBins; b += blockDim.x) T->hist[b] = 0;
+        if (tid == 0) T->st.n_gt = 0;
+    }
+    if (!b0 || gridDim.x == 1) {
+        const int first = gridDim.x == 1 ? 0 : blockIdx.x - 1;
+        const int step = gridDim.x == 1 ? 1 : gridDim.x - 1;
+        for (int vb = first; vb < A.npart; vb += step)
+            zmul_body(A.G, A.stride, A.rowb, A.S, A.k, A.coef, 1.0, A.u64, A.v64, A.used, nullptr,
+                      nullptr, A.zv, A.partials, A.n_pad, A.p, A.zc, vb);
+    }
+    if (!grid_sync(T)) return tail_stop(A);
+
+    // D: attempts: projection (block 0), the candidate's residual (all blocks),
+    // the backtracking decision (block 0), until one is accepted or the solve stops
+    for (int attempt = 0;; ++attempt) {
+        if (b0) {
+            MergeArgs M;
+            M.g = A.g;
+            M.S = A.S;
+            M.bS = A.bS;
+            M.cand = A.cand;
+            M.K = A.K;
+            M.partials = A.partials;
+            M.npart = A.npart;
+            M.first = attempt == 0;
+            M.skip = nullptr;
+            M.Sp = A.Sp;
+            M.bSp = A.bSp;
+            M.sc = sc;
+            merge_body<MergeSharedT<kTailKM>>(M);
+        }
+        if (!grid_sync(T)) return tail_stop(A);
+        if (tid == 0) s_state = *(volatile int32_t *)&sc->done;
+        __syncthreads();
+        if (s_state) break;
+        for (int vb = blockIdx.x; vb < A.npart; vb += gridDim.x)
+            zmul_body(A.G, A.stride, A.rowb, A.Sp, A.k, A.bSp, -1.0, A.u64, A.v64, A.used, A.y64,
+                      A.r64, A.rc64, A.partials, A.n_pad, A.p, A.zc, vb);
+        if (!grid_sync(T)) return tail_stop(A);
+        if (b0) decide_body(sc, A.partials, A.npart, A.S, A.bS, A.Sp, A.bSp, TraceDev{});
+        if (!grid_sync(T)) return tail_stop(A);
+        if (tid == 0)
+            s_state = (*(volatile int32_t *)&sc->done ? 1 : 0) | (*(volatile int32_t *)&sc->retry ? 2 : 0);
+        __syncthreads();
+        if ((s_state & 1) || !(s_state & 2)) break;
+    }
+
+    // E: the accepted residual, centred, and the next pass's limb image
+    __syncthreads();                      // every thread has read s_state in the loop
+    if (tid == 0) s_state = *(volatile int32_t *)&sc->done;
+    __syncthreads();
+    if (!s_state) {
+        const int64_t nthr = (int64_t)gridDim.x * blockDim.x;
+        for (int64_t i = (int64_t)blockIdx.x * blockDim.x + tid; i < A.n_pad; i += nthr)
+            center_elem(A.rc64, A.r64, A.used, i, sc, A.r32);
+        if (!grid_sync(T)) return tail_stop(A);
+        for (int64_t t = (int64_t)blockIdx.x * blockDim.x + tid; t < 1024; t += nthr) {
+            float m = 0.0f;
+            double acc = 0.0;
+            for (int64_t i = t; i < A.nlim; i += 1024) {
+                const float r = A.r32[i];
+                m = fmaxf(m, fabsf(r));
+                acc += (double)r;
+            }
+            T->part_m[t] = m;
+            T->part_acc[t] = acc;
+        }
+        if (!grid_sync(T)) return tail_stop(A);
+        float m = 0.0f;
+        for (int t = tid; t < 1024; t += blockDim.x) m = fmaxf(m, T->part_m[t]);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+        if ((tid & 31) == 0) reinterpret_cast<float *>(wsum)[tid >> 5] = m;
+        __syncthreads();
+        m = 0.0f;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) m = fmaxf(m, reinterpret_cast<float *>(wsum)[w]);
+        const float s0 = limb_scale(m);
+        if (b0) {
+            // R by the limb kernel's reduction: a shuffle tree per 32 of its 1024
+            // threads, then the same tree over the 32 warp sums
+            const int lane = tid & 31, warp = tid >> 5;
+            for (int w = warp; w < 32; w += blockDim.x >> 5) {
+                const double x = warp_sum(T->part_acc[32 * w + lane]);
+                if (lane == 0) red[w] = x;
+            }
+            __syncthreads();
+            if (warp == 0) {
+                const double R = warp_sum(red[lane]);
+                if (lane == 0) {
+                    A.prm->s0 = s0;
+                    A.prm->R = (float)R;
+                }
+            }
+            for (int b = tid; b < 256; b += blockDim.x) A.bimg[256 + 256 * (A.nlim >> 5) + b] = 0;
+        }
+        for (int64_t i = (int64_t)blockIdx.x * blockDim.x + tid; i < A.nlim; i += nthr)
+            limb_encode(A.r32[i], s0, A.bimg, i);
+    }
+    if (b0 && tid == 0) cudaGraphSetConditional(A.cond, *(volatile int32_t *)&sc->done ? 0u : 1u);
+}
+
+// ---------------------------------------------------------------------------
+// Host side.
+
+static size_t tail_smem()
+{
+    return std::max(sizeof(MergeSharedT<kTailKM>), sizeof(unsigned long long) * kSelCap);
+}
+
+bool fused_supported(const iht_dataset *ds, int k, int impl)
+{
+    return (impl == 0 || impl == 2) && grad_tc_supported(ds) && k <= kTailKM &&
+           zmul_blocks(ds) <= kPartials;
+}
+
+void free_fused(Workspace *ws)
+{
+    if (ws->fused_exec) cudaGraphExecDestroy(ws->fused_exec);
+    if (ws->tail) cudaFree(ws->tail);
+    ws->fused_exec = nullptr;
+    ws->tail = nullptr;
+}
+
+// Blocks of the cooperative launch: as many as are resident at once, at most
+// two per SM (more only lengthen the barriers).
+static int tail_grid(iht_dataset *ds)
+{
+    static thread_local int cfg_dev = -1, per_sm = 0;
+    if (cfg_dev != ds->ctx->device) {
+        if (cudaFuncSetAttribute(k_tail, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tail_smem()) !=
+                cudaSuccess ||
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_tail, kTailThreads, tail_smem()) !=
+                cudaSuccess)
+            per_sm = 0;
+        cfg_dev = ds->ctx->device;
+    }
+    return std::min(per_sm, 2) * ds->ctx->num_sms;
+}
+
+// Captures the solve loop: while (condition) { fused iteration; missing-call
+// sums; gradient pass }.
+static int build_fused_graph(iht_dataset *ds, int k, int K, const TailArgs &args, int grid,
+                             cudaGraphExec_t *exec)
+{
+    Workspace *ws = ds->ws;
+    cudaGraph_t graph = nullptr;
+    IHT_CUDA(cudaGraphCreate(&graph, 0));
+    cudaGraphConditionalHandle cond;
+    cudaError_t e = cudaGraphConditionalHandleCreate(&cond, graph, 1u, cudaGraphCondAssignDefault);
+    cudaGraphNodeParams cp = {};
+    cudaGraphNode_t node;
+    if (e == cudaSuccess) {
+        cp.type = cudaGraphNodeTypeConditional;
+        cp.conditional.handle = cond;
+        cp.conditional.type = cudaGraphCondTypeWhile;
+        cp.conditional.size = 1;
+        e = cudaGraphAddNode(&node, graph, nullptr, nullptr, 0, &cp);
+    }
+    if (e != cudaSuccess) {
+        cudaGraphDestroy(graph);
+        set_cuda_error(e, "fused solve graph");
+        return IHT_ECUDA;
+    }
+    cudaGraph_t body = cp.conditional.phGraph_out[0];
+    if (!ws->cap_stream) {
+        e = cudaStreamCreateWithFlags(&ws->cap_stream, cudaStreamNonBlocking);
+        if (e != cudaSuccess) {
+            cudaGraphDestroy(graph);
+            set_cuda_error(e, "capture stream");
+            return IHT_ECUDA;
+        }
+    }
+    cudaStream_t user = ds->ctx->stream;
+    ds->ctx->stream = ws->cap_stream;
+    const uint64_t before = launches_noted();
+    e = cudaStreamBeginCaptureToGraph(ws->cap_stream, body, nullptr, nullptr, 0,
+                                      cudaStreamCaptureModeThreadLocal);
+    int rc = IHT_OK;
+    if (e == cudaSuccess) {
+        TailArgs a = args;
+        a.cond = cond;
+        cudaLaunchConfig_t lc = {};
+        lc.gridDim = dim3((unsigned)grid);
+        lc.blockDim = dim3(kTailThreads);
+        lc.dynamicSmemBytes = tail_smem();
+        lc.stream = ws->cap_stream;
+        cudaLaunchAttribute at[1];
+        at[0].id = cudaLaunchAttributeCooperative;
+        at[0].val.cooperative = 1;
+        lc.attrs = at;
+        lc.numAttrs = 1;
+        e = cudaLaunchKernelEx(&lc, k_tail, a);
+        note_launch();
+        if (e != cudaSuccess) {
+            set_cuda_error(e, "fused iteration launch");
+            rc = IHT_ECUDA;
+        }
+        const int32_t *done = &ws->sc->done;
+        if (rc == IHT_OK) rc = launch_missing_sums(ds, ws->r32, ws->Mj, done);
+        if (rc == IHT_OK) rc = launch_grad_tc_main(ds, ws->r32, ws->g, done);
+        if (rc == IHT_OK) rc = launch_cov_grad(ds, ws->r32, ws->g, done);
+        cudaGraph_t captured = nullptr;
+        const cudaError_t e2 = cudaStreamEndCapture(ws->cap_stream, &captured);
+        if (rc == IHT_OK && e2 != cudaSuccess) {
+            set_cuda_error(e2, "fused solve capture");
+            rc = IHT_ECUDA;
+        }
+    } else {
+        set_cuda_error(e, "fused solve capture");
+        rc = IHT_ECUDA;
+    }
+    ds->ctx->stream = user;
+    const int n = (int)(launches_noted() - before);
+    note_launch(-n);                                   // captured, not run
+    if (rc == IHT_OK) {
+        e = cudaGraphInstantiate(exec, graph, 0);
+        if (e != cudaSuccess) {
+            set_cuda_error(e, "fused solve instantiate");
+            *exec = nullptr;
+            rc = IHT_ECUDA;
+        }
+    }
+    cudaGraphDestroy(graph);
+    if (rc == IHT_OK) ws->fused_launches = n;
+    (void)k;
+    (void)K;
+    return rc;
+}
+
+// After the first gradient pass and S (S^0, or a resumed support): the rest of
+// the solve as one graph launch.  Returns IHT_EAGAIN, with nothing enqueued,
+// when the graph cannot be built here (the caller then runs the per-iteration
+// graph); ETIMEOUT when a barrier of the fused kernel gave up.
+int run_fused_solve(iht_dataset *ds, int k, int K, int impl)
+{
+    Workspace *ws = ds->ws;
+    cudaStream_t s = ds->ctx->stream;
+    const int grid = tail_grid(ds);
+    if (grid < 1) return IHT_EAGAIN;
+    if (!ws->tail) IHT_CUDA(dev_malloc(&ws->tail, sizeof(TailWork)));
+    uint8_t *bimg = nullptr;
+    TcParams *prm = nullptr;
+    int64_t nlim = 0;
+    int rc = grad_tc_limb_buffers(ds, &bimg, &prm, &nlim);
+    if (rc) return rc;
+    TailArgs a = {};
+    a.G = ds->G;
+    a.stride = ds->stride;
+    a.rowb = ds->rowb;
+    a.n_pad = ds->n_pad;
+    a.p = ds->p;
+    a.P = ds->p + ds->q;
+    a.zc = ds->q > 0 ? ws->zc : nullptr;
+    a.sc = ws->sc;
+    a.g = ws->g;
+    a.S = ws->S;
+    a.Sp = ws->Sp;
+    a.cand = ws->cand;
+    a.bS = ws->bS;
+    a.bSp = ws->bSp;
+    a.coef = ws->coef;
+    a.u64 = ws->u64;
+    a.v64 = ws->v64;
+    a.used = ws->used;
+    a.y64 = ws->y64;
+    a.r64 = ws->r64;
+    a.rc64 = ws->rc64;
+    a.zv = ws->zv;
+    a.r32 = ws->r32;
+    a.partials = ws->partials;
+    a.npart = zmul_blocks(ds);
+    a.k = k;
+    a.K = K;
+    a.T = ws->tail;
+    a.bimg = bimg;
+    a.prm = prm;
+    a.nlim = nlim;
+    const uint64_t key[10] = {(uint64_t)k | ((uint64_t)ds->q << 32), (uint64_t)K, (uint64_t)impl,
+                              (uint64_t)(uintptr_t)ws->tail, (uint64_t)(uintptr_t)bimg,
+                              grad_tc_scratch_id(), (uint64_t)(uintptr_t)ws->S,
+                              (uint64_t)(uintptr_t)ws->used, (uint64_t)grid,
+                              (uint64_t)(uintptr_t)ds->G};
+    if (!ws->fused_exec || !std::equal(key, key + 10, ws->fused_key)) {
+        if (ws->fused_exec) cudaGraphExecDestroy(ws->fused_exec);
+        ws->fused_exec = nullptr;
+        if (build_fused_graph(ds, k, K, a, grid, &ws->fused_exec) != IHT_OK) {
+            cudaGetLastError();                        // the per-iteration graph runs instead
+            return IHT_EAGAIN;
+        }
+        std::copy(key, key + 10, ws->fused_key);
+    }
+    IHT_CUDA(cudaMemsetAsync(ws->tail, 0, sizeof(TailWork), s));   // barrier, histogram, state
+    IHT_CUDA(cudaGraphLaunch(ws->fused_exec, s));
+    int err = 0;
+    IHT_CUDA(cudaMemcpyAsync(&err, &ws->tail->bar_err, sizeof(int), cudaMemcpyDeviceToHost, s));
+    IHT_CUDA(cudaStreamSynchronize(s));
+    return err ? IHT_ETIMEOUT : IHT_OK;
+}
+
+}  // namespace iht

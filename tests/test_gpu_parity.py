@@ -315,3 +315,44 @@ def test_topk_nan_is_reported(iht, ctx):
     assert e.value.status == iht.IHT_ENUMERIC
     idx = iht.iht_topk(ctx, torch.from_numpy(w).cuda(), 10).cpu().numpy()
     assert np.array_equal(idx, np.sort(np.lexsort((np.arange(w.size), -np.abs(w.astype(np.float64))))[:10]))
+
+
+@pytest.mark.parametrize("case", ["config1", "rows", "covariates", "k256", "backtracking"])
+def test_fused_solve_matches_per_iteration_paths(iht, ctx, case):
+    """A solve run as one graph (the fused per-iteration kernel in a conditional
+    loop) gives the bits of the per-iteration graph (profiled solves) and of the
+    traced per-launch path, and launches a few kernels per iteration."""
+    rng = np.random.default_rng(55)
+    if case == "config1":
+        pn = synth.config_panel(1)
+        G = oracle.Geno.from_bed(pn.bed(), pn.n, pn.p)
+        y, _, _ = synth.config_phenotype(1, pn)
+        rows, k, kw = None, 10, {}
+    else:
+        G, codes = random_geno(rng, 700, 3000, miss=0.02)
+        Z = np_Z(codes)
+        y = Z[:, rng.choice(3000, 12, replace=False)] @ rng.normal(0, 0.5, 12) + rng.normal(size=700)
+        rows, k, kw = None, 12, {}
+        if case == "rows":
+            rows = np.sort(rng.choice(700, size=611, replace=False)).astype(np.int32)
+            y = y[rows]
+        if case == "k256":
+            k = 256
+        if case == "backtracking":
+            kw = dict(c=0.3)
+    ds = load(iht, ctx, G)
+    if case == "covariates":
+        ds.set_covariates(np.vstack([rng.normal(size=G.n), rng.gamma(2.0, size=G.n)]))
+    l0 = iht.iht_kernel_launches()
+    a = iht.iht_fit(ds, y, k, rows=rows, **kw)
+    launches = iht.iht_kernel_launches() - l0
+    b = iht.iht_fit(ds, y, k, rows=rows, profile=1, **kw)
+    c = iht.iht_fit_trace(ds, y, k, rows=rows, **kw)
+    for other in (b, c):
+        assert np.array_equal(a.beta, other.beta) and np.array_equal(a.support, other.support)
+        assert (a.iterations, a.status, a.backtracks) == (other.iterations, other.status, other.backtracks)
+        assert a.objective == other.objective and a.mu == other.mu
+    print(f"[fused] {case}: {a.iterations} iterations, {a.backtracks} shrinks, {launches} launches")
+    assert a.iterations >= 2 and launches <= 12 + 6 * a.iterations
+    if case == "backtracking":
+        assert a.backtracks > 0
