@@ -167,10 +167,16 @@ struct MergeArgs {
     int32_t *Sp;
     double *bSp;
     Scalars *sc;
+    int shrinks = 0;          // first attempt only: mu / kappa this many times after num / den
+                              // (a later attempt evaluated ahead of the decision on this one)
 };
 
 constexpr int kMergeThreads = 1024;
-constexpr int kMergeRank = 768;         // up to this many candidates: selection by rank
+// Up to this many entries of S u C the selection is by rank (each thread counts
+// the entries before its own), above it by a bitonic sort of the block; both
+// choose the same set in the same order (measured: the rank is the faster of
+// the two at the sizes of the single-solve workload, with 128 threads or 1024).
+constexpr int kMergeRank = 768;
 
 // Shared memory of the projection for supports of at most KM indices (the
 // candidates are at most 2 KM, |S u C| at most 3 KM).
@@ -286,6 +292,7 @@ template <typename SH = MergeShared> __device__ __forceinline__ void merge_body(
                 sh.stop = 1;
             } else {
                 sc->mu = num / den;
+                for (int q = 0; q < A.shrinks; ++q) sc->mu = sc->mu / sc->kappa;   // as the decision shrinks it
             }
         }
     }

@@ -228,6 +228,8 @@ struct Workspace {
     // a whole solve as one graph: a conditional while loop over the fused
     // per-iteration kernel and the gradient pass (tail.cu)
     TailWork *tail = nullptr;
+    int32_t *Sp2 = nullptr;                // the second candidate of the fused kernel (mu / kappa)
+    double *bSp2 = nullptr, *rc64_2 = nullptr, *partials2 = nullptr;
     cudaGraphExec_t fused_exec = nullptr;
     uint64_t fused_key[10] = {};
     int fused_launches = 0;                // kernels per loop trip

@@ -653,23 +653,30 @@ __global__ void __launch_bounds__(512) k_missing_sum_smem(const int64_t *__restr
     for (int64_t i = threadIdx.x; i < n_pad; i += blockDim.x) rs_miss[i] = r32[i];
     __syncthreads();
     const uint4 *__restrict__ idx4 = reinterpret_cast<const uint4 *>(idx);
+    constexpr int kBatch = 8;                                 // 16-byte list pieces in flight
     for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < p;
          j += (int64_t)gridDim.x * blockDim.x) {
         const int64_t e0 = off[j], e1 = off[j + 1];
         const int64_t a0 = e0 & ~(int64_t)(kPer - 1);
         const int lo = (int)(e0 - a0), hi = (int)(e1 - a0);   // valid positions [lo, hi) from a0
         const uint4 *__restrict__ src = idx4 + a0 / kPer;     // (lists end with 16 spare entries)
+        const int nq = (hi + kPer - 1) / kPer;                // pieces holding the list
         float m = 0.0f;
-        uint4 w = src[0];
-        for (int q = 0; q * kPer < hi; ++q) {
-            const uint4 wn = (q + 1) * kPer < hi ? src[q + 1] : w;
-            const IdxT *ent = reinterpret_cast<const IdxT *>(&w);
+        for (int q0 = 0; q0 < nq; q0 += kBatch) {
+            uint4 w[kBatch];
 #pragma unroll
-            for (int t = 0; t < kPer; ++t) {
-                const int pos = q * kPer + t;
-                if (pos >= lo && pos < hi) m += rs_miss[ent[t]];
+            for (int u = 0; u < kBatch; ++u)
+                if (q0 + u < nq) w[u] = src[q0 + u];
+#pragma unroll
+            for (int u = 0; u < kBatch; ++u) {
+                if (q0 + u >= nq) break;
+                const IdxT *ent = reinterpret_cast<const IdxT *>(&w[u]);
+#pragma unroll
+                for (int t = 0; t < kPer; ++t) {
+                    const int pos = (q0 + u) * kPer + t;
+                    if (pos >= lo && pos < hi) m += rs_miss[ent[t]];
+                }
             }
-            w = wn;
         }
         M[j] = m;
     }
@@ -721,7 +728,7 @@ int launch_missing_sums(iht_dataset *ds, const float *r32, float *M, const int32
                                           cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024));
             configured = ds->ctx->device;
         }
-        const int per_sm = smem <= 48 * 1024 ? 3 : 1;
+        const int per_sm = smem <= 40 * 1024 ? 4 : (smem <= 48 * 1024 ? 3 : 1);
         const int blocks = (int)std::min<int64_t>(ceil_div(ds->p, 512), (int64_t)ds->ctx->num_sms * per_sm);
         if (ds->miss_idx16)
             k_missing_sum_smem<uint16_t><<<blocks, 512, smem, s>>>(

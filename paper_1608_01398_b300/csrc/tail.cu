@@ -24,11 +24,12 @@ namespace iht {
 
 constexpr int kTailThreads = kZmulThreads;    // one 128-sample block of the sparse product per pass
 constexpr int kTailKM = 256;                  // largest k of the fused path
-constexpr uint32_t kBarSpin = 1u << 24;       // bounded barrier waits (each poll may sleep ~64 ns)
+constexpr uint32_t kBarSpin = 1u << 22;       // bounded barrier waits (polls; sleeps up to 512 ns each)
 
 struct TailWork {                     // zeroed before every solve
     unsigned int bar_count, bar_gen;  // grid barrier: arrivals, generation
-    int bar_err, pad;                 // 1: a barrier wait gave up
+    int bar_err, acc2;                // 1: a barrier wait gave up; the second candidate was accepted
+    Scalars spec;                     // the second candidate's projection scalars (mu / kappa)
     SelState st;                      // selection state (boundary bin, candidate count)
     uint32_t hist[kSelBins];          // histogram of |g| bits 30..20
     unsigned long long cand[kSelCap]; // candidate words (key << 32 | ~index)
@@ -42,14 +43,14 @@ struct TailArgs {
     const double *zc;                    // standardised covariates, or null
     Scalars *sc;
     const float *g;
-    int32_t *S, *Sp, *cand;
-    double *bS, *bSp, *coef;
+    int32_t *S, *Sp, *cand, *Sp2;
+    double *bS, *bSp, *coef, *bSp2;
     const double *u64, *v64;
     const int32_t *used;
     const double *y64;
-    double *r64, *rc64, *zv;
+    double *r64, *rc64, *zv, *rc64_2;
     float *r32;
-    double *partials;
+    double *partials, *partials2;
     int npart;                           // 128-sample blocks of the sparse product
     int k, K;
     TailWork *T;
@@ -78,13 +79,16 @@ __device__ __forceinline__ bool grid_sync(TailWork *T)
             __threadfence();
             atomicAdd(&T->bar_gen, 1u);
         } else {
-            uint32_t it = 0;
+            // back off: a waiting block polls rarely, so the blocks still at work
+            // (often block 0 alone) do not queue behind the polls in L2
+            uint32_t it = 0, ns = 32;
             while (*gen == g) {
                 if (++it > kBarSpin) {
                     ok = 0;
                     break;
                 }
-                __nanosleep(64);
+                __nanosleep(ns);
+                if (ns < 512) ns <<= 1;
             }
         }
         __threadfence();
@@ -124,7 +128,10 @@ __global__ void __launch_bounds__(kTailThreads) k_tail(const __grid_constant__ T
     }
 
     // A: g_S and ||g_S||^2 for the step size (block 0, first warp); histogram of |g|
-    if (b0) gather_gS_body(A.g, A.S, A.k, A.coef, sc);
+    if (b0) {
+        if (tid == 0) T->acc2 = 0;
+        gather_gS_body(A.g, A.S, A.k, A.coef, sc);
+    }
     {
         uint32_t *hs = reinterpret_cast<uint32_t *>(smem_raw);
         for (int b = tid; b < kSelBins; b += blockDim.x) hs[b] = 0;
@@ -187,39 +194,94 @@ __global__ void __launch_bounds__(kTailThreads) k_tail(const __grid_constant__ T
     }
     if (!grid_sync(T)) return tail_stop(A);
 
-    // D: attempts: projection (block 0), the candidate's residual (all blocks),
-    // the backtracking decision (block 0), until one is accepted or the solve stops
-    for (int attempt = 0;; ++attempt) {
-        if (b0) {
-            MergeArgs M;
-            M.g = A.g;
-            M.S = A.S;
-            M.bS = A.bS;
-            M.cand = A.cand;
-            M.K = A.K;
-            M.partials = A.partials;
-            M.npart = A.npart;
-            M.first = attempt == 0;
-            M.skip = nullptr;
-            M.Sp = A.Sp;
-            M.bSp = A.bSp;
-            M.sc = sc;
-            merge_body<MergeSharedT<kTailKM>>(M);
+    // D: the first two attempts side by side: block 0 projects with mu, block 1
+    // with mu / kappa (the step the decision takes when it rejects the first),
+    // both candidates' residuals in one pass, then the decisions in order on
+    // block 0 -- the same arithmetic as one attempt after the other.  Later
+    // attempts, when both are rejected, run one at a time.
+    if (b0 || blockIdx.x == 1) {
+        Scalars *msc = b0 ? sc : &T->spec;
+        if (!b0 && tid == 0) T->spec = *sc;
+        __syncthreads();
+        MergeArgs M;
+        M.g = A.g;
+        M.S = A.S;
+        M.bS = A.bS;
+        M.cand = A.cand;
+        M.K = A.K;
+        M.partials = A.partials;
+        M.npart = A.npart;
+        M.first = 1;
+        M.shrinks = b0 ? 0 : 1;
+        M.skip = nullptr;
+        M.Sp = b0 ? A.Sp : A.Sp2;
+        M.bSp = b0 ? A.bSp : A.bSp2;
+        M.sc = msc;
+        merge_body<MergeSharedT<kTailKM>>(M);
+    }
+    if (!grid_sync(T)) return tail_stop(A);
+    if (tid == 0) s_state = *(volatile int32_t *)&sc->done;
+    __syncthreads();
+    if (!s_state) {
+        for (int v = blockIdx.x; v < 2 * A.npart; v += gridDim.x) {
+            const bool two = v >= A.npart;
+            zmul_body(A.G, A.stride, A.rowb, two ? A.Sp2 : A.Sp, A.k, two ? A.bSp2 : A.bSp, -1.0, A.u64,
+                      A.v64, A.used, A.y64, A.r64, two ? A.rc64_2 : A.rc64, two ? A.partials2 : A.partials,
+                      A.n_pad, A.p, A.zc, two ? v - A.npart : v);
         }
         if (!grid_sync(T)) return tail_stop(A);
-        if (tid == 0) s_state = *(volatile int32_t *)&sc->done;
-        __syncthreads();
-        if (s_state) break;
-        for (int vb = blockIdx.x; vb < A.npart; vb += gridDim.x)
-            zmul_body(A.G, A.stride, A.rowb, A.Sp, A.k, A.bSp, -1.0, A.u64, A.v64, A.used, A.y64,
-                      A.r64, A.rc64, A.partials, A.n_pad, A.p, A.zc, vb);
-        if (!grid_sync(T)) return tail_stop(A);
-        if (b0) decide_body(sc, A.partials, A.npart, A.S, A.bS, A.Sp, A.bSp, TraceDev{});
+        if (b0) {
+            __shared__ int s_second;
+            decide_body(sc, A.partials, A.npart, A.S, A.bS, A.Sp, A.bSp, TraceDev{});
+            __syncthreads();
+            if (tid == 0) {
+                s_second = sc->retry && !sc->done && sc->bt_last == 1;
+                if (s_second) {                      // the second candidate is the shrunk step
+                    sc->changed = T->spec.changed;
+                    sc->dd = T->spec.dd;
+                    sc->bb = T->spec.bb;
+                }
+            }
+            __syncthreads();
+            if (s_second) {
+                decide_body(sc, A.partials2, A.npart, A.S, A.bS, A.Sp2, A.bSp2, TraceDev{});
+                __syncthreads();
+                if (tid == 0) T->acc2 = !sc->retry;
+            }
+        }
         if (!grid_sync(T)) return tail_stop(A);
         if (tid == 0)
             s_state = (*(volatile int32_t *)&sc->done ? 1 : 0) | (*(volatile int32_t *)&sc->retry ? 2 : 0);
         __syncthreads();
-        if ((s_state & 1) || !(s_state & 2)) break;
+        // later attempts: projection (block 0), residual (all), decision (block 0)
+        while (!(s_state & 1) && (s_state & 2)) {
+            if (b0) {
+                MergeArgs M;
+                M.g = A.g;
+                M.S = A.S;
+                M.bS = A.bS;
+                M.cand = A.cand;
+                M.K = A.K;
+                M.partials = A.partials;
+                M.npart = A.npart;
+                M.first = 0;
+                M.skip = nullptr;
+                M.Sp = A.Sp;
+                M.bSp = A.bSp;
+                M.sc = sc;
+                merge_body<MergeSharedT<kTailKM>>(M);
+            }
+            if (!grid_sync(T)) return tail_stop(A);
+            for (int vb = blockIdx.x; vb < A.npart; vb += gridDim.x)
+                zmul_body(A.G, A.stride, A.rowb, A.Sp, A.k, A.bSp, -1.0, A.u64, A.v64, A.used, A.y64,
+                          A.r64, A.rc64, A.partials, A.n_pad, A.p, A.zc, vb);
+            if (!grid_sync(T)) return tail_stop(A);
+            if (b0) decide_body(sc, A.partials, A.npart, A.S, A.bS, A.Sp, A.bSp, TraceDev{});
+            if (!grid_sync(T)) return tail_stop(A);
+            if (tid == 0)
+                s_state = (*(volatile int32_t *)&sc->done ? 1 : 0) | (*(volatile int32_t *)&sc->retry ? 2 : 0);
+            __syncthreads();
+        }
     }
 
     // E: the accepted residual, centred, and the next pass's limb image
@@ -228,8 +290,9 @@ __global__ void __launch_bounds__(kTailThreads) k_tail(const __grid_constant__ T
     __syncthreads();
     if (!s_state) {
         const int64_t nthr = (int64_t)gridDim.x * blockDim.x;
+        const double *acc = *(volatile int *)&T->acc2 ? A.rc64_2 : A.rc64;   // the accepted residual
         for (int64_t i = (int64_t)blockIdx.x * blockDim.x + tid; i < A.n_pad; i += nthr)
-            center_elem(A.rc64, A.r64, A.used, i, sc, A.r32);
+            center_elem(acc, A.r64, A.used, i, sc, A.r32);
         if (!grid_sync(T)) return tail_stop(A);
         for (int64_t t = (int64_t)blockIdx.x * blockDim.x + tid; t < 1024; t += nthr) {
             float m = 0.0f;
@@ -293,13 +356,17 @@ bool fused_supported(const iht_dataset *ds, int k, int impl)
 void free_fused(Workspace *ws)
 {
     if (ws->fused_exec) cudaGraphExecDestroy(ws->fused_exec);
-    if (ws->tail) cudaFree(ws->tail);
+    void *ptrs[] = {ws->tail, ws->Sp2, ws->bSp2, ws->rc64_2, ws->partials2};
+    for (void *x : ptrs)
+        if (x) cudaFree(x);
     ws->fused_exec = nullptr;
     ws->tail = nullptr;
+    ws->Sp2 = nullptr;
+    ws->bSp2 = ws->rc64_2 = ws->partials2 = nullptr;
 }
 
-// Blocks of the cooperative launch: as many as are resident at once, at most
-// two per SM (more only lengthen the barriers).
+// Blocks of the cooperative launch: one per SM when it fits (more blocks
+// lengthen the barriers and multiply the histogram's global atomics).
 static int tail_grid(iht_dataset *ds)
 {
     static thread_local int cfg_dev = -1, per_sm = 0;
@@ -311,7 +378,7 @@ static int tail_grid(iht_dataset *ds)
             per_sm = 0;
         cfg_dev = ds->ctx->device;
     }
-    return std::min(per_sm, 2) * ds->ctx->num_sms;
+    return std::min(per_sm, 1) * ds->ctx->num_sms;
 }
 
 // Captures the solve loop: while (condition) { fused iteration; missing-call
@@ -414,7 +481,13 @@ int run_fused_solve(iht_dataset *ds, int k, int K, int impl)
     cudaStream_t s = ds->ctx->stream;
     const int grid = tail_grid(ds);
     if (grid < 1) return IHT_EAGAIN;
-    if (!ws->tail) IHT_CUDA(dev_malloc(&ws->tail, sizeof(TailWork)));
+    if (!ws->tail) {
+        IHT_CUDA(dev_malloc(&ws->tail, sizeof(TailWork)));
+        IHT_CUDA(dev_malloc(&ws->Sp2, sizeof(int32_t) * kTailKM));
+        IHT_CUDA(dev_malloc(&ws->bSp2, sizeof(double) * kTailKM));
+        IHT_CUDA(dev_malloc(&ws->rc64_2, sizeof(double) * ds->n_pad));
+        IHT_CUDA(dev_malloc(&ws->partials2, sizeof(double) * 3 * kPartials));
+    }
     uint8_t *bimg = nullptr;
     TcParams *prm = nullptr;
     int64_t nlim = 0;
@@ -433,8 +506,12 @@ int run_fused_solve(iht_dataset *ds, int k, int K, int impl)
     a.S = ws->S;
     a.Sp = ws->Sp;
     a.cand = ws->cand;
+    a.Sp2 = ws->Sp2;
     a.bS = ws->bS;
     a.bSp = ws->bSp;
+    a.bSp2 = ws->bSp2;
+    a.rc64_2 = ws->rc64_2;
+    a.partials2 = ws->partials2;
     a.coef = ws->coef;
     a.u64 = ws->u64;
     a.v64 = ws->v64;
