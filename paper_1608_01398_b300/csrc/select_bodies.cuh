@@ -216,4 +216,74 @@ __device__ __forceinline__ void sel_finish(const float *keys, int64_t p, const S
     sort_idx_body(out, (int)K);
 }
 
+// The same result as sel_finish for a block with few threads: with more than
+// 256 candidates, a histogram of bits 19..10 of the boundary bin's keys finds
+// the sub-bin holding the K-th key; only the keys above it and in it (every key
+// that can be among the K, ties included) are sorted.  sk: room for kSelCap
+// words plus `extra` words (the kept keys are compacted there); when they do
+// not fit, all candidates are sorted as in sel_finish.
+__device__ __forceinline__ void sel_finish_narrow(const float *keys, int64_t p, const SelState *st,
+                                                  const unsigned long long *cand, uint32_t ncand,
+                                                  int32_t *out, uint32_t K, unsigned long long *sk,
+                                                  int extra, uint32_t *wsum)
+{
+    __shared__ uint32_t h[1024];
+    __shared__ uint32_t res[3];
+    if (ncand <= 256u || ncand > (uint32_t)kSelCap) {
+        sel_finish(keys, p, st, cand, ncand, out, K, sk, wsum);
+        return;
+    }
+    const uint32_t bin = st->prefix >> 20;
+    for (int b = threadIdx.x; b < 1024; b += blockDim.x) h[b] = 0;
+    for (int i = threadIdx.x; i < (int)ncand; i += blockDim.x) sk[i] = __ldcg(&cand[i]);
+    __syncthreads();
+    for (int i = threadIdx.x; i < (int)ncand; i += blockDim.x) {
+        const uint32_t key = (uint32_t)(sk[i] >> 32);
+        if ((key >> 20) == bin) atomicAdd(&h[(key >> 10) & 0x3ffu], 1u);
+    }
+    __syncthreads();
+    sel_find(h, 1024, st->need, wsum, res);
+    const uint32_t lo = (bin << 20) | (res[0] << 10);          // keys >= lo can be among the K
+    // compact the keys >= lo after the candidates (order kept: a block-wide scan)
+    unsigned long long *kept = sk + kSelCap;
+    uint32_t nk = 0;
+    for (int base = 0; base < (int)ncand; base += blockDim.x) {
+        const int i = base + threadIdx.x;
+        const uint32_t f = (i < (int)ncand && (uint32_t)(sk[i] >> 32) >= lo) ? 1u : 0u;
+        uint32_t tot = 0;
+        const uint32_t r = sel_excl_scan(f, wsum, &tot);
+        if (f && nk + r < (uint32_t)extra) kept[nk + r] = sk[i];
+        nk += tot;
+    }
+    __syncthreads();
+    if (nk > (uint32_t)extra) {                                 // no room: sort them all
+        sel_finish(keys, p, st, cand, ncand, out, K, sk, wsum);
+        return;
+    }
+    int P = 1;
+    while (P < (int)nk) P <<= 1;
+    for (int i = (int)nk + threadIdx.x; i < P; i += blockDim.x) kept[i] = 0ull;
+    __syncthreads();
+    for (int size = 2; size <= P; size <<= 1) {                 // bitonic, descending
+        for (int stride = size >> 1; stride > 0; stride >>= 1) {
+            for (int i = threadIdx.x; i < P; i += blockDim.x) {
+                const int jx = i ^ stride;
+                if (jx > i) {
+                    const bool up = (i & size) == 0;
+                    const unsigned long long a = kept[i], b = kept[jx];
+                    if ((a < b) == up) {
+                        kept[i] = b;
+                        kept[jx] = a;
+                    }
+                }
+            }
+            __syncthreads();
+        }
+    }
+    for (int i = threadIdx.x; i < (int)K; i += blockDim.x)
+        out[i] = (int32_t)(~(uint32_t)(kept[i] & 0xffffffffull));
+    __syncthreads();
+    sort_idx_body(out, (int)K);
+}
+
 }  // namespace iht

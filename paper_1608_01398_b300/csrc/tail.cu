@@ -24,6 +24,7 @@ namespace iht {
 
 constexpr int kTailThreads = kZmulThreads;    // one 128-sample block of the sparse product per pass
 constexpr int kTailKM = 256;                  // largest k of the fused path
+constexpr int kTailKept = 1024;               // candidates the selection's narrow finish sorts
 constexpr uint32_t kBarSpin = 1u << 22;       // bounded barrier waits (polls; sleeps up to 512 ns each)
 
 struct TailWork {                     // zeroed before every solve
@@ -180,8 +181,8 @@ __global__ void __launch_bounds__(kTailThreads) k_tail(const __grid_constant__ T
     // the selection scratch; the other blocks form Z_S g_S
     if (b0) {
         const uint32_t ncand = T->st.ncand;
-        sel_finish(A.g, A.P, &T->st, T->cand, ncand, A.cand, (uint32_t)A.K,
-                   reinterpret_cast<unsigned long long *>(smem_raw), wsum);
+        sel_finish_narrow(A.g, A.P, &T->st, T->cand, ncand, A.cand, (uint32_t)A.K,
+                          reinterpret_cast<unsigned long long *>(smem_raw), kTailKept, wsum);
         for (int b = tid; b < kSelBins; b += blockDim.x) T->hist[b] = 0;
         if (tid == 0) T->st.n_gt = 0;
     }
@@ -291,19 +292,21 @@ __global__ void __launch_bounds__(kTailThreads) k_tail(const __grid_constant__ T
     if (!s_state) {
         const int64_t nthr = (int64_t)gridDim.x * blockDim.x;
         const double *acc = *(volatile int *)&T->acc2 ? A.rc64_2 : A.rc64;   // the accepted residual
-        for (int64_t i = (int64_t)blockIdx.x * blockDim.x + tid; i < A.n_pad; i += nthr)
-            center_elem(acc, A.r64, A.used, i, sc, A.r32);
-        if (!grid_sync(T)) return tail_stop(A);
+        // thread t of the limb kernel's 1024 centres the samples i = t mod 1024 and
+        // forms their max |r| and sum of r in that kernel's order
         for (int64_t t = (int64_t)blockIdx.x * blockDim.x + tid; t < 1024; t += nthr) {
             float m = 0.0f;
-            double acc = 0.0;
-            for (int64_t i = t; i < A.nlim; i += 1024) {
-                const float r = A.r32[i];
-                m = fmaxf(m, fabsf(r));
-                acc += (double)r;
+            double sum = 0.0;
+            for (int64_t i = t; i < A.n_pad; i += 1024) {
+                center_elem(acc, A.r64, A.used, i, sc, A.r32);
+                if (i < A.nlim) {
+                    const float r = A.r32[i];
+                    m = fmaxf(m, fabsf(r));
+                    sum += (double)r;
+                }
             }
             T->part_m[t] = m;
-            T->part_acc[t] = acc;
+            T->part_acc[t] = sum;
         }
         if (!grid_sync(T)) return tail_stop(A);
         float m = 0.0f;
@@ -344,7 +347,7 @@ __global__ void __launch_bounds__(kTailThreads) k_tail(const __grid_constant__ T
 
 static size_t tail_smem()
 {
-    return std::max(sizeof(MergeSharedT<kTailKM>), sizeof(unsigned long long) * kSelCap);
+    return std::max(sizeof(MergeSharedT<kTailKM>), sizeof(unsigned long long) * (kSelCap + kTailKept));
 }
 
 bool fused_supported(const iht_dataset *ds, int k, int impl)
