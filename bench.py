@@ -192,6 +192,28 @@ def run_oracle_sample(cfg: int, max_iter: int, pn=None, bed=None, y=None):
     return f.iterations, dt, oracle.max_threads()
 
 
+def oracle_parity(fo, beta, support, iterations, status, gtol=1e-5):
+    """The GPU solve against the oracle's solve of the same problem: iterations
+    the oracle certifies (the k-th and (k+1)-th |w| further apart than the FP32
+    gradient error can move them, no backtracking decision within 1e-3 of its
+    threshold) before its first tie-ambiguous one, the tie-ambiguous exclusion
+    rate, and the final support and beta."""
+    tr = fo.trace
+    lead = fo.iterations
+    for t in range(fo.iterations):
+        if not (tr["gap"][t] > 10 * gtol * tr["wscale"][t] and not (tr["margin"][t] < 1e-3)):
+            lead = t
+            break
+    beta = np.asarray(beta)
+    rel = float(np.max(np.abs(beta - fo.beta)) / max(np.max(np.abs(fo.beta)), 1e-300))
+    return {"oracle_iterations": int(fo.iterations), "certified_iterations": int(lead),
+            "tie_ambiguous_exclusion_rate": 1.0 - lead / max(fo.iterations, 1),
+            "same_iterations": int(iterations) == int(fo.iterations),
+            "same_status": int(status) == int(fo.status),
+            "support_equal": bool(np.array_equal(np.sort(np.asarray(support)), fo.support)),
+            "beta_max_rel_err": rel, "beta_tolerance": 1e-4}
+
+
 def reference_arm(args):
     rank, _, world = dist_env()
     if rank != 0:
@@ -355,11 +377,17 @@ def ours_arm(args):
             "pass_shapes": iht.tuning_summary().strip().splitlines(),
         }
         if not args.no_cpu_baseline and world == 1:
-            iters, secs, threads = run_oracle_sample(cfg, args.oracle_iters, pn, bed, y)
+            import oracle
+            G = oracle.Geno.from_bed(bed, pn.n, pn.p)
+            t0 = time.perf_counter()
+            fo = oracle.iht(G, y, k, tol=c["tol"], max_iter=c["max_iter"], trace=True)
+            secs = time.perf_counter() - t0
+            threads = oracle.max_threads()
             out["cpu_baseline"] = {
-                "value": iters / secs, "unit": "iter/s", "cores": threads, "kind": "oracle",
-                "sample": f"FP64 oracle IHT on {c['name']}, first {iters} iterations "
-                          f"(incl. setup), {secs:.1f}s"}
+                "value": fo.iterations / secs, "unit": "iter/s", "cores": threads, "kind": "oracle",
+                "sample": f"FP64 oracle IHT on {c['name']}: one full solve from beta = 0 "
+                          f"({fo.iterations} iterations incl. set-up), {secs:.1f}s"}
+            out["parity"] = oracle_parity(fo, beta_host, supp_host, r.iterations, r.status)
             # the same oracle on one host thread (its column-parallel loops serial)
             import oracle
             oracle.set_threads(1)
@@ -370,11 +398,39 @@ def ours_arm(args):
             out["cpu_baseline"]["single_thread"] = {
                 "value": i1 / s1, "unit": "iter/s", "cores": 1,
                 "sample": f"first {i1} iteration (incl. setup), {s1:.1f}s"}
+        if cfg == 2 and world == 1 and not args.no_extra:
+            del ds, ctx
+            torch.cuda.empty_cache()
+            out["batched"] = sub_run(3, ["--steps", "3", "--warmup", "1"], BATCHED_KEYS)
+            out["serving"] = sub_run(4, ["--steps", "1", "--warmup", "1"], SERVING_KEYS)
         print(json.dumps(out), flush=True)
-    del ds, ctx
     if world > 1:
         torch.distributed.destroy_process_group()
     return 0
+
+
+BATCHED_KEYS = ("metric", "value", "unit", "ms_per_step", "config", "plain", "speedup_vs_plain",
+                "roofline", "e2e", "model_selection", "clocks", "graph_replays_per_step")
+SERVING_KEYS = ("metric", "value", "unit", "ms_per_step", "config", "plain", "speedup_vs_plain",
+                "poisson", "latency_ms_all_queued", "e2e", "server", "clocks")
+
+
+def sub_run(config: int, extra: list, keys) -> dict:
+    """The batched (config 3) or serving (config 4) workload in a child process of
+    this bench (same GPU, run after the single-solve line's timed region); its
+    JSON line, reduced to the given keys."""
+    cmd = [sys.executable, os.path.abspath(__file__), "--config", str(config), "--no-cpu-baseline",
+           *extra]
+    t0 = time.perf_counter()
+    r = subprocess.run(cmd, capture_output=True, text=True, cwd=ROOT)
+    lines = [l for l in r.stdout.splitlines() if l.startswith("{")]
+    if r.returncode != 0 or not lines:
+        return {"error": f"exit {r.returncode}: {r.stderr.strip().splitlines()[-1:] }"}
+    d = json.loads(lines[-1])
+    sub = {k: d[k] for k in keys if k in d}
+    sub["command"] = " ".join(["python bench.py", "--config", str(config), "--no-cpu-baseline", *extra])
+    sub["wall_s"] = time.perf_counter() - t0
+    return sub
 
 
 MR_PEAK_KEY = "bf16_tflops_sustained"
@@ -545,9 +601,11 @@ def cv_arm(args):
         e2e_value = weak_rate(allv, 2, 3)
         peak, peak_kind = measured_tensor_peak()
         n_k = 4 * ((((n + 3) // 4) + 15) // 16) * 16     # samples of the contraction (K-steps x 16)
-        flops = 2.0 * n * p * MR_LIMBS * cols              # X0^T [limbs of r] over all passes
-        achieved = flops / (grad_ms / 1e3) / 1e12 if grad_ms > 0 else None
-        solve_tflops = achieved / MR_LIMBS if achieved else None
+        # the method's flops: 2 n p per residual column, x 2 for the two-part residual
+        # the scope counts (the pass computes five E4M3 limb columns per residual column)
+        method_flops = 2.0 * n * p * 2 * cols
+        achieved = method_flops / (grad_ms / 1e3) / 1e12 if grad_ms > 0 else None
+        limb_tflops = (2.0 * n * p * MR_LIMBS * cols) / (grad_ms / 1e3) / 1e12 if grad_ms > 0 else None
         ktot = sum(c["ks"]) * c["folds"]
         h2d = sum(8 * t.size * len(c["ks"]) + 4 * t.size for t in train)   # y per solve, rows per fold
         out = {
@@ -578,9 +636,11 @@ def cv_arm(args):
                          "traffic_first_launch": K2_TRAFFIC_FIRST_LAUNCH_BYTES,
                          "kernel": "multi-column gradient pass (k_grad_mrhs)",
                          "peak_source": peak_kind,
-                         "algorithmic_flops": "2 n p per residual limb column, five E4M3 limb "
-                                              "columns per solve column",
-                         "solve_column_tflops": solve_tflops,
+                         "algorithmic_flops": "2 n p x 2 per residual column and pass (the "
+                                              "two-part residual); launch durations by CUDA events",
+                         "limb_column_tflops": limb_tflops,
+                         "limb_columns_note": "the pass runs five E4M3 limb columns per residual "
+                                              "column; limb_column_tflops counts those",
                          "columns_total": cols, "launches": grad_n,
                          "ms_per_launch": grad_ms / max(grad_n, 1), "contraction_samples": n_k},
             "e2e": {"value": e2e_value, "unit": "solves/s", "h2d_bytes_per_step": int(h2d),
@@ -1043,6 +1103,8 @@ def main():
     ap.add_argument("--grad-impl", type=int, default=0, choices=[0, 1, 2])
     ap.add_argument("--oracle-iters", type=int, default=10)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extra", action="store_true",
+                    help="single-solve line only (no batched / serving sub-runs)")
     args = ap.parse_args()
     if args.steps is None:
         args.steps = {3: 3, 4: 1, 5: 1, 6: 1}.get(args.config, 50)
