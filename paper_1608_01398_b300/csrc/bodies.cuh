@@ -33,6 +33,7 @@ __device__ __forceinline__ void warp_partials(const double *partials, int npart,
     s = 0.0;
     s2 = 0.0;
     d2 = 0.0;
+#pragma unroll 2
     for (int b = lane; b < npart; b += 32) {
         s += partials[3 * b];
         s2 += partials[3 * b + 1];
@@ -47,20 +48,18 @@ __device__ __forceinline__ void warp_partials(const double *partials, int npart,
 // the observed calls (Z[:, cols] coef, Sec. 2.3.2-2.3.3), on used rows (0
 // elsewhere); per-block sums of out, out^2 and (out - prev)^2 (0 without
 // prev) go to partials[3 b .. 3 b + 2].  One thread per sample, 128 samples
-// per block (smaller blocks only multiply the partial triples every consumer
-// sums); each column's three possible terms a (x - u) for x = 0, 1, 2 are
-// staged in shared memory kZmulChunk columns at a time, so a term costs one
-// FP64 add, added in column order.  The product is a chain of dependent steps
-// (global loads, FP64 adds, block reductions) on a few warps per SM, so the
-// body shortens the chain: the row values (used, base, prev) are requested
-// first; a thread loads the genotype bytes of a chunk's first kZmulFirst
-// columns (column index, then byte) while the block stages the terms, and the
-// rest kZmulBatch columns at a time; the three block sums share one
-// reduction.
+// per block (every caller launches kZmulThreads threads; smaller blocks would
+// only multiply the partial triples every consumer sums).  Per chunk of
+// kZmulChunk columns the block stages in shared memory each column's three
+// possible terms a (x - u) for x = 0, 1, 2 and the block's 32 genotype bytes
+// of the column (two 16-byte loads, one per thread, all in flight at once);
+// a thread then adds its terms in column order, one shared-memory lookup and
+// one FP64 add each.  The body runs once per pass of a launch that is itself
+// run once per iteration, so its code is fetched cold each time: the loops
+// stay rolled (a few lines of code) rather than unrolled per column.
 constexpr int kZmulChunk = 256;
-constexpr int kZmulThreads = 128;           // largest block
-constexpr int kZmulFirst = 64;
-constexpr int kZmulBatch = 16;
+constexpr int kZmulThreads = 128;           // the block every caller launches
+constexpr int kZmulBytes = kZmulThreads / 4;   // genotype bytes of a block per column
 
 // vb: the 128-sample block to compute (blockIdx.x in a kernel of its own; a
 // fused kernel passes its own index).  The column list, coefficients, base,
@@ -79,11 +78,12 @@ __device__ __forceinline__ void zmul_body(const uint8_t *__restrict__ G, int64_t
 {
     __shared__ double red[3 * (kZmulThreads / 32)];
     __shared__ double term[kZmulChunk][4];     // terms for codes 00, 01 (missing: 0), 10, 11
-    __shared__ const uint8_t *srow[kZmulChunk];
-    const int64_t i = (int64_t)vb * blockDim.x + threadIdx.x;
-    const int64_t byte = i >> 2;
-    const int shift = 2 * (int)(i & 3);
-    const bool inb = i < n_pad && byte < rowb;
+    __shared__ __align__(16) uint8_t gtile[kZmulChunk][kZmulBytes];
+    const int64_t i = (int64_t)vb * kZmulThreads + threadIdx.x;
+    const int64_t b0 = (int64_t)vb * kZmulBytes;     // first byte of the block in a row (< stride)
+    const int bl = threadIdx.x >> 2;                   // this sample's byte in the tile
+    const int shift = 2 * (int)(threadIdx.x & 3);
+    const bool inb = i < n_pad && b0 + bl < rowb;
     const bool in = i < n_pad;
     const int32_t ui = in ? used[i] : 0;
     const double bi = in && base ? base[i] : 0.0;
@@ -94,50 +94,36 @@ __device__ __forceinline__ void zmul_body(const uint8_t *__restrict__ G, int64_t
     if (zc)
         while (m > 0 && cols[m - 1] >= psnp) --m;
     double acc = 0.0;
+#pragma unroll 1
     for (int c0 = 0; c0 < m; c0 += kZmulChunk) {
         const int mc = min(kZmulChunk, m - c0);
-        const int mf = min(mc, kZmulFirst);
-        uint32_t bf[kZmulFirst];
-        if (inb) {
-#pragma unroll
-            for (int q = 0; q < kZmulFirst; ++q)
-                if (q < mf) bf[q] = __ldg(G + (int64_t)cols[c0 + q] * stride + byte);
-        }
-        __syncthreads();
-        for (int c = threadIdx.x; c < mc; c += blockDim.x) {
+        __syncthreads();                           // the previous chunk's reads are done
+        // thread t: half t & 1 of column t >> 1's 32 bytes (rows are 128-byte
+        // aligned and b0 + 32 <= stride, so the loads stay inside the row);
+        // the even thread also stages the column's terms
+#pragma unroll 2
+        for (int t = threadIdx.x; t < 2 * mc; t += kZmulThreads) {
+            const int c = t >> 1;
             const int col = cols[c0 + c];
-            const double a = sign * coef[c0 + c] * v64[col];
-            const double b = a * u64[col];
-            term[c][0] = a * 0.0 - b;
-            term[c][1] = 0.0;
-            term[c][2] = a * 1.0 - b;
-            term[c][3] = a * 2.0 - b;
-            srow[c] = G + (int64_t)col * stride;
+            const uint4 *src = reinterpret_cast<const uint4 *>(G + (int64_t)col * stride + b0) + (t & 1);
+            reinterpret_cast<uint4 *>(gtile[c])[t & 1] = __ldg(src);
+            if (!(t & 1)) {
+                const double a = sign * coef[c0 + c] * v64[col];
+                const double b = a * u64[col];
+                term[c][0] = a * 0.0 - b;
+                term[c][1] = 0.0;
+                term[c][2] = a * 1.0 - b;
+                term[c][3] = a * 2.0 - b;
+            }
         }
         __syncthreads();
         if (inb) {
-#pragma unroll
-            for (int q = 0; q < kZmulFirst; ++q)
-                if (q < mf) acc += term[q][(bf[q] >> shift) & 3u];
-            int c = mf;
-            for (; c + kZmulBatch <= mc; c += kZmulBatch) {
-                uint32_t b[kZmulBatch];
-#pragma unroll
-                for (int q = 0; q < kZmulBatch; ++q) b[q] = __ldg(srow[c + q] + byte);
-#pragma unroll
-                for (int q = 0; q < kZmulBatch; ++q) acc += term[c + q][(b[q] >> shift) & 3u];
-            }
-            for (; c + 4 <= mc; c += 4) {
-                uint32_t b[4];
-#pragma unroll
-                for (int q = 0; q < 4; ++q) b[q] = __ldg(srow[c + q] + byte);
-#pragma unroll
-                for (int q = 0; q < 4; ++q) acc += term[c + q][(b[q] >> shift) & 3u];
-            }
-            for (; c < mc; ++c) acc += term[c][((uint32_t)__ldg(srow[c] + byte) >> shift) & 3u];
+#pragma unroll 4
+            for (int c = 0; c < mc; ++c) acc += term[c][((uint32_t)gtile[c][bl] >> shift) & 3u];
         }
     }
     if (in)
+#pragma unroll 1
         for (int c = m; c < mall; ++c) acc += (sign * coef[c]) * zc[(int64_t)(cols[c] - psnp) * n_pad + i];
     double o = 0.0, d = 0.0;
     if (in) {
@@ -222,6 +208,7 @@ template <typename SH> __device__ void sort_by_w(SH &sh, int nU)
 {
     int P = 1;
     while (P < nU) P <<= 1;
+#pragma unroll 1
     for (int i = threadIdx.x; i < P; i += blockDim.x) {
         if (i < nU) {
             sh.skey[i] = (unsigned long long)__double_as_longlong(fabs(sh.uw[i]));
@@ -232,8 +219,11 @@ template <typename SH> __device__ void sort_by_w(SH &sh, int nU)
         }
     }
     __syncthreads();
+#pragma unroll 1
     for (int size = 2; size <= P; size <<= 1) {
+#pragma unroll 1
         for (int st = size >> 1; st > 0; st >>= 1) {
+#pragma unroll 1
             for (int i = threadIdx.x; i < P; i += blockDim.x) {
                 const int j = i ^ st;
                 if (j > i) {
@@ -262,10 +252,12 @@ template <typename SH = MergeShared> __device__ __forceinline__ void merge_body(
     SH &sh = *reinterpret_cast<SH *>(smem_raw);
     Scalars *sc = A.sc;
     const int k = sc->k;
+#pragma unroll 1
     for (int i = threadIdx.x; i < k; i += blockDim.x) {
         sh.sS[i] = A.S[i];
         sh.sbS[i] = A.bS[i];
     }
+#pragma unroll 1
     for (int i = threadIdx.x; i < A.K; i += blockDim.x) sh.scand[i] = A.cand[i];
 
     double den = 0.0;
@@ -292,6 +284,7 @@ template <typename SH = MergeShared> __device__ __forceinline__ void merge_body(
                 sh.stop = 1;
             } else {
                 sc->mu = num / den;
+#pragma unroll 1
                 for (int q = 0; q < A.shrinks; ++q) sc->mu = sc->mu / sc->kappa;   // as the decision shrinks it
             }
         }
@@ -302,6 +295,7 @@ template <typename SH = MergeShared> __device__ __forceinline__ void merge_body(
 
     // U = C (ascending) followed by S \ C (in S order)
     const int K = A.K;
+#pragma unroll 1
     for (int b = threadIdx.x; b < K; b += blockDim.x) {
         const int32_t j = sh.scand[b];
         const int pos = lower_bound_i32(sh.sS, k, j);
@@ -316,6 +310,7 @@ template <typename SH = MergeShared> __device__ __forceinline__ void merge_body(
     {
         const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
         int base = 0;
+#pragma unroll 1
         for (int a0 = 0; a0 < k; a0 += blockDim.x) {
             const int a = a0 + threadIdx.x;
             int32_t j = 0;
@@ -329,6 +324,7 @@ template <typename SH = MergeShared> __device__ __forceinline__ void merge_body(
             if (lane == 0) sh.wsum[wid] = __popc(bal);
             __syncthreads();
             int off = base, tot = 0;
+#pragma unroll 1
             for (int w = 0; w < nw; ++w) {
                 if (w < wid) off += sh.wsum[w];
                 tot += sh.wsum[w];
@@ -349,6 +345,7 @@ template <typename SH = MergeShared> __device__ __forceinline__ void merge_body(
     __syncthreads();
     const int nU = K + sh.nS_extra;
 
+#pragma unroll 1
     for (int u = threadIdx.x; u < nU; u += blockDim.x) {
         sh.uw[u] = __dadd_rn(sh.ubeta[u], __dmul_rn(mu, sh.ug[u]));
         sh.skey[u] = (unsigned long long)__double_as_longlong(fabs(sh.uw[u]));
@@ -359,6 +356,7 @@ template <typename SH = MergeShared> __device__ __forceinline__ void merge_body(
         // S+ by rank: u is in S+ iff fewer than k entries come before it
         // (|w| descending, index ascending); every thread reads the same v
         // at the same time (shared-memory broadcast)
+#pragma unroll 1
         for (int u = threadIdx.x; u < nU; u += blockDim.x) {
             const unsigned long long ku = sh.skey[u];
             const int32_t iu = sh.uidx[u];
@@ -369,8 +367,10 @@ template <typename SH = MergeShared> __device__ __forceinline__ void merge_body(
         __syncthreads();
     } else {
         sort_by_w(sh, nU);
+#pragma unroll 1
         for (int u = threadIdx.x; u < nU; u += blockDim.x) sh.inSp[u] = 0;
         __syncthreads();
+#pragma unroll 1
         for (int r = threadIdx.x; r < k; r += blockDim.x) sh.inSp[sh.spos[r]] = 1;
         __syncthreads();
     }
@@ -380,6 +380,7 @@ template <typename SH = MergeShared> __device__ __forceinline__ void merge_body(
     int kept = 0;
     double dd = 0.0, bb = 0.0;
     if (threadIdx.x < 32) {
+#pragma unroll 1
         for (int u = threadIdx.x; u < nU; u += 32) {
             kept += sh.inS[u] && sh.inSp[u];
             const double d = (sh.inSp[u] ? sh.uw[u] : 0.0) - sh.ubeta[u];
@@ -394,6 +395,7 @@ template <typename SH = MergeShared> __device__ __forceinline__ void merge_body(
     // S+ in index order with beta+
     if (small) {
         // position of u among the members of S+ = members with a lower index
+#pragma unroll 1
         for (int u = threadIdx.x; u < nU; u += blockDim.x) {
             if (!sh.inSp[u]) continue;
             const int32_t iu = sh.uidx[u];
@@ -410,8 +412,10 @@ template <typename SH = MergeShared> __device__ __forceinline__ void merge_body(
         return;
     }
     __syncthreads();
+#pragma unroll 1
     for (int r = threadIdx.x; r < SH::kSort; r += blockDim.x) sh.skey[r] = ~0ull;
     __syncthreads();
+#pragma unroll 1
     for (int r = threadIdx.x; r < k; r += blockDim.x) {
         const int u = sh.spos[r];
         sh.skey[r] = ((unsigned long long)(uint32_t)sh.uidx[u] << 32) | (uint32_t)u;
@@ -420,8 +424,11 @@ template <typename SH = MergeShared> __device__ __forceinline__ void merge_body(
     {
         int P = 1;
         while (P < k) P <<= 1;
+#pragma unroll 1
         for (int size = 2; size <= P; size <<= 1)
+#pragma unroll 1
             for (int st = size >> 1; st > 0; st >>= 1) {
+#pragma unroll 1
                 for (int i = threadIdx.x; i < P; i += blockDim.x) {
                     const int j = i ^ st;
                     if (j > i) {
@@ -433,6 +440,7 @@ template <typename SH = MergeShared> __device__ __forceinline__ void merge_body(
                 __syncthreads();
             }
     }
+#pragma unroll 1
     for (int r = threadIdx.x; r < k; r += blockDim.x) {
         const int u = (int)(uint32_t)(sh.skey[r] & 0xffffffffull);
         A.Sp[r] = sh.uidx[u];
@@ -505,6 +513,7 @@ __device__ __forceinline__ void decide_body(Scalars *sc, const double *partials,
     }
     if (sc->htp) return;
     const int it = sc->iter;
+#pragma unroll 1
     for (int c = threadIdx.x; c < k; c += blockDim.x) {
         S[c] = Sp[c];
         bS[c] = bSp[c];
@@ -551,17 +560,5 @@ __device__ __forceinline__ void center_body(const double *__restrict__ src, doub
     if (src != r64) r64[i] = v;
     r32[i] = used[i] ? (float)(v - mean) : 0.0f;
 }
-
-// The same for sample i (a fused kernel's own indexing); src may have been
-// written earlier in the same launch.
-__device__ __forceinline__ void center_elem(const double *src, double *r64, const int32_t *used,
-                                            int64_t i, const Scalars *sc, float *r32)
-{
-    const double mean = sc->sum_r / (double)sc->n_rows;
-    const double v = src[i];
-    if (src != r64) r64[i] = v;
-    r32[i] = used[i] ? (float)(v - mean) : 0.0f;
-}
-
 
 }  // namespace iht

@@ -517,6 +517,7 @@ __device__ __forceinline__ void gather_gS_body(const float *__restrict__ g,
 {
     if (threadIdx.x >= 32) return;
     double s = 0.0;
+#pragma unroll 2
     for (int c = threadIdx.x; c < k; c += 32) {
         const double x = (double)g[S[c]];
         coef[c] = x;

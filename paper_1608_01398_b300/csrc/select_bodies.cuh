@@ -51,8 +51,10 @@ __device__ __forceinline__ void sel_find(const uint32_t *h, int nbins, uint32_t 
     const int t = threadIdx.x;
     if (t == 0) res[0] = res[1] = res[2] = 0;
     uint32_t tot = 0;
+#pragma unroll 1
     for (int i = 0; i < per; ++i) tot += h[nbins - 1 - (per * t + i)];
     uint32_t before = sel_excl_scan(tot, wsum);
+#pragma unroll 1
     for (int i = 0; i < per; ++i) {
         const int bin = nbins - 1 - (per * t + i);
         const uint32_t c = h[bin];
@@ -111,11 +113,14 @@ static __device__ void sel_exact_block(const float *__restrict__ keys, int64_t p
         s_cnt = 0;
     }
     __syncthreads();
+#pragma unroll 1
     for (int ps = 0; ps < 2; ++ps) {
         const int shift = ps == 0 ? 10 : 0;
+#pragma unroll 1
         for (int b = tid; b < 1024; b += blockDim.x) h[b] = 0;
         __syncthreads();
         const uint32_t prefix = s_prefix, mask = s_mask;
+#pragma unroll 1
         for (int64_t j = tid; j < p; j += blockDim.x) {
             const uint32_t k = sel_key(keys[j]);
             if ((k & mask) == prefix) atomicAdd(&h[(k >> shift) & 0x3ffu], 1u);
@@ -131,6 +136,7 @@ static __device__ void sel_exact_block(const float *__restrict__ keys, int64_t p
         __syncthreads();
     }
     const uint32_t T = s_prefix, gt = s_gt, need = s_need;
+#pragma unroll 1
     for (int64_t j = tid; j < p; j += blockDim.x) {
         if (sel_key(keys[j]) > T) {
             const uint32_t slot = atomicAdd(&s_cnt, 1u);
@@ -138,6 +144,7 @@ static __device__ void sel_exact_block(const float *__restrict__ keys, int64_t p
         }
     }
     uint32_t taken = 0;
+#pragma unroll 1
     for (int64_t base = 0; base < p && taken < need; base += blockDim.x) {
         const int64_t j = base + tid;
         const uint32_t f = (j < p && sel_key(keys[j]) == T) ? 1u : 0u;
@@ -155,10 +162,14 @@ __device__ __forceinline__ void sort_idx_body(int32_t *idx, int K)
     __shared__ int32_t s[kMaxCand];
     int P = 1;
     while (P < K) P <<= 1;
+#pragma unroll 1
     for (int i = threadIdx.x; i < P; i += blockDim.x) s[i] = i < K ? idx[i] : 0x7fffffff;
     __syncthreads();
+#pragma unroll 1
     for (int size = 2; size <= P; size <<= 1) {
+#pragma unroll 1
         for (int stride = size >> 1; stride > 0; stride >>= 1) {
+#pragma unroll 1
             for (int i = threadIdx.x; i < P; i += blockDim.x) {
                 const int jx = i ^ stride;
                 if (jx > i) {
@@ -173,6 +184,7 @@ __device__ __forceinline__ void sort_idx_body(int32_t *idx, int K)
             __syncthreads();
         }
     }
+#pragma unroll 1
     for (int i = threadIdx.x; i < K; i += blockDim.x) idx[i] = s[i];
 }
 
@@ -191,8 +203,11 @@ __device__ __forceinline__ void sel_finish(const float *keys, int64_t p, const S
         while (P < (int)ncand) P <<= 1;
         for (int i = threadIdx.x; i < P; i += blockDim.x) sk[i] = i < (int)ncand ? __ldcg(&cand[i]) : 0ull;
         __syncthreads();
+#pragma unroll 1
         for (int size = 2; size <= P; size <<= 1) {               // bitonic, descending
+#pragma unroll 1
             for (int stride = size >> 1; stride > 0; stride >>= 1) {
+#pragma unroll 1
                 for (int i = threadIdx.x; i < P; i += blockDim.x) {
                     const int jx = i ^ stride;
                     if (jx > i) {
@@ -207,6 +222,7 @@ __device__ __forceinline__ void sel_finish(const float *keys, int64_t p, const S
                 __syncthreads();
             }
         }
+#pragma unroll 1
         for (int i = threadIdx.x; i < (int)K; i += blockDim.x)
             out[i] = (int32_t)(~(uint32_t)(sk[i] & 0xffffffffull));
         __syncthreads();
@@ -234,9 +250,11 @@ __device__ __forceinline__ void sel_finish_narrow(const float *keys, int64_t p, 
         return;
     }
     const uint32_t bin = st->prefix >> 20;
+#pragma unroll 1
     for (int b = threadIdx.x; b < 1024; b += blockDim.x) h[b] = 0;
     for (int i = threadIdx.x; i < (int)ncand; i += blockDim.x) sk[i] = __ldcg(&cand[i]);
     __syncthreads();
+#pragma unroll 1
     for (int i = threadIdx.x; i < (int)ncand; i += blockDim.x) {
         const uint32_t key = (uint32_t)(sk[i] >> 32);
         if ((key >> 20) == bin) atomicAdd(&h[(key >> 10) & 0x3ffu], 1u);
@@ -247,6 +265,7 @@ __device__ __forceinline__ void sel_finish_narrow(const float *keys, int64_t p, 
     // compact the keys >= lo after the candidates (order kept: a block-wide scan)
     unsigned long long *kept = sk + kSelCap;
     uint32_t nk = 0;
+#pragma unroll 1
     for (int base = 0; base < (int)ncand; base += blockDim.x) {
         const int i = base + threadIdx.x;
         const uint32_t f = (i < (int)ncand && (uint32_t)(sk[i] >> 32) >= lo) ? 1u : 0u;
@@ -262,10 +281,14 @@ __device__ __forceinline__ void sel_finish_narrow(const float *keys, int64_t p, 
     }
     int P = 1;
     while (P < (int)nk) P <<= 1;
+#pragma unroll 1
     for (int i = (int)nk + threadIdx.x; i < P; i += blockDim.x) kept[i] = 0ull;
     __syncthreads();
+#pragma unroll 1
     for (int size = 2; size <= P; size <<= 1) {                 // bitonic, descending
+#pragma unroll 1
         for (int stride = size >> 1; stride > 0; stride >>= 1) {
+#pragma unroll 1
             for (int i = threadIdx.x; i < P; i += blockDim.x) {
                 const int jx = i ^ stride;
                 if (jx > i) {
@@ -280,6 +303,7 @@ __device__ __forceinline__ void sel_finish_narrow(const float *keys, int64_t p, 
             __syncthreads();
         }
     }
+#pragma unroll 1
     for (int i = threadIdx.x; i < (int)K; i += blockDim.x)
         out[i] = (int32_t)(~(uint32_t)(kept[i] & 0xffffffffull));
     __syncthreads();

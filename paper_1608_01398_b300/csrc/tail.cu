@@ -135,6 +135,7 @@ __global__ void __launch_bounds__(kTailThreads) k_tail(const __grid_constant__ T
     }
     {
         uint32_t *hs = reinterpret_cast<uint32_t *>(smem_raw);
+#pragma unroll 1
         for (int b = tid; b < kSelBins; b += blockDim.x) hs[b] = 0;
         __syncthreads();
         bool nan = false;
@@ -145,6 +146,7 @@ __global__ void __launch_bounds__(kTailThreads) k_tail(const __grid_constant__ T
         });
         if (nan) atomicOr(&T->st.err, 1u);
         __syncthreads();
+#pragma unroll 1
         for (int b = tid; b < kSelBins; b += blockDim.x)
             if (hs[b]) atomicAdd(&T->hist[b], hs[b]);
     }
@@ -183,12 +185,14 @@ __global__ void __launch_bounds__(kTailThreads) k_tail(const __grid_constant__ T
         const uint32_t ncand = T->st.ncand;
         sel_finish_narrow(A.g, A.P, &T->st, T->cand, ncand, A.cand, (uint32_t)A.K,
                           reinterpret_cast<unsigned long long *>(smem_raw), kTailKept, wsum);
+#pragma unroll 1
         for (int b = tid; b < kSelBins; b += blockDim.x) T->hist[b] = 0;
         if (tid == 0) T->st.n_gt = 0;
     }
     if (!b0 || gridDim.x == 1) {
         const int first = gridDim.x == 1 ? 0 : blockIdx.x - 1;
         const int step = gridDim.x == 1 ? 1 : gridDim.x - 1;
+#pragma unroll 1
         for (int vb = first; vb < A.npart; vb += step)
             zmul_body(A.G, A.stride, A.rowb, A.S, A.k, A.coef, 1.0, A.u64, A.v64, A.used, nullptr,
                       nullptr, A.zv, A.partials, A.n_pad, A.p, A.zc, vb);
@@ -224,6 +228,7 @@ __global__ void __launch_bounds__(kTailThreads) k_tail(const __grid_constant__ T
     if (tid == 0) s_state = *(volatile int32_t *)&sc->done;
     __syncthreads();
     if (!s_state) {
+#pragma unroll 1
         for (int v = blockIdx.x; v < 2 * A.npart; v += gridDim.x) {
             const bool two = v >= A.npart;
             zmul_body(A.G, A.stride, A.rowb, two ? A.Sp2 : A.Sp, A.k, two ? A.bSp2 : A.bSp, -1.0, A.u64,
@@ -273,6 +278,7 @@ __global__ void __launch_bounds__(kTailThreads) k_tail(const __grid_constant__ T
                 merge_body<MergeSharedT<kTailKM>>(M);
             }
             if (!grid_sync(T)) return tail_stop(A);
+#pragma unroll 1
             for (int vb = blockIdx.x; vb < A.npart; vb += gridDim.x)
                 zmul_body(A.G, A.stride, A.rowb, A.Sp, A.k, A.bSp, -1.0, A.u64, A.v64, A.used, A.y64,
                           A.r64, A.rc64, A.partials, A.n_pad, A.p, A.zc, vb);
@@ -292,21 +298,47 @@ __global__ void __launch_bounds__(kTailThreads) k_tail(const __grid_constant__ T
     if (!s_state) {
         const int64_t nthr = (int64_t)gridDim.x * blockDim.x;
         const double *acc = *(volatile int *)&T->acc2 ? A.rc64_2 : A.rc64;   // the accepted residual
-        // thread t of the limb kernel's 1024 centres the samples i = t mod 1024 and
-        // forms their max |r| and sum of r in that kernel's order
-        for (int64_t t = (int64_t)blockIdx.x * blockDim.x + tid; t < 1024; t += nthr) {
+        // the limb kernel's thread t (of 1024) forms the max |r| and the sum of r
+        // over the samples i = t mod 1024 in increasing i; here block b takes
+        // t = 8 b .. 8 b + 7, its thread (t, j) centres sample t + 1024 (j0 + j)
+        // (16 at a time), and the first 8 threads run the sums in that order
+        __shared__ float s_r[kTailThreads / 8][8];
+        const double mean = sc->sum_r / (double)sc->n_rows;
+        const int tt = tid & 7, jj = tid >> 3;
+#pragma unroll 1
+        for (int64_t t0 = 8 * (int64_t)blockIdx.x; t0 < 1024; t0 += 8 * (int64_t)gridDim.x) {
+            const int64_t t = t0 + tt;
             float m = 0.0f;
             double sum = 0.0;
-            for (int64_t i = t; i < A.n_pad; i += 1024) {
-                center_elem(acc, A.r64, A.used, i, sc, A.r32);
-                if (i < A.nlim) {
-                    const float r = A.r32[i];
-                    m = fmaxf(m, fabsf(r));
-                    sum += (double)r;
+#pragma unroll 1
+            for (int64_t j0 = 0; 1024 * j0 < A.n_pad; j0 += kTailThreads / 8) {
+                const int64_t i = t + 1024 * (j0 + jj);
+                float r = 0.0f;
+                if (i < A.n_pad) {
+                    const double v = acc[i];
+                    if (acc != A.r64) A.r64[i] = v;
+                    r = A.used[i] ? (float)(v - mean) : 0.0f;
+                    A.r32[i] = r;
                 }
+                s_r[jj][tt] = r;
+                __syncthreads();
+                if (tid < 8) {
+#pragma unroll 1
+                    for (int j = 0; j < kTailThreads / 8; ++j) {
+                        const int64_t ij = t + 1024 * (j0 + j);
+                        if (ij < A.nlim) {
+                            const float rj = s_r[j][tid];
+                            m = fmaxf(m, fabsf(rj));
+                            sum += (double)rj;
+                        }
+                    }
+                }
+                __syncthreads();
             }
-            T->part_m[t] = m;
-            T->part_acc[t] = sum;
+            if (tid < 8) {
+                T->part_m[t] = m;
+                T->part_acc[t] = sum;
+            }
         }
         if (!grid_sync(T)) return tail_stop(A);
         float m = 0.0f;
@@ -316,6 +348,7 @@ __global__ void __launch_bounds__(kTailThreads) k_tail(const __grid_constant__ T
         if ((tid & 31) == 0) reinterpret_cast<float *>(wsum)[tid >> 5] = m;
         __syncthreads();
         m = 0.0f;
+#pragma unroll 1
         for (int w = 0; w < (int)(blockDim.x >> 5); ++w) m = fmaxf(m, reinterpret_cast<float *>(wsum)[w]);
         const float s0 = limb_scale(m);
         if (b0) {
@@ -334,8 +367,10 @@ __global__ void __launch_bounds__(kTailThreads) k_tail(const __grid_constant__ T
                     A.prm->R = (float)R;
                 }
             }
+#pragma unroll 1
             for (int b = tid; b < 256; b += blockDim.x) A.bimg[256 + 256 * (A.nlim >> 5) + b] = 0;
         }
+#pragma unroll 1
         for (int64_t i = (int64_t)blockIdx.x * blockDim.x + tid; i < A.nlim; i += nthr)
             limb_encode(A.r32[i], s0, A.bimg, i);
     }
