@@ -656,7 +656,7 @@ __global__ void __launch_bounds__(512) k_missing_sum_smem(const int64_t *__restr
     constexpr int kBatch = 8;                                 // 16-byte list pieces in flight
     for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < p;
          j += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t e0 = off[j], e1 = off[j + 1];
+        const int64_t e0 = __ldcs(&off[j]), e1 = __ldcs(&off[j + 1]);
         const int64_t a0 = e0 & ~(int64_t)(kPer - 1);
         const int lo = (int)(e0 - a0), hi = (int)(e1 - a0);   // valid positions [lo, hi) from a0
         const uint4 *__restrict__ src = idx4 + a0 / kPer;     // (lists end with 16 spare entries)
@@ -666,7 +666,7 @@ __global__ void __launch_bounds__(512) k_missing_sum_smem(const int64_t *__restr
             uint4 w[kBatch];
 #pragma unroll
             for (int u = 0; u < kBatch; ++u)
-                if (q0 + u < nq) w[u] = src[q0 + u];
+                if (q0 + u < nq) w[u] = __ldcs(src + q0 + u);   // read once a pass: evict first
 #pragma unroll
             for (int u = 0; u < kBatch; ++u) {
                 if (q0 + u >= nq) break;

@@ -148,13 +148,23 @@ __device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes)
                  : "memory");
 }
 
+// An L2 policy that evicts first what it covers: the panel is read once per
+// pass, so its lines go before anything else in L2 (the residual, the
+// gradient, and the code and data of the kernels that run between passes).
+__device__ __forceinline__ uint64_t l2_evict_first()
+{
+    uint64_t pol;
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
+    return pol;
+}
+
 __device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, int x, int y,
-                                            uint64_t *bar)
+                                            uint64_t *bar, uint64_t policy)
 {
     asm volatile(
-        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, "
-        "%3}], [%4];" ::"r"(smem_addr(dst)),
-        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_addr(bar))
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint"
+        " [%0], [%1, {%2, %3}], [%4], %5;" ::"r"(smem_addr(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_addr(bar)), "l"(policy)
         : "memory");
 }
 
@@ -484,6 +494,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_grad_tc(const __grid_constant
             uint32_t slot = 0, phase = 0;
             int64_t tile = first;
             int st = 0;
+            const uint64_t policy = l2_evict_first();
             for (; kk < total && !abort_flag; ++kk) {
                 if (kk >= nst && !mbar_wait(&P.tma_empty[slot], phase ^ 1u)) {
                     abort_flag = 1;
@@ -491,7 +502,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_grad_tc(const __grid_constant
                 }
                 mbar_expect_tx(&P.tma_full[slot], kTcStageTile);
                 tma_load_2d(stages + (w * nst + slot) * kTcStageTile, &gmap, st * kTcStageBytes,
-                            (int)(tile * 128), &P.tma_full[slot]);
+                            (int)(tile * 128), &P.tma_full[slot], policy);
                 if (++slot == (uint32_t)nst) {
                     slot = 0;
                     phase ^= 1u;
