@@ -182,6 +182,7 @@ template <int KM> struct MergeSharedT {
     int32_t spos[kSort];
     double red[32];
     uint32_t wsum[32];
+    double mu;                    // the step of this attempt, read once
     int nS_extra;
     int stop;
 };
@@ -289,9 +290,10 @@ template <typename SH = MergeShared> __device__ __forceinline__ void merge_body(
             }
         }
     }
+    if (threadIdx.x == 0 && !sh.stop) sh.mu = sc->mu;
     __syncthreads();
     if (sh.stop) return;
-    const double mu = sc->mu;
+    const double mu = sh.mu;
 
     // U = C (ascending) followed by S \ C (in S order)
     const int K = A.K;
@@ -354,15 +356,25 @@ template <typename SH = MergeShared> __device__ __forceinline__ void merge_body(
     const bool small = nU <= kMergeRank;
     if (small) {
         // S+ by rank: u is in S+ iff fewer than k entries come before it
-        // (|w| descending, index ascending); every thread reads the same v
-        // at the same time (shared-memory broadcast)
+        // (|w| descending, index ascending); a thread ranks two entries in one
+        // sweep over v, and every thread reads the same v at the same time
+        // (shared-memory broadcast)
 #pragma unroll 1
-        for (int u = threadIdx.x; u < nU; u += blockDim.x) {
-            const unsigned long long ku = sh.skey[u];
-            const int32_t iu = sh.uidx[u];
-            int rank = 0;
-            for (int v = 0; v < nU; ++v) rank += before(sh.skey[v], sh.uidx[v], ku, iu) ? 1 : 0;
-            sh.inSp[u] = rank < k ? 1 : 0;
+        for (int ub = 0; ub < nU; ub += 2 * (int)blockDim.x) {
+            const int ua = ub + threadIdx.x, uc = ua + blockDim.x;
+            const int la = min(ua, nU - 1), lc = min(uc, nU - 1);
+            const unsigned long long ka = sh.skey[la], kc = sh.skey[lc];
+            const int32_t ia = sh.uidx[la], ic = sh.uidx[lc];
+            int ra = 0, rc = 0;
+#pragma unroll 4
+            for (int v = 0; v < nU; ++v) {
+                const unsigned long long kv = sh.skey[v];
+                const int32_t iv = sh.uidx[v];
+                ra += (int)((kv > ka) | ((kv == ka) & (iv < ia)));
+                rc += (int)((kv > kc) | ((kv == kc) & (iv < ic)));
+            }
+            if (ua < nU) sh.inSp[ua] = ra < k ? 1 : 0;
+            if (uc < nU) sh.inSp[uc] = rc < k ? 1 : 0;
         }
         __syncthreads();
     } else {
@@ -394,13 +406,47 @@ template <typename SH = MergeShared> __device__ __forceinline__ void merge_body(
 
     // S+ in index order with beta+
     if (small) {
-        // position of u among the members of S+ = members with a lower index
+        // position of u among the members of S+ = members with a lower index.
+        // U is two ascending runs, C (positions < K) and S \ C (K .. nU - 1):
+        // pre[u] = members of S+ before position u (a block scan), and the
+        // members of the other run with a lower index are found by a binary
+        // search of that run
+        int32_t *pre = sh.spos;
+        {
+            const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+            int base = 0;
+#pragma unroll 1
+            for (int a0 = 0; a0 < nU; a0 += blockDim.x) {
+                const int u = a0 + threadIdx.x;
+                const bool f = u < nU && sh.inSp[u];
+                const unsigned bal = __ballot_sync(0xffffffffu, f);
+                __syncthreads();          // the previous chunk's wsum reads are done
+                if (lane == 0) sh.wsum[wid] = __popc(bal);
+                __syncthreads();
+                int off = base, tot = 0;
+#pragma unroll 1
+                for (int w = 0; w < nw; ++w) {
+                    if (w < wid) off += sh.wsum[w];
+                    tot += sh.wsum[w];
+                }
+                if (u < nU) pre[u] = off + __popc(bal & ((1u << lane) - 1u));
+                base += tot;
+            }
+            if (threadIdx.x == 0) pre[nU] = base;
+        }
+        __syncthreads();
 #pragma unroll 1
         for (int u = threadIdx.x; u < nU; u += blockDim.x) {
             if (!sh.inSp[u]) continue;
             const int32_t iu = sh.uidx[u];
-            int pos = 0;
-            for (int v = 0; v < nU; ++v) pos += (sh.inSp[v] && sh.uidx[v] < iu) ? 1 : 0;
+            int pos;
+            if (u < K) {
+                const int lb = lower_bound_i32(sh.uidx + K, nU - K, iu);
+                pos = pre[u] + (pre[K + lb] - pre[K]);
+            } else {
+                const int lb = lower_bound_i32(sh.uidx, K, iu);
+                pos = (pre[u] - pre[K]) + pre[lb];
+            }
             A.Sp[pos] = iu;
             A.bSp[pos] = sh.uw[u];
         }

@@ -28,7 +28,7 @@ constexpr int kTailKept = 1024;               // candidates the selection's narr
 constexpr uint32_t kBarSpin = 1u << 22;       // bounded barrier waits (polls; sleeps up to 512 ns each)
 
 struct TailWork {                     // zeroed before every solve
-    unsigned int bar_count, bar_gen;  // grid barrier: arrivals, generation
+    unsigned long long bar_count;     // grid barrier: arrivals since the solve began (+ kBarAbort)
     int bar_err, acc2;                // 1: a barrier wait gave up; the second candidate was accepted
     Scalars spec;                     // the second candidate's projection scalars (mu / kappa)
     SelState st;                      // selection state (boundary bin, candidate count)
@@ -61,40 +61,47 @@ struct TailArgs {
     cudaGraphConditionalHandle cond;
 };
 
-// Grid-wide barrier (sense by generation).  Thread 0 arrives after the
-// block's writes (block barrier, then a device-scope fence); the last block to
-// arrive resets the count and opens the next generation; the others poll the
-// generation with a bounded number of sleeps.  Returns false when this block
-// or another gave up.
+// Grid-wide barrier on one monotone arrival count: every block of every
+// launch passes the same barriers, so the count is a multiple of the grid at
+// each barrier's start and the barrier the arrival old + 1 belongs to ends at
+// the next multiple.  Thread 0 arrives after the block's writes (block
+// barrier, then a device-scope fence) and, unless it is the last to arrive,
+// polls the count with a bounded number of short sleeps; a block that gives up
+// adds kBarAbort, which every waiter (now and at later barriers) sees at once.
+// One atomic per block and no reset: the last block to arrive leaves at once.
+// Returns false when this block or another gave up.
+constexpr unsigned long long kBarAbort = 1ull << 62;
+
 __device__ __forceinline__ bool grid_sync(TailWork *T)
 {
     __shared__ int s_ok;
     __syncthreads();
     if (threadIdx.x == 0) {
-        volatile unsigned int *gen = &T->bar_gen;
-        const unsigned int g = *gen;
-        int ok = 1;
+        const unsigned long long G = gridDim.x;
         __threadfence();
-        if (atomicAdd(&T->bar_count, 1u) == gridDim.x - 1) {
-            atomicExch(&T->bar_count, 0u);
-            __threadfence();
-            atomicAdd(&T->bar_gen, 1u);
-        } else {
-            // back off: a waiting block polls rarely, so the blocks still at work
-            // (often block 0 alone) do not queue behind the polls in L2
+        const unsigned long long old = atomicAdd(&T->bar_count, 1ull);
+        int ok = old < kBarAbort;
+        if (ok) {
+            const unsigned long long target = (old / G + 1) * G;
+            volatile unsigned long long *cnt = &T->bar_count;
+            unsigned long long now = old + 1;
             uint32_t it = 0, ns = 32;
-            while (*gen == g) {
+            while (now < target) {
                 if (++it > kBarSpin) {
-                    ok = 0;
+                    atomicAdd(&T->bar_count, kBarAbort);
+                    atomicExch(&T->bar_err, 1);
                     break;
                 }
+                // back off: the blocks still at work (often block 0 alone) do
+                // not queue behind the polls in L2
                 __nanosleep(ns);
-                if (ns < 512) ns <<= 1;
+                if (ns < 256) ns <<= 1;
+                now = *cnt;
             }
+            ok = now >= target && now < kBarAbort;
         }
         __threadfence();
-        if (!ok) atomicExch(&T->bar_err, 1);
-        s_ok = ok && !*(volatile int *)&T->bar_err;
+        s_ok = ok;
     }
     __syncthreads();
     return s_ok != 0;
