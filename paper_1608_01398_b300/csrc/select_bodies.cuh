@@ -189,15 +189,71 @@ __device__ __forceinline__ void sort_idx_body(int32_t *idx, int K)
 }
 
 
-// One block: the K indices from the candidate words (a bitonic sort
-// descending: larger key first, lower index first among equal keys), or the
-// exact radix finish when more than kSelCap keys lie in or above the boundary
-// bin; then the K indices ascending.  sk: kSelCap words of shared memory.
+// Up to this many candidate words the finish ranks them instead of sorting.
+constexpr int kSelRank = 512;
+
+// The K largest of n <= kSelRank distinct words w (shared memory; key << 32 |
+// ~index, so larger key first and lower index first among equal keys), their
+// indices written to out in ascending index order: a word is among the K iff
+// fewer than K words are larger, and its place is the number of chosen words
+// with a lower index.  Two sweeps over w per pair of words a thread ranks
+// (every thread reads the same word at the same time: a broadcast), instead of
+// the bitonic networks' two dozen block barriers each.
+__device__ __forceinline__ void sel_rank_finish(const unsigned long long *w, int n, int32_t *out,
+                                                uint32_t K)
+{
+    __shared__ uint8_t s_sel[kSelRank];
+#pragma unroll 1
+    for (int ub = 0; ub < n; ub += 2 * (int)blockDim.x) {
+        const int ua = ub + threadIdx.x, uc = ua + blockDim.x;
+        const unsigned long long wa = w[min(ua, n - 1)], wc = w[min(uc, n - 1)];
+        uint32_t ra = 0, rc = 0;
+#pragma unroll 4
+        for (int v = 0; v < n; ++v) {
+            const unsigned long long wv = w[v];
+            ra += wv > wa ? 1u : 0u;
+            rc += wv > wc ? 1u : 0u;
+        }
+        if (ua < n) s_sel[ua] = ra < K ? 1 : 0;
+        if (uc < n) s_sel[uc] = rc < K ? 1 : 0;
+    }
+    __syncthreads();
+#pragma unroll 1
+    for (int ub = 0; ub < n; ub += 2 * (int)blockDim.x) {
+        const int ua = ub + threadIdx.x, uc = ua + blockDim.x;
+        const uint32_t ia = ~(uint32_t)(w[min(ua, n - 1)] & 0xffffffffull);
+        const uint32_t ic = ~(uint32_t)(w[min(uc, n - 1)] & 0xffffffffull);
+        uint32_t pa = 0, pc = 0;
+#pragma unroll 4
+        for (int v = 0; v < n; ++v) {
+            const uint32_t sv = s_sel[v];
+            const uint32_t iv = ~(uint32_t)(w[v] & 0xffffffffull);
+            pa += sv & (iv < ia ? 1u : 0u);
+            pc += sv & (iv < ic ? 1u : 0u);
+        }
+        if (ua < n && s_sel[ua]) out[pa] = (int32_t)ia;
+        if (uc < n && s_sel[uc]) out[pc] = (int32_t)ic;
+    }
+    __syncthreads();
+}
+
+// One block: the K indices from the candidate words (larger key first, lower
+// index first among equal keys): ranked up to kSelRank words, else a bitonic
+// sort descending, or the exact radix finish when more than kSelCap keys lie
+// in or above the boundary bin; the K indices come out ascending.  sk: kSelCap
+// words of shared memory.
 __device__ __forceinline__ void sel_finish(const float *keys, int64_t p, const SelState *st,
                                            const unsigned long long *cand, uint32_t ncand,
                                            int32_t *out, uint32_t K, unsigned long long *sk,
                                            uint32_t *wsum)
 {
+    if (ncand <= (uint32_t)kSelRank) {
+#pragma unroll 1
+        for (int i = threadIdx.x; i < (int)ncand; i += blockDim.x) sk[i] = __ldcg(&cand[i]);
+        __syncthreads();
+        sel_rank_finish(sk, (int)ncand, out, K);
+        return;
+    }
     if (ncand <= (uint32_t)kSelCap) {
         int P = 1;
         while (P < (int)ncand) P <<= 1;
@@ -233,9 +289,9 @@ __device__ __forceinline__ void sel_finish(const float *keys, int64_t p, const S
 }
 
 // The same result as sel_finish for a block with few threads: with more than
-// 256 candidates, a histogram of bits 19..10 of the boundary bin's keys finds
-// the sub-bin holding the K-th key; only the keys above it and in it (every key
-// that can be among the K, ties included) are sorted.  sk: room for kSelCap
+// kSelRank candidates, a histogram of bits 19..10 of the boundary bin's keys
+// finds the sub-bin holding the K-th key; only the keys above it and in it
+// (every key that can be among the K, ties included) are ranked or sorted.  sk: room for kSelCap
 // words plus `extra` words (the kept keys are compacted there); when they do
 // not fit, all candidates are sorted as in sel_finish.
 __device__ __forceinline__ void sel_finish_narrow(const float *keys, int64_t p, const SelState *st,
@@ -245,7 +301,7 @@ __device__ __forceinline__ void sel_finish_narrow(const float *keys, int64_t p, 
 {
     __shared__ uint32_t h[1024];
     __shared__ uint32_t res[3];
-    if (ncand <= 256u || ncand > (uint32_t)kSelCap) {
+    if (ncand <= (uint32_t)kSelRank || ncand > (uint32_t)kSelCap) {
         sel_finish(keys, p, st, cand, ncand, out, K, sk, wsum);
         return;
     }
@@ -277,6 +333,10 @@ __device__ __forceinline__ void sel_finish_narrow(const float *keys, int64_t p, 
     __syncthreads();
     if (nk > (uint32_t)extra) {                                 // no room: sort them all
         sel_finish(keys, p, st, cand, ncand, out, K, sk, wsum);
+        return;
+    }
+    if (nk <= (uint32_t)kSelRank) {
+        sel_rank_finish(kept, (int)nk, out, K);
         return;
     }
     int P = 1;

@@ -107,6 +107,22 @@ __device__ __forceinline__ bool grid_sync(TailWork *T)
     return s_ok != 0;
 }
 
+// Block 0 runs the serial steps (step size, projection, decisions) on a
+// shared-memory copy of the solve's scalars and writes it back before every
+// grid barrier, so the other blocks read the current values after it; no
+// other block writes them.
+constexpr int kScWords = (int)(sizeof(Scalars) / sizeof(unsigned long long));
+static_assert(sizeof(Scalars) % sizeof(unsigned long long) == 0, "Scalars: whole words");
+
+__device__ __forceinline__ bool grid_sync_put(TailWork *T, Scalars *sc, const Scalars *ssc, bool b0)
+{
+    __syncthreads();
+    if (b0 && threadIdx.x < kScWords)
+        reinterpret_cast<unsigned long long *>(sc)[threadIdx.x] =
+            reinterpret_cast<const unsigned long long *>(ssc)[threadIdx.x];
+    return grid_sync(T);
+}
+
 __device__ __forceinline__ void tail_stop(const TailArgs &A)
 {
     if (blockIdx.x == 0 && threadIdx.x == 0) {
@@ -128,7 +144,11 @@ __global__ void __launch_bounds__(kTailThreads) k_tail(const __grid_constant__ T
     const int tid = threadIdx.x;
     const bool b0 = blockIdx.x == 0;
 
+    __shared__ Scalars ssc;               // block 0's working copy of the scalars
     if (tid == 0) s_state = *(volatile int32_t *)&sc->done;
+    if (b0 && tid < kScWords)
+        reinterpret_cast<unsigned long long *>(&ssc)[tid] =
+            reinterpret_cast<const volatile unsigned long long *>(sc)[tid];
     __syncthreads();
     if (s_state) {
         if (b0 && tid == 0) cudaGraphSetConditional(A.cond, 0u);
@@ -138,7 +158,7 @@ __global__ void __launch_bounds__(kTailThreads) k_tail(const __grid_constant__ T
     // A: g_S and ||g_S||^2 for the step size (block 0, first warp); histogram of |g|
     if (b0) {
         if (tid == 0) T->acc2 = 0;
-        gather_gS_body(A.g, A.S, A.k, A.coef, sc);
+        gather_gS_body(A.g, A.S, A.k, A.coef, &ssc);
     }
     {
         uint32_t *hs = reinterpret_cast<uint32_t *>(smem_raw);
@@ -157,7 +177,7 @@ __global__ void __launch_bounds__(kTailThreads) k_tail(const __grid_constant__ T
         for (int b = tid; b < kSelBins; b += blockDim.x)
             if (hs[b]) atomicAdd(&T->hist[b], hs[b]);
     }
-    if (!grid_sync(T)) return tail_stop(A);
+    if (!grid_sync_put(T, sc, &ssc, b0)) return tail_stop(A);
 
     // B: the boundary bin (every block, from the whole histogram) and the keys
     // in or above it as candidate words
@@ -184,7 +204,7 @@ __global__ void __launch_bounds__(kTailThreads) k_tail(const __grid_constant__ T
             T->st.ncand = ncand;
         }
     }
-    if (!grid_sync(T)) return tail_stop(A);
+    if (!grid_sync_put(T, sc, &ssc, b0)) return tail_stop(A);
 
     // C: block 0 sorts the candidates into the K indices (ascending) and cleans
     // the selection scratch; the other blocks form Z_S g_S
@@ -204,7 +224,7 @@ __global__ void __launch_bounds__(kTailThreads) k_tail(const __grid_constant__ T
             zmul_body(A.G, A.stride, A.rowb, A.S, A.k, A.coef, 1.0, A.u64, A.v64, A.used, nullptr,
                       nullptr, A.zv, A.partials, A.n_pad, A.p, A.zc, vb);
     }
-    if (!grid_sync(T)) return tail_stop(A);
+    if (!grid_sync_put(T, sc, &ssc, b0)) return tail_stop(A);
 
     // D: the first two attempts side by side: block 0 projects with mu, block 1
     // with mu / kappa (the step the decision takes when it rejects the first),
@@ -212,7 +232,7 @@ __global__ void __launch_bounds__(kTailThreads) k_tail(const __grid_constant__ T
     // block 0 -- the same arithmetic as one attempt after the other.  Later
     // attempts, when both are rejected, run one at a time.
     if (b0 || blockIdx.x == 1) {
-        Scalars *msc = b0 ? sc : &T->spec;
+        Scalars *msc = b0 ? &ssc : &T->spec;
         if (!b0 && tid == 0) T->spec = *sc;
         __syncthreads();
         MergeArgs M;
@@ -231,7 +251,7 @@ __global__ void __launch_bounds__(kTailThreads) k_tail(const __grid_constant__ T
         M.sc = msc;
         merge_body<MergeSharedT<kTailKM>>(M);
     }
-    if (!grid_sync(T)) return tail_stop(A);
+    if (!grid_sync_put(T, sc, &ssc, b0)) return tail_stop(A);
     if (tid == 0) s_state = *(volatile int32_t *)&sc->done;
     __syncthreads();
     if (!s_state) {
@@ -242,27 +262,27 @@ __global__ void __launch_bounds__(kTailThreads) k_tail(const __grid_constant__ T
                       A.v64, A.used, A.y64, A.r64, two ? A.rc64_2 : A.rc64, two ? A.partials2 : A.partials,
                       A.n_pad, A.p, A.zc, two ? v - A.npart : v);
         }
-        if (!grid_sync(T)) return tail_stop(A);
+        if (!grid_sync_put(T, sc, &ssc, b0)) return tail_stop(A);
         if (b0) {
             __shared__ int s_second;
-            decide_body(sc, A.partials, A.npart, A.S, A.bS, A.Sp, A.bSp, TraceDev{});
+            decide_body(&ssc, A.partials, A.npart, A.S, A.bS, A.Sp, A.bSp, TraceDev{});
             __syncthreads();
             if (tid == 0) {
-                s_second = sc->retry && !sc->done && sc->bt_last == 1;
+                s_second = ssc.retry && !ssc.done && ssc.bt_last == 1;
                 if (s_second) {                      // the second candidate is the shrunk step
-                    sc->changed = T->spec.changed;
-                    sc->dd = T->spec.dd;
-                    sc->bb = T->spec.bb;
+                    ssc.changed = T->spec.changed;
+                    ssc.dd = T->spec.dd;
+                    ssc.bb = T->spec.bb;
                 }
             }
             __syncthreads();
             if (s_second) {
-                decide_body(sc, A.partials2, A.npart, A.S, A.bS, A.Sp2, A.bSp2, TraceDev{});
+                decide_body(&ssc, A.partials2, A.npart, A.S, A.bS, A.Sp2, A.bSp2, TraceDev{});
                 __syncthreads();
-                if (tid == 0) T->acc2 = !sc->retry;
+                if (tid == 0) T->acc2 = !ssc.retry;
             }
         }
-        if (!grid_sync(T)) return tail_stop(A);
+        if (!grid_sync_put(T, sc, &ssc, b0)) return tail_stop(A);
         if (tid == 0)
             s_state = (*(volatile int32_t *)&sc->done ? 1 : 0) | (*(volatile int32_t *)&sc->retry ? 2 : 0);
         __syncthreads();
@@ -281,17 +301,17 @@ __global__ void __launch_bounds__(kTailThreads) k_tail(const __grid_constant__ T
                 M.skip = nullptr;
                 M.Sp = A.Sp;
                 M.bSp = A.bSp;
-                M.sc = sc;
+                M.sc = &ssc;
                 merge_body<MergeSharedT<kTailKM>>(M);
             }
-            if (!grid_sync(T)) return tail_stop(A);
+            if (!grid_sync_put(T, sc, &ssc, b0)) return tail_stop(A);
 #pragma unroll 1
             for (int vb = blockIdx.x; vb < A.npart; vb += gridDim.x)
                 zmul_body(A.G, A.stride, A.rowb, A.Sp, A.k, A.bSp, -1.0, A.u64, A.v64, A.used, A.y64,
                           A.r64, A.rc64, A.partials, A.n_pad, A.p, A.zc, vb);
-            if (!grid_sync(T)) return tail_stop(A);
-            if (b0) decide_body(sc, A.partials, A.npart, A.S, A.bS, A.Sp, A.bSp, TraceDev{});
-            if (!grid_sync(T)) return tail_stop(A);
+            if (!grid_sync_put(T, sc, &ssc, b0)) return tail_stop(A);
+            if (b0) decide_body(&ssc, A.partials, A.npart, A.S, A.bS, A.Sp, A.bSp, TraceDev{});
+            if (!grid_sync_put(T, sc, &ssc, b0)) return tail_stop(A);
             if (tid == 0)
                 s_state = (*(volatile int32_t *)&sc->done ? 1 : 0) | (*(volatile int32_t *)&sc->retry ? 2 : 0);
             __syncthreads();
@@ -347,7 +367,7 @@ __global__ void __launch_bounds__(kTailThreads) k_tail(const __grid_constant__ T
                 T->part_acc[t] = sum;
             }
         }
-        if (!grid_sync(T)) return tail_stop(A);
+        if (!grid_sync_put(T, sc, &ssc, b0)) return tail_stop(A);
         float m = 0.0f;
         for (int t = tid; t < 1024; t += blockDim.x) m = fmaxf(m, T->part_m[t]);
 #pragma unroll
