@@ -30,6 +30,7 @@ constexpr uint32_t kBarSpin = 1u << 22;       // bounded barrier waits (polls; s
 struct TailWork {                     // zeroed before every solve
     unsigned long long bar_count;     // grid barrier: arrivals since the solve began (+ kBarAbort)
     int bar_err, acc2;                // 1: a barrier wait gave up; the second candidate was accepted
+    unsigned int den_ticket;          // blocks done with Z_S g_S in this launch
     Scalars spec;                     // the second candidate's projection scalars (mu / kappa)
     SelState st;                      // selection state (boundary bin, candidate count)
     uint32_t hist[kSelBins];          // histogram of |g| bits 30..20
@@ -44,7 +45,7 @@ struct TailArgs {
     const double *zc;                    // standardised covariates, or null
     Scalars *sc;
     const float *g;
-    int32_t *S, *Sp, *cand, *Sp2;
+    int32_t *S, *Sp, *Sp2;
     double *bS, *bSp, *coef, *bSp2;
     const double *u64, *v64;
     const int32_t *used;
@@ -144,9 +145,9 @@ __global__ void __launch_bounds__(kTailThreads) k_tail(const __grid_constant__ T
     const int tid = threadIdx.x;
     const bool b0 = blockIdx.x == 0;
 
-    __shared__ Scalars ssc;               // block 0's working copy of the scalars
+    __shared__ Scalars ssc;               // the block's working copy of the scalars (block 0's is the solve's)
     if (tid == 0) s_state = *(volatile int32_t *)&sc->done;
-    if (b0 && tid < kScWords)
+    if (tid < kScWords)
         reinterpret_cast<unsigned long long *>(&ssc)[tid] =
             reinterpret_cast<const volatile unsigned long long *>(sc)[tid];
     __syncthreads();
@@ -179,6 +180,12 @@ __global__ void __launch_bounds__(kTailThreads) k_tail(const __grid_constant__ T
     }
     if (!grid_sync_put(T, sc, &ssc, b0)) return tail_stop(A);
 
+    // Z_S g_S for the step size: formed in C by the blocks no candidate needs
+    // (nden of them, each then counted in den_ticket), while the others select
+    // the candidates; in B when every block forms a candidate's residual
+    const int nfree = (int)gridDim.x - 2 * A.npart;
+    const int nden = nfree > 0 ? min(nfree, A.npart) : 0;
+
     // B: the boundary bin (every block, from the whole histogram) and the keys
     // in or above it as candidate words
     {
@@ -203,69 +210,128 @@ __global__ void __launch_bounds__(kTailThreads) k_tail(const __grid_constant__ T
             T->st.need = (uint32_t)A.K - res[1];
             T->st.ncand = ncand;
         }
+        if (nden == 0) {
+#pragma unroll 1
+            for (int vb = (int)gridDim.x - 1 - (int)blockIdx.x; vb < A.npart; vb += gridDim.x)
+                zmul_body(A.G, A.stride, A.rowb, A.S, A.k, A.coef, 1.0, A.u64, A.v64, A.used, nullptr,
+                          nullptr, A.zv, A.partials, A.n_pad, A.p, A.zc, vb);
+        }
     }
     if (!grid_sync_put(T, sc, &ssc, b0)) return tail_stop(A);
 
-    // C: block 0 sorts the candidates into the K indices (ascending) and cleans
-    // the selection scratch; the other blocks form Z_S g_S
-    if (b0) {
-        const uint32_t ncand = T->st.ncand;
-        sel_finish_narrow(A.g, A.P, &T->st, T->cand, ncand, A.cand, (uint32_t)A.K,
-                          reinterpret_cast<unsigned long long *>(smem_raw), kTailKept, wsum);
+    // C: every block that forms a candidate's residual selects the K candidates
+    // and projects for itself (the same inputs give every block the same
+    // result, so no barrier separates the steps): blocks v < npart take the
+    // step mu, blocks npart <= v < 2 npart mu / kappa (the step the decision
+    // takes when it rejects the first), and each forms its 128 samples of that
+    // candidate's residual.  Block 0 keeps the first candidate (its scalars
+    // are the solve's); the block of v = npart publishes the second one's.
+    // The decisions then run in order on block 0 -- the same arithmetic as one
+    // attempt after the other; later attempts, when both are rejected, run one
+    // at a time.
+    __shared__ int32_t s_cand[2 * kTailKM];
+    __shared__ int32_t s_Sp[2][kTailKM];
+    __shared__ double s_bSp[2][kTailKM];
+    __shared__ Scalars ssc2;              // the second candidate's scalars
+    {
+        bool want[2] = {false, false};
 #pragma unroll 1
-        for (int b = tid; b < kSelBins; b += blockDim.x) T->hist[b] = 0;
-        if (tid == 0) T->st.n_gt = 0;
-    }
-    if (!b0 || gridDim.x == 1) {
-        const int first = gridDim.x == 1 ? 0 : blockIdx.x - 1;
-        const int step = gridDim.x == 1 ? 1 : gridDim.x - 1;
+        for (int v = blockIdx.x; v < 2 * A.npart; v += gridDim.x) want[v >= A.npart] = true;
+        if (b0) want[0] = true;
+        if (want[0] || want[1]) {
+            // the step size's inputs: ||g_S||^2 (block 0) and the other scalars
+            if (tid < kScWords && !b0)
+                reinterpret_cast<unsigned long long *>(&ssc)[tid] =
+                    reinterpret_cast<const volatile unsigned long long *>(sc)[tid];
+            const uint32_t ncand = res[1] + res[2];
+            sel_finish_narrow(A.g, A.P, &T->st, T->cand, ncand, s_cand, (uint32_t)A.K,
+                              reinterpret_cast<unsigned long long *>(smem_raw), kTailKept, wsum);
+            if (nden > 0 && tid == 0) {           // Z_S g_S complete (bounded wait)
+                volatile unsigned int *tk = &T->den_ticket;
+                uint32_t it = 0, ns = 32;
+                while (*tk < (unsigned int)nden) {
+                    if (++it > kBarSpin) {
+                        atomicAdd(&T->bar_count, kBarAbort);
+                        atomicExch(&T->bar_err, 1);
+                        break;
+                    }
+                    __nanosleep(ns);
+                    if (ns < 256) ns <<= 1;
+                }
+                __threadfence();
+            }
+            __syncthreads();
 #pragma unroll 1
-        for (int vb = first; vb < A.npart; vb += step)
-            zmul_body(A.G, A.stride, A.rowb, A.S, A.k, A.coef, 1.0, A.u64, A.v64, A.used, nullptr,
-                      nullptr, A.zv, A.partials, A.n_pad, A.p, A.zc, vb);
+            for (int c = 0; c < 2; ++c) {
+                if (!want[c]) continue;
+                if (c == 1 && tid < kScWords)
+                    reinterpret_cast<unsigned long long *>(&ssc2)[tid] =
+                        reinterpret_cast<const unsigned long long *>(&ssc)[tid];
+                __syncthreads();
+                MergeArgs M;
+                M.g = A.g;
+                M.S = A.S;
+                M.bS = A.bS;
+                M.cand = s_cand;
+                M.K = A.K;
+                M.partials = A.partials;
+                M.npart = A.npart;
+                M.first = 1;
+                M.shrinks = c;
+                M.skip = nullptr;
+                M.Sp = s_Sp[c];
+                M.bSp = s_bSp[c];
+                M.sc = c ? &ssc2 : &ssc;
+                merge_body<MergeSharedT<kTailKM>>(M);
+                __syncthreads();
+                const Scalars &ms = c ? ssc2 : ssc;
+                if (ms.done) continue;            // g_S = 0 or a non-finite step: no candidate
+                // block 0 decides on the first candidate from its own copy; the
+                // block of v = npart publishes the second for it
+                if (c == 1 && (int)(A.npart % gridDim.x) == (int)blockIdx.x) {
+#pragma unroll 1
+                    for (int i = tid; i < A.k; i += blockDim.x) {
+                        A.Sp2[i] = s_Sp[1][i];
+                        A.bSp2[i] = s_bSp[1][i];
+                    }
+                    if (tid < kScWords)
+                        reinterpret_cast<unsigned long long *>(&T->spec)[tid] =
+                            reinterpret_cast<const unsigned long long *>(&ssc2)[tid];
+                }
+#pragma unroll 1
+                for (int v = blockIdx.x; v < 2 * A.npart; v += gridDim.x) {
+                    if ((v >= A.npart) != (c == 1)) continue;
+                    zmul_body(A.G, A.stride, A.rowb, s_Sp[c], A.k, s_bSp[c], -1.0, A.u64, A.v64, A.used,
+                              A.y64, A.r64, c ? A.rc64_2 : A.rc64, c ? A.partials2 : A.partials, A.n_pad,
+                              A.p, A.zc, c ? v - A.npart : v);
+                }
+            }
+        }
+        if (nden > 0 && (int)blockIdx.x >= 2 * A.npart && (int)blockIdx.x < 2 * A.npart + nden) {
+#pragma unroll 1
+            for (int vb = (int)blockIdx.x - 2 * A.npart; vb < A.npart; vb += nden)
+                zmul_body(A.G, A.stride, A.rowb, A.S, A.k, A.coef, 1.0, A.u64, A.v64, A.used, nullptr,
+                          nullptr, A.zv, A.partials, A.n_pad, A.p, A.zc, vb);
+            __syncthreads();
+            if (tid == 0) {
+                __threadfence();
+                atomicAdd(&T->den_ticket, 1u);
+            }
+        }
+        if (b0) {
+#pragma unroll 1
+            for (int b = tid; b < kSelBins; b += blockDim.x) T->hist[b] = 0;
+            if (tid == 0) T->st.n_gt = 0;
+        }
     }
     if (!grid_sync_put(T, sc, &ssc, b0)) return tail_stop(A);
-
-    // D: the first two attempts side by side: block 0 projects with mu, block 1
-    // with mu / kappa (the step the decision takes when it rejects the first),
-    // both candidates' residuals in one pass, then the decisions in order on
-    // block 0 -- the same arithmetic as one attempt after the other.  Later
-    // attempts, when both are rejected, run one at a time.
-    if (b0 || blockIdx.x == 1) {
-        Scalars *msc = b0 ? &ssc : &T->spec;
-        if (!b0 && tid == 0) T->spec = *sc;
-        __syncthreads();
-        MergeArgs M;
-        M.g = A.g;
-        M.S = A.S;
-        M.bS = A.bS;
-        M.cand = A.cand;
-        M.K = A.K;
-        M.partials = A.partials;
-        M.npart = A.npart;
-        M.first = 1;
-        M.shrinks = b0 ? 0 : 1;
-        M.skip = nullptr;
-        M.Sp = b0 ? A.Sp : A.Sp2;
-        M.bSp = b0 ? A.bSp : A.bSp2;
-        M.sc = msc;
-        merge_body<MergeSharedT<kTailKM>>(M);
-    }
-    if (!grid_sync_put(T, sc, &ssc, b0)) return tail_stop(A);
+    if (b0 && tid == 0) T->den_ticket = 0;    // every projection has passed its wait
     if (tid == 0) s_state = *(volatile int32_t *)&sc->done;
     __syncthreads();
     if (!s_state) {
-#pragma unroll 1
-        for (int v = blockIdx.x; v < 2 * A.npart; v += gridDim.x) {
-            const bool two = v >= A.npart;
-            zmul_body(A.G, A.stride, A.rowb, two ? A.Sp2 : A.Sp, A.k, two ? A.bSp2 : A.bSp, -1.0, A.u64,
-                      A.v64, A.used, A.y64, A.r64, two ? A.rc64_2 : A.rc64, two ? A.partials2 : A.partials,
-                      A.n_pad, A.p, A.zc, two ? v - A.npart : v);
-        }
-        if (!grid_sync_put(T, sc, &ssc, b0)) return tail_stop(A);
         if (b0) {
             __shared__ int s_second;
-            decide_body(&ssc, A.partials, A.npart, A.S, A.bS, A.Sp, A.bSp, TraceDev{});
+            decide_body(&ssc, A.partials, A.npart, A.S, A.bS, s_Sp[0], s_bSp[0], TraceDev{});
             __syncthreads();
             if (tid == 0) {
                 s_second = ssc.retry && !ssc.done && ssc.bt_last == 1;
@@ -293,7 +359,7 @@ __global__ void __launch_bounds__(kTailThreads) k_tail(const __grid_constant__ T
                 M.g = A.g;
                 M.S = A.S;
                 M.bS = A.bS;
-                M.cand = A.cand;
+                M.cand = s_cand;
                 M.K = A.K;
                 M.partials = A.partials;
                 M.npart = A.npart;
@@ -570,7 +636,6 @@ int run_fused_solve(iht_dataset *ds, int k, int K, int impl)
     a.g = ws->g;
     a.S = ws->S;
     a.Sp = ws->Sp;
-    a.cand = ws->cand;
     a.Sp2 = ws->Sp2;
     a.bS = ws->bS;
     a.bSp = ws->bSp;
