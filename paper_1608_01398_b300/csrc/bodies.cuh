@@ -49,17 +49,30 @@ __device__ __forceinline__ void warp_partials(const double *partials, int npart,
 // elsewhere); per-block sums of out, out^2 and (out - prev)^2 (0 without
 // prev) go to partials[3 b .. 3 b + 2].  One thread per sample, 128 samples
 // per block (every caller launches kZmulThreads threads; smaller blocks would
-// only multiply the partial triples every consumer sums).  Per chunk of
-// kZmulChunk columns the block stages in shared memory each column's three
-// possible terms a (x - u) for x = 0, 1, 2 and the block's 32 genotype bytes
-// of the column (two 16-byte loads, one per thread, all in flight at once);
-// a thread then adds its terms in column order, one shared-memory lookup and
-// one FP64 add each.  The body runs once per pass of a launch that is itself
-// run once per iteration, so its code is fetched cold each time: the loops
-// stay rolled (a few lines of code) rather than unrolled per column.
+// only multiply the partial triples every consumer sums).
+//
+// The sum over columns is exact: each column's three possible terms
+// a (x - u), x = 0, 1, 2, are rounded once to multiples of 2^-E and added as
+// 64-bit integers, E chosen from the largest |a| and the column count so that
+// no partial sum can reach 2^62 (|x - u| <= 2); the integer sum is rounded
+// once back to FP64.  Its error is below that of any FP64 summation order,
+// and the FP64 unit (a few operations per clock per SM on this part) is
+// left to the per-sample base add and the block sums.  A non-finite a or u
+// makes every output NaN.  Per chunk of kZmulChunk columns the block stages
+// the integer terms and its 32 genotype bytes of each column (two 16-byte
+// loads, one per thread, all in flight at once) in shared memory; a thread
+// then adds one staged term per column.  The body runs once per pass of a
+// launch that is itself run once per iteration, so its code is fetched cold
+// each time: the loops stay rolled (a few lines of code).
 constexpr int kZmulChunk = 256;
 constexpr int kZmulThreads = 128;           // the block every caller launches
 constexpr int kZmulBytes = kZmulThreads / 4;   // genotype bytes of a block per column
+
+// a_c of column c of the list (the expression every pass uses)
+__device__ __forceinline__ double zmul_coef(const double *coef, int c, double sign, double v)
+{
+    return sign * coef[c] * v;
+}
 
 // vb: the 128-sample block to compute (blockIdx.x in a kernel of its own; a
 // fused kernel passes its own index).  The column list, coefficients, base,
@@ -77,8 +90,10 @@ __device__ __forceinline__ void zmul_body(const uint8_t *__restrict__ G, int64_t
                                           int64_t psnp, const double *zc, int vb)
 {
     __shared__ double red[3 * (kZmulThreads / 32)];
-    __shared__ double term[kZmulChunk][4];     // terms for codes 00, 01 (missing: 0), 10, 11
+    __shared__ long long term[kZmulChunk][4];  // terms for codes 00, 01 (missing: 0), 10, 11
+    __shared__ double sa[kZmulChunk], su[kZmulChunk];
     __shared__ __align__(16) uint8_t gtile[kZmulChunk][kZmulBytes];
+    __shared__ int s_ebits, s_bad;             // largest biased exponent of |a|; a non-finite input
     const int64_t i = (int64_t)vb * kZmulThreads + threadIdx.x;
     const int64_t b0 = (int64_t)vb * kZmulBytes;     // first byte of the block in a row (< stride)
     const int bl = threadIdx.x >> 2;                   // this sample's byte in the tile
@@ -93,14 +108,15 @@ __device__ __forceinline__ void zmul_body(const uint8_t *__restrict__ G, int64_t
     const int mall = m;
     if (zc)
         while (m > 0 && cols[m - 1] >= psnp) --m;
-    double acc = 0.0;
-#pragma unroll 1
-    for (int c0 = 0; c0 < m; c0 += kZmulChunk) {
-        const int mc = min(kZmulChunk, m - c0);
-        __syncthreads();                           // the previous chunk's reads are done
-        // thread t: half t & 1 of column t >> 1's 32 bytes (rows are 128-byte
-        // aligned and b0 + 32 <= stride, so the loads stay inside the row);
-        // the even thread also stages the column's terms
+    if (threadIdx.x == 0) {
+        s_ebits = 0;
+        s_bad = 0;
+    }
+    __syncthreads();
+    // a chunk's bytes, a and u into shared memory (thread t: half t & 1 of
+    // column t >> 1's 32 bytes -- rows are 128-byte aligned and b0 + 32 <=
+    // stride, so the loads stay inside the row; the even thread takes a, u)
+    auto stage = [&](int c0, int mc) {
 #pragma unroll 2
         for (int t = threadIdx.x; t < 2 * mc; t += kZmulThreads) {
             const int c = t >> 1;
@@ -108,13 +124,48 @@ __device__ __forceinline__ void zmul_body(const uint8_t *__restrict__ G, int64_t
             const uint4 *src = reinterpret_cast<const uint4 *>(G + (int64_t)col * stride + b0) + (t & 1);
             reinterpret_cast<uint4 *>(gtile[c])[t & 1] = __ldg(src);
             if (!(t & 1)) {
-                const double a = sign * coef[c0 + c] * v64[col];
-                const double b = a * u64[col];
-                term[c][0] = a * 0.0 - b;
-                term[c][1] = 0.0;
-                term[c][2] = a * 1.0 - b;
-                term[c][3] = a * 2.0 - b;
+                const double a = zmul_coef(coef, c0 + c, sign, v64[col]);
+                const double u = u64[col];
+                sa[c] = a;
+                su[c] = u;
+                if (!isfinite(a) || !isfinite(u)) s_bad = 1;
+                atomicMax(&s_ebits, (int)((__double_as_longlong(a) >> 52) & 0x7ff));
             }
+        }
+    };
+    // the scale 2^E: m 2^(emax + 1) 2^E <= 2^62 with |a| < 2^emax, from every
+    // column (the first chunk's while it is staged)
+    if (m > 0) stage(0, min(m, kZmulChunk));
+#pragma unroll 1
+    for (int c = kZmulChunk + threadIdx.x; c < m; c += kZmulThreads) {
+        const int col = cols[c];
+        const double a = zmul_coef(coef, c, sign, v64[col]);
+        if (!isfinite(a) || !isfinite(u64[col])) s_bad = 1;
+        atomicMax(&s_ebits, (int)((__double_as_longlong(a) >> 52) & 0x7ff));
+    }
+    __syncthreads();
+    int L = 0;
+    while ((1 << L) < m) ++L;
+    const int emax = s_ebits - 1022;                   // |a| < 2^emax (0 bits: every a is 0 or tiny)
+    const int E = max(-1000, min(1000, 61 - L - emax));
+    const double scale = __longlong_as_double((long long)(E + 1023) << 52);
+    const bool bad = s_bad != 0;
+    long long acc = 0;
+#pragma unroll 1
+    for (int c0 = 0; c0 < m && !bad; c0 += kZmulChunk) {
+        const int mc = min(kZmulChunk, m - c0);
+        if (c0 > 0) {
+            __syncthreads();                       // the previous chunk's reads are done
+            stage(c0, mc);
+            __syncthreads();
+        }
+#pragma unroll 1
+        for (int c = threadIdx.x; c < mc; c += kZmulThreads) {
+            const double a = sa[c], u = su[c];
+            term[c][0] = __double2ll_rn((a * (0.0 - u)) * scale);
+            term[c][1] = 0;
+            term[c][2] = __double2ll_rn((a * (1.0 - u)) * scale);
+            term[c][3] = __double2ll_rn((a * (2.0 - u)) * scale);
         }
         __syncthreads();
         if (inb) {
@@ -122,22 +173,40 @@ __device__ __forceinline__ void zmul_body(const uint8_t *__restrict__ G, int64_t
             for (int c = 0; c < mc; ++c) acc += term[c][((uint32_t)gtile[c][bl] >> shift) & 3u];
         }
     }
+    double sum = bad ? __longlong_as_double(0x7ff8000000000000ll)
+                     : __ll2double_rn(acc) * __longlong_as_double((long long)(1023 - E) << 52);
     if (in)
 #pragma unroll 1
-        for (int c = m; c < mall; ++c) acc += (sign * coef[c]) * zc[(int64_t)(cols[c] - psnp) * n_pad + i];
+        for (int c = m; c < mall; ++c) sum += (sign * coef[c]) * zc[(int64_t)(cols[c] - psnp) * n_pad + i];
     double o = 0.0, d = 0.0;
     if (in) {
-        o = ui ? bi + acc : 0.0;
+        o = ui ? bi + sum : 0.0;
         out[i] = o;
         if (prev) d = o - pi;
     }
+    // the block's sums of out, out^2 and (out - prev)^2: a shuffle tree per
+    // warp, then lanes 0..2 each add one quantity's warp sums in warp order
     double s = o, s2 = o * o, d2 = d * d;
-    block_sum3(s, s2, d2, red);
-    if (threadIdx.x == 0 && partials) {
-        partials[3 * vb] = s;
-        partials[3 * vb + 1] = s2;
-        partials[3 * vb + 2] = d2;
+    constexpr int nw = kZmulThreads / 32;
+#pragma unroll
+    for (int q = 16; q > 0; q >>= 1) {
+        s += __shfl_xor_sync(0xffffffffu, s, q);
+        s2 += __shfl_xor_sync(0xffffffffu, s2, q);
+        d2 += __shfl_xor_sync(0xffffffffu, d2, q);
     }
+    if ((threadIdx.x & 31) == 0) {
+        red[threadIdx.x >> 5] = s;
+        red[nw + (threadIdx.x >> 5)] = s2;
+        red[2 * nw + (threadIdx.x >> 5)] = d2;
+    }
+    __syncthreads();
+    if (threadIdx.x < 3 && partials) {
+        double t = red[threadIdx.x * nw];
+#pragma unroll
+        for (int w = 1; w < nw; ++w) t += red[threadIdx.x * nw + w];
+        partials[3 * vb + threadIdx.x] = t;
+    }
+    __syncthreads();                                   // red is free for the next call
 }
 
 struct MergeArgs {

@@ -465,39 +465,6 @@ __device__ __forceinline__ double block_sum(double x, double *sh)
     return t;
 }
 
-// Three fixed-order block sums at once (each in the order block_sum uses);
-// `sh` needs 3 blockDim.x / 32 doubles.
-__device__ __forceinline__ void block_sum3(double &x, double &y, double &z, double *sh)
-{
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        x += __shfl_xor_sync(0xffffffffu, x, o);
-        y += __shfl_xor_sync(0xffffffffu, y, o);
-        z += __shfl_xor_sync(0xffffffffu, z, o);
-    }
-    __syncthreads();
-    if (lane == 0) {
-        sh[wid] = x;
-        sh[nw + wid] = y;
-        sh[2 * nw + wid] = z;
-    }
-    __syncthreads();
-    if (wid == 0) {
-        double a = lane < nw ? sh[lane] : 0.0, b = lane < nw ? sh[nw + lane] : 0.0,
-               c = lane < nw ? sh[2 * nw + lane] : 0.0;
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            a += __shfl_xor_sync(0xffffffffu, a, o);
-            b += __shfl_xor_sync(0xffffffffu, b, o);
-            c += __shfl_xor_sync(0xffffffffu, c, o);
-        }
-        x = a;
-        y = b;
-        z = c;
-    }
-}
-
 inline int ceil_div(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
 
 // g = v (S1 - u (R - M)) with every operation rounded on its own (no

@@ -244,6 +244,17 @@ __global__ void __launch_bounds__(kTailThreads) k_tail(const __grid_constant__ T
                 reinterpret_cast<unsigned long long *>(&ssc)[tid] =
                     reinterpret_cast<const volatile unsigned long long *>(sc)[tid];
             const uint32_t ncand = res[1] + res[2];
+            // the genotype bytes of this block's residual on their way to L2
+            // while the candidates are chosen (S+ mostly repeats S)
+            {
+                const int vb0 = (int)blockIdx.x < A.npart ? (int)blockIdx.x : (int)blockIdx.x - A.npart;
+                const uint8_t *gb = A.G + (int64_t)vb0 * kZmulBytes;
+#pragma unroll 1
+                for (int c = tid; c < A.k; c += blockDim.x) {
+                    const int64_t j = A.S[c];
+                    if (j < A.p) asm volatile("prefetch.global.L2 [%0];" ::"l"(gb + j * A.stride));
+                }
+            }
             sel_finish_narrow(A.g, A.P, &T->st, T->cand, ncand, s_cand, (uint32_t)A.K,
                               reinterpret_cast<unsigned long long *>(smem_raw), kTailKept, wsum);
             if (nden > 0 && tid == 0) {           // Z_S g_S complete (bounded wait)
