@@ -431,16 +431,25 @@ template <typename SH = MergeShared> __device__ __forceinline__ void merge_body(
 #pragma unroll 1
         for (int ub = 0; ub < nU; ub += 2 * (int)blockDim.x) {
             const int ua = ub + threadIdx.x, uc = ua + blockDim.x;
-            const int la = min(ua, nU - 1), lc = min(uc, nU - 1);
+            if (ua >= nU) continue;               // (a large block: most threads have none)
+            const int la = ua, lc = min(uc, nU - 1);
             const unsigned long long ka = sh.skey[la], kc = sh.skey[lc];
             const int32_t ia = sh.uidx[la], ic = sh.uidx[lc];
             int ra = 0, rc = 0;
+            if (uc < nU) {
 #pragma unroll 4
-            for (int v = 0; v < nU; ++v) {
-                const unsigned long long kv = sh.skey[v];
-                const int32_t iv = sh.uidx[v];
-                ra += (int)((kv > ka) | ((kv == ka) & (iv < ia)));
-                rc += (int)((kv > kc) | ((kv == kc) & (iv < ic)));
+                for (int v = 0; v < nU; ++v) {
+                    const unsigned long long kv = sh.skey[v];
+                    const int32_t iv = sh.uidx[v];
+                    ra += (int)((kv > ka) | ((kv == ka) & (iv < ia)));
+                    rc += (int)((kv > kc) | ((kv == kc) & (iv < ic)));
+                }
+            } else {
+#pragma unroll 4
+                for (int v = 0; v < nU; ++v) {
+                    const unsigned long long kv = sh.skey[v];
+                    ra += (int)((kv > ka) | ((kv == ka) & (sh.uidx[v] < ia)));
+                }
             }
             if (ua < nU) sh.inSp[ua] = ra < k ? 1 : 0;
             if (uc < nU) sh.inSp[uc] = rc < k ? 1 : 0;

@@ -206,7 +206,8 @@ __device__ __forceinline__ void sel_rank_finish(const unsigned long long *w, int
 #pragma unroll 1
     for (int ub = 0; ub < n; ub += 2 * (int)blockDim.x) {
         const int ua = ub + threadIdx.x, uc = ua + blockDim.x;
-        const unsigned long long wa = w[min(ua, n - 1)], wc = w[min(uc, n - 1)];
+        if (ua >= n) continue;                   // (a large block: most threads have none)
+        const unsigned long long wa = w[ua], wc = w[min(uc, n - 1)];
         uint32_t ra = 0, rc = 0;
 #pragma unroll 4
         for (int v = 0; v < n; ++v) {
@@ -221,7 +222,8 @@ __device__ __forceinline__ void sel_rank_finish(const unsigned long long *w, int
 #pragma unroll 1
     for (int ub = 0; ub < n; ub += 2 * (int)blockDim.x) {
         const int ua = ub + threadIdx.x, uc = ua + blockDim.x;
-        const uint32_t ia = ~(uint32_t)(w[min(ua, n - 1)] & 0xffffffffull);
+        if (ua >= n) continue;
+        const uint32_t ia = ~(uint32_t)(w[ua] & 0xffffffffull);
         const uint32_t ic = ~(uint32_t)(w[min(uc, n - 1)] & 0xffffffffull);
         uint32_t pa = 0, pc = 0;
 #pragma unroll 4
