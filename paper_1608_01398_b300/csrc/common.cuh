@@ -287,6 +287,11 @@ int build_missing_lists(iht_dataset *ds);
 constexpr int kPadGroup = 8;
 bool padded_lists_wanted(const iht_dataset *ds);
 int launch_missing_sums(iht_dataset *ds, const float *r32, float *M, const int32_t *done);
+// The missing-call sums plus the limb image of r for the next tensor-core pass
+// (the fused solve); EINVAL when r does not fit the kernel's shared memory.
+bool missing_limbs_supported(const iht_dataset *ds, int64_t nlim);
+int launch_missing_sums_limbs(iht_dataset *ds, const float *r32, float *M, const int32_t *done,
+                              uint8_t *bimg, TcParams *prm, int64_t nlim);
 int setup_rows(iht_dataset *ds, const int32_t *rows_dev, int64_t n_rows);
 int launch_counts(iht_dataset *ds, int64_t n_rows);
 int scatter_rows_f64(iht_dataset *ds, const int32_t *rows_dev, int64_t n_rows, const double *src,

@@ -8,6 +8,7 @@
 // an (n_obs - 1) denominator), with every operation correctly rounded so the
 // values match any IEEE FP64 evaluation of the same expression bit for bit.
 #include "common.cuh"
+#include "limbs.cuh"
 
 namespace iht {
 
@@ -640,18 +641,67 @@ int build_missing_lists(iht_dataset *ds)
 // sample offsets) at a time, adding in list order; the next 16-byte piece is
 // requested before the current one is summed, so one list latency is exposed
 // per SNP rather than one per piece.
-template <typename IdxT>
+//
+// With kLimbs (the fused solve), the blocks also write the next tensor-core
+// pass's limb image of r, which otherwise the limb kernel writes: every block
+// has all of r in shared memory, so each finds max |r| (the limbs' scale) by
+// itself and encodes its own share of the samples, and block 0 forms R = sum
+// of r in the limb kernel's order (a running FP64 sum per residue of i mod
+// 1024, a shuffle tree per 32 residues, the same tree over the 32 warp sums)
+// -- the limb kernel's bytes and R, bit for bit.
+template <typename IdxT, bool kLimbs>
 __global__ void __launch_bounds__(512) k_missing_sum_smem(const int64_t *__restrict__ off,
                                                           const IdxT *__restrict__ idx, int64_t p,
                                                           const float *__restrict__ r32,
                                                           int64_t n_pad, float *__restrict__ M,
-                                                          const int32_t *__restrict__ done)
+                                                          const int32_t *__restrict__ done,
+                                                          uint8_t *__restrict__ bimg, TcParams *prm,
+                                                          int64_t nlim)
 {
     extern __shared__ float rs_miss[];
     if (done && *done) return;
     constexpr int kPer = 16 / (int)sizeof(IdxT);
     for (int64_t i = threadIdx.x; i < n_pad; i += blockDim.x) rs_miss[i] = r32[i];
     __syncthreads();
+    if constexpr (kLimbs) {
+        __shared__ float smax[16];
+        __shared__ double wsr[32];
+        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+        float m = 0.0f;
+        for (int64_t i = threadIdx.x; i < nlim; i += blockDim.x) m = fmaxf(m, fabsf(rs_miss[i]));
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+        if (lane == 0) smax[warp] = m;
+        __syncthreads();
+        m = 0.0f;
+#pragma unroll 1
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) m = fmaxf(m, smax[w]);
+        const float s0 = limb_scale(m);
+        const int64_t per = (nlim + gridDim.x - 1) / gridDim.x;
+        const int64_t i0 = (int64_t)blockIdx.x * per, i1 = min(nlim, i0 + per);
+        for (int64_t i = i0 + threadIdx.x; i < i1; i += blockDim.x) limb_encode(rs_miss[i], s0, bimg, i);
+        if (blockIdx.x == 0) {
+            // thread h holds the limb kernel's residues t = h and t = h + 512
+            double a0 = 0.0, a1 = 0.0;
+            for (int64_t i = threadIdx.x; i < nlim; i += 1024) a0 += (double)rs_miss[i];
+            for (int64_t i = threadIdx.x + 512; i < nlim; i += 1024) a1 += (double)rs_miss[i];
+            a0 = warp_sum(a0);
+            a1 = warp_sum(a1);
+            if (lane == 0) {
+                wsr[warp] = a0;
+                wsr[warp + 16] = a1;
+            }
+            for (int b = threadIdx.x; b < 256; b += blockDim.x) bimg[256 + 256 * (nlim >> 5) + b] = 0;
+            __syncthreads();
+            if (warp == 0) {
+                const double R = warp_sum(wsr[lane]);
+                if (lane == 0) {
+                    prm->s0 = s0;
+                    prm->R = (float)R;
+                }
+            }
+        }
+    }
     const uint4 *__restrict__ idx4 = reinterpret_cast<const uint4 *>(idx);
     constexpr int kBatch = 8;                                 // 16-byte list pieces in flight
     for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < p;
@@ -715,31 +765,51 @@ __global__ void __launch_bounds__(256) k_missing_sum(const int64_t *__restrict__
     }
 }
 
+bool missing_limbs_supported(const iht_dataset *ds, int64_t nlim)
+{
+    return sizeof(float) * (size_t)ds->n_pad <= 160 * 1024 && nlim <= ds->n_pad;
+}
+
+template <bool kLimbs>
+static int launch_missing_smem(iht_dataset *ds, const float *r32, float *M, const int32_t *done,
+                               uint8_t *bimg, TcParams *prm, int64_t nlim)
+{
+    cudaStream_t s = ds->ctx->stream;
+    const size_t smem = sizeof(float) * (size_t)ds->n_pad;
+    static thread_local int configured = -1;
+    if (configured != ds->ctx->device) {
+        IHT_CUDA(cudaFuncSetAttribute(k_missing_sum_smem<uint16_t, kLimbs>,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024));
+        IHT_CUDA(cudaFuncSetAttribute(k_missing_sum_smem<int32_t, kLimbs>,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024));
+        configured = ds->ctx->device;
+    }
+    const int per_sm = smem <= 40 * 1024 ? 4 : (smem <= 48 * 1024 ? 3 : 1);
+    const int blocks = (int)std::min<int64_t>(std::max<int64_t>(ceil_div(ds->p, 512), 1),
+                                              (int64_t)ds->ctx->num_sms * per_sm);
+    if (ds->miss_idx16)
+        k_missing_sum_smem<uint16_t, kLimbs><<<blocks, 512, smem, s>>>(
+            ds->miss_off, (const uint16_t *)ds->miss_idx, ds->p, r32, ds->n_pad, M, done, bimg, prm, nlim);
+    else
+        k_missing_sum_smem<int32_t, kLimbs><<<blocks, 512, smem, s>>>(
+            ds->miss_off, (const int32_t *)ds->miss_idx, ds->p, r32, ds->n_pad, M, done, bimg, prm, nlim);
+    note_launch();
+    IHT_CUDA(cudaGetLastError());
+    return IHT_OK;
+}
+
+int launch_missing_sums_limbs(iht_dataset *ds, const float *r32, float *M, const int32_t *done,
+                              uint8_t *bimg, TcParams *prm, int64_t nlim)
+{
+    if (!missing_limbs_supported(ds, nlim)) return IHT_EINVAL;
+    return launch_missing_smem<true>(ds, r32, M, done, bimg, prm, nlim);
+}
+
 int launch_missing_sums(iht_dataset *ds, const float *r32, float *M, const int32_t *done)
 {
     cudaStream_t s = ds->ctx->stream;
     const size_t smem = sizeof(float) * (size_t)ds->n_pad;
-    if (smem <= 160 * 1024) {
-        static thread_local int configured = -1;
-        if (configured != ds->ctx->device) {
-            IHT_CUDA(cudaFuncSetAttribute(k_missing_sum_smem<uint16_t>,
-                                          cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024));
-            IHT_CUDA(cudaFuncSetAttribute(k_missing_sum_smem<int32_t>,
-                                          cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024));
-            configured = ds->ctx->device;
-        }
-        const int per_sm = smem <= 40 * 1024 ? 4 : (smem <= 48 * 1024 ? 3 : 1);
-        const int blocks = (int)std::min<int64_t>(ceil_div(ds->p, 512), (int64_t)ds->ctx->num_sms * per_sm);
-        if (ds->miss_idx16)
-            k_missing_sum_smem<uint16_t><<<blocks, 512, smem, s>>>(
-                ds->miss_off, (const uint16_t *)ds->miss_idx, ds->p, r32, ds->n_pad, M, done);
-        else
-            k_missing_sum_smem<int32_t><<<blocks, 512, smem, s>>>(
-                ds->miss_off, (const int32_t *)ds->miss_idx, ds->p, r32, ds->n_pad, M, done);
-        note_launch();
-        IHT_CUDA(cudaGetLastError());
-        return IHT_OK;
-    }
+    if (smem <= 160 * 1024) return launch_missing_smem<false>(ds, r32, M, done, nullptr, nullptr, 0);
     const int blocks = (int)std::min<int64_t>(ceil_div(ds->p, 64), (int64_t)ds->ctx->num_sms * 16);
     if (ds->miss_idx16)
         k_missing_sum<uint16_t><<<blocks, 256, 0, s>>>(ds->miss_off, (const uint16_t *)ds->miss_idx,

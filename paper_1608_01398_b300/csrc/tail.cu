@@ -59,6 +59,8 @@ struct TailArgs {
     uint8_t *bimg;                       // limb image of the next tensor-core pass
     TcParams *prm;
     int64_t nlim;                        // samples the limb image covers
+    int limbs_here;                      // 1: this kernel writes the limb image (else the
+                                         //   missing-call sums kernel that follows does)
     cudaGraphConditionalHandle cond;
 };
 
@@ -395,11 +397,25 @@ __global__ void __launch_bounds__(kTailThreads) k_tail(const __grid_constant__ T
         }
     }
 
-    // E: the accepted residual, centred, and the next pass's limb image
+    // E: the accepted residual, centred, and -- when the missing-call sums
+    // kernel cannot (r too long for its shared memory) -- the next pass's limb
+    // image
     __syncthreads();                      // every thread has read s_state in the loop
     if (tid == 0) s_state = *(volatile int32_t *)&sc->done;
     __syncthreads();
-    if (!s_state) {
+    if (!s_state && !A.limbs_here) {
+        // the accepted residual, centred; the limb image follows in the
+        // missing-call sums kernel (it holds all of r in shared memory)
+        const double *acc = *(volatile int *)&T->acc2 ? A.rc64_2 : A.rc64;
+        const double mean = sc->sum_r / (double)sc->n_rows;
+#pragma unroll 1
+        for (int64_t i = (int64_t)blockIdx.x * blockDim.x + tid; i < A.n_pad;
+             i += (int64_t)gridDim.x * blockDim.x) {
+            const double v = acc[i];
+            if (acc != A.r64) A.r64[i] = v;
+            A.r32[i] = A.used[i] ? (float)(v - mean) : 0.0f;
+        }
+    } else if (!s_state) {
         const int64_t nthr = (int64_t)gridDim.x * blockDim.x;
         const double *acc = *(volatile int *)&T->acc2 ? A.rc64_2 : A.rc64;   // the accepted residual
         // the limb kernel's thread t (of 1024) forms the max |r| and the sum of r
@@ -582,7 +598,10 @@ static int build_fused_graph(iht_dataset *ds, int k, int K, const TailArgs &args
             rc = IHT_ECUDA;
         }
         const int32_t *done = &ws->sc->done;
-        if (rc == IHT_OK) rc = launch_missing_sums(ds, ws->r32, ws->Mj, done);
+        if (rc == IHT_OK)
+            rc = args.limbs_here ? launch_missing_sums(ds, ws->r32, ws->Mj, done)
+                                 : launch_missing_sums_limbs(ds, ws->r32, ws->Mj, done, args.bimg,
+                                                             args.prm, args.nlim);
         if (rc == IHT_OK) rc = launch_grad_tc_main(ds, ws->r32, ws->g, done);
         if (rc == IHT_OK) rc = launch_cov_grad(ds, ws->r32, ws->g, done);
         cudaGraph_t captured = nullptr;
@@ -670,7 +689,9 @@ int run_fused_solve(iht_dataset *ds, int k, int K, int impl)
     a.bimg = bimg;
     a.prm = prm;
     a.nlim = nlim;
-    const uint64_t key[10] = {(uint64_t)k | ((uint64_t)ds->q << 32), (uint64_t)K, (uint64_t)impl,
+    a.limbs_here = missing_limbs_supported(ds, nlim) ? 0 : 1;
+    const uint64_t key[10] = {(uint64_t)k | ((uint64_t)ds->q << 32) | ((uint64_t)a.limbs_here << 48),
+                              (uint64_t)K, (uint64_t)impl,
                               (uint64_t)(uintptr_t)ws->tail, (uint64_t)(uintptr_t)bimg,
                               grad_tc_scratch_id(), (uint64_t)(uintptr_t)ws->S,
                               (uint64_t)(uintptr_t)ws->used, (uint64_t)grid,
