@@ -638,7 +638,7 @@ __device__ __forceinline__ void decide_body(Scalars *sc, const double *partials,
     if (sc->htp) return;
     const int it = sc->iter;
 #pragma unroll 1
-    for (int c = threadIdx.x; c < k; c += blockDim.x) {
+    for (int c = threadIdx.x; c < k && S; c += blockDim.x) {    // (S null: only the scalars)
         S[c] = Sp[c];
         bS[c] = bSp[c];
         if (tr.supp) tr.supp[(size_t)it * k + c] = Sp[c];

@@ -29,7 +29,7 @@ constexpr uint32_t kBarSpin = 1u << 22;       // bounded barrier waits (polls; s
 
 struct TailWork {                     // zeroed before every solve
     unsigned long long bar_count;     // grid barrier: arrivals since the solve began (+ kBarAbort)
-    int bar_err, acc2;                // 1: a barrier wait gave up; the second candidate was accepted
+    int bar_err, pad_;                // 1: a barrier wait gave up
     unsigned int den_ticket;          // blocks done with Z_S g_S in this launch
     Scalars spec;                     // the second candidate's projection scalars (mu / kappa)
     SelState st;                      // selection state (boundary bin, candidate count)
@@ -159,10 +159,7 @@ __global__ void __launch_bounds__(kTailThreads) k_tail(const __grid_constant__ T
     }
 
     // A: g_S and ||g_S||^2 for the step size (block 0, first warp); histogram of |g|
-    if (b0) {
-        if (tid == 0) T->acc2 = 0;
-        gather_gS_body(A.g, A.S, A.k, A.coef, &ssc);
-    }
+    if (b0) gather_gS_body(A.g, A.S, A.k, A.coef, &ssc);
     {
         uint32_t *hs = reinterpret_cast<uint32_t *>(smem_raw);
 #pragma unroll 1
@@ -339,60 +336,80 @@ __global__ void __launch_bounds__(kTailThreads) k_tail(const __grid_constant__ T
     }
     if (!grid_sync_put(T, sc, &ssc, b0)) return tail_stop(A);
     if (b0 && tid == 0) T->den_ticket = 0;    // every projection has passed its wait
-    if (tid == 0) s_state = *(volatile int32_t *)&sc->done;
+
+    // D: every block takes the decisions itself -- the scalars block 0 wrote
+    // back, both candidates' partial sums and the second one's scalars give
+    // every block the same outcome -- so the centring needs no barrier; block
+    // 0's scalars remain the solve's and only block 0 copies S+ into S.
+    // Later attempts (both candidates rejected) run one at a time: projection
+    // on block 0, residual on all, decision on block 0.
+    __shared__ int s_acc2;                // 1: the second candidate was accepted
+    if (!b0 && tid < kScWords)
+        reinterpret_cast<unsigned long long *>(&ssc)[tid] =
+            reinterpret_cast<const volatile unsigned long long *>(sc)[tid];
+    __syncthreads();
+    if (tid == 0) {
+        s_state = ssc.done;
+        s_acc2 = 0;
+    }
     __syncthreads();
     if (!s_state) {
-        if (b0) {
-            __shared__ int s_second;
-            decide_body(&ssc, A.partials, A.npart, A.S, A.bS, s_Sp[0], s_bSp[0], TraceDev{});
-            __syncthreads();
-            if (tid == 0) {
-                s_second = ssc.retry && !ssc.done && ssc.bt_last == 1;
-                if (s_second) {                      // the second candidate is the shrunk step
-                    ssc.changed = T->spec.changed;
-                    ssc.dd = T->spec.dd;
-                    ssc.bb = T->spec.bb;
-                }
-            }
-            __syncthreads();
-            if (s_second) {
-                decide_body(&ssc, A.partials2, A.npart, A.S, A.bS, A.Sp2, A.bSp2, TraceDev{});
-                __syncthreads();
-                if (tid == 0) T->acc2 = !ssc.retry;
+        __shared__ int s_second;
+        int32_t *dS = b0 ? A.S : nullptr;
+        double *dbS = b0 ? A.bS : nullptr;
+        decide_body(&ssc, A.partials, A.npart, dS, dbS, s_Sp[0], s_bSp[0], TraceDev{});
+        __syncthreads();
+        if (tid == 0) {
+            s_second = ssc.retry && !ssc.done && ssc.bt_last == 1;
+            if (s_second) {                      // the second candidate is the shrunk step
+                ssc.changed = T->spec.changed;
+                ssc.dd = T->spec.dd;
+                ssc.bb = T->spec.bb;
             }
         }
-        if (!grid_sync_put(T, sc, &ssc, b0)) return tail_stop(A);
-        if (tid == 0)
-            s_state = (*(volatile int32_t *)&sc->done ? 1 : 0) | (*(volatile int32_t *)&sc->retry ? 2 : 0);
         __syncthreads();
-        // later attempts: projection (block 0), residual (all), decision (block 0)
-        while (!(s_state & 1) && (s_state & 2)) {
-            if (b0) {
-                MergeArgs M;
-                M.g = A.g;
-                M.S = A.S;
-                M.bS = A.bS;
-                M.cand = s_cand;
-                M.K = A.K;
-                M.partials = A.partials;
-                M.npart = A.npart;
-                M.first = 0;
-                M.skip = nullptr;
-                M.Sp = A.Sp;
-                M.bSp = A.bSp;
-                M.sc = &ssc;
-                merge_body<MergeSharedT<kTailKM>>(M);
-            }
-            if (!grid_sync_put(T, sc, &ssc, b0)) return tail_stop(A);
+        if (s_second) {
+            decide_body(&ssc, A.partials2, A.npart, dS, dbS, A.Sp2, A.bSp2, TraceDev{});
+            __syncthreads();
+            if (tid == 0) s_acc2 = !ssc.retry;
+        }
+        if (tid == 0) s_state = (ssc.done ? 1 : 0) | (ssc.retry ? 2 : 0);
+        __syncthreads();
+        if (!(s_state & 1) && (s_state & 2)) {
+            while (!(s_state & 1) && (s_state & 2)) {
+                if (b0) {
+                    MergeArgs M;
+                    M.g = A.g;
+                    M.S = A.S;
+                    M.bS = A.bS;
+                    M.cand = s_cand;
+                    M.K = A.K;
+                    M.partials = A.partials;
+                    M.npart = A.npart;
+                    M.first = 0;
+                    M.skip = nullptr;
+                    M.Sp = A.Sp;
+                    M.bSp = A.bSp;
+                    M.sc = &ssc;
+                    merge_body<MergeSharedT<kTailKM>>(M);
+                }
+                if (!grid_sync_put(T, sc, &ssc, b0)) return tail_stop(A);
 #pragma unroll 1
-            for (int vb = blockIdx.x; vb < A.npart; vb += gridDim.x)
-                zmul_body(A.G, A.stride, A.rowb, A.Sp, A.k, A.bSp, -1.0, A.u64, A.v64, A.used, A.y64,
-                          A.r64, A.rc64, A.partials, A.n_pad, A.p, A.zc, vb);
-            if (!grid_sync_put(T, sc, &ssc, b0)) return tail_stop(A);
-            if (b0) decide_body(&ssc, A.partials, A.npart, A.S, A.bS, A.Sp, A.bSp, TraceDev{});
-            if (!grid_sync_put(T, sc, &ssc, b0)) return tail_stop(A);
-            if (tid == 0)
-                s_state = (*(volatile int32_t *)&sc->done ? 1 : 0) | (*(volatile int32_t *)&sc->retry ? 2 : 0);
+                for (int vb = blockIdx.x; vb < A.npart; vb += gridDim.x)
+                    zmul_body(A.G, A.stride, A.rowb, A.Sp, A.k, A.bSp, -1.0, A.u64, A.v64, A.used, A.y64,
+                              A.r64, A.rc64, A.partials, A.n_pad, A.p, A.zc, vb);
+                if (!grid_sync_put(T, sc, &ssc, b0)) return tail_stop(A);
+                if (b0) decide_body(&ssc, A.partials, A.npart, A.S, A.bS, A.Sp, A.bSp, TraceDev{});
+                if (!grid_sync_put(T, sc, &ssc, b0)) return tail_stop(A);
+                if (tid == 0)
+                    s_state = (*(volatile int32_t *)&sc->done ? 1 : 0) | (*(volatile int32_t *)&sc->retry ? 2 : 0);
+                __syncthreads();
+            }
+            // the scalars block 0 wrote back at the last barrier
+            if (!b0 && tid < kScWords)
+                reinterpret_cast<unsigned long long *>(&ssc)[tid] =
+                    reinterpret_cast<const volatile unsigned long long *>(sc)[tid];
+            if (tid == 0) s_acc2 = 0;
             __syncthreads();
         }
     }
@@ -400,14 +417,13 @@ __global__ void __launch_bounds__(kTailThreads) k_tail(const __grid_constant__ T
     // E: the accepted residual, centred, and -- when the missing-call sums
     // kernel cannot (r too long for its shared memory) -- the next pass's limb
     // image
-    __syncthreads();                      // every thread has read s_state in the loop
-    if (tid == 0) s_state = *(volatile int32_t *)&sc->done;
+    if (tid == 0) s_state = ssc.done;
     __syncthreads();
     if (!s_state && !A.limbs_here) {
-        // the accepted residual, centred; the limb image follows in the
-        // missing-call sums kernel (it holds all of r in shared memory)
-        const double *acc = *(volatile int *)&T->acc2 ? A.rc64_2 : A.rc64;
-        const double mean = sc->sum_r / (double)sc->n_rows;
+        // the limb image follows in the missing-call sums kernel (it holds all
+        // of r in shared memory)
+        const double *acc = s_acc2 ? A.rc64_2 : A.rc64;
+        const double mean = ssc.sum_r / (double)ssc.n_rows;
 #pragma unroll 1
         for (int64_t i = (int64_t)blockIdx.x * blockDim.x + tid; i < A.n_pad;
              i += (int64_t)gridDim.x * blockDim.x) {
@@ -417,13 +433,13 @@ __global__ void __launch_bounds__(kTailThreads) k_tail(const __grid_constant__ T
         }
     } else if (!s_state) {
         const int64_t nthr = (int64_t)gridDim.x * blockDim.x;
-        const double *acc = *(volatile int *)&T->acc2 ? A.rc64_2 : A.rc64;   // the accepted residual
+        const double *acc = s_acc2 ? A.rc64_2 : A.rc64;                   // the accepted residual
         // the limb kernel's thread t (of 1024) forms the max |r| and the sum of r
         // over the samples i = t mod 1024 in increasing i; here block b takes
         // t = 8 b .. 8 b + 7, its thread (t, j) centres sample t + 1024 (j0 + j)
         // (16 at a time), and the first 8 threads run the sums in that order
         __shared__ float s_r[kTailThreads / 8][8];
-        const double mean = sc->sum_r / (double)sc->n_rows;
+        const double mean = ssc.sum_r / (double)ssc.n_rows;
         const int tt = tid & 7, jj = tid >> 3;
 #pragma unroll 1
         for (int64_t t0 = 8 * (int64_t)blockIdx.x; t0 < 1024; t0 += 8 * (int64_t)gridDim.x) {
@@ -494,7 +510,13 @@ __global__ void __launch_bounds__(kTailThreads) k_tail(const __grid_constant__ T
         for (int64_t i = (int64_t)blockIdx.x * blockDim.x + tid; i < A.nlim; i += nthr)
             limb_encode(A.r32[i], s0, A.bimg, i);
     }
-    if (b0 && tid == 0) cudaGraphSetConditional(A.cond, *(volatile int32_t *)&sc->done ? 0u : 1u);
+    if (b0) {                             // block 0's scalars are the solve's
+        __syncthreads();
+        if (tid < kScWords)
+            reinterpret_cast<unsigned long long *>(sc)[tid] = reinterpret_cast<const unsigned long long *>(&ssc)[tid];
+        __syncthreads();
+    }
+    if (b0 && tid == 0) cudaGraphSetConditional(A.cond, ssc.done ? 0u : 1u);
 }
 
 // ---------------------------------------------------------------------------
