@@ -431,12 +431,13 @@ template <typename SH = MergeShared> __device__ __forceinline__ void merge_body(
 #pragma unroll 1
         for (int ub = 0; ub < nU; ub += 2 * (int)blockDim.x) {
             const int ua = ub + threadIdx.x, uc = ua + blockDim.x;
+            const bool two = __any_sync(0xffffffffu, uc < nU);   // one path per warp
             if (ua >= nU) continue;               // (a large block: most threads have none)
             const int la = ua, lc = min(uc, nU - 1);
             const unsigned long long ka = sh.skey[la], kc = sh.skey[lc];
             const int32_t ia = sh.uidx[la], ic = sh.uidx[lc];
             int ra = 0, rc = 0;
-            if (uc < nU) {
+            if (two) {
 #pragma unroll 4
                 for (int v = 0; v < nU; ++v) {
                     const unsigned long long kv = sh.skey[v];

@@ -71,13 +71,20 @@ __device__ __forceinline__ void sel_find(const uint32_t *h, int nbins, uint32_t 
 // Calls f(key, index) for every key; 16-byte loads, two in flight per thread,
 // over the 16-byte aligned middle, the (at most 3 + 3) keys around it one at a
 // time.
+// (b, nb: this block's index among the nb blocks that share the keys; by
+// default the grid's)
 template <typename F>
-__device__ __forceinline__ void sel_each(const float *__restrict__ keys, int64_t p, F &&f)
+__device__ __forceinline__ void sel_each(const float *__restrict__ keys, int64_t p, F &&f, int b = -1,
+                                         int nb = -1)
 {
+    if (nb < 0) {
+        b = blockIdx.x;
+        nb = gridDim.x;
+    }
     const int64_t head = std::min<int64_t>(p, (int64_t)((16u - ((uintptr_t)keys & 15u)) & 15u) >> 2);
     const float4 *k4 = reinterpret_cast<const float4 *>(keys + head);
-    const int64_t n4 = (p - head) >> 2, step = (int64_t)gridDim.x * blockDim.x;
-    const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t n4 = (p - head) >> 2, step = (int64_t)nb * blockDim.x;
+    const int64_t tid = (int64_t)b * blockDim.x + threadIdx.x;
     int64_t q = tid;
     for (; q + step < n4; q += 2 * step) {
         const float4 a = k4[q], b = k4[q + step];

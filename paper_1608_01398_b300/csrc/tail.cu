@@ -35,8 +35,6 @@ struct TailWork {                     // zeroed before every solve
     SelState st;                      // selection state (boundary bin, candidate count)
     uint32_t hist[kSelBins];          // histogram of |g| bits 30..20
     unsigned long long cand[kSelCap]; // candidate words (key << 32 | ~index)
-    float part_m[1024];               // limb prerequisites: max |r| and sum of r over
-    double part_acc[1024];            //   the samples i = t mod 1024 (the limb kernel's layout)
 };
 
 struct TailArgs {
@@ -59,8 +57,6 @@ struct TailArgs {
     uint8_t *bimg;                       // limb image of the next tensor-core pass
     TcParams *prm;
     int64_t nlim;                        // samples the limb image covers
-    int limbs_here;                      // 1: this kernel writes the limb image (else the
-                                         //   missing-call sums kernel that follows does)
     cudaGraphConditionalHandle cond;
 };
 
@@ -140,7 +136,6 @@ __global__ void __launch_bounds__(kTailThreads) k_tail(const __grid_constant__ T
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ uint32_t wsum[32];
     __shared__ uint32_t res[3];
-    __shared__ double red[32];
     __shared__ int s_state;
     TailWork *T = A.T;
     Scalars *sc = A.sc;
@@ -158,9 +153,11 @@ __global__ void __launch_bounds__(kTailThreads) k_tail(const __grid_constant__ T
         return;
     }
 
-    // A: g_S and ||g_S||^2 for the step size (block 0, first warp); histogram of |g|
+    // A: g_S and ||g_S||^2 for the step size (block 0, first warp); histogram of
+    // |g| over the other blocks (all of them on a one-block grid)
     if (b0) gather_gS_body(A.g, A.S, A.k, A.coef, &ssc);
-    {
+    const int hb = gridDim.x > 1 ? (int)blockIdx.x - 1 : 0, hnb = gridDim.x > 1 ? (int)gridDim.x - 1 : 1;
+    if (hb >= 0) {
         uint32_t *hs = reinterpret_cast<uint32_t *>(smem_raw);
 #pragma unroll 1
         for (int b = tid; b < kSelBins; b += blockDim.x) hs[b] = 0;
@@ -170,7 +167,7 @@ __global__ void __launch_bounds__(kTailThreads) k_tail(const __grid_constant__ T
             const uint32_t key = sel_key(x);
             nan |= key > 0x7f800000u;
             atomicAdd(&hs[key >> 20], 1u);
-        });
+        }, hb, hnb);
         if (nan) atomicOr(&T->st.err, 1u);
         __syncthreads();
 #pragma unroll 1
@@ -229,6 +226,8 @@ __global__ void __launch_bounds__(kTailThreads) k_tail(const __grid_constant__ T
     // attempt after the other; later attempts, when both are rejected, run one
     // at a time.
     __shared__ int32_t s_cand[2 * kTailKM];
+    __shared__ int32_t s_S[kTailKM];
+    __shared__ double s_bS[kTailKM];
     __shared__ int32_t s_Sp[2][kTailKM];
     __shared__ double s_bSp[2][kTailKM];
     __shared__ Scalars ssc2;              // the second candidate's scalars
@@ -243,15 +242,18 @@ __global__ void __launch_bounds__(kTailThreads) k_tail(const __grid_constant__ T
                 reinterpret_cast<unsigned long long *>(&ssc)[tid] =
                     reinterpret_cast<const volatile unsigned long long *>(sc)[tid];
             const uint32_t ncand = res[1] + res[2];
-            // the genotype bytes of this block's residual on their way to L2
-            // while the candidates are chosen (S+ mostly repeats S)
+            // S and beta_S into shared memory for the projection, and the
+            // genotype bytes of this block's residual on their way to L2, while
+            // the candidates are chosen (S+ mostly repeats S)
             {
                 const int vb0 = (int)blockIdx.x < A.npart ? (int)blockIdx.x : (int)blockIdx.x - A.npart;
                 const uint8_t *gb = A.G + (int64_t)vb0 * kZmulBytes;
 #pragma unroll 1
                 for (int c = tid; c < A.k; c += blockDim.x) {
-                    const int64_t j = A.S[c];
-                    if (j < A.p) asm volatile("prefetch.global.L2 [%0];" ::"l"(gb + j * A.stride));
+                    const int32_t j = A.S[c];
+                    s_S[c] = j;
+                    s_bS[c] = A.bS[c];
+                    if (j < A.p) asm volatile("prefetch.global.L2 [%0];" ::"l"(gb + (int64_t)j * A.stride));
                 }
             }
             sel_finish_narrow(A.g, A.P, &T->st, T->cand, ncand, s_cand, (uint32_t)A.K,
@@ -280,8 +282,8 @@ __global__ void __launch_bounds__(kTailThreads) k_tail(const __grid_constant__ T
                 __syncthreads();
                 MergeArgs M;
                 M.g = A.g;
-                M.S = A.S;
-                M.bS = A.bS;
+                M.S = s_S;
+                M.bS = s_bS;
                 M.cand = s_cand;
                 M.K = A.K;
                 M.partials = A.partials;
@@ -414,14 +416,11 @@ __global__ void __launch_bounds__(kTailThreads) k_tail(const __grid_constant__ T
         }
     }
 
-    // E: the accepted residual, centred, and -- when the missing-call sums
-    // kernel cannot (r too long for its shared memory) -- the next pass's limb
-    // image
+    // E: the accepted residual, centred (the next pass's limb image follows in
+    // the missing-call sums kernel, which holds all of r in shared memory)
     if (tid == 0) s_state = ssc.done;
     __syncthreads();
-    if (!s_state && !A.limbs_here) {
-        // the limb image follows in the missing-call sums kernel (it holds all
-        // of r in shared memory)
+    if (!s_state) {
         const double *acc = s_acc2 ? A.rc64_2 : A.rc64;
         const double mean = ssc.sum_r / (double)ssc.n_rows;
 #pragma unroll 1
@@ -431,84 +430,6 @@ __global__ void __launch_bounds__(kTailThreads) k_tail(const __grid_constant__ T
             if (acc != A.r64) A.r64[i] = v;
             A.r32[i] = A.used[i] ? (float)(v - mean) : 0.0f;
         }
-    } else if (!s_state) {
-        const int64_t nthr = (int64_t)gridDim.x * blockDim.x;
-        const double *acc = s_acc2 ? A.rc64_2 : A.rc64;                   // the accepted residual
-        // the limb kernel's thread t (of 1024) forms the max |r| and the sum of r
-        // over the samples i = t mod 1024 in increasing i; here block b takes
-        // t = 8 b .. 8 b + 7, its thread (t, j) centres sample t + 1024 (j0 + j)
-        // (16 at a time), and the first 8 threads run the sums in that order
-        __shared__ float s_r[kTailThreads / 8][8];
-        const double mean = ssc.sum_r / (double)ssc.n_rows;
-        const int tt = tid & 7, jj = tid >> 3;
-#pragma unroll 1
-        for (int64_t t0 = 8 * (int64_t)blockIdx.x; t0 < 1024; t0 += 8 * (int64_t)gridDim.x) {
-            const int64_t t = t0 + tt;
-            float m = 0.0f;
-            double sum = 0.0;
-#pragma unroll 1
-            for (int64_t j0 = 0; 1024 * j0 < A.n_pad; j0 += kTailThreads / 8) {
-                const int64_t i = t + 1024 * (j0 + jj);
-                float r = 0.0f;
-                if (i < A.n_pad) {
-                    const double v = acc[i];
-                    if (acc != A.r64) A.r64[i] = v;
-                    r = A.used[i] ? (float)(v - mean) : 0.0f;
-                    A.r32[i] = r;
-                }
-                s_r[jj][tt] = r;
-                __syncthreads();
-                if (tid < 8) {
-#pragma unroll 1
-                    for (int j = 0; j < kTailThreads / 8; ++j) {
-                        const int64_t ij = t + 1024 * (j0 + j);
-                        if (ij < A.nlim) {
-                            const float rj = s_r[j][tid];
-                            m = fmaxf(m, fabsf(rj));
-                            sum += (double)rj;
-                        }
-                    }
-                }
-                __syncthreads();
-            }
-            if (tid < 8) {
-                T->part_m[t] = m;
-                T->part_acc[t] = sum;
-            }
-        }
-        if (!grid_sync_put(T, sc, &ssc, b0)) return tail_stop(A);
-        float m = 0.0f;
-        for (int t = tid; t < 1024; t += blockDim.x) m = fmaxf(m, T->part_m[t]);
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
-        if ((tid & 31) == 0) reinterpret_cast<float *>(wsum)[tid >> 5] = m;
-        __syncthreads();
-        m = 0.0f;
-#pragma unroll 1
-        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) m = fmaxf(m, reinterpret_cast<float *>(wsum)[w]);
-        const float s0 = limb_scale(m);
-        if (b0) {
-            // R by the limb kernel's reduction: a shuffle tree per 32 of its 1024
-            // threads, then the same tree over the 32 warp sums
-            const int lane = tid & 31, warp = tid >> 5;
-            for (int w = warp; w < 32; w += blockDim.x >> 5) {
-                const double x = warp_sum(T->part_acc[32 * w + lane]);
-                if (lane == 0) red[w] = x;
-            }
-            __syncthreads();
-            if (warp == 0) {
-                const double R = warp_sum(red[lane]);
-                if (lane == 0) {
-                    A.prm->s0 = s0;
-                    A.prm->R = (float)R;
-                }
-            }
-#pragma unroll 1
-            for (int b = tid; b < 256; b += blockDim.x) A.bimg[256 + 256 * (A.nlim >> 5) + b] = 0;
-        }
-#pragma unroll 1
-        for (int64_t i = (int64_t)blockIdx.x * blockDim.x + tid; i < A.nlim; i += nthr)
-            limb_encode(A.r32[i], s0, A.bimg, i);
     }
     if (b0) {                             // block 0's scalars are the solve's
         __syncthreads();
@@ -621,9 +542,7 @@ static int build_fused_graph(iht_dataset *ds, int k, int K, const TailArgs &args
         }
         const int32_t *done = &ws->sc->done;
         if (rc == IHT_OK)
-            rc = args.limbs_here ? launch_missing_sums(ds, ws->r32, ws->Mj, done)
-                                 : launch_missing_sums_limbs(ds, ws->r32, ws->Mj, done, args.bimg,
-                                                             args.prm, args.nlim);
+            rc = launch_missing_sums_limbs(ds, ws->r32, ws->Mj, done, args.bimg, args.prm, args.nlim);
         if (rc == IHT_OK) rc = launch_grad_tc_main(ds, ws->r32, ws->g, done);
         if (rc == IHT_OK) rc = launch_cov_grad(ds, ws->r32, ws->g, done);
         cudaGraph_t captured = nullptr;
@@ -676,6 +595,7 @@ int run_fused_solve(iht_dataset *ds, int k, int K, int impl)
     int64_t nlim = 0;
     int rc = grad_tc_limb_buffers(ds, &bimg, &prm, &nlim);
     if (rc) return rc;
+    if (!missing_limbs_supported(ds, nlim)) return IHT_EAGAIN;   // (the pass's B operand fits first)
     TailArgs a = {};
     a.G = ds->G;
     a.stride = ds->stride;
@@ -711,8 +631,7 @@ int run_fused_solve(iht_dataset *ds, int k, int K, int impl)
     a.bimg = bimg;
     a.prm = prm;
     a.nlim = nlim;
-    a.limbs_here = missing_limbs_supported(ds, nlim) ? 0 : 1;
-    const uint64_t key[10] = {(uint64_t)k | ((uint64_t)ds->q << 32) | ((uint64_t)a.limbs_here << 48),
+    const uint64_t key[10] = {(uint64_t)k | ((uint64_t)ds->q << 32),
                               (uint64_t)K, (uint64_t)impl,
                               (uint64_t)(uintptr_t)ws->tail, (uint64_t)(uintptr_t)bimg,
                               grad_tc_scratch_id(), (uint64_t)(uintptr_t)ws->S,
