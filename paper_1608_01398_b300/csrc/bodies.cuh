@@ -586,20 +586,32 @@ struct TraceDev {
 
 // Backtracking decision for the candidate of k_merge, whose residual r+ the
 // preceding pass wrote (partials: sum r+, sum r+^2, sum (r+ - r)^2).
+//
+// pre (optional): the values the body would compute, formed ahead by the
+// caller with the same expressions -- {sum r+, sum r+^2, ||ZΔ||^2, omega,
+// the stopping measure, mu / kappa} -- so a fused kernel can form them for
+// both candidates at once.
 __device__ __forceinline__ void decide_body(Scalars *sc, const double *partials, int npart,
                                             int32_t *S, double *bS, const int32_t *Sp,
-                                            const double *bSp, const TraceDev &tr)
+                                            const double *bSp, const TraceDev &tr,
+                                            const double *pre = nullptr)
 {
     __shared__ int accept;
     const int k = sc->k;
     double s = 0.0, s2 = 0.0, zz = 0.0;
-    if (threadIdx.x < 32) warp_partials(partials, npart, s, s2, zz);
+    if (pre) {
+        s = pre[0];
+        s2 = pre[1];
+        zz = pre[2];
+    } else if (threadIdx.x < 32) {
+        warp_partials(partials, npart, s, s2, zz);
+    }
     if (threadIdx.x == 0) {
         accept = 1;
         if (sc->changed && zz > 0.0) {
-            const double omega = (1.0 - sc->c) * sc->dd / zz;
+            const double omega = pre ? pre[3] : (1.0 - sc->c) * sc->dd / zz;
             if (sc->mu >= omega && sc->bt_last < sc->max_backtrack) {
-                sc->mu = sc->mu / sc->kappa;
+                sc->mu = pre ? pre[5] : sc->mu / sc->kappa;
                 sc->bt_last += 1;
                 accept = 0;
             }
@@ -621,7 +633,7 @@ __device__ __forceinline__ void decide_body(Scalars *sc, const double *partials,
             sc->sum_r = s;
             sc->sumsq_r = s2;
             sc->f = 0.5 * s2;
-            sc->step = sqrt(sc->dd) / (sqrt(sc->bb) + 1.0);
+            sc->step = pre ? pre[4] : sqrt(sc->dd) / (sqrt(sc->bb) + 1.0);
             if (tr.objective) tr.objective[it] = sc->f;
             if (tr.mu) tr.mu[it] = sc->mu;
             if (tr.backtracks) tr.backtracks[it] = sc->bt_last;

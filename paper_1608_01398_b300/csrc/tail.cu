@@ -357,9 +357,32 @@ __global__ void __launch_bounds__(kTailThreads) k_tail(const __grid_constant__ T
     __syncthreads();
     if (!s_state) {
         __shared__ int s_second;
+        // both candidates' decision values at once, with the body's own
+        // expressions: warp c sums candidate c's partials and forms omega,
+        // warp 2 + c its stopping measure and mu / kappa
+        __shared__ double s_pre[2][6];
+        {
+            const int w = tid >> 5, c = w & 1, lane = tid & 31;
+            const double dd = c ? T->spec.dd : ssc.dd;
+            if (w < 2) {
+                double ps, ps2, pzz;
+                warp_partials(c ? A.partials2 : A.partials, A.npart, ps, ps2, pzz);
+                if (lane == 0) {
+                    s_pre[c][0] = ps;
+                    s_pre[c][1] = ps2;
+                    s_pre[c][2] = pzz;
+                    s_pre[c][3] = (1.0 - ssc.c) * dd / pzz;
+                }
+            } else if (lane == 0) {
+                const double bb = c ? T->spec.bb : ssc.bb, mu = c ? T->spec.mu : ssc.mu;
+                s_pre[c][4] = sqrt(dd) / (sqrt(bb) + 1.0);
+                s_pre[c][5] = mu / ssc.kappa;
+            }
+        }
+        __syncthreads();
         int32_t *dS = b0 ? A.S : nullptr;
         double *dbS = b0 ? A.bS : nullptr;
-        decide_body(&ssc, A.partials, A.npart, dS, dbS, s_Sp[0], s_bSp[0], TraceDev{});
+        decide_body(&ssc, A.partials, A.npart, dS, dbS, s_Sp[0], s_bSp[0], TraceDev{}, s_pre[0]);
         __syncthreads();
         if (tid == 0) {
             s_second = ssc.retry && !ssc.done && ssc.bt_last == 1;
@@ -371,7 +394,7 @@ __global__ void __launch_bounds__(kTailThreads) k_tail(const __grid_constant__ T
         }
         __syncthreads();
         if (s_second) {
-            decide_body(&ssc, A.partials2, A.npart, dS, dbS, A.Sp2, A.bSp2, TraceDev{});
+            decide_body(&ssc, A.partials2, A.npart, dS, dbS, A.Sp2, A.bSp2, TraceDev{}, s_pre[1]);
             __syncthreads();
             if (tid == 0) s_acc2 = !ssc.retry;
         }
