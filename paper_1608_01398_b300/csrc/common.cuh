@@ -231,8 +231,11 @@ struct Workspace {
     int32_t *Sp2 = nullptr;                // the second candidate of the fused kernel (mu / kappa)
     double *bSp2 = nullptr, *rc64_2 = nullptr, *partials2 = nullptr;
     cudaGraphExec_t fused_exec = nullptr;
-    uint64_t fused_key[10] = {};
+    uint64_t fused_key[12] = {};
     int fused_launches = 0;                // kernels per loop trip
+    int fused_setup_launches = 0;          // kernels ahead of the loop (whole-solve graph)
+    Scalars *sc_init = nullptr;            // device: a whole-solve graph's starting scalars
+    int32_t *flags_host = nullptr;         // pinned: barrier and pass error words after a solve
 };
 constexpr int kProfEvents = 256;
 
@@ -414,6 +417,12 @@ int write_beta_device(iht_dataset *ds, int k, double *beta_out);
 // supported (then the per-iteration graph runs)
 bool fused_supported(const iht_dataset *ds, int k, int impl);
 int run_fused_solve(iht_dataset *ds, int k, int K, int impl);
+// The whole solve from beta = 0 as one graph launch (set-up, then the loop):
+// h is the solve's starting scalars; on return ws->sc_host holds the final
+// ones.  EAGAIN (nothing enqueued) when the graph cannot be built.
+int run_whole_fused_solve(iht_dataset *ds, int k, int K, int impl, const Scalars &h);
+int enqueue_solve_setup(iht_dataset *ds, int k, int impl);
+bool grad_tc_shape_settled(const iht_dataset *ds);
 void free_fused(Workspace *ws);
 // htp.cu: covariates of the current row set, their gradient entries, and the
 // least-squares refit of HTP

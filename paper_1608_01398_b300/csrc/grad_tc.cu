@@ -749,6 +749,15 @@ int launch_grad_tc_main_with(iht_dataset *ds, const float *r32, float *g, const 
     return tc_launch(ds, map, tc_stages(ds), g, u32, v32, Mj, done);
 }
 
+// True when a pass launched now would take its settled shape (a tuned one is
+// cached, or tuning is off): a graph captured now keeps what an eager pass
+// would have used.
+bool grad_tc_shape_settled(const iht_dataset *ds)
+{
+    int prm[kTuneParams];
+    return !autotune_enabled() || (tune_lookup(ds, IHT_PASS_SINGLE, 0, prm) && grad_tc_shape_fits(ds, prm));
+}
+
 int launch_grad_tc_main(iht_dataset *ds, const float *r32, float *g, const int32_t *done)
 {
     return launch_grad_tc_main_with(ds, r32, g, ds->ws->u32, ds->ws->v32, ds->ws->Mj, done);

@@ -173,6 +173,33 @@ __global__ void k_init_objective(Scalars *sc, const double *partials, int npart)
     init_objective_body(sc, partials, npart);
 }
 
+// The start of a solve captured in a graph (one warp): the solve's scalars
+// from init, keeping the flags the set-up kernels raised (bit 0: non-finite
+// input, bit 1: bad rows), which stop the solve at once with ENUMERIC /
+// EINVAL; then the objective of beta = 0 as k_init_objective forms it.
+__global__ void k_init_solve(Scalars *sc, const Scalars *init, const double *partials, int npart)
+{
+    constexpr int kWords = (int)(sizeof(Scalars) / sizeof(unsigned long long));
+    const int lane = threadIdx.x & 31;
+    int32_t err = lane == 0 ? sc->err : 0;
+    err = __shfl_sync(0xffffffffu, err, 0);
+    for (int w = lane; w < kWords; w += 32)
+        reinterpret_cast<unsigned long long *>(sc)[w] = reinterpret_cast<const unsigned long long *>(init)[w];
+    __syncwarp();
+    if (lane == 0) {
+        sc->err = err;
+        if (err) {
+            sc->status = (err & 1) ? IHT_ENUMERIC : IHT_EINVAL;
+            sc->done = 1;
+            sc->skip1 = sc->skip2 = 1;
+        }
+    }
+    __syncwarp();
+    if (sc->done) return;
+    init_objective_body(sc, partials, npart);
+}
+
+
 
 __global__ void k_center(const double *__restrict__ src, double *__restrict__ r64,
                          const int32_t *__restrict__ used, int64_t n_pad, const Scalars *sc,
@@ -356,6 +383,31 @@ static int iteration_graph(iht_dataset *ds, int k, int K, int impl, bool prof, c
 }
 
 // y64 and the row set are in place; runs the solve, leaves S/bS and scalars.
+// A solve's first steps from beta = 0 (r = y, objective, centred residual, g^0,
+// S^0 = top-k |g^0|, beta_S = 0), enqueued on the context's stream (the fused
+// solve captures them ahead of its loop); the scalars come from ws->sc_init.
+int enqueue_solve_setup(iht_dataset *ds, int k, int impl)
+{
+    Workspace *ws = ds->ws;
+    cudaStream_t s = ds->ctx->stream;
+    const int npart = zmul_blocks(ds);
+    const int64_t P = ds->p + ds->q;
+    int rc;
+    if ((rc = zmul_run(ds, ws->cols, 0, ws->coef, -1.0, ws->u64, ws->v64, ws->used, ws->y64, ws->r64,
+                       ws->partials, nullptr)))
+        return rc;
+    k_init_solve<<<1, 32, 0, s>>>(ws->sc, ws->sc_init, ws->partials, npart);
+    k_center<<<ceil_div(ds->n_pad, 256), 256, 0, s>>>(ws->r64, ws->r64, ws->used, ds->n_pad, ws->sc,
+                                                      ws->r32);
+    note_launch(2);
+    IHT_CUDA(cudaGetLastError());
+    const int32_t *done = &ws->sc->done;
+    if ((rc = launch_grad(ds, impl, done, false))) return rc;
+    if ((rc = select_topk(ds->ctx, ws->g, P, k, ws->S, done))) return rc;
+    IHT_CUDA(cudaMemsetAsync(ws->bS, 0, sizeof(double) * k, s));
+    return IHT_OK;
+}
+
 int run_solve(iht_dataset *ds, int k, const iht_options *opt, int n_rows, const TraceDev &tr,
               const SolveInit *init)
 {
@@ -380,6 +432,21 @@ int run_solve(iht_dataset *ds, int k, const iht_options *opt, int n_rows, const 
     h.iter = init ? init->iter : 0;
     h.bt_total = init ? init->backtracks : 0;
     h.done = opt->max_iter <= h.iter ? 1 : 0;
+    const bool traced = tr.objective || tr.mu || tr.backtracks || tr.changed || tr.supp || tr.beta;
+    if (!init && !traced && !htp && !opt->profile && fused_supported(ds, k, opt->grad_impl)) {
+        // the whole solve as one graph launch and one host synchronisation;
+        // the set-up kernels' flags are read with the final scalars
+        ws->nprof = 0;
+        ws->prof_ms = 0.0;
+        rc = run_whole_fused_solve(ds, k, K, opt->grad_impl, h);
+        if (rc != IHT_EAGAIN) {
+            if (rc) return rc;
+            const int32_t err = ws->sc_host->err;
+            if (err) return (err & 1) ? IHT_ENUMERIC : IHT_EINVAL;
+            ws->graph_replays = ws->sc_host->iter;
+            return IHT_OK;
+        }
+    }
     IHT_CUDA(cudaMemcpyAsync(ws->sc_host, ws->sc, sizeof(Scalars), cudaMemcpyDeviceToHost, s));
     IHT_CUDA(cudaStreamSynchronize(s));
     h.err = ws->sc_host->err;        // row / input flags from the set-up kernels
@@ -417,7 +484,6 @@ int run_solve(iht_dataset *ds, int k, const iht_options *opt, int n_rows, const 
         IHT_CUDA(cudaMemsetAsync(ws->bS, 0, sizeof(double) * k, s));
     }
 
-    const bool traced = tr.objective || tr.mu || tr.backtracks || tr.changed || tr.supp || tr.beta;
     ws->graph_replays = 0;
     double graph_ms = 0.0;
     int graph_n = 0;

@@ -480,13 +480,16 @@ bool fused_supported(const iht_dataset *ds, int k, int impl)
 void free_fused(Workspace *ws)
 {
     if (ws->fused_exec) cudaGraphExecDestroy(ws->fused_exec);
-    void *ptrs[] = {ws->tail, ws->Sp2, ws->bSp2, ws->rc64_2, ws->partials2};
+    void *ptrs[] = {ws->tail, ws->Sp2, ws->bSp2, ws->rc64_2, ws->partials2, ws->sc_init};
     for (void *x : ptrs)
         if (x) cudaFree(x);
+    if (ws->flags_host) cudaFreeHost(ws->flags_host);
     ws->fused_exec = nullptr;
     ws->tail = nullptr;
     ws->Sp2 = nullptr;
     ws->bSp2 = ws->rc64_2 = ws->partials2 = nullptr;
+    ws->sc_init = nullptr;
+    ws->flags_host = nullptr;
 }
 
 // Blocks of the cooperative launch: one per SM when it fits (more blocks
@@ -507,29 +510,15 @@ static int tail_grid(iht_dataset *ds)
 
 // Captures the solve loop: while (condition) { fused iteration; missing-call
 // sums; gradient pass }.
-static int build_fused_graph(iht_dataset *ds, int k, int K, const TailArgs &args, int grid,
-                             cudaGraphExec_t *exec)
+// whole: the solve's set-up (enqueue_solve_setup, after clearing the kernel's
+// work area) is captured as a child graph the loop depends on.
+static int build_fused_graph(iht_dataset *ds, int k, int K, int impl, const TailArgs &args,
+                             int grid, cudaGraphExec_t *exec, bool whole)
 {
     Workspace *ws = ds->ws;
     cudaGraph_t graph = nullptr;
     IHT_CUDA(cudaGraphCreate(&graph, 0));
-    cudaGraphConditionalHandle cond;
-    cudaError_t e = cudaGraphConditionalHandleCreate(&cond, graph, 1u, cudaGraphCondAssignDefault);
-    cudaGraphNodeParams cp = {};
-    cudaGraphNode_t node;
-    if (e == cudaSuccess) {
-        cp.type = cudaGraphNodeTypeConditional;
-        cp.conditional.handle = cond;
-        cp.conditional.type = cudaGraphCondTypeWhile;
-        cp.conditional.size = 1;
-        e = cudaGraphAddNode(&node, graph, nullptr, nullptr, 0, &cp);
-    }
-    if (e != cudaSuccess) {
-        cudaGraphDestroy(graph);
-        set_cuda_error(e, "fused solve graph");
-        return IHT_ECUDA;
-    }
-    cudaGraph_t body = cp.conditional.phGraph_out[0];
+    cudaError_t e = cudaSuccess;
     if (!ws->cap_stream) {
         e = cudaStreamCreateWithFlags(&ws->cap_stream, cudaStreamNonBlocking);
         if (e != cudaSuccess) {
@@ -538,6 +527,49 @@ static int build_fused_graph(iht_dataset *ds, int k, int K, const TailArgs &args
             return IHT_ECUDA;
         }
     }
+    cudaGraphNode_t setup_node = nullptr;
+    if (whole) {
+        cudaStream_t user0 = ds->ctx->stream;
+        ds->ctx->stream = ws->cap_stream;
+        const uint64_t before0 = launches_noted();
+        cudaGraph_t setup = nullptr;
+        int rc0 = IHT_OK;
+        e = cudaStreamBeginCapture(ws->cap_stream, cudaStreamCaptureModeThreadLocal);
+        if (e == cudaSuccess) {
+            e = cudaMemsetAsync(ws->tail, 0, sizeof(TailWork), ws->cap_stream);
+            if (e == cudaSuccess) rc0 = enqueue_solve_setup(ds, k, impl);
+            const cudaError_t e2 = cudaStreamEndCapture(ws->cap_stream, &setup);
+            if (e == cudaSuccess) e = e2;
+        }
+        ds->ctx->stream = user0;
+        ws->fused_setup_launches = (int)(launches_noted() - before0);
+        note_launch(-ws->fused_setup_launches);            // captured, not run
+        if (e == cudaSuccess && rc0 == IHT_OK)
+            e = cudaGraphAddChildGraphNode(&setup_node, graph, nullptr, 0, setup);
+        if (setup) cudaGraphDestroy(setup);
+        if (e != cudaSuccess || rc0 != IHT_OK) {
+            cudaGraphDestroy(graph);
+            if (e != cudaSuccess) set_cuda_error(e, "fused solve set-up capture");
+            return rc0 != IHT_OK ? rc0 : IHT_ECUDA;
+        }
+    }
+    cudaGraphConditionalHandle cond;
+    e = cudaGraphConditionalHandleCreate(&cond, graph, 1u, cudaGraphCondAssignDefault);
+    cudaGraphNodeParams cp = {};
+    cudaGraphNode_t node;
+    if (e == cudaSuccess) {
+        cp.type = cudaGraphNodeTypeConditional;
+        cp.conditional.handle = cond;
+        cp.conditional.type = cudaGraphCondTypeWhile;
+        cp.conditional.size = 1;
+        e = cudaGraphAddNode(&node, graph, whole ? &setup_node : nullptr, nullptr, whole ? 1 : 0, &cp);
+    }
+    if (e != cudaSuccess) {
+        cudaGraphDestroy(graph);
+        set_cuda_error(e, "fused solve graph");
+        return IHT_ECUDA;
+    }
+    cudaGraph_t body = cp.conditional.phGraph_out[0];
     cudaStream_t user = ds->ctx->stream;
     ds->ctx->stream = ws->cap_stream;
     const uint64_t before = launches_noted();
@@ -596,14 +628,12 @@ static int build_fused_graph(iht_dataset *ds, int k, int K, const TailArgs &args
     return rc;
 }
 
-// After the first gradient pass and S (S^0, or a resumed support): the rest of
-// the solve as one graph launch.  Returns IHT_EAGAIN, with nothing enqueued,
-// when the graph cannot be built here (the caller then runs the per-iteration
-// graph); ETIMEOUT when a barrier of the fused kernel gave up.
-int run_fused_solve(iht_dataset *ds, int k, int K, int impl)
+// The fused graph for this solve's shape, built when its key changes: the
+// loop alone (after a first gradient pass run outside), or with the solve's
+// set-up ahead of it (whole).  EAGAIN when it cannot be built here.
+static int ensure_fused_exec(iht_dataset *ds, int k, int K, int impl, bool whole, TcParams **prm_out)
 {
     Workspace *ws = ds->ws;
-    cudaStream_t s = ds->ctx->stream;
     const int grid = tail_grid(ds);
     if (grid < 1) return IHT_EAGAIN;
     if (!ws->tail) {
@@ -654,27 +684,79 @@ int run_fused_solve(iht_dataset *ds, int k, int K, int impl)
     a.bimg = bimg;
     a.prm = prm;
     a.nlim = nlim;
-    const uint64_t key[10] = {(uint64_t)k | ((uint64_t)ds->q << 32),
-                              (uint64_t)K, (uint64_t)impl,
+    *prm_out = prm;
+    const uint64_t key[12] = {(uint64_t)k | ((uint64_t)ds->q << 32),
+                              (uint64_t)K, (uint64_t)impl | ((uint64_t)whole << 8),
                               (uint64_t)(uintptr_t)ws->tail, (uint64_t)(uintptr_t)bimg,
                               grad_tc_scratch_id(), (uint64_t)(uintptr_t)ws->S,
                               (uint64_t)(uintptr_t)ws->used, (uint64_t)grid,
-                              (uint64_t)(uintptr_t)ds->G};
-    if (!ws->fused_exec || !std::equal(key, key + 10, ws->fused_key)) {
+                              (uint64_t)(uintptr_t)ds->G, (uint64_t)(uintptr_t)ds->ctx->sel.st,
+                              (uint64_t)(uintptr_t)ws->zc};
+    if (!ws->fused_exec || !std::equal(key, key + 12, ws->fused_key)) {
         if (ws->fused_exec) cudaGraphExecDestroy(ws->fused_exec);
         ws->fused_exec = nullptr;
-        if (build_fused_graph(ds, k, K, a, grid, &ws->fused_exec) != IHT_OK) {
+        if (build_fused_graph(ds, k, K, impl, a, grid, &ws->fused_exec, whole) != IHT_OK) {
             cudaGetLastError();                        // the per-iteration graph runs instead
             return IHT_EAGAIN;
         }
-        std::copy(key, key + 10, ws->fused_key);
+        std::copy(key, key + 12, ws->fused_key);
     }
+    return IHT_OK;
+}
+
+// After the first gradient pass and S (a resumed support): the rest of the
+// solve as one graph launch.  Returns IHT_EAGAIN, with nothing enqueued, when
+// the graph cannot be built here (the caller then runs the per-iteration
+// graph); ETIMEOUT when a barrier of the fused kernel gave up.
+int run_fused_solve(iht_dataset *ds, int k, int K, int impl)
+{
+    Workspace *ws = ds->ws;
+    cudaStream_t s = ds->ctx->stream;
+    TcParams *prm = nullptr;
+    int rc = ensure_fused_exec(ds, k, K, impl, false, &prm);
+    if (rc) return rc;
     IHT_CUDA(cudaMemsetAsync(ws->tail, 0, sizeof(TailWork), s));   // barrier, histogram, state
     IHT_CUDA(cudaGraphLaunch(ws->fused_exec, s));
     int err = 0;
     IHT_CUDA(cudaMemcpyAsync(&err, &ws->tail->bar_err, sizeof(int), cudaMemcpyDeviceToHost, s));
     IHT_CUDA(cudaStreamSynchronize(s));
     return err ? IHT_ETIMEOUT : IHT_OK;
+}
+
+// A solve from beta = 0 as one graph launch: the starting scalars go to
+// ws->sc_init (the graph's first kernel merges them with the set-up kernels'
+// flags); the final scalars and both error words come back with one host
+// synchronisation.
+int run_whole_fused_solve(iht_dataset *ds, int k, int K, int impl, const Scalars &h)
+{
+    Workspace *ws = ds->ws;
+    cudaStream_t s = ds->ctx->stream;
+    if (!ws->sc_init) IHT_CUDA(dev_malloc(&ws->sc_init, sizeof(Scalars)));
+    if (!ws->flags_host) {
+        const cudaError_t e = cudaMallocHost((void **)&ws->flags_host, 2 * sizeof(int32_t));
+        if (e != cudaSuccess) {
+            set_cuda_error(e, "pinned error words");
+            return e == cudaErrorMemoryAllocation ? IHT_ENOMEM : IHT_ECUDA;
+        }
+    }
+    // (the first solve of a panel tunes its pass outside a graph)
+    if (!grad_tc_shape_settled(ds)) return IHT_EAGAIN;
+    TcParams *prm = nullptr;
+    int rc = ensure_fused_exec(ds, k, K, impl, true, &prm);
+    if (rc) return rc;
+    *ws->sc_host = h;
+    IHT_CUDA(cudaMemcpyAsync(ws->sc_init, ws->sc_host, sizeof(Scalars), cudaMemcpyHostToDevice, s));
+    if ((rc = grad_tc_reset_status(ds))) return rc;
+    IHT_CUDA(cudaGraphLaunch(ws->fused_exec, s));
+    if (fault_take(IHT_FAULT_TIMEOUT))                 // (host-injected: a pass that gave up)
+        IHT_CUDA(cudaMemsetAsync(&prm->err, 0x01, sizeof(int), s));
+    IHT_CUDA(cudaMemcpyAsync(ws->sc_host, ws->sc, sizeof(Scalars), cudaMemcpyDeviceToHost, s));
+    IHT_CUDA(cudaMemcpyAsync(&ws->flags_host[0], &ws->tail->bar_err, sizeof(int32_t),
+                             cudaMemcpyDeviceToHost, s));
+    IHT_CUDA(cudaMemcpyAsync(&ws->flags_host[1], &prm->err, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    IHT_CUDA(cudaStreamSynchronize(s));
+    note_launch(ws->fused_setup_launches + ws->fused_launches * std::max(ws->sc_host->iter, 1));
+    return (ws->flags_host[0] || ws->flags_host[1]) ? IHT_ETIMEOUT : IHT_OK;
 }
 
 }  // namespace iht
