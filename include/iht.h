@@ -61,8 +61,15 @@ typedef struct iht_options {
     int32_t grad_impl;     /* gradient kernel: 0 default, 1 CUDA-core, 2 tensor-core  */
     int32_t profile;       /* 1: time every gradient launch with CUDA events [0]     */
     int32_t variant;       /* IHT_VARIANT_IHT [default] or IHT_VARIANT_HTP (below)   */
-    int32_t reserved;
+    int32_t flags;         /* IHT_FIT_* bits (below) [0]                              */
 } iht_options;
+
+/* iht_options.flags.
+ *   IHT_FIT_BETA_ZEROED: a host beta_out holds zeros on entry, so iht_fit writes
+ *     only its support entries (without it, iht_fit first writes zeros to all
+ *     p + q entries: the bytes of a freshly allocated buffer are then all
+ *     touched once).  Ignored for device outputs.  Other bits: EINVAL. */
+enum { IHT_FIT_BETA_ZEROED = 1 };
 
 /* Solver variants (iht_options.variant).
  *   IHT: the projected gradient step of Eq. ihta.

@@ -23,6 +23,7 @@ IHT_HOST, IHT_DEVICE = 0, 1
 IHT_PASS_SINGLE, IHT_PASS_MULTI = 0, 1
 IHT_FAULT_NONE, IHT_FAULT_ALLOC, IHT_FAULT_TIMEOUT = 0, 1, 2
 IHT_VARIANT_IHT, IHT_VARIANT_HTP = 0, 1
+IHT_FIT_BETA_ZEROED = 1
 VARIANTS = {"iht": IHT_VARIANT_IHT, "htp": IHT_VARIANT_HTP}
 
 EXPORTED = ["iht_default_options", "iht_strerror", "iht_last_cuda_error", "iht_kernel_launches",
@@ -50,7 +51,7 @@ class iht_options(ctypes.Structure):
                 ("tol", ctypes.c_double), ("c", ctypes.c_double), ("kappa", ctypes.c_double),
                 ("in_mem", ctypes.c_int32), ("out_mem", ctypes.c_int32),
                 ("grad_impl", ctypes.c_int32), ("profile", ctypes.c_int32),
-                ("variant", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("variant", ctypes.c_int32), ("flags", ctypes.c_int32)]
 
 
 class iht_result(ctypes.Structure):
@@ -391,7 +392,8 @@ def _fit(ds: Dataset, y, k: int, rows, opts: iht_options, trace: bool, state: by
         supp = torch.empty(k, dtype=torch.int32, device=f"cuda:{ds.ctx.device}")
         bp, sp = beta.data_ptr(), supp.data_ptr()
     else:
-        beta = np.empty(P)
+        beta = np.zeros(P)                # zero pages: the library writes the support only
+        opts.flags |= IHT_FIT_BETA_ZEROED
         supp = np.empty(k, dtype=np.int32)
         bp, sp = beta.ctypes.data, supp.ctypes.data
     res = iht_result()

@@ -207,7 +207,7 @@ void iht_default_options(iht_options *o)
     o->grad_impl = 0;
     o->profile = 0;
     o->variant = IHT_VARIANT_IHT;
-    o->reserved = 0;
+    o->flags = 0;
 }
 
 const char *iht_strerror(int s)
@@ -493,7 +493,8 @@ static int fit_impl(iht_dataset *ds, const int32_t *rows, int64_t n_rows, const 
         (opt.out_mem != IHT_HOST && opt.out_mem != IHT_DEVICE) || opt.max_iter < 0 ||
         opt.max_backtrack < 0 || !(opt.kappa > 1.0) || !(opt.c >= 0.0 && opt.c < 1.0) ||
         !(opt.tol >= 0.0) || opt.grad_impl < 0 || opt.grad_impl > 2 ||
-        (opt.variant != IHT_VARIANT_IHT && opt.variant != IHT_VARIANT_HTP))
+        (opt.variant != IHT_VARIANT_IHT && opt.variant != IHT_VARIANT_HTP) ||
+        (opt.flags & ~IHT_FIT_BETA_ZEROED))
         return IHT_EINVAL;
     if (init && (ds->q > 0 || opt.variant != IHT_VARIANT_IHT)) return IHT_EINVAL;
     DeviceGuard g(ds->ctx->device);
@@ -532,7 +533,7 @@ static int fit_impl(iht_dataset *ds, const int32_t *rows, int64_t n_rows, const 
             set_cuda_error(e, "iht_fit outputs");
             return IHT_ECUDA;
         }
-        memset(beta_out, 0, sizeof(double) * P);
+        if (!(opt.flags & IHT_FIT_BETA_ZEROED)) memset(beta_out, 0, sizeof(double) * P);
         for (int c = 0; c < k; ++c) beta_out[support_out[c]] = bS[c];
         free(bS);
     }

@@ -30,6 +30,7 @@ def test_host_only_entry_points():
     o = iht.iht_default_options()
     assert (o.max_iter, o.max_backtrack, o.tol, o.c, o.kappa) == (100, 50, 1e-4, 0.01, 2.0)
     assert o.variant == iht.IHT_VARIANT_IHT
+    assert o.flags == 0
     assert ctypes.sizeof(iht.iht_options) == 56 and ctypes.sizeof(iht.iht_result) == 48
     assert lib.iht_kernel_launches() == 0
 

@@ -6,6 +6,8 @@ beta max|db| / max|b| <= 1e-4; supports compared where the oracle certifies that
 the k-th and (k+1)-th |w| are further apart than the FP32 gradient error can
 move them and no backtracking decision sits within 1e-3 of its threshold.
 """
+import ctypes
+
 import numpy as np
 import pytest
 
@@ -244,6 +246,21 @@ def test_fit_status_and_io_paths(iht, ctx):
     assert np.array_equal(a.support, b.support.cpu().numpy())
     c = iht.iht_fit(ds, y, 7)
     assert np.array_equal(a.beta, c.beta) and a.iterations == c.iterations   # run to run
+    # the zeroed-output flag: the binding passes calloc'ed zeros and sets it;
+    # without it the library zero-fills a dirty buffer itself; other bits: EINVAL
+    o = iht.iht_default_options()
+    beta = np.full(ds.p, 7.0)
+    supp = np.empty(7, np.int32)
+    res = iht.iht_result()
+    yy = np.ascontiguousarray(y, dtype=np.float64)
+    rc = iht._lib().iht_fit(ds.h, None, ds.n, ctypes.c_void_p(yy.ctypes.data), 7, ctypes.byref(o),
+                            ctypes.c_void_p(beta.ctypes.data), ctypes.c_void_p(supp.ctypes.data),
+                            ctypes.byref(res))
+    assert rc == a.status and np.array_equal(beta, a.beta) and np.array_equal(supp, a.support)
+    o.flags = 2
+    assert iht._lib().iht_fit(ds.h, None, ds.n, ctypes.c_void_p(yy.ctypes.data), 7, ctypes.byref(o),
+                              ctypes.c_void_p(beta.ctypes.data), ctypes.c_void_p(supp.ctypes.data),
+                              ctypes.byref(res)) == iht.IHT_EINVAL
 
 
 @pytest.fixture(scope="module")
