@@ -1,21 +1,25 @@
 // One IHT iteration after its gradient pass as a single cooperative kernel,
-// and the rest of a solve as one CUDA graph launch.
+// and a whole solve as one CUDA graph launch.
 //
 // Between two gradient passes an iteration (Sec. 2.2-2.3.1) is a chain of small
 // dependent steps: the top-2k candidates of |g|, g_S and Z_S g_S for the step
 // size, the projection, the residual of the candidate, the backtracking test
-// (repeated while it rejects), the centred residual and its limb image for the
-// next tensor-core pass.  As separate launches each step costs a launch and a
-// drain of the GPU; here they are the phases of one kernel whose blocks meet at
-// grid barriers (a cooperative launch, so every block is resident; every wait
-// is bounded and a barrier that gives up stops the solve with an error word the
-// host reads).  Each phase runs the same device code as the separate kernels
-// (bodies.cuh, select_bodies.cuh, limbs.cuh), so a solve gives the same bits on
+// (repeated while it rejects) and the centred residual.  As separate launches
+// each step costs a launch and a drain of the GPU; here they are the phases of
+// one kernel whose blocks meet at grid barriers (a cooperative launch, so every
+// block is resident; every wait is bounded and a barrier that gives up stops
+// the solve with an error word the host reads).  Where every block can form
+// the same result from the same inputs (the candidates, the projection, the
+// decisions), the blocks that need it do so, instead of one block doing it
+// between two barriers.  Each phase runs the same device code as the separate
+// kernels (bodies.cuh, select_bodies.cuh), so a solve gives the same bits on
 // either path and in a batch.
 //
-// The solve graph is a conditional while node whose body is this kernel, the
-// missing-call sums and the gradient pass; the kernel clears the condition once
-// the solve has stopped, so the host synchronises once per solve.
+// The solve graph holds the solve's set-up (first gradient pass, S^0) and a
+// conditional while node whose body is this kernel, the missing-call sums
+// (which also write the next pass's limb image) and the gradient pass; the
+// kernel clears the condition once the solve has stopped, so the host
+// synchronises once per solve.
 #include "bodies.cuh"
 #include "limbs.cuh"
 #include "select_bodies.cuh"
@@ -25,7 +29,7 @@ namespace iht {
 constexpr int kTailThreads = kZmulThreads;    // one 128-sample block of the sparse product per pass
 constexpr int kTailKM = 256;                  // largest k of the fused path
 constexpr int kTailKept = 1024;               // candidates the selection's narrow finish sorts
-constexpr uint32_t kBarSpin = 1u << 22;       // bounded barrier waits (polls; sleeps up to 512 ns each)
+constexpr uint32_t kBarSpin = 1u << 22;       // bounded barrier waits (polls; sleeps up to 256 ns each)
 
 struct TailWork {                     // zeroed before every solve
     unsigned long long bar_count;     // grid barrier: arrivals since the solve began (+ kBarAbort)
@@ -54,7 +58,7 @@ struct TailArgs {
     int npart;                           // 128-sample blocks of the sparse product
     int k, K;
     TailWork *T;
-    uint8_t *bimg;                       // limb image of the next tensor-core pass
+    uint8_t *bimg;                       // limb image of the next pass (the missing-call sums write it)
     TcParams *prm;
     int64_t nlim;                        // samples the limb image covers
     cudaGraphConditionalHandle cond;
