@@ -306,10 +306,14 @@ int launch_grad_simt(iht_dataset *ds, const float *r32, float *g, const int32_t 
 int launch_grad_tc(iht_dataset *ds, const float *r32, float *g, const int32_t *done);
 bool grad_tc_supported(const iht_dataset *ds);
 int prepare_grad_tc(iht_dataset *ds, const float *r32, const int32_t *done);
-int launch_grad_tc_main(iht_dataset *ds, const float *r32, float *g, const int32_t *done);
+// hist (optional): the selection's 2048-bin histogram of |g| bits 30..20 the
+// pass adds its keys to (hflag bit 0: a non-finite g)
+int launch_grad_tc_main(iht_dataset *ds, const float *r32, float *g, const int32_t *done,
+                        uint32_t *hist = nullptr, uint32_t *hflag = nullptr);
 int prepare_grad_tc_to(iht_dataset *ds, const float *r32, float *Mj, const int32_t *done);
 int launch_grad_tc_main_with(iht_dataset *ds, const float *r32, float *g, const float *u32,
-                             const float *v32, const float *Mj, const int32_t *done);
+                             const float *v32, const float *Mj, const int32_t *done,
+                             uint32_t *hist = nullptr, uint32_t *hflag = nullptr);
 void grad_tc_release_thread();
 uint64_t grad_tc_scratch_id();
 int grad_tc_status(iht_dataset *ds, int *timed_out);
@@ -421,13 +425,16 @@ int run_fused_solve(iht_dataset *ds, int k, int K, int impl);
 // h is the solve's starting scalars; on return ws->sc_host holds the final
 // ones.  EAGAIN (nothing enqueued) when the graph cannot be built.
 int run_whole_fused_solve(iht_dataset *ds, int k, int K, int impl, const Scalars &h);
-int enqueue_solve_setup(iht_dataset *ds, int k, int impl);
+// (hist, hflag: the gradient pass's keys go to this histogram, as in launch_grad_tc_main)
+int enqueue_solve_setup(iht_dataset *ds, int k, int impl, uint32_t *hist = nullptr,
+                        uint32_t *hflag = nullptr);
 bool grad_tc_shape_settled(const iht_dataset *ds);
 void free_fused(Workspace *ws);
 // htp.cu: covariates of the current row set, their gradient entries, and the
 // least-squares refit of HTP
 int cov_setup(iht_dataset *ds, int64_t n_rows);
-int launch_cov_grad(iht_dataset *ds, const float *r32, float *g, const int32_t *done);
+int launch_cov_grad(iht_dataset *ds, const float *r32, float *g, const int32_t *done,
+                    uint32_t *hist = nullptr, uint32_t *hflag = nullptr);
 int htp_refit(iht_dataset *ds, int k, const int32_t *Sp, double *bSp, const int32_t *done);
 int ensure_htp_scratch(iht_dataset *ds, int k);
 // batched tails (blockIdx selects the solve; finished solves return at once)

@@ -66,6 +66,7 @@ constexpr int kTcThreads = kTcNWG * (128 + 32 + 32);   // decoders, MMA warps, T
 constexpr int kTcStageTile = 128 * kTcStageBytes;  // 8 KB
 
 constexpr uint32_t kTcSpin = 1u << 24;             // bounded waits (each poll may suspend up to 128 ns)
+constexpr int kTcHistBins = 2048;                  // bits 30..20 of |g| (the selection's histogram)
 
 
 __device__ __forceinline__ uint32_t smem_addr(const void *p)
@@ -278,7 +279,7 @@ __device__ __forceinline__ bool tc_epilogue(TcPipe &P, uint32_t tb, uint32_t lan
                                             const float *__restrict__ Mj,
                                             const float *__restrict__ u32,
                                             const float *__restrict__ v32, float *__restrict__ g,
-                                            volatile int &abort_flag)
+                                            volatile int &abort_flag, uint32_t *s_hist, bool &nan)
 {
     bool ok = true;
     if (!mbar_wait(&P.accfull, (uint32_t)t & 1u)) {
@@ -299,7 +300,13 @@ __device__ __forceinline__ bool tc_epilogue(TcPipe &P, uint32_t tb, uint32_t lan
             s *= 0.0625f;
         }
         const float D = 16384.0f * Ssum;
-        g[row] = standardise_d(D, R, Mj[row], u32[row], v32[row]);
+        const float gv = standardise_d(D, R, Mj[row], u32[row], v32[row]);
+        g[row] = gv;
+        if (s_hist) {
+            const uint32_t key = __float_as_uint(gv) & 0x7fffffffu;
+            nan |= key > 0x7f800000u;
+            atomicAdd(&s_hist[key >> 20], 1u);
+        }
     }
     return ok;
 }
@@ -315,10 +322,12 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_grad_tc(const __grid_constant
                                                            const float *__restrict__ u32,
                                                            const float *__restrict__ v32,
                                                            float *__restrict__ g, TcParams *prm,
-                                                           const int32_t *__restrict__ done)
+                                                           const int32_t *__restrict__ done,
+                                                           uint32_t *hist, uint32_t *hflag)
 {
     extern __shared__ __align__(1024) uint8_t smem[];
     __shared__ __align__(8) TcPipe pipe[kTcNWG];
+    __shared__ uint32_t s_hist[kTcHistBins];     // with hist: this CTA's counts of |g| bits 30..20
     __shared__ uint32_t tmem_base;
     __shared__ volatile int abort_flag;
     constexpr int kDecoders = kTcNWG * 128;
@@ -351,6 +360,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_grad_tc(const __grid_constant
         abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
+    if (hist)
+        for (int b = tid; b < kTcHistBins; b += blockDim.x) s_hist[b] = 0;
     if (warp == kProducerWarp) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                          smem_addr(&tmem_base)),
@@ -378,6 +389,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_grad_tc(const __grid_constant
         uint32_t buf = 0, bphase = 0;           // A-buffer ring
         int T = 0;
         bool ok = true;
+        bool nan = false;                       // a non-finite g among this thread's rows
         const int cps = kTcStageBytes / kTcGroupBytes;                 // chunks per stage (4)
         // swizzled offsets of the stage's four 16-byte chunks in this thread's row
         const int swz = (r >> 1) & 3;
@@ -421,8 +433,11 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_grad_tc(const __grid_constant
                 }
                 if (abort_flag) ok = false;
             }
-            if (ok) ok &= tc_epilogue(P, tb, lane_off, T, row, p, s0, R, Mj, u32, v32, g, abort_flag);
+            if (ok)
+                ok &= tc_epilogue(P, tb, lane_off, T, row, p, s0, R, Mj, u32, v32, g, abort_flag,
+                                  hist ? s_hist : nullptr, nan);
         }
+        if (nan && hflag) atomicOr(hflag, 1u);
     } else if (warp < kProducerWarp) {
         // ------------------------------------------------------------ MMA issuers
         const int w = warp - kTcNWG * 4;
@@ -522,6 +537,9 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_grad_tc(const __grid_constant
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
+    if (hist)                                    // this CTA's counts into the selection's histogram
+        for (int b = tid; b < kTcHistBins; b += blockDim.x)
+            if (s_hist[b]) atomicAdd(&hist[b], s_hist[b]);
     if (warp == kProducerWarp)
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base),
                      "r"(kTcNWG * 128));
@@ -546,7 +564,7 @@ static int tc_ngroups(const iht_dataset *ds)
 
 static size_t tc_bbytes(const iht_dataset *ds) { return 512 + 256 * (size_t)(2 * tc_ngroups(ds)); }
 
-constexpr size_t kTcSmemMax = 220 * 1024;
+constexpr size_t kTcSmemMax = 212 * 1024;   // dynamic; the static part (histogram, pipes) fits beside it
 
 // TMA stages per warpgroup that fit beside B and r (0: the pass does not fit).
 static int tc_stages(const iht_dataset *ds)
@@ -676,14 +694,15 @@ bool grad_tc_shape_fits(const iht_dataset *ds, const int *params)
 }
 
 static int tc_launch(iht_dataset *ds, const CUtensorMap &map, int nst, float *g, const float *u32,
-                     const float *v32, const float *Mj, const int32_t *done)
+                     const float *v32, const float *Mj, const int32_t *done, uint32_t *hist = nullptr,
+                     uint32_t *hflag = nullptr)
 {
     const int64_t tiles = (ds->p + 127) / 128;
     const int grid = (int)std::min<int64_t>((tiles + kTcNWG - 1) / kTcNWG, (int64_t)ds->ctx->num_sms);
     const size_t smem = (size_t)kTcNWG * nst * kTcStageTile + tc_bbytes(ds);
     k_grad_tc<<<grid, kTcThreads, smem, ds->ctx->stream>>>(map, ds->p, tc_ngroups(ds), nst, g_tc.bimg,
                                                            (int)tc_bbytes(ds), Mj, u32, v32, g, g_tc.prm,
-                                                           done);
+                                                           done, hist, hflag);
     note_launch();
     IHT_CUDA(cudaGetLastError());
     return IHT_OK;
@@ -730,7 +749,8 @@ static int tc_tune(iht_dataset *ds, const CUtensorMap &map, float *g, const floa
 // cached tuned one (tuned on this call when none is cached, tuning is on and
 // the stream is not being captured), else the most that fit.
 int launch_grad_tc_main_with(iht_dataset *ds, const float *r32, float *g, const float *u32,
-                             const float *v32, const float *Mj, const int32_t *done)
+                             const float *v32, const float *Mj, const int32_t *done, uint32_t *hist,
+                             uint32_t *hflag)
 {
     cudaStream_t s = ds->ctx->stream;
     CUtensorMap map;
@@ -739,14 +759,14 @@ int launch_grad_tc_main_with(iht_dataset *ds, const float *r32, float *g, const 
     static thread_local int cfg = -1;
     if (cfg != ds->ctx->device) {
         IHT_CUDA(cudaFuncSetAttribute(k_grad_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      220 * 1024));
+                                      (int)kTcSmemMax));
         cfg = ds->ctx->device;
     }
     int prm[kTuneParams];
     if (tune_lookup(ds, IHT_PASS_SINGLE, 0, prm) && grad_tc_shape_fits(ds, prm))
-        return tc_launch(ds, map, prm[0], g, u32, v32, Mj, done);
-    if (autotune_enabled() && !stream_capturing(s)) return tc_tune(ds, map, g, u32, v32, Mj, done);
-    return tc_launch(ds, map, tc_stages(ds), g, u32, v32, Mj, done);
+        return tc_launch(ds, map, prm[0], g, u32, v32, Mj, done, hist, hflag);
+    if (!hist && autotune_enabled() && !stream_capturing(s)) return tc_tune(ds, map, g, u32, v32, Mj, done);
+    return tc_launch(ds, map, tc_stages(ds), g, u32, v32, Mj, done, hist, hflag);
 }
 
 // True when a pass launched now would take its settled shape (a tuned one is
@@ -758,9 +778,10 @@ bool grad_tc_shape_settled(const iht_dataset *ds)
     return !autotune_enabled() || (tune_lookup(ds, IHT_PASS_SINGLE, 0, prm) && grad_tc_shape_fits(ds, prm));
 }
 
-int launch_grad_tc_main(iht_dataset *ds, const float *r32, float *g, const int32_t *done)
+int launch_grad_tc_main(iht_dataset *ds, const float *r32, float *g, const int32_t *done,
+                        uint32_t *hist, uint32_t *hflag)
 {
-    return launch_grad_tc_main_with(ds, r32, g, ds->ws->u32, ds->ws->v32, ds->ws->Mj, done);
+    return launch_grad_tc_main_with(ds, r32, g, ds->ws->u32, ds->ws->v32, ds->ws->Mj, done, hist, hflag);
 }
 
 // Identifies the calling thread's pass scratch (changes when it is reallocated).

@@ -61,9 +61,11 @@ __global__ void __launch_bounds__(256) k_cov_setup(const double *__restrict__ co
 }
 
 // g[p + t] = sum_i zc_t,i r_i (FP64 sum, one block per covariate).
+// (hist: also its key into the selection's histogram, as the SNPs' pass does)
 __global__ void __launch_bounds__(256) k_cov_grad(const double *__restrict__ zc, int64_t n_pad,
                                                   const float *__restrict__ r32, float *__restrict__ g,
-                                                  int64_t p, const int32_t *__restrict__ done)
+                                                  int64_t p, const int32_t *__restrict__ done,
+                                                  uint32_t *hist, uint32_t *hflag)
 {
     __shared__ double red[8];
     if (done && *done) return;
@@ -72,7 +74,15 @@ __global__ void __launch_bounds__(256) k_cov_grad(const double *__restrict__ zc,
     for (int64_t i = threadIdx.x; i < n_pad; i += blockDim.x)
         s += zc[(int64_t)t * n_pad + i] * (double)r32[i];
     s = block_sum(s, red);
-    if (threadIdx.x == 0) g[p + t] = (float)s;
+    if (threadIdx.x == 0) {
+        const float gv = (float)s;
+        g[p + t] = gv;
+        if (hist) {
+            const uint32_t key = __float_as_uint(gv) & 0x7fffffffu;
+            if (key > 0x7f800000u) atomicOr(hflag, 1u);
+            atomicAdd(&hist[key >> 20], 1u);
+        }
+    }
 }
 
 int cov_setup(iht_dataset *ds, int64_t n_rows)
@@ -91,10 +101,12 @@ int cov_setup(iht_dataset *ds, int64_t n_rows)
     return IHT_OK;
 }
 
-int launch_cov_grad(iht_dataset *ds, const float *r32, float *g, const int32_t *done)
+int launch_cov_grad(iht_dataset *ds, const float *r32, float *g, const int32_t *done, uint32_t *hist,
+                    uint32_t *hflag)
 {
     if (ds->q <= 0) return IHT_OK;
-    k_cov_grad<<<(int)ds->q, 256, 0, ds->ctx->stream>>>(ds->ws->zc, ds->n_pad, r32, g, ds->p, done);
+    k_cov_grad<<<(int)ds->q, 256, 0, ds->ctx->stream>>>(ds->ws->zc, ds->n_pad, r32, g, ds->p, done,
+                                                       hist, hflag);
     note_launch();
     IHT_CUDA(cudaGetLastError());
     return IHT_OK;

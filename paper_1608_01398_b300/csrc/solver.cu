@@ -256,7 +256,8 @@ int launch_merge(iht_dataset *ds, int K, int first, const int32_t *skip = nullpt
 }
 
 // The gradient pass; e0/e1 (optional) are recorded around its main kernel.
-static int launch_grad_ev(iht_dataset *ds, int impl, const int32_t *done, cudaEvent_t e0, cudaEvent_t e1)
+static int launch_grad_ev(iht_dataset *ds, int impl, const int32_t *done, cudaEvent_t e0, cudaEvent_t e1,
+                          uint32_t *hist = nullptr, uint32_t *hflag = nullptr)
 {
     Workspace *ws = ds->ws;
     cudaStream_t s = ds->ctx->stream;
@@ -268,18 +269,21 @@ static int launch_grad_ev(iht_dataset *ds, int impl, const int32_t *done, cudaEv
     if (e0 || e1) IHT_CUDA(cudaStreamIsCapturing(s, &cap));
     const unsigned flags = cap == cudaStreamCaptureStatusActive ? cudaEventRecordExternal : cudaEventRecordDefault;
     if (e0) IHT_CUDA(cudaEventRecordWithFlags(e0, s, flags));
-    rc = tc ? launch_grad_tc_main(ds, ws->r32, ws->g, done) : launch_grad_simt(ds, ws->r32, ws->g, done);
+    if (hist && !tc) return IHT_EINVAL;                      // (only the tensor-core pass counts keys)
+    rc = tc ? launch_grad_tc_main(ds, ws->r32, ws->g, done, hist, hflag)
+            : launch_grad_simt(ds, ws->r32, ws->g, done);
     if (rc) return rc;
     if (e1) IHT_CUDA(cudaEventRecordWithFlags(e1, s, flags));
-    return launch_cov_grad(ds, ws->r32, ws->g, done);       // covariate entries p .. p+q-1
+    return launch_cov_grad(ds, ws->r32, ws->g, done, hist, hflag);   // covariate entries p .. p+q-1
 }
 
-int launch_grad(iht_dataset *ds, int impl, const int32_t *done, bool profile)
+int launch_grad(iht_dataset *ds, int impl, const int32_t *done, bool profile, uint32_t *hist = nullptr,
+                uint32_t *hflag = nullptr)
 {
     Workspace *ws = ds->ws;
     const bool rec = profile && ws->nprof < kProfEvents;
     const int rc = launch_grad_ev(ds, impl, done, rec ? ws->prof_ev[2 * ws->nprof] : nullptr,
-                                  rec ? ws->prof_ev[2 * ws->nprof + 1] : nullptr);
+                                  rec ? ws->prof_ev[2 * ws->nprof + 1] : nullptr, hist, hflag);
     if (rc) return rc;
     if (rec) ++ws->nprof;
     return IHT_OK;
@@ -386,7 +390,7 @@ static int iteration_graph(iht_dataset *ds, int k, int K, int impl, bool prof, c
 // A solve's first steps from beta = 0 (r = y, objective, centred residual, g^0,
 // S^0 = top-k |g^0|, beta_S = 0), enqueued on the context's stream (the fused
 // solve captures them ahead of its loop); the scalars come from ws->sc_init.
-int enqueue_solve_setup(iht_dataset *ds, int k, int impl)
+int enqueue_solve_setup(iht_dataset *ds, int k, int impl, uint32_t *hist, uint32_t *hflag)
 {
     Workspace *ws = ds->ws;
     cudaStream_t s = ds->ctx->stream;
@@ -402,7 +406,7 @@ int enqueue_solve_setup(iht_dataset *ds, int k, int impl)
     note_launch(2);
     IHT_CUDA(cudaGetLastError());
     const int32_t *done = &ws->sc->done;
-    if ((rc = launch_grad(ds, impl, done, false))) return rc;
+    if ((rc = launch_grad(ds, impl, done, false, hist, hflag))) return rc;
     if ((rc = select_topk(ds->ctx, ws->g, P, k, ws->S, done))) return rc;
     IHT_CUDA(cudaMemsetAsync(ws->bS, 0, sizeof(double) * k, s));
     return IHT_OK;

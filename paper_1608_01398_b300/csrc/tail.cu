@@ -35,6 +35,7 @@ struct TailWork {                     // zeroed before every solve
     unsigned long long bar_count;     // grid barrier: arrivals since the solve began (+ kBarAbort)
     int bar_err, pad_;                // 1: a barrier wait gave up
     unsigned int den_ticket;          // blocks done with Z_S g_S in this launch
+    double num;                       // ||g_S||^2, from the blocks that form Z_S g_S
     Scalars spec;                     // the second candidate's projection scalars (mu / kappa)
     SelState st;                      // selection state (boundary bin, candidate count)
     uint32_t hist[kSelBins];          // histogram of |g| bits 30..20
@@ -61,6 +62,8 @@ struct TailArgs {
     uint8_t *bimg;                       // limb image of the next pass (the missing-call sums write it)
     TcParams *prm;
     int64_t nlim;                        // samples the limb image covers
+    int own_hist;                        // 1: phase A forms the histogram of |g| (else the
+                                         //   gradient pass before this kernel counted its keys)
     cudaGraphConditionalHandle cond;
 };
 
@@ -157,11 +160,9 @@ __global__ void __launch_bounds__(kTailThreads) k_tail(const __grid_constant__ T
         return;
     }
 
-    // A: g_S and ||g_S||^2 for the step size (block 0, first warp); histogram of
-    // |g| over the other blocks (all of them on a one-block grid)
-    if (b0) gather_gS_body(A.g, A.S, A.k, A.coef, &ssc);
-    const int hb = gridDim.x > 1 ? (int)blockIdx.x - 1 : 0, hnb = gridDim.x > 1 ? (int)gridDim.x - 1 : 1;
-    if (hb >= 0) {
+    // A (when the gradient pass before this kernel did not count its keys): the
+    // histogram of |g| over every block
+    if (A.own_hist) {
         uint32_t *hs = reinterpret_cast<uint32_t *>(smem_raw);
 #pragma unroll 1
         for (int b = tid; b < kSelBins; b += blockDim.x) hs[b] = 0;
@@ -171,14 +172,26 @@ __global__ void __launch_bounds__(kTailThreads) k_tail(const __grid_constant__ T
             const uint32_t key = sel_key(x);
             nan |= key > 0x7f800000u;
             atomicAdd(&hs[key >> 20], 1u);
-        }, hb, hnb);
+        });
         if (nan) atomicOr(&T->st.err, 1u);
         __syncthreads();
 #pragma unroll 1
         for (int b = tid; b < kSelBins; b += blockDim.x)
             if (hs[b]) atomicAdd(&T->hist[b], hs[b]);
+        if (!grid_sync_put(T, sc, &ssc, b0)) return tail_stop(A);
     }
-    if (!grid_sync_put(T, sc, &ssc, b0)) return tail_stop(A);
+
+    // g_S (in shared memory) for the blocks that form Z_S g_S; the one that
+    // forms sample block 0 publishes ||g_S||^2 in T->num before it is counted
+    __shared__ double s_coef[kTailKM];
+    __shared__ Scalars s_g;               // (only its num is used)
+    auto zsgs = [&](int vb) {
+        gather_gS_body(A.g, A.S, A.k, s_coef, &s_g);
+        __syncthreads();
+        if (vb == 0 && tid == 0) T->num = s_g.num;
+        zmul_body(A.G, A.stride, A.rowb, A.S, A.k, s_coef, 1.0, A.u64, A.v64, A.used, nullptr, nullptr,
+                  A.zv, A.partials, A.n_pad, A.p, A.zc, vb);
+    };
 
     // Z_S g_S for the step size: formed in C by the blocks no candidate needs
     // (nden of them, each then counted in den_ticket), while the others select
@@ -212,9 +225,7 @@ __global__ void __launch_bounds__(kTailThreads) k_tail(const __grid_constant__ T
         }
         if (nden == 0) {
 #pragma unroll 1
-            for (int vb = (int)gridDim.x - 1 - (int)blockIdx.x; vb < A.npart; vb += gridDim.x)
-                zmul_body(A.G, A.stride, A.rowb, A.S, A.k, A.coef, 1.0, A.u64, A.v64, A.used, nullptr,
-                          nullptr, A.zv, A.partials, A.n_pad, A.p, A.zc, vb);
+            for (int vb = (int)gridDim.x - 1 - (int)blockIdx.x; vb < A.npart; vb += gridDim.x) zsgs(vb);
         }
     }
     if (!grid_sync_put(T, sc, &ssc, b0)) return tail_stop(A);
@@ -277,6 +288,8 @@ __global__ void __launch_bounds__(kTailThreads) k_tail(const __grid_constant__ T
                 __threadfence();
             }
             __syncthreads();
+            if (tid == 0) ssc.num = *(volatile double *)&T->num;    // the step size's numerator
+            __syncthreads();
 #pragma unroll 1
             for (int c = 0; c < 2; ++c) {
                 if (!want[c]) continue;
@@ -325,9 +338,7 @@ __global__ void __launch_bounds__(kTailThreads) k_tail(const __grid_constant__ T
         }
         if (nden > 0 && (int)blockIdx.x >= 2 * A.npart && (int)blockIdx.x < 2 * A.npart + nden) {
 #pragma unroll 1
-            for (int vb = (int)blockIdx.x - 2 * A.npart; vb < A.npart; vb += nden)
-                zmul_body(A.G, A.stride, A.rowb, A.S, A.k, A.coef, 1.0, A.u64, A.v64, A.used, nullptr,
-                          nullptr, A.zv, A.partials, A.n_pad, A.p, A.zc, vb);
+            for (int vb = (int)blockIdx.x - 2 * A.npart; vb < A.npart; vb += nden) zsgs(vb);
             __syncthreads();
             if (tid == 0) {
                 __threadfence();
@@ -541,7 +552,7 @@ static int build_fused_graph(iht_dataset *ds, int k, int K, int impl, const Tail
         e = cudaStreamBeginCapture(ws->cap_stream, cudaStreamCaptureModeThreadLocal);
         if (e == cudaSuccess) {
             e = cudaMemsetAsync(ws->tail, 0, sizeof(TailWork), ws->cap_stream);
-            if (e == cudaSuccess) rc0 = enqueue_solve_setup(ds, k, impl);
+            if (e == cudaSuccess) rc0 = enqueue_solve_setup(ds, k, impl, ws->tail->hist, &ws->tail->st.err);
             const cudaError_t e2 = cudaStreamEndCapture(ws->cap_stream, &setup);
             if (e == cudaSuccess) e = e2;
         }
@@ -602,8 +613,12 @@ static int build_fused_graph(iht_dataset *ds, int k, int K, int impl, const Tail
         const int32_t *done = &ws->sc->done;
         if (rc == IHT_OK)
             rc = launch_missing_sums_limbs(ds, ws->r32, ws->Mj, done, args.bimg, args.prm, args.nlim);
-        if (rc == IHT_OK) rc = launch_grad_tc_main(ds, ws->r32, ws->g, done);
-        if (rc == IHT_OK) rc = launch_cov_grad(ds, ws->r32, ws->g, done);
+        // the pass counts its keys into the next trip's histogram unless the
+        // kernel forms it itself
+        uint32_t *hist = args.own_hist ? nullptr : ws->tail->hist;
+        uint32_t *hflag = args.own_hist ? nullptr : &ws->tail->st.err;
+        if (rc == IHT_OK) rc = launch_grad_tc_main(ds, ws->r32, ws->g, done, hist, hflag);
+        if (rc == IHT_OK) rc = launch_cov_grad(ds, ws->r32, ws->g, done, hist, hflag);
         cudaGraph_t captured = nullptr;
         const cudaError_t e2 = cudaStreamEndCapture(ws->cap_stream, &captured);
         if (rc == IHT_OK && e2 != cudaSuccess) {
@@ -688,6 +703,7 @@ static int ensure_fused_exec(iht_dataset *ds, int k, int K, int impl, bool whole
     a.bimg = bimg;
     a.prm = prm;
     a.nlim = nlim;
+    a.own_hist = whole ? 0 : 1;
     *prm_out = prm;
     const uint64_t key[12] = {(uint64_t)k | ((uint64_t)ds->q << 32),
                               (uint64_t)K, (uint64_t)impl | ((uint64_t)whole << 8),
