@@ -34,7 +34,6 @@ constexpr uint32_t kBarSpin = 1u << 22;       // bounded barrier waits (polls; s
 struct TailWork {                     // zeroed before every solve
     unsigned long long bar_count;     // grid barrier: arrivals since the solve began (+ kBarAbort)
     int bar_err, pad_;                // 1: a barrier wait gave up
-    unsigned int den_ticket;          // blocks done with Z_S g_S in this launch
     double num;                       // ||g_S||^2, from the blocks that form Z_S g_S
     Scalars spec;                     // the second candidate's projection scalars (mu / kappa)
     SelState st;                      // selection state (boundary bin, candidate count)
@@ -193,20 +192,25 @@ __global__ void __launch_bounds__(kTailThreads) k_tail(const __grid_constant__ T
                   A.zv, A.partials, A.n_pad, A.p, A.zc, vb);
     };
 
-    // Z_S g_S for the step size: formed in C by the blocks no candidate needs
-    // (nden of them, each then counted in den_ticket), while the others select
-    // the candidates; in B when every block forms a candidate's residual
+    // Z_S g_S for the step size, in B: on the nden blocks no candidate needs
+    // (which then leave the candidate scan to the others), or, when every
+    // block forms a candidate's residual, on the last blocks besides their scan
     const int nfree = (int)gridDim.x - 2 * A.npart;
     const int nden = nfree > 0 ? min(nfree, A.npart) : 0;
+    const bool den_block = nden > 0 && (int)blockIdx.x >= 2 * A.npart && (int)blockIdx.x < 2 * A.npart + nden;
 
-    // B: the boundary bin (every block, from the whole histogram) and the keys
-    // in or above it as candidate words
-    {
+    // B: the boundary bin (every scanning block, from the whole histogram) and
+    // the keys in or above it as candidate words
+    if (den_block) {
+#pragma unroll 1
+        for (int vb = (int)blockIdx.x - 2 * A.npart; vb < A.npart; vb += nden) zsgs(vb);
+    } else {
         uint32_t *hs = reinterpret_cast<uint32_t *>(smem_raw);
         for (int b = tid; b < kSelBins; b += blockDim.x) hs[b] = __ldcg(&T->hist[b]);
         __syncthreads();
         sel_find(hs, kSelBins, (uint32_t)A.K, wsum, res);
         const uint32_t lo = res[0] << 20, ncand = res[1] + res[2];
+        const int sb = (int)blockIdx.x < 2 * A.npart ? (int)blockIdx.x : (int)blockIdx.x - nden;
         if (ncand <= (uint32_t)kSelCap)
             sel_each(A.g, A.P, [&](float x, int64_t j) {
                 const uint32_t key = sel_key(x);
@@ -215,7 +219,7 @@ __global__ void __launch_bounds__(kTailThreads) k_tail(const __grid_constant__ T
                     if (slot < (uint32_t)kSelCap)
                         T->cand[slot] = ((unsigned long long)key << 32) | (unsigned long long)(~(uint32_t)j);
                 }
-            });
+            }, sb, (int)gridDim.x - nden);
         if (b0 && tid == 0) {
             T->st.prefix = res[0] << 20;
             T->st.mask = 0x7ffu << 20;
@@ -252,7 +256,8 @@ __global__ void __launch_bounds__(kTailThreads) k_tail(const __grid_constant__ T
         for (int v = blockIdx.x; v < 2 * A.npart; v += gridDim.x) want[v >= A.npart] = true;
         if (b0) want[0] = true;
         if (want[0] || want[1]) {
-            // the step size's inputs: ||g_S||^2 (block 0) and the other scalars
+            // the solve's scalars as block 0 wrote them back (||g_S||^2 follows
+            // from T->num, published in B)
             if (tid < kScWords && !b0)
                 reinterpret_cast<unsigned long long *>(&ssc)[tid] =
                     reinterpret_cast<const volatile unsigned long long *>(sc)[tid];
@@ -273,20 +278,6 @@ __global__ void __launch_bounds__(kTailThreads) k_tail(const __grid_constant__ T
             }
             sel_finish_narrow(A.g, A.P, &T->st, T->cand, ncand, s_cand, (uint32_t)A.K,
                               reinterpret_cast<unsigned long long *>(smem_raw), kTailKept, wsum);
-            if (nden > 0 && tid == 0) {           // Z_S g_S complete (bounded wait)
-                volatile unsigned int *tk = &T->den_ticket;
-                uint32_t it = 0, ns = 32;
-                while (*tk < (unsigned int)nden) {
-                    if (++it > kBarSpin) {
-                        atomicAdd(&T->bar_count, kBarAbort);
-                        atomicExch(&T->bar_err, 1);
-                        break;
-                    }
-                    __nanosleep(ns);
-                    if (ns < 256) ns <<= 1;
-                }
-                __threadfence();
-            }
             __syncthreads();
             if (tid == 0) ssc.num = *(volatile double *)&T->num;    // the step size's numerator
             __syncthreads();
@@ -336,15 +327,6 @@ __global__ void __launch_bounds__(kTailThreads) k_tail(const __grid_constant__ T
                 }
             }
         }
-        if (nden > 0 && (int)blockIdx.x >= 2 * A.npart && (int)blockIdx.x < 2 * A.npart + nden) {
-#pragma unroll 1
-            for (int vb = (int)blockIdx.x - 2 * A.npart; vb < A.npart; vb += nden) zsgs(vb);
-            __syncthreads();
-            if (tid == 0) {
-                __threadfence();
-                atomicAdd(&T->den_ticket, 1u);
-            }
-        }
         if (b0) {
 #pragma unroll 1
             for (int b = tid; b < kSelBins; b += blockDim.x) T->hist[b] = 0;
@@ -352,7 +334,6 @@ __global__ void __launch_bounds__(kTailThreads) k_tail(const __grid_constant__ T
         }
     }
     if (!grid_sync_put(T, sc, &ssc, b0)) return tail_stop(A);
-    if (b0 && tid == 0) T->den_ticket = 0;    // every projection has passed its wait
 
     // D: every block takes the decisions itself -- the scalars block 0 wrote
     // back, both candidates' partial sums and the second one's scalars give
