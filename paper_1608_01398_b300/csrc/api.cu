@@ -335,6 +335,8 @@ int iht_load_bed(iht_ctx *ctx, const uint8_t *bed, size_t bed_bytes, int mem, in
         if (ds->miss_idx) cudaFree(ds->miss_idx);
         if (ds->miss_goff) cudaFree(ds->miss_goff);
         if (ds->miss_gidx) cudaFree(ds->miss_gidx);
+        if (ds->miss_ioff) cudaFree(ds->miss_ioff);
+        if (ds->miss_iidx) cudaFree(ds->miss_iidx);
         delete ds;
         return rc;
     }
@@ -354,6 +356,8 @@ int iht_dataset_free(iht_dataset *ds)
     if (ds->miss_idx) cudaFree(ds->miss_idx);
     if (ds->miss_goff) cudaFree(ds->miss_goff);
     if (ds->miss_gidx) cudaFree(ds->miss_gidx);
+    if (ds->miss_ioff) cudaFree(ds->miss_ioff);
+    if (ds->miss_iidx) cudaFree(ds->miss_iidx);
     delete ds;
     return IHT_OK;
 }

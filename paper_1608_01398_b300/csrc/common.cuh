@@ -172,6 +172,15 @@ struct iht_dataset {
     // at miss_goff[g] + (j mod 8) L_g, L_g = (miss_goff[g + 1] - miss_goff[g]) / 8
     int64_t *miss_goff = nullptr;
     uint16_t *miss_gidx = nullptr;
+    // the same lists interleaved for the single-column missing-call sums
+    // (uint16, built when r and 32 zero slots fit the sums kernel's shared
+    // memory): groups of 32 consecutive SNPs, group g's sequences of common
+    // length L_g (its longest list rounded up to a multiple of 8, padded with
+    // the zero slot n_pad + (j mod 32)); entry t of SNP j at miss_ioff[g] +
+    // 256 (t / 8) + 8 (j mod 32) + t mod 8, L_g = (miss_ioff[g + 1] -
+    // miss_ioff[g]) / 32
+    int64_t *miss_ioff = nullptr;
+    uint16_t *miss_iidx = nullptr;
     // nongenetic covariates (iht_set_covariates): q dense columns, predictors
     // p .. p+q-1; cov[t * n_pad + i] = covariate t of subject i (0 on pad samples)
     int64_t q = 0;

@@ -583,6 +583,84 @@ static int build_padded_lists(iht_dataset *ds)
     return IHT_OK;
 }
 
+// Interleaved lists (see iht_dataset): group g's sequence length L_g, the
+// longest list of its 32 SNPs rounded up to a multiple of 8.  One warp per group.
+__global__ void __launch_bounds__(256) k_ilv_len(const int64_t *__restrict__ off, int64_t p,
+                                                 int32_t *__restrict__ glen)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t ngroups = (p + 31) / 32;
+    const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t g = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); g < ngroups; g += nwarps) {
+        const int64_t j = 32 * g + lane;
+        const int len = j < p ? (int)(off[j + 1] - off[j]) : 0;
+        const int L = __reduce_max_sync(0xffffffffu, len);
+        if (lane == 0) glen[g] = (L + 7) & ~7;
+    }
+}
+
+// Entry t of lane l's sequence in group g sits at ioff[g] + 256 (t / 8) +
+// 8 l + t mod 8; past the lane's list (and for lanes past p) it is the zero
+// slot n_pad + l.
+__global__ void __launch_bounds__(256) k_ilv_fill(const int64_t *__restrict__ off, const uint16_t *__restrict__ idx,
+                                                  int64_t p, int64_t n_pad, const int64_t *__restrict__ ioff,
+                                                  uint16_t *__restrict__ iidx)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t ngroups = (p + 31) / 32;
+    const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t g = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); g < ngroups; g += nwarps) {
+        const int64_t j = 32 * g + lane;
+        const int64_t e0 = j < p ? off[j] : 0;
+        const int len = j < p ? (int)(off[j + 1] - e0) : 0;
+        const int L = (int)((ioff[g + 1] - ioff[g]) / 32);
+        uint16_t *dst = iidx + ioff[g] + 8 * lane;
+        const uint16_t z = (uint16_t)(n_pad + lane);
+        for (int t = 0; t < L; ++t) dst[256 * (t >> 3) + (t & 7)] = t < len ? idx[e0 + t] : z;
+    }
+}
+
+bool interleaved_lists_wanted(const iht_dataset *ds)
+{
+    return ds->miss_idx16 && ds->n_pad + 32 <= 65536 && sizeof(float) * (size_t)(ds->n_pad + 32) <= 160 * 1024;
+}
+
+static int build_interleaved_lists(iht_dataset *ds)
+{
+    cudaStream_t s = ds->ctx->stream;
+    const int64_t p = ds->p, ngroups = (p + 31) / 32;
+    const int blocks = (int)std::min<int64_t>(ceil_div(ngroups, 8), (int64_t)ds->ctx->num_sms * 8);
+    int32_t *glen = nullptr;
+    IHT_CUDA(dev_malloc(&glen, sizeof(int32_t) * ngroups));
+    k_ilv_len<<<blocks, 256, 0, s>>>(ds->miss_off, p, glen);
+    note_launch();
+    std::vector<int32_t> hl(ngroups);
+    std::vector<int64_t> ho(ngroups + 1);
+    cudaError_t e = cudaMemcpyAsync(hl.data(), glen, sizeof(int32_t) * ngroups, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    cudaFree(glen);
+    if (e != cudaSuccess) {
+        set_cuda_error(e, "interleaved list lengths");
+        return IHT_ECUDA;
+    }
+    ho[0] = 0;
+    for (int64_t g = 0; g < ngroups; ++g) ho[g + 1] = ho[g] + 32 * (int64_t)hl[g];
+    e = dev_malloc(&ds->miss_ioff, sizeof(int64_t) * (ngroups + 1));
+    if (e == cudaSuccess) e = dev_malloc(&ds->miss_iidx, sizeof(uint16_t) * std::max<int64_t>(ho[ngroups], 8));
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(ds->miss_ioff, ho.data(), sizeof(int64_t) * (ngroups + 1), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) {
+        set_cuda_error(e, "interleaved lists");
+        return e == cudaErrorMemoryAllocation ? IHT_ENOMEM : IHT_ECUDA;
+    }
+    k_ilv_fill<<<blocks, 256, 0, s>>>(ds->miss_off, (const uint16_t *)ds->miss_idx, p, ds->n_pad, ds->miss_ioff,
+                                      ds->miss_iidx);
+    note_launch();
+    IHT_CUDA(cudaGetLastError());
+    return IHT_OK;
+}
+
 int build_missing_lists(iht_dataset *ds)
 {
     cudaStream_t s = ds->ctx->stream;
@@ -633,7 +711,56 @@ int build_missing_lists(iht_dataset *ds)
                                                     (int32_t *)ds->miss_idx);
     note_launch();
     IHT_CUDA(cudaGetLastError());
+    if (interleaved_lists_wanted(ds)) {
+        const int rc = build_interleaved_lists(ds);
+        if (rc != IHT_OK) return rc;
+    }
     return padded_lists_wanted(ds) ? build_padded_lists(ds) : IHT_OK;
+}
+
+// Limb image of the residual staged in shared memory (512-thread blocks): every
+// block finds max |r| (the limbs' scale) itself and encodes its own share of
+// the samples; block 0 forms R in the limb kernel's order.
+__device__ __noinline__ void missing_limb_image(const float *rs, int64_t nlim, uint8_t *__restrict__ bimg,
+                                                   TcParams *prm)
+{
+    __shared__ float smax[16];
+    __shared__ double wsr[32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    float m = 0.0f;
+    for (int64_t i = threadIdx.x; i < nlim; i += blockDim.x) m = fmaxf(m, fabsf(rs[i]));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if (lane == 0) smax[warp] = m;
+    __syncthreads();
+    m = 0.0f;
+#pragma unroll 1
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) m = fmaxf(m, smax[w]);
+    const float s0 = limb_scale(m);
+    const int64_t per = (nlim + gridDim.x - 1) / gridDim.x;
+    const int64_t i0 = (int64_t)blockIdx.x * per, i1 = min(nlim, i0 + per);
+    for (int64_t i = i0 + threadIdx.x; i < i1; i += blockDim.x) limb_encode(rs[i], s0, bimg, i);
+    if (blockIdx.x == 0) {
+        // thread h holds the limb kernel's residues t = h and t = h + 512
+        double a0 = 0.0, a1 = 0.0;
+        for (int64_t i = threadIdx.x; i < nlim; i += 1024) a0 += (double)rs[i];
+        for (int64_t i = threadIdx.x + 512; i < nlim; i += 1024) a1 += (double)rs[i];
+        a0 = warp_sum(a0);
+        a1 = warp_sum(a1);
+        if (lane == 0) {
+            wsr[warp] = a0;
+            wsr[warp + 16] = a1;
+        }
+        for (int b = threadIdx.x; b < 256; b += blockDim.x) bimg[256 + 256 * (nlim >> 5) + b] = 0;
+        __syncthreads();
+        if (warp == 0) {
+            const double R = warp_sum(wsr[lane]);
+            if (lane == 0) {
+                prm->s0 = s0;
+                prm->R = (float)R;
+            }
+        }
+    }
 }
 
 // M_j = sum of r over the missing calls of SNP j.  The block stages r in
@@ -663,45 +790,7 @@ __global__ void __launch_bounds__(512) k_missing_sum_smem(const int64_t *__restr
     constexpr int kPer = 16 / (int)sizeof(IdxT);
     for (int64_t i = threadIdx.x; i < n_pad; i += blockDim.x) rs_miss[i] = r32[i];
     __syncthreads();
-    if constexpr (kLimbs) {
-        __shared__ float smax[16];
-        __shared__ double wsr[32];
-        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-        float m = 0.0f;
-        for (int64_t i = threadIdx.x; i < nlim; i += blockDim.x) m = fmaxf(m, fabsf(rs_miss[i]));
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
-        if (lane == 0) smax[warp] = m;
-        __syncthreads();
-        m = 0.0f;
-#pragma unroll 1
-        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) m = fmaxf(m, smax[w]);
-        const float s0 = limb_scale(m);
-        const int64_t per = (nlim + gridDim.x - 1) / gridDim.x;
-        const int64_t i0 = (int64_t)blockIdx.x * per, i1 = min(nlim, i0 + per);
-        for (int64_t i = i0 + threadIdx.x; i < i1; i += blockDim.x) limb_encode(rs_miss[i], s0, bimg, i);
-        if (blockIdx.x == 0) {
-            // thread h holds the limb kernel's residues t = h and t = h + 512
-            double a0 = 0.0, a1 = 0.0;
-            for (int64_t i = threadIdx.x; i < nlim; i += 1024) a0 += (double)rs_miss[i];
-            for (int64_t i = threadIdx.x + 512; i < nlim; i += 1024) a1 += (double)rs_miss[i];
-            a0 = warp_sum(a0);
-            a1 = warp_sum(a1);
-            if (lane == 0) {
-                wsr[warp] = a0;
-                wsr[warp + 16] = a1;
-            }
-            for (int b = threadIdx.x; b < 256; b += blockDim.x) bimg[256 + 256 * (nlim >> 5) + b] = 0;
-            __syncthreads();
-            if (warp == 0) {
-                const double R = warp_sum(wsr[lane]);
-                if (lane == 0) {
-                    prm->s0 = s0;
-                    prm->R = (float)R;
-                }
-            }
-        }
-    }
+    if constexpr (kLimbs) missing_limb_image(rs_miss, nlim, bimg, prm);
     const uint4 *__restrict__ idx4 = reinterpret_cast<const uint4 *>(idx);
     constexpr int kBatch = 8;                                 // 16-byte list pieces in flight
     for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < p;
@@ -729,6 +818,92 @@ __global__ void __launch_bounds__(512) k_missing_sum_smem(const int64_t *__restr
             }
         }
         M[j] = m;
+    }
+}
+
+// The same sums over the interleaved lists (iht_dataset::miss_ioff): a warp
+// takes whole groups of 32 SNPs, lane l SNP 32 g + l, and piece q of group g
+// -- 512 contiguous bytes, entries 8q .. 8q+7 of every lane's sequence -- is
+// one coalesced request of the warp instead of 32 scattered 16-byte ones.
+// Two pieces are requested ahead of the two being summed, and the next
+// group's offsets ahead of the group.  Pads index the 32 zero slots after r
+// (lane l's at n_pad + l, a bank of its own); adding +0.0f to a sum that
+// starts at 0.0f leaves it unchanged, so every M_j is the plain lists' sum in
+// the same order, bit for bit.
+__device__ __forceinline__ float miss_sum8(float m, uint4 w, const float *rs)
+{
+    m += rs[w.x & 0xffffu];
+    m += rs[w.x >> 16];
+    m += rs[w.y & 0xffffu];
+    m += rs[w.y >> 16];
+    m += rs[w.z & 0xffffu];
+    m += rs[w.z >> 16];
+    m += rs[w.w & 0xffffu];
+    m += rs[w.w >> 16];
+    return m;
+}
+
+template <bool kLimbs>
+__global__ void __launch_bounds__(512, 3) k_missing_sum_ilv(const int64_t *__restrict__ ioff,
+                                                            const uint16_t *__restrict__ iidx, int64_t p,
+                                                            const float *__restrict__ r32, int64_t n_pad,
+                                                            float *__restrict__ M,
+                                                            const int32_t *__restrict__ done,
+                                                            uint8_t *__restrict__ bimg, TcParams *prm,
+                                                            int64_t nlim)
+{
+    extern __shared__ __align__(16) float rs_miss[];   // r, then 32 zero slots
+    if (done && *done) return;
+    const int lane = threadIdx.x & 31;
+    const int64_t ngroups = (p + 31) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    int64_t g = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const uint4 *__restrict__ i4 = reinterpret_cast<const uint4 *>(iidx);
+    // the first group's offsets and first two pieces are requested before r is staged
+    int64_t a = 0, b = 0;
+    if (g < ngroups) {
+        a = __ldg(&ioff[g]);
+        b = __ldg(&ioff[g + 1]);
+    }
+    uint4 w0 = make_uint4(0u, 0u, 0u, 0u), w1 = w0;
+    if (b - a > 0) w0 = __ldcs(i4 + (a >> 3) + lane);
+    if (b - a > 256) w1 = __ldcs(i4 + (a >> 3) + 32 + lane);
+    if ((reinterpret_cast<uintptr_t>(r32) & 15u) == 0 && (n_pad & 3) == 0) {
+        const float4 *__restrict__ r4 = reinterpret_cast<const float4 *>(r32);
+        float4 *rs4 = reinterpret_cast<float4 *>(rs_miss);
+        for (int64_t i = threadIdx.x; i < (n_pad >> 2); i += blockDim.x) rs4[i] = __ldcg(r4 + i);
+    } else {
+        for (int64_t i = threadIdx.x; i < n_pad; i += blockDim.x) rs_miss[i] = __ldcg(r32 + i);
+    }
+    if (threadIdx.x < 32) rs_miss[n_pad + threadIdx.x] = 0.0f;
+    __syncthreads();
+    if constexpr (kLimbs) missing_limb_image(rs_miss, nlim, bimg, prm);
+    for (; g < ngroups; g += nwarps) {
+        const int64_t gn = g + nwarps;
+        int64_t an = 0, bn = 0;
+        if (gn < ngroups) {
+            an = __ldg(&ioff[gn]);
+            bn = __ldg(&ioff[gn + 1]);
+        }
+        const int nq = (int)((b - a) >> 8);                 // pieces of 256 entries
+        const uint4 *__restrict__ src = i4 + (a >> 3) + lane;
+        float m = 0.0f;
+#pragma unroll 1
+        for (int q = 0; q < nq; q += 2) {
+            uint4 n0 = w0, n1 = w1;
+            if (q + 2 < nq) n0 = __ldcs(src + 32 * (q + 2));
+            if (q + 3 < nq) n1 = __ldcs(src + 32 * (q + 3));
+            m = miss_sum8(m, w0, rs_miss);
+            if (q + 1 < nq) m = miss_sum8(m, w1, rs_miss);
+            w0 = n0;
+            w1 = n1;
+        }
+        const int64_t j = (g << 5) + lane;
+        if (j < p) M[j] = m;
+        a = an;
+        b = bn;
+        if (b - a > 0) w0 = __ldcs(i4 + (a >> 3) + lane);
+        if (b - a > 256) w1 = __ldcs(i4 + (a >> 3) + 32 + lane);
     }
 }
 
@@ -771,9 +946,38 @@ bool missing_limbs_supported(const iht_dataset *ds, int64_t nlim)
 }
 
 template <bool kLimbs>
+static int launch_missing_ilv(iht_dataset *ds, const float *r32, float *M, const int32_t *done,
+                              uint8_t *bimg, TcParams *prm, int64_t nlim)
+{
+    const size_t smem = sizeof(float) * (size_t)(ds->n_pad + 32);
+    static thread_local int configured = -1, per_sm = 1;
+    static thread_local size_t sized = 0;
+    if (configured != ds->ctx->device) {
+        IHT_CUDA(cudaFuncSetAttribute(k_missing_sum_ilv<kLimbs>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      160 * 1024));
+        configured = ds->ctx->device;
+        sized = 0;
+    }
+    if (sized != smem) {   // resident blocks per SM for this residual length
+        IHT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_missing_sum_ilv<kLimbs>, 512, smem));
+        per_sm = std::max(per_sm, 1);
+        sized = smem;
+    }
+    const int64_t ngroups = (ds->p + 31) / 32;
+    const int blocks = (int)std::min<int64_t>(std::max<int64_t>(ceil_div(ngroups, 16), 1),
+                                              (int64_t)ds->ctx->num_sms * per_sm);
+    k_missing_sum_ilv<kLimbs><<<blocks, 512, smem, ds->ctx->stream>>>(ds->miss_ioff, ds->miss_iidx, ds->p, r32,
+                                                                      ds->n_pad, M, done, bimg, prm, nlim);
+    note_launch();
+    IHT_CUDA(cudaGetLastError());
+    return IHT_OK;
+}
+
+template <bool kLimbs>
 static int launch_missing_smem(iht_dataset *ds, const float *r32, float *M, const int32_t *done,
                                uint8_t *bimg, TcParams *prm, int64_t nlim)
 {
+    if (ds->miss_iidx) return launch_missing_ilv<kLimbs>(ds, r32, M, done, bimg, prm, nlim);
     cudaStream_t s = ds->ctx->stream;
     const size_t smem = sizeof(float) * (size_t)ds->n_pad;
     static thread_local int configured = -1;
@@ -784,9 +988,15 @@ static int launch_missing_smem(iht_dataset *ds, const float *r32, float *M, cons
                                       cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024));
         configured = ds->ctx->device;
     }
-    const int per_sm = smem <= 40 * 1024 ? 4 : (smem <= 48 * 1024 ? 3 : 1);
+    int per_sm = 1;   // resident blocks per SM (registers and shared memory)
+    if (ds->miss_idx16)
+        IHT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_missing_sum_smem<uint16_t, kLimbs>, 512,
+                                                               smem));
+    else
+        IHT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_missing_sum_smem<int32_t, kLimbs>, 512,
+                                                               smem));
     const int blocks = (int)std::min<int64_t>(std::max<int64_t>(ceil_div(ds->p, 512), 1),
-                                              (int64_t)ds->ctx->num_sms * per_sm);
+                                              (int64_t)ds->ctx->num_sms * std::max(per_sm, 1));
     if (ds->miss_idx16)
         k_missing_sum_smem<uint16_t, kLimbs><<<blocks, 512, smem, s>>>(
             ds->miss_off, (const uint16_t *)ds->miss_idx, ds->p, r32, ds->n_pad, M, done, bimg, prm, nlim);
