@@ -303,7 +303,7 @@ int launch_missing_sums(iht_dataset *ds, const float *r32, float *M, const int32
 // (the fused solve); EINVAL when r does not fit the kernel's shared memory.
 bool missing_limbs_supported(const iht_dataset *ds, int64_t nlim);
 int launch_missing_sums_limbs(iht_dataset *ds, const float *r32, float *M, const int32_t *done,
-                              uint8_t *bimg, TcParams *prm, int64_t nlim);
+                              uint8_t *bimg, TcParams *prm, int64_t nlim, bool programmatic = false);
 int setup_rows(iht_dataset *ds, const int32_t *rows_dev, int64_t n_rows);
 int launch_counts(iht_dataset *ds, int64_t n_rows);
 int scatter_rows_f64(iht_dataset *ds, const int32_t *rows_dev, int64_t n_rows, const double *src,
@@ -317,12 +317,14 @@ bool grad_tc_supported(const iht_dataset *ds);
 int prepare_grad_tc(iht_dataset *ds, const float *r32, const int32_t *done);
 // hist (optional): the selection's 2048-bin histogram of |g| bits 30..20 the
 // pass adds its keys to (hflag bit 0: a non-finite g)
+// (programmatic: launched with programmatic stream serialization -- it may
+// start while the kernel before it runs, and waits for it before reading)
 int launch_grad_tc_main(iht_dataset *ds, const float *r32, float *g, const int32_t *done,
-                        uint32_t *hist = nullptr, uint32_t *hflag = nullptr);
+                        uint32_t *hist = nullptr, uint32_t *hflag = nullptr, bool programmatic = false);
 int prepare_grad_tc_to(iht_dataset *ds, const float *r32, float *Mj, const int32_t *done);
 int launch_grad_tc_main_with(iht_dataset *ds, const float *r32, float *g, const float *u32,
                              const float *v32, const float *Mj, const int32_t *done,
-                             uint32_t *hist = nullptr, uint32_t *hflag = nullptr);
+                             uint32_t *hist = nullptr, uint32_t *hflag = nullptr, bool programmatic = false);
 void grad_tc_release_thread();
 uint64_t grad_tc_scratch_id();
 int grad_tc_status(iht_dataset *ds, int *timed_out);
@@ -460,6 +462,14 @@ int launch_compact_support_batch(iht_dataset *ds, const BSolve *bs, int nb, int 
                                  int32_t *supports, double *beta_s);
 
 // device helpers ------------------------------------------------------------
+// Programmatic dependent launch (a kernel launched with programmatic stream
+// serialization may start while the grid before it still runs): wait for the
+// grids this one depends on to complete with their memory visible (at once
+// when launched without such a dependency), and let the dependent grid launch
+// once every block of this one has called it or exited.
+__device__ __forceinline__ void grid_dep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void grid_dep_launch() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
 __device__ __forceinline__ float warp_sum(float x)
 {
 #pragma unroll

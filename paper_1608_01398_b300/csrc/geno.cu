@@ -853,7 +853,7 @@ __global__ void __launch_bounds__(512, 3) k_missing_sum_ilv(const int64_t *__res
                                                             int64_t nlim)
 {
     extern __shared__ __align__(16) float rs_miss[];   // r, then 32 zero slots
-    if (done && *done) return;
+    grid_dep_launch();
     const int lane = threadIdx.x & 31;
     const int64_t ngroups = (p + 31) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -868,6 +868,8 @@ __global__ void __launch_bounds__(512, 3) k_missing_sum_ilv(const int64_t *__res
     uint4 w0 = make_uint4(0u, 0u, 0u, 0u), w1 = w0;
     if (b - a > 0) w0 = __ldcs(i4 + (a >> 3) + lane);
     if (b - a > 256) w1 = __ldcs(i4 + (a >> 3) + 32 + lane);
+    grid_dep_wait();   // r and the stop flag, when launched programmatically after the kernel forming them
+    if (done && *done) return;
     if ((reinterpret_cast<uintptr_t>(r32) & 15u) == 0 && (n_pad & 3) == 0) {
         const float4 *__restrict__ r4 = reinterpret_cast<const float4 *>(r32);
         float4 *rs4 = reinterpret_cast<float4 *>(rs_miss);
@@ -947,7 +949,7 @@ bool missing_limbs_supported(const iht_dataset *ds, int64_t nlim)
 
 template <bool kLimbs>
 static int launch_missing_ilv(iht_dataset *ds, const float *r32, float *M, const int32_t *done,
-                              uint8_t *bimg, TcParams *prm, int64_t nlim)
+                              uint8_t *bimg, TcParams *prm, int64_t nlim, bool programmatic)
 {
     const size_t smem = sizeof(float) * (size_t)(ds->n_pad + 32);
     static thread_local int configured = -1, per_sm = 1;
@@ -966,18 +968,29 @@ static int launch_missing_ilv(iht_dataset *ds, const float *r32, float *M, const
     const int64_t ngroups = (ds->p + 31) / 32;
     const int blocks = (int)std::min<int64_t>(std::max<int64_t>(ceil_div(ngroups, 16), 1),
                                               (int64_t)ds->ctx->num_sms * per_sm);
-    k_missing_sum_ilv<kLimbs><<<blocks, 512, smem, ds->ctx->stream>>>(ds->miss_ioff, ds->miss_iidx, ds->p, r32,
-                                                                      ds->n_pad, M, done, bimg, prm, nlim);
+    cudaLaunchConfig_t lc = {};
+    lc.gridDim = dim3((unsigned)blocks);
+    lc.blockDim = dim3(512);
+    lc.dynamicSmemBytes = smem;
+    lc.stream = ds->ctx->stream;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    lc.attrs = at;
+    lc.numAttrs = programmatic ? 1 : 0;
+    const cudaError_t e = cudaLaunchKernelEx(&lc, k_missing_sum_ilv<kLimbs>, (const int64_t *)ds->miss_ioff,
+                                             (const uint16_t *)ds->miss_iidx, ds->p, r32, ds->n_pad, M, done,
+                                             bimg, prm, nlim);
     note_launch();
-    IHT_CUDA(cudaGetLastError());
+    IHT_CUDA(e);
     return IHT_OK;
 }
 
 template <bool kLimbs>
 static int launch_missing_smem(iht_dataset *ds, const float *r32, float *M, const int32_t *done,
-                               uint8_t *bimg, TcParams *prm, int64_t nlim)
+                               uint8_t *bimg, TcParams *prm, int64_t nlim, bool programmatic = false)
 {
-    if (ds->miss_iidx) return launch_missing_ilv<kLimbs>(ds, r32, M, done, bimg, prm, nlim);
+    if (ds->miss_iidx) return launch_missing_ilv<kLimbs>(ds, r32, M, done, bimg, prm, nlim, programmatic);
     cudaStream_t s = ds->ctx->stream;
     const size_t smem = sizeof(float) * (size_t)ds->n_pad;
     static thread_local int configured = -1;
@@ -1009,10 +1022,10 @@ static int launch_missing_smem(iht_dataset *ds, const float *r32, float *M, cons
 }
 
 int launch_missing_sums_limbs(iht_dataset *ds, const float *r32, float *M, const int32_t *done,
-                              uint8_t *bimg, TcParams *prm, int64_t nlim)
+                              uint8_t *bimg, TcParams *prm, int64_t nlim, bool programmatic)
 {
     if (!missing_limbs_supported(ds, nlim)) return IHT_EINVAL;
-    return launch_missing_smem<true>(ds, r32, M, done, bimg, prm, nlim);
+    return launch_missing_smem<true>(ds, r32, M, done, bimg, prm, nlim, programmatic);
 }
 
 int launch_missing_sums(iht_dataset *ds, const float *r32, float *M, const int32_t *done)

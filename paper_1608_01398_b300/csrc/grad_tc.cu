@@ -333,6 +333,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_grad_tc(const __grid_constant
     constexpr int kDecoders = kTcNWG * 128;
     constexpr int kProducerWarp = kTcNWG * 5;          // first TMA warp
 
+    grid_dep_wait();   // the missing-call sums and limb image when launched programmatically
     if (done && *done) return;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     uint8_t *stages = smem;                      // kTcNWG * nst stages, 1024-aligned
@@ -695,16 +696,25 @@ bool grad_tc_shape_fits(const iht_dataset *ds, const int *params)
 
 static int tc_launch(iht_dataset *ds, const CUtensorMap &map, int nst, float *g, const float *u32,
                      const float *v32, const float *Mj, const int32_t *done, uint32_t *hist = nullptr,
-                     uint32_t *hflag = nullptr)
+                     uint32_t *hflag = nullptr, bool programmatic = false)
 {
     const int64_t tiles = (ds->p + 127) / 128;
     const int grid = (int)std::min<int64_t>((tiles + kTcNWG - 1) / kTcNWG, (int64_t)ds->ctx->num_sms);
-    const size_t smem = (size_t)kTcNWG * nst * kTcStageTile + tc_bbytes(ds);
-    k_grad_tc<<<grid, kTcThreads, smem, ds->ctx->stream>>>(map, ds->p, tc_ngroups(ds), nst, g_tc.bimg,
-                                                           (int)tc_bbytes(ds), Mj, u32, v32, g, g_tc.prm,
-                                                           done, hist, hflag);
+    cudaLaunchConfig_t lc = {};
+    lc.gridDim = dim3((unsigned)grid);
+    lc.blockDim = dim3(kTcThreads);
+    lc.dynamicSmemBytes = (size_t)kTcNWG * nst * kTcStageTile + tc_bbytes(ds);
+    lc.stream = ds->ctx->stream;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    lc.attrs = at;
+    lc.numAttrs = programmatic ? 1 : 0;
+    const cudaError_t e = cudaLaunchKernelEx(&lc, k_grad_tc, map, ds->p, tc_ngroups(ds), nst,
+                                             (const uint8_t *)g_tc.bimg, (int)tc_bbytes(ds), Mj, u32, v32, g,
+                                             g_tc.prm, done, hist, hflag);
     note_launch();
-    IHT_CUDA(cudaGetLastError());
+    IHT_CUDA(e);
     return IHT_OK;
 }
 
@@ -750,7 +760,7 @@ static int tc_tune(iht_dataset *ds, const CUtensorMap &map, float *g, const floa
 // the stream is not being captured), else the most that fit.
 int launch_grad_tc_main_with(iht_dataset *ds, const float *r32, float *g, const float *u32,
                              const float *v32, const float *Mj, const int32_t *done, uint32_t *hist,
-                             uint32_t *hflag)
+                             uint32_t *hflag, bool programmatic)
 {
     cudaStream_t s = ds->ctx->stream;
     CUtensorMap map;
@@ -764,9 +774,9 @@ int launch_grad_tc_main_with(iht_dataset *ds, const float *r32, float *g, const 
     }
     int prm[kTuneParams];
     if (tune_lookup(ds, IHT_PASS_SINGLE, 0, prm) && grad_tc_shape_fits(ds, prm))
-        return tc_launch(ds, map, prm[0], g, u32, v32, Mj, done, hist, hflag);
+        return tc_launch(ds, map, prm[0], g, u32, v32, Mj, done, hist, hflag, programmatic);
     if (!hist && autotune_enabled() && !stream_capturing(s)) return tc_tune(ds, map, g, u32, v32, Mj, done);
-    return tc_launch(ds, map, tc_stages(ds), g, u32, v32, Mj, done, hist, hflag);
+    return tc_launch(ds, map, tc_stages(ds), g, u32, v32, Mj, done, hist, hflag, programmatic);
 }
 
 // True when a pass launched now would take its settled shape (a tuned one is
@@ -779,9 +789,10 @@ bool grad_tc_shape_settled(const iht_dataset *ds)
 }
 
 int launch_grad_tc_main(iht_dataset *ds, const float *r32, float *g, const int32_t *done,
-                        uint32_t *hist, uint32_t *hflag)
+                        uint32_t *hist, uint32_t *hflag, bool programmatic)
 {
-    return launch_grad_tc_main_with(ds, r32, g, ds->ws->u32, ds->ws->v32, ds->ws->Mj, done, hist, hflag);
+    return launch_grad_tc_main_with(ds, r32, g, ds->ws->u32, ds->ws->v32, ds->ws->Mj, done, hist, hflag,
+                                    programmatic);
 }
 
 // Identifies the calling thread's pass scratch (changes when it is reallocated).

@@ -149,6 +149,7 @@ __global__ void __launch_bounds__(kTailThreads) k_tail(const __grid_constant__ T
     const bool b0 = blockIdx.x == 0;
 
     __shared__ Scalars ssc;               // the block's working copy of the scalars (block 0's is the solve's)
+    grid_dep_launch();   // the missing-call sums may launch now; they wait for this grid before reading
     if (tid == 0) s_state = *(volatile int32_t *)&sc->done;
     if (tid < kScWords)
         reinterpret_cast<unsigned long long *>(&ssc)[tid] =
@@ -593,12 +594,12 @@ static int build_fused_graph(iht_dataset *ds, int k, int K, int impl, const Tail
         }
         const int32_t *done = &ws->sc->done;
         if (rc == IHT_OK)
-            rc = launch_missing_sums_limbs(ds, ws->r32, ws->Mj, done, args.bimg, args.prm, args.nlim);
+            rc = launch_missing_sums_limbs(ds, ws->r32, ws->Mj, done, args.bimg, args.prm, args.nlim, true);
         // the pass counts its keys into the next trip's histogram unless the
         // kernel forms it itself
         uint32_t *hist = args.own_hist ? nullptr : ws->tail->hist;
         uint32_t *hflag = args.own_hist ? nullptr : &ws->tail->st.err;
-        if (rc == IHT_OK) rc = launch_grad_tc_main(ds, ws->r32, ws->g, done, hist, hflag);
+        if (rc == IHT_OK) rc = launch_grad_tc_main(ds, ws->r32, ws->g, done, hist, hflag, true);
         if (rc == IHT_OK) rc = launch_cov_grad(ds, ws->r32, ws->g, done, hist, hflag);
         cudaGraph_t captured = nullptr;
         const cudaError_t e2 = cudaStreamEndCapture(ws->cap_stream, &captured);
