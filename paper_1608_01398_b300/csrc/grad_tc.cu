@@ -406,18 +406,29 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_grad_tc(const __grid_constant
                 }
                 const uint8_t *base = stages + (w * nst + slot) * kTcStageTile + r * kTcStageBytes;
                 const int nchunks = min(cps, ngroups - st * cps);
-                for (int c = 0; c < nchunks && ok; c += 2) {              // one A group per pair
-                    const uint4 x0 = *reinterpret_cast<const uint4 *>(base + (c == 0 ? off0 : off2));
-                    uint4 x1 = make_uint4(0u, 0u, 0u, 0u);
-                    if (c + 1 < nchunks)
-                        x1 = *reinterpret_cast<const uint4 *>(base + (c == 0 ? off1 : off3));
+                // the row's chunks of this stage into registers, and the stage
+                // handed back to the producer before they are decoded
+                const uint4 zero = make_uint4(0u, 0u, 0u, 0u);
+                uint4 xc[4];
+                xc[0] = *reinterpret_cast<const uint4 *>(base + off0);
+                xc[1] = nchunks > 1 ? *reinterpret_cast<const uint4 *>(base + off1) : zero;
+                xc[2] = nchunks > 2 ? *reinterpret_cast<const uint4 *>(base + off2) : zero;
+                xc[3] = nchunks > 3 ? *reinterpret_cast<const uint4 *>(base + off3) : zero;
+                mbar_arrive(&P.tma_empty[slot]);
+                if (++slot == (uint32_t)nst) {
+                    slot = 0;
+                    sphase ^= 1u;
+                }
+#pragma unroll
+                for (int c = 0; c < 4; c += 2) {                         // one A group per pair
+                    if (c >= nchunks || !ok) break;
                     // (a fresh barrier passes the wait on parity 1: the first round is free)
                     if (!mbar_wait(&P.empty[buf], bphase ^ 1u)) {
                         abort_flag = 1;
                         ok = false;
                     }
                     tc_fence_after();
-                    tc_put_group(abase + 32 * buf, x0, x1);
+                    tc_put_group(abase + 32 * buf, xc[c], xc[c + 1]);
                     asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
                     tc_fence_before();
                     mbar_arrive(&P.full[buf]);
@@ -426,11 +437,6 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_grad_tc(const __grid_constant
                         buf = 0;
                         bphase ^= 1u;
                     }
-                }
-                mbar_arrive(&P.tma_empty[slot]);
-                if (++slot == (uint32_t)nst) {
-                    slot = 0;
-                    sphase ^= 1u;
                 }
                 if (abort_flag) ok = false;
             }
