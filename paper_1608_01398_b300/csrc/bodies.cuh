@@ -224,6 +224,7 @@ struct MergeArgs {
     Scalars *sc;
     int shrinks = 0;          // first attempt only: mu / kappa this many times after num / den
                               // (a later attempt evaluated ahead of the decision on this one)
+    const float *gS = nullptr;    // g on S in S order, when the caller has it at hand
 };
 
 constexpr int kMergeThreads = 1024;
@@ -247,7 +248,9 @@ template <int KM> struct MergeSharedT {
     double uw[kU];
     uint8_t inS[kU];
     uint8_t inSp[kU];
-    unsigned long long skey[kSort];
+    // sort keys and positions; the rank reads skey and spos together as one
+    // array of kU 16-byte keys (16 kU = 12 kSort bytes)
+    alignas(16) unsigned long long skey[kSort];
     int32_t spos[kSort];
     double red[32];
     uint32_t wsum[32];
@@ -261,6 +264,18 @@ __device__ __forceinline__ bool before(unsigned long long ka, int32_t ia, unsign
                                        int32_t ib)
 {
     return ka > kb || (ka == kb && ia < ib);
+}
+
+// 96-bit unsigned (a.z, a.y, a.x) < (v.z, v.y, v.x): all ones if so, else 0
+// (the borrow of a - v).
+__device__ __forceinline__ uint32_t lt96(uint4 a, uint4 v)
+{
+    uint32_t b;
+    asm("{\n.reg .u32 t, z;\nmov.u32 z, 0;\nsub.cc.u32 t, %1, %4;\nsubc.cc.u32 t, %2, %5;\n"
+        "subc.cc.u32 t, %3, %6;\nsubc.u32 %0, z, z;\n}"
+        : "=r"(b)
+        : "r"(a.x), "r"(a.y), "r"(a.z), "r"(v.x), "r"(v.y), "r"(v.z));
+    return b;
 }
 
 __device__ __forceinline__ int lower_bound_i32(const int32_t *a, int n, int32_t x)
@@ -406,7 +421,7 @@ template <typename SH = MergeShared> __device__ __forceinline__ void merge_body(
                 sh.uidx[u] = j;
                 sh.inS[u] = 1;
                 sh.ubeta[u] = sh.sbS[a];
-                sh.ug[u] = (double)A.g[j];
+                sh.ug[u] = (double)(A.gS ? A.gS[a] : A.g[j]);
             }
             base += tot;
             __syncthreads();              // wsum is reused by the next chunk
@@ -416,41 +431,41 @@ template <typename SH = MergeShared> __device__ __forceinline__ void merge_body(
     __syncthreads();
     const int nU = K + sh.nS_extra;
 
+    const bool small = nU <= kMergeRank;
+    // rank keys {~index, |w| low word, |w| high word, 0}: v comes before u
+    // (|w| descending, index ascending) iff key u < key v as 96-bit integers
+    uint4 *rk = reinterpret_cast<uint4 *>(sh.skey);
 #pragma unroll 1
     for (int u = threadIdx.x; u < nU; u += blockDim.x) {
-        sh.uw[u] = __dadd_rn(sh.ubeta[u], __dmul_rn(mu, sh.ug[u]));
-        sh.skey[u] = (unsigned long long)__double_as_longlong(fabs(sh.uw[u]));
+        const double w = __dadd_rn(sh.ubeta[u], __dmul_rn(mu, sh.ug[u]));
+        sh.uw[u] = w;
+        if (small) {
+            const unsigned long long kb = (unsigned long long)__double_as_longlong(fabs(w));
+            rk[u] = make_uint4(~(uint32_t)sh.uidx[u], (uint32_t)kb, (uint32_t)(kb >> 32), 0u);
+        }
     }
     __syncthreads();
-    const bool small = nU <= kMergeRank;
     if (small) {
-        // S+ by rank: u is in S+ iff fewer than k entries come before it
-        // (|w| descending, index ascending); a thread ranks two entries in one
-        // sweep over v, and every thread reads the same v at the same time
-        // (shared-memory broadcast)
+        // S+ by rank: u is in S+ iff fewer than k entries come before it; a
+        // thread ranks two entries in one sweep over v, and every thread reads
+        // the same v at the same time (shared-memory broadcast)
 #pragma unroll 1
         for (int ub = 0; ub < nU; ub += 2 * (int)blockDim.x) {
             const int ua = ub + threadIdx.x, uc = ua + blockDim.x;
             const bool two = __any_sync(0xffffffffu, uc < nU);   // one path per warp
             if (ua >= nU) continue;               // (a large block: most threads have none)
-            const int la = ua, lc = min(uc, nU - 1);
-            const unsigned long long ka = sh.skey[la], kc = sh.skey[lc];
-            const int32_t ia = sh.uidx[la], ic = sh.uidx[lc];
+            const uint4 ka = rk[ua], kc = rk[min(uc, nU - 1)];
             int ra = 0, rc = 0;
             if (two) {
 #pragma unroll 4
                 for (int v = 0; v < nU; ++v) {
-                    const unsigned long long kv = sh.skey[v];
-                    const int32_t iv = sh.uidx[v];
-                    ra += (int)((kv > ka) | ((kv == ka) & (iv < ia)));
-                    rc += (int)((kv > kc) | ((kv == kc) & (iv < ic)));
+                    const uint4 kv = rk[v];
+                    ra -= (int)lt96(ka, kv);
+                    rc -= (int)lt96(kc, kv);
                 }
             } else {
 #pragma unroll 4
-                for (int v = 0; v < nU; ++v) {
-                    const unsigned long long kv = sh.skey[v];
-                    ra += (int)((kv > ka) | ((kv == ka) & (sh.uidx[v] < ia)));
-                }
+                for (int v = 0; v < nU; ++v) ra -= (int)lt96(ka, rk[v]);
             }
             if (ua < nU) sh.inSp[ua] = ra < k ? 1 : 0;
             if (uc < nU) sh.inSp[uc] = rc < k ? 1 : 0;
@@ -465,22 +480,34 @@ template <typename SH = MergeShared> __device__ __forceinline__ void merge_body(
         for (int r = threadIdx.x; r < k; r += blockDim.x) sh.inSp[sh.spos[r]] = 1;
         __syncthreads();
     }
-    // ||beta+ - beta||^2, ||beta||^2 and |S n S+| by one warp (FP64 issue is
-    // scarce: a block-wide reduction would spend it on empty threads); only
-    // thread 0 uses them
+    // ||beta+ - beta||^2 by warp 0, ||beta||^2 by warp 1 and |S n S+| by warp 2
+    // (all three by warp 0 in a block of fewer warps), each over u = lane
+    // (mod 32) and a shuffle tree: FP64 issue is scarce, and a block-wide
+    // reduction would spend it on empty threads.  Only thread 0 uses them
+    // (warps 1 and 2 hand theirs over in shared memory, read after the
+    // barriers below).
     int kept = 0;
     double dd = 0.0, bb = 0.0;
-    if (threadIdx.x < 32) {
-#pragma unroll 1
-        for (int u = threadIdx.x; u < nU; u += 32) {
-            kept += sh.inS[u] && sh.inSp[u];
-            const double d = (sh.inSp[u] ? sh.uw[u] : 0.0) - sh.ubeta[u];
-            dd += d * d;
-            bb += sh.ubeta[u] * sh.ubeta[u];
+    {
+        const int wq = threadIdx.x >> 5;
+        const bool split = blockDim.x >= 96;
+        const bool do_dd = wq == 0, do_bb = split ? wq == 1 : wq == 0, do_kept = split ? wq == 2 : wq == 0;
+        if (do_dd || do_bb || do_kept) {
+#pragma unroll 2
+            for (int u = threadIdx.x & 31; u < nU; u += 32) {
+                if (do_kept) kept += sh.inS[u] && sh.inSp[u];
+                if (do_dd) {
+                    const double d = (sh.inSp[u] ? sh.uw[u] : 0.0) - sh.ubeta[u];
+                    dd += d * d;
+                }
+                if (do_bb) bb += sh.ubeta[u] * sh.ubeta[u];
+            }
+            if (do_kept) kept = __reduce_add_sync(0xffffffffu, kept);
+            if (do_dd) dd = warp_sum(dd);
+            if (do_bb) bb = warp_sum(bb);
+            if (split && (threadIdx.x == 32)) sh.red[0] = bb;
+            if (split && (threadIdx.x == 64)) sh.red[1] = (double)kept;
         }
-        kept = __reduce_add_sync(0xffffffffu, kept);
-        dd = warp_sum(dd);
-        bb = warp_sum(bb);
     }
 
     // S+ in index order with beta+
@@ -530,6 +557,10 @@ template <typename SH = MergeShared> __device__ __forceinline__ void merge_body(
             A.bSp[pos] = sh.uw[u];
         }
         if (threadIdx.x == 0) {
+            if (blockDim.x >= 96) {
+                bb = sh.red[0];
+                kept = (int)sh.red[1];
+            }
             sc->changed = kept < k ? 1 : 0;
             sc->dd = dd;
             sc->bb = bb;
@@ -572,6 +603,10 @@ template <typename SH = MergeShared> __device__ __forceinline__ void merge_body(
         A.bSp[r] = sh.uw[u];
     }
     if (threadIdx.x == 0) {
+        if (blockDim.x >= 96) {
+            bb = sh.red[0];
+            kept = (int)sh.red[1];
+        }
         sc->changed = kept < k ? 1 : 0;
         sc->dd = dd;
         sc->bb = bb;

@@ -68,6 +68,31 @@ __device__ __forceinline__ void sel_find(const uint32_t *h, int nbins, uint32_t 
     __syncthreads();
 }
 
+// sel_find over a histogram of kPer * blockDim.x bins held in registers:
+// thread t holds bins nbins - 1 - (kPer t + i) in c[i], i = 0 .. kPer-1 --
+// the same scan in the same order, so the same result.
+template <int kPer>
+__device__ __forceinline__ void sel_find_regs(const uint32_t (&c)[kPer], uint32_t need, uint32_t *wsum,
+                                              uint32_t *res)
+{
+    const int t = threadIdx.x, nbins = kPer * (int)blockDim.x;
+    if (t == 0) res[0] = res[1] = res[2] = 0;
+    uint32_t tot = 0;
+#pragma unroll
+    for (int i = 0; i < kPer; ++i) tot += c[i];
+    uint32_t before = sel_excl_scan(tot, wsum);
+#pragma unroll
+    for (int i = 0; i < kPer; ++i) {
+        if (before < need && before + c[i] >= need) {
+            res[0] = (uint32_t)(nbins - 1 - (kPer * t + i));
+            res[1] = before;
+            res[2] = c[i];
+        }
+        before += c[i];
+    }
+    __syncthreads();
+}
+
 // Calls f(key, index) for every key; 16-byte loads, two in flight per thread,
 // over the 16-byte aligned middle, the (at most 3 + 3) keys around it one at a
 // time.

@@ -37,7 +37,7 @@ struct TailWork {                     // zeroed before every solve
     double num;                       // ||g_S||^2, from the blocks that form Z_S g_S
     Scalars spec;                     // the second candidate's projection scalars (mu / kappa)
     SelState st;                      // selection state (boundary bin, candidate count)
-    uint32_t hist[kSelBins];          // histogram of |g| bits 30..20
+    alignas(16) uint32_t hist[kSelBins];   // histogram of |g| bits 30..20
     unsigned long long cand[kSelCap]; // candidate words (key << 32 | ~index)
 };
 
@@ -150,6 +150,28 @@ __global__ void __launch_bounds__(kTailThreads) k_tail(const __grid_constant__ T
 
     __shared__ Scalars ssc;               // the block's working copy of the scalars (block 0's is the solve's)
     grid_dep_launch();   // the missing-call sums may launch now; they wait for this grid before reading
+
+    // Z_S g_S for the step size, in B: on the nden blocks no candidate needs
+    // (which then leave the candidate scan to the others), or, when every
+    // block forms a candidate's residual, on the last blocks besides their scan
+    const int nfree = (int)gridDim.x - 2 * A.npart;
+    const int nden = nfree > 0 ? min(nfree, A.npart) : 0;
+    const bool den_block = nden > 0 && (int)blockIdx.x >= 2 * A.npart && (int)blockIdx.x < 2 * A.npart + nden;
+
+    // the histogram of |g| for B in registers, thread t holding bins 2047 -
+    // (16 t + i) in hc[i]; requested first when the pass before this kernel
+    // counted it
+    static_assert(kTailThreads * 16 == kSelBins, "one 16-bin slice of the histogram per thread");
+    uint32_t hc[16];
+    auto load_hist = [&]() {
+        const uint4 *h4 = reinterpret_cast<const uint4 *>(T->hist + kSelBins - 16 * (tid + 1));
+        const uint4 q0 = __ldcg(h4), q1 = __ldcg(h4 + 1), q2 = __ldcg(h4 + 2), q3 = __ldcg(h4 + 3);
+        const uint32_t w[16] = {q0.x, q0.y, q0.z, q0.w, q1.x, q1.y, q1.z, q1.w,
+                                q2.x, q2.y, q2.z, q2.w, q3.x, q3.y, q3.z, q3.w};
+#pragma unroll
+        for (int i = 0; i < 16; ++i) hc[i] = w[15 - i];
+    };
+    if (!A.own_hist && !den_block) load_hist();
     if (tid == 0) s_state = *(volatile int32_t *)&sc->done;
     if (tid < kScWords)
         reinterpret_cast<unsigned long long *>(&ssc)[tid] =
@@ -193,23 +215,14 @@ __global__ void __launch_bounds__(kTailThreads) k_tail(const __grid_constant__ T
                   A.zv, A.partials, A.n_pad, A.p, A.zc, vb);
     };
 
-    // Z_S g_S for the step size, in B: on the nden blocks no candidate needs
-    // (which then leave the candidate scan to the others), or, when every
-    // block forms a candidate's residual, on the last blocks besides their scan
-    const int nfree = (int)gridDim.x - 2 * A.npart;
-    const int nden = nfree > 0 ? min(nfree, A.npart) : 0;
-    const bool den_block = nden > 0 && (int)blockIdx.x >= 2 * A.npart && (int)blockIdx.x < 2 * A.npart + nden;
-
     // B: the boundary bin (every scanning block, from the whole histogram) and
     // the keys in or above it as candidate words
     if (den_block) {
 #pragma unroll 1
         for (int vb = (int)blockIdx.x - 2 * A.npart; vb < A.npart; vb += nden) zsgs(vb);
     } else {
-        uint32_t *hs = reinterpret_cast<uint32_t *>(smem_raw);
-        for (int b = tid; b < kSelBins; b += blockDim.x) hs[b] = __ldcg(&T->hist[b]);
-        __syncthreads();
-        sel_find(hs, kSelBins, (uint32_t)A.K, wsum, res);
+        if (A.own_hist) load_hist();
+        sel_find_regs<16>(hc, (uint32_t)A.K, wsum, res);
         const uint32_t lo = res[0] << 20, ncand = res[1] + res[2];
         const int sb = (int)blockIdx.x < 2 * A.npart ? (int)blockIdx.x : (int)blockIdx.x - nden;
         if (ncand <= (uint32_t)kSelCap)
@@ -248,6 +261,7 @@ __global__ void __launch_bounds__(kTailThreads) k_tail(const __grid_constant__ T
     __shared__ int32_t s_cand[2 * kTailKM];
     __shared__ int32_t s_S[kTailKM];
     __shared__ double s_bS[kTailKM];
+    __shared__ float s_gS[kTailKM];
     __shared__ int32_t s_Sp[2][kTailKM];
     __shared__ double s_bSp[2][kTailKM];
     __shared__ Scalars ssc2;              // the second candidate's scalars
@@ -263,7 +277,7 @@ __global__ void __launch_bounds__(kTailThreads) k_tail(const __grid_constant__ T
                 reinterpret_cast<unsigned long long *>(&ssc)[tid] =
                     reinterpret_cast<const volatile unsigned long long *>(sc)[tid];
             const uint32_t ncand = res[1] + res[2];
-            // S and beta_S into shared memory for the projection, and the
+            // S, beta_S and g_S into shared memory for the projection, and the
             // genotype bytes of this block's residual on their way to L2, while
             // the candidates are chosen (S+ mostly repeats S)
             {
@@ -274,6 +288,7 @@ __global__ void __launch_bounds__(kTailThreads) k_tail(const __grid_constant__ T
                     const int32_t j = A.S[c];
                     s_S[c] = j;
                     s_bS[c] = A.bS[c];
+                    s_gS[c] = A.g[j];
                     if (j < A.p) asm volatile("prefetch.global.L2 [%0];" ::"l"(gb + (int64_t)j * A.stride));
                 }
             }
@@ -303,6 +318,7 @@ __global__ void __launch_bounds__(kTailThreads) k_tail(const __grid_constant__ T
                 M.Sp = s_Sp[c];
                 M.bSp = s_bSp[c];
                 M.sc = c ? &ssc2 : &ssc;
+                M.gS = s_gS;
                 merge_body<MergeSharedT<kTailKM>>(M);
                 __syncthreads();
                 const Scalars &ms = c ? ssc2 : ssc;
