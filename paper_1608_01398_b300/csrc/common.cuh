@@ -518,6 +518,19 @@ __device__ __forceinline__ float standardise(float S1, float R, float M, float u
 // block, lanes strided over S then a shuffle tree, so the sum's order does not
 // depend on the block size (the single-solve selection's last block and the
 // batched kernel give the same bits).
+// ||g_S||^2 from g_S by one warp: lane l adds its squares c = l, l + 32, ...
+// in order with fused multiply-adds, then an xor shuffle tree (every caller
+// forms it this way, so every path has the same bits).
+__device__ __forceinline__ double gS_sumsq_warp(const double *coef, int k)
+{
+    double s = 0.0;
+#pragma unroll 2
+    for (int c = threadIdx.x & 31; c < k; c += 32) s = __fma_rn(coef[c], coef[c], s);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    return s;
+}
+
 __device__ __forceinline__ void gather_gS_body(const float *__restrict__ g,
                                                const int32_t *__restrict__ S, int k,
                                                double *__restrict__ coef, Scalars *sc)
@@ -528,7 +541,7 @@ __device__ __forceinline__ void gather_gS_body(const float *__restrict__ g,
     for (int c = threadIdx.x; c < k; c += 32) {
         const double x = (double)g[S[c]];
         coef[c] = x;
-        s += x * x;
+        s = __fma_rn(x, x, s);
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);

@@ -172,6 +172,12 @@ __global__ void __launch_bounds__(kTailThreads) k_tail(const __grid_constant__ T
         for (int i = 0; i < 16; ++i) hc[i] = w[15 - i];
     };
     if (!A.own_hist && !den_block) load_hist();
+    // S for Z_S g_S, requested first on the blocks that form it (the barrier
+    // after the scalars' copy makes it visible)
+    __shared__ int32_t s_Sd[kTailKM];
+    if (den_block)
+#pragma unroll 1
+        for (int c = tid; c < A.k; c += blockDim.x) s_Sd[c] = A.S[c];
     if (tid == 0) s_state = *(volatile int32_t *)&sc->done;
     if (tid < kScWords)
         reinterpret_cast<unsigned long long *>(&ssc)[tid] =
@@ -205,13 +211,24 @@ __global__ void __launch_bounds__(kTailThreads) k_tail(const __grid_constant__ T
 
     // g_S (in shared memory) for the blocks that form Z_S g_S; the one that
     // forms sample block 0 publishes ||g_S||^2 in T->num before it is counted
+    // g_S (and, for sample block 0, ||g_S||^2 to T->num) and this block's
+    // samples of Z_S g_S; S in s_Sd (staged by the caller), the genotype bytes
+    // of the columns requested into L2 together with g_S
     __shared__ double s_coef[kTailKM];
-    __shared__ Scalars s_g;               // (only its num is used)
     auto zsgs = [&](int vb) {
-        gather_gS_body(A.g, A.S, A.k, s_coef, &s_g);
+        const uint8_t *gb = A.G + (int64_t)vb * kZmulBytes;
+#pragma unroll 1
+        for (int c = tid; c < A.k; c += blockDim.x) {
+            const int32_t j = s_Sd[c];
+            s_coef[c] = (double)A.g[j];
+            if (j < A.p) asm volatile("prefetch.global.L2 [%0];" ::"l"(gb + (int64_t)j * A.stride));
+        }
         __syncthreads();
-        if (vb == 0 && tid == 0) T->num = s_g.num;
-        zmul_body(A.G, A.stride, A.rowb, A.S, A.k, s_coef, 1.0, A.u64, A.v64, A.used, nullptr, nullptr,
+        if (vb == 0 && tid < 32) {
+            const double s = gS_sumsq_warp(s_coef, A.k);
+            if (tid == 0) T->num = s;
+        }
+        zmul_body(A.G, A.stride, A.rowb, s_Sd, A.k, s_coef, 1.0, A.u64, A.v64, A.used, nullptr, nullptr,
                   A.zv, A.partials, A.n_pad, A.p, A.zc, vb);
     };
 
@@ -241,7 +258,10 @@ __global__ void __launch_bounds__(kTailThreads) k_tail(const __grid_constant__ T
             T->st.need = (uint32_t)A.K - res[1];
             T->st.ncand = ncand;
         }
-        if (nden == 0) {
+        if (nden == 0 && (int)gridDim.x - 1 - (int)blockIdx.x < A.npart) {
+#pragma unroll 1
+            for (int c = tid; c < A.k; c += blockDim.x) s_Sd[c] = A.S[c];
+            __syncthreads();
 #pragma unroll 1
             for (int vb = (int)gridDim.x - 1 - (int)blockIdx.x; vb < A.npart; vb += gridDim.x) zsgs(vb);
         }
