@@ -227,46 +227,58 @@ constexpr int kSelRank = 512;
 // The K largest of n <= kSelRank distinct words w (shared memory; key << 32 |
 // ~index, so larger key first and lower index first among equal keys), their
 // indices written to out in ascending index order: a word is among the K iff
-// fewer than K words are larger, and its place is the number of chosen words
-// with a lower index.  Two sweeps over w per pair of words a thread ranks
-// (every thread reads the same word at the same time: a broadcast), instead of
-// the bitonic networks' two dozen block barriers each.
+// fewer than K words are larger.  One sweep over w ranks up to four words per
+// thread (every thread reads the same word at the same time: a broadcast);
+// the chosen indices are then compacted, and each one's place is the number
+// of chosen indices below it -- a sweep over the K chosen, not over all n.
 __device__ __forceinline__ void sel_rank_finish(const unsigned long long *w, int n, int32_t *out,
                                                 uint32_t K)
 {
     __shared__ uint8_t s_sel[kSelRank];
+    __shared__ uint32_t s_ix[kSelRank];
+    __shared__ uint32_t s_ws[32];
+    const int bd = (int)blockDim.x;
 #pragma unroll 1
-    for (int ub = 0; ub < n; ub += 2 * (int)blockDim.x) {
-        const int ua = ub + threadIdx.x, uc = ua + blockDim.x;
-        if (ua >= n) continue;                   // (a large block: most threads have none)
-        const unsigned long long wa = w[ua], wc = w[min(uc, n - 1)];
-        uint32_t ra = 0, rc = 0;
+    for (int ub = 0; ub < n; ub += 4 * bd) {
+        const int e0 = ub + (int)threadIdx.x;
+        if (e0 >= n) continue;                   // (a large block: most threads have none)
+        unsigned long long we[4];
+        uint32_t r[4] = {0u, 0u, 0u, 0u};
+#pragma unroll
+        for (int q = 0; q < 4; ++q) we[q] = w[min(e0 + q * bd, n - 1)];
 #pragma unroll 4
         for (int v = 0; v < n; ++v) {
             const unsigned long long wv = w[v];
-            ra += wv > wa ? 1u : 0u;
-            rc += wv > wc ? 1u : 0u;
+#pragma unroll
+            for (int q = 0; q < 4; ++q) r[q] += wv > we[q] ? 1u : 0u;
         }
-        if (ua < n) s_sel[ua] = ra < K ? 1 : 0;
-        if (uc < n) s_sel[uc] = rc < K ? 1 : 0;
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+            if (e0 + q * bd < n) s_sel[e0 + q * bd] = r[q] < K ? 1 : 0;
+    }
+    __syncthreads();
+    // the chosen indices, compacted in word order (thread t: words per t ..)
+    const int per = (n + bd - 1) / bd;
+    uint32_t c = 0, m = 0;
+#pragma unroll 1
+    for (int q = 0; q < per; ++q) {
+        const int e = per * (int)threadIdx.x + q;
+        if (e < n) c += s_sel[e];
+    }
+    uint32_t o = sel_excl_scan(c, s_ws, &m);
+#pragma unroll 1
+    for (int q = 0; q < per; ++q) {
+        const int e = per * (int)threadIdx.x + q;
+        if (e < n && s_sel[e]) s_ix[o++] = ~(uint32_t)(w[e] & 0xffffffffull);
     }
     __syncthreads();
 #pragma unroll 1
-    for (int ub = 0; ub < n; ub += 2 * (int)blockDim.x) {
-        const int ua = ub + threadIdx.x, uc = ua + blockDim.x;
-        if (ua >= n) continue;
-        const uint32_t ia = ~(uint32_t)(w[ua] & 0xffffffffull);
-        const uint32_t ic = ~(uint32_t)(w[min(uc, n - 1)] & 0xffffffffull);
-        uint32_t pa = 0, pc = 0;
+    for (int t = threadIdx.x; t < (int)m; t += bd) {
+        const uint32_t ia = s_ix[t];
+        uint32_t pa = 0;
 #pragma unroll 4
-        for (int v = 0; v < n; ++v) {
-            const uint32_t sv = s_sel[v];
-            const uint32_t iv = ~(uint32_t)(w[v] & 0xffffffffull);
-            pa += sv & (iv < ia ? 1u : 0u);
-            pc += sv & (iv < ic ? 1u : 0u);
-        }
-        if (ua < n && s_sel[ua]) out[pa] = (int32_t)ia;
-        if (uc < n && s_sel[uc]) out[pc] = (int32_t)ic;
+        for (int v = 0; v < (int)m; ++v) pa += s_ix[v] < ia ? 1u : 0u;
+        out[pa] = (int32_t)ia;
     }
     __syncthreads();
 }
