@@ -224,11 +224,41 @@ __device__ __forceinline__ void sort_idx_body(int32_t *idx, int K)
 // Up to this many candidate words the finish ranks them instead of sorting.
 constexpr int kSelRank = 512;
 
+// s_sel[e] = 1 iff fewer than K words of w are larger than w[e]: Q words per
+// thread in one sweep over w.
+template <int Q>
+__device__ __forceinline__ void sel_rank_sweep(const unsigned long long *w, int n, uint32_t K, uint8_t *s_sel)
+{
+    const int bd = (int)blockDim.x;
+#pragma unroll 1
+    for (int ub = 0; ub < n; ub += Q * bd) {
+        const int e0 = ub + (int)threadIdx.x;
+        if (e0 >= n) continue;                   // (a large block: most threads have none)
+        unsigned long long we[Q];
+        uint32_t r[Q];
+#pragma unroll
+        for (int q = 0; q < Q; ++q) {
+            we[q] = w[min(e0 + q * bd, n - 1)];
+            r[q] = 0u;
+        }
+#pragma unroll 4
+        for (int v = 0; v < n; ++v) {
+            const unsigned long long wv = w[v];
+#pragma unroll
+            for (int q = 0; q < Q; ++q) r[q] += wv > we[q] ? 1u : 0u;
+        }
+#pragma unroll
+        for (int q = 0; q < Q; ++q)
+            if (e0 + q * bd < n) s_sel[e0 + q * bd] = r[q] < K ? 1 : 0;
+    }
+}
+
 // The K largest of n <= kSelRank distinct words w (shared memory; key << 32 |
 // ~index, so larger key first and lower index first among equal keys), their
 // indices written to out in ascending index order: a word is among the K iff
-// fewer than K words are larger.  One sweep over w ranks up to four words per
-// thread (every thread reads the same word at the same time: a broadcast);
+// fewer than K words are larger.  One sweep over w ranks two words per thread,
+// or four when there are more than two per thread (every thread reads the
+// same word at the same time: a broadcast);
 // the chosen indices are then compacted, and each one's place is the number
 // of chosen indices below it -- a sweep over the K chosen, not over all n.
 __device__ __forceinline__ void sel_rank_finish(const unsigned long long *w, int n, int32_t *out,
@@ -238,24 +268,10 @@ __device__ __forceinline__ void sel_rank_finish(const unsigned long long *w, int
     __shared__ uint32_t s_ix[kSelRank];
     __shared__ uint32_t s_ws[32];
     const int bd = (int)blockDim.x;
-#pragma unroll 1
-    for (int ub = 0; ub < n; ub += 4 * bd) {
-        const int e0 = ub + (int)threadIdx.x;
-        if (e0 >= n) continue;                   // (a large block: most threads have none)
-        unsigned long long we[4];
-        uint32_t r[4] = {0u, 0u, 0u, 0u};
-#pragma unroll
-        for (int q = 0; q < 4; ++q) we[q] = w[min(e0 + q * bd, n - 1)];
-#pragma unroll 4
-        for (int v = 0; v < n; ++v) {
-            const unsigned long long wv = w[v];
-#pragma unroll
-            for (int q = 0; q < 4; ++q) r[q] += wv > we[q] ? 1u : 0u;
-        }
-#pragma unroll
-        for (int q = 0; q < 4; ++q)
-            if (e0 + q * bd < n) s_sel[e0 + q * bd] = r[q] < K ? 1 : 0;
-    }
+    if (n <= 2 * bd)
+        sel_rank_sweep<2>(w, n, K, s_sel);
+    else
+        sel_rank_sweep<4>(w, n, K, s_sel);
     __syncthreads();
     // the chosen indices, compacted in word order (thread t: words per t ..)
     const int per = (n + bd - 1) / bd;
