@@ -120,6 +120,20 @@ def measured_peaks():
         return FALLBACK_HBM_GBS, "fallback"
 
 
+def warm_up(step, warmup: int, min_s: float = 0.5) -> int:
+    """Untimed warm-up steps right before a timed region: at least `warmup` of
+    them, continued until `min_s` seconds of steps have run.  The clock sampler
+    starts just before, and a GPU that has idled runs its first few hundred
+    milliseconds of work measurably slower (up to 8 % on the single-solve
+    workload), so the timed steps start on a GPU already under load.  Returns
+    the number of steps run (reported as warmup_steps_run)."""
+    n, t0 = 0, time.perf_counter()
+    while n < max(warmup, 0) or time.perf_counter() - t0 < min_s:
+        step()
+        n += 1
+    return n
+
+
 class ClockSampler:
     """nvidia-smi clocks / throttle reasons sampled every 200 ms during the timed region."""
     FIELDS = ("uuid,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
@@ -281,13 +295,9 @@ def ours_arm(args):
         if world > 1:
             torch.distributed.barrier()
 
-    # the clock sampler starts first; the warm-up steps then run after its
-    # start-up pause, so the timed steps do not begin on a GPU that idled
     clocks = ClockSampler(gpu_uuid(torch, dev))
     clocks.start()
-    time.sleep(0.3)
-    for _ in range(max(args.warmup, 0)):
-        iht.iht_fit(ds, y_dev, k, **fit_kw)
+    warm_steps = warm_up(lambda: iht.iht_fit(ds, y_dev, k, **fit_kw), args.warmup)
     torch.cuda.synchronize(dev)
 
     # ---- device-timed region: inputs resident in HBM -------------------------
@@ -355,7 +365,8 @@ def ours_arm(args):
         ctl = 4 + 2 * 120 + 4 * iters_mean                   # status words and done flags
         out = {
             "metric": "IHT iterations/sec", "value": value, "unit": "iter/s", "n_gpus": world,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * max_el / args.steps,
+            "steps": args.steps, "warmup": args.warmup, "warmup_steps_run": warm_steps,
+            "ms_per_step": 1e3 * max_el / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "paper_context": PAPER_CONTEXT,
             "dtype": "f32",
             "data": "synthetic",
@@ -537,9 +548,7 @@ def cv_arm(args):
 
     clocks = ClockSampler(gpu_uuid(torch, dev))
     clocks.start()
-    time.sleep(0.3)
-    for _ in range(max(args.warmup, 0)):                       # after the sampler's start-up pause
-        iht.iht_fit_batch(ds, probs, **kw)
+    warm_steps = warm_up(lambda: iht.iht_fit_batch(ds, probs, **kw), args.warmup)
     torch.cuda.synchronize(dev)
     barrier()
     torch.cuda.synchronize(dev)
@@ -613,7 +622,7 @@ def cv_arm(args):
         h2d = sum(8 * t.size * len(c["ks"]) + 4 * t.size for t in train)   # y per solve, rows per fold
         out = {
             "metric": "batched IHT solves/sec", "value": value, "unit": "solves/s",
-            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "warmup_steps_run": warm_steps,
             "ms_per_step": 1e3 * float(allv[:, 1].max()) / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "paper_context": PAPER_CONTEXT,
             "dtype": "e4m3 operands (exact dosage, residual in 5 limbs), f32 accumulate, f64 scalars",
@@ -692,9 +701,7 @@ def panel_arm(args):
     kw = dict(out_device=True, dense=False, grad_impl=args.grad_impl, tol=c["tol"], max_iter=c["max_iter"])
     clocks = ClockSampler(gpu_uuid(torch, dev))
     clocks.start()
-    time.sleep(0.3)
-    for _ in range(max(args.warmup, 0)):                       # after the sampler's start-up pause
-        iht.iht_fit_batch(ds, probs, **kw)
+    warm_steps = warm_up(lambda: iht.iht_fit_batch(ds, probs, **kw), args.warmup)
     torch.cuda.synchronize(dev)
     if world > 1:
         torch.distributed.barrier()
@@ -747,7 +754,7 @@ def panel_arm(args):
         achieved = 2.0 * n * p * MR_LIMBS * cols / (grad_ms / 1e3) / 1e12 if grad_ms > 0 else None
         out = {
             "metric": "batched IHT solves/sec", "value": value, "unit": "solves/s",
-            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "warmup_steps_run": warm_steps,
             "ms_per_step": 1e3 * float(allv[:, 1].max()) / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "paper_context": PAPER_CONTEXT,
             "dtype": "e4m3 operands (exact dosage, residual in 5 limbs), f32 accumulate, f64 scalars",
@@ -907,8 +914,8 @@ def serve_arm(args):
     srv = iht.Server(ds, max_slots=args.slots, hbm_budget=int(args.hbm_gb * 2**30), **solve)
     clocks = ClockSampler(gpu_uuid(torch, dev))
     clocks.start()
-    time.sleep(0.3)
-    _serve_run(iht, srv, reqs[:min(len(reqs), 2 * args.slots)], np.zeros(len(reqs)))   # warm-up
+    warm_steps = warm_up(lambda: _serve_run(iht, srv, reqs[:min(len(reqs), 2 * args.slots)],
+                                            np.zeros(len(reqs))), 1)
     if world > 1:
         torch.distributed.barrier()
     l0 = iht.iht_kernel_launches()
@@ -946,7 +953,7 @@ def serve_arm(args):
         d2h = sum(12 * q["k"] + 48 for q in reqs)
         out = {
             "metric": "served IHT solves/sec", "value": value, "unit": "solves/s", "n_gpus": world,
-            "steps": args.steps, "warmup": args.warmup,
+            "steps": args.steps, "warmup": args.warmup, "warmup_steps_run": warm_steps,
             "ms_per_step": 1e3 * sum(cap_walls) / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "paper_context": PAPER_CONTEXT,
             "dtype": "e4m3 operands (exact dosage, residual in 5 limbs), f32 accumulate, f64 scalars",
@@ -1028,9 +1035,9 @@ def sim_arm(args):
     kw = dict(tol=c["tol"], max_iter=c["max_iter"], grad_impl=args.grad_impl)
     clocks = ClockSampler(gpu_uuid(torch, dev))
     clocks.start()
-    time.sleep(0.3)
-    for _ in range(max(args.warmup, 0)):                       # tuning, graphs, allocations
-        iht.iht_cv(ds, jobs[0][3], lab, synth.sim_path(jobs[0][1], c["path"], c["path_step"]), **kw)
+    warm_steps = warm_up(lambda: iht.iht_cv(ds, jobs[0][3], lab, synth.sim_path(jobs[0][1], c["path"],
+                                                                                c["path_step"]), **kw),
+                         args.warmup)                         # tuning, graphs, allocations
     torch.cuda.synchronize(dev)
     if world > 1:
         torch.distributed.barrier()
@@ -1064,7 +1071,7 @@ def sim_arm(args):
         value = weak_rate(allv, 0, 1)
         out = {
             "metric": "simulation replicates/sec", "value": value, "unit": "replicates/s",
-            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "warmup_steps_run": warm_steps,
             "ms_per_step": 1e3 * float(allv[:, 1].max()) / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "paper_context": PAPER_CONTEXT,
             "dtype": "e4m3 operands (exact dosage, residual in 5 limbs), f32 accumulate, f64 scalars",
