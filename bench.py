@@ -336,8 +336,8 @@ def ours_arm(args):
     y_pin = torch.empty(n, dtype=torch.float64).pin_memory()
     y_pin.numpy()[:] = y
     y_host = y_pin.numpy()
-    for _ in range(max(args.warmup, 0)):                       # untimed, as for the device-timed steps
-        iht.iht_fit(ds, y_host, k, grad_impl=args.grad_impl, tol=c["tol"], max_iter=c["max_iter"])
+    warm_up(lambda: iht.iht_fit(ds, y_host, k, grad_impl=args.grad_impl, tol=c["tol"], max_iter=c["max_iter"]),
+            args.warmup)                                     # untimed, as for the device-timed steps
     barrier()
     torch.cuda.synchronize(dev)
     w0 = time.perf_counter()
