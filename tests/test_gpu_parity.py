@@ -85,6 +85,27 @@ def test_gradient_parity(iht, ctx, impl, n, p):
         assert rel_err(g, go) <= GTOL
 
 
+@pytest.mark.parametrize("n", [40500, 41000])
+def test_gradient_long_residual_paths(iht, ctx, n):
+    """Sample counts past the interleaved missing-call lists: n_pad = 40 960 sums
+    over the plain lists with r in shared memory, n = 41 000 over the global-
+    memory kernel (r too long for shared memory); gradient and a short solve
+    against the oracle."""
+    torch = _torch()
+    rng = np.random.default_rng(n)
+    G, codes = random_geno(rng, n, 40, miss=0.02)
+    ds = load(iht, ctx, G)
+    r = rng.normal(size=n).astype(np.float32)
+    g = iht.iht_gradient(ds, torch.from_numpy(r).cuda()).cpu().numpy()
+    assert rel_err(g, oracle.gradient(G, r.astype(np.float64))) <= GTOL
+    Z = np_Z(codes)
+    y = Z[:, [3, 17, 29]] @ np.array([0.4, -0.3, 0.5]) + rng.normal(size=n)
+    fg = iht.iht_fit(ds, y, 3)
+    fo = oracle.iht(G, y, 3, trace=False)
+    assert np.array_equal(np.asarray(fg.support), np.asarray(fo.support))
+    assert fg.status == fo.status
+
+
 def test_gradient_uncentred_residual(iht, ctx):
     """A residual with a large mean: the R and M terms still cancel correctly."""
     torch = _torch()
