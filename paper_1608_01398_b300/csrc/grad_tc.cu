@@ -142,6 +142,40 @@ __device__ __forceinline__ void mbar_arrive(uint64_t *bar)
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
 }
 
+// The decoders' waits, on barriers that have almost always passed by then:
+// one poll in line, the bounded loop out of line (shared-space addresses).
+__device__ __noinline__ bool mbar_wait_slow(uint32_t a, uint32_t parity)
+{
+    for (uint32_t it = 0; it < kTcSpin; ++it) {
+        uint32_t ok;
+        asm volatile(
+            "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n"
+            "selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(ok)
+            : "r"(a), "r"(parity), "n"(128)
+            : "memory");
+        if (ok) return true;
+    }
+    return false;
+}
+
+__device__ __forceinline__ bool mbar_wait_fast(uint32_t a, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n"
+        "selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(a), "r"(parity), "n"(128)
+        : "memory");
+    return ok ? true : mbar_wait_slow(a, parity);
+}
+
+__device__ __forceinline__ void mbar_arrive_at(uint32_t a)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(a) : "memory");
+}
+
 __device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes)
 {
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)),
@@ -385,65 +419,81 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_grad_tc(const __grid_constant
         const uint32_t tb = tmem_base + (uint32_t)(w * 128);
         const uint32_t lane_off = (uint32_t)((warp & 3) * 32) << 16;
         const float s0 = prm->s0, R = prm->R;
-        uint32_t grp = 0;                       // A-buffer groups written
         uint32_t slot = 0, sphase = 0;          // TMA stage ring (slot, phase bit)
         uint32_t buf = 0, bphase = 0;           // A-buffer ring
         int T = 0;
         bool ok = true;
         bool nan = false;                       // a non-finite g among this thread's rows
-        const int cps = kTcStageBytes / kTcGroupBytes;                 // chunks per stage (4)
         // swizzled offsets of the stage's four 16-byte chunks in this thread's row
         const int swz = (r >> 1) & 3;
         const uint32_t off0 = (uint32_t)((0 ^ swz) << 4), off1 = (uint32_t)((1 ^ swz) << 4);
         const uint32_t off2 = (uint32_t)((2 ^ swz) << 4), off3 = (uint32_t)((3 ^ swz) << 4);
         const uint32_t abase = tb + 32 + lane_off;
+        // this row of slot 0, and the barriers' shared-space addresses (slot
+        // or buffer b at + 8 b), set once
+        const uint8_t *row0 = stages + (size_t)w * nst * kTcStageTile + (size_t)r * kTcStageBytes;
+        const uint8_t *sp = row0;
+        const uint32_t tfull0 = smem_addr(&P.tma_full[0]), tempty0 = smem_addr(&P.tma_empty[0]);
+        const uint32_t afull0 = smem_addr(&P.full[0]), aempty0 = smem_addr(&P.empty[0]);
+        // one A group (two chunks) into buffer buf
+        auto put = [&](uint4 x0, uint4 x1) -> bool {
+            // (a fresh barrier passes the wait on parity 1: the first round is free)
+            if (!mbar_wait_fast(aempty0 + 8u * buf, bphase ^ 1u)) return false;
+            tc_fence_after();
+            tc_put_group(abase + 32u * buf, x0, x1);
+            asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+            tc_fence_before();
+            mbar_arrive_at(afull0 + 8u * buf);
+            if (++buf == kTcBufs) {
+                buf = 0;
+                bphase ^= 1u;
+            }
+            return true;
+        };
         for (int64_t tile = (int64_t)blockIdx.x * kTcNWG + w; tile < ntiles && ok; tile += tile_step, ++T) {
             const int64_t row = tile * 128 + r;
-            for (int st = 0; st < spt && ok; ++st) {
-                if (!mbar_wait(&P.tma_full[slot], sphase)) {
-                    abort_flag = 1;
+#pragma unroll 1
+            for (int st = 0; st < spt; ++st) {
+                if (!mbar_wait_fast(tfull0 + 8u * slot, sphase)) {
                     ok = false;
+                    break;
                 }
-                const uint8_t *base = stages + (w * nst + slot) * kTcStageTile + r * kTcStageBytes;
-                const int nchunks = min(cps, ngroups - st * cps);
+                const int nchunks = ngroups - 4 * st;    // chunks of this stage: 4 but at the row's end
                 // the row's chunks of this stage into registers, and the stage
                 // handed back to the producer before they are decoded
-                const uint4 zero = make_uint4(0u, 0u, 0u, 0u);
                 uint4 xc[4];
-                xc[0] = *reinterpret_cast<const uint4 *>(base + off0);
-                xc[1] = nchunks > 1 ? *reinterpret_cast<const uint4 *>(base + off1) : zero;
-                xc[2] = nchunks > 2 ? *reinterpret_cast<const uint4 *>(base + off2) : zero;
-                xc[3] = nchunks > 3 ? *reinterpret_cast<const uint4 *>(base + off3) : zero;
-                mbar_arrive(&P.tma_empty[slot]);
+                if (nchunks >= 4) {
+                    xc[0] = *reinterpret_cast<const uint4 *>(sp + off0);
+                    xc[1] = *reinterpret_cast<const uint4 *>(sp + off1);
+                    xc[2] = *reinterpret_cast<const uint4 *>(sp + off2);
+                    xc[3] = *reinterpret_cast<const uint4 *>(sp + off3);
+                } else {
+                    const uint4 zero = make_uint4(0u, 0u, 0u, 0u);
+                    xc[0] = *reinterpret_cast<const uint4 *>(sp + off0);
+                    xc[1] = nchunks > 1 ? *reinterpret_cast<const uint4 *>(sp + off1) : zero;
+                    xc[2] = nchunks > 2 ? *reinterpret_cast<const uint4 *>(sp + off2) : zero;
+                    xc[3] = zero;
+                }
+                mbar_arrive_at(tempty0 + 8u * slot);
+                sp += kTcStageTile;
                 if (++slot == (uint32_t)nst) {
                     slot = 0;
                     sphase ^= 1u;
+                    sp = row0;
                 }
-#pragma unroll
-                for (int c = 0; c < 4; c += 2) {                         // one A group per pair
-                    if (c >= nchunks || !ok) break;
-                    // (a fresh barrier passes the wait on parity 1: the first round is free)
-                    if (!mbar_wait(&P.empty[buf], bphase ^ 1u)) {
-                        abort_flag = 1;
-                        ok = false;
-                    }
-                    tc_fence_after();
-                    tc_put_group(abase + 32 * buf, xc[c], xc[c + 1]);
-                    asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
-                    tc_fence_before();
-                    mbar_arrive(&P.full[buf]);
-                    ++grp;
-                    if (++buf == kTcBufs) {
-                        buf = 0;
-                        bphase ^= 1u;
-                    }
+                if (!put(xc[0], xc[1]) || (nchunks > 2 && !put(xc[2], xc[3]))) {
+                    ok = false;
+                    break;
                 }
-                if (abort_flag) ok = false;
             }
-            if (ok)
-                ok &= tc_epilogue(P, tb, lane_off, T, row, p, s0, R, Mj, u32, v32, g, abort_flag,
-                                  hist ? s_hist : nullptr, nan);
+            if (!ok || abort_flag) {                     // this warp's wait gave up, or another's
+                ok = false;
+                break;
+            }
+            ok &= tc_epilogue(P, tb, lane_off, T, row, p, s0, R, Mj, u32, v32, g, abort_flag,
+                              hist ? s_hist : nullptr, nan);
         }
+        if (!ok) abort_flag = 1;
         if (nan && hflag) atomicOr(hflag, 1u);
     } else if (warp < kProducerWarp) {
         // ------------------------------------------------------------ MMA issuers
