@@ -450,42 +450,33 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_grad_tc(const __grid_constant
             }
             return true;
         };
+        // one TMA stage of nch chunks (4 but at the row's end): the row's chunks
+        // into registers, the stage handed back to the producer before they are
+        // decoded, then one A group per pair of chunks
+        auto stage = [&](int nch) -> bool {
+            if (!mbar_wait_fast(tfull0 + 8u * slot, sphase)) return false;
+            const uint4 zero = make_uint4(0u, 0u, 0u, 0u);
+            uint4 xc[4];
+            xc[0] = *reinterpret_cast<const uint4 *>(sp + off0);
+            xc[1] = nch > 1 ? *reinterpret_cast<const uint4 *>(sp + off1) : zero;
+            xc[2] = nch > 2 ? *reinterpret_cast<const uint4 *>(sp + off2) : zero;
+            xc[3] = nch > 3 ? *reinterpret_cast<const uint4 *>(sp + off3) : zero;
+            mbar_arrive_at(tempty0 + 8u * slot);
+            sp += kTcStageTile;
+            if (++slot == (uint32_t)nst) {
+                slot = 0;
+                sphase ^= 1u;
+                sp = row0;
+            }
+            if (!put(xc[0], xc[1])) return false;
+            return nch <= 2 || put(xc[2], xc[3]);
+        };
+        const int nfull = ngroups / 4, ntail = ngroups - 4 * nfull;   // stages of a row: full, then the rest
         for (int64_t tile = (int64_t)blockIdx.x * kTcNWG + w; tile < ntiles && ok; tile += tile_step, ++T) {
             const int64_t row = tile * 128 + r;
-#pragma unroll 1
-            for (int st = 0; st < spt; ++st) {
-                if (!mbar_wait_fast(tfull0 + 8u * slot, sphase)) {
-                    ok = false;
-                    break;
-                }
-                const int nchunks = ngroups - 4 * st;    // chunks of this stage: 4 but at the row's end
-                // the row's chunks of this stage into registers, and the stage
-                // handed back to the producer before they are decoded
-                uint4 xc[4];
-                if (nchunks >= 4) {
-                    xc[0] = *reinterpret_cast<const uint4 *>(sp + off0);
-                    xc[1] = *reinterpret_cast<const uint4 *>(sp + off1);
-                    xc[2] = *reinterpret_cast<const uint4 *>(sp + off2);
-                    xc[3] = *reinterpret_cast<const uint4 *>(sp + off3);
-                } else {
-                    const uint4 zero = make_uint4(0u, 0u, 0u, 0u);
-                    xc[0] = *reinterpret_cast<const uint4 *>(sp + off0);
-                    xc[1] = nchunks > 1 ? *reinterpret_cast<const uint4 *>(sp + off1) : zero;
-                    xc[2] = nchunks > 2 ? *reinterpret_cast<const uint4 *>(sp + off2) : zero;
-                    xc[3] = zero;
-                }
-                mbar_arrive_at(tempty0 + 8u * slot);
-                sp += kTcStageTile;
-                if (++slot == (uint32_t)nst) {
-                    slot = 0;
-                    sphase ^= 1u;
-                    sp = row0;
-                }
-                if (!put(xc[0], xc[1]) || (nchunks > 2 && !put(xc[2], xc[3]))) {
-                    ok = false;
-                    break;
-                }
-            }
+#pragma unroll 2
+            for (int st = 0; st < nfull && ok; ++st) ok = stage(4);
+            if (ok && ntail) ok = stage(ntail);
             if (!ok || abort_flag) {                     // this warp's wait gave up, or another's
                 ok = false;
                 break;
