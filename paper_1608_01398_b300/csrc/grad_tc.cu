@@ -279,32 +279,22 @@ struct TcPipe {
     uint64_t accempty;              // decoders -> MMA warp: accumulators read out (128)
 };
 
-__device__ __forceinline__ void tmem_st32(uint32_t taddr, const uint32_t (&v)[32])
-{
-    asm volatile(
-        "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,"
-        "%13,%14,%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31,%32};" ::"r"(taddr),
-        "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7]),
-        "r"(v[8]), "r"(v[9]), "r"(v[10]), "r"(v[11]), "r"(v[12]), "r"(v[13]), "r"(v[14]), "r"(v[15]),
-        "r"(v[16]), "r"(v[17]), "r"(v[18]), "r"(v[19]), "r"(v[20]), "r"(v[21]), "r"(v[22]), "r"(v[23]),
-        "r"(v[24]), "r"(v[25]), "r"(v[26]), "r"(v[27]), "r"(v[28]), "r"(v[29]), "r"(v[30]), "r"(v[31])
-        : "memory");
-}
-
 // One group of two 16-byte chunks (128 samples = 4 K-steps) of the row into A
-// buffer `buf` with one 32-column store (x1 is zero past the row's last chunk).
+// buffer `buf` with two 16-column stores, one per chunk (x1 is zero past the
+// row's last chunk).
 __device__ __forceinline__ void tc_put_group(uint32_t taddr, uint4 x0, uint4 x1)
 {
-    uint32_t v[32];
+    uint32_t v[16], u[16];
     decode_word(x0.x, &v[0]);
     decode_word(x0.y, &v[4]);
     decode_word(x0.z, &v[8]);
     decode_word(x0.w, &v[12]);
-    decode_word(x1.x, &v[16]);
-    decode_word(x1.y, &v[20]);
-    decode_word(x1.z, &v[24]);
-    decode_word(x1.w, &v[28]);
-    tmem_st32(taddr, v);
+    tmem_st16(taddr, v);                 // (the second chunk decodes while this store runs)
+    decode_word(x1.x, &u[0]);
+    decode_word(x1.y, &u[4]);
+    decode_word(x1.z, &u[8]);
+    decode_word(x1.w, &u[12]);
+    tmem_st16(taddr + 16, u);
 }
 
 // Read out the accumulator of local tile t and write g for this thread's row.
