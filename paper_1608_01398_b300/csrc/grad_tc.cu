@@ -400,6 +400,10 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_grad_tc(const __grid_constant
     const int64_t ntiles = (p + 127) / 128;
     const int ksteps = 2 * ngroups;
     const int spt = (ksteps + kTcStageSteps - 1) / kTcStageSteps;   // TMA stages per tile
+    // warpgroup w of CTA b takes tiles w gridDim.x + b, then every tile_step on:
+    // a round's tiles go first to one warpgroup of every CTA, so in the last,
+    // partial round every SM keeps some warpgroups busy and each runs faster
+    // with fewer decoders beside it
     const int64_t tile_step = (int64_t)gridDim.x * kTcNWG;
 
     if (tid < kDecoders) {
@@ -462,7 +466,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_grad_tc(const __grid_constant
             return nch <= 2 || put(xc[2], xc[3]);
         };
         const int nfull = ngroups / 4, ntail = ngroups - 4 * nfull;   // stages of a row: full, then the rest
-        for (int64_t tile = (int64_t)blockIdx.x * kTcNWG + w; tile < ntiles && ok; tile += tile_step, ++T) {
+        for (int64_t tile = (int64_t)w * gridDim.x + blockIdx.x; tile < ntiles && ok; tile += tile_step, ++T) {
             const int64_t row = tile * 128 + r;
 #pragma unroll 2
             for (int st = 0; st < nfull && ok; ++st) ok = stage(4);
@@ -490,7 +494,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_grad_tc(const __grid_constant
             int T = 0;
             bool ok = true;
             const int ngrp = (ngroups + 1) / 2;                          // A groups per tile
-            for (int64_t tile = (int64_t)blockIdx.x * kTcNWG + w; tile < ntiles && ok; tile += tile_step, ++T) {
+            for (int64_t tile = (int64_t)w * gridDim.x + blockIdx.x; tile < ntiles && ok; tile += tile_step, ++T) {
                 if (T >= 1) {
                     if (!mbar_wait(&P.accempty, (uint32_t)(T - 1) & 1u)) { abort_flag = 1; ok = false; }
                     tc_fence_after();
@@ -540,7 +544,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_grad_tc(const __grid_constant
         const int w = warp - kProducerWarp;
         TcPipe &P = pipe[w];
         if (lane == 0) {
-            const int64_t first = (int64_t)blockIdx.x * kTcNWG + w;
+            const int64_t first = (int64_t)w * gridDim.x + blockIdx.x;
             const int64_t tiles_w = first < ntiles ? (ntiles - 1 - first) / tile_step + 1 : 0;
             const int64_t total = tiles_w * spt;
             int64_t kk = 0;
