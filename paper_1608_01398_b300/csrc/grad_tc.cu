@@ -357,18 +357,10 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_grad_tc(const __grid_constant
     constexpr int kDecoders = kTcNWG * 128;
     constexpr int kProducerWarp = kTcNWG * 5;          // first TMA warp
 
-    grid_dep_wait();   // the missing-call sums and limb image when launched programmatically
-    if (done && *done) return;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     uint8_t *stages = smem;                      // kTcNWG * nst stages, 1024-aligned
     uint8_t *bsm = smem + kTcNWG * nst * kTcStageTile;   // B image
 
-    {
-        const uint4 *src = reinterpret_cast<const uint4 *>(bimg);
-        uint4 *dst = reinterpret_cast<uint4 *>(bsm);
-        for (int i = tid; i < bbytes / 16; i += blockDim.x) dst[i] = src[i];
-    }
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     if (tid == 0) {
         for (int w = 0; w < kTcNWG; ++w) {
             for (int b = 0; b < nst; ++b) {
@@ -397,7 +389,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_grad_tc(const __grid_constant
     __syncthreads();
     tc_fence_after();
 
-    const int64_t ntiles = (p + 127) / 128;
+    const int64_t ntiles_all = (p + 127) / 128;
     const int ksteps = 2 * ngroups;
     const int spt = (ksteps + kTcStageSteps - 1) / kTcStageSteps;   // TMA stages per tile
     // warpgroup w of CTA b takes tiles w gridDim.x + b, then every tile_step on:
@@ -405,6 +397,54 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_grad_tc(const __grid_constant
     // partial round every SM keeps some warpgroups busy and each runs faster
     // with fewer decoders beside it
     const int64_t tile_step = (int64_t)gridDim.x * kTcNWG;
+
+    // TMA producer state (lane 0 of the producer warps): the panel depends on
+    // nothing the grids before this one write, so each producer fills its
+    // first stages before this grid waits for them
+    const bool producer = warp >= kProducerWarp && lane == 0;
+    const int pw = warp - kProducerWarp;
+    int64_t kk = 0, total = 0, ptile = 0;
+    uint32_t pslot = 0, pphase = 0;
+    int pst = 0;
+    auto issue = [&](int64_t upto) {
+        TcPipe &P = pipe[pw];
+        const uint64_t policy = l2_evict_first();
+        for (; kk < upto && !abort_flag; ++kk) {
+            if (kk >= nst && !mbar_wait(&P.tma_empty[pslot], pphase ^ 1u)) {
+                abort_flag = 1;
+                break;
+            }
+            mbar_expect_tx(&P.tma_full[pslot], kTcStageTile);
+            tma_load_2d(stages + (pw * nst + pslot) * kTcStageTile, &gmap, pst * kTcStageBytes,
+                        (int)(ptile * 128), &P.tma_full[pslot], policy);
+            if (++pslot == (uint32_t)nst) {
+                pslot = 0;
+                pphase ^= 1u;
+            }
+            if (++pst == spt) {
+                pst = 0;
+                ptile += tile_step;
+            }
+        }
+    };
+    if (producer) {
+        const int64_t first = (int64_t)pw * gridDim.x + blockIdx.x;
+        total = first < ntiles_all ? ((ntiles_all - 1 - first) / tile_step + 1) * spt : 0;
+        ptile = first;
+        issue(std::min<int64_t>(total, (int64_t)nst));
+    }
+
+    grid_dep_wait();   // the missing-call sums and limb image when launched programmatically
+    const bool stop = done && *done;             // (the solve has stopped: no pass)
+    if (!stop) {
+        const uint4 *src = reinterpret_cast<const uint4 *>(bimg);
+        uint4 *dst = reinterpret_cast<uint4 *>(bsm);
+        for (int i = tid; i < bbytes / 16; i += blockDim.x) dst[i] = src[i];
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    __syncthreads();
+    const int64_t ntiles = stop ? 0 : ntiles_all;
+    if (stop) total = 0;                         // (the stages already requested are waited for below)
 
     if (tid < kDecoders) {
         // ------------------------------------------------------------ decoders
@@ -541,35 +581,11 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_grad_tc(const __grid_constant
         __syncwarp();
     } else {
         // ------------------------------------------------------------ TMA producers
-        const int w = warp - kProducerWarp;
-        TcPipe &P = pipe[w];
-        if (lane == 0) {
-            const int64_t first = (int64_t)w * gridDim.x + blockIdx.x;
-            const int64_t tiles_w = first < ntiles ? (ntiles - 1 - first) / tile_step + 1 : 0;
-            const int64_t total = tiles_w * spt;
-            int64_t kk = 0;
-            uint32_t slot = 0, phase = 0;
-            int64_t tile = first;
-            int st = 0;
-            const uint64_t policy = l2_evict_first();
-            for (; kk < total && !abort_flag; ++kk) {
-                if (kk >= nst && !mbar_wait(&P.tma_empty[slot], phase ^ 1u)) {
-                    abort_flag = 1;
-                    break;
-                }
-                mbar_expect_tx(&P.tma_full[slot], kTcStageTile);
-                tma_load_2d(stages + (w * nst + slot) * kTcStageTile, &gmap, st * kTcStageBytes,
-                            (int)(tile * 128), &P.tma_full[slot], policy);
-                if (++slot == (uint32_t)nst) {
-                    slot = 0;
-                    phase ^= 1u;
-                }
-                if (++st == spt) {
-                    st = 0;
-                    tile += tile_step;
-                }
-            }
-            // copies still in flight (only after an abort) are waited for, bounded
+        if (producer) {
+            issue(total);
+            // copies still in flight (after an abort, or when the solve had
+            // stopped) are waited for, bounded
+            TcPipe &P = pipe[pw];
             for (int64_t j = kk - nst; j < kk; ++j)
                 if (j >= 0) mbar_wait(&P.tma_full[j % nst], (uint32_t)(j / nst) & 1u);
         }
