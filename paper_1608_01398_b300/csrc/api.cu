@@ -517,13 +517,23 @@ static int fit_impl(iht_dataset *ds, const int32_t *rows, int64_t n_rows, const 
     if ((rc = check_finite_y(ds, n_rows, y_dev))) return rc;
     if ((rc = scatter_rows_f64(ds, rows_dev, n_rows, y_dev, ws->y64))) return rc;
     if ((rc = cov_setup(ds, n_rows))) return rc;
+    ws->out_want = opt.out_mem == IHT_HOST && !trace ? 1 : 0;
+    ws->out_ready = 0;
     rc = run_solve_host(ds, k, &opt, (int)n_rows, trace, opt.max_iter, init);
+    ws->out_want = 0;
     if (rc) return rc;
     const Scalars &h = *ws->sc_host;
     if (opt.out_mem == IHT_DEVICE) {
         if ((rc = write_beta_device(ds, k, beta_out))) return rc;
         IHT_CUDA(cudaMemcpyAsync(support_out, ws->S, sizeof(int32_t) * k, cudaMemcpyDeviceToDevice, s));
         IHT_CUDA(cudaStreamSynchronize(s));
+    } else if (ws->out_ready) {                  // copied with the solve's final scalars
+        ws->out_ready = 0;
+        const int32_t *hS = static_cast<const int32_t *>(ws->out_host);
+        const double *hb = reinterpret_cast<const double *>(hS + kMaxK);
+        memcpy(support_out, hS, sizeof(int32_t) * k);
+        if (!(opt.flags & IHT_FIT_BETA_ZEROED)) memset(beta_out, 0, sizeof(double) * P);
+        for (int c = 0; c < k; ++c) beta_out[hS[c]] = hb[c];
     } else {
         double *bS = (double *)malloc(sizeof(double) * k);
         if (!bS) return IHT_ENOMEM;

@@ -245,6 +245,11 @@ struct Workspace {
     int fused_setup_launches = 0;          // kernels ahead of the loop (whole-solve graph)
     Scalars *sc_init = nullptr;            // device: a whole-solve graph's starting scalars
     int32_t *flags_host = nullptr;         // pinned: barrier and pass error words after a solve
+    // pinned: a whole solve's support (kMaxK int32) then beta_S (kMaxK doubles),
+    // copied with its final scalars ahead of its one synchronisation when the
+    // caller wants host outputs (out_want); out_ready: they are there
+    void *out_host = nullptr;
+    int out_want = 0, out_ready = 0;
 };
 constexpr int kProfEvents = 256;
 

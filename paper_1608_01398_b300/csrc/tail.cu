@@ -517,6 +517,8 @@ void free_fused(Workspace *ws)
     for (void *x : ptrs)
         if (x) cudaFree(x);
     if (ws->flags_host) cudaFreeHost(ws->flags_host);
+    if (ws->out_host) cudaFreeHost(ws->out_host);
+    ws->out_host = nullptr;
     ws->fused_exec = nullptr;
     ws->tail = nullptr;
     ws->Sp2 = nullptr;
@@ -777,6 +779,13 @@ int run_whole_fused_solve(iht_dataset *ds, int k, int K, int impl, const Scalars
             return e == cudaErrorMemoryAllocation ? IHT_ENOMEM : IHT_ECUDA;
         }
     }
+    if (ws->out_want && !ws->out_host) {
+        const cudaError_t e = cudaMallocHost(&ws->out_host, (size_t)kMaxK * (sizeof(int32_t) + sizeof(double)));
+        if (e != cudaSuccess) {
+            set_cuda_error(e, "pinned outputs");
+            return e == cudaErrorMemoryAllocation ? IHT_ENOMEM : IHT_ECUDA;
+        }
+    }
     // (the first solve of a panel tunes its pass outside a graph)
     if (!grad_tc_shape_settled(ds)) return IHT_EAGAIN;
     TcParams *prm = nullptr;
@@ -792,7 +801,14 @@ int run_whole_fused_solve(iht_dataset *ds, int k, int K, int impl, const Scalars
     IHT_CUDA(cudaMemcpyAsync(&ws->flags_host[0], &ws->tail->bar_err, sizeof(int32_t),
                              cudaMemcpyDeviceToHost, s));
     IHT_CUDA(cudaMemcpyAsync(&ws->flags_host[1], &prm->err, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    if (ws->out_want) {                                  // the host outputs, before the same synchronisation
+        int32_t *hS = static_cast<int32_t *>(ws->out_host);
+        IHT_CUDA(cudaMemcpyAsync(hS, ws->S, sizeof(int32_t) * k, cudaMemcpyDeviceToHost, s));
+        IHT_CUDA(cudaMemcpyAsync(reinterpret_cast<double *>(hS + kMaxK), ws->bS, sizeof(double) * k,
+                                 cudaMemcpyDeviceToHost, s));
+    }
     IHT_CUDA(cudaStreamSynchronize(s));
+    ws->out_ready = ws->out_want;
     note_launch(ws->fused_setup_launches + ws->fused_launches * std::max(ws->sc_host->iter, 1));
     return (ws->flags_host[0] || ws->flags_host[1]) ? IHT_ETIMEOUT : IHT_OK;
 }
