@@ -9,6 +9,7 @@ missing.  PyTorch supplies device memory and the current CUDA stream.
 from __future__ import annotations
 
 import ctypes
+import mmap
 import os
 from dataclasses import dataclass
 
@@ -369,6 +370,16 @@ class FitResult:
     graph_replays: int = 0
 
 
+def _zeroed_f64(n: int) -> np.ndarray:
+    """n zero doubles.  Large ones come from an anonymous mapping: its pages
+    are zero until written, so a mostly-zero result (a k-sparse beta) costs a
+    page fault per written page instead of clearing the whole array (a heap
+    allocation that calloc must clear)."""
+    if n * 8 < (1 << 20):
+        return np.zeros(n)
+    return np.frombuffer(mmap.mmap(-1, n * 8), dtype=np.float64)
+
+
 def _fit(ds: Dataset, y, k: int, rows, opts: iht_options, trace: bool, state: bytes = None):
     torch = _torch()
     dev_in = isinstance(y, torch.Tensor)
@@ -392,7 +403,7 @@ def _fit(ds: Dataset, y, k: int, rows, opts: iht_options, trace: bool, state: by
         supp = torch.empty(k, dtype=torch.int32, device=f"cuda:{ds.ctx.device}")
         bp, sp = beta.data_ptr(), supp.data_ptr()
     else:
-        beta = np.zeros(P)                # zero pages: the library writes the support only
+        beta = _zeroed_f64(P)             # zero pages: the library writes the support only
         opts.flags |= IHT_FIT_BETA_ZEROED
         supp = np.empty(k, dtype=np.int32)
         bp, sp = beta.ctypes.data, supp.ctypes.data
