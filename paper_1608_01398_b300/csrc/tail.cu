@@ -29,6 +29,7 @@ namespace iht {
 constexpr int kTailThreads = kZmulThreads;    // one 128-sample block of the sparse product per pass
 constexpr int kTailKM = 256;                  // largest k of the fused path
 constexpr int kTailKept = 1024;               // candidates the selection's narrow finish sorts
+constexpr int kFusedUnroll = 2;               // iterations per trip of the fused solve's conditional loop
 constexpr uint32_t kBarSpin = 1u << 22;       // bounded barrier waits (polls; sleeps up to 256 ns each)
 
 struct TailWork {                     // zeroed before every solve
@@ -624,21 +625,27 @@ static int build_fused_graph(iht_dataset *ds, int k, int K, int impl, const Tail
         at[0].val.cooperative = 1;
         lc.attrs = at;
         lc.numAttrs = 1;
-        e = cudaLaunchKernelEx(&lc, k_tail, a);
-        note_launch();
-        if (e != cudaSuccess) {
-            set_cuda_error(e, "fused iteration launch");
-            rc = IHT_ECUDA;
-        }
+        // kFusedUnroll iterations per trip of the conditional loop (a trip's
+        // relaunch of the body costs more than a few kernels that return at
+        // once after the solve has stopped)
         const int32_t *done = &ws->sc->done;
-        if (rc == IHT_OK)
-            rc = launch_missing_sums_limbs(ds, ws->r32, ws->Mj, done, args.bimg, args.prm, args.nlim, true);
         // the pass counts its keys into the next trip's histogram unless the
         // kernel forms it itself
         uint32_t *hist = args.own_hist ? nullptr : ws->tail->hist;
         uint32_t *hflag = args.own_hist ? nullptr : &ws->tail->st.err;
-        if (rc == IHT_OK) rc = launch_grad_tc_main(ds, ws->r32, ws->g, done, hist, hflag, true);
-        if (rc == IHT_OK) rc = launch_cov_grad(ds, ws->r32, ws->g, done, hist, hflag);
+#pragma unroll 1
+        for (int u = 0; u < kFusedUnroll && rc == IHT_OK; ++u) {
+            e = cudaLaunchKernelEx(&lc, k_tail, a);
+            note_launch();
+            if (e != cudaSuccess) {
+                set_cuda_error(e, "fused iteration launch");
+                rc = IHT_ECUDA;
+            }
+            if (rc == IHT_OK)
+                rc = launch_missing_sums_limbs(ds, ws->r32, ws->Mj, done, args.bimg, args.prm, args.nlim, true);
+            if (rc == IHT_OK) rc = launch_grad_tc_main(ds, ws->r32, ws->g, done, hist, hflag, true);
+            if (rc == IHT_OK) rc = launch_cov_grad(ds, ws->r32, ws->g, done, hist, hflag);
+        }
         cudaGraph_t captured = nullptr;
         const cudaError_t e2 = cudaStreamEndCapture(ws->cap_stream, &captured);
         if (rc == IHT_OK && e2 != cudaSuccess) {
@@ -661,7 +668,7 @@ static int build_fused_graph(iht_dataset *ds, int k, int K, int impl, const Tail
         }
     }
     cudaGraphDestroy(graph);
-    if (rc == IHT_OK) ws->fused_launches = n;
+    if (rc == IHT_OK) ws->fused_launches = n / kFusedUnroll;   // per iteration
     (void)k;
     (void)K;
     return rc;
