@@ -307,11 +307,13 @@ __device__ __forceinline__ void sel_rank_finish(const unsigned long long *w, int
 __device__ __forceinline__ void sel_finish(const float *keys, int64_t p, const SelState *st,
                                            const unsigned long long *cand, uint32_t ncand,
                                            int32_t *out, uint32_t K, unsigned long long *sk,
-                                           uint32_t *wsum)
+                                           uint32_t *wsum, bool staged = false)
 {
     if (ncand <= (uint32_t)kSelRank) {
+        // (staged: the caller has copied the words into sk already)
+        if (!staged)
 #pragma unroll 1
-        for (int i = threadIdx.x; i < (int)ncand; i += blockDim.x) sk[i] = __ldcg(&cand[i]);
+            for (int i = threadIdx.x; i < (int)ncand; i += blockDim.x) sk[i] = __ldcg(&cand[i]);
         __syncthreads();
         sel_rank_finish(sk, (int)ncand, out, K);
         return;
@@ -359,12 +361,12 @@ __device__ __forceinline__ void sel_finish(const float *keys, int64_t p, const S
 __device__ __forceinline__ void sel_finish_narrow(const float *keys, int64_t p, const SelState *st,
                                                   const unsigned long long *cand, uint32_t ncand,
                                                   int32_t *out, uint32_t K, unsigned long long *sk,
-                                                  int extra, uint32_t *wsum)
+                                                  int extra, uint32_t *wsum, bool staged = false)
 {
     __shared__ uint32_t h[1024];
     __shared__ uint32_t res[3];
     if (ncand <= (uint32_t)kSelRank || ncand > (uint32_t)kSelCap) {
-        sel_finish(keys, p, st, cand, ncand, out, K, sk, wsum);
+        sel_finish(keys, p, st, cand, ncand, out, K, sk, wsum, staged && ncand <= (uint32_t)kSelRank);
         return;
     }
     const uint32_t bin = st->prefix >> 20;

@@ -298,6 +298,17 @@ __global__ void __launch_bounds__(kTailThreads) k_tail(const __grid_constant__ T
                 reinterpret_cast<unsigned long long *>(&ssc)[tid] =
                     reinterpret_cast<const volatile unsigned long long *>(sc)[tid];
             const uint32_t ncand = res[1] + res[2];
+            // the candidate words (when few enough to rank) requested first,
+            // into registers, so their loads and S's are in flight together
+            static_assert(4 * kTailThreads >= kSelRank, "four candidate words per thread");
+            const bool stage_cand = ncand <= (uint32_t)kSelRank;
+            unsigned long long cw[4] = {0ull, 0ull, 0ull, 0ull};
+            if (stage_cand)
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const int i = tid + q * kTailThreads;
+                    if (i < (int)ncand) cw[q] = __ldcg(&T->cand[i]);
+                }
             // S, beta_S and g_S into shared memory for the projection, and the
             // genotype bytes of this block's residual on their way to L2, while
             // the candidates are chosen (S+ mostly repeats S)
@@ -313,8 +324,17 @@ __global__ void __launch_bounds__(kTailThreads) k_tail(const __grid_constant__ T
                     if (j < A.p) asm volatile("prefetch.global.L2 [%0];" ::"l"(gb + (int64_t)j * A.stride));
                 }
             }
+            if (stage_cand) {
+                unsigned long long *sk = reinterpret_cast<unsigned long long *>(smem_raw);
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const int i = tid + q * kTailThreads;
+                    if (i < (int)ncand) sk[i] = cw[q];
+                }
+            }
             sel_finish_narrow(A.g, A.P, &T->st, T->cand, ncand, s_cand, (uint32_t)A.K,
-                              reinterpret_cast<unsigned long long *>(smem_raw), kTailKept, wsum);
+                              reinterpret_cast<unsigned long long *>(smem_raw), kTailKept, wsum,
+                              stage_cand);
             __syncthreads();
             if (tid == 0) ssc.num = *(volatile double *)&T->num;    // the step size's numerator
             __syncthreads();
