@@ -57,7 +57,7 @@ FALLBACK_HBM_GBS = 6400.0
 # n = 5000, p = 500 000 panel, from one ncu capture of this kernel version
 # at the tuned stage count (dram__bytes_read.sum + dram__bytes_write.sum;
 # summary in profiles/).
-K1_TRAFFIC_BYTES = 646210560 + 3859200
+K1_TRAFFIC_BYTES = 646192384 + 3213568
 # The same for the first multi-column launch of the cross-validation batch
 # (44 residual columns of the 100 solves, the widest pass).
 K2_TRAFFIC_FIRST_LAUNCH_BYTES = 1538364416 + 167354112
